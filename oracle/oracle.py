@@ -1,0 +1,184 @@
+"""Python access to the FP64 CPU oracle (``cfs_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the oracle is the plain, slow reference the CUDA library is checked
+against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import this module.  It shares no code with the product library; it is compiled with gcc from
+its single C file and loaded with ctypes.
+
+Every function cites the passage of arXiv 2506.03027 it restates (see the C file's header).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cfs_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libcfs_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class OrParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("px", ctypes.c_int), ("py", ctypes.c_int), ("pz", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("mach", ctypes.c_double), ("re", ctypes.c_double),
+        ("pr", ctypes.c_double),
+        ("viscous", ctypes.c_int), ("visc_law", ctypes.c_int), ("visc_exp", ctypes.c_double),
+        ("order", ctypes.c_int), ("algo", ctypes.c_int), ("at", ctypes.c_int),
+        ("caa_L", ctypes.c_int), ("kmax", ctypes.c_int),
+        ("filter", ctypes.c_int), ("alpha_f", ctypes.c_double), ("dt", ctypes.c_double),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C99 + optional OpenMP); returns the library path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER
+            d = P(ctypes.c_double)
+            lib.or_run.argtypes = [P(OrParams), d, P(ctypes.c_int8), ctypes.c_long, ctypes.c_long, d, d]
+            lib.or_run.restype = ctypes.c_int
+            lib.or_rhs.argtypes = [P(OrParams), d, d]
+            lib.or_rhs.restype = ctypes.c_int
+            lib.or_diagnostics.argtypes = [P(OrParams), d, d]
+            lib.or_extrap_weights.argtypes = [ctypes.c_int, ctypes.c_double, d]
+            lib.or_buffer_dudt.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, d]
+            lib.or_nu.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            lib.or_nu.restype = ctypes.c_double
+            lib.or_lserk.argtypes = [ctypes.c_int, d, d]
+            lib.or_lserk.restype = ctypes.c_int
+            lib.or_filter_coeffs.argtypes = [ctypes.c_double, d]
+            lib.or_filter_line.argtypes = [ctypes.c_int, ctypes.c_double, d, d]
+            lib.or_num_threads.restype = ctypes.c_int
+            lib.or_set_num_threads.argtypes = [ctypes.c_int]
+            _lib = lib
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+ALGOS = {"SA": 0, "CAA": 1, "SAA": 2}
+
+
+def params(case) -> OrParams:
+    """Translate a ``inputs.Case`` description into the oracle's parameter struct."""
+    return OrParams(
+        nx=case.nx, ny=case.ny, nz=case.nz, px=case.px, py=case.py, pz=case.pz,
+        dx=case.dx, dy=case.dy, dz=case.dz, gamma=case.gamma, mach=case.mach, re=case.re,
+        pr=case.pr, viscous=int(case.viscous), visc_law=int(case.visc_law),
+        visc_exp=case.visc_exp, order=case.order, algo=ALGOS[case.algo], at=int(case.at),
+        caa_L=case.caa_L, kmax=case.kmax, filter=int(case.filter), alpha_f=case.alpha_f,
+        dt=case.dt)
+
+
+def run(case, U0: np.ndarray, nsteps: int, delays: np.ndarray | None = None, n0: int = 0,
+        hist: np.ndarray | None = None, diag: bool = False):
+    """Advance ``nsteps`` steps of the method (Alg. 1-3 with Eq. 3, 8, 14-15); returns U
+    (and the per-step diagnostics [nsteps][8] if ``diag``)."""
+    lib = _load()
+    p = params(case)
+    U = np.ascontiguousarray(U0, dtype=np.float64).copy()
+    if delays is None:
+        dl = np.zeros(1, dtype=np.int8)
+    else:
+        dl = np.ascontiguousarray(delays, dtype=np.int8)
+    hp = None if hist is None else _dptr(np.ascontiguousarray(hist, dtype=np.float64))
+    dg = np.zeros((max(nsteps, 1), 8), dtype=np.float64) if diag else None
+    rc = lib.or_run(ctypes.byref(p), _dptr(U), dl.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                    n0, nsteps, hp, _dptr(dg) if diag else None)
+    if rc != 0:
+        raise ValueError(f"oracle rejected the case (code {rc})")
+    return (U, dg[:nsteps]) if diag else U
+
+
+def rhs(case, U: np.ndarray) -> np.ndarray:
+    """R(U) of Eq. 1 with synchronous halos (the CD right-hand side of the whole field)."""
+    lib = _load()
+    p = params(case)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    R = np.zeros_like(U)
+    if lib.or_rhs(ctypes.byref(p), _dptr(U), _dptr(R)) != 0:
+        raise ValueError("oracle rejected the case")
+    return R
+
+
+def diagnostics(case, U: np.ndarray) -> np.ndarray:
+    """[K, enstrophy, sum rho, sum rho u, sum rho v, sum rho w, sum rho E, nan-flag]."""
+    lib = _load()
+    p = params(case)
+    out = np.zeros(8)
+    lib.or_diagnostics(ctypes.byref(p), _dptr(np.ascontiguousarray(U, dtype=np.float64)), _dptr(out))
+    return out
+
+
+def extrap_weights(order: int, k: float) -> np.ndarray:
+    """Eq. 14 (order 2) / Eq. 15 (order 4)."""
+    c = np.zeros(5)
+    _load().or_extrap_weights(order, float(k), _dptr(c))
+    return c[: (5 if order == 4 else 3)]
+
+
+def buffer_dudt(order: int, e: int, k: float) -> np.ndarray:
+    """App. C: dt * dphi/dt at stage e as weights on levels n-k, n-k-1, ..."""
+    d = np.zeros(5)
+    _load().or_buffer_dudt(order, e, float(k), _dptr(d))
+    return d[: (5 if order == 4 else 3)]
+
+
+def nu(order: int, e: int, j: int) -> float:
+    """Eq. 10: nu_j^e."""
+    return _load().or_nu(order, e, j)
+
+
+def lserk(order: int):
+    """Table 4 / App. B LSERK coefficients (A, B)."""
+    A = np.zeros(5)
+    B = np.zeros(5)
+    s = _load().or_lserk(order, _dptr(A), _dptr(B))
+    return A[:s], B[:s]
+
+
+def filter_coeffs(alpha: float) -> np.ndarray:
+    a = np.zeros(6)
+    _load().or_filter_coeffs(alpha, _dptr(a))
+    return a
+
+
+def filter_line(alpha: float, f: np.ndarray) -> np.ndarray:
+    """Filter one line: f holds n values plus 5 halo values on each side."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    n = f.size - 10
+    out = np.zeros(n)
+    _load().or_filter_line(n, alpha, _dptr(f), _dptr(out))
+    return out
+
+
+def num_threads() -> int:
+    return _load().or_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    _load().or_set_num_threads(n)

@@ -1,0 +1,392 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: textbook definitions (Lagrange
+extrapolation, Taylor order conditions of RK methods, the continuous Navier-Stokes operator
+differentiated symbolically), closed forms (modified wavenumbers, exact translating vortex),
+invariants (discrete conservation, polynomial reproduction of the filter) and the orders of
+accuracy of Table 1.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2506_03027_gb300 import inputs as I
+
+
+# ------------------------------------------------------------------ coefficient tables
+
+def lagrange_at_zero(nodes):
+    """Lagrange basis weights evaluating at t = 0 from samples at the given times (textbook)."""
+    w = []
+    for i, ti in enumerate(nodes):
+        num = 1.0
+        den = 1.0
+        for j, tj in enumerate(nodes):
+            if j != i:
+                num *= (0.0 - tj)
+                den *= (ti - tj)
+        w.append(num / den)
+    return np.array(w)
+
+
+@pytest.mark.parametrize("order,C", [(2, 3), (4, 5)])
+@pytest.mark.parametrize("k", range(0, 9))
+def test_extrapolation_weights_are_lagrange(order, C, k):
+    """Eq. 14/15: polynomial extrapolation to t_n from levels n-k-l (l = 0..C-1)."""
+    c = orc.extrap_weights(order, k)
+    ref = lagrange_at_zero([-(k + l) for l in range(C)])
+    np.testing.assert_allclose(c, ref, rtol=1e-13, atol=1e-12 * max(1.0, np.abs(ref).max()))
+    assert abs(c.sum() - 1.0) < 1e-12 * np.abs(c).sum()
+
+
+def test_zero_delay_extrapolation_is_identity():
+    """c~(0) = e_0 exactly (printed polynomials at k = 0)."""
+    for order in (2, 4):
+        c = orc.extrap_weights(order, 0)
+        assert c[0] == 1.0 and np.all(c[1:] == 0.0)
+
+
+def stage_polynomials(A, B):
+    """Stage polynomials P_e(z) of the 2N-storage RK of Eq. 3 applied to y' = z y (coefficient
+    lists, lowest power first), computed with numpy polynomial arithmetic."""
+    P = np.polynomial.Polynomial([1.0])
+    Q = np.polynomial.Polynomial([0.0])
+    z = np.polynomial.Polynomial([0.0, 1.0])
+    out = [P]
+    for a, b in zip(A, B):
+        Q = a * Q + z * P
+        P = P + b * Q
+        out.append(P)
+    return out
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_lserk_order_conditions(order):
+    """Table 4 / App. B: the full step reproduces e^z to the stated order (exactly for LSERK2,
+    to the 8 printed digits, about 5e-8, for LSERK4)."""
+    A, B = orc.lserk(order)
+    s = len(A)
+    for j in range(order + 1):
+        assert abs(orc.nu(order, s, j) - 1.0 / math.factorial(j)) < (1e-15 if order == 2 else 1e-7)
+
+
+def test_nu_matches_paper_closed_forms():
+    """Eq. 10: nu_1^e = sum B + sum A_j B_j + ... (first-order coefficient) and nu_e^e = prod B_j."""
+    A, B = orc.lserk(4)
+    polys = stage_polynomials(A, B)
+    for e in range(1, 5):
+        coef = polys[e].coef
+        for j in range(0, e + 1):
+            assert abs(orc.nu(4, e, j) - (coef[j] if j < len(coef) else 0.0)) < 1e-15
+        assert abs(orc.nu(4, e, e) - np.prod(B[:e])) < 1e-16
+    # first-order coefficient written out as in Eq. 10 for e = 3:
+    # nu_1^3 = B1 + B2 + B3 + A2 B2 + A3 B3 + A2 A3 B3
+    n13 = B[0] + B[1] + B[2] + A[1] * B[1] + A[2] * B[2] + A[1] * A[2] * B[2]
+    assert abs(orc.nu(4, 3, 1) - n13) < 1e-15
+
+
+@pytest.mark.parametrize("e", [0, 1, 2, 3])
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 4])
+def test_buffer_derivative_satisfies_eq13(e, k):
+    """App. C / Table 5 polynomials solve the Taylor constraints of Eq. 13 with (q, r) = (4, 1)."""
+    d = orc.buffer_dudt(4, e, k)
+    for th in range(0, 5):
+        s = sum(d[l] * (-(k + l)) ** th / math.factorial(th) for l in range(5))
+        tgt = orc.nu(4, e, th - 1) if 1 <= th <= e + 1 else 0.0
+        assert abs(s - tgt) < 1e-11 * max(1.0, np.abs(d).sum())
+
+
+def test_buffer_derivative_order2():
+    for k in range(5):
+        d = orc.buffer_dudt(2, 0, k)
+        for th, tgt in [(0, 0.0), (1, 1.0), (2, 0.0)]:
+            s = sum(d[l] * (-(k + l)) ** th / math.factorial(th) for l in range(3))
+            assert abs(s - tgt) < 1e-12
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("k", [0, 1, 3])
+def test_buffer_machinery_tracks_rk_stages(order, k):
+    """Stage-0 extrapolation plus the buffer updates of Eq. 8, fed with samples of e^{lambda t}
+    at the delayed levels, reproduce the LSERK stage values of y' = lambda y; the local error
+    falls as dt^{q/r+1}."""
+    A, B = orc.lserk(order)
+    C = 5 if order == 4 else 3
+    s = len(A)
+    lam = -0.7 + 1.3j
+    errs = []
+    for dt in (0.04, 0.02, 0.01):
+        lev = [np.exp(lam * (-(k + l)) * dt) for l in range(C)]  # y(t_n) = 1
+        ub = np.dot(orc.extrap_weights(order, k), lev)
+        qb = 0.0
+        # exact stage values of the RK scheme on y' = lam y
+        y = 1.0 + 0j
+        qy = 0.0
+        err = abs(ub - y)
+        for m in range(1, s):
+            qy = A[m - 1] * qy + dt * lam * y
+            y = y + B[m - 1] * qy
+            qb = A[m - 1] * qb + np.dot(orc.buffer_dudt(order, m - 1, k), lev)
+            ub = ub + B[m - 1] * qb
+            err = max(err, abs(ub - y))
+        errs.append(err)
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates.min() > (order + 1) - 0.6, (errs, rates)
+
+
+# ------------------------------------------------------------------ filter
+
+def test_filter_transfer_function():
+    """Tenth-order Pade filter: T(0) = 1, T(pi) = 0, 1 - T(w) = O(w^10)."""
+    for al in (0.0, 0.3, 0.45, 0.499):
+        a = orc.filter_coeffs(al)
+
+        def T(w):
+            return sum(a[n] * math.cos(n * w) for n in range(6)) / (1.0 + 2.0 * al * math.cos(w))
+        assert abs(T(0.0) - 1.0) < 1e-14
+        # numerator of T at the Nyquist wavenumber (the denominator 1 - 2 alpha is tiny near 0.5)
+        assert abs(sum(a[n] * (-1) ** n for n in range(6))) < 1e-15
+        # local slope of log(1 - T) against log w tends to 10 (tenth-order filter)
+        slope = math.log((1.0 - T(0.6)) / (1.0 - T(0.4))) / math.log(0.6 / 0.4)
+        assert abs(slope - 10.0) < 0.3, slope  # an 8th-order filter would give about 8
+
+
+@pytest.mark.parametrize("deg", [0, 1, 4, 9])
+def test_filter_line_reproduces_polynomials(deg):
+    """A tenth-order filter leaves polynomials of degree <= 9 unchanged (with the Dirichlet
+    closure holding the exact values at the first halo point)."""
+    n = 17
+    t = np.arange(-5, n + 5, dtype=np.float64) / n
+    f = t ** deg - 0.3 * t ** max(deg - 1, 0) + 0.1
+    out = orc.filter_line(0.499, f)
+    np.testing.assert_allclose(out, f[5:5 + n], rtol=0, atol=1e-11)
+
+
+def test_filter_line_matches_dense_solve():
+    """Brute force on a tiny line: assemble the tridiagonal system densely and solve it."""
+    rng = np.random.default_rng(7)
+    n, al = 9, 0.4
+    f = rng.standard_normal(n + 10)
+    a = orc.filter_coeffs(al)
+    M = np.eye(n) + al * (np.eye(n, k=1) + np.eye(n, k=-1))
+    rhs = np.array([a[0] * f[5 + i] + sum(0.5 * a[m] * (f[5 + i + m] + f[5 + i - m]) for m in range(1, 6))
+                    for i in range(n)])
+    rhs[0] -= al * f[4]
+    rhs[-1] -= al * f[5 + n]
+    np.testing.assert_allclose(orc.filter_line(al, f), np.linalg.solve(M, rhs), rtol=1e-13, atol=1e-13)
+
+
+# ------------------------------------------------------------------ right-hand side
+
+def continuous_rhs(case, viscous):
+    """The exact (continuous) right-hand side of Eq. 1 for the Taylor-Green initial field, from the
+    textbook tensor form of the Navier-Stokes equations, differentiated symbolically."""
+    sp = pytest.importorskip("sympy")
+    x, y, z = sp.symbols("x y z", real=True)
+    g, M, Re, Pr = case.gamma, case.mach, case.re, case.pr
+    gm2 = g * M ** 2
+    vel = [sp.sin(x) * sp.cos(y) * sp.cos(z), -sp.cos(x) * sp.sin(y) * sp.cos(z), sp.Integer(0)]
+    p = 1 / gm2 + (sp.cos(2 * x) + sp.cos(2 * y)) * (sp.cos(2 * z) + 2) / 16
+    rho = gm2 * p
+    T = gm2 * p / rho
+    X = [x, y, z]
+    rhoE = p / (g - 1) + rho * sum(v ** 2 for v in vel) / 2
+    out = []
+    # conservative fluxes and the stress tensor written in vector form
+    grad = [[sp.diff(vel[i], X[j]) for j in range(3)] for i in range(3)]
+    div = sum(grad[i][i] for i in range(3))
+    mu = 1
+    tau = [[mu * (grad[i][j] + grad[j][i]) - sp.Rational(2, 3) * mu * div * (1 if i == j else 0)
+            for j in range(3)] for i in range(3)]
+    heat = [mu / ((g - 1) * Pr * M ** 2) * sp.diff(T, X[i]) for i in range(3)]
+    cons_flux = []
+    cons_flux.append([rho * vel[a] for a in range(3)])
+    for c in range(3):
+        cons_flux.append([rho * vel[c] * vel[a] + (p if a == c else 0) for a in range(3)])
+    cons_flux.append([(rhoE + p) * vel[a] for a in range(3)])
+    visc_flux = [[0, 0, 0]] + [[tau[a][c] for a in range(3)] for c in range(3)]
+    visc_flux.append([sum(vel[j] * tau[a][j] for j in range(3)) + heat[a] for a in range(3)])
+    for v in range(5):
+        r = -sum(sp.diff(cons_flux[v][a], X[a]) for a in range(3))
+        if viscous:
+            r += sum(sp.diff(visc_flux[v][a], X[a]) for a in range(3)) / Re
+        out.append(sp.lambdify((x, y, z), r, "numpy"))
+    return out
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+@pytest.mark.parametrize("order", [4, 2])
+def test_rhs_converges_to_continuous_operator(viscous, order):
+    """The discrete R(U) of the oracle (CD2/CD4 derivatives, Eq. A2-A4 fluxes, sub-domain halos)
+    converges to the exact Navier-Stokes operator at the scheme's order (TGV field at t = 0)."""
+    errs = []
+    fns = None
+    ns = (16, 32) if order == 4 else (16, 32)
+    for n in ns:
+        c = I.tgv_case(n, 2, "SA", viscous=viscous, order=order, filter=False)
+        if fns is None:
+            fns = continuous_rhs(c, viscous)
+        x, y, z = I.grid(c)
+        Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+        R = orc.rhs(c, I.tgv_state(c))
+        e = 0.0
+        for v in range(5):
+            ex = np.broadcast_to(fns[v](X, Y, Z), R[v].shape)
+            e = max(e, np.abs(R[v] - ex).max())
+        errs.append(e)
+    rate = math.log2(errs[0] / errs[1])
+    assert abs(rate - order) < 0.35, (errs, rate)
+
+
+def test_decomposed_sa_equals_single_domain():
+    """SA with P sub-domains and periodic halos is the same computation as one domain."""
+    c1 = I.tgv_case(16, 1, "SA", filter=False, nx=16, ny=16, nz=16)
+    c8 = c1.replace(px=2, py=2, pz=2)
+    c_rag = c1.replace(nx=18, ny=17, nz=16, px=3, py=2, pz=2)
+    U = I.tgv_state(c1)
+    np.testing.assert_array_equal(orc.run(c1, U, 3), orc.run(c8, U, 3))
+    c_rag1 = c_rag.replace(px=1, py=1, pz=1)
+    Ur = I.tgv_state(c_rag)
+    np.testing.assert_array_equal(orc.run(c_rag1, Ur, 2), orc.run(c_rag, Ur, 2))
+
+
+def test_conservation_periodic_sa():
+    """Central differences telescope on a periodic grid: totals of all conserved variables stay
+    constant to roundoff (SA, filter off)."""
+    c = I.tgv_case(16, 2, "SA", filter=False)
+    U0 = I.tgv_state(c)
+    U = orc.run(c, U0, 10)
+    d0 = orc.diagnostics(c, U0)
+    d1 = orc.diagnostics(c, U)
+    scale = np.abs(U0).reshape(5, -1).sum(axis=1) * c.dx * c.dy * c.dz
+    scale = np.maximum(scale, scale[1])  # rho w is zero at t = 0: measure it on the momentum scale
+    assert np.all(np.abs(d1[2:7] - d0[2:7]) < 1e-13 * scale), (d1[2:7] - d0[2:7]) / scale
+
+
+def test_diagnostics_closed_form_at_t0():
+    """K(0) of the TGV field is exactly 1/8 (the density correction averages out), and the
+    CD4 enstrophy equals the exact vorticity scaled by the modified wavenumber of mode 1."""
+    c = I.tgv_case(24, 2, "SA", filter=False)
+    U = I.tgv_state(c)
+    d = orc.diagnostics(c, U)
+    assert abs(d[0] - 0.125) < 1e-15
+    x, y, z = I.grid(c)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    h = c.dx
+    kp = ((4 / 3) * math.sin(h) - (1 / 6) * math.sin(2 * h)) / h  # CD4 modified wavenumber, mode 1
+    wx = -np.cos(X) * np.sin(Y) * np.sin(Z)
+    wy = -np.sin(X) * np.cos(Y) * np.sin(Z)
+    wz = 2 * np.sin(X) * np.sin(Y) * np.cos(Z)
+    ens = np.mean(0.5 * U[0] * (wx ** 2 + wy ** 2 + wz ** 2)) * kp ** 2
+    assert abs(d[1] - ens) < 1e-13
+
+
+def test_tgv_initial_dissipation_rate():
+    """dK/dt(0) of the TGV is close to -2 eps(0)/Re = -(3/4)/Re (incompressible estimate)."""
+    c = I.tgv_case(32, 2, "SA", filter=False)
+    c.dt = c.dt / 4
+    U0 = I.tgv_state(c)
+    U, dg = orc.run(c, U0, 2, diag=True)
+    rate = (dg[1, 0] - dg[0, 0]) / c.dt
+    assert abs(rate / (-0.75 / 1600.0) - 1.0) < 0.03, rate
+
+
+# ------------------------------------------------------------------ orders of accuracy (Table 1)
+
+def vortex_run(order, algo, at, n, T=0.5, cfl=0.2, kmax=2, L=4):
+    c = I.vortex_case(n, 2, lx=16.0, ly=16.0, order=order)
+    dt0 = I.cfl_dt(c, I.vortex_state(c), cfl)
+    ns = int(math.ceil(T / dt0))
+    c = c.replace(dt=T / ns, algo=algo, at=at, kmax=kmax, caa_L=L)
+    d = I.saa_delays(c, ns) if algo == "SAA" else None
+    return c, orc.run(c, I.vortex_state(c), ns, delays=d)
+
+
+@pytest.mark.parametrize("order", [4, 2])
+def test_vortex_order_of_accuracy(order):
+    """Synchronous runs (Table 1 cases 1 and 4) converge to the exact translated vortex at the
+    scheme's order."""
+    e = []
+    for n in ((96, 192) if order == 4 else (64, 128)):
+        c, U = vortex_run(order, "SA", True, n, cfl=0.4)
+        ex = I.vortex_state(c, t=0.5)
+        e.append(math.sqrt(np.mean((U[0] - ex[0]) ** 2)))
+    rate = math.log2(e[0] / e[1])
+    assert abs(rate - order) < 0.35, (e, rate)
+
+
+@pytest.mark.parametrize("order,algo,at,cfl,kmax,lo,hi", [
+    (4, "CAA", True, 0.2, 0, 3.5, 99),   # case 6, CAA-AT: asynchrony error at least 4th order
+    (4, "SAA", True, 0.2, 1, 3.5, 99),   # case 6, SAA-AT
+    (4, "CAA", False, 0.2, 0, 0.8, 1.2),  # case 5, CAA-AS: first order
+    (4, "SAA", False, 0.2, 2, 0.8, 1.2),  # case 5, SAA-AS
+    (2, "CAA", True, 0.2, 0, 1.8, 99),   # case 3, CAA-AT: at least 2nd order
+    (2, "SAA", True, 0.2, 2, 1.8, 99),   # case 3, SAA-AT
+    (2, "CAA", False, 0.2, 0, 0.8, 1.2),  # case 2
+])
+def test_async_error_order(order, algo, at, cfl, kmax, lo, hi):
+    """The error the delays add (asynchronous run minus the synchronous run at the same
+    resolution and step) falls at the AT scheme's order, and at first order for AS (Table 1,
+    Sec. 5.1)."""
+    e = []
+    for n in (64, 128):
+        _, Ua = vortex_run(order, algo, at, n, cfl=cfl, kmax=kmax)
+        _, Us = vortex_run(order, "SA", True, n, cfl=cfl)
+        e.append(math.sqrt(np.mean((Ua[0] - Us[0]) ** 2)))
+    assert e[1] > 0
+    rate = math.log2(e[0] / e[1])
+    assert lo < rate < hi, (e, rate)
+
+
+def test_zero_delay_at_reduces_to_sa():
+    """AT with all delays 0: the difference from SA is the buffer-update truncation error only,
+    vanishing at least like dx^4 at fixed time."""
+    diffs = []
+    for n in (48, 96):
+        c = I.vortex_case(n, 2, lx=16.0, ly=16.0)
+        ns = 20
+        c = c.replace(dt=0.2 * c.dx / 4.0)
+        Usa = orc.run(c, I.vortex_state(c), ns)
+        cat = c.replace(algo="SAA", at=True, kmax=0)
+        Uat = orc.run(cat, I.vortex_state(c), ns, delays=np.zeros((ns, c.nsub, 6), np.int8))
+        diffs.append(np.abs(Uat - Usa).max())
+    assert diffs[0] > 0
+    assert math.log2(diffs[0] / diffs[1]) > 3.5, diffs
+
+
+@pytest.mark.parametrize("at,lo,hi", [(True, 3.5, 99), (False, 0.8, 1.8)])
+def test_async_error_order_with_filter(at, lo, hi):
+    """With the once-per-step Pade filter on (alpha_f = 0.499 as in Sec. 5.2), the delays still add
+    an error of the AT order (the filter halo is the extrapolation to t_{n+1}) or of about first
+    order (AS)."""
+    e = []
+    for n in (64, 128):
+        runs = []
+        for algo in ("CAA", "SA"):
+            c = I.vortex_case(n, 2, lx=16.0, ly=16.0, filter=True, alpha_f=0.499)
+            dt0 = I.cfl_dt(c, I.vortex_state(c), 0.2)
+            ns = int(math.ceil(0.5 / dt0))
+            c = c.replace(dt=0.5 / ns, algo=algo, at=at, caa_L=4)
+            runs.append(orc.run(c, I.vortex_state(c), ns))
+        e.append(math.sqrt(np.mean((runs[0][0] - runs[1][0]) ** 2)))
+    rate = math.log2(e[0] / e[1])
+    assert lo < rate < hi, (e, rate)
+
+
+def test_async_error_order_viscous_3d():
+    """Navier-Stokes in 3-D with face and edge halos under CAA-AT: the asynchrony error is of
+    high order (at least 3.5 observed between 16^3 and 32^3 at fixed time)."""
+    e = []
+    for n in (16, 32):
+        runs = []
+        for algo in ("CAA", "SA"):
+            c = I.tgv_case(n, 2, algo, filter=False, re=100.0)
+            dt0 = I.cfl_dt(c, I.tgv_state(c), 0.2)
+            ns = int(math.ceil(0.08 / dt0))
+            c = c.replace(dt=0.08 / ns)
+            runs.append(orc.run(c, I.tgv_state(c), ns))
+        e.append(max(math.sqrt(np.mean((runs[0][v] - runs[1][v]) ** 2)) for v in range(5)))
+    rate = math.log2(e[0] / e[1])
+    assert rate > 3.5, (e, rate)
