@@ -1,0 +1,407 @@
+#!/usr/bin/env python3
+"""Benchmark of the asynchronous compressible-flow hot path on GB300.
+
+Workload (one "step" = one full time step of the method: 5 LSERK4 stages, each a fused
+RHS + AT-halo + stage update over all sub-domains, then the three tenth-order filter passes):
+3-D Taylor-Green vortex, Navier-Stokes, Re 1600, Mach 0.1, gamma 1.4, Pr 0.71, periodic
+[0, 2 pi]^3 at 128^3, FP64, 4 x 4 x 4 = 64 sub-domains of 32^3, SAA with seeded uniform delays
+0..3 per face per step (AT4 schemes), after the 5 synchronous warm-up steps.
+
+Metric: point-RK-stage updates per second (Mpoint-stage/s) = 128^3 x 5 x steps / time.
+
+  value     device-resident, CUDA events on the solver's stream around K steps (barrier and
+            synchronize on both sides, max over ranks); the working set (~1.8 GB) is larger
+            than the 129 MB L2.
+  e2e       the same metric through the public API with host buffers: per step the state is
+            copied in from pinned host memory, stepped, and copied back out.
+  roofline  the dominant kernel's achieved FP64 rate (algorithmic flops per launch / average
+            event-timed launch duration) against the GB300 FP64 peak.
+  cpu_baseline  the FP64 CPU oracle on the host cores on a bounded sample of the workload.
+
+--impl reference times the oracle itself (the CPU program the GPU path is checked against) on
+the same configuration and metric; under torchrun only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpoint-RK-stage updates/s and % HBM peak; forms vs plain FP64 at stated L2 error"
+UNIT = "Mpoint-stage/s"
+SM_COUNT = 152
+FP64_FLOP_PER_CLK_SM = 4        # 2 FP64 FMA per clock per SM on GB300
+HBM_GBS_FALLBACK = 6800.0
+
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel kind, with the sha1 of
+# the kernel source they were taken from (null once the kernels change); filled from profiles/.
+TRAFFIC = {"source_sha1": None, "bytes_per_launch": {}}
+
+
+def kernels_sha1() -> str:
+    with open(os.path.join(ROOT, "paper_2506_03027_gb300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def workload(algo="SAA"):
+    from paper_2506_03027_gb300 import inputs as I
+    c = I.tgv_case(128, 4, algo)
+    # asynchronous runs need a smaller step for stability (the paper reduced it 2-10x); the cost
+    # of a step does not depend on dt
+    c = c.replace(dt=I.cfl_dt(c, I.tgv_state(c), 0.25))
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def face_points(case, depth):
+    """Points of the face strips (depth `depth`) of all sub-domains along each axis."""
+    from paper_2506_03027_gb300 import inputs as I  # noqa: F401
+    tot = 0
+    for ix in range(case.px):
+        sx = case.nx // case.px + (1 if ix < case.nx % case.px else 0)
+        for iy in range(case.py):
+            sy = case.ny // case.py + (1 if iy < case.ny % case.py else 0)
+            for iz in range(case.pz):
+                sz = case.nz // case.pz + (1 if iz < case.nz % case.pz else 0)
+                tot += 2 * depth * (sy * sz + sx * sz + sx * sy)
+    return tot
+
+
+def algorithmic_flops(case, kind):
+    """FP64 flops per launch that the method needs in each kernel (FMA = 2 flops), counted from
+    the operations of the 3-D Navier-Stokes CD4 path; see the design notes for the breakdown."""
+    N = case.npts
+    r = 2 if case.order == 4 else 1
+    if kind == "flux":
+        # 12 CD gradients (5 flops each) + divergence (2) + per direction 33 flops of fluxes
+        return N * (60 + 2 + 3 * 33) + face_points(case, r) * (60 + 2 + 33)
+    if kind == "stage_update":
+        # 15 CD derivatives (5 flops) + 3 adds per variable, then Q and U updates (5 per variable)
+        return N * (5 * (15 + 3) + 5 * 5)
+    if kind == "view":
+        g = 2 * r
+        halo = face_points(case, g) + 0  # face halos; edges and AT weights counted in the notes
+        return (N + halo) * 16 + halo * 5 * case.levels * 2
+    if kind == "filter":
+        return N * 5 * 21
+    return 0
+
+
+def algorithmic_bytes_per_step(case):
+    """HBM bytes the method must move per step: state and LSERK register traffic (FP64) of the
+    5 stages (120 + 3 x 160 + 120 B per point), the filter passes (read + write, 80 B per point
+    per pass) and the ring levels the AT halos read once per stage (C levels x 40 B per halo
+    point)."""
+    N = case.npts
+    r = 2 if case.order == 4 else 1
+    g = 2 * r if case.viscous else r
+    halo = face_points(case, g)
+    stage = N * (120 + 160 * (case.stages - 2) + 120)
+    filt = N * 80 * (3 if case.nz > 1 else 2) if case.filter else 0
+    ring = halo * case.levels * 40 * case.stages
+    return stage + filt + ring
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2506_03027_gb300 import build as B
+    from paper_2506_03027_gb300 import cfs
+    from paper_2506_03027_gb300 import inputs as I
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    B.build()
+    case = workload(args.schedule)
+    case = case.replace(seed=case.seed + rank)
+    K, W = args.steps, args.warmup
+    total = W + 2 * K + 8
+    delays = I.saa_delays(case, total)
+    U0 = I.tgv_state(case)
+    stream = torch.cuda.current_stream()
+
+    solver = cfs.Solver(case, precision=args.precision)
+    solver.set_schedule(delays=delays)
+    solver.set_state(U0)
+    solver.step(W)
+    torch.cuda.synchronize()
+
+    # ---------------- device-resident timed region
+    cfs.cfs_set_timing(solver.ctx, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        e0.record(stream)
+        solver.step(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = solver.launches()
+    ktimes = cfs.cfs_get_timing(solver.ctx)
+    cfs.cfs_set_timing(solver.ctx, False)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    n_units = case.npts * case.stages * K * world
+    value = n_units / (ms * 1e-3) / 1e6
+
+    # ---------------- end to end through the public API with host buffers
+    host = torch.empty((5, case.nz, case.ny, case.nx), dtype=torch.float64, pin_memory=True)
+    hnp = host.numpy()
+    solver.get_state(hnp)
+    Ke = max(3, K // 2)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        solver.set_state(hnp)          # host -> device copy of the step's input
+        solver.step(1)
+        solver.get_state(hnp)          # device -> host copy of the step's result (synchronises)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([te], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        te = float(t.item())
+    e2e_value = case.npts * case.stages * Ke * world / te / 1e6
+    state_bytes = 5 * case.npts * 8
+    U_fp64 = solver.get_state()
+    n_done = solver.n
+    solver.close()
+
+    # ---------------- precision form (FP32 intermediates), same steps, error vs the FP64 path
+    forms = None
+    if args.precision == 0 and not args.no_forms:
+        s32 = cfs.Solver(case, precision=1)
+        s32.set_schedule(delays=delays)
+        s32.set_state(U0)
+        s32.step(W)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s32.step(K)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = f0.elapsed_time(f1)
+        s32.step(n_done - s32.n)
+        U32 = s32.get_state()
+        s32.close()
+        err = [float(np.linalg.norm(U32[v] - U_fp64[v]) / max(np.linalg.norm(U_fp64[v]), 1e-30)) for v in range(5)]
+        forms = {"fp32_intermediates": {"value": n_units / (ms32 * 1e-3) / 1e6, "unit": UNIT,
+                                        "speedup_vs_fp64": ms / ms32,
+                                        "rel_l2_vs_fp64_path": err, "after_steps": n_done}}
+
+    # ---------------- roofline of the dominant kernel
+    peaks = measured_peaks()
+    clocks = clk.summary()
+    sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    kinds = {k: v for k, v in ktimes.items() if v[1] > 0 and k != "diagnostics"}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms, dom_n = kinds[dom]
+    flops = algorithmic_flops(case, dom)
+    achieved_tf = flops / (dom_ms / dom_n * 1e-3) / 1e12
+    if args.precision == 0:
+        peak_tf = SM_COUNT * FP64_FLOP_PER_CLK_SM * sm_max * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved_tf / peak_tf, "kernel": dom,
+                "peak_source": f"FP64 pipe: {SM_COUNT} SMs x {FP64_FLOP_PER_CLK_SM} flop/clk x {sm_max:.0f} MHz"}
+    else:
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": None, "unit": "TFLOP/s", "frac": None,
+                "kernel": dom}
+    tr = TRAFFIC["bytes_per_launch"].get(dom) if TRAFFIC["source_sha1"] == kernels_sha1() else None
+    roof["traffic"] = tr
+    roof["per_kernel_ms"] = {k: round(v[0] / max(v[1], 1), 4) for k, v in kinds.items()}
+    hbm = peaks.get("hbm_gbs", HBM_GBS_FALLBACK)
+    step_bytes = algorithmic_bytes_per_step(case)
+    hbm_frac = step_bytes * K / (ms * 1e-3) / 1e9 / hbm
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == 0 else "f64-state/f32-intermediates", "data": "synthetic",
+        "config": {"workload": f"Taylor-Green vortex NS 128^3, 4x4x4 sub-domains of 32^3, {args.schedule}-AT "
+                               "delays 0..3 per face per step, LSERK4-CD4-AT4, 10th-order filter alpha_f 0.499",
+                   "grid": [case.nx, case.ny, case.nz], "subdomains": case.nsub, "schedule": args.schedule,
+                   "precision": "fp64" if args.precision == 0 else "fp32-intermediates",
+                   "l2_policy": "working set larger than L2 (no flush needed)",
+                   "replicas": "independent problem per rank" if world > 1 else None},
+        "hbm_frac_algorithmic": hbm_frac,
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if forms:
+        line["forms"] = forms
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(case)
+    return line
+
+
+def oracle_sample(case, nsteps):
+    """Time `nsteps` asynchronous oracle steps of the workload (starting after the warm-up with a
+    history of copies of the initial state: the cost does not depend on the values)."""
+    from oracle import oracle as orc
+    from paper_2506_03027_gb300 import inputs as I
+    U0 = I.tgv_state(case)
+    R = 3 + case.levels + 1
+    hist = np.broadcast_to(U0, (R,) + U0.shape).copy()
+    n0 = case.levels
+    delays = I.saa_delays(case, n0 + nsteps)
+    t0 = time.perf_counter()
+    orc.run(case, U0, nsteps, delays=delays, n0=n0, hist=hist)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(case):
+    from oracle import oracle as orc
+    orc.build()
+    steps = 1
+    dt = oracle_sample(case, steps)
+    return {"value": case.npts * case.stages * steps / dt / 1e6, "unit": UNIT, "cores": orc.num_threads(),
+            "kind": "oracle",
+            "sample": f"{steps} asynchronous step(s) of the full 128^3 workload (SAA-AT, filter), {dt:.1f} s"}
+
+
+def run_reference(args):
+    from oracle import oracle as orc
+    orc.build()
+    case = workload(args.schedule)
+    for _ in range(args.warmup):
+        oracle_sample(case, 1)
+    ts = [oracle_sample(case, 1) for _ in range(args.steps)]
+    tot = sum(ts)
+    value = case.npts * case.stages * args.steps / tot / 1e6
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "Taylor-Green vortex NS 128^3, 4x4x4 sub-domains of 32^3, SAA-AT delays 0..3, "
+                                   "LSERK4-CD4-AT4, 10th-order filter alpha_f 0.499",
+                       "grid": [case.nx, case.ny, case.nz], "subdomains": case.nsub, "schedule": args.schedule},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} full asynchronous steps of the 128^3 workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=6)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--schedule", default="SAA", choices=["SA", "CAA", "SAA"])
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * cfs.h -- C ABI of the GB300 asynchronous compressible flow solver library (libcfs.so).
+ *
+ * The library advances the compressible Navier-Stokes (or Euler) equations on a periodic uniform
+ * Cartesian block split into sub-domains ("processing elements" of arXiv 2506.03027, Sec. 3),
+ * with the asynchrony-tolerant (AT) halo treatment of Sec. 3.1-3.2 under the SA, CAA and SAA
+ * algorithms of Alg. 1-3.  Every step of the hot path runs in the library's CUDA kernels for
+ * sm_103a; there is no CPU fallback: a call that needs the GPU fails with CFS_ECUDA when the
+ * device or the kernels are unavailable.
+ *
+ * Conventions
+ *   - State arrays are structure-of-arrays FP64, U[5][nz][ny][nx] with x fastest, variables
+ *     {rho, rho u, rho v, rho w, rho E_t} (Eq. 1).  2-D runs use nz = 1 and rho w = 0.
+ *   - Pointers are plain host or device addresses as stated per call; sizes are element counts.
+ *   - The library never frees memory it did not allocate.  Device memory comes from the
+ *     allocator set with cfs_set_allocator (default: cudaMalloc / cudaFree).
+ *   - All device work is issued on the stream passed to cfs_create (borrowed, not owned).
+ *     Calls that return data to the host synchronise that stream.
+ *   - Errors: every call returns a cfs_status; cfs_last_error gives a message.  A CUDA error is
+ *     sticky for the context.  No C++ exception crosses this interface.
+ */
+#ifndef CFS_H_
+#define CFS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CFS_OK = 0,
+  CFS_EINVAL = 1,   /* invalid argument (sizes, schedule, scheme) */
+  CFS_ENOMEM = 2,   /* the allocator returned NULL */
+  CFS_ECUDA = 3,    /* CUDA runtime error (sticky) */
+  CFS_ESTATE = 4,   /* call out of order (e.g. cfs_step before cfs_finalize) */
+  CFS_ENAN = 5,     /* non-finite value found in the state */
+  CFS_ETIMEOUT = 6  /* a bounded device wait gave up */
+} cfs_status;
+
+typedef struct cfs_ctx cfs_ctx;
+
+/* Scheme and physics (Table 1, App. A-B).  Nondimensionalisation of App. A:
+ * E_t = T/(gamma (gamma-1) M^2) + |u|^2/2, p = rho T/(gamma M^2), viscous terms scaled by 1/Re,
+ * heat flux mu/((gamma-1) Pr M^2) dT/dx. */
+typedef struct {
+  int order;         /* 4: LSERK4-CD4-AT4 (5 stages, C = 5 levels); 2: LSERK2-CD2-AT2 (2, 3) */
+  int viscous;       /* 1: Navier-Stokes (Eq. A3-A4), 0: Euler */
+  int visc_law;      /* 0: mu = 1; 1: mu = T^visc_exp */
+  double visc_exp;
+  double gamma, mach, re, pr;
+  int filter;        /* 1: tenth-order Pade filter (coefficient alpha_f) once per step */
+  double alpha_f;
+  int precision;     /* 0: FP64 throughout; 1: FP32 derivative/flux/filter intermediates with
+                        FP64 state, RK accumulation and AT coefficient application */
+} cfs_params;
+
+/* Device allocator used by cfs_finalize and cfs_set_schedule.  alloc returns a device pointer
+ * aligned to at least 256 bytes or NULL; free releases it. */
+typedef void* (*cfs_alloc_fn)(size_t bytes, void* user);
+typedef void (*cfs_free_fn)(void* ptr, void* user);
+
+/* Create a context.  p is copied.  cuda_stream is a cudaStream_t (NULL = legacy default stream)
+ * that the caller keeps alive until cfs_destroy.  *out receives the context.
+ * EINVAL: unsupported order/precision/filter coefficient (|alpha_f| must be < 0.5). */
+cfs_status cfs_create(const cfs_params* p, void* cuda_stream, cfs_ctx** out);
+
+/* Replace the device allocator (before cfs_finalize).  user is passed back unchanged. */
+cfs_status cfs_set_allocator(cfs_ctx* ctx, cfs_alloc_fn alloc, cfs_free_fn free_fn, void* user);
+
+/* Add a uniform Cartesian block of ni x nj x nk points with spacing {dx, dy, dz} (host array of
+ * 3 doubles), periodic in every direction (each face connected to the opposite face of the same
+ * block).  nk = 1 makes the run two-dimensional.  *block_id receives the index (0 for the first
+ * block; this version supports one block).  EINVAL for non-positive sizes or a second block. */
+cfs_status cfs_add_block(cfs_ctx* ctx, int ni, int nj, int nk, const double* spacing, int* block_id);
+
+/* Decompose a block into pi x pj x pk sub-domains (the paper's PEs, Sec. 3): along each axis
+ * n points split into p parts as evenly as possible, the first n mod p parts one point longer.
+ * Every sub-domain must be at least as wide as the halo it needs (2 r for viscous runs, r for
+ * Euler, r = 2 for CD4 and 1 for CD2; 5 with the filter).  EINVAL otherwise. */
+cfs_status cfs_split_block(cfs_ctx* ctx, int block, int pi, int pj, int pk);
+
+/* Connect face faceA of blockA to faceB of blockB (faces 0..5 = -i,+i,-j,+j,-k,+k).
+ * This version supports only the periodic self-connection (blockA == blockB, opposite faces,
+ * orientation 0), which is also the default; anything else returns EINVAL. */
+cfs_status cfs_connect(cfs_ctx* ctx, int blockA, int faceA, int blockB, int faceB, int orientation);
+
+/* Physical boundary condition on a face (wall, far field, inflow).  Not supported in this
+ * version: every face is periodic.  Returns EINVAL. */
+cfs_status cfs_set_bc(cfs_ctx* ctx, int block, int face, int type, const double* data);
+
+/* Allocate device memory for the state ring, stage buffers and scratch, and build the
+ * sub-domain tables.  max_delay is the largest delay any schedule will use (sizes the ring of
+ * delayed levels: max_delay + C + 1 full states).  ESTATE if called twice, ENOMEM on
+ * allocation failure. */
+cfs_status cfs_finalize(cfs_ctx* ctx, int max_delay);
+
+/* Delay schedule (Alg. 1-3).  algo: 0 SA, 1 CAA, 2 SAA.  at: 1 AT schemes, 0 AS (standard
+ * stencils on the latest delayed level).  The first C steps of CAA/SAA run synchronously.
+ *   CAA: delay of every face at step n >= C is (n - C) mod L (L >= 1, L - 1 <= max_delay).
+ *   SAA: delays is a HOST table int8[nsteps][nsub][6] (step, sub-domain, face), copied; each
+ *        entry must lie in [0, max_delay].  Steps beyond nsteps are an error at cfs_step.
+ * Delays are clamped to n - C + 1 so that every referenced level exists.  Sub-domains are
+ * numbered x fastest.  EINVAL on out-of-range entries. */
+cfs_status cfs_set_schedule(cfs_ctx* ctx, int algo, int at, int L, long long nsteps, const int8_t* delays);
+
+/* Copy the state of block `block` in (set) or out (get).  where: 0 = host pointer, 1 = device
+ * pointer.  set_state defines the state at the current step index (0 after cfs_finalize; see
+ * cfs_set_step) and is the start of a fresh history unless the ring is restored as well.
+ * get_state synchronises the stream. */
+cfs_status cfs_set_state(cfs_ctx* ctx, int block, const double* U, int where);
+cfs_status cfs_get_state(cfs_ctx* ctx, int block, double* U, int where);
+
+/* Fixed time step (the AT weights assume equally spaced levels, Eq. 5 and Eq. 9). */
+cfs_status cfs_set_dt(cfs_ctx* ctx, double dt);
+
+/* Current step index n (levels U^0..U^n exist).  cfs_set_step moves it (with cfs_set_ring for
+ * checkpoint / resume). */
+cfs_status cfs_get_step(cfs_ctx* ctx, long long* n);
+cfs_status cfs_set_step(cfs_ctx* ctx, long long n);
+
+/* Advance nsteps time steps: per step, s LSERK stages of the fused RHS + stage update with the
+ * halos of the schedule, then the filter (if on); the new state is U^{n+1}.  Asynchronous on the
+ * stream; errors of device work surface at the next synchronising call. */
+cfs_status cfs_step(cfs_ctx* ctx, long long nsteps);
+
+/* Diagnostics of the current state U^n (synchronises): out[8] = {K, enstrophy, sum rho,
+ * sum rho u, sum rho v, sum rho w, sum rho E, non-finite flag}, K and enstrophy volume averages
+ * with rho_0 = 1 (Sec. 5.2), vorticity by the scheme's central difference, sums weighted by the
+ * cell volume.  Returns ENAN (and fills out) when the state holds a non-finite value. */
+cfs_status cfs_diagnostics(cfs_ctx* ctx, double* out);
+
+/* Checkpoint / resume of the ring of delayed levels: R = max_delay + C + 1 full states,
+ * slot i holds level n - R + 1 + i (host or device buffer of R * 5 * npoints doubles). */
+cfs_status cfs_ring_depth(cfs_ctx* ctx, int* R);
+cfs_status cfs_get_ring(cfs_ctx* ctx, double* buf, int where);
+cfs_status cfs_set_ring(cfs_ctx* ctx, const double* buf, int where);
+
+/* Host-side coefficient tables generated by the library (no GPU needed), for inspection:
+ * W[(k * s + m) * C + l] = weight of level n-k-l in the stage-m halo value (m = 0: Eq. 14/15
+ * extrapolation; m >= 1: after the buffer updates of Eq. 8 at stages 1..m), k = 0..kmax.
+ * Returns the number of doubles written (kmax+1)*s*C, or -1 on bad arguments. */
+int cfs_at_weights(int order, int kmax, double* W);
+
+/* Counters of the last cfs_step call: number of kernel launches issued. */
+cfs_status cfs_launch_count(cfs_ctx* ctx, long long* launches);
+
+/* Per-kernel timing with CUDA events recorded on the context's stream around every launch.
+ * cfs_set_timing(ctx, 1) starts (and clears) the accumulation, 0 stops it.  cfs_get_timing
+ * synchronises and returns, for each kernel kind k (CFS_NKINDS entries: 0 view, 1 flux,
+ * 2 stage update, 3 filter, 4 diagnostics), the summed duration ms[k] in milliseconds and the
+ * number of timed launches count[k].  Either array may be NULL. */
+#define CFS_NKINDS 5
+cfs_status cfs_set_timing(cfs_ctx* ctx, int on);
+cfs_status cfs_get_timing(cfs_ctx* ctx, double* ms, long long* count);
+
+/* Last error message of the context (static string if ctx is NULL). */
+const char* cfs_last_error(cfs_ctx* ctx);
+
+/* Release device memory (through the allocator) and the context. */
+void cfs_destroy(cfs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CFS_H_ */

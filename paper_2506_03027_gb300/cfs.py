@@ -1,0 +1,353 @@
+"""Thin Python binding of libcfs (the C ABI in include/cfs.h).
+
+Argument marshalling only: every step of the hot path runs in the library's CUDA kernels.  The
+functions ``cfs_*`` mirror the C entry points one to one and raise ``CfsError`` on a non-OK
+status.  ``Solver`` strings them together for one block and lets PyTorch own the device memory
+(through the allocator callback) and the stream.
+
+There is no fallback: if ``libcfs.so`` has not been built, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libcfs.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "cfs.h")
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENAN", 6: "ETIMEOUT"}
+CFS_OK, CFS_EINVAL, CFS_ENOMEM, CFS_ECUDA, CFS_ESTATE, CFS_ENAN, CFS_ETIMEOUT = range(7)
+ALGO = {"SA": 0, "CAA": 1, "SAA": 2}
+HOST, DEVICE = 0, 1
+
+
+class CfsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CfsParams(ctypes.Structure):
+    _fields_ = [
+        ("order", ctypes.c_int), ("viscous", ctypes.c_int), ("visc_law", ctypes.c_int),
+        ("visc_exp", ctypes.c_double), ("gamma", ctypes.c_double), ("mach", ctypes.c_double),
+        ("re", ctypes.c_double), ("pr", ctypes.c_double), ("filter", ctypes.c_int),
+        ("alpha_f", ctypes.c_double), ("precision", ctypes.c_int),
+    ]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+
+
+def header_symbols() -> list[str]:
+    """Entry points declared in include/cfs.h."""
+    with open(HEADER) as f:
+        src = f.read()
+    return sorted(set(re.findall(r"^\s*(?:cfs_status|int|void|const char\*)\s+(cfs_\w+)\s*\(", src, re.M)))
+
+
+def load() -> ctypes.CDLL:
+    """Open libcfs.so (built by ``paper_2506_03027_gb300.build``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libcfs.so not found at {LIB_PATH}: run paper_2506_03027_gb300/build.py "
+                               "(the solver has no CPU fallback)")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+        ll = ctypes.c_longlong
+        sig = {
+            "cfs_create": ([ctypes.POINTER(CfsParams), vp, ctypes.POINTER(vp)], ip),
+            "cfs_set_allocator": ([vp, ALLOC_FN, FREE_FN, vp], ip),
+            "cfs_add_block": ([vp, ip, ip, ip, dp, ctypes.POINTER(ip)], ip),
+            "cfs_split_block": ([vp, ip, ip, ip, ip], ip),
+            "cfs_connect": ([vp, ip, ip, ip, ip, ip], ip),
+            "cfs_set_bc": ([vp, ip, ip, ip, dp], ip),
+            "cfs_finalize": ([vp, ip], ip),
+            "cfs_set_schedule": ([vp, ip, ip, ip, ll, ctypes.POINTER(ctypes.c_int8)], ip),
+            "cfs_set_state": ([vp, ip, vp, ip], ip),
+            "cfs_get_state": ([vp, ip, vp, ip], ip),
+            "cfs_set_dt": ([vp, ctypes.c_double], ip),
+            "cfs_get_step": ([vp, ctypes.POINTER(ll)], ip),
+            "cfs_set_step": ([vp, ll], ip),
+            "cfs_step": ([vp, ll], ip),
+            "cfs_diagnostics": ([vp, dp], ip),
+            "cfs_ring_depth": ([vp, ctypes.POINTER(ip)], ip),
+            "cfs_get_ring": ([vp, vp, ip], ip),
+            "cfs_set_ring": ([vp, vp, ip], ip),
+            "cfs_at_weights": ([ip, ip, dp], ip),
+            "cfs_launch_count": ([vp, ctypes.POINTER(ll)], ip),
+            "cfs_set_timing": ([vp, ip], ip),
+            "cfs_get_timing": ([vp, dp, ctypes.POINTER(ll)], ip),
+            "cfs_last_error": ([vp], ctypes.c_char_p),
+            "cfs_destroy": ([vp], None),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(ctx, status: int) -> None:
+    if status != CFS_OK:
+        msg = load().cfs_last_error(ctx)
+        raise CfsError(status, msg.decode() if msg else "")
+
+
+# ------------------------------------------------------------------ one-to-one wrappers
+
+def cfs_create(params: CfsParams, stream: int | None = None):
+    ctx = ctypes.c_void_p()
+    st = load().cfs_create(ctypes.byref(params), ctypes.c_void_p(stream or 0), ctypes.byref(ctx))
+    if st != CFS_OK:
+        raise CfsError(st, "cfs_create rejected the parameters")
+    return ctx
+
+
+def cfs_set_allocator(ctx, alloc, free, user=None):
+    _check(ctx, load().cfs_set_allocator(ctx, alloc, free, user))
+
+
+def cfs_add_block(ctx, ni: int, nj: int, nk: int, spacing) -> int:
+    sp = (ctypes.c_double * 3)(*spacing)
+    bid = ctypes.c_int()
+    _check(ctx, load().cfs_add_block(ctx, ni, nj, nk, sp, ctypes.byref(bid)))
+    return bid.value
+
+
+def cfs_split_block(ctx, block: int, pi: int, pj: int, pk: int):
+    _check(ctx, load().cfs_split_block(ctx, block, pi, pj, pk))
+
+
+def cfs_connect(ctx, block_a: int, face_a: int, block_b: int, face_b: int, orientation: int = 0):
+    _check(ctx, load().cfs_connect(ctx, block_a, face_a, block_b, face_b, orientation))
+
+
+def cfs_set_bc(ctx, block: int, face: int, bc_type: int, data=None):
+    _check(ctx, load().cfs_set_bc(ctx, block, face, bc_type, None))
+
+
+def cfs_finalize(ctx, max_delay: int):
+    _check(ctx, load().cfs_finalize(ctx, max_delay))
+
+
+def cfs_set_schedule(ctx, algo: int, at: int, L: int, delays: np.ndarray | None):
+    if delays is None:
+        _check(ctx, load().cfs_set_schedule(ctx, algo, at, L, 0, None))
+        return
+    d = np.ascontiguousarray(delays, dtype=np.int8)
+    _check(ctx, load().cfs_set_schedule(ctx, algo, at, L, d.shape[0],
+                                        d.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))))
+
+
+def cfs_set_state(ctx, block: int, ptr: int, where: int):
+    _check(ctx, load().cfs_set_state(ctx, block, ctypes.c_void_p(ptr), where))
+
+
+def cfs_get_state(ctx, block: int, ptr: int, where: int):
+    _check(ctx, load().cfs_get_state(ctx, block, ctypes.c_void_p(ptr), where))
+
+
+def cfs_set_dt(ctx, dt: float):
+    _check(ctx, load().cfs_set_dt(ctx, dt))
+
+
+def cfs_get_step(ctx) -> int:
+    n = ctypes.c_longlong()
+    _check(ctx, load().cfs_get_step(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def cfs_set_step(ctx, n: int):
+    _check(ctx, load().cfs_set_step(ctx, n))
+
+
+def cfs_step(ctx, nsteps: int):
+    _check(ctx, load().cfs_step(ctx, nsteps))
+
+
+def cfs_diagnostics(ctx, check_finite: bool = True) -> np.ndarray:
+    out = np.zeros(8)
+    st = load().cfs_diagnostics(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if st == CFS_ENAN and not check_finite:
+        return out
+    _check(ctx, st)
+    return out
+
+
+def cfs_ring_depth(ctx) -> int:
+    r = ctypes.c_int()
+    _check(ctx, load().cfs_ring_depth(ctx, ctypes.byref(r)))
+    return r.value
+
+
+def cfs_get_ring(ctx, ptr: int, where: int):
+    _check(ctx, load().cfs_get_ring(ctx, ctypes.c_void_p(ptr), where))
+
+
+def cfs_set_ring(ctx, ptr: int, where: int):
+    _check(ctx, load().cfs_set_ring(ctx, ctypes.c_void_p(ptr), where))
+
+
+def cfs_at_weights(order: int, kmax: int) -> np.ndarray:
+    s = 5 if order == 4 else 2
+    C = 5 if order == 4 else 3
+    W = np.zeros((kmax + 1) * s * C)
+    n = load().cfs_at_weights(order, kmax, W.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if n < 0:
+        raise CfsError(CFS_EINVAL, "bad order or kmax")
+    return W.reshape(kmax + 1, s, C)
+
+
+def cfs_launch_count(ctx) -> int:
+    n = ctypes.c_longlong()
+    _check(ctx, load().cfs_launch_count(ctx, ctypes.byref(n)))
+    return n.value
+
+
+NKINDS = 5
+KIND_NAMES = ("view", "flux", "stage_update", "filter", "diagnostics")
+
+
+def cfs_set_timing(ctx, on: bool):
+    _check(ctx, load().cfs_set_timing(ctx, int(on)))
+
+
+def cfs_get_timing(ctx):
+    ms = np.zeros(NKINDS)
+    cnt = (ctypes.c_longlong * NKINDS)()
+    _check(ctx, load().cfs_get_timing(ctx, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cnt))
+    return {KIND_NAMES[k]: (float(ms[k]), int(cnt[k])) for k in range(NKINDS)}
+
+
+def cfs_last_error(ctx) -> str:
+    m = load().cfs_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def cfs_destroy(ctx):
+    load().cfs_destroy(ctx)
+
+
+# ------------------------------------------------------------------ convenience wrapper
+
+def params_from_case(case, precision: int = 0) -> CfsParams:
+    return CfsParams(order=case.order, viscous=int(case.viscous), visc_law=int(case.visc_law),
+                     visc_exp=case.visc_exp, gamma=case.gamma, mach=case.mach, re=case.re, pr=case.pr,
+                     filter=int(case.filter), alpha_f=case.alpha_f, precision=precision)
+
+
+class TorchAllocator:
+    """Device memory for the library from PyTorch's caching allocator (tensors kept alive here)."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.live = {}
+        self.alloc_cb = ALLOC_FN(self._alloc)
+        self.free_cb = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, user):
+        try:
+            t = self.torch.empty(int(nbytes) + 256, dtype=self.torch.uint8, device=self.device)
+        except Exception:
+            return None
+        ptr = (t.data_ptr() + 255) // 256 * 256
+        self.live[ptr] = t
+        return ptr
+
+    def _free(self, ptr, user):
+        self.live.pop(ptr, None)
+
+
+class Solver:
+    """One periodic block of ``case`` on the current CUDA device and stream."""
+
+    def __init__(self, case, max_delay: int | None = None, precision: int = 0, stream=None,
+                 use_torch_allocator: bool = True):
+        import torch
+        self.torch = torch
+        self.case = case
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.ctx = cfs_create(params_from_case(case, precision), self.stream.cuda_stream)
+        self.alloc = None
+        if use_torch_allocator:
+            self.alloc = TorchAllocator(self.device)
+            cfs_set_allocator(self.ctx, self.alloc.alloc_cb, self.alloc.free_cb)
+        cfs_add_block(self.ctx, case.nx, case.ny, case.nz, (case.dx, case.dy, case.dz))
+        cfs_split_block(self.ctx, 0, case.px, case.py, case.pz)
+        if max_delay is None:
+            max_delay = {"SA": 0, "CAA": case.caa_L - 1, "SAA": case.kmax}[case.algo]
+        cfs_finalize(self.ctx, max_delay)
+        self.npts = case.nx * case.ny * case.nz
+        cfs_set_dt(self.ctx, case.dt)
+
+    def set_schedule(self, algo: str | None = None, at: bool | None = None, L: int | None = None,
+                     delays: np.ndarray | None = None):
+        c = self.case
+        algo = c.algo if algo is None else algo
+        at = c.at if at is None else at
+        L = c.caa_L if L is None else L
+        cfs_set_schedule(self.ctx, ALGO[algo], int(at), L, delays if algo == "SAA" else None)
+
+    def set_state(self, U):
+        """U: numpy array (host) or CUDA tensor (device), FP64 [5][nz][ny][nx]."""
+        if isinstance(U, np.ndarray):
+            a = np.ascontiguousarray(U, dtype=np.float64)
+            assert a.size == 5 * self.npts
+            cfs_set_state(self.ctx, 0, a.ctypes.data, HOST)
+        else:
+            t = U.contiguous()
+            assert t.dtype == self.torch.float64 and t.numel() == 5 * self.npts and t.is_cuda
+            cfs_set_state(self.ctx, 0, t.data_ptr(), DEVICE)
+
+    def get_state(self, out=None):
+        """Current state to a new numpy array, or into ``out`` (numpy or CUDA tensor)."""
+        c = self.case
+        if out is None:
+            out = np.empty((5, c.nz, c.ny, c.nx), dtype=np.float64)
+        if isinstance(out, np.ndarray):
+            assert out.flags.c_contiguous and out.dtype == np.float64
+            cfs_get_state(self.ctx, 0, out.ctypes.data, HOST)
+        else:
+            cfs_get_state(self.ctx, 0, out.data_ptr(), DEVICE)
+        return out
+
+    def step(self, n: int = 1):
+        cfs_step(self.ctx, n)
+
+    def diagnostics(self, check_finite: bool = True) -> np.ndarray:
+        return cfs_diagnostics(self.ctx, check_finite)
+
+    @property
+    def n(self) -> int:
+        return cfs_get_step(self.ctx)
+
+    def launches(self) -> int:
+        return cfs_launch_count(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            cfs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

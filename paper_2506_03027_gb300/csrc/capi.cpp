@@ -1,0 +1,589 @@
+// capi.cpp -- the C ABI of libcfs (declared in include/cfs.h): context, decomposition,
+// device memory, schedule and the per-step launch sequence of arXiv 2506.03027's method.
+#include "cfs.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cfs_internal.h"
+
+using cfs::Geometry;
+using cfs::Physics;
+using cfs::StepSched;
+using cfs::SubDev;
+
+struct cfs_ctx {
+  cfs_params p{};
+  cudaStream_t stream = nullptr;
+  cfs_alloc_fn alloc = nullptr;
+  cfs_free_fn freef = nullptr;
+  void* user = nullptr;
+  std::vector<void*> owned;
+
+  bool has_block = false, finalized = false;
+  int nx = 0, ny = 0, nz = 0;
+  double h[3] = {1, 1, 1};
+  int P[3] = {1, 1, 1};
+
+  int s = 0, C = 0, r = 0, G = 0, Gz = 0, ndim = 0;
+  int max_delay = 0, R = 0;
+  long long n = 0;
+  double dt = 0.0;
+  bool dt_set = false;
+  double A[5] = {0}, B[5] = {0};
+
+  int algo = 0, at = 1, L = 1;
+  long long sched_steps = 0;
+  int8_t* d_sched = nullptr;
+
+  double* ring = nullptr;
+  double* buf[2] = {nullptr, nullptr};
+  double* Q = nullptr;
+  void* Wp = nullptr;
+  void* Phi = nullptr;
+  double* d_W = nullptr;
+  double* d_Wf = nullptr;
+  SubDev* d_subs = nullptr;
+  std::vector<SubDev> subs;
+  int max_pad = 0, max_own = 0, max_flux = 0;
+  int* d_owner[3] = {nullptr, nullptr, nullptr};
+  int* d_axis_off[3] = {nullptr, nullptr, nullptr};
+  int* d_axis_len[3] = {nullptr, nullptr, nullptr};
+  double* d_thomas = nullptr;
+  int Lmax = 0;
+  double filt_h[6] = {0};
+  double* d_partial = nullptr;
+  double* d_out = nullptr;
+  int diag_blocks = 0;
+
+  Geometry geo{};
+  Physics phys{};
+
+  std::string err;
+  bool sticky = false;
+  long long launches = 0;
+
+  // per-kernel event timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> ev_pairs;  // (kind, index of the begin event)
+  double t_ms[CFS_NKINDS] = {0};
+  long long t_cnt[CFS_NKINDS] = {0};
+  cfs::Timer timer{};
+};
+
+static void timer_rec(void* self, int kind, int begin) {
+  cfs_ctx* c = (cfs_ctx*)self;
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    c->ev_pool.push_back(e);
+  }
+  const size_t idx = c->ev_used++;
+  cudaEventRecord(c->ev_pool[idx], c->stream);
+  if (begin) c->ev_pairs.push_back({kind, idx});
+}
+
+// Fold recorded event pairs into the per-kind totals (synchronises the stream).
+static void timer_flush(cfs_ctx* c) {
+  if (c->ev_pairs.empty()) { c->ev_used = 0; return; }
+  cudaStreamSynchronize(c->stream);
+  for (auto& pr : c->ev_pairs) {
+    float ms = 0.f;
+    if (pr.second + 1 < c->ev_used && cudaEventElapsedTime(&ms, c->ev_pool[pr.second], c->ev_pool[pr.second + 1]) == cudaSuccess) {
+      c->t_ms[pr.first] += ms;
+      c->t_cnt[pr.first] += 1;
+    }
+  }
+  c->ev_pairs.clear();
+  c->ev_used = 0;
+}
+
+static const char* kNoCtx = "null context";
+
+static cfs_status fail(cfs_ctx* c, cfs_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+static cfs_status cuda_fail(cfs_ctx* c, cudaError_t e, const char* where) {
+  c->sticky = true;
+  c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return CFS_ECUDA;
+}
+
+#define CUDA_TRY(c, expr, where)                  \
+  do {                                            \
+    cudaError_t e_ = (expr);                      \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+  } while (0)
+
+static void* default_alloc(size_t bytes, void*) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  return p;
+}
+static void default_free(void* p, void*) { cudaFree(p); }
+
+static void* dev_alloc(cfs_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  void* p = c->alloc(bytes, c->user);
+  if (p) c->owned.push_back(p);
+  return p;
+}
+
+static void dev_free(cfs_ctx* c, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->owned.size(); ++i)
+    if (c->owned[i] == p) {
+      c->owned.erase(c->owned.begin() + (long)i);
+      c->freef(p, c->user);
+      return;
+    }
+}
+
+static void split_axis(int n, int p, int idx, int* off, int* len) {
+  int base = n / p, rem = n % p;
+  *len = base + (idx < rem ? 1 : 0);
+  *off = idx * base + (idx < rem ? idx : rem);
+}
+
+extern "C" {
+
+cfs_status cfs_create(const cfs_params* p, void* cuda_stream, cfs_ctx** out) {
+  if (!p || !out) return CFS_EINVAL;
+  *out = nullptr;
+  if (p->order != 2 && p->order != 4) return CFS_EINVAL;
+  if (p->precision != 0 && p->precision != 1) return CFS_EINVAL;
+  if (p->filter && !(std::fabs(p->alpha_f) < 0.5)) return CFS_EINVAL;
+  if (!(p->gamma > 1.0) || !(p->mach > 0.0) || (p->viscous && (!(p->re > 0.0) || !(p->pr > 0.0)))) return CFS_EINVAL;
+  cfs_ctx* c = new cfs_ctx();
+  c->p = *p;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->alloc = default_alloc;
+  c->freef = default_free;
+  c->s = cfs::lserk_coeffs(p->order, c->A, c->B);
+  c->C = p->order == 4 ? 5 : 3;
+  c->r = p->order == 4 ? 2 : 1;
+  c->G = p->viscous ? 2 * c->r : c->r;
+  *out = c;
+  return CFS_OK;
+}
+
+cfs_status cfs_set_allocator(cfs_ctx* c, cfs_alloc_fn alloc, cfs_free_fn free_fn, void* user) {
+  if (!c) return CFS_EINVAL;
+  if (c->finalized) return fail(c, CFS_ESTATE, "allocator must be set before cfs_finalize");
+  if (!alloc || !free_fn) return fail(c, CFS_EINVAL, "allocator and free function required");
+  c->alloc = alloc;
+  c->freef = free_fn;
+  c->user = user;
+  return CFS_OK;
+}
+
+cfs_status cfs_add_block(cfs_ctx* c, int ni, int nj, int nk, const double* spacing, int* block_id) {
+  if (!c) return CFS_EINVAL;
+  if (c->finalized) return fail(c, CFS_ESTATE, "blocks must be added before cfs_finalize");
+  if (c->has_block) return fail(c, CFS_EINVAL, "this version supports a single block");
+  if (ni < 1 || nj < 1 || nk < 1 || !spacing) return fail(c, CFS_EINVAL, "bad block size");
+  for (int a = 0; a < 3; ++a)
+    if (!(spacing[a] > 0.0)) return fail(c, CFS_EINVAL, "spacing must be positive");
+  if ((long long)ni * nj * nk > (1LL << 31)) return fail(c, CFS_EINVAL, "block too large");
+  c->nx = ni; c->ny = nj; c->nz = nk;
+  for (int a = 0; a < 3; ++a) c->h[a] = spacing[a];
+  c->has_block = true;
+  c->ndim = nk > 1 ? 3 : 2;
+  c->Gz = nk > 1 ? c->G : 0;
+  if (block_id) *block_id = 0;
+  return CFS_OK;
+}
+
+cfs_status cfs_split_block(cfs_ctx* c, int block, int pi, int pj, int pk) {
+  if (!c) return CFS_EINVAL;
+  if (c->finalized) return fail(c, CFS_ESTATE, "split before cfs_finalize");
+  if (!c->has_block || block != 0) return fail(c, CFS_EINVAL, "unknown block");
+  if (pi < 1 || pj < 1 || pk < 1 || pi > c->nx || pj > c->ny || pk > c->nz)
+    return fail(c, CFS_EINVAL, "bad split");
+  c->P[0] = pi; c->P[1] = pj; c->P[2] = pk;
+  return CFS_OK;
+}
+
+cfs_status cfs_connect(cfs_ctx* c, int blockA, int faceA, int blockB, int faceB, int orientation) {
+  if (!c) return CFS_EINVAL;
+  if (blockA == 0 && blockB == 0 && c->has_block && orientation == 0 && faceA >= 0 && faceA < 6 &&
+      faceB == (faceA ^ 1))
+    return CFS_OK;  // periodic self-connection: the default
+  return fail(c, CFS_EINVAL, "only periodic self-connections are supported in this version");
+}
+
+cfs_status cfs_set_bc(cfs_ctx* c, int, int, int, const double*) {
+  if (!c) return CFS_EINVAL;
+  return fail(c, CFS_EINVAL, "physical boundary conditions are not supported in this version");
+}
+
+cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
+  if (!c) return CFS_EINVAL;
+  if (c->finalized) return fail(c, CFS_ESTATE, "already finalized");
+  if (!c->has_block) return fail(c, CFS_ESTATE, "no block");
+  if (max_delay < 0 || max_delay > CFS_MAX_DELAY) return fail(c, CFS_EINVAL, "max_delay out of range");
+  const int need = c->p.filter ? (c->G > 5 ? c->G : 5) : c->G;
+  // sub-domain table
+  const int nsub = c->P[0] * c->P[1] * c->P[2];
+  c->subs.resize(nsub);
+  long long pbase = 0;
+  c->max_pad = c->max_own = c->max_flux = 0;
+  const int rz = c->ndim == 3 ? c->r : 0;
+  for (int iz = 0; iz < c->P[2]; ++iz)
+    for (int iy = 0; iy < c->P[1]; ++iy)
+      for (int ix = 0; ix < c->P[0]; ++ix) {
+        SubDev d{};
+        split_axis(c->nx, c->P[0], ix, &d.ox, &d.sx);
+        split_axis(c->ny, c->P[1], iy, &d.oy, &d.sy);
+        split_axis(c->nz, c->P[2], iz, &d.oz, &d.sz);
+        if (d.sx < need || d.sy < need || (c->ndim == 3 && d.sz < need))
+          return fail(c, CFS_EINVAL, "sub-domain smaller than the halo it needs");
+        d.ex = d.sx + 2 * c->G;
+        d.ey = d.sy + 2 * c->G;
+        d.ez = d.sz + 2 * c->Gz;
+        d.ix = ix; d.iy = iy; d.iz = iz;
+        d.pbase = pbase;
+        const long long npad = (long long)d.ex * d.ey * d.ez;
+        pbase += npad;
+        const long long nown = (long long)d.sx * d.sy * d.sz;
+        const long long nfl = (long long)(d.sx + 2 * c->r) * (d.sy + 2 * c->r) * (d.sz + 2 * rz);
+        if (npad > (1LL << 30)) return fail(c, CFS_EINVAL, "sub-domain too large");
+        c->max_pad = (int)std::max<long long>(c->max_pad, npad);
+        c->max_own = (int)std::max<long long>(c->max_own, nown);
+        c->max_flux = (int)std::max<long long>(c->max_flux, nfl);
+        c->subs[ix + c->P[0] * (iy + c->P[1] * iz)] = d;
+      }
+  c->max_delay = max_delay;
+  c->R = max_delay + c->C + 1;
+  const long long N = (long long)c->nx * c->ny * c->nz;
+  const size_t tsz = c->p.precision == 1 ? sizeof(float) : sizeof(double);
+  // geometry / physics
+  Geometry& g = c->geo;
+  g.nx = c->nx; g.ny = c->ny; g.nz = c->nz; g.N = N; g.nsub = nsub;
+  g.G = c->G; g.Gz = c->Gz; g.r = c->r; g.ndim = c->ndim; g.viscous = c->p.viscous; g.Ptot = pbase;
+  Physics& ph = c->phys;
+  ph.gamma = c->p.gamma; ph.gm1 = c->p.gamma - 1.0; ph.gM2 = c->p.gamma * c->p.mach * c->p.mach;
+  ph.ire = c->p.viscous ? 1.0 / c->p.re : 0.0;
+  ph.kappa = c->p.viscous ? 1.0 / ((c->p.gamma - 1.0) * c->p.pr * c->p.mach * c->p.mach) : 0.0;
+  ph.visc_law = c->p.visc_law; ph.visc_exp = c->p.visc_exp;
+  // CD coefficients of Eq. 2 with alpha = 0: CD4 a = 4/3, b = -1/3; CD2 a = 1, b = 0
+  const double a_cd = c->p.order == 4 ? 4.0 / 3.0 : 1.0, b_cd = c->p.order == 4 ? -1.0 / 3.0 : 0.0;
+  for (int a = 0; a < 3; ++a) {
+    ph.c1[a] = (a_cd / 2.0) / c->h[a];
+    ph.c2[a] = (b_cd / 4.0) / c->h[a];
+  }
+  // device memory
+  c->ring = (double*)dev_alloc(c, sizeof(double) * 5 * N * c->R);
+  c->buf[0] = (double*)dev_alloc(c, sizeof(double) * 5 * N);
+  c->buf[1] = (double*)dev_alloc(c, sizeof(double) * 5 * N);
+  c->Q = (double*)dev_alloc(c, sizeof(double) * 5 * N);
+  c->Wp = dev_alloc(c, tsz * 7 * (size_t)pbase);
+  c->Phi = dev_alloc(c, tsz * 15 * (size_t)pbase);
+  c->d_subs = (SubDev*)dev_alloc(c, sizeof(SubDev) * nsub);
+  const int nW = (max_delay + 1) * c->s * c->C, nWf = (max_delay + 1) * c->C;
+  c->d_W = (double*)dev_alloc(c, sizeof(double) * nW);
+  c->d_Wf = (double*)dev_alloc(c, sizeof(double) * nWf);
+  c->diag_blocks = 4 * 152;
+  c->d_partial = (double*)dev_alloc(c, sizeof(double) * 8 * c->diag_blocks);
+  c->d_out = (double*)dev_alloc(c, sizeof(double) * 8);
+  const int n3[3] = {c->nx, c->ny, c->nz};
+  c->Lmax = 0;
+  for (int a = 0; a < 3; ++a) {
+    c->d_owner[a] = (int*)dev_alloc(c, sizeof(int) * n3[a]);
+    c->d_axis_off[a] = (int*)dev_alloc(c, sizeof(int) * c->P[a]);
+    c->d_axis_len[a] = (int*)dev_alloc(c, sizeof(int) * c->P[a]);
+    c->Lmax = std::max(c->Lmax, (n3[a] + c->P[a] - 1) / c->P[a]);
+  }
+  c->d_thomas = (double*)dev_alloc(c, sizeof(double) * (size_t)(c->Lmax + 1) * 2 * c->Lmax);
+  for (void* q : c->owned)
+    if (!q) return fail(c, CFS_ENOMEM, "device allocation failed");
+  if (!c->ring || !c->buf[0] || !c->buf[1] || !c->Q || !c->Wp || !c->Phi || !c->d_subs || !c->d_W || !c->d_Wf ||
+      !c->d_partial || !c->d_out || !c->d_thomas)
+    return fail(c, CFS_ENOMEM, "device allocation failed");
+  for (int a = 0; a < 3; ++a)
+    if (!c->d_owner[a] || !c->d_axis_off[a] || !c->d_axis_len[a]) return fail(c, CFS_ENOMEM, "device allocation failed");
+  // host tables
+  std::vector<double> W(nW), Wf(nWf);
+  if (cfs::at_weight_table(c->p.order, max_delay, W.data()) != nW ||
+      cfs::filter_extrap_table(c->p.order, max_delay, Wf.data()) != nWf)
+    return fail(c, CFS_EINVAL, "coefficient generation failed");
+  double filt[6] = {1, 0, 0, 0, 0, 0};
+  if (c->p.filter && !cfs::pade10_coeffs(c->p.alpha_f, filt)) return fail(c, CFS_EINVAL, "filter coefficients failed");
+  c->filt_h[0] = filt[0];
+  for (int m = 1; m < 6; ++m) c->filt_h[m] = 0.5 * filt[m];
+  std::vector<double> th((size_t)(c->Lmax + 1) * 2 * c->Lmax, 0.0);
+  const double al = c->p.alpha_f;
+  for (int len = 1; len <= c->Lmax; ++len) {
+    double* cp = th.data() + (size_t)len * 2 * c->Lmax;
+    double* im = cp + c->Lmax;
+    double m = 1.0;
+    cp[0] = al / m;
+    im[0] = 1.0 / m;
+    for (int i = 1; i < len; ++i) {
+      m = 1.0 - al * cp[i - 1];
+      cp[i] = al / m;
+      im[i] = 1.0 / m;
+    }
+  }
+  std::vector<int> owner[3], aoff[3], alen[3];
+  for (int a = 0; a < 3; ++a) {
+    owner[a].resize(n3[a]);
+    aoff[a].resize(c->P[a]);
+    alen[a].resize(c->P[a]);
+    for (int i = 0; i < c->P[a]; ++i) {
+      split_axis(n3[a], c->P[a], i, &aoff[a][i], &alen[a][i]);
+      for (int t = 0; t < alen[a][i]; ++t) owner[a][aoff[a][i] + t] = i;
+    }
+  }
+  cudaStream_t st = c->stream;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_subs, c->subs.data(), sizeof(SubDev) * nsub, cudaMemcpyHostToDevice, st), "upload sub-domains");
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_W, W.data(), sizeof(double) * nW, cudaMemcpyHostToDevice, st), "upload weights");
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_Wf, Wf.data(), sizeof(double) * nWf, cudaMemcpyHostToDevice, st), "upload weights");
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_thomas, th.data(), sizeof(double) * th.size(), cudaMemcpyHostToDevice, st), "upload filter");
+  for (int a = 0; a < 3; ++a) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_owner[a], owner[a].data(), sizeof(int) * n3[a], cudaMemcpyHostToDevice, st), "upload tables");
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_axis_off[a], aoff[a].data(), sizeof(int) * c->P[a], cudaMemcpyHostToDevice, st), "upload tables");
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_axis_len[a], alen[a].data(), sizeof(int) * c->P[a], cudaMemcpyHostToDevice, st), "upload tables");
+  }
+  CUDA_TRY(c, cudaMemsetAsync(c->ring, 0, sizeof(double) * 5 * N * c->R, st), "clear ring");
+  // the host vectors above are pageable: make sure the copies have consumed them
+  CUDA_TRY(c, cudaStreamSynchronize(st), "finalize");
+  c->finalized = true;
+  c->n = 0;
+  return CFS_OK;
+}
+
+cfs_status cfs_set_schedule(cfs_ctx* c, int algo, int at, int L, long long nsteps, const int8_t* delays) {
+  if (!c) return CFS_EINVAL;
+  if (!c->finalized) return fail(c, CFS_ESTATE, "schedule after cfs_finalize");
+  if (algo < 0 || algo > 2) return fail(c, CFS_EINVAL, "algo must be 0 (SA), 1 (CAA) or 2 (SAA)");
+  if (algo == 1 && (L < 1 || L - 1 > c->max_delay)) return fail(c, CFS_EINVAL, "CAA needs 1 <= L <= max_delay + 1");
+  if (algo == 2) {
+    if (nsteps < 1 || !delays) return fail(c, CFS_EINVAL, "SAA needs a delay table");
+    const long long cnt = nsteps * (long long)c->subs.size() * 6;
+    for (long long i = 0; i < cnt; ++i)
+      if (delays[i] < 0 || delays[i] > c->max_delay) return fail(c, CFS_EINVAL, "delay outside [0, max_delay]");
+    if (c->d_sched) {
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream), "schedule");
+      dev_free(c, c->d_sched);
+      c->d_sched = nullptr;
+    }
+    c->d_sched = (int8_t*)dev_alloc(c, (size_t)cnt);
+    if (!c->d_sched) return fail(c, CFS_ENOMEM, "schedule allocation failed");
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_sched, delays, (size_t)cnt, cudaMemcpyHostToDevice, c->stream), "upload schedule");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream), "upload schedule");
+    c->sched_steps = nsteps;
+  }
+  c->algo = algo;
+  c->at = at ? 1 : 0;
+  c->L = algo == 1 ? L : 1;
+  return CFS_OK;
+}
+
+static double* level_ptr(cfs_ctx* c, long long level) { return c->ring + (size_t)(level % c->R) * 5 * c->geo.N; }
+
+cfs_status cfs_set_state(cfs_ctx* c, int block, const double* U, int where) {
+  if (!c) return CFS_EINVAL;
+  if (!c->finalized) return fail(c, CFS_ESTATE, "set_state after cfs_finalize");
+  if (block != 0 || !U) return fail(c, CFS_EINVAL, "bad block or pointer");
+  if (c->sticky) return CFS_ECUDA;
+  const size_t bytes = sizeof(double) * 5 * c->geo.N;
+  CUDA_TRY(c, cudaMemcpyAsync(level_ptr(c, c->n), U, bytes, where ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream), "set_state");
+  if (!where) CUDA_TRY(c, cudaStreamSynchronize(c->stream), "set_state");
+  return CFS_OK;
+}
+
+cfs_status cfs_get_state(cfs_ctx* c, int block, double* U, int where) {
+  if (!c) return CFS_EINVAL;
+  if (!c->finalized) return fail(c, CFS_ESTATE, "get_state after cfs_finalize");
+  if (block != 0 || !U) return fail(c, CFS_EINVAL, "bad block or pointer");
+  if (c->sticky) return CFS_ECUDA;
+  const size_t bytes = sizeof(double) * 5 * c->geo.N;
+  CUDA_TRY(c, cudaMemcpyAsync(U, level_ptr(c, c->n), bytes, where ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream), "get_state");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream), "get_state");
+  return CFS_OK;
+}
+
+cfs_status cfs_set_dt(cfs_ctx* c, double dt) {
+  if (!c) return CFS_EINVAL;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CFS_EINVAL, "dt must be positive");
+  c->dt = dt;
+  c->dt_set = true;
+  return CFS_OK;
+}
+
+cfs_status cfs_get_step(cfs_ctx* c, long long* n) {
+  if (!c || !n) return CFS_EINVAL;
+  *n = c->n;
+  return CFS_OK;
+}
+
+cfs_status cfs_set_step(cfs_ctx* c, long long n) {
+  if (!c) return CFS_EINVAL;
+  if (n < 0) return fail(c, CFS_EINVAL, "negative step");
+  c->n = n;
+  return CFS_OK;
+}
+
+cfs_status cfs_step(cfs_ctx* c, long long nsteps) {
+  if (!c) return CFS_EINVAL;
+  if (!c->finalized) return fail(c, CFS_ESTATE, "step after cfs_finalize");
+  if (!c->dt_set) return fail(c, CFS_ESTATE, "dt not set");
+  if (c->sticky) return CFS_ECUDA;
+  if (nsteps < 0) return fail(c, CFS_EINVAL, "negative step count");
+  c->launches = 0;
+  const Geometry& g = c->geo;
+  const int nops = c->s + (c->p.filter ? c->ndim : 0);
+  for (long long it = 0; it < nsteps; ++it) {
+    const long long n = c->n;
+    StepSched sc{};
+    sc.n = n;
+    sc.R = c->R;
+    sc.algo = c->algo;
+    sc.L = c->L;
+    sc.C = c->C;
+    sc.cap = n - c->C + 1;
+    sc.mode = (c->algo == 0 || n < c->C) ? 0 : (c->at ? 1 : 2);
+    sc.W = c->d_W;
+    sc.Wf = c->d_Wf;
+    sc.table = nullptr;
+    if (sc.mode != 0 && c->algo == 2) {
+      if (n >= c->sched_steps) return fail(c, CFS_EINVAL, "step beyond the SAA delay table");
+      sc.table = c->d_sched + (size_t)n * c->subs.size() * 6;
+    }
+    const double* src = level_ptr(c, n);
+    int pp = 0;
+    for (int op = 0; op < nops; ++op) {
+      double* dst = (op == nops - 1) ? level_ptr(c, n + 1) : c->buf[pp];
+      int rc;
+      if (op < c->s) {
+        cfs::StageLaunch a{};
+        a.Uin = src; a.Uout = dst; a.Q = c->Q; a.ring = c->ring; a.subs = c->d_subs;
+        a.Wp = c->Wp; a.Phi = c->Phi; a.stage = op; a.s = c->s;
+        a.A = c->A[op]; a.B = c->B[op]; a.dt = c->dt;
+        a.first = op == 0; a.last = op == c->s - 1;
+        a.max_pad = c->max_pad; a.max_own = c->max_own; a.max_flux = c->max_flux;
+        rc = cfs::launch_stage(g, c->phys, sc, a, c->p.precision, c->stream, &c->launches,
+                               c->timing ? &c->timer : nullptr);
+      } else {
+        cfs::FilterLaunch f{};
+        f.Uin = src; f.Uout = dst; f.ring = c->ring;
+        for (int a = 0; a < 3; ++a) {
+          f.owner[a] = c->d_owner[a]; f.axis_off[a] = c->d_axis_off[a]; f.axis_len[a] = c->d_axis_len[a];
+          f.P[a] = c->P[a];
+        }
+        f.thomas = c->d_thomas; f.Lmax = c->Lmax; f.alpha = c->p.alpha_f;
+        for (int m = 0; m < 6; ++m) f.h[m] = c->filt_h[m];
+        rc = cfs::launch_filter(g, sc, f, op - c->s, c->p.precision, c->stream, &c->launches,
+                                c->timing ? &c->timer : nullptr);
+      }
+      if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
+      src = dst;
+      if (op != nops - 1) pp ^= 1;
+    }
+    c->n = n + 1;
+    if (c->timing && c->ev_used > 4096) timer_flush(c);
+  }
+  return CFS_OK;
+}
+
+cfs_status cfs_set_timing(cfs_ctx* c, int on) {
+  if (!c) return CFS_EINVAL;
+  if (c->timing) timer_flush(c);
+  c->timing = on != 0;
+  for (int k = 0; k < CFS_NKINDS; ++k) { c->t_ms[k] = 0.0; c->t_cnt[k] = 0; }
+  c->timer.rec = timer_rec;
+  c->timer.self = c;
+  return CFS_OK;
+}
+
+cfs_status cfs_get_timing(cfs_ctx* c, double* ms, long long* count) {
+  if (!c) return CFS_EINVAL;
+  timer_flush(c);
+  for (int k = 0; k < CFS_NKINDS; ++k) {
+    if (ms) ms[k] = c->t_ms[k];
+    if (count) count[k] = c->t_cnt[k];
+  }
+  return CFS_OK;
+}
+
+cfs_status cfs_diagnostics(cfs_ctx* c, double* out) {
+  if (!c || !out) return CFS_EINVAL;
+  if (!c->finalized) return fail(c, CFS_ESTATE, "diagnostics after cfs_finalize");
+  if (c->sticky) return CFS_ECUDA;
+  const double dV = c->h[0] * c->h[1] * (c->ndim == 3 ? c->h[2] : 1.0);
+  int rc = cfs::launch_diagnostics(c->geo, c->phys, level_ptr(c, c->n), c->d_partial, c->diag_blocks, c->d_out, dV,
+                                   c->stream, nullptr);
+  if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "diagnostics launch");
+  CUDA_TRY(c, cudaMemcpyAsync(out, c->d_out, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream), "diagnostics");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream), "diagnostics");
+  if (out[7] != 0.0) return fail(c, CFS_ENAN, "non-finite value in the state");
+  return CFS_OK;
+}
+
+cfs_status cfs_ring_depth(cfs_ctx* c, int* R) {
+  if (!c || !R) return CFS_EINVAL;
+  if (!c->finalized) return fail(c, CFS_ESTATE, "ring depth after cfs_finalize");
+  *R = c->R;
+  return CFS_OK;
+}
+
+static cfs_status ring_copy(cfs_ctx* c, double* buf, int where, bool to_ring) {
+  const size_t lvl = sizeof(double) * 5 * c->geo.N;
+  for (int i = 0; i < c->R; ++i) {
+    const long long level = c->n - c->R + 1 + i;
+    if (level < 0) continue;
+    double* dev = level_ptr(c, level);
+    double* other = buf + (size_t)i * 5 * c->geo.N;
+    cudaMemcpyKind kind = where ? cudaMemcpyDeviceToDevice : (to_ring ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+    CUDA_TRY(c, cudaMemcpyAsync(to_ring ? dev : other, to_ring ? other : dev, lvl, kind, c->stream), "ring copy");
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream), "ring copy");
+  return CFS_OK;
+}
+
+cfs_status cfs_get_ring(cfs_ctx* c, double* buf, int where) {
+  if (!c || !buf) return CFS_EINVAL;
+  if (!c->finalized) return fail(c, CFS_ESTATE, "ring after cfs_finalize");
+  if (c->sticky) return CFS_ECUDA;
+  return ring_copy(c, buf, where, false);
+}
+
+cfs_status cfs_set_ring(cfs_ctx* c, const double* buf, int where) {
+  if (!c || !buf) return CFS_EINVAL;
+  if (!c->finalized) return fail(c, CFS_ESTATE, "ring after cfs_finalize");
+  if (c->sticky) return CFS_ECUDA;
+  return ring_copy(c, const_cast<double*>(buf), where, true);
+}
+
+cfs_status cfs_launch_count(cfs_ctx* c, long long* launches) {
+  if (!c || !launches) return CFS_EINVAL;
+  *launches = c->launches;
+  return CFS_OK;
+}
+
+const char* cfs_last_error(cfs_ctx* c) {
+  if (!c) return kNoCtx;
+  return c->err.c_str();
+}
+
+void cfs_destroy(cfs_ctx* c) {
+  if (!c) return;
+  if (c->finalized) cudaStreamSynchronize(c->stream);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (void* q : c->owned) c->freef(q, c->user);
+  c->owned.clear();
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,115 @@
+// cfs_internal.h -- library-private declarations shared by the host (capi.cpp, coeffs.cpp) and
+// the CUDA translation units of libcfs.  Not part of the public C ABI (include/cfs.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#define CFS_MAX_DELAY 15   // largest supported delay k (ring depth <= 15 + 5 + 1)
+#define CFS_MAX_LEVELS 5   // C: delayed levels of AT4
+#define CFS_MAX_STAGES 5   // s: stages of LSERK4
+
+namespace cfs {
+
+// Sub-domain descriptor (one per processing element of Sec. 3).
+struct SubDev {
+  int ox, oy, oz;     // owned box origin (global point indices)
+  int sx, sy, sz;     // owned box size
+  int ex, ey, ez;     // padded ("view") box size: owned + halo G (Gz = 0 in 2-D)
+  int ix, iy, iz;     // sub-domain coordinates in the decomposition grid
+  long long pbase;    // offset of the padded box in the scratch arrays (points)
+};
+
+// Scalars every kernel needs; passed by value.
+struct Geometry {
+  int nx, ny, nz;        // global block size
+  long long N;           // nx * ny * nz
+  int nsub;              // number of sub-domains
+  int G, Gz;             // halo depth in x/y and in z
+  int r;                 // stencil radius (2 for CD4, 1 for CD2)
+  int ndim;              // 2 or 3
+  int viscous;
+  long long Ptot;        // total padded points (scratch length per component)
+};
+
+struct Physics {
+  double gamma, gm1, gM2;  // gamma, gamma - 1, gamma M^2
+  double ire;              // 1 / Re
+  double kappa;            // 1 / ((gamma - 1) Pr M^2)
+  int visc_law;
+  double visc_exp;
+  double c1[3], c2[3];     // CD coefficients per axis: c1 = (a/2)/h, c2 = (b/4)/h
+};
+
+// Delay schedule as seen by the kernels of one step.
+struct StepSched {
+  int mode;              // 0 SA (halo = live neighbour), 1 AT, 2 AS
+  long long n;           // step index
+  int R;                 // ring depth
+  int algo;              // 0 SA, 1 CAA, 2 SAA
+  int L;                 // CAA interval
+  int C;                 // delayed levels
+  long long cap;         // clamp: k <= n - C + 1
+  const int8_t* table;   // SAA delays of this step [nsub][6] (device), or null
+  const double* W;       // device: AT halo weights [(k * s + m) * C + l]
+  const double* Wf;      // device: filter-halo extrapolation weights c(k+1) [k * C + l]
+};
+
+// coefficient generation (coeffs.cpp)
+int lserk_coeffs(int order, double* A, double* B);
+bool extrap_weights(int order, int k, long double* c);
+bool buffer_dudt_weights(int order, int e, int k, long double* d);
+int at_weight_table(int order, int kmax, double* W);
+int filter_extrap_table(int order, int kmax, double* Wf);
+bool pade10_coeffs(double alpha, double* a);
+
+// kernel launchers (kernels.cu); all return a cudaError_t cast to int
+
+struct StageLaunch {
+  const double* Uin;
+  double* Uout;
+  double* Q;
+  const double* ring;   // [R][5][N]
+  const SubDev* subs;   // device table
+  void* Wp;             // scratch [7][Ptot] primitives, in the intermediate precision
+  void* Phi;            // scratch [15][Ptot] combined fluxes, in the intermediate precision
+  int stage;            // 0-based stage index m-1 (selects the halo weights W^(m-1))
+  int s;                // number of stages
+  double A, B, dt;
+  int first, last;      // first stage skips reading Q, last stage skips writing Q
+  int max_pad;          // largest padded box (points)
+  int max_own;          // largest owned box (points)
+  int max_flux;         // largest flux region box (points)
+};
+
+// Optional per-kernel event timing: when non-null, the launchers call rec(kind, begin) around
+// every kernel on the launch stream.
+struct Timer {
+  void (*rec)(void* self, int kind, int begin);
+  void* self;
+};
+
+int launch_stage(const Geometry& g, const Physics& ph, const StepSched& sc, const StageLaunch& a,
+                 int precision, void* stream, long long* launches, const Timer* tm);
+
+struct FilterLaunch {
+  const double* Uin;
+  double* Uout;
+  const double* ring;
+  const int* owner[3];     // device: sub-domain index along each axis for every global coordinate
+  const int* axis_off[3];  // device: per sub-domain index along the axis, its origin
+  const int* axis_len[3];  // device: ... and its length
+  const double* thomas;    // device: [Lmax+1 rows][2][Lmax] Thomas factors per line length
+  int Lmax;
+  int P[3];                // sub-domains per axis
+  double alpha;
+  double h[6];             // filter right side: a_0, a_1/2, ..., a_5/2
+};
+
+int launch_filter(const Geometry& g, const StepSched& sc, const FilterLaunch& f, int axis, int precision,
+                  void* stream, long long* launches, const Timer* tm);
+
+int launch_diagnostics(const Geometry& g, const Physics& ph, const double* U, double* partial, int nblocks,
+                       double* out, double dV, void* stream, long long* launches);
+
+}  // namespace cfs

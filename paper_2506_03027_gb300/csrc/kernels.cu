@@ -1,0 +1,411 @@
+// kernels.cu -- CUDA kernels (sm_103a) of the asynchronous compressible-flow hot path.
+//
+// One LSERK stage (Eq. 3) of the method of arXiv 2506.03027 runs as three kernels over every
+// sub-domain ("PE", Sec. 3):
+//   k_view  : the stage input U^(m-1) as the sub-domain sees it -- its own points plus a halo
+//             taken from the live neighbour values (SA, Alg. 1), from the delayed levels of the
+//             ring combined with the AT weights W^(m-1)(k) (Eq. 14-15 at m = 1, then the buffer
+//             updates of Eq. 8 / Table 5 collapsed into weights), or from the latest delayed level
+//             (AS) -- converted to primitives (App. A).
+//   k_flux  : combined fluxes Phi_a = -F_a + Fv_a / Re (Eq. A2-A4) at the owned points and at
+//             the halo points within the stencil radius along a; viscous gradients by CD.
+//   k_rk    : R = sum_a D_a Phi_a with the CD scheme of Eq. 2, fused with the low-storage RK
+//             update Q = A Q + dt R, U^(m) = U^(m-1) + B Q (FP64 accumulation).
+// The tenth-order Pade filter (once per step) is k_filter, one tridiagonal line solve per
+// thread with a Dirichlet closure at the first halo point.  k_diag* reduce the diagnostics.
+//
+// Data layout: global state arrays are SoA FP64 [5][nz][ny][nx]; the ring holds R full states
+// (level t in slot t mod R).  Scratch arrays are component-major over the concatenated padded
+// boxes of all sub-domains.
+#include <cuda_runtime.h>
+
+#include "cfs_internal.h"
+
+namespace cfs {
+
+__device__ __forceinline__ int wrapc(int i, int n) {
+  int r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+// Delay of face f (0..5) of sub-domain sid at this step, clamped so every level exists.
+__device__ __forceinline__ int face_delay(const StepSched& sc, int sid, int f) {
+  int k = 0;
+  if (sc.algo == 1) k = (int)((sc.n - sc.C) % sc.L);
+  else if (sc.algo == 2) k = sc.table[sid * 6 + f];
+  if (k > sc.cap) k = (int)sc.cap;
+  if (k < 0) k = 0;
+  return k;
+}
+
+// ------------------------------------------------------------------------------- k_view
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_view(Geometry g, Physics ph, StepSched sc, const double* __restrict__ Uin,
+                                              const double* __restrict__ ring, const SubDev* __restrict__ subs,
+                                              T* __restrict__ Wp, int stage, int s) {
+  const int sid = blockIdx.y;
+  const SubDev d = subs[sid];
+  const long long npad = (long long)d.ex * d.ey * d.ez;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npad) return;
+  const int i = (int)(t % d.ex);
+  const int j = (int)((t / d.ex) % d.ey);
+  const int k = (int)(t / ((long long)d.ex * d.ey));
+  const int ci = i - g.G, cj = j - g.G, ck = k - g.Gz;
+  const int dx = ci < 0 ? -ci : (ci >= d.sx ? ci - d.sx + 1 : 0);
+  const int dy = cj < 0 ? -cj : (cj >= d.sy ? cj - d.sy + 1 : 0);
+  const int dz = ck < 0 ? -ck : (ck >= d.sz ? ck - d.sz + 1 : 0);
+  const int nout = (dx > 0) + (dy > 0) + (dz > 0);
+  if (nout >= 3) return;
+  if (nout == 2) {
+    // viscous cross derivatives need r x r edge halos only
+    if (!g.viscous) return;
+    if (dx > g.r || dy > g.r || dz > g.r) return;
+  }
+  const int gx = wrapc(d.ox + ci, g.nx), gy = wrapc(d.oy + cj, g.ny), gz = wrapc(d.oz + ck, g.nz);
+  const long long gi = (long long)gx + (long long)g.nx * ((long long)gy + (long long)g.ny * gz);
+  double u[5];
+  if (nout == 0 || sc.mode == 0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = Uin[v * g.N + gi];
+  } else {
+    int kd = 0;
+    if (dx > 0) kd = max(kd, face_delay(sc, sid, ci < 0 ? 0 : 1));
+    if (dy > 0) kd = max(kd, face_delay(sc, sid, cj < 0 ? 2 : 3));
+    if (dz > 0) kd = max(kd, face_delay(sc, sid, ck < 0 ? 4 : 5));
+    const long long lvN = 5 * g.N;
+    if (sc.mode == 2) {
+      const double* src = ring + (long long)((sc.n - kd) % sc.R) * lvN;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) u[v] = src[v * g.N + gi];
+    } else {
+      const double* w = sc.W + (kd * s + stage) * sc.C;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) u[v] = 0.0;
+      for (int l = 0; l < sc.C; ++l) {
+        const double* src = ring + (long long)((sc.n - kd - l) % sc.R) * lvN;
+        const double wl = __ldg(w + l);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = fma(wl, src[v * g.N + gi], u[v]);
+      }
+    }
+  }
+  // primitives (App. A): p = (gamma-1)(rho E - rho|u|^2/2), T = gamma M^2 p / rho
+  const T rho = (T)u[0];
+  const T ir = (T)1 / rho;
+  const T uu = (T)u[1] * ir, vv = (T)u[2] * ir, ww = (T)u[3] * ir;
+  const T ke = (T)0.5 * ((T)u[1] * uu + (T)u[2] * vv + (T)u[3] * ww);
+  const T p = (T)ph.gm1 * ((T)u[4] - ke);
+  const T temp = (T)ph.gM2 * p * ir;
+  const long long P = g.Ptot, o = d.pbase + t;
+  Wp[o] = rho;
+  Wp[P + o] = uu;
+  Wp[2 * P + o] = vv;
+  Wp[3 * P + o] = ww;
+  Wp[4 * P + o] = p;
+  Wp[5 * P + o] = temp;
+  Wp[6 * P + o] = (T)u[4] + p;  // rho E + p (energy flux factor)
+}
+
+// ------------------------------------------------------------------------------- k_flux
+
+template <typename T>
+__device__ __forceinline__ T cdiff(const T* __restrict__ f, long long q, long long st, T c1, T c2, int r) {
+  T d = c1 * (f[q + st] - f[q - st]);
+  if (r == 2) d = fma(c2, f[q + 2 * st] - f[q - 2 * st], d);
+  return d;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_flux(Geometry g, Physics ph, const SubDev* __restrict__ subs,
+                                              const T* __restrict__ Wp, T* __restrict__ Phi) {
+  const int sid = blockIdx.y;
+  const SubDev d = subs[sid];
+  const int r = g.r;
+  const int rz = (g.ndim == 3) ? r : 0;
+  const int fx = d.sx + 2 * r, fy = d.sy + 2 * r, fz = d.sz + 2 * rz;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)fx * fy * fz) return;
+  const int a0 = (int)(t % fx), b0 = (int)((t / fx) % fy), c0 = (int)(t / ((long long)fx * fy));
+  const int ci = a0 - r, cj = b0 - r, ck = c0 - rz;
+  const bool ox = ci < 0 || ci >= d.sx, oy = cj < 0 || cj >= d.sy, oz = ck < 0 || ck >= d.sz;
+  const int nout = (int)ox + (int)oy + (int)oz;
+  if (nout >= 2) return;
+  const long long sty = d.ex, stz = (long long)d.ex * d.ey;
+  const long long q = (long long)(ci + g.G) + sty * (cj + g.G) + stz * (ck + g.Gz);
+  const long long P = g.Ptot;
+  const T* W = Wp + d.pbase;
+  const T rho = W[q], u = W[P + q], v = W[2 * P + q], w = W[3 * P + q], p = W[4 * P + q];
+  const T et = W[6 * P + q];
+  const T vel[3] = {u, v, w};
+  // gradients du[i][j] = d u_i / d x_j, dT[j]
+  T du[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  T dT[3] = {0, 0, 0};
+  T mu = (T)1;
+  if (g.viscous) {
+    const long long st[3] = {1, sty, stz};
+    for (int b = 0; b < g.ndim; ++b) {
+      const T c1 = (T)ph.c1[b], c2 = (T)ph.c2[b];
+      du[0][b] = cdiff(W + P, q, st[b], c1, c2, r);
+      du[1][b] = cdiff(W + 2 * P, q, st[b], c1, c2, r);
+      du[2][b] = cdiff(W + 3 * P, q, st[b], c1, c2, r);
+      dT[b] = cdiff(W + 5 * P, q, st[b], c1, c2, r);
+    }
+    if (ph.visc_law == 1) mu = (T)pow((double)W[5 * P + q], ph.visc_exp);
+  }
+  const T div = du[0][0] + du[1][1] + du[2][2];
+  const T ire = (T)ph.ire, kap = (T)ph.kappa;
+  T* out = Phi + d.pbase;
+  for (int a = 0; a < g.ndim; ++a) {
+    if (nout == 1) {
+      if ((a == 0 && !ox) || (a == 1 && !oy) || (a == 2 && !oz)) continue;
+    }
+    const T ua = vel[a];
+    const T mflux = rho * ua;
+    T f[5];
+    f[0] = -mflux;
+    f[1] = -(mflux * u + (a == 0 ? p : (T)0));
+    f[2] = -(mflux * v + (a == 1 ? p : (T)0));
+    f[3] = -(mflux * w + (a == 2 ? p : (T)0));
+    f[4] = -(et * ua);
+    if (g.viscous) {
+      // tau_ai = mu (du_a/dx_i + du_i/dx_a) - 2/3 mu div delta_ai
+      T tau[3];
+#pragma unroll
+      for (int i2 = 0; i2 < 3; ++i2) tau[i2] = mu * (du[a][i2] + du[i2][a]);
+      tau[a] -= (T)(2.0 / 3.0) * mu * div;
+      const T qa = u * tau[0] + v * tau[1] + w * tau[2] + kap * mu * dT[a];
+      f[1] = fma(ire, tau[0], f[1]);
+      f[2] = fma(ire, tau[1], f[2]);
+      f[3] = fma(ire, tau[2], f[3]);
+      f[4] = fma(ire, qa, f[4]);
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[(long long)(a * 5 + c) * P + q] = f[c];
+  }
+}
+
+// ------------------------------------------------------------------------------- k_rk
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rk(Geometry g, Physics ph, const SubDev* __restrict__ subs,
+                                            const T* __restrict__ Phi, const double* __restrict__ Uin,
+                                            double* __restrict__ Uout, double* __restrict__ Q, double A, double B,
+                                            double dt, int first, int last) {
+  const int sid = blockIdx.y;
+  const SubDev d = subs[sid];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)d.sx * d.sy * d.sz) return;
+  const int ci = (int)(t % d.sx), cj = (int)((t / d.sx) % d.sy), ck = (int)(t / ((long long)d.sx * d.sy));
+  const long long sty = d.ex, stz = (long long)d.ex * d.ey;
+  const long long q = (long long)(ci + g.G) + sty * (cj + g.G) + stz * (ck + g.Gz);
+  const long long gi = (long long)(d.ox + ci) + (long long)g.nx * ((long long)(d.oy + cj) + (long long)g.ny * (d.oz + ck));
+  const long long P = g.Ptot;
+  const T* F = Phi + d.pbase;
+  const long long st[3] = {1, sty, stz};
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    T acc = (T)0;
+    for (int a = 0; a < g.ndim; ++a)
+      acc += cdiff(F + (long long)(a * 5 + c) * P, q, st[a], (T)ph.c1[a], (T)ph.c2[a], g.r);
+    const double R = (double)acc;
+    const double qn = first ? dt * R : fma(A, Q[c * g.N + gi], dt * R);
+    if (!last) Q[c * g.N + gi] = qn;
+    Uout[c * g.N + gi] = fma(B, qn, Uin[c * g.N + gi]);
+  }
+}
+
+static inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+#define TIMED(tm, kind, launch)              \
+  do {                                       \
+    if (tm) tm->rec(tm->self, kind, 1);      \
+    launch;                                  \
+    if (tm) tm->rec(tm->self, kind, 0);      \
+  } while (0)
+
+template <typename T>
+static int stage_impl(const Geometry& g, const Physics& ph, const StepSched& sc, const StageLaunch& a,
+                      cudaStream_t st, long long* launches, const Timer* tm) {
+  const int B = 256;
+  dim3 gv(nblk(a.max_pad, B), g.nsub), gf(nblk(a.max_flux, B), g.nsub), gr(nblk(a.max_own, B), g.nsub);
+  TIMED(tm, 0, (k_view<T><<<gv, B, 0, st>>>(g, ph, sc, a.Uin, a.ring, a.subs, (T*)a.Wp, a.stage, a.s)));
+  TIMED(tm, 1, (k_flux<T><<<gf, B, 0, st>>>(g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
+  TIMED(tm, 2, (k_rk<T><<<gr, B, 0, st>>>(g, ph, a.subs, (const T*)a.Phi, a.Uin, a.Uout, a.Q, a.A, a.B, a.dt,
+                                          a.first, a.last)));
+  if (launches) *launches += 3;
+  return (int)cudaGetLastError();
+}
+
+int launch_stage(const Geometry& g, const Physics& ph, const StepSched& sc, const StageLaunch& a, int precision,
+                 void* stream, long long* launches, const Timer* tm) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == 1) return stage_impl<float>(g, ph, sc, a, st, launches, tm);
+  return stage_impl<double>(g, ph, sc, a, st, launches, tm);
+}
+
+// ------------------------------------------------------------------------------- k_filter
+
+// One thread per (variable, line segment of one sub-domain).  Lines along `axis`; the two other
+// axes are f1 (x unless axis is x) and f2.  Right side: sum_n (a_n/2)(f_{i+n} + f_{i-n}) over an
+// 11-point window; Dirichlet closure f^_{-1} = f_{-1}, f^_L = f_L; forward elimination stores
+// the intermediate values in the output line, back substitution overwrites them.
+template <typename T>
+__global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, FilterLaunch f, int axis) {
+  const int f1 = (axis == 0) ? 1 : 0;
+  const int f2 = (axis == 2) ? 1 : 2;
+  const int n[3] = {g.nx, g.ny, g.nz};
+  const long long strides[3] = {1, g.nx, (long long)g.nx * g.ny};
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = 5LL * f.P[axis] * n[f1] * n[f2];
+  if (t >= total) return;
+  long long rest = t;
+  const int t1 = (int)(rest % n[f1]); rest /= n[f1];
+  const int t2 = (int)(rest % n[f2]); rest /= n[f2];
+  const int seg = (int)(rest % f.P[axis]);
+  const int var = (int)(rest / f.P[axis]);
+  int sidx[3];
+  sidx[axis] = seg;
+  sidx[f1] = f.owner[f1][t1];
+  sidx[f2] = f.owner[f2][t2];
+  const int sid = sidx[0] + f.P[0] * (sidx[1] + f.P[1] * sidx[2]);
+  const int off = f.axis_off[axis][seg], len = f.axis_len[axis][seg];
+  const long long st = strides[axis];
+  const long long base = (long long)var * g.N + (long long)t1 * strides[f1] + (long long)t2 * strides[f2];
+  const double* Uin = f.Uin;
+  const int kl = (sc.mode == 0) ? 0 : face_delay(sc, sid, 2 * axis);
+  const int kr = (sc.mode == 0) ? 0 : face_delay(sc, sid, 2 * axis + 1);
+  const long long lvN = 5 * g.N;
+  // value at line position i (halo for i < 0 or i >= len)
+  auto fetch = [&](int i) -> T {
+    const int c = wrapc(off + i, n[axis]);
+    const long long gi = base + (long long)c * st;
+    if ((i >= 0 && i < len) || sc.mode == 0) return (T)Uin[gi];
+    const int kd = i < 0 ? kl : kr;
+    if (sc.mode == 2) return (T)f.ring[(long long)((sc.n - kd) % sc.R) * lvN + gi];
+    double acc = 0.0;  // extrapolation to t_{n+1} with weights c(k+1), in FP64
+    for (int l = 0; l < sc.C; ++l)
+      acc = fma(__ldg(sc.Wf + kd * sc.C + l), f.ring[(long long)((sc.n - kd - l) % sc.R) * lvN + gi], acc);
+    return (T)acc;
+  };
+  T win[11];
+#pragma unroll
+  for (int m = 0; m < 11; ++m) win[m] = fetch(m - 5);
+  const T al = (T)f.alpha;
+  const T hm1 = fetch(-1), hpl = fetch(len);
+  const double* cp = f.thomas + (long long)len * 2 * f.Lmax;
+  const double* im = cp + f.Lmax;
+  double* out = f.Uout + base + (long long)off * st;
+  T dprev = (T)0;
+  for (int i = 0; i < len; ++i) {
+    T rhs = (T)f.h[0] * win[5];
+#pragma unroll
+    for (int m = 1; m <= 5; ++m) rhs = fma((T)f.h[m], win[5 + m] + win[5 - m], rhs);
+    if (i == 0) rhs -= al * hm1;
+    if (i == len - 1) rhs -= al * hpl;
+    const T dcur = (i == 0 ? rhs : rhs - al * dprev) * (T)im[i];
+    out[(long long)i * st] = (double)dcur;
+    dprev = dcur;
+#pragma unroll
+    for (int m = 0; m < 10; ++m) win[m] = win[m + 1];
+    win[10] = fetch(i + 6);
+  }
+  T xnext = dprev;
+  for (int i = len - 2; i >= 0; --i) {
+    const T x = (T)out[(long long)i * st] - (T)cp[i] * xnext;
+    out[(long long)i * st] = (double)x;
+    xnext = x;
+  }
+}
+
+int launch_filter(const Geometry& g, const StepSched& sc, const FilterLaunch& f, int axis, int precision,
+                  void* stream, long long* launches, const Timer* tm) {
+  const int n[3] = {g.nx, g.ny, g.nz};
+  const int f1 = (axis == 0) ? 1 : 0;
+  const int f2 = (axis == 2) ? 1 : 2;
+  const long long total = 5LL * f.P[axis] * n[f1] * n[f2];
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == 1) TIMED(tm, 3, (k_filter<float><<<nblk(total, 128), 128, 0, st>>>(g, sc, f, axis)));
+  else TIMED(tm, 3, (k_filter<double><<<nblk(total, 128), 128, 0, st>>>(g, sc, f, axis)));
+  if (launches) *launches += 1;
+  return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------- diagnostics
+
+// Velocity component c at global (x, y, z) with periodic wrap.
+__device__ __forceinline__ double vel_at(const double* U, const Geometry& g, int x, int y, int z, int c) {
+  const long long gi = (long long)wrapc(x, g.nx) + (long long)g.nx * ((long long)wrapc(y, g.ny) + (long long)g.ny * wrapc(z, g.nz));
+  return U[(1 + c) * g.N + gi] / U[gi];
+}
+
+__global__ void __launch_bounds__(256) k_diag(Geometry g, Physics ph, const double* __restrict__ U,
+                                              double* __restrict__ partial, double dV) {
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / ((long long)g.nx * g.ny));
+    double u[5];
+    for (int v = 0; v < 5; ++v) {
+      u[v] = U[v * g.N + i];
+      if (!isfinite(u[v])) acc[7] = 1.0;
+      acc[2 + v] += u[v] * dV;
+    }
+    const double rho = u[0];
+    const double vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
+    acc[0] += 0.5 * rho * (vx * vx + vy * vy + vz * vz);
+    // vorticity by the CD scheme
+    double dv[3][3];
+    for (int c = 0; c < 3; ++c)
+      for (int a = 0; a < 3; ++a) {
+        if (a >= g.ndim) { dv[c][a] = 0.0; continue; }
+        const int ex = a == 0, ey = a == 1, ez = a == 2;
+        double dd = ph.c1[a] * (vel_at(U, g, x + ex, y + ey, z + ez, c) - vel_at(U, g, x - ex, y - ey, z - ez, c));
+        if (g.r == 2)
+          dd += ph.c2[a] * (vel_at(U, g, x + 2 * ex, y + 2 * ey, z + 2 * ez, c) -
+                            vel_at(U, g, x - 2 * ex, y - 2 * ey, z - 2 * ez, c));
+        dv[c][a] = dd;
+      }
+    const double wx = dv[2][1] - dv[1][2], wy = dv[0][2] - dv[2][0], wz = dv[1][0] - dv[0][1];
+    acc[1] += 0.5 * rho * (wx * wx + wy * wy + wz * wz);
+  }
+  // block reduction: warp shuffles, then one warp over the warp sums
+  __shared__ double sh[8][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c = 0; c < 8; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double other = __shfl_down_sync(0xffffffffu, v, o);
+      v = (c == 7) ? fmax(v, other) : v + other;
+    }
+    if (lane == 0) sh[c][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    const int c = threadIdx.x;
+    double v = (c == 7) ? 0.0 : 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = (c == 7) ? fmax(v, sh[c][w]) : v + sh[c][w];
+    partial[(long long)blockIdx.x * 8 + c] = v;
+  }
+}
+
+// Deterministic second pass: one thread per quantity sums the block partials in block order.
+__global__ void k_diag_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out, long long N) {
+  const int c = threadIdx.x;
+  if (c >= 8) return;
+  double v = 0.0;
+  for (int b = 0; b < nblocks; ++b) v = (c == 7) ? fmax(v, partial[(long long)b * 8 + c]) : v + partial[(long long)b * 8 + c];
+  if (c < 2) v /= (double)N;
+  out[c] = v;
+}
+
+int launch_diagnostics(const Geometry& g, const Physics& ph, const double* U, double* partial, int nblocks,
+                       double* out, double dV, void* stream, long long* launches) {
+  cudaStream_t st = (cudaStream_t)stream;
+  k_diag<<<nblocks, 256, 0, st>>>(g, ph, U, partial, dV);
+  k_diag_final<<<1, 32, 0, st>>>(partial, nblocks, out, g.N);
+  if (launches) *launches += 2;
+  return (int)cudaGetLastError();
+}
+
+}  // namespace cfs

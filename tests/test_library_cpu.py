@@ -1,0 +1,107 @@
+"""Library checks that need no GPU: build, exported symbols, host-side coefficient generation
+and argument validation of the C ABI."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2506_03027_gb300 import build as B
+from paper_2506_03027_gb300 import cfs
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return cfs.load()
+
+
+def test_header_declares_the_boundary():
+    names = cfs.header_symbols()
+    for must in ("cfs_create", "cfs_add_block", "cfs_split_block", "cfs_finalize", "cfs_set_schedule",
+                 "cfs_set_state", "cfs_get_state", "cfs_step", "cfs_diagnostics", "cfs_get_ring",
+                 "cfs_set_ring", "cfs_last_error", "cfs_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in cfs.header_symbols():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_at_weights_match_oracle_tables(lib, order):
+    """The library solves the constraint systems of Eq. 6 and Eq. 13 itself; its collapsed halo
+    weights must equal the oracle's printed polynomials (Eq. 14-15, Table 5) run through the
+    buffer recursion of Eq. 8."""
+    kmax = 6
+    W = cfs.cfs_at_weights(order, kmax)
+    A, Bc = orc.lserk(order)
+    s = len(A)
+    for k in range(kmax + 1):
+        w = orc.extrap_weights(order, k).copy()
+        v = np.zeros_like(w)
+        np.testing.assert_allclose(W[k, 0], w, rtol=1e-13, atol=1e-13 * np.abs(w).max())
+        for m in range(1, s):
+            v = A[m - 1] * v + orc.buffer_dudt(order, m - 1, k)
+            w = w + Bc[m - 1] * v
+            np.testing.assert_allclose(W[k, m], w, rtol=1e-12, atol=1e-12 * np.abs(w).max())
+
+
+def test_zero_delay_stage0_weights_are_exact_identity(lib):
+    for order in (2, 4):
+        W = cfs.cfs_at_weights(order, 0)
+        assert W[0, 0, 0] == 1.0 and np.all(W[0, 0, 1:] == 0.0)
+
+
+def test_at_weights_reject_bad_arguments(lib):
+    out = np.zeros(1000)
+    p = out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert lib.cfs_at_weights(3, 2, p) == -1
+    assert lib.cfs_at_weights(4, -1, p) == -1
+    assert lib.cfs_at_weights(4, 99, p) == -1
+
+
+def test_create_validates_parameters(lib):
+    good = dict(order=4, viscous=1, visc_law=0, visc_exp=0.76, gamma=1.4, mach=0.1, re=1600.0, pr=0.71,
+                filter=1, alpha_f=0.499, precision=0)
+    ctx = cfs.cfs_create(cfs.CfsParams(**good))
+    cfs.cfs_destroy(ctx)
+    for bad in (dict(order=3), dict(precision=2), dict(alpha_f=0.5), dict(gamma=1.0), dict(re=0.0)):
+        with pytest.raises(cfs.CfsError) as e:
+            cfs.cfs_create(cfs.CfsParams(**{**good, **bad}))
+        assert e.value.status == cfs.CFS_EINVAL
+
+
+def test_call_order_and_block_validation(lib):
+    p = cfs.CfsParams(order=4, viscous=0, gamma=1.4, mach=0.5, re=1.0, pr=1.0, filter=0, alpha_f=0.0)
+    ctx = cfs.cfs_create(p)
+    try:
+        with pytest.raises(cfs.CfsError) as e:
+            cfs.cfs_step(ctx, 1)
+        assert e.value.status == cfs.CFS_ESTATE
+        with pytest.raises(cfs.CfsError) as e:
+            cfs.cfs_finalize(ctx, 0)
+        assert e.value.status == cfs.CFS_ESTATE  # no block yet
+        with pytest.raises(cfs.CfsError) as e:
+            cfs.cfs_add_block(ctx, 0, 4, 4, (1.0, 1.0, 1.0))
+        assert e.value.status == cfs.CFS_EINVAL
+        assert cfs.cfs_add_block(ctx, 16, 16, 1, (0.1, 0.1, 1.0)) == 0
+        with pytest.raises(cfs.CfsError):
+            cfs.cfs_add_block(ctx, 16, 16, 1, (0.1, 0.1, 1.0))  # one block in this version
+        with pytest.raises(cfs.CfsError):
+            cfs.cfs_split_block(ctx, 0, 17, 1, 1)
+        with pytest.raises(cfs.CfsError):
+            cfs.cfs_connect(ctx, 0, 0, 0, 2)
+        cfs.cfs_connect(ctx, 0, 0, 0, 1)
+        with pytest.raises(cfs.CfsError):
+            cfs.cfs_set_bc(ctx, 0, 0, 1)
+        with pytest.raises(cfs.CfsError) as e:
+            cfs.cfs_set_schedule(ctx, 1, 1, 4, None)
+        assert e.value.status == cfs.CFS_ESTATE
+        with pytest.raises(cfs.CfsError):
+            cfs.cfs_set_dt(ctx, -1.0)
+        assert "dt" in cfs.cfs_last_error(ctx)
+    finally:
+        cfs.cfs_destroy(ctx)

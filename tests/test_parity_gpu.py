@@ -1,0 +1,182 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, on seeded inputs shaped
+like the paper's cases: element by element over whole fields, relative L2 per conserved variable
+at most 1e-12 for the FP64 path."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2506_03027_gb300 import cfs
+from paper_2506_03027_gb300 import inputs as I
+
+from gpu_util import PARITY_TOL, ensure_built, gpu_run, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+
+
+def small_tgv(algo, n=34, p=4, cfl=0.25, **kw):
+    """Ragged decomposition: 34 points over 4 sub-domains gives widths 9, 9, 8, 8."""
+    c = I.tgv_case(n, p, algo, **kw)
+    return c.replace(dt=I.cfl_dt(c, I.tgv_state(c), cfl))
+
+
+def check(U, ref, tol=PARITY_TOL):
+    e = rel_l2(U, ref)
+    assert np.all(np.isfinite(U))
+    assert np.all(e <= tol), e
+    return e
+
+
+def test_vortex_c1_parity():
+    """2-D isentropic vortex, Euler, 64^2 on 2x2 sub-domains, SA, CFL 0.5, 200 steps."""
+    c = I.vortex_case(64, 2)
+    U0 = I.vortex_state(c)
+    Ug, dg = gpu_run(c, U0, 200)
+    Uo = orc.run(c, U0, 200)
+    check(Ug, Uo)
+    ex = I.vortex_state(c, t=200 * c.dt)
+    eg = np.sqrt(np.mean((Ug[0] - ex[0]) ** 2))
+    eo = np.sqrt(np.mean((Uo[0] - ex[0]) ** 2))
+    assert abs(eg - eo) <= 1e-10 * eo
+    np.testing.assert_allclose(dg[:7], orc.diagnostics(c, Uo)[:7], rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("algo,at,kmax", [("SA", True, 0), ("CAA", True, 0), ("SAA", True, 3),
+                                          ("SAA", False, 2), ("CAA", False, 0)])
+def test_tgv_ragged_parity(algo, at, kmax):
+    """3-D Navier-Stokes TGV with the tenth-order filter on ragged sub-domains, 24 steps (the
+    first 5 synchronous, then the schedule)."""
+    c = small_tgv(algo, at=at)
+    if algo == "SAA":
+        c = c.replace(kmax=kmax)
+    nsteps = 24
+    d = I.saa_delays(c, nsteps) if algo == "SAA" else None
+    U0 = I.tgv_state(c)
+    Ug, dg = gpu_run(c, U0, nsteps, delays=d)
+    Uo = orc.run(c, U0, nsteps, delays=d)
+    check(Ug, Uo)
+    np.testing.assert_allclose(dg[:7], orc.diagnostics(c, Uo)[:7], rtol=1e-11, atol=1e-13)
+
+
+def test_order2_euler_3d_parity():
+    """LSERK2-CD2-AT2 (Table 1 case 3) Euler in 3-D on an uneven 3x2x2 split, CAA L = 3."""
+    c = I.tgv_case(20, 2, "CAA", viscous=False, order=2, filter=False, caa_L=3)
+    c = c.replace(px=3, dt=I.cfl_dt(c, I.tgv_state(c), 0.2))
+    U0 = I.tgv_state(c)
+    Ug, _ = gpu_run(c, U0, 16)
+    Uo = orc.run(c, U0, 16)
+    check(Ug, Uo)
+
+
+def test_order2_viscous_saa_parity():
+    c = small_tgv("SAA", n=24, p=3, order=2, kmax=2, filter=True)
+    d = I.saa_delays(c, 14)
+    U0 = I.tgv_state(c)
+    Ug, _ = gpu_run(c, U0, 14, delays=d)
+    Uo = orc.run(c, U0, 14, delays=d)
+    check(Ug, Uo)
+
+
+def test_vortex_2d_async_filter_parity():
+    """2-D Euler with the filter under SAA-AT (2-D filter passes, no z halo)."""
+    c = I.vortex_case(48, 3, filter=True, algo="SAA", kmax=2)
+    c = c.replace(dt=c.dt * 0.4)
+    d = I.saa_delays(c, 30)
+    U0 = I.vortex_state(c)
+    Ug, _ = gpu_run(c, U0, 30, delays=d)
+    Uo = orc.run(c, U0, 30, delays=d)
+    check(Ug, Uo)
+
+
+def test_full_size_tgv_saa_parity():
+    """The benchmark configuration itself: TGV 128^3, 4x4x4 sub-domains of 32^3, SAA delays
+    0..3, filter on; 8 steps (5 synchronous + 3 asynchronous), whole fields compared."""
+    c = I.tgv_case(128, 4, "SAA")
+    nsteps = 8
+    d = I.saa_delays(c, nsteps)
+    U0 = I.tgv_state(c)
+    Ug, _ = gpu_run(c, U0, nsteps, delays=d)
+    Uo = orc.run(c, U0, nsteps, delays=d)
+    check(Ug, Uo)
+
+
+def test_checkpoint_resume_is_exact():
+    """Ring + step index restore: 7 steps, checkpoint, 5 more in a new context equals 12 steps."""
+    c = small_tgv("SAA", n=24, p=2, kmax=3)
+    d = I.saa_delays(c, 12)
+    U0 = I.tgv_state(c)
+    U12, _ = gpu_run(c, U0, 12, delays=d)
+    s = cfs.Solver(c)
+    s.set_schedule(delays=d)
+    s.set_state(U0)
+    s.step(7)
+    R = cfs.cfs_ring_depth(s.ctx)
+    ring = np.empty((R, 5, c.nz, c.ny, c.nx))
+    cfs.cfs_get_ring(s.ctx, ring.ctypes.data, cfs.HOST)
+    s.close()
+    s2 = cfs.Solver(c)
+    s2.set_schedule(delays=d)
+    cfs.cfs_set_step(s2.ctx, 7)
+    cfs.cfs_set_ring(s2.ctx, ring.ctypes.data, cfs.HOST)
+    s2.step(5)
+    U = s2.get_state()
+    s2.close()
+    np.testing.assert_array_equal(U, U12)
+
+
+def test_nonfinite_state_is_reported():
+    """A NaN planted in the host copy of the state makes the diagnostics return ENAN."""
+    c = small_tgv("SA", n=16, p=2, filter=False)
+    U0 = I.tgv_state(c)
+    U0[4, 3, 2, 1] = np.nan
+    s = cfs.Solver(c)
+    s.set_schedule()
+    s.set_state(U0)
+    with pytest.raises(cfs.CfsError) as e:
+        s.diagnostics()
+    assert e.value.status == cfs.CFS_ENAN
+    s.close()
+
+
+def test_schedule_validation():
+    c = small_tgv("SAA", n=16, p=2, kmax=2)
+    s = cfs.Solver(c)
+    bad = np.full((4, c.nsub, 6), 3, np.int8)  # above max_delay = 2
+    with pytest.raises(cfs.CfsError) as e:
+        s.set_schedule(delays=bad)
+    assert e.value.status == cfs.CFS_EINVAL
+    s.set_schedule(delays=np.zeros((2, c.nsub, 6), np.int8))
+    s.set_state(I.tgv_state(c))
+    s.step(2)
+    with pytest.raises(cfs.CfsError):
+        s.step(10)  # asynchronous steps beyond the table (steps 5.. need entries)
+    s.close()
+
+
+def test_launch_count():
+    c = small_tgv("SA", n=16, p=2)
+    s = cfs.Solver(c)
+    s.set_schedule()
+    s.set_state(I.tgv_state(c))
+    s.step(3)
+    assert s.launches() == 3 * (5 * 3 + 3)  # per step: 5 stages x 3 kernels + 3 filter passes
+    s.close()
+
+
+def test_fp32_intermediates_error_is_small():
+    """Precision form: FP32 derivative/flux/filter intermediates, FP64 state and RK/AT
+    accumulation.  Its error against the FP64 oracle is reported and bounded."""
+    c = small_tgv("CAA")
+    U0 = I.tgv_state(c)
+    Ug, _ = gpu_run(c, U0, 24, precision=1)
+    Uo = orc.run(c, U0, 24)
+    e = rel_l2(Ug, Uo)
+    assert np.all(np.isfinite(Ug))
+    assert np.all(e < 1e-6), e
