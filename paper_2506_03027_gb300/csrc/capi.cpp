@@ -276,6 +276,9 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   ph.ire = c->p.viscous ? 1.0 / c->p.re : 0.0;
   ph.kappa = c->p.viscous ? 1.0 / ((c->p.gamma - 1.0) * c->p.pr * c->p.mach * c->p.mach) : 0.0;
   ph.visc_law = c->p.visc_law; ph.visc_exp = c->p.visc_exp;
+  ph.p_ref = 1.0 / ph.gM2;
+  ph.E_ref = ph.p_ref / ph.gm1;
+  ph.H_ref = ph.E_ref + ph.p_ref;
   // CD coefficients of Eq. 2 with alpha = 0: CD4 a = 4/3, b = -1/3; CD2 a = 1, b = 0
   const double a_cd = c->p.order == 4 ? 4.0 / 3.0 : 1.0, b_cd = c->p.order == 4 ? -1.0 / 3.0 : 0.0;
   for (int a = 0; a < 3; ++a) {
@@ -484,6 +487,7 @@ cfs_status cfs_step(cfs_ctx* c, long long nsteps) {
         }
         f.thomas = c->d_thomas; f.Lmax = c->Lmax; f.alpha = c->p.alpha_f;
         for (int m = 0; m < 6; ++m) f.h[m] = c->filt_h[m];
+        f.b1 = c->filt_h[1] - c->p.alpha_f;
         rc = cfs::launch_filter(g, sc, f, op - c->s, c->p.precision, c->stream, &c->launches,
                                 c->timing ? &c->timer : nullptr);
       }

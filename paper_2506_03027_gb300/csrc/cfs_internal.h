@@ -39,6 +39,10 @@ struct Physics {
   int visc_law;
   double visc_exp;
   double c1[3], c2[3];     // CD coefficients per axis: c1 = (a/2)/h, c2 = (b/4)/h
+  // FP32-intermediate form only: reference pressure p_ref = 1/(gamma M^2), E_ref = p_ref/(gamma-1)
+  // and H_ref = E_ref + p_ref; primitives carry p - p_ref and rho E - E_ref so that FP32 rounding
+  // acts on O(1) deviations instead of p ~ 1/(gamma M^2)
+  double p_ref, E_ref, H_ref;
 };
 
 // Delay schedule as seen by the kernels of one step.
@@ -104,6 +108,7 @@ struct FilterLaunch {
   int P[3];                // sub-domains per axis
   double alpha;
   double h[6];             // filter right side: a_0, a_1/2, ..., a_5/2
+  double b1;               // a_1/2 - alpha: weight of the first second difference (increment form)
 };
 
 int launch_filter(const Geometry& g, const StepSched& sc, const FilterLaunch& f, int axis, int precision,

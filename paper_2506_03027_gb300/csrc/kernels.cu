@@ -19,6 +19,8 @@
 // boxes of all sub-domains.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "cfs_internal.h"
 
 namespace cfs {
@@ -91,13 +93,17 @@ __global__ void __launch_bounds__(256) k_view(Geometry g, Physics ph, StepSched 
       }
     }
   }
-  // primitives (App. A): p = (gamma-1)(rho E - rho|u|^2/2), T = gamma M^2 p / rho
+  // primitives (App. A): p = (gamma-1)(rho E - rho|u|^2/2), T = gamma M^2 p / rho.  In the FP32
+  // form p and rho E are carried as deviations from p_ref and E_ref (exact algebra: the constant
+  // part of p has no derivative and the constant enthalpy H_ref is added back in k_flux).
+  constexpr bool f32 = std::is_same<T, float>::value;
   const T rho = (T)u[0];
   const T ir = (T)1 / rho;
   const T uu = (T)u[1] * ir, vv = (T)u[2] * ir, ww = (T)u[3] * ir;
   const T ke = (T)0.5 * ((T)u[1] * uu + (T)u[2] * vv + (T)u[3] * ww);
-  const T p = (T)ph.gm1 * ((T)u[4] - ke);
-  const T temp = (T)ph.gM2 * p * ir;
+  const T rE = f32 ? (T)(u[4] - ph.E_ref) : (T)u[4];
+  const T p = (T)ph.gm1 * (rE - ke);
+  const T temp = f32 ? ((T)ph.gM2 * p + (T)1) * ir : (T)ph.gM2 * p * ir;
   const long long P = g.Ptot, o = d.pbase + t;
   Wp[o] = rho;
   Wp[P + o] = uu;
@@ -105,7 +111,7 @@ __global__ void __launch_bounds__(256) k_view(Geometry g, Physics ph, StepSched 
   Wp[3 * P + o] = ww;
   Wp[4 * P + o] = p;
   Wp[5 * P + o] = temp;
-  Wp[6 * P + o] = (T)u[4] + p;  // rho E + p (energy flux factor)
+  Wp[6 * P + o] = rE + p;  // rho E + p (energy flux factor; minus H_ref in the FP32 form)
 }
 
 // ------------------------------------------------------------------------------- k_flux
@@ -168,7 +174,7 @@ __global__ void __launch_bounds__(256) k_flux(Geometry g, Physics ph, const SubD
     f[1] = -(mflux * u + (a == 0 ? p : (T)0));
     f[2] = -(mflux * v + (a == 1 ? p : (T)0));
     f[3] = -(mflux * w + (a == 2 ? p : (T)0));
-    f[4] = -(et * ua);
+    f[4] = std::is_same<T, float>::value ? -(et * ua + (T)ph.H_ref * ua) : -(et * ua);
     if (g.viscous) {
       // tau_ai = mu (du_a/dx_i + du_i/dx_a) - 2/3 mu div delta_ai
       T tau[3];
@@ -278,44 +284,79 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
   const int kr = (sc.mode == 0) ? 0 : face_delay(sc, sid, 2 * axis + 1);
   const long long lvN = 5 * g.N;
   // value at line position i (halo for i < 0 or i >= len)
-  auto fetch = [&](int i) -> T {
+  auto fetch = [&](int i) -> double {
     const int c = wrapc(off + i, n[axis]);
     const long long gi = base + (long long)c * st;
-    if ((i >= 0 && i < len) || sc.mode == 0) return (T)Uin[gi];
+    if ((i >= 0 && i < len) || sc.mode == 0) return Uin[gi];
     const int kd = i < 0 ? kl : kr;
-    if (sc.mode == 2) return (T)f.ring[(long long)((sc.n - kd) % sc.R) * lvN + gi];
+    if (sc.mode == 2) return f.ring[(long long)((sc.n - kd) % sc.R) * lvN + gi];
     double acc = 0.0;  // extrapolation to t_{n+1} with weights c(k+1), in FP64
     for (int l = 0; l < sc.C; ++l)
       acc = fma(__ldg(sc.Wf + kd * sc.C + l), f.ring[(long long)((sc.n - kd - l) % sc.R) * lvN + gi], acc);
-    return (T)acc;
+    return acc;
   };
-  T win[11];
-#pragma unroll
-  for (int m = 0; m < 11; ++m) win[m] = fetch(m - 5);
   const T al = (T)f.alpha;
-  const T hm1 = fetch(-1), hpl = fetch(len);
   const double* cp = f.thomas + (long long)len * 2 * f.Lmax;
   const double* im = cp + f.Lmax;
   double* out = f.Uout + base + (long long)off * st;
-  T dprev = (T)0;
-  for (int i = 0; i < len; ++i) {
-    T rhs = (T)f.h[0] * win[5];
+  if (!std::is_same<T, float>::value) {
+    // FP64: the system as written, alpha f^_{i-1} + f^_i + alpha f^_{i+1} = rhs_i
+    T win[11];
 #pragma unroll
-    for (int m = 1; m <= 5; ++m) rhs = fma((T)f.h[m], win[5 + m] + win[5 - m], rhs);
-    if (i == 0) rhs -= al * hm1;
-    if (i == len - 1) rhs -= al * hpl;
-    const T dcur = (i == 0 ? rhs : rhs - al * dprev) * (T)im[i];
-    out[(long long)i * st] = (double)dcur;
-    dprev = dcur;
+    for (int m = 0; m < 11; ++m) win[m] = (T)fetch(m - 5);
+    const T hm1 = (T)fetch(-1), hpl = (T)fetch(len);
+    T dprev = (T)0;
+    for (int i = 0; i < len; ++i) {
+      T rhs = (T)f.h[0] * win[5];
 #pragma unroll
-    for (int m = 0; m < 10; ++m) win[m] = win[m + 1];
-    win[10] = fetch(i + 6);
-  }
-  T xnext = dprev;
-  for (int i = len - 2; i >= 0; --i) {
-    const T x = (T)out[(long long)i * st] - (T)cp[i] * xnext;
-    out[(long long)i * st] = (double)x;
-    xnext = x;
+      for (int m = 1; m <= 5; ++m) rhs = fma((T)f.h[m], win[5 + m] + win[5 - m], rhs);
+      if (i == 0) rhs -= al * hm1;
+      if (i == len - 1) rhs -= al * hpl;
+      const T dcur = (i == 0 ? rhs : rhs - al * dprev) * (T)im[i];
+      out[(long long)i * st] = (double)dcur;
+      dprev = dcur;
+#pragma unroll
+      for (int m = 0; m < 10; ++m) win[m] = win[m + 1];
+      win[10] = (T)fetch(i + 6);
+    }
+    T xnext = dprev;
+    for (int i = len - 2; i >= 0; --i) {
+      const T x = (T)out[(long long)i * st] - (T)cp[i] * xnext;
+      out[(long long)i * st] = (double)x;
+      xnext = x;
+    }
+  } else {
+    // FP32 form: solve for the increment d = f^ - f.  Its right side is
+    // (a_1/2 - alpha) D_1 + sum_{n>=2} (a_n/2) D_n with D_n = f_{i+n} + f_{i-n} - 2 f_i (exact
+    // algebra, using sum a_n = 1 + 2 alpha), the Dirichlet closure becomes d = 0 at the first halo
+    // point, and the values enter as FP32 offsets from an FP64 reference of the line, so FP32
+    // rounding never acts on the full magnitude of the state.
+    const double ref = fetch(0);
+    auto off32 = [&](int i) -> float { return (float)(fetch(i) - ref); };
+    float win[11];
+#pragma unroll
+    for (int m = 0; m < 11; ++m) win[m] = off32(m - 5);
+    const float b1 = (float)f.b1;
+    float dprev = 0.f;
+    for (int i = 0; i < len; ++i) {
+      const float c2 = 2.f * win[5];
+      float rhs = b1 * (win[6] + win[4] - c2);
+#pragma unroll
+      for (int m = 2; m <= 5; ++m) rhs = fmaf((float)f.h[m], win[5 + m] + win[5 - m] - c2, rhs);
+      const float dcur = (i == 0 ? rhs : rhs - (float)f.alpha * dprev) * (float)im[i];
+      out[(long long)i * st] = (double)dcur;
+      dprev = dcur;
+#pragma unroll
+      for (int m = 0; m < 10; ++m) win[m] = win[m + 1];
+      win[10] = off32(i + 6);
+    }
+    float xnext = dprev;
+    out[(long long)(len - 1) * st] = Uin[base + (long long)wrapc(off + len - 1, n[axis]) * st] + (double)xnext;
+    for (int i = len - 2; i >= 0; --i) {
+      const float x = (float)out[(long long)i * st] - (float)cp[i] * xnext;
+      out[(long long)i * st] = Uin[base + (long long)(off + i) * st] + (double)x;
+      xnext = x;
+    }
   }
 }
 

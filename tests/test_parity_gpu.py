@@ -48,12 +48,15 @@ def test_vortex_c1_parity():
     np.testing.assert_allclose(dg[:7], orc.diagnostics(c, Uo)[:7], rtol=1e-12, atol=1e-14)
 
 
-@pytest.mark.parametrize("algo,at,kmax", [("SA", True, 0), ("CAA", True, 0), ("SAA", True, 3),
-                                          ("SAA", False, 2), ("CAA", False, 0)])
-def test_tgv_ragged_parity(algo, at, kmax):
+@pytest.mark.parametrize("algo,at,kmax,cfl", [("SA", True, 0, 0.25), ("CAA", True, 0, 0.25), ("SAA", True, 3, 0.1),
+                                              ("SAA", False, 2, 0.25), ("CAA", False, 0, 0.25)])
+def test_tgv_ragged_parity(algo, at, kmax, cfl):
     """3-D Navier-Stokes TGV with the tenth-order filter on ragged sub-domains, 24 steps (the
-    first 5 synchronous, then the schedule)."""
-    c = small_tgv(algo, at=at)
+    first 5 synchronous, then the schedule).  SAA-AT with delays 0..3 on 8-9 point sub-domains
+    runs at CFL 0.1: at 0.25 the scheme amplifies a 1e-15 perturbation of the initial state to
+    7e-12 within 24 steps (measured with the oracle alone), so no two FP64 evaluation orders can
+    agree to 1e-12 there."""
+    c = small_tgv(algo, at=at, cfl=cfl)
     if algo == "SAA":
         c = c.replace(kmax=kmax)
     nsteps = 24
@@ -170,13 +173,15 @@ def test_launch_count():
     s.close()
 
 
-def test_fp32_intermediates_error_is_small():
+@pytest.mark.parametrize("algo", ["SA", "CAA"])
+def test_fp32_intermediates_error_is_small(algo):
     """Precision form: FP32 derivative/flux/filter intermediates, FP64 state and RK/AT
     accumulation.  Its error against the FP64 oracle is reported and bounded."""
-    c = small_tgv("CAA")
+    c = small_tgv(algo)
     U0 = I.tgv_state(c)
     Ug, _ = gpu_run(c, U0, 24, precision=1)
     Uo = orc.run(c, U0, 24)
     e = rel_l2(Ug, Uo)
+    print(f"FP32-intermediate form, {algo}, 24 steps: relative L2 per variable {e}")
     assert np.all(np.isfinite(Ug))
     assert np.all(e < 1e-6), e
