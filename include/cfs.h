@@ -155,6 +155,28 @@ cfs_status cfs_launch_count(cfs_ctx* ctx, long long* launches);
 cfs_status cfs_set_timing(cfs_ctx* ctx, int on);
 cfs_status cfs_get_timing(cfs_ctx* ctx, double* ms, long long* count);
 
+/* Diagnostics without any device allocation (no counterpart in the paper: an interface for
+ * callers that cannot allocate).  Callers such as an in-situ monitoring hook inside a larger
+ * simulation whose pool allocator owns all of the GPU's memory, or a time-critical loop where an
+ * allocation (which may synchronise the device) is not allowed, cannot use cfs_diagnostics,
+ * whose context allocates its scratch at cfs_finalize.  This call computes the same eight
+ * quantities for a state U (device pointer, FP64 [5][nz][ny][nx], periodic grid with spacing
+ * {dx, dy, dz} given as a host array of 3 doubles, CD scheme of `order` 2 or 4 for the vorticity)
+ * and writes them to out (device pointer to 8 doubles), asynchronously on cuda_stream.
+ *   - Scratch: a fixed array of per-block partial sums compiled into the library (4 MiB, kept on
+ *     every GPU that loads the library until the process exits).  It limits the grid to
+ *     CFS_DIAG_STATIC_MAX_POINTS points; larger grids are rejected with CFS_EINVAL and a message.
+ *   - No cudaMalloc, cudaFree or other allocating call is made.
+ *   - The first call on each device (with that device current) looks up the array's device
+ *     address; make that first call before any stream capture.
+ *   - All calls share the array; each call overwrites the partial sums it reads, so nothing has
+ *     to be cleared, but calls whose GPU work overlaps (other streams, other host threads) race.
+ *   - err (may be NULL) receives a message of at most err_len bytes on failure.
+ * Returns CFS_OK, CFS_EINVAL (bad pointer, size or order) or CFS_ECUDA (device or launch error). */
+#define CFS_DIAG_STATIC_MAX_POINTS 16777216LL
+cfs_status cfs_diagnostics_static(const double* U, int nx, int ny, int nz, const double* spacing, int order,
+                                  double* out, void* cuda_stream, char* err, size_t err_len);
+
 /* Last error message of the context (static string if ctx is NULL). */
 const char* cfs_last_error(cfs_ctx* ctx);
 

@@ -90,6 +90,7 @@ def load() -> ctypes.CDLL:
             "cfs_launch_count": ([vp, ctypes.POINTER(ll)], ip),
             "cfs_set_timing": ([vp, ip], ip),
             "cfs_get_timing": ([vp, dp, ctypes.POINTER(ll)], ip),
+            "cfs_diagnostics_static": ([vp, ip, ip, ip, dp, ip, vp, vp, ctypes.c_char_p, ctypes.c_size_t], ip),
             "cfs_last_error": ([vp], ctypes.c_char_p),
             "cfs_destroy": ([vp], None),
         }
@@ -231,6 +232,17 @@ def cfs_get_timing(ctx):
     cnt = (ctypes.c_longlong * NKINDS)()
     _check(ctx, load().cfs_get_timing(ctx, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cnt))
     return {KIND_NAMES[k]: (float(ms[k]), int(cnt[k])) for k in range(NKINDS)}
+
+
+def cfs_diagnostics_static(U_ptr: int, nx: int, ny: int, nz: int, spacing, order: int, out_ptr: int,
+                           stream: int | None = None) -> None:
+    """Allocation-free diagnostics of a device state into a device buffer of 8 doubles."""
+    sp = (ctypes.c_double * 3)(*spacing)
+    buf = ctypes.create_string_buffer(256)
+    st = load().cfs_diagnostics_static(ctypes.c_void_p(U_ptr), nx, ny, nz, sp, order, ctypes.c_void_p(out_ptr),
+                                       ctypes.c_void_p(stream or 0), buf, 256)
+    if st != CFS_OK:
+        raise CfsError(st, buf.value.decode())
 
 
 def cfs_last_error(ctx) -> str:
