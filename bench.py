@@ -267,11 +267,14 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
+        cfs.cfs_set_timing(s32.ctx, True)
         f0.record(stream)
         s32.step(K)
         f1.record(stream)
         torch.cuda.synchronize()
         ms32 = f0.elapsed_time(f1)
+        kt32 = cfs.cfs_get_timing(s32.ctx)
+        cfs.cfs_set_timing(s32.ctx, False)
         s32.step(n_done - s32.n)
         U32 = s32.get_state()
         s32.close()
@@ -280,7 +283,8 @@ def run_ours(args, rank, world, local_rank):
                for v in range(5)]
         forms = {"fp32_intermediates": {"value": n_units / (ms32 * 1e-3) / 1e6, "unit": UNIT,
                                         "speedup_vs_fp64": ms / ms32,
-                                        "rel_l2_vs_fp64_path": err, "after_steps": n_done}}
+                                        "rel_l2_vs_fp64_path": err, "after_steps": n_done,
+                                        "per_kernel_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in kt32.items() if v[1]}}}
 
     # ---------------- roofline of the dominant kernel
     peaks = measured_peaks()

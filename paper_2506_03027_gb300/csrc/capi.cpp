@@ -62,6 +62,19 @@ struct cfs_ctx {
   double* d_out = nullptr;
   int diag_blocks = 0;
 
+  // compact list of the halo points of every sub-domain: (sub-domain, padded index)
+  int* d_halo = nullptr;
+  long long nhalo = 0;
+
+  // fused FP32-intermediate stage (3-D Navier-Stokes, CD4)
+  bool fused = false;
+  int fused_zc = 16;
+  int fused_fy = 8;
+  int fused_grid = 0;
+  int nwork = 0;
+  int* d_work = nullptr;
+  float* Wh = nullptr;
+
   Geometry geo{};
   Physics phys{};
 
@@ -290,8 +303,34 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   c->buf[0] = (double*)dev_alloc(c, sizeof(double) * 5 * N);
   c->buf[1] = (double*)dev_alloc(c, sizeof(double) * 5 * N);
   c->Q = (double*)dev_alloc(c, sizeof(double) * 5 * N);
-  c->Wp = dev_alloc(c, tsz * 7 * (size_t)pbase);
-  c->Phi = dev_alloc(c, tsz * 15 * (size_t)pbase);
+  c->fused = c->p.precision == 1 && c->ndim == 3 && c->p.viscous && c->p.order == 4;
+  if (c->fused) {
+    // tiles of 32 x fy columns per sub-domain, marching z; one CTA per tile (persistent grid)
+    std::vector<int> work;
+    for (int sid = 0; sid < nsub; ++sid) {
+      const SubDev& d = c->subs[sid];
+      for (int z0 = 0; z0 < d.sz; z0 += c->fused_zc)
+        for (int y0 = 0; y0 < d.sy; y0 += c->fused_fy)
+          for (int x0 = 0; x0 < d.sx; x0 += 32) {
+            const int z1 = std::min(d.sz, z0 + c->fused_zc);
+            work.push_back(sid); work.push_back(x0); work.push_back(y0); work.push_back(z0 | (z1 << 16));
+          }
+    }
+    c->nwork = (int)(work.size() / 4);
+    c->d_work = (int*)dev_alloc(c, sizeof(int) * work.size());
+    c->Wh = (float*)dev_alloc(c, sizeof(float) * 7 * c->s * (size_t)pbase);
+    if (!c->d_work || !c->Wh) return fail(c, CFS_ENOMEM, "device allocation failed");
+    CUDA_TRY(c, cudaMemcpy(c->d_work, work.data(), sizeof(int) * work.size(), cudaMemcpyHostToDevice), "upload work list");
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int smem = cfs::fused_smem_bytes(c->fused_fy);
+    const int per_sm = std::max(1, (227 * 1024) / std::max(1, smem + 1024));
+    c->fused_grid = std::max(1, std::min(c->nwork, per_sm * std::max(1, sms)));
+  } else {
+    c->Wp = dev_alloc(c, tsz * 7 * (size_t)pbase);
+    c->Phi = dev_alloc(c, tsz * 15 * (size_t)pbase);
+  }
   c->d_subs = (SubDev*)dev_alloc(c, sizeof(SubDev) * nsub);
   const int nW = (max_delay + 1) * c->s * c->C, nWf = (max_delay + 1) * c->C;
   c->d_W = (double*)dev_alloc(c, sizeof(double) * nW);
@@ -310,11 +349,38 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   c->d_thomas = (double*)dev_alloc(c, sizeof(double) * (size_t)(c->Lmax + 1) * 2 * c->Lmax);
   for (void* q : c->owned)
     if (!q) return fail(c, CFS_ENOMEM, "device allocation failed");
-  if (!c->ring || !c->buf[0] || !c->buf[1] || !c->Q || !c->Wp || !c->Phi || !c->d_subs || !c->d_W || !c->d_Wf ||
+  if (!c->ring || !c->buf[0] || !c->buf[1] || !c->Q || (!c->fused && (!c->Wp || !c->Phi)) || !c->d_subs || !c->d_W || !c->d_Wf ||
       !c->d_partial || !c->d_out || !c->d_thomas)
     return fail(c, CFS_ENOMEM, "device allocation failed");
   for (int a = 0; a < 3; ++a)
     if (!c->d_owner[a] || !c->d_axis_off[a] || !c->d_axis_len[a]) return fail(c, CFS_ENOMEM, "device allocation failed");
+  // halo list: faces to depth G, viscous edges to r x r (the points each sub-domain reads from
+  // its neighbours)
+  {
+    std::vector<int> hl;
+    for (int sid = 0; sid < nsub; ++sid) {
+      const SubDev& d = c->subs[sid];
+      for (int k = 0; k < d.ez; ++k)
+        for (int j = 0; j < d.ey; ++j)
+          for (int i = 0; i < d.ex; ++i) {
+            const int ci = i - c->G, cj = j - c->G, ck = k - c->Gz;
+            const int dx = ci < 0 ? -ci : (ci >= d.sx ? ci - d.sx + 1 : 0);
+            const int dy = cj < 0 ? -cj : (cj >= d.sy ? cj - d.sy + 1 : 0);
+            const int dz = ck < 0 ? -ck : (ck >= d.sz ? ck - d.sz + 1 : 0);
+            const int nout = (dx > 0) + (dy > 0) + (dz > 0);
+            const bool need = nout == 1 || (nout == 2 && c->p.viscous && dx <= c->r && dy <= c->r && dz <= c->r);
+            if (!need) continue;
+            hl.push_back(sid);
+            hl.push_back(i + d.ex * (j + d.ey * k));
+          }
+    }
+    c->nhalo = (long long)(hl.size() / 2);
+    if (c->nhalo > 0) {
+      c->d_halo = (int*)dev_alloc(c, sizeof(int) * hl.size());
+      if (!c->d_halo) return fail(c, CFS_ENOMEM, "device allocation failed");
+      CUDA_TRY(c, cudaMemcpy(c->d_halo, hl.data(), sizeof(int) * hl.size(), cudaMemcpyHostToDevice), "upload halo list");
+    }
+  }
   // host tables
   std::vector<double> W(nW), Wf(nWf);
   if (cfs::at_weight_table(c->p.order, max_delay, W.data()) != nW ||
@@ -466,16 +532,28 @@ cfs_status cfs_step(cfs_ctx* c, long long nsteps) {
     }
     const double* src = level_ptr(c, n);
     int pp = 0;
+    if (c->fused && sc.mode != 0) {
+      const int rc = cfs::launch_halo_prims(g, c->phys, sc, c->ring, c->d_subs, c->d_halo, c->nhalo, c->Wh, c->s,
+                                            c->stream, &c->launches, c->timing ? &c->timer : nullptr);
+      if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
+    }
     for (int op = 0; op < nops; ++op) {
       double* dst = (op == nops - 1) ? level_ptr(c, n + 1) : c->buf[pp];
       int rc;
-      if (op < c->s) {
+      if (op < c->s && c->fused) {
+        cfs::FusedLaunch a{};
+        a.Uin = src; a.Uout = dst; a.Q = c->Q; a.subs = c->d_subs; a.work = c->d_work; a.nwork = c->nwork;
+        a.grid = c->fused_grid; a.fy = c->fused_fy; a.Wh = c->Wh; a.stage = op;
+        a.A = c->A[op]; a.B = c->B[op]; a.dt = c->dt; a.first = op == 0; a.last = op == c->s - 1;
+        rc = cfs::launch_stage_fused(g, c->phys, sc, a, c->stream, &c->launches, c->timing ? &c->timer : nullptr);
+      } else if (op < c->s) {
         cfs::StageLaunch a{};
         a.Uin = src; a.Uout = dst; a.Q = c->Q; a.ring = c->ring; a.subs = c->d_subs;
         a.Wp = c->Wp; a.Phi = c->Phi; a.stage = op; a.s = c->s;
         a.A = c->A[op]; a.B = c->B[op]; a.dt = c->dt;
         a.first = op == 0; a.last = op == c->s - 1;
         a.max_pad = c->max_pad; a.max_own = c->max_own; a.max_flux = c->max_flux;
+        a.halo = c->d_halo; a.nhalo = c->nhalo;
         rc = cfs::launch_stage(g, c->phys, sc, a, c->p.precision, c->stream, &c->launches,
                                c->timing ? &c->timer : nullptr);
       } else {

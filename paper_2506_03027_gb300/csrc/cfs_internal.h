@@ -82,6 +82,8 @@ struct StageLaunch {
   double A, B, dt;
   int first, last;      // first stage skips reading Q, last stage skips writing Q
   int max_pad;          // largest padded box (points)
+  const int* halo;      // device: (sub-domain, padded index) pairs of every halo point
+  long long nhalo;
   int max_own;          // largest owned box (points)
   int max_flux;         // largest flux region box (points)
 };
@@ -113,6 +115,28 @@ struct FilterLaunch {
 
 int launch_filter(const Geometry& g, const StepSched& sc, const FilterLaunch& f, int axis, int precision,
                   void* stream, long long* launches, const Timer* tm);
+
+// Fused stage for the FP32-intermediate form (fused.cu): 3-D Navier-Stokes, CD4/AT4.
+struct FusedLaunch {
+  const double* Uin;
+  double* Uout;
+  double* Q;
+  const SubDev* subs;
+  const int* work;      // device: 4 ints per tile (sub-domain, x0, y0, z0 | z1 << 16)
+  int nwork;
+  int grid;             // persistent grid size
+  int fy;               // tile height: 4, 8 or 16 (tile width 32)
+  const float* Wh;      // per-step AT/AS halo primitives [s][7][Ptot]
+  int stage;
+  double A, B, dt;
+  int first, last;
+};
+int fused_smem_bytes(int fy);
+int launch_halo_prims(const Geometry& g, const Physics& ph, const StepSched& sc, const double* ring, const SubDev* subs,
+                      const int* halo, long long nhalo, float* Wh, int s, void* stream, long long* launches,
+                      const Timer* tm);
+int launch_stage_fused(const Geometry& g, const Physics& ph, const StepSched& sc, const FusedLaunch& a, void* stream,
+                       long long* launches, const Timer* tm);
 
 int launch_diagnostics(const Geometry& g, const Physics& ph, const double* U, double* partial, int nblocks,
                        double* out, double dV, void* stream, long long* launches);

@@ -22,60 +22,82 @@
 #include <type_traits>
 
 #include "cfs_internal.h"
+#include "device_common.cuh"
 
 namespace cfs {
 
-__device__ __forceinline__ int wrapc(int i, int n) {
-  int r = i % n;
-  return r < 0 ? r + n : r;
-}
-
-// Delay of face f (0..5) of sub-domain sid at this step, clamped so every level exists.
-__device__ __forceinline__ int face_delay(const StepSched& sc, int sid, int f) {
-  int k = 0;
-  if (sc.algo == 1) k = (int)((sc.n - sc.C) % sc.L);
-  else if (sc.algo == 2) k = sc.table[sid * 6 + f];
-  if (k > sc.cap) k = (int)sc.cap;
-  if (k < 0) k = 0;
-  return k;
-}
-
 // ------------------------------------------------------------------------------- k_view
 
+// Store the primitives of conserved state u at padded index q of sub-domain d (App. A:
+// p = (gamma-1)(rho E - rho|u|^2/2), T = gamma M^2 p / rho).  In the FP32 form p and rho E are
+// carried as deviations from p_ref and E_ref (exact algebra: the constant part of p has no
+// derivative and the constant enthalpy H_ref is added back in k_flux).
 template <typename T>
-__global__ void __launch_bounds__(256) k_view(Geometry g, Physics ph, StepSched sc, const double* __restrict__ Uin,
-                                              const double* __restrict__ ring, const SubDev* __restrict__ subs,
-                                              T* __restrict__ Wp, int stage, int s) {
+__device__ __forceinline__ void store_prims(const Geometry& g, const Physics& ph, const double* u, long long o,
+                                            T* __restrict__ Wp) {
+  constexpr bool f32 = std::is_same<T, float>::value;
+  const T rho = (T)u[0];
+  const T ir = recip(rho);
+  const T uu = (T)u[1] * ir, vv = (T)u[2] * ir, ww = (T)u[3] * ir;
+  const T ke = (T)0.5 * ((T)u[1] * uu + (T)u[2] * vv + (T)u[3] * ww);
+  const T rE = f32 ? (T)(u[4] - ph.E_ref) : (T)u[4];
+  const T p = (T)ph.gm1 * (rE - ke);
+  const T temp = f32 ? ((T)ph.gM2 * p + (T)1) * ir : (T)ph.gM2 * p * ir;
+  const long long P = g.Ptot;
+  Wp[o] = rho;
+  Wp[P + o] = uu;
+  Wp[2 * P + o] = vv;
+  Wp[3 * P + o] = ww;
+  Wp[4 * P + o] = p;
+  Wp[5 * P + o] = temp;
+  Wp[6 * P + o] = rE + p;  // rho E + p (energy flux factor; minus H_ref in the FP32 form)
+}
+
+// k_view, owned points: the stage input of the sub-domain's own points as primitives.
+template <typename T>
+__global__ void __launch_bounds__(256) k_view_own(Geometry g, Physics ph, const double* __restrict__ Uin,
+                                                  const SubDev* __restrict__ subs, T* __restrict__ Wp) {
   const int sid = blockIdx.y;
   const SubDev d = subs[sid];
-  const long long npad = (long long)d.ex * d.ey * d.ez;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= npad) return;
-  const int i = (int)(t % d.ex);
-  const int j = (int)((t / d.ex) % d.ey);
-  const int k = (int)(t / ((long long)d.ex * d.ey));
+  if (t >= (long long)d.sx * d.sy * d.sz) return;
+  const int ci = (int)(t % d.sx), cj = (int)((t / d.sx) % d.sy), ck = (int)(t / ((long long)d.sx * d.sy));
+  const long long gi = (long long)(d.ox + ci) + (long long)g.nx * ((long long)(d.oy + cj) + (long long)g.ny * (d.oz + ck));
+  const long long q = (long long)(ci + g.G) + (long long)d.ex * ((long long)(cj + g.G) + (long long)d.ey * (ck + g.Gz));
+  double u[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) u[v] = Uin[v * g.N + gi];
+  store_prims<T>(g, ph, u, d.pbase + q, Wp);
+}
+
+// k_view, halo points: one thread per entry of the compact list of (sub-domain, padded index) of
+// the points a sub-domain reads from neighbours -- faces to depth G, viscous edges to r x r -- so
+// that no warp mixes owned points with the AT weighting.  SA: the neighbour's live value; AT:
+// sum_l W^(m)_l(k) U^{n-k-l} in FP64 (Eq. 14-15, buffer updates of Eq. 8 collapsed); AS: U^{n-k}.
+template <typename T>
+__global__ void __launch_bounds__(256) k_view_halo(Geometry g, Physics ph, StepSched sc, const double* __restrict__ Uin,
+                                                   const double* __restrict__ ring, const SubDev* __restrict__ subs,
+                                                   const int2* __restrict__ halo, long long nhalo, T* __restrict__ Wp,
+                                                   int stage, int s) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nhalo) return;
+  const int2 e = halo[t];
+  const int sid = e.x;
+  const long long q = e.y;
+  const SubDev d = subs[sid];
+  const int i = (int)(q % d.ex), j = (int)((q / d.ex) % d.ey), k = (int)(q / ((long long)d.ex * d.ey));
   const int ci = i - g.G, cj = j - g.G, ck = k - g.Gz;
-  const int dx = ci < 0 ? -ci : (ci >= d.sx ? ci - d.sx + 1 : 0);
-  const int dy = cj < 0 ? -cj : (cj >= d.sy ? cj - d.sy + 1 : 0);
-  const int dz = ck < 0 ? -ck : (ck >= d.sz ? ck - d.sz + 1 : 0);
-  const int nout = (dx > 0) + (dy > 0) + (dz > 0);
-  if (nout >= 3) return;
-  if (nout == 2) {
-    // viscous cross derivatives need r x r edge halos only
-    if (!g.viscous) return;
-    if (dx > g.r || dy > g.r || dz > g.r) return;
-  }
   const int gx = wrapc(d.ox + ci, g.nx), gy = wrapc(d.oy + cj, g.ny), gz = wrapc(d.oz + ck, g.nz);
   const long long gi = (long long)gx + (long long)g.nx * ((long long)gy + (long long)g.ny * gz);
   double u[5];
-  if (nout == 0 || sc.mode == 0) {
+  if (sc.mode == 0) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) u[v] = Uin[v * g.N + gi];
   } else {
     int kd = 0;
-    if (dx > 0) kd = max(kd, face_delay(sc, sid, ci < 0 ? 0 : 1));
-    if (dy > 0) kd = max(kd, face_delay(sc, sid, cj < 0 ? 2 : 3));
-    if (dz > 0) kd = max(kd, face_delay(sc, sid, ck < 0 ? 4 : 5));
+    if (ci < 0 || ci >= d.sx) kd = max(kd, face_delay(sc, sid, ci < 0 ? 0 : 1));
+    if (cj < 0 || cj >= d.sy) kd = max(kd, face_delay(sc, sid, cj < 0 ? 2 : 3));
+    if (ck < 0 || ck >= d.sz) kd = max(kd, face_delay(sc, sid, ck < 0 ? 4 : 5));
     const long long lvN = 5 * g.N;
     if (sc.mode == 2) {
       const double* src = ring + (long long)((sc.n - kd) % sc.R) * lvN;
@@ -93,25 +115,7 @@ __global__ void __launch_bounds__(256) k_view(Geometry g, Physics ph, StepSched 
       }
     }
   }
-  // primitives (App. A): p = (gamma-1)(rho E - rho|u|^2/2), T = gamma M^2 p / rho.  In the FP32
-  // form p and rho E are carried as deviations from p_ref and E_ref (exact algebra: the constant
-  // part of p has no derivative and the constant enthalpy H_ref is added back in k_flux).
-  constexpr bool f32 = std::is_same<T, float>::value;
-  const T rho = (T)u[0];
-  const T ir = (T)1 / rho;
-  const T uu = (T)u[1] * ir, vv = (T)u[2] * ir, ww = (T)u[3] * ir;
-  const T ke = (T)0.5 * ((T)u[1] * uu + (T)u[2] * vv + (T)u[3] * ww);
-  const T rE = f32 ? (T)(u[4] - ph.E_ref) : (T)u[4];
-  const T p = (T)ph.gm1 * (rE - ke);
-  const T temp = f32 ? ((T)ph.gM2 * p + (T)1) * ir : (T)ph.gM2 * p * ir;
-  const long long P = g.Ptot, o = d.pbase + t;
-  Wp[o] = rho;
-  Wp[P + o] = uu;
-  Wp[2 * P + o] = vv;
-  Wp[3 * P + o] = ww;
-  Wp[4 * P + o] = p;
-  Wp[5 * P + o] = temp;
-  Wp[6 * P + o] = rE + p;  // rho E + p (energy flux factor; minus H_ref in the FP32 form)
+  store_prims<T>(g, ph, u, d.pbase + q, Wp);
 }
 
 // ------------------------------------------------------------------------------- k_flux
@@ -176,12 +180,20 @@ __global__ void __launch_bounds__(256) k_flux(Geometry g, Physics ph, const SubD
     f[3] = -(mflux * w + (a == 2 ? p : (T)0));
     f[4] = std::is_same<T, float>::value ? -(et * ua + (T)ph.H_ref * ua) : -(et * ua);
     if (g.viscous) {
-      // tau_ai = mu (du_a/dx_i + du_i/dx_a) - 2/3 mu div delta_ai
+      // tau_ai = mu (du_a/dx_i + du_i/dx_a) - 2/3 mu div delta_ai,  q_a = u_i tau_ai + kappa mu dT/dx_a
       T tau[3];
+      T qa;
+      if (ph.visc_law == 0) {  // mu = 1: the products with mu are exact and skipped
 #pragma unroll
-      for (int i2 = 0; i2 < 3; ++i2) tau[i2] = mu * (du[a][i2] + du[i2][a]);
-      tau[a] -= (T)(2.0 / 3.0) * mu * div;
-      const T qa = u * tau[0] + v * tau[1] + w * tau[2] + kap * mu * dT[a];
+        for (int i2 = 0; i2 < 3; ++i2) tau[i2] = du[a][i2] + du[i2][a];
+        tau[a] = fma((T)(-2.0 / 3.0), div, tau[a]);
+        qa = fma(u, tau[0], fma(v, tau[1], fma(w, tau[2], kap * dT[a])));
+      } else {
+#pragma unroll
+        for (int i2 = 0; i2 < 3; ++i2) tau[i2] = mu * (du[a][i2] + du[i2][a]);
+        tau[a] -= (T)(2.0 / 3.0) * mu * div;
+        qa = u * tau[0] + v * tau[1] + w * tau[2] + kap * mu * dT[a];
+      }
       f[1] = fma(ire, tau[0], f[1]);
       f[2] = fma(ire, tau[1], f[2]);
       f[3] = fma(ire, tau[2], f[3]);
@@ -210,13 +222,25 @@ __global__ void __launch_bounds__(256) k_rk(Geometry g, Physics ph, const SubDev
   const long long P = g.Ptot;
   const T* F = Phi + d.pbase;
   const long long st[3] = {1, sty, stz};
+  // dt R = sum_a (dt c1_a)(Phi_{+1} - Phi_{-1}) + (dt c2_a)(Phi_{+2} - Phi_{-2}) as one FMA chain
+  T k1[3], k2[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    k1[a] = (T)(dt * ph.c1[a]);
+    k2[a] = (T)(dt * ph.c2[a]);
+  }
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    T acc = (T)0;
-    for (int a = 0; a < g.ndim; ++a)
-      acc += cdiff(F + (long long)(a * 5 + c) * P, q, st[a], (T)ph.c1[a], (T)ph.c2[a], g.r);
-    const double R = (double)acc;
-    const double qn = first ? dt * R : fma(A, Q[c * g.N + gi], dt * R);
+    const T* Fx = F + (long long)c * P;
+    T acc = k1[0] * (Fx[q + 1] - Fx[q - 1]);
+    if (g.r == 2) acc = fma(k2[0], Fx[q + 2] - Fx[q - 2], acc);
+    for (int a = 1; a < g.ndim; ++a) {
+      const T* Fa = F + (long long)(a * 5 + c) * P;
+      acc = fma(k1[a], Fa[q + st[a]] - Fa[q - st[a]], acc);
+      if (g.r == 2) acc = fma(k2[a], Fa[q + 2 * st[a]] - Fa[q - 2 * st[a]], acc);
+    }
+    const double dtR = (double)acc;
+    const double qn = first ? dtR : fma(A, Q[c * g.N + gi], dtR);
     if (!last) Q[c * g.N + gi] = qn;
     Uout[c * g.N + gi] = fma(B, qn, Uin[c * g.N + gi]);
   }
@@ -235,12 +259,15 @@ template <typename T>
 static int stage_impl(const Geometry& g, const Physics& ph, const StepSched& sc, const StageLaunch& a,
                       cudaStream_t st, long long* launches, const Timer* tm) {
   const int B = 256;
-  dim3 gv(nblk(a.max_pad, B), g.nsub), gf(nblk(a.max_flux, B), g.nsub), gr(nblk(a.max_own, B), g.nsub);
-  TIMED(tm, 0, (k_view<T><<<gv, B, 0, st>>>(g, ph, sc, a.Uin, a.ring, a.subs, (T*)a.Wp, a.stage, a.s)));
+  dim3 gf(nblk(a.max_flux, B), g.nsub), gr(nblk(a.max_own, B), g.nsub);
+  TIMED(tm, 0, (k_view_own<T><<<gr, B, 0, st>>>(g, ph, a.Uin, a.subs, (T*)a.Wp)));
+  if (a.nhalo > 0)
+    TIMED(tm, 0, (k_view_halo<T><<<nblk(a.nhalo, B), B, 0, st>>>(g, ph, sc, a.Uin, a.ring, a.subs, (const int2*)a.halo,
+                                                                 a.nhalo, (T*)a.Wp, a.stage, a.s)));
   TIMED(tm, 1, (k_flux<T><<<gf, B, 0, st>>>(g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
   TIMED(tm, 2, (k_rk<T><<<gr, B, 0, st>>>(g, ph, a.subs, (const T*)a.Phi, a.Uin, a.Uout, a.Q, a.A, a.B, a.dt,
                                           a.first, a.last)));
-  if (launches) *launches += 3;
+  if (launches) *launches += a.nhalo > 0 ? 4 : 3;
   return (int)cudaGetLastError();
 }
 

@@ -39,3 +39,17 @@ def rel_l2(a, ref):
         num = np.linalg.norm(a[v] - ref[v])
         out.append(num / den if den > 0 else num)
     return np.array(out)
+
+
+def check_diagnostics(dg, ref, U, case, rtol=1e-11):
+    """Diagnostics parity: K and enstrophy relative; each conserved total against the scale of
+    its own sum of magnitudes (totals of rho u, rho v, rho w are ~0 by symmetry and carry the
+    rounding of sums of O(1) values)."""
+    dV = case.dx * case.dy * (case.dz if case.nz > 1 else 1.0)
+    mag = np.abs(U).reshape(5, -1).sum(axis=1) * dV
+    mom = mag[1:4].max()
+    for i in range(2):
+        assert abs(dg[i] - ref[i]) <= rtol * abs(ref[i]), (i, dg[i], ref[i])
+    for v in range(5):
+        scale = mom if v in (1, 2, 3) else mag[v]
+        assert abs(dg[2 + v] - ref[2 + v]) <= rtol * scale, (v, dg[2 + v], ref[2 + v], scale)
