@@ -155,6 +155,53 @@ cfs_status cfs_launch_count(cfs_ctx* ctx, long long* launches);
 cfs_status cfs_set_timing(cfs_ctx* ctx, int on);
 cfs_status cfs_get_timing(cfs_ctx* ctx, double* ms, long long* count);
 
+/* ------------------------------------------------------------------ learned halo predictor
+ * A 3-layer perceptron (CFS_MLP_NIN -> 64 -> 64 -> CFS_MLP_NOUT, GELU in tanh form) predicts for
+ * one face column of a sub-domain's halo (4 points deep, 5 variables) the residual of the current
+ * level over the 3-level extrapolation of Eq. 14, from BF16 features of the delayed levels:
+ *   x[0..19]   (U^{n-k} - U^{n-k-1}) * in_scale[v] at the 4 halo points,
+ *   x[20..39]  (U^{n-k-1} - U^{n-k-2}) * in_scale[v],
+ *   x[40..59]  (U^n - U^{n-k}) * own_scale[v] at the 4 own points next to the face,
+ *   x[60..64]  one-hot delay k (0..4),
+ * each rounded FP64 -> FP32 -> BF16 (round to nearest even), index (depth - 1) * 5 + v.
+ * Output y[(depth - 1) * 5 + v] = (U^n - extrapolation) * out_scale[v].  Parameters are FP32:
+ * W1[64][65], b1[64], W2[64][64], b2[64], W3[20][64], b3[20] (CFS_MLP_NPARAM floats).  The paper has
+ * no counterpart: this is the learned form of the halo that the plain AT stencil is judged against. */
+#define CFS_MLP_NIN 65
+#define CFS_MLP_NOUT 20
+#define CFS_MLP_NPARAM 9684
+
+/* Forward pass: y[n][20] (device, FP32) from x[n][65] (device, BF16 bit patterns) and params
+ * (device).  Asynchronous on stream. */
+cfs_status cfs_mlp_forward(const float* params, const uint16_t* x, float* y, long long n, void* stream);
+
+/* Bytes of the caller-provided device workspace cfs_mlp_grad needs for n samples. */
+size_t cfs_mlp_workspace_bytes(long long n);
+
+/* Gradient of the mean squared error mean((y - target)^2) over n samples and 20 outputs with
+ * respect to all parameters into grad (device, CFS_MLP_NPARAM floats) and the loss into *loss
+ * (device float, may be NULL).  Deterministic: per-chunk sums in a fixed order, then chunk order. */
+cfs_status cfs_mlp_grad(const float* params, const uint16_t* x, const float* target, long long n, void* workspace,
+                        float* grad, float* loss, void* stream);
+
+/* One AdamW update (decoupled weight decay, bias-corrected moments) of all parameters; m and v are
+ * the caller's device moment buffers; step counts from 1. */
+cfs_status cfs_mlp_adamw(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1,
+                         float beta2, float eps, float weight_decay, void* stream);
+
+/* Training samples from the context's ring at its current step n (a synchronous run gives the true
+ * current halo values): spec (device int32 [n][5]) = (sub-domain, face 0..5, t1, t2, delay k) with
+ * t1, t2 the owned coordinates along the axes (a+1)%3 and (a+2)%3 of the face's axis a; scales
+ * (host, 15 doubles: in_scale[5], own_scale[5], out_scale[5]); writes x (device BF16 [n][65]) and
+ * target (device FP32 [n][20]).  Needs n >= 6 and a ring that holds levels n-6..n. */
+cfs_status cfs_halo_samples(cfs_ctx* ctx, const int* spec, long long n, const double* scales, uint16_t* x, float* target);
+
+/* Use (enable = 1) or stop using (0) the network for the stage-0 face halos of AT steps: each step,
+ * every face column's U_buf^(0) = extrapolation + y / out_scale; later stages add the AT buffer-update
+ * increments (W^(m) - W^(0)) R.  Edge halos keep the AT weights.  params and scales are host arrays,
+ * copied.  EINVAL if max_delay > 4 or the run is not viscous CD4 (face halo depth 4). */
+cfs_status cfs_set_halo_model(cfs_ctx* ctx, const float* params, const double* scales, int enable);
+
 /* Diagnostics without any device allocation (no counterpart in the paper: an interface for
  * callers that cannot allocate).  Callers such as an in-situ monitoring hook inside a larger
  * simulation whose pool allocator owns all of the GPU's memory, or a time-critical loop where an

@@ -58,6 +58,8 @@ typedef struct {
   int filter;            /* 1: tenth-order Pade filter once per step */
   double alpha_f;
   double dt;
+  const float* mlp;          /* learned halo network parameters (NULL: plain AT) */
+  const double* mlp_scales;  /* in_scale[5], own_scale[5], out_scale[5] */
 } or_params;
 
 /* ---------------------------------------------------------------- coefficient tables */
@@ -359,6 +361,94 @@ static void rhs_ext(const or_params* p, const subdom* d, work_t* w, double* R) {
       }
 }
 
+/* ---------------------------------------------------------------- learned halo (FP64 reference)
+ * A 3-layer perceptron 65 -> 64 -> 64 -> 20 (GELU, tanh form) predicts, per face column of 4 halo
+ * points, (U^n - three-level extrapolation of Eq. 14) * out_scale from features of the delayed
+ * levels rounded to BF16.  Parameter layout: W1[64][65], b1[64], W2[64][64], b2[64], W3[20][64], b3[20]. */
+#define OM_NIN 65
+#define OM_NH 64
+#define OM_NOUT 20
+#define OM_DEPTH 4
+
+/* FP64 -> FP32 (round to nearest) -> BF16 (round to nearest even), returned as a double */
+double or_bf16(double x) {
+  float f = (float)x;
+  uint32_t b;
+  memcpy(&b, &f, 4);
+  b += 0x7FFFu + ((b >> 16) & 1u);
+  b &= 0xFFFF0000u;
+  memcpy(&f, &b, 4);
+  return (double)f;
+}
+
+static double om_gelu(double z) {
+  const double k0 = 0.7978845608028654, k1 = 0.044715;
+  return 0.5 * z * (1.0 + tanh(k0 * (z + k1 * z * z * z)));
+}
+
+/* y = MLP(x) in FP64 with the FP32 parameters */
+void or_mlp_forward(const float* P, const double* x, double* y) {
+  const float* W1 = P;
+  const float* b1 = W1 + OM_NH * OM_NIN;
+  const float* W2 = b1 + OM_NH;
+  const float* b2 = W2 + OM_NH * OM_NH;
+  const float* W3 = b2 + OM_NH;
+  const float* b3 = W3 + OM_NOUT * OM_NH;
+  double h1[OM_NH], h2[OM_NH];
+  for (int o = 0; o < OM_NH; ++o) {
+    double a = b1[o];
+    for (int i = 0; i < OM_NIN; ++i) a += (double)W1[o * OM_NIN + i] * x[i];
+    h1[o] = om_gelu(a);
+  }
+  for (int o = 0; o < OM_NH; ++o) {
+    double a = b2[o];
+    for (int i = 0; i < OM_NH; ++i) a += (double)W2[o * OM_NH + i] * h1[i];
+    h2[o] = om_gelu(a);
+  }
+  for (int o = 0; o < OM_NOUT; ++o) {
+    double a = b3[o];
+    for (int i = 0; i < OM_NH; ++i) a += (double)W3[o * OM_NH + i] * h2[i];
+    y[o] = a;
+  }
+}
+
+/* Global index of point j (1..4) of the column of face f at owned tangential coordinates (t1, t2):
+ * the halo point at depth j outside the face (halo = 1) or the own point at depth j inside it. */
+static size_t om_point(const or_params* p, const subdom* d, int f, int t1, int t2, int j, int halo) {
+  int a = f / 2, side = f % 2;
+  int c[3], o[3] = {d->ox, d->oy, d->oz}, sz[3] = {d->sx, d->sy, d->sz}, n[3] = {p->nx, p->ny, p->nz};
+  c[(a + 1) % 3] = t1;
+  c[(a + 2) % 3] = t2;
+  if (halo) c[a] = side == 0 ? -j : sz[a] - 1 + j;
+  else c[a] = side == 0 ? j - 1 : sz[a] - j;
+  int g[3];
+  for (int q = 0; q < 3; ++q) g[q] = wrapi(o[q] + c[q], n[q]);
+  return (size_t)g[0] + (size_t)p->nx * (g[1] + (size_t)p->ny * g[2]);
+}
+
+/* Features (BF16-rounded) and the three-level extrapolation of one column at delay k. */
+void or_column_features(const or_params* p, const double* const* lev /* [0]=U^n [1]=U^{n-k} [2]=U^{n-k-1} [3]=U^{n-k-2} */,
+                        int s, int f, int t1, int t2, int k, double* x, double* at3) {
+  const size_t N = (size_t)p->nx * p->ny * p->nz;
+  subdom d;
+  make_subdom(p, s, 0, &d);
+  const double* in = p->mlp_scales;
+  const double* own = p->mlp_scales + 5;
+  double c3[5];
+  or_extrap_weights(2, (double)k, c3);
+  for (int j = 1; j <= OM_DEPTH; ++j) {
+    size_t gh = om_point(p, &d, f, t1, t2, j, 1), go = om_point(p, &d, f, t1, t2, j, 0);
+    for (int v = 0; v < 5; ++v) {
+      double a = lev[1][v * N + gh], b = lev[2][v * N + gh], c = lev[3][v * N + gh];
+      x[(j - 1) * 5 + v] = or_bf16((a - b) * in[v]);
+      x[20 + (j - 1) * 5 + v] = or_bf16((b - c) * in[v]);
+      x[40 + (j - 1) * 5 + v] = or_bf16((lev[0][v * N + go] - lev[1][v * N + go]) * own[v]);
+      at3[(j - 1) * 5 + v] = c3[0] * a + c3[1] * b + c3[2] * c;
+    }
+  }
+  for (int q = 0; q < 5; ++q) x[60 + q] = (q == k) ? 1.0 : 0.0;
+}
+
 /* ---------------------------------------------------------------- the time loop (Alg. 1-3) */
 
 /* delay of face f of sub-domain s at step n before clamping */
@@ -474,6 +564,38 @@ static void halo_init(const or_params* p, const subdom* d, const hist_t* h, long
           hb->qb[v * ne + q] = 0.0;
         }
       }
+}
+
+/* With a learned halo model: U_buf^(0) of every face column is the extrapolation plus the
+ * network's residual; Q_buf stays zero and the buffer updates of Eq. 8 proceed unchanged. */
+static void halo_init_learned(const or_params* p, const subdom* d, int s, const hist_t* h, long n, const int* kf,
+                              halo_t* hb) {
+  const size_t ex = d->ex, ey = d->ey, ne = ex * ey * d->ez;
+  const int nd = p->nz > 1 ? 3 : 2;
+  const int sz[3] = {d->sx, d->sy, d->sz};
+  const double* out = p->mlp_scales + 10;
+  for (int f = 0; f < 2 * nd; ++f) {
+    int a = f / 2, side = f % 2, b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+    int k = kf[f];
+    const double* lev[4] = {H(h, n), H(h, n - k), H(h, n - k - 1), H(h, n - k - 2)};
+    for (int t2 = 0; t2 < sz[b2]; ++t2)
+      for (int t1 = 0; t1 < sz[b1]; ++t1) {
+        double x[OM_NIN], at3[OM_NOUT], y[OM_NOUT];
+        or_column_features(p, lev, s, f, t1, t2, k, x, at3);
+        or_mlp_forward(p->mlp, x, y);
+        for (int j = 1; j <= OM_DEPTH; ++j) {
+          int c[3];
+          c[b1] = t1;
+          c[b2] = t2;
+          c[a] = side == 0 ? -j : sz[a] - 1 + j;
+          size_t q = (size_t)(c[0] + d->g) + ex * ((c[1] + d->g) + ey * (c[2] + d->gz));
+          for (int v = 0; v < 5; ++v) {
+            hb->ub[v * ne + q] = at3[(j - 1) * 5 + v] + y[(j - 1) * 5 + v] / out[v];
+            hb->qb[v * ne + q] = 0.0;
+          }
+        }
+      }
+  }
 }
 
 static void halo_update(const or_params* p, const subdom* d, const hist_t* h, long n, const int* kf, int m,
@@ -650,7 +772,10 @@ int or_run(const or_params* p, double* U, const int8_t* delays, long n0, long ns
               hbs[s].qb = (double*)malloc(sizeof(double) * NV * ne);
               hbs[s].cap = ne;
             }
-            if (m == 1) halo_init(p, &d, &h, n, kfs[s], &hbs[s]);
+            if (m == 1) {
+              halo_init(p, &d, &h, n, kfs[s], &hbs[s]);
+              if (p->mlp) halo_init_learned(p, &d, s, &h, n, kfs[s], &hbs[s]);
+            }
           }
           fill_ext(p, &d, Ucur, mode, &h, n, kfs[s], &hbs[s], &w);
           size_t no = (size_t)d.sx * d.sy * d.sz;

@@ -35,6 +35,7 @@ class OrParams(ctypes.Structure):
         ("order", ctypes.c_int), ("algo", ctypes.c_int), ("at", ctypes.c_int),
         ("caa_L", ctypes.c_int), ("kmax", ctypes.c_int),
         ("filter", ctypes.c_int), ("alpha_f", ctypes.c_double), ("dt", ctypes.c_double),
+        ("mlp", ctypes.POINTER(ctypes.c_float)), ("mlp_scales", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -70,6 +71,9 @@ def _load():
             lib.or_filter_coeffs.argtypes = [ctypes.c_double, d]
             lib.or_filter_line.argtypes = [ctypes.c_int, ctypes.c_double, d, d]
             lib.or_num_threads.restype = ctypes.c_int
+            lib.or_bf16.argtypes = [ctypes.c_double]
+            lib.or_bf16.restype = ctypes.c_double
+            lib.or_mlp_forward.argtypes = [ctypes.POINTER(ctypes.c_float), d, d]
             lib.or_set_num_threads.argtypes = [ctypes.c_int]
             _lib = lib
     return _lib
@@ -95,11 +99,17 @@ def params(case) -> OrParams:
 
 
 def run(case, U0: np.ndarray, nsteps: int, delays: np.ndarray | None = None, n0: int = 0,
-        hist: np.ndarray | None = None, diag: bool = False):
+        hist: np.ndarray | None = None, diag: bool = False, model=None):
     """Advance ``nsteps`` steps of the method (Alg. 1-3 with Eq. 3, 8, 14-15); returns U
-    (and the per-step diagnostics [nsteps][8] if ``diag``)."""
+    (and the per-step diagnostics [nsteps][8] if ``diag``).  ``model`` = (params float32[9684],
+    scales float64[15]) replaces the stage-0 face halos of AT steps by the learned predictor."""
     lib = _load()
     p = params(case)
+    if model is not None:
+        mp = np.ascontiguousarray(model[0], dtype=np.float32)
+        ms = np.ascontiguousarray(model[1], dtype=np.float64)
+        p.mlp = mp.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        p.mlp_scales = ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     U = np.ascontiguousarray(U0, dtype=np.float64).copy()
     if delays is None:
         dl = np.zeros(1, dtype=np.int8)
@@ -182,3 +192,17 @@ def num_threads() -> int:
 
 def set_num_threads(n: int) -> None:
     _load().or_set_num_threads(n)
+
+
+def bf16(x: float) -> float:
+    """FP64 -> FP32 -> BF16 (round to nearest even), the feature rounding of the learned halo."""
+    return _load().or_bf16(float(x))
+
+
+def mlp_forward_c(params: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """The C oracle's FP64 forward pass of the halo network for one feature vector."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros(20)
+    _load().or_mlp_forward(p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _dptr(xx), _dptr(y))
+    return y

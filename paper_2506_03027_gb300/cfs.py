@@ -52,7 +52,7 @@ def header_symbols() -> list[str]:
     """Entry points declared in include/cfs.h."""
     with open(HEADER) as f:
         src = f.read()
-    return sorted(set(re.findall(r"^\s*(?:cfs_status|int|void|const char\*)\s+(cfs_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:cfs_status|int|void|size_t|const char\*)\s+(cfs_\w+)\s*\(", src, re.M)))
 
 
 def load() -> ctypes.CDLL:
@@ -90,6 +90,13 @@ def load() -> ctypes.CDLL:
             "cfs_launch_count": ([vp, ctypes.POINTER(ll)], ip),
             "cfs_set_timing": ([vp, ip], ip),
             "cfs_get_timing": ([vp, dp, ctypes.POINTER(ll)], ip),
+            "cfs_mlp_forward": ([vp, vp, vp, ll, vp], ip),
+            "cfs_mlp_workspace_bytes": ([ll], ctypes.c_size_t),
+            "cfs_mlp_grad": ([vp, vp, vp, ll, vp, vp, vp, vp], ip),
+            "cfs_mlp_adamw": ([vp, vp, vp, vp, ip, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_float, vp], ip),
+            "cfs_halo_samples": ([vp, vp, ll, dp, vp, vp], ip),
+            "cfs_set_halo_model": ([vp, vp, dp, ip], ip),
             "cfs_diagnostics_static": ([vp, ip, ip, ip, dp, ip, vp, vp, ctypes.c_char_p, ctypes.c_size_t], ip),
             "cfs_last_error": ([vp], ctypes.c_char_p),
             "cfs_destroy": ([vp], None),
@@ -243,6 +250,52 @@ def cfs_diagnostics_static(U_ptr: int, nx: int, ny: int, nz: int, spacing, order
                                        ctypes.c_void_p(stream or 0), buf, 256)
     if st != CFS_OK:
         raise CfsError(st, buf.value.decode())
+
+
+MLP_NIN, MLP_NOUT, MLP_NPARAM = 65, 20, 9684
+
+
+def cfs_mlp_forward(params_ptr: int, x_ptr: int, y_ptr: int, n: int, stream: int | None = None):
+    st = load().cfs_mlp_forward(ctypes.c_void_p(params_ptr), ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), n,
+                                ctypes.c_void_p(stream or 0))
+    if st != CFS_OK:
+        raise CfsError(st, "cfs_mlp_forward failed")
+
+
+def cfs_mlp_workspace_bytes(n: int) -> int:
+    return int(load().cfs_mlp_workspace_bytes(n))
+
+
+def cfs_mlp_grad(params_ptr, x_ptr, t_ptr, n, ws_ptr, grad_ptr, loss_ptr, stream=None):
+    st = load().cfs_mlp_grad(ctypes.c_void_p(params_ptr), ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr), n,
+                             ctypes.c_void_p(ws_ptr), ctypes.c_void_p(grad_ptr), ctypes.c_void_p(loss_ptr or 0),
+                             ctypes.c_void_p(stream or 0))
+    if st != CFS_OK:
+        raise CfsError(st, "cfs_mlp_grad failed")
+
+
+def cfs_mlp_adamw(params_ptr, grad_ptr, m_ptr, v_ptr, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0,
+                  stream=None):
+    st = load().cfs_mlp_adamw(ctypes.c_void_p(params_ptr), ctypes.c_void_p(grad_ptr), ctypes.c_void_p(m_ptr),
+                              ctypes.c_void_p(v_ptr), step, lr, beta1, beta2, eps, wd, ctypes.c_void_p(stream or 0))
+    if st != CFS_OK:
+        raise CfsError(st, "cfs_mlp_adamw failed")
+
+
+def cfs_halo_samples(ctx, spec_ptr: int, n: int, scales: np.ndarray, x_ptr: int, t_ptr: int):
+    sc = np.ascontiguousarray(scales, dtype=np.float64)
+    _check(ctx, load().cfs_halo_samples(ctx, ctypes.c_void_p(spec_ptr), n, sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr)))
+
+
+def cfs_set_halo_model(ctx, params: np.ndarray | None, scales: np.ndarray | None, enable: bool = True):
+    if not enable:
+        _check(ctx, load().cfs_set_halo_model(ctx, None, None, 0))
+        return
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    sc = np.ascontiguousarray(scales, dtype=np.float64)
+    _check(ctx, load().cfs_set_halo_model(ctx, ctypes.c_void_p(p.ctypes.data),
+                                          sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1))
 
 
 def cfs_last_error(ctx) -> str:

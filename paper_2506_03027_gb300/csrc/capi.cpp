@@ -66,6 +66,14 @@ struct cfs_ctx {
   int* d_halo = nullptr;
   long long nhalo = 0;
 
+  // learned halo predictor
+  bool learned = false;
+  float* d_mlp = nullptr;
+  double* LH = nullptr;
+  int* d_cols = nullptr;
+  long long ncol = 0;
+  cfs::MlpScales mlp_scales{};
+
   // fused FP32-intermediate stage (3-D Navier-Stokes, CD4)
   bool fused = false;
   int fused_zc = 16;
@@ -525,6 +533,7 @@ cfs_status cfs_step(cfs_ctx* c, long long nsteps) {
     sc.mode = (c->algo == 0 || n < c->C) ? 0 : (c->at ? 1 : 2);
     sc.W = c->d_W;
     sc.Wf = c->d_Wf;
+    sc.LH = nullptr;
     sc.table = nullptr;
     if (sc.mode != 0 && c->algo == 2) {
       if (n >= c->sched_steps) return fail(c, CFS_EINVAL, "step beyond the SAA delay table");
@@ -532,6 +541,13 @@ cfs_status cfs_step(cfs_ctx* c, long long nsteps) {
     }
     const double* src = level_ptr(c, n);
     int pp = 0;
+    if (c->learned && sc.mode == 1) {
+      // stage-0 face halos from the network, once per step (the later stages add AT increments)
+      const int rc = cfs::launch_mlp_halo(g, sc, c->ring, c->d_subs, c->d_cols, c->ncol, c->d_mlp, c->mlp_scales, c->LH,
+                                          c->stream, &c->launches, c->timing ? &c->timer : nullptr);
+      if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
+      sc.LH = c->LH;
+    }
     if (c->fused && sc.mode != 0) {
       const int rc = cfs::launch_halo_prims(g, c->phys, sc, c->ring, c->d_subs, c->d_halo, c->nhalo, c->Wh, c->s,
                                             c->stream, &c->launches, c->timing ? &c->timer : nullptr);
@@ -646,6 +662,99 @@ cfs_status cfs_set_ring(cfs_ctx* c, const double* buf, int where) {
   if (!c->finalized) return fail(c, CFS_ESTATE, "ring after cfs_finalize");
   if (c->sticky) return CFS_ECUDA;
   return ring_copy(c, const_cast<double*>(buf), where, true);
+}
+
+// ------------------------------------------------------------------ learned halo predictor
+
+size_t cfs_mlp_workspace_bytes(long long n) {
+  if (n <= 0) return 0;
+  return sizeof(float) * (size_t)cfs::mlp_workspace_floats(n);
+}
+
+cfs_status cfs_mlp_forward(const float* params, const uint16_t* x, float* y, long long n, void* stream) {
+  if (!params || !x || !y || n < 0) return CFS_EINVAL;
+  if (n == 0) return CFS_OK;
+  return cfs::launch_mlp_forward(params, x, y, n, stream) == 0 ? CFS_OK : CFS_ECUDA;
+}
+
+cfs_status cfs_mlp_grad(const float* params, const uint16_t* x, const float* target, long long n, void* workspace,
+                        float* grad, float* loss, void* stream) {
+  if (!params || !x || !target || !workspace || !grad || n <= 0) return CFS_EINVAL;
+  return cfs::launch_mlp_grad(params, x, target, n, (float*)workspace, grad, loss, stream) == 0 ? CFS_OK : CFS_ECUDA;
+}
+
+cfs_status cfs_mlp_adamw(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1,
+                         float beta2, float eps, float weight_decay, void* stream) {
+  if (!params || !grad || !m || !v || step < 1) return CFS_EINVAL;
+  return cfs::launch_adamw(params, grad, m, v, MLP_NPARAM, step, lr, beta1, beta2, eps, weight_decay, stream) == 0
+             ? CFS_OK
+             : CFS_ECUDA;
+}
+
+static cfs::MlpScales scales_from(const double* sc) {
+  cfs::MlpScales m{};
+  for (int v = 0; v < 5; ++v) {
+    m.in[v] = sc[v];
+    m.own[v] = sc[5 + v];
+    m.out[v] = sc[10 + v];
+  }
+  return m;
+}
+
+cfs_status cfs_halo_samples(cfs_ctx* c, const int* spec, long long n, const double* scales, uint16_t* x, float* target) {
+  if (!c || !spec || !scales || !x || !target || n < 0) return CFS_EINVAL;
+  if (!c->finalized) return fail(c, CFS_ESTATE, "samples after cfs_finalize");
+  if (c->sticky) return CFS_ECUDA;
+  if (c->n < MLP_KMAX + 2 || c->R < MLP_KMAX + 3)
+    return fail(c, CFS_ESTATE, "samples need levels n-k-2 for k up to 4 in the ring (n >= 6, max_delay >= 2)");
+  StepSched sc{};
+  sc.n = c->n;
+  sc.R = c->R;
+  sc.C = c->C;
+  const int rc = cfs::launch_halo_samples(c->geo, sc, c->ring, c->d_subs, spec, n, scales_from(scales), x, target, c->stream);
+  if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "samples launch");
+  return CFS_OK;
+}
+
+cfs_status cfs_set_halo_model(cfs_ctx* c, const float* params, const double* scales, int enable) {
+  if (!c) return CFS_EINVAL;
+  if (!c->finalized) return fail(c, CFS_ESTATE, "halo model after cfs_finalize");
+  if (!enable) {
+    c->learned = false;
+    return CFS_OK;
+  }
+  if (!params || !scales) return fail(c, CFS_EINVAL, "model parameters and scales required");
+  if (c->max_delay > MLP_KMAX) return fail(c, CFS_EINVAL, "the halo model covers delays 0..4: max_delay must be <= 4");
+  if (c->G < MLP_HDEPTH) return fail(c, CFS_EINVAL, "the halo model needs a face halo of depth 4 (viscous CD4)");
+  for (int v = 0; v < 15; ++v)
+    if (!(scales[v] > 0.0) || !std::isfinite(scales[v])) return fail(c, CFS_EINVAL, "scales must be positive");
+  if (!c->d_mlp) {
+    std::vector<int> cols;
+    const int nsub = (int)c->subs.size();
+    for (int sid = 0; sid < nsub; ++sid) {
+      const SubDev& d = c->subs[sid];
+      const int sz[3] = {d.sx, d.sy, d.sz};
+      for (int f = 0; f < 2 * c->ndim; ++f) {
+        const int a = f >> 1, b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+        for (int t2 = 0; t2 < sz[b2]; ++t2)
+          for (int t1 = 0; t1 < sz[b1]; ++t1) {
+            cols.push_back(sid); cols.push_back(f); cols.push_back(t1); cols.push_back(t2);
+          }
+      }
+    }
+    c->ncol = (long long)(cols.size() / 4);
+    c->d_cols = (int*)dev_alloc(c, sizeof(int) * cols.size());
+    c->d_mlp = (float*)dev_alloc(c, sizeof(float) * MLP_NPARAM);
+    c->LH = (double*)dev_alloc(c, sizeof(double) * 5 * (size_t)c->geo.Ptot);
+    if (!c->d_cols || !c->d_mlp || !c->LH) return fail(c, CFS_ENOMEM, "device allocation failed");
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_cols, cols.data(), sizeof(int) * cols.size(), cudaMemcpyHostToDevice, c->stream), "upload columns");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream), "upload columns");
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_mlp, params, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice, c->stream), "upload model");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream), "upload model");
+  c->mlp_scales = scales_from(scales);
+  c->learned = true;
+  return CFS_OK;
 }
 
 cfs_status cfs_launch_count(cfs_ctx* c, long long* launches) {

@@ -9,6 +9,20 @@
 #define CFS_MAX_LEVELS 5   // C: delayed levels of AT4
 #define CFS_MAX_STAGES 5   // s: stages of LSERK4
 
+// learned halo predictor: one face column of HDEPTH halo points, 5 variables
+#define MLP_HDEPTH 4
+#define MLP_KMAX 4                                   // delays 0..4 (one-hot)
+#define MLP_NIN (3 * MLP_HDEPTH * 5 + MLP_KMAX + 1)  // 65
+#define MLP_NH 64
+#define MLP_NOUT (MLP_HDEPTH * 5)                    // 20
+#define MLP_OFF_W1 0
+#define MLP_OFF_B1 (MLP_OFF_W1 + MLP_NH * MLP_NIN)
+#define MLP_OFF_W2 (MLP_OFF_B1 + MLP_NH)
+#define MLP_OFF_B2 (MLP_OFF_W2 + MLP_NH * MLP_NH)
+#define MLP_OFF_W3 (MLP_OFF_B2 + MLP_NH)
+#define MLP_OFF_B3 (MLP_OFF_W3 + MLP_NOUT * MLP_NH)
+#define MLP_NPARAM (MLP_OFF_B3 + MLP_NOUT)           // 9684
+
 namespace cfs {
 
 // Sub-domain descriptor (one per processing element of Sec. 3).
@@ -56,6 +70,7 @@ struct StepSched {
   long long cap;         // clamp: k <= n - C + 1
   const int8_t* table;   // SAA delays of this step [nsub][6] (device), or null
   const double* W;       // device: AT halo weights [(k * s + m) * C + l]
+  const double* LH;      // device: learned stage-0 face-halo values [5][Ptot], or null (plain AT)
   const double* Wf;      // device: filter-halo extrapolation weights c(k+1) [k * C + l]
 };
 
@@ -137,6 +152,27 @@ int launch_halo_prims(const Geometry& g, const Physics& ph, const StepSched& sc,
                       const Timer* tm);
 int launch_stage_fused(const Geometry& g, const Physics& ph, const StepSched& sc, const FusedLaunch& a, void* stream,
                        long long* launches, const Timer* tm);
+
+// learned halo network (mlp.cu)
+size_t mlp_smem_bytes();
+long long mlp_workspace_floats(long long nsamp);
+int launch_mlp_forward(const float* params, const void* x_bf16, float* y, long long nsamp, void* stream);
+int launch_mlp_grad(const float* params, const void* x_bf16, const float* target, long long nsamp, float* workspace,
+                    float* grad, float* loss, void* stream);
+int launch_adamw(float* params, const float* grad, float* m, float* v, int n, int step, float lr, float b1, float b2,
+                 float eps, float wd, void* stream);
+// feature scales: in_scale[5] (delayed-level differences), own_scale[5], out_scale[5]
+struct MlpScales {
+  double in[5], own[5], out[5];
+};
+// Samples for training: spec[i] = (sub-domain, face, t1, t2, k); features from levels n-k..n-k-2 of
+// the ring (halo) and n, n-k (own), target = (U^n - 3-level extrapolation) * out scale.
+int launch_halo_samples(const Geometry& g, const StepSched& sc, const double* ring, const SubDev* subs, const int* spec,
+                        long long n, MlpScales sc_, void* x_bf16, float* target, void* stream);
+// Solver: stage-0 halo values of every face column from the network (AT mode), into LH[5][Ptot].
+int launch_mlp_halo(const Geometry& g, const StepSched& sc, const double* ring, const SubDev* subs, const int* cols,
+                    long long ncol, const float* params, MlpScales sc_, double* LH, void* stream, long long* launches,
+                    const Timer* tm);
 
 int launch_diagnostics(const Geometry& g, const Physics& ph, const double* U, double* partial, int nblocks,
                        double* out, double dV, void* stream, long long* launches);

@@ -74,16 +74,19 @@ __global__ void __launch_bounds__(256) k_halo_prims(Geometry g, Physics ph, Step
     for (int c = 0; c < 7; ++c) Wh[(long long)c * P + o] = w[c];
     return;
   }
-  // AT: U_buf^(m) = sum_l W^(m)_l(k) U^{n-k-l} for every stage m, accumulated in FP64
+  // AT: U_buf^(m) = sum_l W^(m)_l(k) U^{n-k-l} for every stage m, accumulated in FP64; with the
+  // learned halo, face points start from the network's stage-0 value and add (W^(m) - W^(0)) R
+  const bool learned = sc.LH && ((int)(ci < 0 || ci >= d.sx) + (int)(cj < 0 || cj >= d.sy) + (int)(ck < 0 || ck >= d.sz) == 1);
   double acc[CFS_MAX_STAGES][5];
   for (int m = 0; m < s; ++m)
-    for (int v = 0; v < 5; ++v) acc[m][v] = 0.0;
+    for (int v = 0; v < 5; ++v) acc[m][v] = learned ? sc.LH[(long long)v * g.Ptot + d.pbase + t] : 0.0;
   for (int l = 0; l < sc.C; ++l) {
     const double* src = ring + (long long)((sc.n - kd - l) % sc.R) * lvN;
     double r[5];
     for (int v = 0; v < 5; ++v) r[v] = src[v * g.N + gi];
-    for (int m = 0; m < s; ++m) {
-      const double wl = __ldg(sc.W + (kd * s + m) * sc.C + l);
+    const double w0 = learned ? __ldg(sc.W + (kd * s) * sc.C + l) : 0.0;
+    for (int m = learned ? 1 : 0; m < s; ++m) {
+      const double wl = __ldg(sc.W + (kd * s + m) * sc.C + l) - w0;
       for (int v = 0; v < 5; ++v) acc[m][v] = fma(wl, r[v], acc[m][v]);
     }
   }

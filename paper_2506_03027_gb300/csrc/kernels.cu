@@ -105,13 +105,29 @@ __global__ void __launch_bounds__(256) k_view_halo(Geometry g, Physics ph, StepS
       for (int v = 0; v < 5; ++v) u[v] = src[v * g.N + gi];
     } else {
       const double* w = sc.W + (kd * s + stage) * sc.C;
+      const bool face = (int)(ci < 0 || ci >= d.sx) + (int)(cj < 0 || cj >= d.sy) + (int)(ck < 0 || ck >= d.sz) == 1;
+      if (sc.LH && face) {
+        // learned stage-0 value (per face column, from the network) plus the AT buffer-update
+        // increments (W^(m) - W^(0)) applied to the delayed levels
+        const double* w0 = sc.W + (kd * s) * sc.C;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) u[v] = 0.0;
-      for (int l = 0; l < sc.C; ++l) {
-        const double* src = ring + (long long)((sc.n - kd - l) % sc.R) * lvN;
-        const double wl = __ldg(w + l);
+        for (int v = 0; v < 5; ++v) u[v] = sc.LH[(long long)v * g.Ptot + d.pbase + q];
+        if (stage > 0)
+          for (int l = 0; l < sc.C; ++l) {
+            const double* src = ring + (long long)((sc.n - kd - l) % sc.R) * lvN;
+            const double wl = __ldg(w + l) - __ldg(w0 + l);
 #pragma unroll
-        for (int v = 0; v < 5; ++v) u[v] = fma(wl, src[v * g.N + gi], u[v]);
+            for (int v = 0; v < 5; ++v) u[v] = fma(wl, src[v * g.N + gi], u[v]);
+          }
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = 0.0;
+        for (int l = 0; l < sc.C; ++l) {
+          const double* src = ring + (long long)((sc.n - kd - l) % sc.R) * lvN;
+          const double wl = __ldg(w + l);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) u[v] = fma(wl, src[v * g.N + gi], u[v]);
+        }
       }
     }
   }

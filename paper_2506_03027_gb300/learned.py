@@ -1,0 +1,152 @@
+"""Learned halo predictor: training data from synchronous runs, training on the GPU with the
+library's own kernels (cfs_mlp_grad / cfs_mlp_adamw), and evaluation.
+
+The network (see include/cfs.h) predicts, per face column of a sub-domain's 4-deep halo, the
+residual of the current-level values over the three-level extrapolation of Eq. 14 from the
+delayed levels n-k, n-k-1, n-k-2 and the change of the sub-domain's own boundary values since
+level n-k.  In a synchronous run every halo value at level n is known exactly, so any step of such
+a run yields training samples for every delay k <= 4 at once.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import cfs
+from .inputs import Case, initial_state
+
+KMAX = 4
+NIN, NOUT, NPARAM = cfs.MLP_NIN, cfs.MLP_NOUT, cfs.MLP_NPARAM
+
+
+def _axis_split(n: int, p: int):
+    base, rem = divmod(n, p)
+    lens = [base + (1 if i < rem else 0) for i in range(p)]
+    return lens
+
+
+def sample_specs(case: Case, n: int, rng: np.random.Generator) -> np.ndarray:
+    """Random (sub-domain, face, t1, t2, k) with k uniform on 0..4 and (t1, t2) uniform over the face."""
+    lx, ly, lz = (_axis_split(case.nx, case.px), _axis_split(case.ny, case.py), _axis_split(case.nz, case.pz))
+    sid = rng.integers(0, case.nsub, size=n)
+    ix = sid % case.px
+    iy = (sid // case.px) % case.py
+    iz = sid // (case.px * case.py)
+    nfaces = 6 if case.nz > 1 else 4
+    face = rng.integers(0, nfaces, size=n)
+    sz = np.stack([np.array(lx)[ix], np.array(ly)[iy], np.array(lz)[iz]], axis=1)
+    a = face // 2
+    n1 = sz[np.arange(n), (a + 1) % 3]
+    n2 = sz[np.arange(n), (a + 2) % 3]
+    t1 = (rng.random(n) * n1).astype(np.int64)
+    t2 = (rng.random(n) * n2).astype(np.int64)
+    k = rng.integers(0, KMAX + 1, size=n)
+    return np.stack([sid, face, t1, t2, k], axis=1).astype(np.int32)
+
+
+def generate(case: Case, first_step: int, last_step: int, per_step: int, seed: int, scales: np.ndarray):
+    """Run the case synchronously and draw `per_step` samples at every step in [first_step,
+    last_step).  Returns device tensors (x BF16 bit patterns as int16 [n][65], target FP32 [n][20])."""
+    import torch
+    assert first_step >= KMAX + 2
+    rng = np.random.default_rng(seed)
+    sa = case.replace(algo="SA")
+    s = cfs.Solver(sa, max_delay=KMAX)
+    s.set_schedule()
+    s.set_state(initial_state(sa))
+    s.step(first_step)
+    xs, ts = [], []
+    for _ in range(first_step, last_step):
+        spec = torch.from_numpy(sample_specs(sa, per_step, rng)).cuda()
+        x = torch.empty((per_step, NIN), dtype=torch.int16, device="cuda")
+        t = torch.empty((per_step, NOUT), dtype=torch.float32, device="cuda")
+        cfs.cfs_halo_samples(s.ctx, spec.data_ptr(), per_step, scales, x.data_ptr(), t.data_ptr())
+        xs.append(x)
+        ts.append(t)
+        s.step(1)
+    torch.cuda.synchronize()
+    s.close()
+    return torch.cat(xs), torch.cat(ts)
+
+
+def bf16_to_float(x):
+    """int16 BF16 bit patterns (torch) to float32."""
+    import torch
+    return (x.to(torch.int32) << 16).view(torch.float32) if x.dtype == torch.int32 else \
+        ((x.to(torch.int32) & 0xFFFF) << 16).view(torch.float32)
+
+
+def fit_scales(case: Case, seed: int = 1, first_step: int = 6, nsteps: int = 6, per_step: int = 20000) -> np.ndarray:
+    """Per-variable scales from unscaled samples: 1 / RMS of each feature group and of the target."""
+    unit = np.ones(15)
+    X, T = generate(case, first_step, first_step + nsteps, per_step, seed, unit)
+    Xf = bf16_to_float(X).double().cpu().numpy()
+    Tf = T.double().cpu().numpy()
+    sc = np.ones(15)
+    for v in range(5):
+        d1 = Xf[:, [j * 5 + v for j in range(4)]]
+        own = Xf[:, [40 + j * 5 + v for j in range(4)]]
+        tv = Tf[:, [j * 5 + v for j in range(4)]]
+        sc[v] = 1.0 / max(math.sqrt(np.mean(d1 ** 2)), 1e-30)
+        sc[5 + v] = 1.0 / max(math.sqrt(np.mean(own ** 2)), 1e-30)
+        sc[10 + v] = 1.0 / max(math.sqrt(np.mean(tv ** 2)), 1e-30)
+    return sc
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """Seeded initial parameters: uniform +-1/sqrt(fan_in) weights, zero biases (FP32)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, shape in ((NIN, (64, NIN)), (None, (64,)), (64, (64, 64)), (None, (64,)), (64, (NOUT, 64)),
+                          (None, (NOUT,))):
+        parts.append(np.zeros(shape) if fan_in is None else rng.uniform(-1, 1, size=shape) / math.sqrt(fan_in))
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+def train(X, T, steps: int = 3000, batch: int = 4096, lr: float = 2e-3, seed: int = 0, log_every: int = 500):
+    """AdamW on the mean squared error with the library's gradient and update kernels; cosine
+    learning-rate decay.  Returns (params as numpy float32, list of (step, loss))."""
+    import torch
+    n = X.shape[0]
+    params = torch.from_numpy(init_params(seed)).cuda()
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    grad = torch.zeros_like(params)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    ws = torch.empty(cfs.cfs_mlp_workspace_bytes(batch) // 4 + 1, dtype=torch.float32, device="cuda")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    stream = torch.cuda.current_stream().cuda_stream
+    hist = []
+    for it in range(1, steps + 1):
+        idx = torch.randint(0, n, (batch,), device="cuda", generator=g)
+        xb = X[idx].contiguous()
+        tb = T[idx].contiguous()
+        cfs.cfs_mlp_grad(params.data_ptr(), xb.data_ptr(), tb.data_ptr(), batch, ws.data_ptr(), grad.data_ptr(),
+                         loss.data_ptr(), stream)
+        rate = lr * 0.5 * (1.0 + math.cos(math.pi * (it - 1) / steps))
+        cfs.cfs_mlp_adamw(params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), it, rate, 0.9, 0.999, 1e-8,
+                          1e-5, stream)
+        if it % log_every == 0 or it == 1 or it == steps:
+            hist.append((it, float(loss.item())))
+    return params.cpu().numpy(), hist
+
+
+def predict(params: np.ndarray, X):
+    """Network outputs for device features X (int16 BF16 patterns) with the library's forward."""
+    import torch
+    p = torch.from_numpy(np.ascontiguousarray(params, dtype=np.float32)).cuda()
+    y = torch.empty((X.shape[0], NOUT), dtype=torch.float32, device="cuda")
+    cfs.cfs_mlp_forward(p.data_ptr(), X.data_ptr(), y.data_ptr(), X.shape[0], torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return y
+
+
+def halo_errors(params: np.ndarray, X, T) -> dict:
+    """Mean squared error of the current-level halo values, in target units, of the three-level
+    extrapolation alone (target itself) and with the network's residual added."""
+    y = predict(params, X)
+    base = float((T.double() ** 2).mean())
+    net = float(((T - y).double() ** 2).mean())
+    return {"extrapolation3_mse": base, "learned_mse": net, "ratio": net / base if base > 0 else float("nan")}
