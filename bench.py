@@ -286,6 +286,16 @@ def run_ours(args, rank, world, local_rank):
                                         "rel_l2_vs_fp64_path": err, "after_steps": n_done,
                                         "per_kernel_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in kt32.items() if v[1]}}}
 
+    # ---------------- batched uneven blocks (one launch per kernel over all blocks, CUDA graph)
+    if args.precision == 0 and not args.no_forms and world == 1:
+        forms = forms or {}
+        forms["batched_blocks"] = batched_form(args, stream)
+
+    # ---------------- learned halo predictor (trained here on synchronous-run halos)
+    if args.precision == 0 and not args.no_forms and not args.no_learned and world == 1:
+        forms = forms or {}
+        forms["learned_halo"] = learned_form(args)
+
     # ---------------- roofline of the dominant kernel
     peaks = measured_peaks()
     clocks = clk.summary()
@@ -332,6 +342,124 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(case)
     return line
+
+
+NACA_BLOCKS = [(512, 192, 64), (384, 192, 64), (256, 192, 64), (256, 128, 64), (192, 128, 64), (128, 128, 64),
+               (192, 96, 32), (128, 96, 32), (96, 96, 32), (128, 64, 32), (96, 64, 32), (96, 64, 32)]
+
+
+def batched_blocks():
+    """Twelve independent periodic blocks with the uneven sizes of a 12-block airfoil C-grid
+    (96 x 64 x 32 up to 512 x 192 x 64, 20.8 M points), Navier-Stokes TGV fields, sub-domains of
+    about 32-64 points per axis, SAA delays 0..2."""
+    from paper_2506_03027_gb300 import inputs as I
+    base = I.tgv_case(32, 1, "SAA", kmax=2)
+    blocks = []
+    for (nx, ny, nz) in NACA_BLOCKS:
+        b = base.replace(nx=nx, ny=ny, nz=nz, px=max(1, nx // 64), py=max(1, ny // 64), pz=max(1, nz // 32),
+                         lx=2 * math.pi * nx / 128, ly=2 * math.pi * ny / 128, lz=2 * math.pi * nz / 128)
+        blocks.append(b)
+    dt = min(I.cfl_dt(b, I.tgv_state(b), 0.05) for b in blocks)
+    return [b.replace(dt=dt) for b in blocks]
+
+
+def batched_form(args, stream_unused):
+    import torch
+    from paper_2506_03027_gb300 import cfs
+    from paper_2506_03027_gb300 import inputs as I
+    blocks = batched_blocks()
+    npts = sum(b.npts for b in blocks)
+    nsub = sum(b.nsub for b in blocks)
+    K, W = max(3, args.steps // 4), args.warmup
+    delays = I.saa_delays(blocks[0].replace(px=nsub, py=1, pz=1), W + K)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        s = cfs.Solver(blocks[0], blocks=blocks, graph=True, stream=st)
+        s.set_schedule(delays=delays)
+        for i, b in enumerate(blocks):
+            s.set_state(I.tgv_state(b), block=i)
+        s.step(W)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.step(K)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = s.launches()
+        s.close()
+    return {"value": npts * 5 * K / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms / K, "points": npts,
+            "blocks": len(blocks), "subdomains": nsub, "cuda_graph": True, "launches_per_step": launches / K,
+            "workload": "12 independent periodic NS blocks with the 12-block airfoil C-grid sizes, SAA 0..2, FP64"}
+
+
+def learned_form(args):
+    """Train the halo network on halos of a synchronous TGV 128^3 run (CFL 0.05), then compare
+    SAA (delays 0..4) with the plain AT halos and with the network against the synchronous run of
+    the same step (relative L2 of the asynchrony error), and time the 256^3, 512-sub-domain case
+    with and without the network."""
+    import torch
+    from paper_2506_03027_gb300 import cfs
+    from paper_2506_03027_gb300 import inputs as I
+    from paper_2506_03027_gb300 import learned as L
+    t0 = time.perf_counter()
+    c = I.tgv_case(128, 4, "SA")
+    c = c.replace(dt=I.cfl_dt(c, I.tgv_state(c), 0.05))
+    scales = L.fit_scales(c, seed=1, first_step=6, nsteps=4, per_step=20000)
+    X, T = L.generate(c, 6, 30, 20000, seed=2, scales=scales)
+    params, hist = L.train(X, T, steps=1200, batch=4096, lr=2e-3, seed=0)
+    Xh, Th = L.generate(c, 40, 46, 20000, seed=3, scales=scales)
+    halo = L.halo_errors(params, Xh, Th)
+    del X, T, Xh, Th
+    train_s = time.perf_counter() - t0
+    nst = 40
+    saa = c.replace(algo="SAA", kmax=4)
+    d = I.saa_delays(saa, nst)
+    runs = {}
+    for name in ("SA", "AT", "learned"):
+        cc = c if name == "SA" else saa
+        s = cfs.Solver(cc, max_delay=4)
+        s.set_schedule(delays=d if name != "SA" else None)
+        if name == "learned":
+            cfs.cfs_set_halo_model(s.ctx, params, scales)
+        s.set_state(I.tgv_state(cc))
+        s.step(nst)
+        runs[name] = s.get_state()
+        s.close()
+    mom = lambda U: math.sqrt(sum(float(np.linalg.norm(U[v])) ** 2 for v in (1, 2, 3)))
+    def err(U):
+        ref = runs["SA"]
+        return [float(np.linalg.norm(U[v] - ref[v]) / (mom(ref) if v in (1, 2, 3) else np.linalg.norm(ref[v])))
+                for v in range(5)]
+    # throughput at 256^3 with 512 sub-domains, SAA delays 0..4
+    big = I.tgv_case(256, 8, "SAA", kmax=4)
+    big = big.replace(dt=I.cfl_dt(big, I.tgv_state(big), 0.05))
+    K, W = 6, 6
+    db = I.saa_delays(big, W + K)
+    tput = {}
+    for name in ("AT", "learned"):
+        s = cfs.Solver(big, max_delay=4)
+        s.set_schedule(delays=db)
+        if name == "learned":
+            cfs.cfs_set_halo_model(s.ctx, params, scales)
+        s.set_state(I.tgv_state(big))
+        s.step(W)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.step(K)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        tput[name] = {"value": big.npts * 5 / (ms * 1e-3) / 1e6, "ms_per_step": ms}
+        s.close()
+    return {"rel_l2_vs_sa_after_40_steps": {"AT": err(runs["AT"]), "learned": err(runs["learned"])},
+            "halo_mse_heldout": halo, "train_loss_first_last": [hist[0][1], hist[-1][1]],
+            "train_seconds": train_s, "throughput_256": tput, "unit": UNIT,
+            "workload": "network trained on synchronous TGV 128^3 halos; SAA delays 0..4 at CFL 0.05; "
+                        "throughput on TGV 256^3 with 8^3 sub-domains"}
 
 
 def oracle_sample(case, nsteps):
@@ -390,6 +518,7 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-halo form (trains a network)")
     ap.add_argument("--grid", type=int, default=128, help="grid points per axis (profiling runs only)")
     ap.add_argument("--split", type=int, default=4, help="sub-domains per axis (profiling runs only)")
     args = ap.parse_args()

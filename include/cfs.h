@@ -71,11 +71,16 @@ cfs_status cfs_set_allocator(cfs_ctx* ctx, cfs_alloc_fn alloc, cfs_free_fn free_
 
 /* Add a uniform Cartesian block of ni x nj x nk points with spacing {dx, dy, dz} (host array of
  * 3 doubles), periodic in every direction (each face connected to the opposite face of the same
- * block).  nk = 1 makes the run two-dimensional.  *block_id receives the index (0 for the first
- * block; this version supports one block).  EINVAL for non-positive sizes or a second block. */
+ * block).  nk = 1 makes the run two-dimensional.  *block_id receives the index (0, 1, ... in the
+ * order of the calls).  Several blocks of uneven sizes form a batch of independent problems that
+ * advance together: every stage launch covers the sub-domains of all blocks, whose states are
+ * stored one after another (block b at offset 5 x the points of blocks 0..b-1 in a state array).
+ * All blocks share the physics, scheme, dt and schedule algorithm; they must all be 2-D or all
+ * 3-D.  EINVAL for non-positive sizes or mixed dimensionality. */
 cfs_status cfs_add_block(cfs_ctx* ctx, int ni, int nj, int nk, const double* spacing, int* block_id);
 
-/* Decompose a block into pi x pj x pk sub-domains (the paper's PEs, Sec. 3): along each axis
+/* Decompose a block into pi x pj x pk sub-domains (the paper's PEs, Sec. 3); sub-domains are
+ * numbered block after block, x fastest within a block.  Along each axis
  * n points split into p parts as evenly as possible, the first n mod p parts one point longer.
  * Every sub-domain must be at least as wide as the halo it needs (2 r for viscous runs, r for
  * Euler, r = 2 for CD4 and 1 for CD2; 5 with the filter).  EINVAL otherwise. */
@@ -105,8 +110,8 @@ cfs_status cfs_finalize(cfs_ctx* ctx, int max_delay);
  * numbered x fastest.  EINVAL on out-of-range entries. */
 cfs_status cfs_set_schedule(cfs_ctx* ctx, int algo, int at, int L, long long nsteps, const int8_t* delays);
 
-/* Copy the state of block `block` in (set) or out (get).  where: 0 = host pointer, 1 = device
- * pointer.  set_state defines the state at the current step index (0 after cfs_finalize; see
+/* Copy the state of block `block` ([5][nz][ny][nx] of that block) in (set) or out (get).
+ * where: 0 = host pointer, 1 = device pointer.  set_state defines the state at the current step index (0 after cfs_finalize; see
  * cfs_set_step) and is the start of a fresh history unless the ring is restored as well.
  * get_state synchronises the stream. */
 cfs_status cfs_set_state(cfs_ctx* ctx, int block, const double* U, int where);
@@ -125,8 +130,21 @@ cfs_status cfs_set_step(cfs_ctx* ctx, long long n);
  * stream; errors of device work surface at the next synchronising call. */
 cfs_status cfs_step(cfs_ctx* ctx, long long nsteps);
 
-/* Diagnostics of the current state U^n (synchronises): out[8] = {K, enstrophy, sum rho,
- * sum rho u, sum rho v, sum rho w, sum rho E, non-finite flag}, K and enstrophy volume averages
+/* Launch shapes (before cfs_finalize): tile height fy (4, 8 or 16) and z chunk zc of the fused
+ * FP32-intermediate stage kernel (tiles of 32 x fy columns marching zc planes), and the threads per
+ * CTA (128, 256, 512) of the other stage kernels.  Results are identical for every choice; the
+ * autotuner of the Python package picks the fastest and stores it. */
+cfs_status cfs_set_tiles(cfs_ctx* ctx, int fy, int zc, int threads);
+
+/* CUDA-graph mode (on = 1): cfs_step captures the kernels of one step once -- the step index is
+ * kept in device memory and every kernel derives the step's mode, delays and ring slots from it --
+ * and replays the graph once per step.  The graph is rebuilt after cfs_set_dt, cfs_set_schedule
+ * or cfs_set_halo_model.  Needs a created (non-default) stream: EINVAL for the legacy stream.
+ * Per-kernel timing (cfs_set_timing) bypasses the graph. */
+cfs_status cfs_set_graph(cfs_ctx* ctx, int on);
+
+/* Diagnostics of the current state U^n over all blocks (synchronises): out[8] = {K, enstrophy,
+ * sum rho, sum rho u, sum rho v, sum rho w, sum rho E, non-finite flag}, K and enstrophy point averages
  * with rho_0 = 1 (Sec. 5.2), vorticity by the scheme's central difference, sums weighted by the
  * cell volume.  Returns ENAN (and fills out) when the state holds a non-finite value. */
 cfs_status cfs_diagnostics(cfs_ctx* ctx, double* out);

@@ -89,6 +89,8 @@ def load() -> ctypes.CDLL:
             "cfs_at_weights": ([ip, ip, dp], ip),
             "cfs_launch_count": ([vp, ctypes.POINTER(ll)], ip),
             "cfs_set_timing": ([vp, ip], ip),
+            "cfs_set_graph": ([vp, ip], ip),
+            "cfs_set_tiles": ([vp, ip, ip, ip], ip),
             "cfs_get_timing": ([vp, dp, ctypes.POINTER(ll)], ip),
             "cfs_mlp_forward": ([vp, vp, vp, ll, vp], ip),
             "cfs_mlp_workspace_bytes": ([ll], ctypes.c_size_t),
@@ -230,6 +232,14 @@ NKINDS = 5
 KIND_NAMES = ("view", "flux", "stage_update", "filter", "diagnostics")
 
 
+def cfs_set_tiles(ctx, fy: int, zc: int, threads: int):
+    _check(ctx, load().cfs_set_tiles(ctx, fy, zc, threads))
+
+
+def cfs_set_graph(ctx, on: bool):
+    _check(ctx, load().cfs_set_graph(ctx, int(on)))
+
+
 def cfs_set_timing(ctx, on: bool):
     _check(ctx, load().cfs_set_timing(ctx, int(on)))
 
@@ -340,12 +350,16 @@ class TorchAllocator:
 
 
 class Solver:
-    """One periodic block of ``case`` on the current CUDA device and stream."""
+    """A context on the current CUDA device and stream for one periodic block (``case``) or for a
+    batch of independent periodic blocks (``blocks``: cases sharing the physics and scheme of the
+    first, each with its own size, spacing and split)."""
 
     def __init__(self, case, max_delay: int | None = None, precision: int = 0, stream=None,
-                 use_torch_allocator: bool = True):
+                 use_torch_allocator: bool = True, blocks=None, tiles=None, graph: bool = False):
         import torch
         self.torch = torch
+        self.blocks = list(blocks) if blocks is not None else [case]
+        case = self.blocks[0]
         self.case = case
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -354,13 +368,18 @@ class Solver:
         if use_torch_allocator:
             self.alloc = TorchAllocator(self.device)
             cfs_set_allocator(self.ctx, self.alloc.alloc_cb, self.alloc.free_cb)
-        cfs_add_block(self.ctx, case.nx, case.ny, case.nz, (case.dx, case.dy, case.dz))
-        cfs_split_block(self.ctx, 0, case.px, case.py, case.pz)
+        for b in self.blocks:
+            bid = cfs_add_block(self.ctx, b.nx, b.ny, b.nz, (b.dx, b.dy, b.dz))
+            cfs_split_block(self.ctx, bid, b.px, b.py, b.pz)
+        if tiles is not None:
+            cfs_set_tiles(self.ctx, *tiles)
         if max_delay is None:
             max_delay = {"SA": 0, "CAA": case.caa_L - 1, "SAA": case.kmax}[case.algo]
         cfs_finalize(self.ctx, max_delay)
         self.npts = case.nx * case.ny * case.nz
         cfs_set_dt(self.ctx, case.dt)
+        if graph:
+            cfs_set_graph(self.ctx, True)
 
     def set_schedule(self, algo: str | None = None, at: bool | None = None, L: int | None = None,
                      delays: np.ndarray | None = None):
@@ -370,27 +389,29 @@ class Solver:
         L = c.caa_L if L is None else L
         cfs_set_schedule(self.ctx, ALGO[algo], int(at), L, delays if algo == "SAA" else None)
 
-    def set_state(self, U):
-        """U: numpy array (host) or CUDA tensor (device), FP64 [5][nz][ny][nx]."""
+    def set_state(self, U, block: int = 0):
+        """U: numpy array (host) or CUDA tensor (device), FP64 [5][nz][ny][nx] of the block."""
+        b = self.blocks[block]
+        n = 5 * b.nx * b.ny * b.nz
         if isinstance(U, np.ndarray):
             a = np.ascontiguousarray(U, dtype=np.float64)
-            assert a.size == 5 * self.npts
-            cfs_set_state(self.ctx, 0, a.ctypes.data, HOST)
+            assert a.size == n
+            cfs_set_state(self.ctx, block, a.ctypes.data, HOST)
         else:
             t = U.contiguous()
-            assert t.dtype == self.torch.float64 and t.numel() == 5 * self.npts and t.is_cuda
-            cfs_set_state(self.ctx, 0, t.data_ptr(), DEVICE)
+            assert t.dtype == self.torch.float64 and t.numel() == n and t.is_cuda
+            cfs_set_state(self.ctx, block, t.data_ptr(), DEVICE)
 
-    def get_state(self, out=None):
-        """Current state to a new numpy array, or into ``out`` (numpy or CUDA tensor)."""
-        c = self.case
+    def get_state(self, out=None, block: int = 0):
+        """Current state of a block to a new numpy array, or into ``out`` (numpy or CUDA tensor)."""
+        c = self.blocks[block]
         if out is None:
             out = np.empty((5, c.nz, c.ny, c.nx), dtype=np.float64)
         if isinstance(out, np.ndarray):
             assert out.flags.c_contiguous and out.dtype == np.float64
-            cfs_get_state(self.ctx, 0, out.ctypes.data, HOST)
+            cfs_get_state(self.ctx, block, out.ctypes.data, HOST)
         else:
-            cfs_get_state(self.ctx, 0, out.data_ptr(), DEVICE)
+            cfs_get_state(self.ctx, block, out.data_ptr(), DEVICE)
         return out
 
     def step(self, n: int = 1):

@@ -18,18 +18,28 @@ using cfs::Physics;
 using cfs::StepSched;
 using cfs::SubDev;
 
+struct Block {
+  int nx = 0, ny = 0, nz = 0;
+  double h[3] = {1, 1, 1};
+  int P[3] = {1, 1, 1};
+  long long N = 0;        // points
+  long long base = 0;     // offset of its state in a state array (doubles): 5 x points before it
+  int sid0 = 0;           // index of its first sub-domain
+  int* d_owner[3] = {nullptr, nullptr, nullptr};
+  int* d_axis_off[3] = {nullptr, nullptr, nullptr};
+  int* d_axis_len[3] = {nullptr, nullptr, nullptr};
+};
+
 struct cfs_ctx {
   cfs_params p{};
+  std::vector<Block> blocks;
   cudaStream_t stream = nullptr;
   cfs_alloc_fn alloc = nullptr;
   cfs_free_fn freef = nullptr;
   void* user = nullptr;
   std::vector<void*> owned;
 
-  bool has_block = false, finalized = false;
-  int nx = 0, ny = 0, nz = 0;
-  double h[3] = {1, 1, 1};
-  int P[3] = {1, 1, 1};
+  bool finalized = false;
 
   int s = 0, C = 0, r = 0, G = 0, Gz = 0, ndim = 0;
   int max_delay = 0, R = 0;
@@ -52,9 +62,6 @@ struct cfs_ctx {
   SubDev* d_subs = nullptr;
   std::vector<SubDev> subs;
   int max_pad = 0, max_own = 0, max_flux = 0;
-  int* d_owner[3] = {nullptr, nullptr, nullptr};
-  int* d_axis_off[3] = {nullptr, nullptr, nullptr};
-  int* d_axis_len[3] = {nullptr, nullptr, nullptr};
   double* d_thomas = nullptr;
   int Lmax = 0;
   double filt_h[6] = {0};
@@ -76,6 +83,7 @@ struct cfs_ctx {
 
   // fused FP32-intermediate stage (3-D Navier-Stokes, CD4)
   bool fused = false;
+  int threads = 256;   // threads per CTA of the FP64 / 3-kernel stage kernels
   int fused_zc = 16;
   int fused_fy = 8;
   int fused_grid = 0;
@@ -89,6 +97,13 @@ struct cfs_ctx {
   std::string err;
   bool sticky = false;
   long long launches = 0;
+
+  // CUDA graph of one step (device-resident step counter)
+  long long* d_n = nullptr;
+  bool graph_on = false;
+  bool graph_dirty = true;
+  cudaGraphExec_t gexec = nullptr;
+  long long graph_launches = 0;  // kernel launches captured in one step
 
   // per-kernel event timing
   bool timing = false;
@@ -211,34 +226,38 @@ cfs_status cfs_set_allocator(cfs_ctx* c, cfs_alloc_fn alloc, cfs_free_fn free_fn
 cfs_status cfs_add_block(cfs_ctx* c, int ni, int nj, int nk, const double* spacing, int* block_id) {
   if (!c) return CFS_EINVAL;
   if (c->finalized) return fail(c, CFS_ESTATE, "blocks must be added before cfs_finalize");
-  if (c->has_block) return fail(c, CFS_EINVAL, "this version supports a single block");
   if (ni < 1 || nj < 1 || nk < 1 || !spacing) return fail(c, CFS_EINVAL, "bad block size");
   for (int a = 0; a < 3; ++a)
     if (!(spacing[a] > 0.0)) return fail(c, CFS_EINVAL, "spacing must be positive");
   if ((long long)ni * nj * nk > (1LL << 31)) return fail(c, CFS_EINVAL, "block too large");
-  c->nx = ni; c->ny = nj; c->nz = nk;
-  for (int a = 0; a < 3; ++a) c->h[a] = spacing[a];
-  c->has_block = true;
-  c->ndim = nk > 1 ? 3 : 2;
+  const int ndim = nk > 1 ? 3 : 2;
+  if (!c->blocks.empty() && ndim != c->ndim) return fail(c, CFS_EINVAL, "all blocks must be 2-D or all 3-D");
+  if (c->blocks.size() >= 4096) return fail(c, CFS_EINVAL, "too many blocks");
+  Block b;
+  b.nx = ni; b.ny = nj; b.nz = nk;
+  for (int a = 0; a < 3; ++a) b.h[a] = spacing[a];
+  b.N = (long long)ni * nj * nk;
+  c->blocks.push_back(b);
+  c->ndim = ndim;
   c->Gz = nk > 1 ? c->G : 0;
-  if (block_id) *block_id = 0;
+  if (block_id) *block_id = (int)c->blocks.size() - 1;
   return CFS_OK;
 }
 
 cfs_status cfs_split_block(cfs_ctx* c, int block, int pi, int pj, int pk) {
   if (!c) return CFS_EINVAL;
   if (c->finalized) return fail(c, CFS_ESTATE, "split before cfs_finalize");
-  if (!c->has_block || block != 0) return fail(c, CFS_EINVAL, "unknown block");
-  if (pi < 1 || pj < 1 || pk < 1 || pi > c->nx || pj > c->ny || pk > c->nz)
-    return fail(c, CFS_EINVAL, "bad split");
-  c->P[0] = pi; c->P[1] = pj; c->P[2] = pk;
+  if (block < 0 || block >= (int)c->blocks.size()) return fail(c, CFS_EINVAL, "unknown block");
+  Block& b = c->blocks[block];
+  if (pi < 1 || pj < 1 || pk < 1 || pi > b.nx || pj > b.ny || pk > b.nz) return fail(c, CFS_EINVAL, "bad split");
+  b.P[0] = pi; b.P[1] = pj; b.P[2] = pk;
   return CFS_OK;
 }
 
 cfs_status cfs_connect(cfs_ctx* c, int blockA, int faceA, int blockB, int faceB, int orientation) {
   if (!c) return CFS_EINVAL;
-  if (blockA == 0 && blockB == 0 && c->has_block && orientation == 0 && faceA >= 0 && faceA < 6 &&
-      faceB == (faceA ^ 1))
+  if (blockA == blockB && blockA >= 0 && blockA < (int)c->blocks.size() && orientation == 0 && faceA >= 0 &&
+      faceA < 6 && faceB == (faceA ^ 1))
     return CFS_OK;  // periodic self-connection: the default
   return fail(c, CFS_EINVAL, "only periodic self-connections are supported in this version");
 }
@@ -251,46 +270,63 @@ cfs_status cfs_set_bc(cfs_ctx* c, int, int, int, const double*) {
 cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   if (!c) return CFS_EINVAL;
   if (c->finalized) return fail(c, CFS_ESTATE, "already finalized");
-  if (!c->has_block) return fail(c, CFS_ESTATE, "no block");
+  if (c->blocks.empty()) return fail(c, CFS_ESTATE, "no block");
   if (max_delay < 0 || max_delay > CFS_MAX_DELAY) return fail(c, CFS_EINVAL, "max_delay out of range");
   const int need = c->p.filter ? (c->G > 5 ? c->G : 5) : c->G;
-  // sub-domain table
-  const int nsub = c->P[0] * c->P[1] * c->P[2];
+  // sub-domain table: blocks in order, x fastest within a block
+  int nsub = 0;
+  long long Ntot = 0;
+  for (Block& b : c->blocks) {
+    b.sid0 = nsub;
+    b.base = 5 * Ntot;
+    nsub += b.P[0] * b.P[1] * b.P[2];
+    Ntot += b.N;
+  }
   c->subs.resize(nsub);
   long long pbase = 0;
   c->max_pad = c->max_own = c->max_flux = 0;
   const int rz = c->ndim == 3 ? c->r : 0;
-  for (int iz = 0; iz < c->P[2]; ++iz)
-    for (int iy = 0; iy < c->P[1]; ++iy)
-      for (int ix = 0; ix < c->P[0]; ++ix) {
-        SubDev d{};
-        split_axis(c->nx, c->P[0], ix, &d.ox, &d.sx);
-        split_axis(c->ny, c->P[1], iy, &d.oy, &d.sy);
-        split_axis(c->nz, c->P[2], iz, &d.oz, &d.sz);
-        if (d.sx < need || d.sy < need || (c->ndim == 3 && d.sz < need))
-          return fail(c, CFS_EINVAL, "sub-domain smaller than the halo it needs");
-        d.ex = d.sx + 2 * c->G;
-        d.ey = d.sy + 2 * c->G;
-        d.ez = d.sz + 2 * c->Gz;
-        d.ix = ix; d.iy = iy; d.iz = iz;
-        d.pbase = pbase;
-        const long long npad = (long long)d.ex * d.ey * d.ez;
-        pbase += npad;
-        const long long nown = (long long)d.sx * d.sy * d.sz;
-        const long long nfl = (long long)(d.sx + 2 * c->r) * (d.sy + 2 * c->r) * (d.sz + 2 * rz);
-        if (npad > (1LL << 30)) return fail(c, CFS_EINVAL, "sub-domain too large");
-        c->max_pad = (int)std::max<long long>(c->max_pad, npad);
-        c->max_own = (int)std::max<long long>(c->max_own, nown);
-        c->max_flux = (int)std::max<long long>(c->max_flux, nfl);
-        c->subs[ix + c->P[0] * (iy + c->P[1] * iz)] = d;
-      }
+  const double a_cd = c->p.order == 4 ? 4.0 / 3.0 : 1.0, b_cd = c->p.order == 4 ? -1.0 / 3.0 : 0.0;
+  for (const Block& b : c->blocks)
+    for (int iz = 0; iz < b.P[2]; ++iz)
+      for (int iy = 0; iy < b.P[1]; ++iy)
+        for (int ix = 0; ix < b.P[0]; ++ix) {
+          SubDev d{};
+          split_axis(b.nx, b.P[0], ix, &d.ox, &d.sx);
+          split_axis(b.ny, b.P[1], iy, &d.oy, &d.sy);
+          split_axis(b.nz, b.P[2], iz, &d.oz, &d.sz);
+          if (d.sx < need || d.sy < need || (c->ndim == 3 && d.sz < need))
+            return fail(c, CFS_EINVAL, "sub-domain smaller than the halo it needs");
+          d.ex = d.sx + 2 * c->G;
+          d.ey = d.sy + 2 * c->G;
+          d.ez = d.sz + 2 * c->Gz;
+          d.ix = ix; d.iy = iy; d.iz = iz;
+          d.pbase = pbase;
+          d.bnx = b.nx; d.bny = b.ny; d.bnz = b.nz;
+          d.bN = b.N;
+          d.bbase = b.base;
+          for (int a = 0; a < 3; ++a) {  // CD coefficients of Eq. 2 (alpha = 0) for the block's spacing
+            d.c1[a] = (a_cd / 2.0) / b.h[a];
+            d.c2[a] = (b_cd / 4.0) / b.h[a];
+          }
+          const long long npad = (long long)d.ex * d.ey * d.ez;
+          pbase += npad;
+          const long long nown = (long long)d.sx * d.sy * d.sz;
+          const long long nfl = (long long)(d.sx + 2 * c->r) * (d.sy + 2 * c->r) * (d.sz + 2 * rz);
+          if (npad > (1LL << 30)) return fail(c, CFS_EINVAL, "sub-domain too large");
+          c->max_pad = (int)std::max<long long>(c->max_pad, npad);
+          c->max_own = (int)std::max<long long>(c->max_own, nown);
+          c->max_flux = (int)std::max<long long>(c->max_flux, nfl);
+          c->subs[b.sid0 + ix + b.P[0] * (iy + b.P[1] * iz)] = d;
+        }
   c->max_delay = max_delay;
   c->R = max_delay + c->C + 1;
-  const long long N = (long long)c->nx * c->ny * c->nz;
+  const long long N = Ntot;
+  const Block& b0 = c->blocks[0];
   const size_t tsz = c->p.precision == 1 ? sizeof(float) : sizeof(double);
   // geometry / physics
   Geometry& g = c->geo;
-  g.nx = c->nx; g.ny = c->ny; g.nz = c->nz; g.N = N; g.nsub = nsub;
+  g.nx = b0.nx; g.ny = b0.ny; g.nz = b0.nz; g.N = N; g.nsub = nsub;
   g.G = c->G; g.Gz = c->Gz; g.r = c->r; g.ndim = c->ndim; g.viscous = c->p.viscous; g.Ptot = pbase;
   Physics& ph = c->phys;
   ph.gamma = c->p.gamma; ph.gm1 = c->p.gamma - 1.0; ph.gM2 = c->p.gamma * c->p.mach * c->p.mach;
@@ -300,11 +336,11 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   ph.p_ref = 1.0 / ph.gM2;
   ph.E_ref = ph.p_ref / ph.gm1;
   ph.H_ref = ph.E_ref + ph.p_ref;
-  // CD coefficients of Eq. 2 with alpha = 0: CD4 a = 4/3, b = -1/3; CD2 a = 1, b = 0
-  const double a_cd = c->p.order == 4 ? 4.0 / 3.0 : 1.0, b_cd = c->p.order == 4 ? -1.0 / 3.0 : 0.0;
+  // CD coefficients of Eq. 2 with alpha = 0 (CD4 a = 4/3, b = -1/3; CD2 a = 1, b = 0) of the
+  // first block; each sub-domain carries those of its own block
   for (int a = 0; a < 3; ++a) {
-    ph.c1[a] = (a_cd / 2.0) / c->h[a];
-    ph.c2[a] = (b_cd / 4.0) / c->h[a];
+    ph.c1[a] = (a_cd / 2.0) / b0.h[a];
+    ph.c2[a] = (b_cd / 4.0) / b0.h[a];
   }
   // device memory
   c->ring = (double*)dev_alloc(c, sizeof(double) * 5 * N * c->R);
@@ -343,25 +379,29 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   const int nW = (max_delay + 1) * c->s * c->C, nWf = (max_delay + 1) * c->C;
   c->d_W = (double*)dev_alloc(c, sizeof(double) * nW);
   c->d_Wf = (double*)dev_alloc(c, sizeof(double) * nWf);
-  c->diag_blocks = 4 * 152;
-  c->d_partial = (double*)dev_alloc(c, sizeof(double) * 8 * c->diag_blocks);
   c->d_out = (double*)dev_alloc(c, sizeof(double) * 8);
-  const int n3[3] = {c->nx, c->ny, c->nz};
+  c->d_n = (long long*)dev_alloc(c, sizeof(long long));
   c->Lmax = 0;
-  for (int a = 0; a < 3; ++a) {
-    c->d_owner[a] = (int*)dev_alloc(c, sizeof(int) * n3[a]);
-    c->d_axis_off[a] = (int*)dev_alloc(c, sizeof(int) * c->P[a]);
-    c->d_axis_len[a] = (int*)dev_alloc(c, sizeof(int) * c->P[a]);
-    c->Lmax = std::max(c->Lmax, (n3[a] + c->P[a] - 1) / c->P[a]);
+  for (Block& b : c->blocks) {
+    const int n3[3] = {b.nx, b.ny, b.nz};
+    for (int a = 0; a < 3; ++a) {
+      b.d_owner[a] = (int*)dev_alloc(c, sizeof(int) * n3[a]);
+      b.d_axis_off[a] = (int*)dev_alloc(c, sizeof(int) * b.P[a]);
+      b.d_axis_len[a] = (int*)dev_alloc(c, sizeof(int) * b.P[a]);
+      c->Lmax = std::max(c->Lmax, (n3[a] + b.P[a] - 1) / b.P[a]);
+    }
   }
+  c->diag_blocks = 2 * 152;
+  c->d_partial = (double*)dev_alloc(c, sizeof(double) * 8 * c->diag_blocks * c->blocks.size());
   c->d_thomas = (double*)dev_alloc(c, sizeof(double) * (size_t)(c->Lmax + 1) * 2 * c->Lmax);
   for (void* q : c->owned)
     if (!q) return fail(c, CFS_ENOMEM, "device allocation failed");
-  if (!c->ring || !c->buf[0] || !c->buf[1] || !c->Q || (!c->fused && (!c->Wp || !c->Phi)) || !c->d_subs || !c->d_W || !c->d_Wf ||
+  if (!c->d_n || !c->ring || !c->buf[0] || !c->buf[1] || !c->Q || (!c->fused && (!c->Wp || !c->Phi)) || !c->d_subs || !c->d_W || !c->d_Wf ||
       !c->d_partial || !c->d_out || !c->d_thomas)
     return fail(c, CFS_ENOMEM, "device allocation failed");
-  for (int a = 0; a < 3; ++a)
-    if (!c->d_owner[a] || !c->d_axis_off[a] || !c->d_axis_len[a]) return fail(c, CFS_ENOMEM, "device allocation failed");
+  for (const Block& b : c->blocks)
+    for (int a = 0; a < 3; ++a)
+      if (!b.d_owner[a] || !b.d_axis_off[a] || !b.d_axis_len[a]) return fail(c, CFS_ENOMEM, "device allocation failed");
   // halo list: faces to depth G, viscous edges to r x r (the points each sub-domain reads from
   // its neighbours)
   {
@@ -412,25 +452,26 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
       im[i] = 1.0 / m;
     }
   }
-  std::vector<int> owner[3], aoff[3], alen[3];
-  for (int a = 0; a < 3; ++a) {
-    owner[a].resize(n3[a]);
-    aoff[a].resize(c->P[a]);
-    alen[a].resize(c->P[a]);
-    for (int i = 0; i < c->P[a]; ++i) {
-      split_axis(n3[a], c->P[a], i, &aoff[a][i], &alen[a][i]);
-      for (int t = 0; t < alen[a][i]; ++t) owner[a][aoff[a][i] + t] = i;
-    }
-  }
   cudaStream_t st = c->stream;
   CUDA_TRY(c, cudaMemcpyAsync(c->d_subs, c->subs.data(), sizeof(SubDev) * nsub, cudaMemcpyHostToDevice, st), "upload sub-domains");
   CUDA_TRY(c, cudaMemcpyAsync(c->d_W, W.data(), sizeof(double) * nW, cudaMemcpyHostToDevice, st), "upload weights");
   CUDA_TRY(c, cudaMemcpyAsync(c->d_Wf, Wf.data(), sizeof(double) * nWf, cudaMemcpyHostToDevice, st), "upload weights");
   CUDA_TRY(c, cudaMemcpyAsync(c->d_thomas, th.data(), sizeof(double) * th.size(), cudaMemcpyHostToDevice, st), "upload filter");
-  for (int a = 0; a < 3; ++a) {
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_owner[a], owner[a].data(), sizeof(int) * n3[a], cudaMemcpyHostToDevice, st), "upload tables");
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_axis_off[a], aoff[a].data(), sizeof(int) * c->P[a], cudaMemcpyHostToDevice, st), "upload tables");
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_axis_len[a], alen[a].data(), sizeof(int) * c->P[a], cudaMemcpyHostToDevice, st), "upload tables");
+  std::vector<std::vector<int>> keep;  // host tables stay alive until the stream is synchronised below
+  for (Block& b : c->blocks) {
+    const int n3[3] = {b.nx, b.ny, b.nz};
+    for (int a = 0; a < 3; ++a) {
+      std::vector<int> owner(n3[a]), aoff(b.P[a]), alen(b.P[a]);
+      for (int i = 0; i < b.P[a]; ++i) {
+        split_axis(n3[a], b.P[a], i, &aoff[i], &alen[i]);
+        for (int t = 0; t < alen[i]; ++t) owner[aoff[i] + t] = i;
+      }
+      keep.push_back(owner); keep.push_back(aoff); keep.push_back(alen);
+      const size_t k0 = keep.size() - 3;
+      CUDA_TRY(c, cudaMemcpyAsync(b.d_owner[a], keep[k0].data(), sizeof(int) * n3[a], cudaMemcpyHostToDevice, st), "upload tables");
+      CUDA_TRY(c, cudaMemcpyAsync(b.d_axis_off[a], keep[k0 + 1].data(), sizeof(int) * b.P[a], cudaMemcpyHostToDevice, st), "upload tables");
+      CUDA_TRY(c, cudaMemcpyAsync(b.d_axis_len[a], keep[k0 + 2].data(), sizeof(int) * b.P[a], cudaMemcpyHostToDevice, st), "upload tables");
+    }
   }
   CUDA_TRY(c, cudaMemsetAsync(c->ring, 0, sizeof(double) * 5 * N * c->R, st), "clear ring");
   // the host vectors above are pageable: make sure the copies have consumed them
@@ -464,6 +505,7 @@ cfs_status cfs_set_schedule(cfs_ctx* c, int algo, int at, int L, long long nstep
   c->algo = algo;
   c->at = at ? 1 : 0;
   c->L = algo == 1 ? L : 1;
+  c->graph_dirty = true;
   return CFS_OK;
 }
 
@@ -472,10 +514,11 @@ static double* level_ptr(cfs_ctx* c, long long level) { return c->ring + (size_t
 cfs_status cfs_set_state(cfs_ctx* c, int block, const double* U, int where) {
   if (!c) return CFS_EINVAL;
   if (!c->finalized) return fail(c, CFS_ESTATE, "set_state after cfs_finalize");
-  if (block != 0 || !U) return fail(c, CFS_EINVAL, "bad block or pointer");
+  if (block < 0 || block >= (int)c->blocks.size() || !U) return fail(c, CFS_EINVAL, "bad block or pointer");
   if (c->sticky) return CFS_ECUDA;
-  const size_t bytes = sizeof(double) * 5 * c->geo.N;
-  CUDA_TRY(c, cudaMemcpyAsync(level_ptr(c, c->n), U, bytes, where ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream), "set_state");
+  const Block& b = c->blocks[block];
+  const size_t bytes = sizeof(double) * 5 * b.N;
+  CUDA_TRY(c, cudaMemcpyAsync(level_ptr(c, c->n) + b.base, U, bytes, where ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream), "set_state");
   if (!where) CUDA_TRY(c, cudaStreamSynchronize(c->stream), "set_state");
   return CFS_OK;
 }
@@ -483,10 +526,11 @@ cfs_status cfs_set_state(cfs_ctx* c, int block, const double* U, int where) {
 cfs_status cfs_get_state(cfs_ctx* c, int block, double* U, int where) {
   if (!c) return CFS_EINVAL;
   if (!c->finalized) return fail(c, CFS_ESTATE, "get_state after cfs_finalize");
-  if (block != 0 || !U) return fail(c, CFS_EINVAL, "bad block or pointer");
+  if (block < 0 || block >= (int)c->blocks.size() || !U) return fail(c, CFS_EINVAL, "bad block or pointer");
   if (c->sticky) return CFS_ECUDA;
-  const size_t bytes = sizeof(double) * 5 * c->geo.N;
-  CUDA_TRY(c, cudaMemcpyAsync(U, level_ptr(c, c->n), bytes, where ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream), "get_state");
+  const Block& b = c->blocks[block];
+  const size_t bytes = sizeof(double) * 5 * b.N;
+  CUDA_TRY(c, cudaMemcpyAsync(U, level_ptr(c, c->n) + b.base, bytes, where ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream), "get_state");
   CUDA_TRY(c, cudaStreamSynchronize(c->stream), "get_state");
   return CFS_OK;
 }
@@ -496,6 +540,7 @@ cfs_status cfs_set_dt(cfs_ctx* c, double dt) {
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CFS_EINVAL, "dt must be positive");
   c->dt = dt;
   c->dt_set = true;
+  c->graph_dirty = true;
   return CFS_OK;
 }
 
@@ -512,6 +557,121 @@ cfs_status cfs_set_step(cfs_ctx* c, long long n) {
   return CFS_OK;
 }
 
+// Enqueue the kernels of step n on the context's stream.  graph = true: the step index and
+// everything derived from it (mode, delays, ring slots) are read by the kernels from d_n, so the
+// enqueued sequence is the same for every step and can be captured once.
+static cfs_status enqueue_step(cfs_ctx* c, long long n, bool graph) {
+  const Geometry& g = c->geo;
+  const int nops = c->s + (c->p.filter ? c->ndim : 0);
+  StepSched sc{};
+  sc.n = n;
+  sc.R = c->R;
+  sc.algo = c->algo;
+  sc.L = c->L;
+  sc.C = c->C;
+  sc.cap = n - c->C + 1;
+  sc.mode = (c->algo == 0 || n < c->C) ? 0 : (c->at ? 1 : 2);
+  sc.W = c->d_W;
+  sc.Wf = c->d_Wf;
+  sc.LH = nullptr;
+  sc.table = nullptr;
+  sc.at = c->at;
+  sc.nsub = (int)c->subs.size();
+  sc.table_base = c->algo == 2 ? c->d_sched : nullptr;
+  sc.Ntot = g.N;
+  sc.dn = graph ? c->d_n : nullptr;
+  if (!graph && sc.mode != 0 && c->algo == 2) sc.table = c->d_sched + (size_t)n * c->subs.size() * 6;
+  const cfs::Timer* tm = (c->timing && !graph) ? &c->timer : nullptr;
+  const double* src = graph ? nullptr : level_ptr(c, n);
+  int pp = 0;
+  if (c->learned && (graph || sc.mode == 1)) {
+    // stage-0 face halos from the network, once per step (the later stages add AT increments)
+    const int rc = cfs::launch_mlp_halo(g, sc, c->ring, c->d_subs, c->d_cols, c->ncol, c->d_mlp, c->mlp_scales, c->LH,
+                                        c->stream, &c->launches, tm);
+    if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
+    sc.LH = c->LH;
+  }
+  if (c->fused && (graph || sc.mode != 0)) {
+    const int rc = cfs::launch_halo_prims(g, c->phys, sc, c->ring, c->d_subs, c->d_halo, c->nhalo, c->Wh, c->s, c->stream,
+                                          &c->launches, tm);
+    if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
+  }
+  for (int op = 0; op < nops; ++op) {
+    const bool last_op = op == nops - 1;
+    double* dst = last_op ? (graph ? nullptr : level_ptr(c, n + 1)) : c->buf[pp];
+    const int in_ring = graph && op == 0, out_ring = graph && last_op;
+    int rc;
+    if (op < c->s && c->fused) {
+      cfs::FusedLaunch a{};
+      a.Uin = src; a.Uout = dst; a.Q = c->Q; a.subs = c->d_subs; a.work = c->d_work; a.nwork = c->nwork;
+      a.grid = c->fused_grid; a.fy = c->fused_fy; a.Wh = c->Wh; a.stage = op;
+      a.A = c->A[op]; a.B = c->B[op]; a.dt = c->dt; a.first = op == 0; a.last = op == c->s - 1;
+      a.ring = c->ring; a.in_ring = in_ring; a.out_ring = out_ring;
+      rc = cfs::launch_stage_fused(g, c->phys, sc, a, c->stream, &c->launches, tm);
+    } else if (op < c->s) {
+      cfs::StageLaunch a{};
+      a.Uin = src; a.Uout = dst; a.Q = c->Q; a.ring = c->ring; a.subs = c->d_subs;
+      a.Wp = c->Wp; a.Phi = c->Phi; a.stage = op; a.s = c->s;
+      a.A = c->A[op]; a.B = c->B[op]; a.dt = c->dt;
+      a.first = op == 0; a.last = op == c->s - 1;
+      a.in_ring = in_ring; a.out_ring = out_ring;
+      a.threads = c->threads;
+      a.max_pad = c->max_pad; a.max_own = c->max_own; a.max_flux = c->max_flux;
+      a.halo = c->d_halo; a.nhalo = c->nhalo;
+      rc = cfs::launch_stage(g, c->phys, sc, a, c->p.precision, c->stream, &c->launches, tm);
+    } else {
+      rc = 0;
+      for (const Block& b : c->blocks) {
+        cfs::FilterLaunch f{};
+        f.Uin = src; f.Uout = dst; f.ring = c->ring;
+        f.in_ring = in_ring; f.out_ring = out_ring;
+        f.nx = b.nx; f.ny = b.ny; f.nz = b.nz; f.bN = b.N; f.bbase = b.base; f.sid0 = b.sid0;
+        for (int a = 0; a < 3; ++a) {
+          f.owner[a] = b.d_owner[a]; f.axis_off[a] = b.d_axis_off[a]; f.axis_len[a] = b.d_axis_len[a];
+          f.P[a] = b.P[a];
+        }
+        f.thomas = c->d_thomas; f.Lmax = c->Lmax; f.alpha = c->p.alpha_f;
+        for (int m = 0; m < 6; ++m) f.h[m] = c->filt_h[m];
+        f.b1 = c->filt_h[1] - c->p.alpha_f;
+        rc = cfs::launch_filter(g, sc, f, op - c->s, c->p.precision, c->stream, &c->launches, tm);
+        if (rc != 0) break;
+      }
+    }
+    if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
+    src = dst;
+    if (!last_op) pp ^= 1;
+  }
+  if (graph) {
+    const int rc = cfs::launch_advance_step(c->d_n, c->stream);
+    if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
+    c->launches += 1;
+  }
+  return CFS_OK;
+}
+
+static cfs_status build_graph(cfs_ctx* c) {
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+  const long long before = c->launches;
+  cfs_status st = enqueue_step(c, c->n, true);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  if (st != CFS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
+  c->graph_launches = c->launches - before;
+  e = cudaGraphInstantiate(&c->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+  c->graph_dirty = false;
+  return CFS_OK;
+}
+
 cfs_status cfs_step(cfs_ctx* c, long long nsteps) {
   if (!c) return CFS_EINVAL;
   if (!c->finalized) return fail(c, CFS_ESTATE, "step after cfs_finalize");
@@ -519,79 +679,55 @@ cfs_status cfs_step(cfs_ctx* c, long long nsteps) {
   if (c->sticky) return CFS_ECUDA;
   if (nsteps < 0) return fail(c, CFS_EINVAL, "negative step count");
   c->launches = 0;
-  const Geometry& g = c->geo;
-  const int nops = c->s + (c->p.filter ? c->ndim : 0);
-  for (long long it = 0; it < nsteps; ++it) {
-    const long long n = c->n;
-    StepSched sc{};
-    sc.n = n;
-    sc.R = c->R;
-    sc.algo = c->algo;
-    sc.L = c->L;
-    sc.C = c->C;
-    sc.cap = n - c->C + 1;
-    sc.mode = (c->algo == 0 || n < c->C) ? 0 : (c->at ? 1 : 2);
-    sc.W = c->d_W;
-    sc.Wf = c->d_Wf;
-    sc.LH = nullptr;
-    sc.table = nullptr;
-    if (sc.mode != 0 && c->algo == 2) {
-      if (n >= c->sched_steps) return fail(c, CFS_EINVAL, "step beyond the SAA delay table");
-      sc.table = c->d_sched + (size_t)n * c->subs.size() * 6;
-    }
-    const double* src = level_ptr(c, n);
-    int pp = 0;
-    if (c->learned && sc.mode == 1) {
-      // stage-0 face halos from the network, once per step (the later stages add AT increments)
-      const int rc = cfs::launch_mlp_halo(g, sc, c->ring, c->d_subs, c->d_cols, c->ncol, c->d_mlp, c->mlp_scales, c->LH,
-                                          c->stream, &c->launches, c->timing ? &c->timer : nullptr);
-      if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
-      sc.LH = c->LH;
-    }
-    if (c->fused && sc.mode != 0) {
-      const int rc = cfs::launch_halo_prims(g, c->phys, sc, c->ring, c->d_subs, c->d_halo, c->nhalo, c->Wh, c->s,
-                                            c->stream, &c->launches, c->timing ? &c->timer : nullptr);
-      if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
-    }
-    for (int op = 0; op < nops; ++op) {
-      double* dst = (op == nops - 1) ? level_ptr(c, n + 1) : c->buf[pp];
-      int rc;
-      if (op < c->s && c->fused) {
-        cfs::FusedLaunch a{};
-        a.Uin = src; a.Uout = dst; a.Q = c->Q; a.subs = c->d_subs; a.work = c->d_work; a.nwork = c->nwork;
-        a.grid = c->fused_grid; a.fy = c->fused_fy; a.Wh = c->Wh; a.stage = op;
-        a.A = c->A[op]; a.B = c->B[op]; a.dt = c->dt; a.first = op == 0; a.last = op == c->s - 1;
-        rc = cfs::launch_stage_fused(g, c->phys, sc, a, c->stream, &c->launches, c->timing ? &c->timer : nullptr);
-      } else if (op < c->s) {
-        cfs::StageLaunch a{};
-        a.Uin = src; a.Uout = dst; a.Q = c->Q; a.ring = c->ring; a.subs = c->d_subs;
-        a.Wp = c->Wp; a.Phi = c->Phi; a.stage = op; a.s = c->s;
-        a.A = c->A[op]; a.B = c->B[op]; a.dt = c->dt;
-        a.first = op == 0; a.last = op == c->s - 1;
-        a.max_pad = c->max_pad; a.max_own = c->max_own; a.max_flux = c->max_flux;
-        a.halo = c->d_halo; a.nhalo = c->nhalo;
-        rc = cfs::launch_stage(g, c->phys, sc, a, c->p.precision, c->stream, &c->launches,
-                               c->timing ? &c->timer : nullptr);
-      } else {
-        cfs::FilterLaunch f{};
-        f.Uin = src; f.Uout = dst; f.ring = c->ring;
-        for (int a = 0; a < 3; ++a) {
-          f.owner[a] = c->d_owner[a]; f.axis_off[a] = c->d_axis_off[a]; f.axis_len[a] = c->d_axis_len[a];
-          f.P[a] = c->P[a];
-        }
-        f.thomas = c->d_thomas; f.Lmax = c->Lmax; f.alpha = c->p.alpha_f;
-        for (int m = 0; m < 6; ++m) f.h[m] = c->filt_h[m];
-        f.b1 = c->filt_h[1] - c->p.alpha_f;
-        rc = cfs::launch_filter(g, sc, f, op - c->s, c->p.precision, c->stream, &c->launches,
-                                c->timing ? &c->timer : nullptr);
+  if (c->algo == 2) {  // asynchronous SAA steps need their rows of the delay table
+    const long long last = c->n + nsteps - 1;
+    if (nsteps > 0 && last >= c->C && last >= c->sched_steps) {
+      // run what the table covers, then report
+      const long long ok = std::max(0LL, std::min(nsteps, std::max(c->sched_steps, (long long)c->C) - c->n));
+      if (ok > 0) {
+        cfs_status st = cfs_step(c, ok);
+        if (st != CFS_OK) return st;
       }
-      if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
-      src = dst;
-      if (op != nops - 1) pp ^= 1;
+      return fail(c, CFS_EINVAL, "step beyond the SAA delay table");
     }
-    c->n = n + 1;
+  }
+  if (c->graph_on && !c->timing && nsteps > 0) {
+    if (c->graph_dirty || !c->gexec) {
+      cfs_status st = build_graph(c);
+      if (st != CFS_OK) return st;
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_n, &c->n, sizeof(long long), cudaMemcpyHostToDevice, c->stream), "step counter");
+    for (long long it = 0; it < nsteps; ++it) CUDA_TRY(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch");
+    c->n += nsteps;
+    c->launches = nsteps * c->graph_launches;
+    return CFS_OK;
+  }
+  for (long long it = 0; it < nsteps; ++it) {
+    cfs_status st = enqueue_step(c, c->n, false);
+    if (st != CFS_OK) return st;
+    c->n += 1;
     if (c->timing && c->ev_used > 4096) timer_flush(c);
   }
+  return CFS_OK;
+}
+
+cfs_status cfs_set_tiles(cfs_ctx* c, int fy, int zc, int threads) {
+  if (!c) return CFS_EINVAL;
+  if (c->finalized) return fail(c, CFS_ESTATE, "tiles are set before cfs_finalize");
+  if (fy != 4 && fy != 8 && fy != 16) return fail(c, CFS_EINVAL, "tile height must be 4, 8 or 16");
+  if (zc < 1 || zc > 4096) return fail(c, CFS_EINVAL, "z chunk must be in 1..4096");
+  if (threads != 128 && threads != 256 && threads != 512) return fail(c, CFS_EINVAL, "threads must be 128, 256 or 512");
+  c->fused_fy = fy;
+  c->fused_zc = zc;
+  c->threads = threads;
+  return CFS_OK;
+}
+
+cfs_status cfs_set_graph(cfs_ctx* c, int on) {
+  if (!c) return CFS_EINVAL;
+  if (on && c->stream == nullptr) return fail(c, CFS_EINVAL, "graph mode needs a created (non-default) stream");
+  c->graph_on = on != 0;
+  c->graph_dirty = true;
   return CFS_OK;
 }
 
@@ -619,10 +755,25 @@ cfs_status cfs_diagnostics(cfs_ctx* c, double* out) {
   if (!c || !out) return CFS_EINVAL;
   if (!c->finalized) return fail(c, CFS_ESTATE, "diagnostics after cfs_finalize");
   if (c->sticky) return CFS_ECUDA;
-  const double dV = c->h[0] * c->h[1] * (c->ndim == 3 ? c->h[2] : 1.0);
-  int rc = cfs::launch_diagnostics(c->geo, c->phys, level_ptr(c, c->n), c->d_partial, c->diag_blocks, c->d_out, dV,
-                                   c->stream, nullptr);
-  if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "diagnostics launch");
+  const double* U = level_ptr(c, c->n);
+  int row = 0;
+  for (const Block& b : c->blocks) {
+    cfs::DiagBlock db{};
+    db.nx = b.nx; db.ny = b.ny; db.nz = b.nz; db.bN = b.N; db.bbase = b.base;
+    const double a_cd = c->p.order == 4 ? 4.0 / 3.0 : 1.0, b_cd = c->p.order == 4 ? -1.0 / 3.0 : 0.0;
+    for (int a = 0; a < 3; ++a) {
+      db.c1[a] = (a_cd / 2.0) / b.h[a];
+      db.c2[a] = (b_cd / 4.0) / b.h[a];
+    }
+    db.dV = b.h[0] * b.h[1] * (c->ndim == 3 ? b.h[2] : 1.0);
+    int rc = cfs::launch_diagnostics_block(c->geo, db, U, c->d_partial, row, c->diag_blocks, c->stream);
+    if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "diagnostics launch");
+    row += c->diag_blocks;
+  }
+  {
+    int rc = cfs::launch_diagnostics_final(c->d_partial, row, c->d_out, c->geo.N, c->stream);
+    if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "diagnostics launch");
+  }
   CUDA_TRY(c, cudaMemcpyAsync(out, c->d_out, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream), "diagnostics");
   CUDA_TRY(c, cudaStreamSynchronize(c->stream), "diagnostics");
   if (out[7] != 0.0) return fail(c, CFS_ENAN, "non-finite value in the state");
@@ -721,6 +872,7 @@ cfs_status cfs_set_halo_model(cfs_ctx* c, const float* params, const double* sca
   if (!c->finalized) return fail(c, CFS_ESTATE, "halo model after cfs_finalize");
   if (!enable) {
     c->learned = false;
+    c->graph_dirty = true;
     return CFS_OK;
   }
   if (!params || !scales) return fail(c, CFS_EINVAL, "model parameters and scales required");
@@ -754,6 +906,7 @@ cfs_status cfs_set_halo_model(cfs_ctx* c, const float* params, const double* sca
   CUDA_TRY(c, cudaStreamSynchronize(c->stream), "upload model");
   c->mlp_scales = scales_from(scales);
   c->learned = true;
+  c->graph_dirty = true;
   return CFS_OK;
 }
 
@@ -772,6 +925,7 @@ void cfs_destroy(cfs_ctx* c) {
   if (!c) return;
   if (c->finalized) cudaStreamSynchronize(c->stream);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (void* q : c->owned) c->freef(q, c->user);
   c->owned.clear();
   delete c;

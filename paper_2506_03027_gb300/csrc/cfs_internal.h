@@ -32,12 +32,17 @@ struct SubDev {
   int ex, ey, ez;     // padded ("view") box size: owned + halo G (Gz = 0 in 2-D)
   int ix, iy, iz;     // sub-domain coordinates in the decomposition grid
   long long pbase;    // offset of the padded box in the scratch arrays (points)
+  // the block the sub-domain belongs to (each block periodic in itself)
+  int bnx, bny, bnz;  // block size
+  long long bN;       // block points
+  long long bbase;    // offset of the block's state [5][bnz][bny][bnx] in a state array (doubles)
+  double c1[3], c2[3];  // CD coefficients of the block's spacing: c1 = (a/2)/h, c2 = (b/4)/h
 };
 
 // Scalars every kernel needs; passed by value.
 struct Geometry {
-  int nx, ny, nz;        // global block size
-  long long N;           // nx * ny * nz
+  int nx, ny, nz;        // size of the first block (single-block runs: the grid)
+  long long N;           // points of all blocks (a state array holds 5 N doubles)
   int nsub;              // number of sub-domains
   int G, Gz;             // halo depth in x/y and in z
   int r;                 // stencil radius (2 for CD4, 1 for CD2)
@@ -72,6 +77,13 @@ struct StepSched {
   const double* W;       // device: AT halo weights [(k * s + m) * C + l]
   const double* LH;      // device: learned stage-0 face-halo values [5][Ptot], or null (plain AT)
   const double* Wf;      // device: filter-halo extrapolation weights c(k+1) [k * C + l]
+  // CUDA-graph mode: the step index lives in device memory (dn); kernels derive n, mode, cap and
+  // the SAA table row from it, so one captured step serves every step
+  const long long* dn;
+  int at;                // 1: AT, 0: AS (for the mode derived from dn)
+  int nsub;
+  const int8_t* table_base;
+  long long Ntot;        // points of a state array (ring level stride / 5)
 };
 
 // coefficient generation (coeffs.cpp)
@@ -96,6 +108,8 @@ struct StageLaunch {
   int s;                // number of stages
   double A, B, dt;
   int first, last;      // first stage skips reading Q, last stage skips writing Q
+  int in_ring, out_ring;  // graph mode: input is ring level n / output is ring level n + 1
+  int threads;          // threads per CTA (128, 256 or 512)
   int max_pad;          // largest padded box (points)
   const int* halo;      // device: (sub-domain, padded index) pairs of every halo point
   long long nhalo;
@@ -117,6 +131,10 @@ struct FilterLaunch {
   const double* Uin;
   double* Uout;
   const double* ring;
+  int nx, ny, nz;          // the block being filtered
+  long long bN, bbase;     // its points and the offset of its state in a state array
+  int sid0;                // index of its first sub-domain
+  int in_ring, out_ring;   // graph mode: input is ring level n / output is ring level n + 1
   const int* owner[3];     // device: sub-domain index along each axis for every global coordinate
   const int* axis_off[3];  // device: per sub-domain index along the axis, its origin
   const int* axis_len[3];  // device: ... and its length
@@ -145,6 +163,8 @@ struct FusedLaunch {
   int stage;
   double A, B, dt;
   int first, last;
+  const double* ring;
+  int in_ring, out_ring;
 };
 int fused_smem_bytes(int fy);
 int launch_halo_prims(const Geometry& g, const Physics& ph, const StepSched& sc, const double* ring, const SubDev* subs,
@@ -174,7 +194,16 @@ int launch_mlp_halo(const Geometry& g, const StepSched& sc, const double* ring, 
                     long long ncol, const float* params, MlpScales sc_, double* LH, void* stream, long long* launches,
                     const Timer* tm);
 
-int launch_diagnostics(const Geometry& g, const Physics& ph, const double* U, double* partial, int nblocks,
-                       double* out, double dV, void* stream, long long* launches);
+// Diagnostics over all blocks: per block (size, state offset, CD coefficients, cell volume) the
+// block partial sums go to rows [row0, row0 + nblocks) of partial; the final pass reduces nrows.
+struct DiagBlock {
+  int nx, ny, nz;
+  long long bN, bbase;
+  double c1[3], c2[3], dV;
+};
+int launch_diagnostics_block(const Geometry& g, const DiagBlock& b, const double* U, double* partial, int row0,
+                             int nblocks, void* stream);
+int launch_diagnostics_final(const double* partial, int nrows, double* out, long long N, void* stream);
+int launch_advance_step(long long* dn, void* stream);
 
 }  // namespace cfs

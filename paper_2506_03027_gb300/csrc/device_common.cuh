@@ -35,4 +35,22 @@ __device__ __forceinline__ int face_delay(const StepSched& sc, int sid, int f) {
   return k;
 }
 
+// In graph mode the step index comes from device memory; derive what depends on it.
+__device__ __forceinline__ StepSched resolve(StepSched sc) {
+  if (sc.dn) {
+    const long long n = *sc.dn;
+    sc.n = n;
+    sc.cap = n - sc.C + 1;
+    sc.mode = (sc.algo == 0 || n < sc.C) ? 0 : (sc.at ? 1 : 2);
+    sc.table = (sc.algo == 2 && sc.table_base) ? sc.table_base + n * (long long)sc.nsub * 6 : nullptr;
+  }
+  return sc;
+}
+
+// Ring level n (plus = 0) or n + 1 (plus = 1) when flagged, otherwise the given buffer.
+__device__ __forceinline__ const double* ring_or(const double* p, int flag, const double* ring, const StepSched& sc,
+                                                 int plus) {
+  return flag ? ring + (long long)((sc.n + plus) % sc.R) * 5 * sc.Ntot : p;
+}
+
 }  // namespace cfs

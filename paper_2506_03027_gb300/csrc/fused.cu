@@ -50,6 +50,8 @@ __device__ __forceinline__ void prims32(const double* u, const Physics& ph, floa
 __global__ void __launch_bounds__(256) k_halo_prims(Geometry g, Physics ph, StepSched sc, const double* __restrict__ ring,
                                                     const SubDev* __restrict__ subs, const int2* __restrict__ halo,
                                                     long long nhalo, float* __restrict__ Wh, int s) {
+  sc = resolve(sc);
+  if (sc.mode == 0) return;  // synchronous step: no halo store is read
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nhalo) return;
   const int2 hv = halo[e];
@@ -62,13 +64,13 @@ __global__ void __launch_bounds__(256) k_halo_prims(Geometry g, Physics ph, Step
   if (ci < 0 || ci >= d.sx) kd = max(kd, face_delay(sc, sid, ci < 0 ? 0 : 1));
   if (cj < 0 || cj >= d.sy) kd = max(kd, face_delay(sc, sid, cj < 0 ? 2 : 3));
   if (ck < 0 || ck >= d.sz) kd = max(kd, face_delay(sc, sid, ck < 0 ? 4 : 5));
-  const int gx = wrapc(d.ox + ci, g.nx), gy = wrapc(d.oy + cj, g.ny), gz = wrapc(d.oz + ck, g.nz);
-  const long long gi = (long long)gx + (long long)g.nx * ((long long)gy + (long long)g.ny * gz);
+  const int gx = wrapc(d.ox + ci, d.bnx), gy = wrapc(d.oy + cj, d.bny), gz = wrapc(d.oz + ck, d.bnz);
+  const long long gi = d.bbase + (long long)gx + (long long)d.bnx * ((long long)gy + (long long)d.bny * gz);
   const long long lvN = 5 * g.N, P = g.Ptot, o = d.pbase + t;
   if (sc.mode == 2) {  // AS: the latest visible level, the same for every stage
     const double* src = ring + (long long)((sc.n - kd) % sc.R) * lvN;
     double u[5];
-    for (int v = 0; v < 5; ++v) u[v] = src[v * g.N + gi];
+    for (int v = 0; v < 5; ++v) u[v] = src[v * d.bN + gi];
     float w[7];
     prims32(u, ph, w);
     for (int c = 0; c < 7; ++c) Wh[(long long)c * P + o] = w[c];
@@ -83,7 +85,7 @@ __global__ void __launch_bounds__(256) k_halo_prims(Geometry g, Physics ph, Step
   for (int l = 0; l < sc.C; ++l) {
     const double* src = ring + (long long)((sc.n - kd - l) % sc.R) * lvN;
     double r[5];
-    for (int v = 0; v < 5; ++v) r[v] = src[v * g.N + gi];
+    for (int v = 0; v < 5; ++v) r[v] = src[v * d.bN + gi];
     const double w0 = learned ? __ldg(sc.W + (kd * s) * sc.C + l) : 0.0;
     for (int m = learned ? 1 : 0; m < s; ++m) {
       const double wl = __ldg(sc.W + (kd * s + m) * sc.C + l) - w0;
@@ -110,11 +112,15 @@ struct FusedSmem {
 
 template <int FX, int FY>
 __global__ void __launch_bounds__(FX* FY) k_stage_fused(Geometry g, Physics ph, StepSched sc,
-                                                        const double* __restrict__ Uin, double* __restrict__ Uout,
+                                                        const double* __restrict__ Uin0, double* __restrict__ Uout0,
+                                                        const double* __restrict__ ring, int in_ring, int out_ring,
                                                         double* __restrict__ Q, const SubDev* __restrict__ subs,
                                                         const int* __restrict__ work, int nwork,
                                                         const float* __restrict__ Wh, int stage, double A, double B,
                                                         double dt, int first, int last) {
+  sc = resolve(sc);
+  const double* __restrict__ Uin = ring_or(Uin0, in_ring, ring, sc, 0);
+  double* __restrict__ Uout = const_cast<double*>(ring_or(Uout0, out_ring, ring, sc, 1));
   using S = FusedSmem<FX, FY>;
   constexpr int BX = S::BX, BY = S::BY, NT = FX * FY, PL = 7 * BY * BX;
   extern __shared__ float smem[];
@@ -122,11 +128,6 @@ __global__ void __launch_bounds__(FX* FY) k_stage_fused(Geometry g, Physics ph, 
   float* sFx = smem + S::W;
   float* sFy = sFx + S::FXS;
   const int tid = threadIdx.x, tx = tid % FX, ty = tid / FX;
-  const float c1x = (float)ph.c1[0], c2x = (float)ph.c2[0], c1y = (float)ph.c1[1], c2y = (float)ph.c2[1];
-  const float c1z = (float)ph.c1[2], c2z = (float)ph.c2[2];
-  const float k1x = (float)(dt * ph.c1[0]), k2x = (float)(dt * ph.c2[0]);
-  const float k1y = (float)(dt * ph.c1[1]), k2y = (float)(dt * ph.c2[1]);
-  const float k1z = (float)(dt * ph.c1[2]), k2z = (float)(dt * ph.c2[2]);
   const float ire = (float)ph.ire, kap = (float)ph.kappa, Href = (float)ph.H_ref;
   const int hslot = (sc.mode == 2) ? 0 : stage;
 
@@ -135,6 +136,11 @@ __global__ void __launch_bounds__(FX* FY) k_stage_fused(Geometry g, Physics ph, 
     const SubDev d = subs[wk[0]];
     const int tx0 = wk[1], ty0 = wk[2];
     const int z0 = wk[3] & 0xffff, z1 = wk[3] >> 16;  // output planes [z0, z1) of the sub-domain
+    const float c1x = (float)d.c1[0], c2x = (float)d.c2[0], c1y = (float)d.c1[1], c2y = (float)d.c2[1];
+    const float c1z = (float)d.c1[2], c2z = (float)d.c2[2];
+    const float k1x = (float)(dt * d.c1[0]), k2x = (float)(dt * d.c2[0]);
+    const float k1y = (float)(dt * d.c1[1]), k2y = (float)(dt * d.c2[1]);
+    const float k1z = (float)(dt * d.c1[2]), k2z = (float)(dt * d.c2[2]);
     float phiz[5][5], rxy[3][5];
 #pragma unroll
     for (int a = 0; a < 5; ++a)
@@ -164,11 +170,11 @@ __global__ void __launch_bounds__(FX* FY) k_stage_fused(Geometry g, Physics ph, 
           float w[7];
           if (nout == 0 || sc.mode == 0 || !inview) {
             // own point, synchronous halo, or a box point no output depends on: the stage input
-            const int gx = wrapc(d.ox + lx, g.nx), gy = wrapc(d.oy + ly, g.ny), gz = wrapc(d.oz + lz, g.nz);
-            const long long gi = (long long)gx + (long long)g.nx * ((long long)gy + (long long)g.ny * gz);
+            const int gx = wrapc(d.ox + lx, d.bnx), gy = wrapc(d.oy + ly, d.bny), gz = wrapc(d.oz + lz, d.bnz);
+            const long long gi = d.bbase + (long long)gx + (long long)d.bnx * ((long long)gy + (long long)d.bny * gz);
             double u[5];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) u[v] = Uin[v * g.N + gi];
+            for (int v = 0; v < 5; ++v) u[v] = Uin[v * d.bN + gi];
             prims32(u, ph, w);
           } else {
             const long long q = (long long)(lx + g.G) + (long long)d.ex * ((long long)(ly + g.G) + (long long)d.ey * (lz + g.Gz));
@@ -188,26 +194,9 @@ __global__ void __launch_bounds__(FX* FY) k_stage_fused(Geometry g, Physics ph, 
         for (int o = 0; o < 5; ++o) pl[o] = sW + ((G - 2 + o + 10) % 5) * PL;  // planes G-2..G+2
         const bool strips = (G >= z0 && G < z1);
         float fz[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int item = 0; item < 2; ++item) {
-          int bi, bj, kind;
-          if (item == 0) {
-            bi = HB + tx; bj = HB + ty; kind = 0;
-          } else {
-            if (!strips || tid >= 4 * (FX + FY)) break;
-            int e = tid;
-            if (e < 4 * FY) {
-              const int col = e % 4, row = e / 4;
-              bi = col < 2 ? (HB - 2 + col) : (HB + FX + col - 2);
-              bj = HB + row;
-              kind = 1;
-            } else {
-              e -= 4 * FY;
-              const int col = e % FX, r4 = e / FX;
-              bj = r4 < 2 ? (HB - 2 + r4) : (HB + FY + r4 - 2);
-              bi = HB + col;
-              kind = 2;
-            }
-          }
+        // one gradient/flux evaluation at box point (bi, bj) of plane G: kind 0 tile point
+        // (Phi_x, Phi_y to shared memory, Phi_z to the queue), 1 x-strip (Phi_x), 2 y-strip (Phi_y)
+        auto point = [&](int bi, int bj, int kind) {
           const float* P0 = pl[2];
           const int q = bj * BX + bi;
           auto at = [&](const float* plane, int c, int qq) { return plane[c * BY * BX + qq]; };
@@ -255,6 +244,18 @@ __global__ void __launch_bounds__(FX* FY) k_stage_fused(Geometry g, Physics ph, 
               for (int c = 0; c < 5; ++c) fz[c] = f[c];
             }
           }
+        };
+        point(HB + tx, HB + ty, 0);
+        // strip points: 4 columns x FY rows (x strips) and 4 rows x FX columns (y strips), spread
+        // over all threads of the CTA
+        for (int e = tid; strips && e < 4 * (FX + FY); e += NT) {
+          if (e < 4 * FY) {
+            const int col = e % 4, row = e / 4;
+            point(col < 2 ? (HB - 2 + col) : (HB + FX + col - 2), HB + row, 1);
+          } else {
+            const int e2 = e - 4 * FY, col = e2 % FX, r4 = e2 / FX;
+            point(HB + col, r4 < 2 ? (HB - 2 + r4) : (HB + FY + r4 - 2), 2);
+          }
         }
         __syncthreads();
         // queues: Phi_z of planes G-4..G, dt (Dx Phi_x + Dy Phi_y) of planes G-2..G
@@ -279,16 +280,16 @@ __global__ void __launch_bounds__(FX* FY) k_stage_fused(Geometry g, Physics ph, 
         const int z = G - 2;
         const int lx = tx0 + tx, ly = ty0 + ty;
         if (z >= z0 && z < z1 && lx < d.sx && ly < d.sy) {
-          const long long gi = (long long)(d.ox + lx) + (long long)g.nx * ((long long)(d.oy + ly) + (long long)g.ny * (d.oz + z));
+          const long long gi = d.bbase + (long long)(d.ox + lx) + (long long)d.bnx * ((long long)(d.oy + ly) + (long long)d.bny * (d.oz + z));
 #pragma unroll
           for (int c = 0; c < 5; ++c) {
             float r = rxy[0][c];
             r = fmaf(k1z, phiz[3][c] - phiz[1][c], r);
             r = fmaf(k2z, phiz[4][c] - phiz[0][c], r);
             const double dtR = (double)r;
-            const double qn = first ? dtR : fma(A, Q[c * g.N + gi], dtR);
-            if (!last) Q[c * g.N + gi] = qn;
-            Uout[c * g.N + gi] = fma(B, qn, Uin[c * g.N + gi]);
+            const double qn = first ? dtR : fma(A, Q[c * d.bN + gi], dtR);
+            if (!last) Q[c * d.bN + gi] = qn;
+            Uout[c * d.bN + gi] = fma(B, qn, Uin[c * d.bN + gi]);
           }
         }
       }
@@ -326,8 +327,9 @@ static int fused_impl(const Geometry& g, const Physics& ph, const StepSched& sc,
     if (e != cudaSuccess) return (int)e;
     attr_set = true;
   }
-  k_stage_fused<FX, FY><<<a.grid, FX * FY, sm, st>>>(g, ph, sc, a.Uin, a.Uout, a.Q, a.subs, a.work, a.nwork, a.Wh,
-                                                    a.stage, a.A, a.B, a.dt, a.first, a.last);
+  k_stage_fused<FX, FY><<<a.grid, FX * FY, sm, st>>>(g, ph, sc, a.Uin, a.Uout, a.ring, a.in_ring, a.out_ring, a.Q,
+                                                    a.subs, a.work, a.nwork, a.Wh, a.stage, a.A, a.B, a.dt, a.first,
+                                                    a.last);
   return (int)cudaGetLastError();
 }
 

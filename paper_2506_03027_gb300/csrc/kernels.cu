@@ -55,18 +55,21 @@ __device__ __forceinline__ void store_prims(const Geometry& g, const Physics& ph
 
 // k_view, owned points: the stage input of the sub-domain's own points as primitives.
 template <typename T>
-__global__ void __launch_bounds__(256) k_view_own(Geometry g, Physics ph, const double* __restrict__ Uin,
+__global__ void __launch_bounds__(512) k_view_own(Geometry g, Physics ph, StepSched sc, const double* __restrict__ Uin0,
+                                                  const double* __restrict__ ring, int in_ring,
                                                   const SubDev* __restrict__ subs, T* __restrict__ Wp) {
+  sc = resolve(sc);
+  const double* Uin = ring_or(Uin0, in_ring, ring, sc, 0);
   const int sid = blockIdx.y;
   const SubDev d = subs[sid];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)d.sx * d.sy * d.sz) return;
   const int ci = (int)(t % d.sx), cj = (int)((t / d.sx) % d.sy), ck = (int)(t / ((long long)d.sx * d.sy));
-  const long long gi = (long long)(d.ox + ci) + (long long)g.nx * ((long long)(d.oy + cj) + (long long)g.ny * (d.oz + ck));
+  const long long gi = (long long)(d.ox + ci) + (long long)d.bnx * ((long long)(d.oy + cj) + (long long)d.bny * (d.oz + ck));
   const long long q = (long long)(ci + g.G) + (long long)d.ex * ((long long)(cj + g.G) + (long long)d.ey * (ck + g.Gz));
   double u[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) u[v] = Uin[v * g.N + gi];
+  for (int v = 0; v < 5; ++v) u[v] = Uin[d.bbase + v * d.bN + gi];
   store_prims<T>(g, ph, u, d.pbase + q, Wp);
 }
 
@@ -75,10 +78,12 @@ __global__ void __launch_bounds__(256) k_view_own(Geometry g, Physics ph, const 
 // that no warp mixes owned points with the AT weighting.  SA: the neighbour's live value; AT:
 // sum_l W^(m)_l(k) U^{n-k-l} in FP64 (Eq. 14-15, buffer updates of Eq. 8 collapsed); AS: U^{n-k}.
 template <typename T>
-__global__ void __launch_bounds__(256) k_view_halo(Geometry g, Physics ph, StepSched sc, const double* __restrict__ Uin,
-                                                   const double* __restrict__ ring, const SubDev* __restrict__ subs,
-                                                   const int2* __restrict__ halo, long long nhalo, T* __restrict__ Wp,
-                                                   int stage, int s) {
+__global__ void __launch_bounds__(512) k_view_halo(Geometry g, Physics ph, StepSched sc, const double* __restrict__ Uin0,
+                                                   const double* __restrict__ ring, int in_ring,
+                                                   const SubDev* __restrict__ subs, const int2* __restrict__ halo,
+                                                   long long nhalo, T* __restrict__ Wp, int stage, int s) {
+  sc = resolve(sc);
+  const double* Uin = ring_or(Uin0, in_ring, ring, sc, 0);
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nhalo) return;
   const int2 e = halo[t];
@@ -87,12 +92,12 @@ __global__ void __launch_bounds__(256) k_view_halo(Geometry g, Physics ph, StepS
   const SubDev d = subs[sid];
   const int i = (int)(q % d.ex), j = (int)((q / d.ex) % d.ey), k = (int)(q / ((long long)d.ex * d.ey));
   const int ci = i - g.G, cj = j - g.G, ck = k - g.Gz;
-  const int gx = wrapc(d.ox + ci, g.nx), gy = wrapc(d.oy + cj, g.ny), gz = wrapc(d.oz + ck, g.nz);
-  const long long gi = (long long)gx + (long long)g.nx * ((long long)gy + (long long)g.ny * gz);
+  const int gx = wrapc(d.ox + ci, d.bnx), gy = wrapc(d.oy + cj, d.bny), gz = wrapc(d.oz + ck, d.bnz);
+  const long long gi = d.bbase + (long long)gx + (long long)d.bnx * ((long long)gy + (long long)d.bny * gz);
   double u[5];
   if (sc.mode == 0) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) u[v] = Uin[v * g.N + gi];
+    for (int v = 0; v < 5; ++v) u[v] = Uin[v * d.bN + gi];
   } else {
     int kd = 0;
     if (ci < 0 || ci >= d.sx) kd = max(kd, face_delay(sc, sid, ci < 0 ? 0 : 1));
@@ -102,7 +107,7 @@ __global__ void __launch_bounds__(256) k_view_halo(Geometry g, Physics ph, StepS
     if (sc.mode == 2) {
       const double* src = ring + (long long)((sc.n - kd) % sc.R) * lvN;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) u[v] = src[v * g.N + gi];
+      for (int v = 0; v < 5; ++v) u[v] = src[v * d.bN + gi];
     } else {
       const double* w = sc.W + (kd * s + stage) * sc.C;
       const bool face = (int)(ci < 0 || ci >= d.sx) + (int)(cj < 0 || cj >= d.sy) + (int)(ck < 0 || ck >= d.sz) == 1;
@@ -117,7 +122,7 @@ __global__ void __launch_bounds__(256) k_view_halo(Geometry g, Physics ph, StepS
             const double* src = ring + (long long)((sc.n - kd - l) % sc.R) * lvN;
             const double wl = __ldg(w + l) - __ldg(w0 + l);
 #pragma unroll
-            for (int v = 0; v < 5; ++v) u[v] = fma(wl, src[v * g.N + gi], u[v]);
+            for (int v = 0; v < 5; ++v) u[v] = fma(wl, src[v * d.bN + gi], u[v]);
           }
       } else {
 #pragma unroll
@@ -126,7 +131,7 @@ __global__ void __launch_bounds__(256) k_view_halo(Geometry g, Physics ph, StepS
           const double* src = ring + (long long)((sc.n - kd - l) % sc.R) * lvN;
           const double wl = __ldg(w + l);
 #pragma unroll
-          for (int v = 0; v < 5; ++v) u[v] = fma(wl, src[v * g.N + gi], u[v]);
+          for (int v = 0; v < 5; ++v) u[v] = fma(wl, src[v * d.bN + gi], u[v]);
         }
       }
     }
@@ -144,7 +149,7 @@ __device__ __forceinline__ T cdiff(const T* __restrict__ f, long long q, long lo
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_flux(Geometry g, Physics ph, const SubDev* __restrict__ subs,
+__global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubDev* __restrict__ subs,
                                               const T* __restrict__ Wp, T* __restrict__ Phi) {
   const int sid = blockIdx.y;
   const SubDev d = subs[sid];
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(256) k_flux(Geometry g, Physics ph, const SubD
   if (g.viscous) {
     const long long st[3] = {1, sty, stz};
     for (int b = 0; b < g.ndim; ++b) {
-      const T c1 = (T)ph.c1[b], c2 = (T)ph.c2[b];
+      const T c1 = (T)d.c1[b], c2 = (T)d.c2[b];
       du[0][b] = cdiff(W + P, q, st[b], c1, c2, r);
       du[1][b] = cdiff(W + 2 * P, q, st[b], c1, c2, r);
       du[2][b] = cdiff(W + 3 * P, q, st[b], c1, c2, r);
@@ -223,10 +228,14 @@ __global__ void __launch_bounds__(256) k_flux(Geometry g, Physics ph, const SubD
 // ------------------------------------------------------------------------------- k_rk
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_rk(Geometry g, Physics ph, const SubDev* __restrict__ subs,
-                                            const T* __restrict__ Phi, const double* __restrict__ Uin,
-                                            double* __restrict__ Uout, double* __restrict__ Q, double A, double B,
-                                            double dt, int first, int last) {
+__global__ void __launch_bounds__(512) k_rk(Geometry g, Physics ph, StepSched sc, const SubDev* __restrict__ subs,
+                                            const T* __restrict__ Phi, const double* __restrict__ Uin0,
+                                            double* __restrict__ Uout0, const double* __restrict__ ring, int in_ring,
+                                            int out_ring, double* __restrict__ Q, double A, double B, double dt,
+                                            int first, int last) {
+  sc = resolve(sc);
+  const double* Uin = ring_or(Uin0, in_ring, ring, sc, 0);
+  double* Uout = const_cast<double*>(ring_or(Uout0, out_ring, ring, sc, 1));
   const int sid = blockIdx.y;
   const SubDev d = subs[sid];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -234,7 +243,7 @@ __global__ void __launch_bounds__(256) k_rk(Geometry g, Physics ph, const SubDev
   const int ci = (int)(t % d.sx), cj = (int)((t / d.sx) % d.sy), ck = (int)(t / ((long long)d.sx * d.sy));
   const long long sty = d.ex, stz = (long long)d.ex * d.ey;
   const long long q = (long long)(ci + g.G) + sty * (cj + g.G) + stz * (ck + g.Gz);
-  const long long gi = (long long)(d.ox + ci) + (long long)g.nx * ((long long)(d.oy + cj) + (long long)g.ny * (d.oz + ck));
+  const long long gi = d.bbase + (long long)(d.ox + ci) + (long long)d.bnx * ((long long)(d.oy + cj) + (long long)d.bny * (d.oz + ck));
   const long long P = g.Ptot;
   const T* F = Phi + d.pbase;
   const long long st[3] = {1, sty, stz};
@@ -242,8 +251,8 @@ __global__ void __launch_bounds__(256) k_rk(Geometry g, Physics ph, const SubDev
   T k1[3], k2[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    k1[a] = (T)(dt * ph.c1[a]);
-    k2[a] = (T)(dt * ph.c2[a]);
+    k1[a] = (T)(dt * d.c1[a]);
+    k2[a] = (T)(dt * d.c2[a]);
   }
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
@@ -256,9 +265,9 @@ __global__ void __launch_bounds__(256) k_rk(Geometry g, Physics ph, const SubDev
       if (g.r == 2) acc = fma(k2[a], Fa[q + 2 * st[a]] - Fa[q - 2 * st[a]], acc);
     }
     const double dtR = (double)acc;
-    const double qn = first ? dtR : fma(A, Q[c * g.N + gi], dtR);
-    if (!last) Q[c * g.N + gi] = qn;
-    Uout[c * g.N + gi] = fma(B, qn, Uin[c * g.N + gi]);
+    const double qn = first ? dtR : fma(A, Q[c * d.bN + gi], dtR);
+    if (!last) Q[c * d.bN + gi] = qn;
+    Uout[c * d.bN + gi] = fma(B, qn, Uin[c * d.bN + gi]);
   }
 }
 
@@ -274,15 +283,15 @@ static inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) 
 template <typename T>
 static int stage_impl(const Geometry& g, const Physics& ph, const StepSched& sc, const StageLaunch& a,
                       cudaStream_t st, long long* launches, const Timer* tm) {
-  const int B = 256;
+  const int B = (a.threads == 128 || a.threads == 512) ? a.threads : 256;
   dim3 gf(nblk(a.max_flux, B), g.nsub), gr(nblk(a.max_own, B), g.nsub);
-  TIMED(tm, 0, (k_view_own<T><<<gr, B, 0, st>>>(g, ph, a.Uin, a.subs, (T*)a.Wp)));
+  TIMED(tm, 0, (k_view_own<T><<<gr, B, 0, st>>>(g, ph, sc, a.Uin, a.ring, a.in_ring, a.subs, (T*)a.Wp)));
   if (a.nhalo > 0)
-    TIMED(tm, 0, (k_view_halo<T><<<nblk(a.nhalo, B), B, 0, st>>>(g, ph, sc, a.Uin, a.ring, a.subs, (const int2*)a.halo,
-                                                                 a.nhalo, (T*)a.Wp, a.stage, a.s)));
+    TIMED(tm, 0, (k_view_halo<T><<<nblk(a.nhalo, B), B, 0, st>>>(g, ph, sc, a.Uin, a.ring, a.in_ring, a.subs,
+                                                                 (const int2*)a.halo, a.nhalo, (T*)a.Wp, a.stage, a.s)));
   TIMED(tm, 1, (k_flux<T><<<gf, B, 0, st>>>(g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
-  TIMED(tm, 2, (k_rk<T><<<gr, B, 0, st>>>(g, ph, a.subs, (const T*)a.Phi, a.Uin, a.Uout, a.Q, a.A, a.B, a.dt,
-                                          a.first, a.last)));
+  TIMED(tm, 2, (k_rk<T><<<gr, B, 0, st>>>(g, ph, sc, a.subs, (const T*)a.Phi, a.Uin, a.Uout, a.ring, a.in_ring,
+                                          a.out_ring, a.Q, a.A, a.B, a.dt, a.first, a.last)));
   if (launches) *launches += a.nhalo > 0 ? 4 : 3;
   return (int)cudaGetLastError();
 }
@@ -302,10 +311,13 @@ int launch_stage(const Geometry& g, const Physics& ph, const StepSched& sc, cons
 // the intermediate values in the output line, back substitution overwrites them.
 template <typename T>
 __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, FilterLaunch f, int axis) {
+  sc = resolve(sc);
+  f.Uin = ring_or(f.Uin, f.in_ring, f.ring, sc, 0);
+  f.Uout = const_cast<double*>(ring_or(f.Uout, f.out_ring, f.ring, sc, 1));
   const int f1 = (axis == 0) ? 1 : 0;
   const int f2 = (axis == 2) ? 1 : 2;
-  const int n[3] = {g.nx, g.ny, g.nz};
-  const long long strides[3] = {1, g.nx, (long long)g.nx * g.ny};
+  const int n[3] = {f.nx, f.ny, f.nz};
+  const long long strides[3] = {1, f.nx, (long long)f.nx * f.ny};
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long total = 5LL * f.P[axis] * n[f1] * n[f2];
   if (t >= total) return;
@@ -318,10 +330,10 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
   sidx[axis] = seg;
   sidx[f1] = f.owner[f1][t1];
   sidx[f2] = f.owner[f2][t2];
-  const int sid = sidx[0] + f.P[0] * (sidx[1] + f.P[1] * sidx[2]);
+  const int sid = f.sid0 + sidx[0] + f.P[0] * (sidx[1] + f.P[1] * sidx[2]);
   const int off = f.axis_off[axis][seg], len = f.axis_len[axis][seg];
   const long long st = strides[axis];
-  const long long base = (long long)var * g.N + (long long)t1 * strides[f1] + (long long)t2 * strides[f2];
+  const long long base = f.bbase + (long long)var * f.bN + (long long)t1 * strides[f1] + (long long)t2 * strides[f2];
   const double* Uin = f.Uin;
   const int kl = (sc.mode == 0) ? 0 : face_delay(sc, sid, 2 * axis);
   const int kr = (sc.mode == 0) ? 0 : face_delay(sc, sid, 2 * axis + 1);
@@ -405,7 +417,7 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
 
 int launch_filter(const Geometry& g, const StepSched& sc, const FilterLaunch& f, int axis, int precision,
                   void* stream, long long* launches, const Timer* tm) {
-  const int n[3] = {g.nx, g.ny, g.nz};
+  const int n[3] = {f.nx, f.ny, f.nz};
   const int f1 = (axis == 0) ? 1 : 0;
   const int f2 = (axis == 2) ? 1 : 2;
   const long long total = 5LL * f.P[axis] * n[f1] * n[f2];
@@ -418,22 +430,22 @@ int launch_filter(const Geometry& g, const StepSched& sc, const FilterLaunch& f,
 
 // ------------------------------------------------------------------------------- diagnostics
 
-// Velocity component c at global (x, y, z) with periodic wrap.
-__device__ __forceinline__ double vel_at(const double* U, const Geometry& g, int x, int y, int z, int c) {
-  const long long gi = (long long)wrapc(x, g.nx) + (long long)g.nx * ((long long)wrapc(y, g.ny) + (long long)g.ny * wrapc(z, g.nz));
-  return U[(1 + c) * g.N + gi] / U[gi];
+// Velocity component c at (x, y, z) of a block with periodic wrap.
+__device__ __forceinline__ double vel_at(const double* U, const DiagBlock& b, int x, int y, int z, int c) {
+  const long long gi = b.bbase + (long long)wrapc(x, b.nx) + (long long)b.nx * ((long long)wrapc(y, b.ny) + (long long)b.ny * wrapc(z, b.nz));
+  return U[(1 + c) * b.bN + gi] / U[gi];
 }
 
-__global__ void __launch_bounds__(256) k_diag(Geometry g, Physics ph, const double* __restrict__ U,
-                                              double* __restrict__ partial, double dV) {
+__global__ void __launch_bounds__(256) k_diag(DiagBlock b, const double* __restrict__ U, double* __restrict__ partial) {
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(i % g.nx), y = (int)((i / g.nx) % g.ny), z = (int)(i / ((long long)g.nx * g.ny));
+  const int ndim = b.nz > 1 ? 3 : 2;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < b.bN; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % b.nx), y = (int)((i / b.nx) % b.ny), z = (int)(i / ((long long)b.nx * b.ny));
     double u[5];
     for (int v = 0; v < 5; ++v) {
-      u[v] = U[v * g.N + i];
+      u[v] = U[b.bbase + v * b.bN + i];
       if (!isfinite(u[v])) acc[7] = 1.0;
-      acc[2 + v] += u[v] * dV;
+      acc[2 + v] += u[v] * b.dV;
     }
     const double rho = u[0];
     const double vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
@@ -442,12 +454,12 @@ __global__ void __launch_bounds__(256) k_diag(Geometry g, Physics ph, const doub
     double dv[3][3];
     for (int c = 0; c < 3; ++c)
       for (int a = 0; a < 3; ++a) {
-        if (a >= g.ndim) { dv[c][a] = 0.0; continue; }
+        if (a >= ndim) { dv[c][a] = 0.0; continue; }
         const int ex = a == 0, ey = a == 1, ez = a == 2;
-        double dd = ph.c1[a] * (vel_at(U, g, x + ex, y + ey, z + ez, c) - vel_at(U, g, x - ex, y - ey, z - ez, c));
-        if (g.r == 2)
-          dd += ph.c2[a] * (vel_at(U, g, x + 2 * ex, y + 2 * ey, z + 2 * ez, c) -
-                            vel_at(U, g, x - 2 * ex, y - 2 * ey, z - 2 * ez, c));
+        double dd = b.c1[a] * (vel_at(U, b, x + ex, y + ey, z + ez, c) - vel_at(U, b, x - ex, y - ey, z - ez, c));
+        if (b.c2[a] != 0.0)
+          dd += b.c2[a] * (vel_at(U, b, x + 2 * ex, y + 2 * ey, z + 2 * ez, c) -
+                           vel_at(U, b, x - 2 * ex, y - 2 * ey, z - 2 * ez, c));
         dv[c][a] = dd;
       }
     const double wx = dv[2][1] - dv[1][2], wy = dv[0][2] - dv[2][0], wz = dv[1][0] - dv[0][1];
@@ -467,7 +479,7 @@ __global__ void __launch_bounds__(256) k_diag(Geometry g, Physics ph, const doub
   __syncthreads();
   if (threadIdx.x < 8) {
     const int c = threadIdx.x;
-    double v = (c == 7) ? 0.0 : 0.0;
+    double v = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = (c == 7) ? fmax(v, sh[c][w]) : v + sh[c][w];
     partial[(long long)blockIdx.x * 8 + c] = v;
   }
@@ -483,12 +495,23 @@ __global__ void k_diag_final(const double* __restrict__ partial, int nblocks, do
   out[c] = v;
 }
 
-int launch_diagnostics(const Geometry& g, const Physics& ph, const double* U, double* partial, int nblocks,
-                       double* out, double dV, void* stream, long long* launches) {
-  cudaStream_t st = (cudaStream_t)stream;
-  k_diag<<<nblocks, 256, 0, st>>>(g, ph, U, partial, dV);
-  k_diag_final<<<1, 32, 0, st>>>(partial, nblocks, out, g.N);
-  if (launches) *launches += 2;
+int launch_diagnostics_block(const Geometry& g, const DiagBlock& b, const double* U, double* partial, int row0,
+                             int nblocks, void* stream) {
+  k_diag<<<nblocks, 256, 0, (cudaStream_t)stream>>>(b, U, partial + (long long)row0 * 8);
+  return (int)cudaGetLastError();
+}
+
+__global__ void k_advance_step(long long* dn) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *dn += 1;
+}
+
+int launch_advance_step(long long* dn, void* stream) {
+  k_advance_step<<<1, 32, 0, (cudaStream_t)stream>>>(dn);
+  return (int)cudaGetLastError();
+}
+
+int launch_diagnostics_final(const double* partial, int nrows, double* out, long long N, void* stream) {
+  k_diag_final<<<1, 32, 0, (cudaStream_t)stream>>>(partial, nrows, out, N);
   return (int)cudaGetLastError();
 }
 

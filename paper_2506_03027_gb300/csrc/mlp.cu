@@ -258,9 +258,10 @@ __device__ __forceinline__ void column_point(const SubDev& d, int f, int t1, int
   else c[a] = side == 0 ? j - 1 : sz[a] - j;
 }
 
+// index within a state array: the block's offset plus the wrapped point of the block (variable 0)
 __device__ __forceinline__ long long global_index(const Geometry& g, const SubDev& d, const int c[3]) {
-  const int gx = wrapc(d.ox + c[0], g.nx), gy = wrapc(d.oy + c[1], g.ny), gz = wrapc(d.oz + c[2], g.nz);
-  return (long long)gx + (long long)g.nx * ((long long)gy + (long long)g.ny * gz);
+  const int gx = wrapc(d.ox + c[0], d.bnx), gy = wrapc(d.oy + c[1], d.bny), gz = wrapc(d.oz + c[2], d.bnz);
+  return d.bbase + (long long)gx + (long long)d.bnx * ((long long)gy + (long long)d.bny * gz);
 }
 
 __device__ __forceinline__ float bf16r(double x) { return __bfloat162float(__float2bfloat16_rn((float)x)); }
@@ -281,12 +282,12 @@ __device__ __forceinline__ void column_depth(const Geometry& g, const StepSched&
   const double* Lk2 = ring + (long long)((sc.n - k - 2) % sc.R) * lvN;
   const double* Ln = ring + (long long)(sc.n % sc.R) * lvN;
   for (int v = 0; v < 5; ++v) {
-    const double a = Lk0[v * g.N + gh], b = Lk1[v * g.N + gh], cc = Lk2[v * g.N + gh];
+    const double a = Lk0[v * d.bN + gh], b = Lk1[v * d.bN + gh], cc = Lk2[v * d.bN + gh];
     xrow[(j - 1) * 5 + v] = bf16r((a - b) * ms.in[v]);
     xrow[MLP_HDEPTH * 5 + (j - 1) * 5 + v] = bf16r((b - cc) * ms.in[v]);
-    xrow[2 * MLP_HDEPTH * 5 + (j - 1) * 5 + v] = bf16r((Ln[v * g.N + go] - Lk0[v * g.N + go]) * ms.own[v]);
+    xrow[2 * MLP_HDEPTH * 5 + (j - 1) * 5 + v] = bf16r((Ln[v * d.bN + go] - Lk0[v * d.bN + go]) * ms.own[v]);
     at3[(j - 1) * 5 + v] = fma(at3w[0], a, fma(at3w[1], b, at3w[2] * cc));
-    if (truth) truth[(j - 1) * 5 + v] = Ln[v * g.N + gh];
+    if (truth) truth[(j - 1) * 5 + v] = Ln[v * d.bN + gh];
   }
 }
 
@@ -320,6 +321,8 @@ __global__ void __launch_bounds__(NT) k_mlp_halo(Geometry g, StepSched sc, const
                                                   const SubDev* __restrict__ subs, const int* __restrict__ cols,
                                                   long long ncol, const float* __restrict__ params, MlpScales ms,
                                                   At3Table t3, double* __restrict__ LH) {
+  sc = resolve(sc);
+  if (sc.mode != 1) return;  // the network replaces AT halos only
   extern __shared__ __align__(16) unsigned char raw[];
   Smem& sm = *reinterpret_cast<Smem*>(raw);
   __shared__ double s_at3[S][MLP_NOUT];

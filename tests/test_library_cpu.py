@@ -88,8 +88,11 @@ def test_call_order_and_block_validation(lib):
             cfs.cfs_add_block(ctx, 0, 4, 4, (1.0, 1.0, 1.0))
         assert e.value.status == cfs.CFS_EINVAL
         assert cfs.cfs_add_block(ctx, 16, 16, 1, (0.1, 0.1, 1.0)) == 0
+        assert cfs.cfs_add_block(ctx, 12, 20, 1, (0.1, 0.1, 1.0)) == 1  # batches of blocks
         with pytest.raises(cfs.CfsError):
-            cfs.cfs_add_block(ctx, 16, 16, 1, (0.1, 0.1, 1.0))  # one block in this version
+            cfs.cfs_add_block(ctx, 16, 16, 8, (0.1, 0.1, 0.1))  # 2-D and 3-D blocks do not mix
+        with pytest.raises(cfs.CfsError):
+            cfs.cfs_split_block(ctx, 2, 1, 1, 1)  # unknown block
         with pytest.raises(cfs.CfsError):
             cfs.cfs_split_block(ctx, 0, 17, 1, 1)
         with pytest.raises(cfs.CfsError):

@@ -185,3 +185,71 @@ def test_fp32_intermediates_error_is_small(algo):
     print(f"FP32-intermediate form, {algo}, 24 steps: relative L2 per variable {e}")
     assert np.all(np.isfinite(Ug))
     assert np.all(e < 1e-6), e
+
+
+def test_batched_uneven_blocks_parity():
+    """Three independent periodic blocks of uneven sizes and splits advance together (one launch
+    per kernel over the sub-domains of all blocks); each block equals its own oracle run, with the
+    SAA delays of its sub-domains."""
+    base = I.tgv_case(20, 2, "SAA", kmax=2)
+    blocks = [base.replace(nx=20, ny=18, nz=16, px=2, py=2, pz=2),
+              base.replace(nx=26, ny=20, nz=22, px=3, py=2, pz=2, lx=3.0, ly=2.5, lz=2.0),
+              base.replace(nx=16, ny=16, nz=24, px=1, py=1, pz=3, lz=4.0)]
+    dt = min(I.cfl_dt(b, I.tgv_state(b), 0.1) for b in blocks)
+    blocks = [b.replace(dt=dt) for b in blocks]
+    nsteps = 14
+    nsub = sum(b.nsub for b in blocks)
+    d = I.saa_delays(blocks[0].replace(px=nsub, py=1, pz=1), nsteps)
+    s = cfs.Solver(blocks[0], blocks=blocks)
+    s.set_schedule(delays=d)
+    for i, b in enumerate(blocks):
+        s.set_state(I.tgv_state(b), block=i)
+    s.step(nsteps)
+    sid0 = 0
+    for i, b in enumerate(blocks):
+        Ug = s.get_state(block=i)
+        Uo = orc.run(b, I.tgv_state(b), nsteps, delays=np.ascontiguousarray(d[:, sid0:sid0 + b.nsub, :]))
+        check(Ug, Uo)
+        sid0 += b.nsub
+    s.close()
+
+
+@pytest.mark.parametrize("precision,learned", [(0, False), (1, False), (0, True)])
+def test_graph_mode_is_bitwise_identical(precision, learned):
+    """Replaying one captured step (step counter in device memory) gives exactly the results of
+    launching the kernels step by step, across the synchronous warm-up into SAA-AT steps."""
+    import torch
+    c = small_tgv("SAA", n=26, p=2, kmax=3, cfl=0.05)
+    d = I.saa_delays(c, 12)
+    out = []
+    for graph in (False, True):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            s = cfs.Solver(c, precision=precision, graph=graph, stream=stream, max_delay=4 if learned else None)
+            s.set_schedule(delays=d)
+            if learned:
+                from paper_2506_03027_gb300 import learned as L
+                scales = np.array([3e3, 2e3, 2e3, 2e3, 1e3, 4e2, 3e2, 3e2, 3e2, 2e2, 1e7, 1e6, 1e6, 1e6, 5e5])
+                cfs.cfs_set_halo_model(s.ctx, L.init_params(1), scales)
+            s.set_state(I.tgv_state(c))
+            s.step(7)
+            s.step(5)
+            out.append(s.get_state())
+            s.close()
+        torch.cuda.synchronize()
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("precision,tiles", [(1, (4, 8, 256)), (1, (16, 32, 256)), (0, (8, 16, 128)), (0, (8, 16, 512))])
+def test_launch_shapes_do_not_change_results(precision, tiles):
+    c = small_tgv("SAA", n=34, p=2, kmax=2, cfl=0.05)
+    d = I.saa_delays(c, 9)
+    res = []
+    for t in ((8, 16, 256), tiles):
+        s = cfs.Solver(c, precision=precision, tiles=t)
+        s.set_schedule(delays=d)
+        s.set_state(I.tgv_state(c))
+        s.step(9)
+        res.append(s.get_state())
+        s.close()
+    np.testing.assert_array_equal(res[0], res[1])
