@@ -181,6 +181,24 @@ def algorithmic_bytes_per_step(case):
     return stage + filt + ring
 
 
+def fused_roofline(case, ktimes):
+    """HBM roofline of the fused FP32-intermediate stage kernel (one launch per RK stage):
+    algorithmic bytes per launch = the FP64 state and LSERK register traffic (144 B per point,
+    averaged over the 5 stages) plus the FP32 halo primitives it reads from the per-step halo
+    store (7 x 4 B per face-halo point), over the event-timed average launch."""
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", HBM_GBS_FALLBACK)
+    t, n = ktimes.get("stage_update", (0.0, 0))
+    if not n:
+        return None
+    per_launch_s = t / n * 1e-3
+    bytes_ = case.npts * (120 + 160 * (case.stages - 2) + 120) / case.stages + face_points(case, 4) * 28
+    achieved = bytes_ / per_launch_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "bytes_per_launch": bytes_, "ms_per_launch": t / n,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2506_03027_gb300 import build as B
@@ -260,7 +278,9 @@ def run_ours(args, rank, world, local_rank):
     # ---------------- precision form (FP32 intermediates), same steps, error vs the FP64 path
     forms = None
     if args.precision == 0 and not args.no_forms:
-        s32 = cfs.Solver(case, precision=1)
+        from paper_2506_03027_gb300 import autotune
+        tiles32 = autotune.tune(case, precision=1, use_cache=False)
+        s32 = cfs.Solver(case, precision=1, tiles=tiles32)
         s32.set_schedule(delays=delays)
         s32.set_state(U0)
         s32.step(W)
@@ -284,12 +304,18 @@ def run_ours(args, rank, world, local_rank):
         forms = {"fp32_intermediates": {"value": n_units / (ms32 * 1e-3) / 1e6, "unit": UNIT,
                                         "speedup_vs_fp64": ms / ms32,
                                         "rel_l2_vs_fp64_path": err, "after_steps": n_done,
-                                        "per_kernel_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in kt32.items() if v[1]}}}
+                                        "tiles_autotuned": list(tiles32),
+                                        "per_kernel_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in kt32.items() if v[1]},
+                                        "fused_stage_roofline": fused_roofline(case, kt32)}}
+
+    if args.precision == 0 and not args.no_forms and world == 1:
+        forms["fp32_intermediates_256"] = precision_form_256(args)
 
     # ---------------- batched uneven blocks (one launch per kernel over all blocks, CUDA graph)
     if args.precision == 0 and not args.no_forms and world == 1:
         forms = forms or {}
-        forms["batched_blocks"] = batched_form(args, stream)
+        forms["batched_blocks"] = batched_form(args, 0)
+        forms["batched_blocks_fp32_intermediates"] = batched_form(args, 1)
 
     # ---------------- learned halo predictor (trained here on synchronous-run halos)
     if args.precision == 0 and not args.no_forms and not args.no_learned and world == 1:
@@ -363,18 +389,24 @@ def batched_blocks():
     return [b.replace(dt=dt) for b in blocks]
 
 
-def batched_form(args, stream_unused):
+def batched_form(args, precision=0):
+    """All 12 blocks advance together: every kernel launch covers the sub-domains of all blocks
+    (work lists over (block, sub-domain, tile)); the FP32-intermediate form runs one persistent
+    fused launch per RK stage.  The step is captured once in a CUDA graph and replayed; launch
+    shapes come from the autotuner."""
     import torch
+    from paper_2506_03027_gb300 import autotune
     from paper_2506_03027_gb300 import cfs
     from paper_2506_03027_gb300 import inputs as I
     blocks = batched_blocks()
+    tiles = autotune.tune(blocks[0], precision=precision, blocks=blocks, use_cache=False)
     npts = sum(b.npts for b in blocks)
     nsub = sum(b.nsub for b in blocks)
     K, W = max(3, args.steps // 4), args.warmup
     delays = I.saa_delays(blocks[0].replace(px=nsub, py=1, pz=1), W + K)
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
-        s = cfs.Solver(blocks[0], blocks=blocks, graph=True, stream=st)
+        s = cfs.Solver(blocks[0], blocks=blocks, graph=True, stream=st, precision=precision, tiles=tiles)
         s.set_schedule(delays=delays)
         for i, b in enumerate(blocks):
             s.set_state(I.tgv_state(b), block=i)
@@ -391,7 +423,67 @@ def batched_form(args, stream_unused):
         s.close()
     return {"value": npts * 5 * K / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms / K, "points": npts,
             "blocks": len(blocks), "subdomains": nsub, "cuda_graph": True, "launches_per_step": launches / K,
-            "workload": "12 independent periodic NS blocks with the 12-block airfoil C-grid sizes, SAA 0..2, FP64"}
+            "tiles_autotuned": list(tiles),
+            "workload": "12 independent periodic NS blocks with the 12-block airfoil C-grid sizes, SAA 0..2, "
+                        + ("FP64" if precision == 0 else "FP32 intermediates (one fused launch per RK stage)")}
+
+
+def precision_form_256(args):
+    """The precision configuration: TGV 256^3 with 8^3 sub-domains, CAA L = 4 (CFL 0.25), FP32
+    derivative/flux/filter intermediates against the FP64 path from the same initial state:
+    relative L2 error per conserved variable after `nst` steps, error of the kinetic-energy
+    dissipation rate -dK/dt (central differences of the per-step K history), and throughput of
+    both paths."""
+    import torch
+    from paper_2506_03027_gb300 import cfs
+    from paper_2506_03027_gb300 import inputs as I
+    case = I.tgv_case(256, 8, "CAA")
+    case = case.replace(dt=I.cfl_dt(case, I.tgv_state(case), 0.25))
+    U0 = I.tgv_state(case)
+    nst, K, W = 40, 10, 4
+    from paper_2506_03027_gb300 import autotune
+    tiles = {0: None, 1: autotune.tune(case, precision=1, use_cache=False)}
+    res = {}
+    for prec in (0, 1):
+        s = cfs.Solver(case, precision=prec, tiles=tiles[prec])
+        cfs.cfs_set_timing(s.ctx, True)
+        s.set_schedule()
+        s.set_state(U0)
+        s.step(W)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.step(K)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        kt = cfs.cfs_get_timing(s.ctx)
+        cfs.cfs_set_timing(s.ctx, False)
+        s.set_step(0)
+        s.set_state(U0)
+        ke = [s.diagnostics()[0]]
+        for _ in range(nst):
+            s.step(1)
+            ke.append(s.diagnostics()[0])
+        res[prec] = {"ms": ms, "U": s.get_state(), "K": np.array(ke), "kt": kt}
+        s.close()
+    U64, U32 = res[0]["U"], res[1]["U"]
+    mom = math.sqrt(sum(float(np.linalg.norm(U64[v])) ** 2 for v in (1, 2, 3)))
+    err = [float(np.linalg.norm(U32[v] - U64[v]) / (mom if v in (1, 2, 3) else np.linalg.norm(U64[v])))
+           for v in range(5)]
+    eps64 = -(res[0]["K"][2:] - res[0]["K"][:-2]) / (2 * case.dt)
+    eps32 = -(res[1]["K"][2:] - res[1]["K"][:-2]) / (2 * case.dt)
+    return {"value": case.npts * 5 / (res[1]["ms"] * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": res[1]["ms"],
+            "fp64_path": {"value": case.npts * 5 / (res[0]["ms"] * 1e-3) / 1e6, "ms_per_step": res[0]["ms"]},
+            "speedup_vs_fp64": res[0]["ms"] / res[1]["ms"],
+            "rel_l2_vs_fp64_path": err, "after_steps": nst,
+            "dissipation_rate_rel_err": float(np.abs(eps32 - eps64).max() / np.abs(eps64).max()),
+            "tiles_autotuned": list(tiles[1]),
+            "per_kernel_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in res[1]["kt"].items() if v[1]},
+            "fused_stage_roofline": fused_roofline(case, res[1]["kt"]),
+            "workload": "TGV NS 256^3, 8x8x8 sub-domains, CAA L=4 AT4 at CFL 0.25, filter alpha_f 0.499; "
+                        "error against the FP64 path from the same initial state"}
 
 
 def learned_form(args):

@@ -79,6 +79,22 @@ cfs_status cfs_set_allocator(cfs_ctx* ctx, cfs_alloc_fn alloc, cfs_free_fn free_
  * 3-D.  EINVAL for non-positive sizes or mixed dimensionality. */
 cfs_status cfs_add_block(cfs_ctx* ctx, int ni, int nj, int nk, const double* spacing, int* block_id);
 
+/* Make block `block` curvilinear (App. A: Eq. A1 in strong conservation form on general
+ * coordinates, fluxes of Eq. A2 with contravariant velocities, viscous terms of Eq. A3-A4 with
+ * the chain rule through the metric terms).  The grid is a smooth mapping of the index plane
+ * (i, j) extruded along z: xy is a HOST array [2][nj][ni] with x(i, j) then y(i, j); z = k dz
+ * with dz the block's third spacing (unit depth in 2-D).  The block stays periodic in every
+ * index direction: shift[0..1] is the (x, y) jump of the coordinates across the wrap in i,
+ * shift[2..3] the jump across the wrap in j (for example (Lx, 0, 0, Ly) for a deformed
+ * rectangle).  At cfs_finalize the library computes the metric terms xi^_x = J^-1 dxi/dx ...
+ * and J from the coordinates with the block's own CD scheme in index space (their cofactor
+ * form keeps a uniform flow uniform to rounding); derivatives of the solution are then taken
+ * in index space.  The data are copied.  Call after cfs_add_block, before cfs_finalize
+ * (ESTATE otherwise); EINVAL for an unknown block, null pointers or non-finite values, and at
+ * cfs_finalize for a grid with a non-positive cell volume.  The FP32-intermediate precision runs
+ * curvilinear blocks through the multi-kernel stage (the fused stage is Cartesian only). */
+cfs_status cfs_set_block_grid(cfs_ctx* ctx, int block, const double* xy, const double* shift);
+
 /* Decompose a block into pi x pj x pk sub-domains (the paper's PEs, Sec. 3); sub-domains are
  * numbered block after block, x fastest within a block.  Along each axis
  * n points split into p parts as evenly as possible, the first n mod p parts one point longer.

@@ -7,8 +7,12 @@
  * table or constant generator with the CUDA library; the two meet only through seeded inputs.
  *
  * What it computes (in the paper's order):
- *   - Eq. 1 / App. A: compressible Navier-Stokes right-hand side on a uniform Cartesian periodic
- *     grid (metric terms reduce to 1/dx), inviscid fluxes Eq. A2, viscous fluxes Eq. A3-A4.
+ *   - Eq. 1 / App. A: compressible Navier-Stokes right-hand side, inviscid fluxes Eq. A2,
+ *     viscous fluxes Eq. A3-A4, on a uniform Cartesian periodic grid (metric terms reduce to
+ *     1/dx) or on a periodic curvilinear grid x(xi, eta), y(xi, eta), z = zeta dz given by its
+ *     point coordinates: strong conservation form Eq. A1 with the metric terms xi^_x = J^-1
+ *     dxi/dx (cofactors of the coordinate derivatives, by the same CD scheme in index space) and
+ *     the contravariant velocities of Eq. A2.
  *   - Eq. 2 / App. B: explicit central differences CD2 (a=1,b=0) and CD4 (a=4/3,b=-1/3).
  *   - Eq. 3 / Table 4: 2N-storage low-storage RK (LSERK2, LSERK4).
  *   - Sec. 3.1, Eq. 14-15: stage-0 buffer extrapolation from delayed levels (printed polynomials).
@@ -60,6 +64,11 @@ typedef struct {
   double dt;
   const float* mlp;          /* learned halo network parameters (NULL: plain AT) */
   const double* mlp_scales;  /* in_scale[5], own_scale[5], out_scale[5] */
+  /* curvilinear grid (NULL: uniform Cartesian): point coordinates x, y as [2][ny][nx] of a
+   * mapping of (xi, eta) extruded along z (z = k dz); shift[0..1] = (x, y) jump across the
+   * periodic wrap in xi, shift[2..3] = the jump across the wrap in eta */
+  const double* grid_xy;
+  double grid_shift[4];
 } or_params;
 
 /* ---------------------------------------------------------------- coefficient tables */
@@ -227,6 +236,50 @@ static int classify(const subdom* d, int i, int j, int k, int dep[3], int face[3
   return nout;
 }
 
+/* ---------------------------------------------------------------- metric terms (curvilinear)
+ * For the extruded mapping the Jacobian matrix d(x,y,z)/d(xi,eta,zeta) is
+ * [[x_xi, x_eta, 0], [y_xi, y_eta, 0], [0, 0, z_zeta]] with z_zeta = dz (1 in 2-D); its
+ * cofactors are the metric terms of App. A:
+ *   xi^_x = y_eta z_zeta, xi^_y = -x_eta z_zeta, eta^_x = -y_xi z_zeta, eta^_y = x_xi z_zeta,
+ *   zeta^_z = x_xi y_eta - x_eta y_xi,  J^-1 = z_zeta (x_xi y_eta - x_eta y_xi),
+ * all other metric terms zero.  The coordinate derivatives use the scheme of Eq. 2 in index
+ * space (spacing 1), periodic with the coordinate jump added across the wrap.  With periodic CD
+ * operators D_xi D_eta = D_eta D_xi, so sum_a D_a (metric column) = 0 holds discretely and a
+ * uniform flow stays uniform (freestream preservation). */
+#define NM 6 /* xi^_x, xi^_y, eta^_x, eta^_y, zeta^_z, J^-1 */
+
+static double coord_at(const or_params* p, int c, int i, int j) {
+  int ii = wrapi(i, p->nx), jj = wrapi(j, p->ny);
+  int wi = (i - ii) / p->nx, wj = (j - jj) / p->ny; /* number of wraps (exact multiples) */
+  return p->grid_xy[(size_t)c * p->nx * p->ny + (size_t)ii + (size_t)p->nx * jj] + wi * p->grid_shift[c] +
+         wj * p->grid_shift[2 + c];
+}
+
+static double cd_coord(const or_params* p, int c, int i, int j, int axis) {
+  double f[5];
+  for (int o = -2; o <= 2; ++o) f[o + 2] = axis == 0 ? coord_at(p, c, i + o, j) : coord_at(p, c, i, j + o);
+  if (p->order == 4) return (-1.0 / 3.0) * (f[4] - f[0]) / 4.0 + (4.0 / 3.0) * (f[3] - f[1]) / 2.0;
+  return (f[3] - f[1]) / 2.0;
+}
+
+/* Metric field [NM][N] of the whole grid (NULL for a Cartesian grid). */
+static double* metric_field(const or_params* p) {
+  if (!p->grid_xy) return NULL;
+  const size_t N = (size_t)p->nx * p->ny * p->nz, n2 = (size_t)p->nx * p->ny;
+  double* M = (double*)malloc(sizeof(double) * NM * N);
+  const double zz = p->nz > 1 ? p->dz : 1.0;
+  for (int j = 0; j < p->ny; ++j)
+    for (int i = 0; i < p->nx; ++i) {
+      double x_xi = cd_coord(p, 0, i, j, 0), x_eta = cd_coord(p, 0, i, j, 1);
+      double y_xi = cd_coord(p, 1, i, j, 0), y_eta = cd_coord(p, 1, i, j, 1);
+      double det = x_xi * y_eta - x_eta * y_xi;
+      double m[NM] = {y_eta * zz, -x_eta * zz, -y_xi * zz, x_xi * zz, det, zz * det};
+      for (int k = 0; k < p->nz; ++k)
+        for (int c = 0; c < NM; ++c) M[(size_t)c * N + (size_t)i + (size_t)p->nx * j + n2 * k] = m[c];
+    }
+  return M;
+}
+
 /* ---------------------------------------------------------------- RHS on an extended array */
 
 typedef struct {
@@ -235,12 +288,14 @@ typedef struct {
   double* G;     /* [12][ext] du/dx.. (u,v,w,T) x (x,y,z) */
   double* F;     /* [3][5][ext] inviscid fluxes per direction */
   double* FV;    /* [3][5][ext] viscous fluxes per direction */
+  double* M;     /* [NM][ext] metric terms (curvilinear grids) */
   size_t cap;
 } work_t;
 
 static void work_reserve(work_t* w, size_t n) {
   if (w->cap >= n) return;
-  free(w->E); free(w->W); free(w->G); free(w->F); free(w->FV);
+  free(w->E); free(w->W); free(w->G); free(w->F); free(w->FV); free(w->M);
+  w->M = (double*)malloc(sizeof(double) * NM * n);
   w->E = (double*)malloc(sizeof(double) * NV * n);
   w->W = (double*)malloc(sizeof(double) * 7 * n);
   w->G = (double*)malloc(sizeof(double) * 12 * n);
@@ -250,7 +305,7 @@ static void work_reserve(work_t* w, size_t n) {
 }
 
 static void work_free(work_t* w) {
-  free(w->E); free(w->W); free(w->G); free(w->F); free(w->FV);
+  free(w->E); free(w->W); free(w->G); free(w->F); free(w->FV); free(w->M);
   memset(w, 0, sizeof(*w));
 }
 
@@ -357,6 +412,138 @@ static void rhs_ext(const or_params* p, const subdom* d, work_t* w, double* R) {
             }
           }
           R[vv * no + o] = acc;
+        }
+      }
+}
+
+/* Curvilinear right-hand side (Eq. A1 with a time-invariant grid): at the owned points
+ *   dU/dt = J [ -sum_a D_a F^_a + (1/Re) sum_a D_a F^v_a ],
+ * D_a the scheme of Eq. 2 along index direction a (spacing 1), F^_a of Eq. A2 with the
+ * contravariant velocity U^_a = (metric row a) . u, F^v_a of Eq. A3 = (metric row a) . (Fv_x, Fv_y,
+ * Fv_z), and the stresses / heat flux of Eq. A4 from physical gradients
+ * d phi / d x_j = J sum_k (metric row k)_j d phi / d xi_k.  Mg: global metric field [NM][N]. */
+static void rhs_ext_curv(const or_params* p, const subdom* d, const double* Mg, work_t* w, double* R) {
+  const size_t ex = d->ex, ey = d->ey, ez = d->ez;
+  const size_t n = ex * ey * ez;
+  const size_t N = (size_t)p->nx * p->ny * p->nz;
+  const size_t sty = ex, stz = ex * ey;
+  const int three_d = p->nz > 1;
+  const int ndim = three_d ? 3 : 2;
+  const double gm = p->gamma, M2 = p->mach * p->mach;
+  const int r = (p->order == 4) ? 2 : 1;
+  double* E = w->E;
+  double* W = w->W;
+  double* Mx = w->M;
+  /* metric terms at every extended point (periodic) */
+  for (int k = 0; k < (int)ez; ++k)
+    for (int j = 0; j < (int)ey; ++j)
+      for (int i = 0; i < (int)ex; ++i) {
+        int gx = wrapi(d->ox + i - d->g, p->nx), gy = wrapi(d->oy + j - d->g, p->ny);
+        int gz = wrapi(d->oz + k - d->gz, p->nz);
+        size_t gq = (size_t)gx + (size_t)p->nx * (gy + (size_t)p->ny * gz);
+        size_t q = (size_t)i + ex * (j + ey * (size_t)k);
+        for (int c = 0; c < NM; ++c) Mx[c * n + q] = Mg[c * N + gq];
+      }
+  /* metric row of index direction a at point q: (d xi_a / d x, d xi_a / d y, d xi_a / d z) / J */
+#define MROW(a, q, out)                                                             \
+  do {                                                                              \
+    if ((a) == 0) { out[0] = Mx[q]; out[1] = Mx[n + (q)]; out[2] = 0.0; }           \
+    else if ((a) == 1) { out[0] = Mx[2 * n + (q)]; out[1] = Mx[3 * n + (q)]; out[2] = 0.0; } \
+    else { out[0] = 0.0; out[1] = 0.0; out[2] = Mx[4 * n + (q)]; }                  \
+  } while (0)
+  for (size_t q = 0; q < n; ++q) {
+    double rho = E[q], ru = E[n + q], rv = E[2 * n + q], rw = E[3 * n + q], rE = E[4 * n + q];
+    double u = ru / rho, v = rv / rho, ww = rw / rho;
+    double pr = (gm - 1.0) * (rE - 0.5 * rho * (u * u + v * v + ww * ww));
+    double T = gm * M2 * pr / rho;
+    W[q] = rho; W[n + q] = u; W[2 * n + q] = v; W[3 * n + q] = ww; W[4 * n + q] = pr; W[5 * n + q] = T;
+    W[6 * n + q] = (p->visc_law == 1) ? pow(T, p->visc_exp) : 1.0;
+  }
+  const size_t st[3] = {1, sty, stz};
+  const int lo2 = three_d ? r : 0, hi2 = three_d ? (int)ez - r : 1;
+  /* Eq. A2: F^_a = [rho U^, rho u U^ + m_x p, rho v U^ + m_y p, rho w U^ + m_z p, (rho E_t + p) U^] */
+  for (int a = 0; a < ndim; ++a) {
+    double* F = w->F + (size_t)a * NV * n;
+    for (size_t q = 0; q < n; ++q) {
+      double m[3];
+      MROW(a, q, m);
+      double rho = W[q], pr = W[4 * n + q];
+      double Uc = m[0] * W[n + q] + m[1] * W[2 * n + q] + m[2] * W[3 * n + q];
+      F[q] = rho * Uc;
+      F[n + q] = rho * W[n + q] * Uc + m[0] * pr;
+      F[2 * n + q] = rho * W[2 * n + q] * Uc + m[1] * pr;
+      F[3 * n + q] = rho * W[3 * n + q] * Uc + m[2] * pr;
+      F[4 * n + q] = (E[4 * n + q] + pr) * Uc;
+    }
+  }
+  if (p->viscous) {
+    double* G = w->G;
+    for (size_t q = 0; q < 12 * n; ++q) G[q] = NAN;
+    for (int k = lo2; k < hi2; ++k)
+      for (int j = r; j < (int)ey - r; ++j)
+        for (int i = r; i < (int)ex - r; ++i) {
+          size_t q = (size_t)i + sty * j + stz * k;
+          double J = 1.0 / Mx[5 * n + q];
+          for (int vv = 0; vv < 4; ++vv) {
+            const double* f = W + (size_t)(vv == 3 ? 5 : 1 + vv) * n;
+            double dxi[3];
+            for (int a = 0; a < 3; ++a) dxi[a] = (a < ndim) ? cd(f, q, st[a], p->order, 1.0) : 0.0;
+            for (int jj = 0; jj < 3; ++jj) {
+              double acc = 0.0;
+              for (int a = 0; a < ndim; ++a) {
+                double m[3];
+                MROW(a, q, m);
+                acc += m[jj] * dxi[a];
+              }
+              G[(size_t)(3 * vv + jj) * n + q] = J * acc;
+            }
+          }
+        }
+    const double kap = 1.0 / ((gm - 1.0) * p->pr * M2);
+    for (size_t q = 0; q < n; ++q) {
+      double mu = W[6 * n + q];
+      double du[3][3];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) du[i][j] = G[(size_t)(3 * i + j) * n + q];
+      double div = du[0][0] + du[1][1] + du[2][2];
+      double tau[3][3], b[3];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          tau[i][j] = mu * (du[i][j] + du[j][i]) - (i == j ? 2.0 / 3.0 * mu * div : 0.0);
+      double uu[3] = {W[n + q], W[2 * n + q], W[3 * n + q]};
+      for (int i = 0; i < 3; ++i)
+        b[i] = uu[0] * tau[i][0] + uu[1] * tau[i][1] + uu[2] * tau[i][2] + kap * mu * G[(size_t)(9 + i) * n + q];
+      /* Eq. A3: F^v_a = [0, m_i tau_i1, m_i tau_i2, m_i tau_i3, m_i b_i] */
+      for (int a = 0; a < ndim; ++a) {
+        double m[3];
+        MROW(a, q, m);
+        double* FV = w->FV + (size_t)a * NV * n;
+        FV[q] = 0.0;
+        for (int c = 0; c < 3; ++c) FV[(1 + c) * n + q] = m[0] * tau[0][c] + m[1] * tau[1][c] + m[2] * tau[2][c];
+        FV[4 * n + q] = m[0] * b[0] + m[1] * b[1] + m[2] * b[2];
+      }
+    }
+  }
+#undef MROW
+  const double ire = 1.0 / p->re;
+  for (int k = 0; k < d->sz; ++k)
+    for (int j = 0; j < d->sy; ++j)
+      for (int i = 0; i < d->sx; ++i) {
+        size_t q = (size_t)(i + d->g) + sty * (j + d->g) + stz * (k + d->gz);
+        size_t o = (size_t)i + (size_t)d->sx * (j + (size_t)d->sy * k);
+        size_t no = (size_t)d->sx * d->sy * d->sz;
+        double J = 1.0 / Mx[5 * n + q];
+        for (int vv = 0; vv < NV; ++vv) {
+          double acc = 0.0;
+          for (int a = 0; a < ndim; ++a) {
+            const double* F = w->F + (size_t)a * NV * n + (size_t)vv * n;
+            acc -= cd(F, q, st[a], p->order, 1.0);
+            if (p->viscous) {
+              const double* FV = w->FV + (size_t)a * NV * n + (size_t)vv * n;
+              acc += ire * cd(FV, q, st[a], p->order, 1.0);
+            }
+          }
+          R[vv * no + o] = J * acc;
         }
       }
 }
@@ -738,6 +925,7 @@ int or_run(const or_params* p, double* U, const int8_t* delays, long n0, long ns
   double* Ucur = (double*)malloc(sizeof(double) * NV * N);
   double* Unew = (double*)malloc(sizeof(double) * NV * N);
   double* Q = (double*)malloc(sizeof(double) * NV * N);
+  double* Mg = metric_field(p);
   int** kfs = (int**)malloc(sizeof(int*) * nsub);
   for (int s = 0; s < nsub; ++s) kfs[s] = (int*)malloc(sizeof(int) * 6);
   halo_t* hbs = (halo_t*)calloc(nsub, sizeof(halo_t));
@@ -780,7 +968,8 @@ int or_run(const or_params* p, double* U, const int8_t* delays, long n0, long ns
           fill_ext(p, &d, Ucur, mode, &h, n, kfs[s], &hbs[s], &w);
           size_t no = (size_t)d.sx * d.sy * d.sz;
           double* R = (double*)malloc(sizeof(double) * NV * no);
-          rhs_ext(p, &d, &w, R);
+          if (Mg) rhs_ext_curv(p, &d, Mg, &w, R);
+          else rhs_ext(p, &d, &w, R);
           /* Eq. 3: Q^(m) = A_m Q^(m-1) + dt R(U^(m-1));  U^(m) = U^(m-1) + B_m Q^(m) */
           for (int v = 0; v < NV; ++v)
             for (int k = 0; k < d.sz; ++k)
@@ -812,7 +1001,7 @@ int or_run(const or_params* p, double* U, const int8_t* delays, long n0, long ns
   memcpy(U, Ucur, sizeof(double) * NV * N);
   for (int i = 0; i < h.R; ++i) free(h.lev[i]);
   free(h.lev);
-  free(Ucur); free(Unew); free(Q);
+  free(Ucur); free(Unew); free(Q); free(Mg);
   for (int s = 0; s < nsub; ++s) { free(kfs[s]); free(hbs[s].ub); free(hbs[s].qb); }
   free(kfs); free(hbs);
   return 0;
@@ -830,6 +1019,7 @@ int or_rhs(const or_params* p, const double* U, double* Rout) {
     make_subdom(p, s, g, &d);
     if (d.sx < g || d.sy < g || (p->nz > 1 && d.sz < g)) return 1;
   }
+  double* Mg = metric_field(p);
 #pragma omp parallel
   {
     work_t w;
@@ -842,7 +1032,8 @@ int or_rhs(const or_params* p, const double* U, double* Rout) {
       fill_ext(p, &d, U, 0, NULL, 0, kf, NULL, &w);
       size_t no = (size_t)d.sx * d.sy * d.sz;
       double* R = (double*)malloc(sizeof(double) * NV * no);
-      rhs_ext(p, &d, &w, R);
+      if (Mg) rhs_ext_curv(p, &d, Mg, &w, R);
+      else rhs_ext(p, &d, &w, R);
       for (int v = 0; v < NV; ++v)
         for (int k = 0; k < d.sz; ++k)
           for (int j = 0; j < d.sy; ++j)
@@ -854,37 +1045,44 @@ int or_rhs(const or_params* p, const double* U, double* Rout) {
     }
     work_free(&w);
   }
+  free(Mg);
   return 0;
 }
 
 /* Volume-averaged kinetic energy and enstrophy (Sec. 5.2, rho_0 = 1) with vorticity from the CD
  * scheme on the periodic field, cell-volume-weighted totals of the conserved variables, and a
- * non-finite flag.  out[8] = {K, eps, sum rho, sum rho u, sum rho v, sum rho w, sum rho E, nan}. */
+ * non-finite flag.  out[8] = {K, eps, sum rho, sum rho u, sum rho v, sum rho w, sum rho E, nan}.
+ * On a curvilinear grid the cell volume is J^-1 and the averages are volume-weighted; velocity
+ * derivatives are taken in index space and mapped by the metric terms. */
 int or_diagnostics(const or_params* p, const double* U, double* out) {
   const int nx = p->nx, ny = p->ny, nz = p->nz;
   const size_t N = (size_t)nx * ny * nz;
-  const double dV = p->dx * p->dy * (nz > 1 ? p->dz : 1.0);
-  double ke = 0, ens = 0, tot[5] = {0, 0, 0, 0, 0};
+  double* Mg = metric_field(p);
+  const double dV0 = p->dx * p->dy * (nz > 1 ? p->dz : 1.0);
+  double ke = 0, ens = 0, vol = 0, tot[5] = {0, 0, 0, 0, 0};
   int bad = 0;
   const int order = p->order;
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
         size_t q = (size_t)i + (size_t)nx * (j + (size_t)ny * k);
+        const double dV = Mg ? Mg[5 * N + q] : dV0;
         double rho = U[q];
         double u = U[N + q] / rho, v = U[2 * N + q] / rho, w = U[3 * N + q] / rho;
         for (int c = 0; c < 5; ++c) {
           if (!isfinite(U[c * N + q])) bad = 1;
           tot[c] += U[c * N + q] * dV;
         }
-        ke += 0.5 * rho * (u * u + v * v + w * w);
+        const double wv = Mg ? dV : 1.0; /* Cartesian: plain point average */
+        vol += wv;
+        ke += 0.5 * rho * (u * u + v * v + w * w) * wv;
         /* velocity derivative along axis a of component c at (i,j,k), periodic CD */
         double dvel[3][3];
         for (int c = 0; c < 3; ++c)
           for (int a = 0; a < 3; ++a) {
             int n_a = a == 0 ? nx : (a == 1 ? ny : nz);
             if (n_a == 1) { dvel[c][a] = 0.0; continue; }
-            double hh = a == 0 ? p->dx : (a == 1 ? p->dy : p->dz);
+            double hh = Mg ? 1.0 : (a == 0 ? p->dx : (a == 1 ? p->dy : p->dz));
             double f[5];
             for (int o = -2; o <= 2; ++o) {
               int ii = i, jj = j, kk = k;
@@ -899,13 +1097,24 @@ int or_diagnostics(const or_params* p, const double* U, double* out) {
             else
               dvel[c][a] = (f[3] - f[1]) / (2.0 * hh);
           }
+        if (Mg) {
+          /* d u_c / d x_j = J sum_a (metric row a)_j d u_c / d xi_a */
+          const double J = 1.0 / Mg[5 * N + q];
+          const double m[3][3] = {{Mg[q], Mg[N + q], 0.0}, {Mg[2 * N + q], Mg[3 * N + q], 0.0}, {0.0, 0.0, Mg[4 * N + q]}};
+          double dphys[3][3];
+          for (int c = 0; c < 3; ++c)
+            for (int jj = 0; jj < 3; ++jj)
+              dphys[c][jj] = J * (m[0][jj] * dvel[c][0] + m[1][jj] * dvel[c][1] + m[2][jj] * dvel[c][2]);
+          memcpy(dvel, dphys, sizeof(dvel));
+        }
         double wx = dvel[2][1] - dvel[1][2], wy = dvel[0][2] - dvel[2][0], wz = dvel[1][0] - dvel[0][1];
-        ens += 0.5 * rho * (wx * wx + wy * wy + wz * wz);
+        ens += 0.5 * rho * (wx * wx + wy * wy + wz * wz) * wv;
       }
-  out[0] = ke / (double)N;
-  out[1] = ens / (double)N;
+  out[0] = ke / vol;
+  out[1] = ens / vol;
   for (int c = 0; c < 5; ++c) out[2 + c] = tot[c];
   out[7] = bad ? 1.0 : 0.0;
+  free(Mg);
   return 0;
 }
 

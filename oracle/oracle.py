@@ -36,6 +36,7 @@ class OrParams(ctypes.Structure):
         ("caa_L", ctypes.c_int), ("kmax", ctypes.c_int),
         ("filter", ctypes.c_int), ("alpha_f", ctypes.c_double), ("dt", ctypes.c_double),
         ("mlp", ctypes.POINTER(ctypes.c_float)), ("mlp_scales", ctypes.POINTER(ctypes.c_double)),
+        ("grid_xy", ctypes.POINTER(ctypes.c_double)), ("grid_shift", ctypes.c_double * 4),
     ]
 
 
@@ -88,14 +89,23 @@ ALGOS = {"SA": 0, "CAA": 1, "SAA": 2}
 
 
 def params(case) -> OrParams:
-    """Translate a ``inputs.Case`` description into the oracle's parameter struct."""
-    return OrParams(
+    """Translate a ``inputs.Case`` description into the oracle's parameter struct (a curvilinear
+    case carries its point coordinates; the array is kept alive on the struct)."""
+    p = OrParams(
         nx=case.nx, ny=case.ny, nz=case.nz, px=case.px, py=case.py, pz=case.pz,
         dx=case.dx, dy=case.dy, dz=case.dz, gamma=case.gamma, mach=case.mach, re=case.re,
         pr=case.pr, viscous=int(case.viscous), visc_law=int(case.visc_law),
         visc_exp=case.visc_exp, order=case.order, algo=ALGOS[case.algo], at=int(case.at),
         caa_L=case.caa_L, kmax=case.kmax, filter=int(case.filter), alpha_f=case.alpha_f,
         dt=case.dt)
+    from paper_2506_03027_gb300.inputs import grid_xy
+    g = grid_xy(case)
+    if g is not None:
+        p._xy = g[0]
+        p.grid_xy = _dptr(g[0])
+        for i in range(4):
+            p.grid_shift[i] = float(g[1][i])
+    return p
 
 
 def run(case, U0: np.ndarray, nsteps: int, delays: np.ndarray | None = None, n0: int = 0,

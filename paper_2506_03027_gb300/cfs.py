@@ -16,6 +16,8 @@ import threading
 
 import numpy as np
 
+from .inputs import grid_xy
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libcfs.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "cfs.h")
@@ -72,6 +74,7 @@ def load() -> ctypes.CDLL:
             "cfs_set_allocator": ([vp, ALLOC_FN, FREE_FN, vp], ip),
             "cfs_add_block": ([vp, ip, ip, ip, dp, ctypes.POINTER(ip)], ip),
             "cfs_split_block": ([vp, ip, ip, ip, ip], ip),
+            "cfs_set_block_grid": ([vp, ip, dp, dp], ip),
             "cfs_connect": ([vp, ip, ip, ip, ip, ip], ip),
             "cfs_set_bc": ([vp, ip, ip, ip, dp], ip),
             "cfs_finalize": ([vp, ip], ip),
@@ -140,6 +143,16 @@ def cfs_add_block(ctx, ni: int, nj: int, nk: int, spacing) -> int:
 
 def cfs_split_block(ctx, block: int, pi: int, pj: int, pk: int):
     _check(ctx, load().cfs_split_block(ctx, block, pi, pj, pk))
+
+
+def cfs_set_block_grid(ctx, block: int, xy: np.ndarray, shift):
+    """Curvilinear block: xy host [2][nj][ni] point coordinates, shift = (x, y) jumps across the
+    periodic wrap in i, then in j."""
+    a = np.ascontiguousarray(xy, dtype=np.float64)
+    sh = np.ascontiguousarray(shift, dtype=np.float64)
+    assert sh.size == 4
+    _check(ctx, load().cfs_set_block_grid(ctx, block, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          sh.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
 
 
 def cfs_connect(ctx, block_a: int, face_a: int, block_b: int, face_b: int, orientation: int = 0):
@@ -371,6 +384,9 @@ class Solver:
         for b in self.blocks:
             bid = cfs_add_block(self.ctx, b.nx, b.ny, b.nz, (b.dx, b.dy, b.dz))
             cfs_split_block(self.ctx, bid, b.px, b.py, b.pz)
+            gxy = grid_xy(b)
+            if gxy is not None:
+                cfs_set_block_grid(self.ctx, bid, gxy[0], gxy[1])
         if tiles is not None:
             cfs_set_tiles(self.ctx, *tiles)
         if max_delay is None:
@@ -423,6 +439,9 @@ class Solver:
     @property
     def n(self) -> int:
         return cfs_get_step(self.ctx)
+
+    def set_step(self, n: int):
+        cfs_set_step(self.ctx, n)
 
     def launches(self) -> int:
         return cfs_launch_count(self.ctx)

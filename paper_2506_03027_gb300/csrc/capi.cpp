@@ -28,6 +28,10 @@ struct Block {
   int* d_owner[3] = {nullptr, nullptr, nullptr};
   int* d_axis_off[3] = {nullptr, nullptr, nullptr};
   int* d_axis_len[3] = {nullptr, nullptr, nullptr};
+  // curvilinear grid (cfs_set_block_grid): x, y of every (i, j), and the periodic coordinate jumps
+  std::vector<double> xy;
+  double shift[4] = {0, 0, 0, 0};
+  long long mbase = -1;   // offset of its metric field in d_metric
 };
 
 struct cfs_ctx {
@@ -87,6 +91,8 @@ struct cfs_ctx {
   int fused_zc = 16;
   int fused_fy = 8;
   int fused_grid = 0;
+  double* d_metric = nullptr;  // metric fields of the curvilinear blocks
+  double volume = 0.0;         // total cell volume (diagnostics averages)
   int nwork = 0;
   int* d_work = nullptr;
   float* Wh = nullptr;
@@ -244,6 +250,22 @@ cfs_status cfs_add_block(cfs_ctx* c, int ni, int nj, int nk, const double* spaci
   return CFS_OK;
 }
 
+cfs_status cfs_set_block_grid(cfs_ctx* c, int block, const double* xy, const double* shift) {
+  if (!c) return CFS_EINVAL;
+  if (c->finalized) return fail(c, CFS_ESTATE, "the grid must be set before cfs_finalize");
+  if (block < 0 || block >= (int)c->blocks.size()) return fail(c, CFS_EINVAL, "unknown block");
+  if (!xy || !shift) return fail(c, CFS_EINVAL, "null grid");
+  Block& b = c->blocks[block];
+  const size_t n2 = (size_t)b.nx * b.ny;
+  for (size_t q = 0; q < 2 * n2; ++q)
+    if (!std::isfinite(xy[q])) return fail(c, CFS_EINVAL, "non-finite grid coordinate");
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(shift[k])) return fail(c, CFS_EINVAL, "non-finite grid shift");
+  b.xy.assign(xy, xy + 2 * n2);
+  for (int k = 0; k < 4; ++k) b.shift[k] = shift[k];
+  return CFS_OK;
+}
+
 cfs_status cfs_split_block(cfs_ctx* c, int block, int pi, int pj, int pk) {
   if (!c) return CFS_EINVAL;
   if (c->finalized) return fail(c, CFS_ESTATE, "split before cfs_finalize");
@@ -279,6 +301,7 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   for (Block& b : c->blocks) {
     b.sid0 = nsub;
     b.base = 5 * Ntot;
+    b.mbase = b.xy.empty() ? -1 : (long long)NMETRIC * Ntot;
     nsub += b.P[0] * b.P[1] * b.P[2];
     Ntot += b.N;
   }
@@ -305,9 +328,11 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
           d.bnx = b.nx; d.bny = b.ny; d.bnz = b.nz;
           d.bN = b.N;
           d.bbase = b.base;
+          d.mbase = b.mbase;
           for (int a = 0; a < 3; ++a) {  // CD coefficients of Eq. 2 (alpha = 0) for the block's spacing
-            d.c1[a] = (a_cd / 2.0) / b.h[a];
-            d.c2[a] = (b_cd / 4.0) / b.h[a];
+            const double h = b.mbase >= 0 ? 1.0 : b.h[a];  // curvilinear: index space
+            d.c1[a] = (a_cd / 2.0) / h;
+            d.c2[a] = (b_cd / 4.0) / h;
           }
           const long long npad = (long long)d.ex * d.ey * d.ez;
           pbase += npad;
@@ -347,7 +372,31 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   c->buf[0] = (double*)dev_alloc(c, sizeof(double) * 5 * N);
   c->buf[1] = (double*)dev_alloc(c, sizeof(double) * 5 * N);
   c->Q = (double*)dev_alloc(c, sizeof(double) * 5 * N);
-  c->fused = c->p.precision == 1 && c->ndim == 3 && c->p.viscous && c->p.order == 4;
+  // metric fields of the curvilinear blocks, and the total volume for the diagnostics
+  bool curv = false;
+  c->volume = 0.0;
+  for (const Block& b : c->blocks) {
+    curv = curv || b.mbase >= 0;
+    if (b.mbase < 0) c->volume += (double)b.N * b.h[0] * b.h[1] * (c->ndim == 3 ? b.h[2] : 1.0);
+  }
+  if (curv) {
+    c->d_metric = (double*)dev_alloc(c, sizeof(double) * NMETRIC * N);
+    if (!c->d_metric) return fail(c, CFS_ENOMEM, "device allocation failed");
+    std::vector<double> M;
+    for (const Block& b : c->blocks) {
+      if (b.mbase < 0) continue;
+      M.assign((size_t)NMETRIC * b.N, 0.0);
+      cfs::grid_metrics(b.nx, b.ny, b.nz, b.h[2], c->p.order, b.xy.data(), b.shift, M.data());
+      for (long long q = 0; q < b.N; ++q) {
+        if (!(M[5 * b.N + q] > 0.0)) return fail(c, CFS_EINVAL, "curvilinear grid with a non-positive cell volume");
+        c->volume += M[5 * b.N + q];
+      }
+      CUDA_TRY(c, cudaMemcpy(c->d_metric + b.mbase, M.data(), sizeof(double) * M.size(), cudaMemcpyHostToDevice),
+               "upload metrics");
+    }
+  }
+  g.metric = c->d_metric;
+  c->fused = c->p.precision == 1 && c->ndim == 3 && c->p.viscous && c->p.order == 4 && !curv;
   if (c->fused) {
     // tiles of 32 x fy columns per sub-domain, marching z; one CTA per tile (persistent grid)
     std::vector<int> work;
@@ -368,8 +417,9 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int smem = cfs::fused_smem_bytes(c->fused_fy);
-    const int per_sm = std::max(1, (227 * 1024) / std::max(1, smem + 1024));
+    int per_sm = 0;
+    if (cfs::fused_blocks_per_sm(c->fused_fy, &per_sm) != 0 || per_sm < 1)
+      return fail(c, CFS_ECUDA, "fused stage kernel does not fit on this device");
     c->fused_grid = std::max(1, std::min(c->nwork, per_sm * std::max(1, sms)));
   } else {
     c->Wp = dev_alloc(c, tsz * 7 * (size_t)pbase);
@@ -391,6 +441,9 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
       c->Lmax = std::max(c->Lmax, (n3[a] + b.P[a] - 1) / b.P[a]);
     }
   }
+  if (c->p.filter && cfs::filter_prepare(c->Lmax, c->p.precision) != 0)
+    return fail(c, CFS_EINVAL, "filter: a sub-domain is too long along an axis for the shared-memory line tiles "
+                               "(at most about 700 points)");
   c->diag_blocks = 2 * 152;
   c->d_partial = (double*)dev_alloc(c, sizeof(double) * 8 * c->diag_blocks * c->blocks.size());
   c->d_thomas = (double*)dev_alloc(c, sizeof(double) * (size_t)(c->Lmax + 1) * 2 * c->Lmax);
@@ -766,12 +819,18 @@ cfs_status cfs_diagnostics(cfs_ctx* c, double* out) {
       db.c2[a] = (b_cd / 4.0) / b.h[a];
     }
     db.dV = b.h[0] * b.h[1] * (c->ndim == 3 ? b.h[2] : 1.0);
+    db.M = b.mbase >= 0 ? c->d_metric + b.mbase : nullptr;
+    if (db.M)
+      for (int a = 0; a < 3; ++a) {  // index-space coefficients
+        db.c1[a] = a_cd / 2.0;
+        db.c2[a] = b_cd / 4.0;
+      }
     int rc = cfs::launch_diagnostics_block(c->geo, db, U, c->d_partial, row, c->diag_blocks, c->stream);
     if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "diagnostics launch");
     row += c->diag_blocks;
   }
   {
-    int rc = cfs::launch_diagnostics_final(c->d_partial, row, c->d_out, c->geo.N, c->stream);
+    int rc = cfs::launch_diagnostics_final(c->d_partial, row, c->d_out, c->volume, c->stream);
     if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "diagnostics launch");
   }
   CUDA_TRY(c, cudaMemcpyAsync(out, c->d_out, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream), "diagnostics");

@@ -37,6 +37,9 @@ struct SubDev {
   long long bN;       // block points
   long long bbase;    // offset of the block's state [5][bnz][bny][bnx] in a state array (doubles)
   double c1[3], c2[3];  // CD coefficients of the block's spacing: c1 = (a/2)/h, c2 = (b/4)/h
+  // curvilinear block: offset of its metric field in Geometry::metric (component stride bN),
+  // -1 for a uniform Cartesian block; c1, c2 are then the index-space coefficients (h = 1)
+  long long mbase;
 };
 
 // Scalars every kernel needs; passed by value.
@@ -49,7 +52,11 @@ struct Geometry {
   int ndim;              // 2 or 3
   int viscous;
   long long Ptot;        // total padded points (scratch length per component)
+  // metric fields of the curvilinear blocks, [NMETRIC][block points] per block (device), or null:
+  // xi^_x, xi^_y, eta^_x, eta^_y, zeta^_z (= J^-1 d(xi,eta,zeta)/dx of App. A), J^-1, J
+  const double* metric;
 };
+#define NMETRIC 7
 
 struct Physics {
   double gamma, gm1, gM2;  // gamma, gamma - 1, gamma M^2
@@ -93,6 +100,7 @@ bool buffer_dudt_weights(int order, int e, int k, long double* d);
 int at_weight_table(int order, int kmax, double* W);
 int filter_extrap_table(int order, int kmax, double* Wf);
 bool pade10_coeffs(double alpha, double* a);
+void grid_metrics(int nx, int ny, int nz, double dz, int order, const double* xy, const double* shift, double* M);
 
 // kernel launchers (kernels.cu); all return a cudaError_t cast to int
 
@@ -146,6 +154,7 @@ struct FilterLaunch {
   double b1;               // a_1/2 - alpha: weight of the first second difference (increment form)
 };
 
+int filter_prepare(int Lmax, int precision);  // shared-memory attribute of the filter kernels; nonzero if too long
 int launch_filter(const Geometry& g, const StepSched& sc, const FilterLaunch& f, int axis, int precision,
                   void* stream, long long* launches, const Timer* tm);
 
@@ -167,6 +176,7 @@ struct FusedLaunch {
   int in_ring, out_ring;
 };
 int fused_smem_bytes(int fy);
+int fused_blocks_per_sm(int fy, int* blocks);  // sets the shared-memory attribute, then asks the occupancy API
 int launch_halo_prims(const Geometry& g, const Physics& ph, const StepSched& sc, const double* ring, const SubDev* subs,
                       const int* halo, long long nhalo, float* Wh, int s, void* stream, long long* launches,
                       const Timer* tm);
@@ -200,10 +210,11 @@ struct DiagBlock {
   int nx, ny, nz;
   long long bN, bbase;
   double c1[3], c2[3], dV;
+  const double* M;  // the block's metric field (curvilinear), or null
 };
 int launch_diagnostics_block(const Geometry& g, const DiagBlock& b, const double* U, double* partial, int row0,
                              int nblocks, void* stream);
-int launch_diagnostics_final(const double* partial, int nrows, double* out, long long N, void* stream);
+int launch_diagnostics_final(const double* partial, int nrows, double* out, double volume, void* stream);
 int launch_advance_step(long long* dn, void* stream);
 
 }  // namespace cfs

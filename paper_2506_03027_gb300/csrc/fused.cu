@@ -1,16 +1,22 @@
 // fused.cu -- fused LSERK stage for the FP32-intermediate form (3-D Navier-Stokes, CD4/AT4).
 //
 // One launch per RK stage (Eq. 3) does what k_view + k_flux + k_rk do in three: each CTA owns an
-// FX x FY column tile of one sub-domain and marches through its z-planes, keeping a ring of five
-// planes of FP32 primitives (tile + halo of 4) in shared memory:
-//   load plane L        own points and synchronous halos from the FP64 stage input; AT/AS halo
-//                       points from the per-step halo store (k_halo_prims);
-//   plane G = L - 2     CD4 gradients (x, y from the plane, z from the ring), viscous stresses and
-//                       heat flux (Eq. A3-A4), combined fluxes Phi_a = -F_a + Fv_a/Re (Eq. A2):
-//                       Phi_x, Phi_y of the tile and its x / y strips to shared memory, Phi_z of
-//                       the tile to a register queue; then dt (D_x Phi_x + D_y Phi_y) of the tile;
-//   plane z = L - 4     dt R = that in-plane part + dt D_z Phi_z from the queue, and the FP64
-//                       low-storage update Q = A Q + dt R, U^(m) = U^(m-1) + B Q.
+// FX x FY column tile of one sub-domain and marches through its z-planes.  Per plane L:
+//   stage  L + 1         asynchronous copies (cp.async) of the raw stage input of the next plane
+//                        -- FP64 conserved values of own points and synchronous halos, FP32
+//                        primitives of AT/AS halo points from the per-step halo store
+//                        (k_halo_prims) -- into a staging buffer, overlapping the work below;
+//   convert L            staging -> FP32 primitives: u, v, w, T into a five-plane ring (the CD4
+//                        gradient stencil in z), rho, p', et' into a three-plane ring over the
+//                        tile and its 2-wide strips (values at flux points only);
+//   plane G = L - 2      CD4 gradients, viscous stresses and heat flux (Eq. A3-A4), combined
+//                        fluxes Phi_a = -F_a + Fv_a / Re (Eq. A2); Phi_x, Phi_y of the tile and
+//                        its x / y strips to shared memory, Phi_z of the tile in registers;
+//   accumulate           dt R of the tile column is gathered in a queue of four planes: Phi_z of
+//                        plane G contributes to planes G-2..G+2 (CD4 in z), dt (D_x Phi_x +
+//                        D_y Phi_y) to plane G;
+//   plane z = G - 2      complete: FP64 low-storage update Q = A Q + dt R, U^(m) = U^(m-1) + B Q.
+// Conversions between FP64 and FP32 use the integer-pipe routines of device_common.cuh.
 // k_halo_prims runs once per asynchronous step: for every halo point a sub-domain reads from a
 // neighbour it applies the AT weights of all s stages to the C delayed levels in FP64 (Eq. 14-15
 // and the buffer updates of Eq. 8 / Table 5) and stores the FP32 primitives per stage.
@@ -25,35 +31,59 @@ namespace {
 
 constexpr int HB = 4;  // halo of the box: 2r for the viscous CD4 operator
 
-// FP32 primitives from an FP64 conserved state; p and rho E are carried as deviations from the
-// reference state (p_ref = 1/(gamma M^2), E_ref = p_ref/(gamma-1)).
-__device__ __forceinline__ void prims32(const double* u, const Physics& ph, float* w) {
-  const float rho = (float)u[0];
-  const float ir = 1.0f / rho;
-  const float uu = (float)u[1] * ir, vv = (float)u[2] * ir, ww = (float)u[3] * ir;
-  const float ke = 0.5f * ((float)u[1] * uu + (float)u[2] * vv + (float)u[3] * ww);
-  const float rE = (float)(u[4] - ph.E_ref);
-  const float p = (float)ph.gm1 * (rE - ke);
+// FP32 copies of the physical constants, converted once per thread.
+struct Phys32 {
+  float gm1, gM2, ire, kap, Href, Eh, El, vexp;
+  int law;
+};
+
+__device__ __forceinline__ Phys32 phys32(const Physics& ph) {
+  Phys32 q;
+  q.gm1 = (float)ph.gm1;
+  q.gM2 = (float)ph.gM2;
+  q.ire = (float)ph.ire;
+  q.kap = (float)ph.kappa;
+  q.Href = (float)ph.H_ref;
+  q.Eh = (float)ph.E_ref;
+  q.El = (float)(ph.E_ref - (double)q.Eh);
+  q.vexp = (float)ph.visc_exp;
+  q.law = ph.visc_law;
+  return q;
+}
+
+// FP32 primitives (rho, u, v, w, p - p_ref, T, rho E + p - H_ref) from an FP64 conserved state
+// (App. A; p and rho E carried as deviations from the reference state p_ref = 1/(gamma M^2),
+// E_ref = p_ref/(gamma-1), so that FP32 rounding acts on O(1) deviations).
+__device__ __forceinline__ void prims32(const double* u, const Phys32& k, float* w) {
+  const float rho = d2f_fast(u[0]);
+  const float ir = __fdividef(1.0f, rho);
+  const float mx = d2f_fast(u[1]), my = d2f_fast(u[2]), mz = d2f_fast(u[3]);
+  const float uu = mx * ir, vv = my * ir, ww = mz * ir;
+  const float ke = 0.5f * (mx * uu + my * vv + mz * ww);
+  const float rE = dev_fast(u[4], k.Eh, k.El);
+  const float p = k.gm1 * (rE - ke);
   w[0] = rho;
   w[1] = uu;
   w[2] = vv;
   w[3] = ww;
   w[4] = p;
-  w[5] = ((float)ph.gM2 * p + 1.0f) * ir;  // T
-  w[6] = rE + p;                          // rho E + p - H_ref
+  w[5] = (k.gM2 * p + 1.0f) * ir;  // T
+  w[6] = rE + p;                   // rho E + p - H_ref
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------------------- k_halo_prims
 
+template <int S>
 __global__ void __launch_bounds__(256) k_halo_prims(Geometry g, Physics ph, StepSched sc, const double* __restrict__ ring,
                                                     const SubDev* __restrict__ subs, const int2* __restrict__ halo,
-                                                    long long nhalo, float* __restrict__ Wh, int s) {
+                                                    long long nhalo, float* __restrict__ Wh) {
   sc = resolve(sc);
   if (sc.mode == 0) return;  // synchronous step: no halo store is read
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nhalo) return;
+  const Phys32 k32 = phys32(ph);
   const int2 hv = halo[e];
   const int sid = hv.x;
   const long long t = hv.y;
@@ -70,31 +100,41 @@ __global__ void __launch_bounds__(256) k_halo_prims(Geometry g, Physics ph, Step
   if (sc.mode == 2) {  // AS: the latest visible level, the same for every stage
     const double* src = ring + (long long)((sc.n - kd) % sc.R) * lvN;
     double u[5];
+#pragma unroll
     for (int v = 0; v < 5; ++v) u[v] = src[v * d.bN + gi];
     float w[7];
-    prims32(u, ph, w);
+    prims32(u, k32, w);
+#pragma unroll
     for (int c = 0; c < 7; ++c) Wh[(long long)c * P + o] = w[c];
     return;
   }
   // AT: U_buf^(m) = sum_l W^(m)_l(k) U^{n-k-l} for every stage m, accumulated in FP64; with the
   // learned halo, face points start from the network's stage-0 value and add (W^(m) - W^(0)) R
   const bool learned = sc.LH && ((int)(ci < 0 || ci >= d.sx) + (int)(cj < 0 || cj >= d.sy) + (int)(ck < 0 || ck >= d.sz) == 1);
-  double acc[CFS_MAX_STAGES][5];
-  for (int m = 0; m < s; ++m)
+  double acc[S][5];
+#pragma unroll
+  for (int m = 0; m < S; ++m)
+#pragma unroll
     for (int v = 0; v < 5; ++v) acc[m][v] = learned ? sc.LH[(long long)v * g.Ptot + d.pbase + t] : 0.0;
   for (int l = 0; l < sc.C; ++l) {
     const double* src = ring + (long long)((sc.n - kd - l) % sc.R) * lvN;
     double r[5];
+#pragma unroll
     for (int v = 0; v < 5; ++v) r[v] = src[v * d.bN + gi];
-    const double w0 = learned ? __ldg(sc.W + (kd * s) * sc.C + l) : 0.0;
-    for (int m = learned ? 1 : 0; m < s; ++m) {
-      const double wl = __ldg(sc.W + (kd * s + m) * sc.C + l) - w0;
+    const double w0 = learned ? __ldg(sc.W + (kd * S) * sc.C + l) : 0.0;
+#pragma unroll
+    for (int m = 0; m < S; ++m) {
+      if (learned && m == 0) continue;
+      const double wl = __ldg(sc.W + (kd * S + m) * sc.C + l) - w0;
+#pragma unroll
       for (int v = 0; v < 5; ++v) acc[m][v] = fma(wl, r[v], acc[m][v]);
     }
   }
-  for (int m = 0; m < s; ++m) {
+#pragma unroll
+  for (int m = 0; m < S; ++m) {
     float w[7];
-    prims32(acc[m], ph, w);
+    prims32(acc[m], k32, w);
+#pragma unroll
     for (int c = 0; c < 7; ++c) Wh[(long long)(m * 7 + c) * P + o] = w[c];
   }
 }
@@ -103,15 +143,36 @@ __global__ void __launch_bounds__(256) k_halo_prims(Geometry g, Physics ph, Step
 
 template <int FX, int FY>
 struct FusedSmem {
-  static constexpr int BX = FX + 2 * HB, BY = FY + 2 * HB;
-  static constexpr int W = 5 * 7 * BY * BX;      // ring of 5 planes of 7 primitives
+  static constexpr int BX = FX + 2 * HB, BY = FY + 2 * HB, NB = BX * BY;  // box: tile + halo of 4
+  static constexpr int WX = FX + 4, WY = FY + 4, NW = WX * WY;            // window: tile + strips of 2
+  static constexpr int STG = 2 * 5 * NB;                                  // staging, 5 x 8 bytes per box point
+  static constexpr int R4 = 5 * 4 * NB;   // u, v, w, T of planes G-2..G+2
+  static constexpr int R3 = 3 * 3 * NW;   // rho, p', et' of planes G..G+2 on the window
   static constexpr int FXS = 5 * FY * (FX + 4);  // Phi_x of tile + x strips
   static constexpr int FYS = 5 * (FY + 4) * FX;  // Phi_y of tile + y strips
-  static constexpr size_t bytes = sizeof(float) * (W + FXS + FYS);
+  static constexpr size_t bytes = sizeof(float) * (STG + R4 + R3 + FXS + FYS);
+};
+
+// Where the stage input of a box point comes from: the FP64 state (own points, synchronous halos,
+// and box points no output depends on) or the per-step halo store.  dx, dy, dz: distance outside
+// the sub-domain along each axis.  The sub-domain's view holds faces up to depth HB and edges up
+// to r x r; a narrow ragged tile's box reaches further, and those points feed no output.
+__device__ __forceinline__ bool from_store(int mode, int r, int dx, int dy, int dz) {
+  const int nout = (dx > 0) + (dy > 0) + (dz > 0);
+  const bool inview = (nout == 1 && dx <= HB && dy <= HB && dz <= HB) || (nout == 2 && dx <= r && dy <= r && dz <= r);
+  return mode != 0 && nout > 0 && inview;
+}
+
+// Per-thread description of the box columns (i, j) it loads on every plane of a work item.
+template <int KB>
+struct BoxCols {
+  int xy[KB];   // gx + bnx gy of the wrapped in-block position
+  int pxy[KB];  // (lx + G) + ex (ly + G) in the padded box
+  int dxy[KB];  // dx | dy << 8 (distance outside the sub-domain), -1 for no column
 };
 
 template <int FX, int FY>
-__global__ void __launch_bounds__(FX* FY) k_stage_fused(Geometry g, Physics ph, StepSched sc,
+__global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fused(Geometry g, Physics ph, StepSched sc,
                                                         const double* __restrict__ Uin0, double* __restrict__ Uout0,
                                                         const double* __restrict__ ring, int in_ring, int out_ring,
                                                         double* __restrict__ Q, const SubDev* __restrict__ subs,
@@ -122,178 +183,241 @@ __global__ void __launch_bounds__(FX* FY) k_stage_fused(Geometry g, Physics ph, 
   const double* __restrict__ Uin = ring_or(Uin0, in_ring, ring, sc, 0);
   double* __restrict__ Uout = const_cast<double*>(ring_or(Uout0, out_ring, ring, sc, 1));
   using S = FusedSmem<FX, FY>;
-  constexpr int BX = S::BX, BY = S::BY, NT = FX * FY, PL = 7 * BY * BX;
-  extern __shared__ float smem[];
-  float* sW = smem;
-  float* sFx = smem + S::W;
+  constexpr int BX = S::BX, NB = S::NB, WX = S::WX, NW = S::NW, NT = FX * FY;
+  extern __shared__ __align__(16) float smem[];
+  double* sStg = reinterpret_cast<double*>(smem);  // [5][NB] FP64, or FP32 pairs for halo points
+  float* sStgF = smem;
+  float* sR4 = smem + S::STG;
+  float* sR3 = sR4 + S::R4;
+  float* sFx = sR3 + S::R3;
   float* sFy = sFx + S::FXS;
   const int tid = threadIdx.x, tx = tid % FX, ty = tid / FX;
-  const float ire = (float)ph.ire, kap = (float)ph.kappa, Href = (float)ph.H_ref;
-  const int hslot = (sc.mode == 2) ? 0 : stage;
+  constexpr int KB = (NB + NT - 1) / NT;
+  // constants converted from FP64 once per CTA (physics) and once per work item (dt x CD
+  // coefficients) by one thread; the work-item set is double-buffered by parity so that thread
+  // can run ahead of the others by one item
+  __shared__ Phys32 sPh;
+  __shared__ float sK[2][12];
+  if (tid == 0) sPh = phys32(ph);
+  __syncthreads();
+  const Phys32 k32 = sPh;
+  const long long P = g.Ptot;
+  const float* __restrict__ WhS = Wh + (long long)((sc.mode == 2) ? 0 : stage) * 7 * P;
 
-  for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+  for (int wi = blockIdx.x, par = 0; wi < nwork; wi += gridDim.x, par ^= 1) {
     const int* wk = work + 4 * wi;  // (sub-domain, x0, y0, z0 | z1 << 16)
     const SubDev d = subs[wk[0]];
     const int tx0 = wk[1], ty0 = wk[2];
     const int z0 = wk[3] & 0xffff, z1 = wk[3] >> 16;  // output planes [z0, z1) of the sub-domain
-    const float c1x = (float)d.c1[0], c2x = (float)d.c2[0], c1y = (float)d.c1[1], c2y = (float)d.c2[1];
-    const float c1z = (float)d.c1[2], c2z = (float)d.c2[2];
-    const float k1x = (float)(dt * d.c1[0]), k2x = (float)(dt * d.c2[0]);
-    const float k1y = (float)(dt * d.c1[1]), k2y = (float)(dt * d.c2[1]);
-    const float k1z = (float)(dt * d.c1[2]), k2z = (float)(dt * d.c2[2]);
-    float phiz[5][5], rxy[3][5];
+    if (tid == 0) {
+      for (int a = 0; a < 3; ++a) {
+        sK[par][a] = (float)d.c1[a];
+        sK[par][3 + a] = (float)d.c2[a];
+        sK[par][6 + a] = (float)(dt * d.c1[a]);
+        sK[par][9 + a] = (float)(dt * d.c2[a]);
+      }
+    }
+    BoxCols<KB> bc;
 #pragma unroll
-    for (int a = 0; a < 5; ++a)
+    for (int k = 0; k < KB; ++k) {
+      const int p = tid + k * NT;
+      bc.dxy[k] = -1;
+      if (p < NB) {
+        const int lx = tx0 - HB + p % BX, ly = ty0 - HB + p / BX;
+        const int dx = lx < 0 ? -lx : (lx >= d.sx ? lx - d.sx + 1 : 0);
+        const int dy = ly < 0 ? -ly : (ly >= d.sy ? ly - d.sy + 1 : 0);
+        bc.xy[k] = wrapc(d.ox + lx, d.bnx) + d.bnx * wrapc(d.oy + ly, d.bny);
+        bc.pxy[k] = (lx + g.G) + d.ex * (ly + g.G);
+        bc.dxy[k] = dx | (dy << 8);
+      }
+    }
+    // dt R of the tile column for planes G-2..G+1 (before the contributions of flux plane G)
+    float acc[4][5];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) phiz[a][c] = 0.f;
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int c = 0; c < 5; ++c) rxy[a][c] = 0.f;
+      for (int c = 0; c < 5; ++c) acc[a][c] = 0.f;
 
+    // plane-dependent parts of the source offsets
+    auto plane_src = [&](int L, long long& zoff, long long& pz, int& dz) {
+      dz = L < 0 ? -L : (L >= d.sz ? L - d.sz + 1 : 0);
+      zoff = d.bbase + (long long)d.bnx * d.bny * wrapc(d.oz + L, d.bnz);
+      pz = d.pbase + (long long)d.ex * d.ey * (L + g.Gz);
+    };
+    auto issue = [&](int L) {
+      long long zoff, pz;
+      int dz;
+      plane_src(L, zoff, pz, dz);
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        const int p = tid + k * NT;
+        if (bc.dxy[k] < 0) continue;
+        if (!from_store(sc.mode, g.r, bc.dxy[k] & 255, bc.dxy[k] >> 8, dz)) {
+          const double* src = Uin + zoff + bc.xy[k];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) cp_async8(sStg + v * NB + p, src + v * d.bN);
+        } else {
+          const float* src = WhS + pz + bc.pxy[k];
+#pragma unroll
+          for (int c = 0; c < 7; ++c) cp_async4(sStgF + 2 * ((c >> 1) * NB + p) + (c & 1), src + (long long)c * P);
+        }
+      }
+      cp_async_commit();
+    };
+
+    issue(z0 - HB);
     for (int L = z0 - HB; L < z1 + HB; ++L) {
-      // ---- load plane L (sub-domain local z) into ring slot
+      // ---- staged plane L -> primitives in the rings
+      cp_async_wait_all();
+      __syncthreads();
       {
-        float* dst = sW + ((L + 10) % 5) * PL;
-        const int lz = L;
-        const int dz = lz < 0 ? -lz : (lz >= d.sz ? lz - d.sz + 1 : 0);
-        for (int p = tid; p < BX * BY; p += NT) {
-          const int i = p % BX, j = p / BX;
-          const int lx = tx0 - HB + i, ly = ty0 - HB + j;
-          const int dx = lx < 0 ? -lx : (lx >= d.sx ? lx - d.sx + 1 : 0);
-          const int dy = ly < 0 ? -ly : (ly >= d.sy ? ly - d.sy + 1 : 0);
-          const int nout = (dx > 0) + (dy > 0) + (dz > 0);
-          // the sub-domain's view: faces up to depth HB, edges up to r x r (a narrow ragged tile's
-          // box reaches further; those points feed no output and read the stage input instead)
-          const bool inview = (nout == 1 && dx <= HB && dy <= HB && dz <= HB) ||
-                              (nout == 2 && dx <= g.r && dy <= g.r && dz <= g.r);
+        float* r4 = sR4 + ((L + 15) % 5) * 4 * NB;
+        float* r3 = sR3 + ((L + 15) % 3) * 3 * NW;
+        const int dz = L < 0 ? -L : (L >= d.sz ? L - d.sz + 1 : 0);
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+          const int p = tid + k * NT;
+          if (bc.dxy[k] < 0) continue;
           float w[7];
-          if (nout == 0 || sc.mode == 0 || !inview) {
-            // own point, synchronous halo, or a box point no output depends on: the stage input
-            const int gx = wrapc(d.ox + lx, d.bnx), gy = wrapc(d.oy + ly, d.bny), gz = wrapc(d.oz + lz, d.bnz);
-            const long long gi = d.bbase + (long long)gx + (long long)d.bnx * ((long long)gy + (long long)d.bny * gz);
+          if (!from_store(sc.mode, g.r, bc.dxy[k] & 255, bc.dxy[k] >> 8, dz)) {
             double u[5];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) u[v] = Uin[v * d.bN + gi];
-            prims32(u, ph, w);
+            for (int v = 0; v < 5; ++v) u[v] = sStg[v * NB + p];
+            prims32(u, k32, w);
           } else {
-            const long long q = (long long)(lx + g.G) + (long long)d.ex * ((long long)(ly + g.G) + (long long)d.ey * (lz + g.Gz));
-            const float* src = Wh + (long long)hslot * 7 * g.Ptot + d.pbase + q;
 #pragma unroll
-            for (int c = 0; c < 7; ++c) w[c] = src[(long long)c * g.Ptot];
+            for (int c = 0; c < 7; ++c) w[c] = sStgF[2 * ((c >> 1) * NB + p) + (c & 1)];
           }
-#pragma unroll
-          for (int c = 0; c < 7; ++c) dst[c * BY * BX + j * BX + i] = w[c];
+          r4[p] = w[1];
+          r4[NB + p] = w[2];
+          r4[2 * NB + p] = w[3];
+          r4[3 * NB + p] = w[5];
+          const int wi2 = p % BX - (HB - 2), wj2 = p / BX - (HB - 2);
+          if (wi2 >= 0 && wi2 < WX && wj2 >= 0 && wj2 < S::WY) {
+            const int qw = wj2 * WX + wi2;
+            r3[qw] = w[0];
+            r3[NW + qw] = w[4];
+            r3[2 * NW + qw] = w[6];
+          }
         }
       }
       __syncthreads();
+      if (L + 1 < z1 + HB) issue(L + 1);
+
       const int G = L - 2;
-      if (G >= z0 - 2 && G <= z1 + 1) {
-        const float* pl[5];
-#pragma unroll
-        for (int o = 0; o < 5; ++o) pl[o] = sW + ((G - 2 + o + 10) % 5) * PL;  // planes G-2..G+2
-        const bool strips = (G >= z0 && G < z1);
-        float fz[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        // one gradient/flux evaluation at box point (bi, bj) of plane G: kind 0 tile point
-        // (Phi_x, Phi_y to shared memory, Phi_z to the queue), 1 x-strip (Phi_x), 2 y-strip (Phi_y)
-        auto point = [&](int bi, int bj, int kind) {
-          const float* P0 = pl[2];
-          const int q = bj * BX + bi;
-          auto at = [&](const float* plane, int c, int qq) { return plane[c * BY * BX + qq]; };
-          // gradients of u, v, w, T
-          float du[3][3], dT[3];
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const int c = v == 3 ? 5 : 1 + v;
-            const float gx_ = c1x * (at(P0, c, q + 1) - at(P0, c, q - 1)) + c2x * (at(P0, c, q + 2) - at(P0, c, q - 2));
-            const float gy_ = c1y * (at(P0, c, q + BX) - at(P0, c, q - BX)) + c2y * (at(P0, c, q + 2 * BX) - at(P0, c, q - 2 * BX));
-            const float gz_ = c1z * (at(pl[3], c, q) - at(pl[1], c, q)) + c2z * (at(pl[4], c, q) - at(pl[0], c, q));
-            if (v < 3) { du[v][0] = gx_; du[v][1] = gy_; du[v][2] = gz_; }
-            else { dT[0] = gx_; dT[1] = gy_; dT[2] = gz_; }
-          }
-          const float rho = at(P0, 0, q), u = at(P0, 1, q), v = at(P0, 2, q), w = at(P0, 3, q);
-          const float p = at(P0, 4, q), T = at(P0, 5, q), et = at(P0, 6, q);
-          float mu = 1.f;
-          if (ph.visc_law == 1) mu = powf(T, (float)ph.visc_exp);
-          const float div = du[0][0] + du[1][1] + du[2][2];
-          const float vel[3] = {u, v, w};
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            if (kind == 1 && a != 0) continue;
-            if (kind == 2 && a != 1) continue;
-            const float ua = vel[a], mflux = rho * ua;
-            float tau[3];
-#pragma unroll
-            for (int i2 = 0; i2 < 3; ++i2) tau[i2] = mu * (du[a][i2] + du[i2][a]);
-            tau[a] -= (2.f / 3.f) * mu * div;
-            const float qa = u * tau[0] + v * tau[1] + w * tau[2] + kap * mu * dT[a];
-            float f[5];
-            f[0] = -mflux;
-            f[1] = -(mflux * u + (a == 0 ? p : 0.f)) + ire * tau[0];
-            f[2] = -(mflux * v + (a == 1 ? p : 0.f)) + ire * tau[1];
-            f[3] = -(mflux * w + (a == 2 ? p : 0.f)) + ire * tau[2];
-            f[4] = -(et * ua + Href * ua) + ire * qa;
-            if (a == 0) {
-#pragma unroll
-              for (int c = 0; c < 5; ++c) sFx[(c * FY + (bj - HB)) * (FX + 4) + (bi - HB + 2)] = f[c];
-            } else if (a == 1) {
-#pragma unroll
-              for (int c = 0; c < 5; ++c) sFy[(c * (FY + 4) + (bj - HB + 2)) * FX + (bi - HB)] = f[c];
-            } else {
-#pragma unroll
-              for (int c = 0; c < 5; ++c) fz[c] = f[c];
-            }
-          }
-        };
-        point(HB + tx, HB + ty, 0);
-        // strip points: 4 columns x FY rows (x strips) and 4 rows x FX columns (y strips), spread
-        // over all threads of the CTA
-        for (int e = tid; strips && e < 4 * (FX + FY); e += NT) {
-          if (e < 4 * FY) {
-            const int col = e % 4, row = e / 4;
-            point(col < 2 ? (HB - 2 + col) : (HB + FX + col - 2), HB + row, 1);
-          } else {
-            const int e2 = e - 4 * FY, col = e2 % FX, r4 = e2 / FX;
-            point(HB + col, r4 < 2 ? (HB - 2 + r4) : (HB + FY + r4 - 2), 2);
-          }
-        }
-        __syncthreads();
-        // queues: Phi_z of planes G-4..G, dt (Dx Phi_x + Dy Phi_y) of planes G-2..G
+      if (G < z0 - 2 || G > z1 + 1) continue;
+      const float c1x = sK[par][0], c1y = sK[par][1], c1z = sK[par][2];
+      const float c2x = sK[par][3], c2y = sK[par][4], c2z = sK[par][5];
+      const float k1x = sK[par][6], k1y = sK[par][7], k1z = sK[par][8];
+      const float k2x = sK[par][9], k2y = sK[par][10], k2z = sK[par][11];
+      // ---- stage input and Q of the output plane z = G - 2 (in flight during the flux work)
+      const int z = G - 2;
+      const int lx = tx0 + tx, ly = ty0 + ty;
+      const bool outp = z >= z0 && z < z1 && lx < d.sx && ly < d.sy;
+      long long go = 0;
+      double uin[5], qin[5];
+      if (outp) {
+        go = d.bbase + (long long)(d.ox + lx) + (long long)d.bnx * ((long long)(d.oy + ly) + (long long)d.bny * (d.oz + z));
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-#pragma unroll
-          for (int a = 0; a < 4; ++a) phiz[a][c] = phiz[a + 1][c];
-          phiz[4][c] = fz[c];
-          rxy[0][c] = rxy[1][c];
-          rxy[1][c] = rxy[2][c];
-          float r = 0.f;
-          if (strips) {
-            const float* Fx = sFx + (c * FY + ty) * (FX + 4) + tx + 2;
-            const float* Fy = sFy + (c * (FY + 4) + ty + 2) * FX + tx;
-            r = k1x * (Fx[1] - Fx[-1]) + k2x * (Fx[2] - Fx[-2]);
-            r = fmaf(k1y, Fy[FX] - Fy[-FX], r);
-            r = fmaf(k2y, Fy[2 * FX] - Fy[-2 * FX], r);
-          }
-          rxy[2][c] = r;
+          uin[c] = Uin[c * d.bN + go];
+          qin[c] = first ? 0.0 : Q[c * d.bN + go];
         }
-        // output plane z = G - 2
-        const int z = G - 2;
-        const int lx = tx0 + tx, ly = ty0 + ty;
-        if (z >= z0 && z < z1 && lx < d.sx && ly < d.sy) {
-          const long long gi = d.bbase + (long long)(d.ox + lx) + (long long)d.bnx * ((long long)(d.oy + ly) + (long long)d.bny * (d.oz + z));
+      }
+      // ---- fluxes of plane G
+      const float* pl[5];
 #pragma unroll
-          for (int c = 0; c < 5; ++c) {
-            float r = rxy[0][c];
-            r = fmaf(k1z, phiz[3][c] - phiz[1][c], r);
-            r = fmaf(k2z, phiz[4][c] - phiz[0][c], r);
-            const double dtR = (double)r;
-            const double qn = first ? dtR : fma(A, Q[c * d.bN + gi], dtR);
-            if (!last) Q[c * d.bN + gi] = qn;
-            Uout[c * d.bN + gi] = fma(B, qn, Uin[c * d.bN + gi]);
+      for (int o = 0; o < 5; ++o) pl[o] = sR4 + ((G - 2 + o + 15) % 5) * 4 * NB;  // planes G-2..G+2
+      const float* r3c = sR3 + ((G + 15) % 3) * 3 * NW;
+      const bool strips = (G >= z0 && G < z1);
+      float fz[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      // one gradient/flux evaluation at box point (bi, bj) of plane G: kind 0 tile point (Phi_x,
+      // Phi_y to shared memory, Phi_z to registers), 1 x-strip (Phi_x), 2 y-strip (Phi_y)
+      auto point = [&](int bi, int bj, int kind) {
+        const float* P0 = pl[2];
+        const int q = bj * BX + bi;
+        const int qw = (bj - (HB - 2)) * WX + (bi - (HB - 2));
+        float du[3][3], dT[3];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float* f = P0 + v * NB;
+          const float gx_ = c1x * (f[q + 1] - f[q - 1]) + c2x * (f[q + 2] - f[q - 2]);
+          const float gy_ = c1y * (f[q + BX] - f[q - BX]) + c2y * (f[q + 2 * BX] - f[q - 2 * BX]);
+          const float gz_ = c1z * (pl[3][v * NB + q] - pl[1][v * NB + q]) + c2z * (pl[4][v * NB + q] - pl[0][v * NB + q]);
+          if (v < 3) { du[v][0] = gx_; du[v][1] = gy_; du[v][2] = gz_; }
+          else { dT[0] = gx_; dT[1] = gy_; dT[2] = gz_; }
+        }
+        const float u = P0[q], v = P0[NB + q], w = P0[2 * NB + q], T = P0[3 * NB + q];
+        const float rho = r3c[qw], p = r3c[NW + qw], et = r3c[2 * NW + qw];
+        float mu = 1.f;
+        if (k32.law == 1) mu = powf(T, k32.vexp);
+        const float div = du[0][0] + du[1][1] + du[2][2];
+        const float vel[3] = {u, v, w};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (kind == 1 && a != 0) continue;
+          if (kind == 2 && a != 1) continue;
+          const float ua = vel[a], mflux = rho * ua;
+          float tau[3];
+#pragma unroll
+          for (int i2 = 0; i2 < 3; ++i2) tau[i2] = mu * (du[a][i2] + du[i2][a]);
+          tau[a] -= (2.f / 3.f) * mu * div;
+          const float qa = u * tau[0] + v * tau[1] + w * tau[2] + k32.kap * mu * dT[a];
+          float f[5];
+          f[0] = -mflux;
+          f[1] = -(mflux * u + (a == 0 ? p : 0.f)) + k32.ire * tau[0];
+          f[2] = -(mflux * v + (a == 1 ? p : 0.f)) + k32.ire * tau[1];
+          f[3] = -(mflux * w + (a == 2 ? p : 0.f)) + k32.ire * tau[2];
+          f[4] = -(et * ua + k32.Href * ua) + k32.ire * qa;
+          if (a == 0) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) sFx[(c * FY + (bj - HB)) * (FX + 4) + (bi - HB + 2)] = f[c];
+          } else if (a == 1) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) sFy[(c * (FY + 4) + (bj - HB + 2)) * FX + (bi - HB)] = f[c];
+          } else {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) fz[c] = f[c];
           }
+        }
+      };
+      point(HB + tx, HB + ty, 0);
+      // strip points: 4 columns x FY rows (x strips) and 4 rows x FX columns (y strips), spread
+      // over all threads of the CTA
+      for (int e = tid; strips && e < 4 * (FX + FY); e += NT) {
+        if (e < 4 * FY) {
+          const int col = e % 4, row = e / 4;
+          point(col < 2 ? (HB - 2 + col) : (HB + FX + col - 2), HB + row, 1);
+        } else {
+          const int e2 = e - 4 * FY, col = e2 % FX, r4 = e2 / FX;
+          point(HB + col, r4 < 2 ? (HB - 2 + r4) : (HB + FY + r4 - 2), 2);
         }
       }
       __syncthreads();
+      // ---- dt R queue: Phi_z(G) enters planes G-2..G+2 with the CD4 weights, the in-plane
+      // divergence enters plane G; plane G-2 is then complete
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        float r = 0.f;
+        if (strips) {
+          const float* Fx = sFx + (c * FY + ty) * (FX + 4) + tx + 2;
+          const float* Fy = sFy + (c * (FY + 4) + ty + 2) * FX + tx;
+          r = k1x * (Fx[1] - Fx[-1]) + k2x * (Fx[2] - Fx[-2]);
+          r = fmaf(k1y, Fy[FX] - Fy[-FX], r);
+          r = fmaf(k2y, Fy[2 * FX] - Fy[-2 * FX], r);
+        }
+        const float out = fmaf(k2z, fz[c], acc[0][c]);
+        acc[0][c] = fmaf(k1z, fz[c], acc[1][c]);
+        acc[1][c] = acc[2][c] + r;
+        acc[2][c] = fmaf(-k1z, fz[c], acc[3][c]);
+        acc[3][c] = -k2z * fz[c];
+        if (outp) {
+          const double dtR = f2d_fast(out);
+          const double qn = first ? dtR : fma(A, qin[c], dtR);
+          if (!last) Q[c * d.bN + go] = qn;
+          Uout[c * d.bN + go] = fma(B, qn, uin[c]);
+        }
+      }
     }
   }
 }
@@ -311,15 +435,17 @@ int launch_halo_prims(const Geometry& g, const Physics& ph, const StepSched& sc,
                       const Timer* tm) {
   cudaStream_t st = (cudaStream_t)stream;
   if (nhalo <= 0) return 0;
+  const unsigned nb = (unsigned)((nhalo + 255) / 256);
   if (tm) tm->rec(tm->self, 0, 1);
-  k_halo_prims<<<(unsigned)((nhalo + 255) / 256), 256, 0, st>>>(g, ph, sc, ring, subs, (const int2*)halo, nhalo, Wh, s);
+  if (s == 2) k_halo_prims<2><<<nb, 256, 0, st>>>(g, ph, sc, ring, subs, (const int2*)halo, nhalo, Wh);
+  else k_halo_prims<5><<<nb, 256, 0, st>>>(g, ph, sc, ring, subs, (const int2*)halo, nhalo, Wh);
   if (tm) tm->rec(tm->self, 0, 0);
   if (launches) *launches += 1;
   return (int)cudaGetLastError();
 }
 
 template <int FX, int FY>
-static int fused_impl(const Geometry& g, const Physics& ph, const StepSched& sc, const FusedLaunch& a, cudaStream_t st) {
+static int fused_prepare(int* blocks_per_sm) {
   const size_t sm = FusedSmem<FX, FY>::bytes;
   static bool attr_set = false;  // per process: the attribute is a property of the kernel
   if (!attr_set) {
@@ -327,9 +453,26 @@ static int fused_impl(const Geometry& g, const Physics& ph, const StepSched& sc,
     if (e != cudaSuccess) return (int)e;
     attr_set = true;
   }
-  k_stage_fused<FX, FY><<<a.grid, FX * FY, sm, st>>>(g, ph, sc, a.Uin, a.Uout, a.ring, a.in_ring, a.out_ring, a.Q,
-                                                    a.subs, a.work, a.nwork, a.Wh, a.stage, a.A, a.B, a.dt, a.first,
-                                                    a.last);
+  if (blocks_per_sm) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_stage_fused<FX, FY>, FX * FY, sm);
+    if (e != cudaSuccess) return (int)e;
+  }
+  return 0;
+}
+
+int fused_blocks_per_sm(int fy, int* blocks) {
+  if (fy == 4) return fused_prepare<32, 4>(blocks);
+  if (fy == 16) return fused_prepare<32, 16>(blocks);
+  return fused_prepare<32, 8>(blocks);
+}
+
+template <int FX, int FY>
+static int fused_impl(const Geometry& g, const Physics& ph, const StepSched& sc, const FusedLaunch& a, cudaStream_t st) {
+  const int rc = fused_prepare<FX, FY>(nullptr);
+  if (rc) return rc;
+  k_stage_fused<FX, FY><<<a.grid, FX * FY, FusedSmem<FX, FY>::bytes, st>>>(
+      g, ph, sc, a.Uin, a.Uout, a.ring, a.in_ring, a.out_ring, a.Q, a.subs, a.work, a.nwork, a.Wh, a.stage, a.A, a.B,
+      a.dt, a.first, a.last);
   return (int)cudaGetLastError();
 }
 

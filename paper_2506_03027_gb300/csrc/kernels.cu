@@ -148,13 +148,86 @@ __device__ __forceinline__ T cdiff(const T* __restrict__ f, long long q, long lo
   return d;
 }
 
-template <typename T>
+// Curvilinear flux point (App. A, Eq. A1-A4 with a time-invariant grid): gradients in index
+// space (c1, c2 of the block are the index-space coefficients), mapped to physical gradients by
+// d phi / d x_j = J sum_k (metric row k)_j d phi / d xi_k; combined fluxes along each index
+// direction a with the metric row m_a = (d xi_a / dx, d xi_a / dy, d xi_a / dz) / J:
+//   Phi_a = -[rho U^, rho u U^ + m_x p, rho v U^ + m_y p, rho w U^ + m_z p, (rho E + p) U^]
+//           + (1/Re) [0, m . tau_1, m . tau_2, m . tau_3, m . b],   U^ = m . u.
+// The grid is extruded in z: rows xi = (m0, m1, 0), eta = (m2, m3, 0), zeta = (0, 0, m4).
+template <typename T, int ND>
+__device__ __forceinline__ void flux_curvilinear(const Geometry& g, const Physics& ph, const SubDev& d,
+                                                 const T* __restrict__ W, T* __restrict__ out, long long q, int ci,
+                                                 int cj, int ck, bool ox, bool oy, bool oz, int nout) {
+  const long long P = g.Ptot;
+  const int r = g.r;
+  const long long sty = d.ex, stz = (long long)d.ex * d.ey;
+  const int gx = wrapc(d.ox + ci, d.bnx), gy = wrapc(d.oy + cj, d.bny), gz = wrapc(d.oz + ck, d.bnz);
+  const long long gp = (long long)gx + (long long)d.bnx * ((long long)gy + (long long)d.bny * gz);
+  const double* M = g.metric + d.mbase + gp;
+  const T m[3][3] = {{(T)M[0], (T)M[d.bN], (T)0}, {(T)M[2 * d.bN], (T)M[3 * d.bN], (T)0}, {(T)0, (T)0, (T)M[4 * d.bN]}};
+  const T J = (T)M[6 * d.bN];
+  const T rho = W[q], u = W[P + q], v = W[2 * P + q], w = W[3 * P + q], p = W[4 * P + q];
+  const T et = W[6 * P + q];
+  const T vel[3] = {u, v, w};
+  T tau[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  T bq[3] = {0, 0, 0};
+  if (g.viscous) {
+    const long long st[3] = {1, sty, stz};
+    T dxi[4][3];  // d (u, v, w, T) / d xi_k
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const T c1 = (T)d.c1[k], c2 = (T)d.c2[k];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        dxi[c][k] = (k < ND) ? cdiff(W + (c == 3 ? 5 : 1 + c) * P, q, st[k], c1, c2, r) : (T)0;
+    }
+    T dx[4][3];  // physical gradients
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) dx[c][j] = J * (m[0][j] * dxi[c][0] + m[1][j] * dxi[c][1] + m[2][j] * dxi[c][2]);
+    T mu = (T)1;
+    if (ph.visc_law == 1) mu = (T)pow((double)W[5 * P + q], ph.visc_exp);
+    const T div = dx[0][0] + dx[1][1] + dx[2][2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) tau[i][j] = mu * (dx[i][j] + dx[j][i]) - (i == j ? (T)(2.0 / 3.0) * mu * div : (T)0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) bq[i] = u * tau[i][0] + v * tau[i][1] + w * tau[i][2] + (T)ph.kappa * mu * dx[3][i];
+  }
+  const T ire = (T)ph.ire;
+#pragma unroll
+  for (int a = 0; a < ND; ++a) {
+    if (nout == 1) {
+      if ((a == 0 && !ox) || (a == 1 && !oy) || (a == 2 && !oz)) continue;
+    }
+    const T Uc = m[a][0] * vel[0] + m[a][1] * vel[1] + m[a][2] * vel[2];
+    const T mflux = rho * Uc;
+    T f[5];
+    f[0] = -mflux;
+    f[1] = -(mflux * u + m[a][0] * p);
+    f[2] = -(mflux * v + m[a][1] * p);
+    f[3] = -(mflux * w + m[a][2] * p);
+    f[4] = std::is_same<T, float>::value ? -(et * Uc + (T)ph.H_ref * Uc) : -(et * Uc);
+    if (g.viscous) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) f[1 + c] += ire * (m[a][0] * tau[0][c] + m[a][1] * tau[1][c] + m[a][2] * tau[2][c]);
+      f[4] += ire * (m[a][0] * bq[0] + m[a][1] * bq[1] + m[a][2] * bq[2]);
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[(long long)(a * 5 + c) * P + q] = f[c];
+  }
+}
+
+template <typename T, int ND>
 __global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubDev* __restrict__ subs,
                                               const T* __restrict__ Wp, T* __restrict__ Phi) {
   const int sid = blockIdx.y;
   const SubDev d = subs[sid];
   const int r = g.r;
-  const int rz = (g.ndim == 3) ? r : 0;
+  const int rz = (ND == 3) ? r : 0;
   const int fx = d.sx + 2 * r, fy = d.sy + 2 * r, fz = d.sz + 2 * rz;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)fx * fy * fz) return;
@@ -167,6 +240,10 @@ __global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubD
   const long long q = (long long)(ci + g.G) + sty * (cj + g.G) + stz * (ck + g.Gz);
   const long long P = g.Ptot;
   const T* W = Wp + d.pbase;
+  if (d.mbase >= 0) {
+    flux_curvilinear<T, ND>(g, ph, d, W, Phi + d.pbase, q, ci, cj, ck, ox, oy, oz, nout);
+    return;
+  }
   const T rho = W[q], u = W[P + q], v = W[2 * P + q], w = W[3 * P + q], p = W[4 * P + q];
   const T et = W[6 * P + q];
   const T vel[3] = {u, v, w};
@@ -176,7 +253,8 @@ __global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubD
   T mu = (T)1;
   if (g.viscous) {
     const long long st[3] = {1, sty, stz};
-    for (int b = 0; b < g.ndim; ++b) {
+#pragma unroll
+    for (int b = 0; b < ND; ++b) {
       const T c1 = (T)d.c1[b], c2 = (T)d.c2[b];
       du[0][b] = cdiff(W + P, q, st[b], c1, c2, r);
       du[1][b] = cdiff(W + 2 * P, q, st[b], c1, c2, r);
@@ -188,7 +266,8 @@ __global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubD
   const T div = du[0][0] + du[1][1] + du[2][2];
   const T ire = (T)ph.ire, kap = (T)ph.kappa;
   T* out = Phi + d.pbase;
-  for (int a = 0; a < g.ndim; ++a) {
+#pragma unroll
+  for (int a = 0; a < ND; ++a) {
     if (nout == 1) {
       if ((a == 0 && !ox) || (a == 1 && !oy) || (a == 2 && !oz)) continue;
     }
@@ -227,7 +306,7 @@ __global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubD
 
 // ------------------------------------------------------------------------------- k_rk
 
-template <typename T>
+template <typename T, int ND>
 __global__ void __launch_bounds__(512) k_rk(Geometry g, Physics ph, StepSched sc, const SubDev* __restrict__ subs,
                                             const T* __restrict__ Phi, const double* __restrict__ Uin0,
                                             double* __restrict__ Uout0, const double* __restrict__ ring, int in_ring,
@@ -259,12 +338,13 @@ __global__ void __launch_bounds__(512) k_rk(Geometry g, Physics ph, StepSched sc
     const T* Fx = F + (long long)c * P;
     T acc = k1[0] * (Fx[q + 1] - Fx[q - 1]);
     if (g.r == 2) acc = fma(k2[0], Fx[q + 2] - Fx[q - 2], acc);
-    for (int a = 1; a < g.ndim; ++a) {
+#pragma unroll
+    for (int a = 1; a < ND; ++a) {
       const T* Fa = F + (long long)(a * 5 + c) * P;
       acc = fma(k1[a], Fa[q + st[a]] - Fa[q - st[a]], acc);
       if (g.r == 2) acc = fma(k2[a], Fa[q + 2 * st[a]] - Fa[q - 2 * st[a]], acc);
     }
-    const double dtR = (double)acc;
+    const double dtR = (d.mbase >= 0) ? (double)acc * g.metric[d.mbase + 6 * d.bN + (gi - d.bbase)] : (double)acc;
     const double qn = first ? dtR : fma(A, Q[c * d.bN + gi], dtR);
     if (!last) Q[c * d.bN + gi] = qn;
     Uout[c * d.bN + gi] = fma(B, qn, Uin[c * d.bN + gi]);
@@ -289,9 +369,15 @@ static int stage_impl(const Geometry& g, const Physics& ph, const StepSched& sc,
   if (a.nhalo > 0)
     TIMED(tm, 0, (k_view_halo<T><<<nblk(a.nhalo, B), B, 0, st>>>(g, ph, sc, a.Uin, a.ring, a.in_ring, a.subs,
                                                                  (const int2*)a.halo, a.nhalo, (T*)a.Wp, a.stage, a.s)));
-  TIMED(tm, 1, (k_flux<T><<<gf, B, 0, st>>>(g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
-  TIMED(tm, 2, (k_rk<T><<<gr, B, 0, st>>>(g, ph, sc, a.subs, (const T*)a.Phi, a.Uin, a.Uout, a.ring, a.in_ring,
-                                          a.out_ring, a.Q, a.A, a.B, a.dt, a.first, a.last)));
+  if (g.ndim == 3) {
+    TIMED(tm, 1, (k_flux<T, 3><<<gf, B, 0, st>>>(g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
+    TIMED(tm, 2, (k_rk<T, 3><<<gr, B, 0, st>>>(g, ph, sc, a.subs, (const T*)a.Phi, a.Uin, a.Uout, a.ring, a.in_ring,
+                                               a.out_ring, a.Q, a.A, a.B, a.dt, a.first, a.last)));
+  } else {
+    TIMED(tm, 1, (k_flux<T, 2><<<gf, B, 0, st>>>(g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
+    TIMED(tm, 2, (k_rk<T, 2><<<gr, B, 0, st>>>(g, ph, sc, a.subs, (const T*)a.Phi, a.Uin, a.Uout, a.ring, a.in_ring,
+                                               a.out_ring, a.Q, a.A, a.B, a.dt, a.first, a.last)));
+  }
   if (launches) *launches += a.nhalo > 0 ? 4 : 3;
   return (int)cudaGetLastError();
 }
@@ -305,114 +391,233 @@ int launch_stage(const Geometry& g, const Physics& ph, const StepSched& sc, cons
 
 // ------------------------------------------------------------------------------- k_filter
 
-// One thread per (variable, line segment of one sub-domain).  Lines along `axis`; the two other
-// axes are f1 (x unless axis is x) and f2.  Right side: sum_n (a_n/2)(f_{i+n} + f_{i-n}) over an
-// 11-point window; Dirichlet closure f^_{-1} = f_{-1}, f^_L = f_L; forward elimination stores
-// the intermediate values in the output line, back substitution overwrites them.
-template <typename T>
-__global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, FilterLaunch f, int axis) {
+// One CTA per (variable, line segment of one sub-domain, group of LN lines); one thread per line
+// in the solve.  Lines along `axis`; the two other axes are f1 (x unless axis is x) and f2.  The
+// CTA first stages the 11-point windows of all its lines -- own values, and halo values by the
+// schedule (SA: live neighbour; AT: extrapolation to t_{n+1} with the weights c(k+1) in FP64;
+// AS: the latest delayed level) -- in shared memory with coalesced loads (consecutive threads
+// along the line for the x pass, across lines for y and z), solves each line from there, and
+// stores the result with the same pattern.  Right side: sum_n (a_n/2)(f_{i+n} + f_{i-n});
+// Dirichlet closure f^_{-1} = f_{-1}, f^_L = f_L; Thomas factors precomputed per line length.
+struct FilterTile {
+  int LN;  // lines per CTA
+  int TW;  // row stride in doubles (odd: 64-bit accesses of a warp's rows hit distinct banks)
+};
+
+__host__ __device__ inline FilterTile filter_tile(int Lmax) {
+  FilterTile t;
+  t.TW = (Lmax + 10) | 1;
+  t.LN = 128;
+  while (t.LN > 32 && (size_t)(t.LN + 1) * t.TW * 12 > 200 * 1024) t.LN /= 2;
+  return t;
+}
+
+__host__ __device__ inline size_t filter_smem_bytes(int Lmax, int precision) {
+  const FilterTile t = filter_tile(Lmax);
+  return (size_t)(t.LN + 1) * t.TW * 8 + (precision == 1 ? (size_t)t.LN * (Lmax + 1) * 4 : 0);
+}
+
+template <typename T, int axis>
+__global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, FilterLaunch f) {
   sc = resolve(sc);
-  f.Uin = ring_or(f.Uin, f.in_ring, f.ring, sc, 0);
-  f.Uout = const_cast<double*>(ring_or(f.Uout, f.out_ring, f.ring, sc, 1));
-  const int f1 = (axis == 0) ? 1 : 0;
-  const int f2 = (axis == 2) ? 1 : 2;
+  constexpr bool F32 = std::is_same<T, float>::value;
+  const double* __restrict__ Uin = ring_or(f.Uin, f.in_ring, f.ring, sc, 0);
+  double* __restrict__ Uout = const_cast<double*>(ring_or(f.Uout, f.out_ring, f.ring, sc, 1));
+  constexpr int f1 = (axis == 0) ? 1 : 0;
+  constexpr int f2 = (axis == 2) ? 1 : 2;
   const int n[3] = {f.nx, f.ny, f.nz};
   const long long strides[3] = {1, f.nx, (long long)f.nx * f.ny};
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = 5LL * f.P[axis] * n[f1] * n[f2];
-  if (t >= total) return;
-  long long rest = t;
-  const int t1 = (int)(rest % n[f1]); rest /= n[f1];
-  const int t2 = (int)(rest % n[f2]); rest /= n[f2];
-  const int seg = (int)(rest % f.P[axis]);
-  const int var = (int)(rest / f.P[axis]);
-  int sidx[3];
-  sidx[axis] = seg;
-  sidx[f1] = f.owner[f1][t1];
-  sidx[f2] = f.owner[f2][t2];
-  const int sid = f.sid0 + sidx[0] + f.P[0] * (sidx[1] + f.P[1] * sidx[2]);
+  const FilterTile tl = filter_tile(f.Lmax);
+  const int LN = tl.LN, TW = tl.TW;
+  extern __shared__ __align__(16) double fsm[];
+  double* tile = fsm;                                              // [LN][TW]: positions -5 .. len+4
+  long long* sPos = reinterpret_cast<long long*>(fsm + (size_t)LN * TW);  // [TW]: offsets of the positions
+  float* fd = reinterpret_cast<float*>(fsm + (size_t)(LN + 1) * TW);      // FP32 form: [LN][Lmax+1]
+
+  const long long nl = (long long)n[f1] * n[f2];
+  const int groups = (int)((nl + LN - 1) / LN);
+  int b = blockIdx.x;
+  const int grp = b % groups;
+  b /= groups;
+  const int seg = b % f.P[axis];
+  const int var = b / f.P[axis];
   const int off = f.axis_off[axis][seg], len = f.axis_len[axis][seg];
+  const int W = len + 10;
+  const long long l0 = (long long)grp * LN;
+  const int nlines = (int)min((long long)LN, nl - l0);
   const long long st = strides[axis];
-  const long long base = f.bbase + (long long)var * f.bN + (long long)t1 * strides[f1] + (long long)t2 * strides[f2];
-  const double* Uin = f.Uin;
-  const int kl = (sc.mode == 0) ? 0 : face_delay(sc, sid, 2 * axis);
-  const int kr = (sc.mode == 0) ? 0 : face_delay(sc, sid, 2 * axis + 1);
   const long long lvN = 5 * g.N;
-  // value at line position i (halo for i < 0 or i >= len)
-  auto fetch = [&](int i) -> double {
-    const int c = wrapc(off + i, n[axis]);
-    const long long gi = base + (long long)c * st;
-    if ((i >= 0 && i < len) || sc.mode == 0) return Uin[gi];
-    const int kd = i < 0 ? kl : kr;
-    if (sc.mode == 2) return f.ring[(long long)((sc.n - kd) % sc.R) * lvN + gi];
-    double acc = 0.0;  // extrapolation to t_{n+1} with weights c(k+1), in FP64
-    for (int l = 0; l < sc.C; ++l)
-      acc = fma(__ldg(sc.Wf + kd * sc.C + l), f.ring[(long long)((sc.n - kd - l) % sc.R) * lvN + gi], acc);
-    return acc;
-  };
-  const T al = (T)f.alpha;
-  const double* cp = f.thomas + (long long)len * 2 * f.Lmax;
-  const double* im = cp + f.Lmax;
-  double* out = f.Uout + base + (long long)off * st;
-  if (!std::is_same<T, float>::value) {
-    // FP64: the system as written, alpha f^_{i-1} + f^_i + alpha f^_{i+1} = rhs_i
-    T win[11];
-#pragma unroll
-    for (int m = 0; m < 11; ++m) win[m] = (T)fetch(m - 5);
-    const T hm1 = (T)fetch(-1), hpl = (T)fetch(len);
-    T dprev = (T)0;
-    for (int i = 0; i < len; ++i) {
-      T rhs = (T)f.h[0] * win[5];
-#pragma unroll
-      for (int m = 1; m <= 5; ++m) rhs = fma((T)f.h[m], win[5 + m] + win[5 - m], rhs);
-      if (i == 0) rhs -= al * hm1;
-      if (i == len - 1) rhs -= al * hpl;
-      const T dcur = (i == 0 ? rhs : rhs - al * dprev) * (T)im[i];
-      out[(long long)i * st] = (double)dcur;
-      dprev = dcur;
-#pragma unroll
-      for (int m = 0; m < 10; ++m) win[m] = win[m + 1];
-      win[10] = (T)fetch(i + 6);
+  // per-CTA tables: line bases and face delays, offsets of the window positions along the line,
+  // and ring-level offsets per (delay, level)
+  __shared__ long long sBase[128];
+  __shared__ long long sLev[(CFS_MAX_DELAY + 2) * CFS_MAX_LEVELS];
+  __shared__ int sKd[2][128];
+  for (int t = threadIdx.x; t < nlines; t += blockDim.x) {
+    const long long t12 = l0 + t;
+    const int t1 = (int)(t12 % n[f1]), t2 = (int)(t12 / n[f1]);
+    sBase[t] = f.bbase + (long long)var * f.bN + (long long)t1 * strides[f1] + (long long)t2 * strides[f2];
+    int kl = 0, kr = 0;
+    if (sc.mode != 0) {
+      int sidx[3];
+      sidx[axis] = seg;
+      sidx[f1] = f.owner[f1][t1];
+      sidx[f2] = f.owner[f2][t2];
+      const int sid = f.sid0 + sidx[0] + f.P[0] * (sidx[1] + f.P[1] * sidx[2]);
+      kl = face_delay(sc, sid, 2 * axis);
+      kr = face_delay(sc, sid, 2 * axis + 1);
     }
-    T xnext = dprev;
-    for (int i = len - 2; i >= 0; --i) {
-      const T x = (T)out[(long long)i * st] - (T)cp[i] * xnext;
-      out[(long long)i * st] = (double)x;
-      xnext = x;
-    }
-  } else {
-    // FP32 form: solve for the increment d = f^ - f.  Its right side is
-    // (a_1/2 - alpha) D_1 + sum_{n>=2} (a_n/2) D_n with D_n = f_{i+n} + f_{i-n} - 2 f_i (exact
-    // algebra, using sum a_n = 1 + 2 alpha), the Dirichlet closure becomes d = 0 at the first halo
-    // point, and the values enter as FP32 offsets from an FP64 reference of the line, so FP32
-    // rounding never acts on the full magnitude of the state.
-    const double ref = fetch(0);
-    auto off32 = [&](int i) -> float { return (float)(fetch(i) - ref); };
-    float win[11];
-#pragma unroll
-    for (int m = 0; m < 11; ++m) win[m] = off32(m - 5);
-    const float b1 = (float)f.b1;
-    float dprev = 0.f;
-    for (int i = 0; i < len; ++i) {
-      const float c2 = 2.f * win[5];
-      float rhs = b1 * (win[6] + win[4] - c2);
-#pragma unroll
-      for (int m = 2; m <= 5; ++m) rhs = fmaf((float)f.h[m], win[5 + m] + win[5 - m] - c2, rhs);
-      const float dcur = (i == 0 ? rhs : rhs - (float)f.alpha * dprev) * (float)im[i];
-      out[(long long)i * st] = (double)dcur;
-      dprev = dcur;
-#pragma unroll
-      for (int m = 0; m < 10; ++m) win[m] = win[m + 1];
-      win[10] = off32(i + 6);
-    }
-    float xnext = dprev;
-    out[(long long)(len - 1) * st] = Uin[base + (long long)wrapc(off + len - 1, n[axis]) * st] + (double)xnext;
-    for (int i = len - 2; i >= 0; --i) {
-      const float x = (float)out[(long long)i * st] - (float)cp[i] * xnext;
-      out[(long long)i * st] = Uin[base + (long long)(off + i) * st] + (double)x;
-      xnext = x;
+    sKd[0][t] = kl;
+    sKd[1][t] = kr;
+  }
+  for (int t = threadIdx.x; t < W; t += blockDim.x) sPos[t] = (long long)wrapc(off + t - 5, n[axis]) * st;
+  if (sc.mode != 0) {
+    const int nk = (int)min((long long)CFS_MAX_DELAY + 1, max(sc.cap, 0LL) + 1);
+    for (int t = threadIdx.x; t < nk * sc.C; t += blockDim.x) {
+      const int kd = t / sc.C, l = t % sc.C;
+      sLev[t] = (long long)((sc.n - kd - l) % sc.R) * lvN;
     }
   }
+  __syncthreads();
+
+  // ---- stage the windows: value at window slot i (position i - 5) of line `line`
+  auto stage = [&](int line, int i) {
+    const int pos = i - 5;
+    const long long gi = sBase[line] + sPos[i];
+    double* dst = tile + line * TW + i;
+    if ((pos >= 0 && pos < len) || sc.mode == 0) {
+      cp_async8(dst, Uin + gi);
+    } else {
+      const int kd = sKd[pos < 0 ? 0 : 1][line];
+      if (sc.mode == 2) {
+        cp_async8(dst, f.ring + sLev[kd * sc.C] + gi);
+      } else {
+        double v = 0.0;  // extrapolation to t_{n+1} with weights c(k+1), in FP64
+        for (int l = 0; l < sc.C; ++l) v = fma(__ldg(sc.Wf + kd * sc.C + l), f.ring[sLev[kd * sc.C + l] + gi], v);
+        *dst = v;
+      }
+    }
+  };
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  if (axis == 0) {
+    // own points: a warp per line, lanes along it (contiguous in memory); the 10 window points
+    // outside the segment: a thread per line, so that no warp mixes copies with extrapolations
+    for (int line = warp; line < nlines; line += nwarp)
+      for (int i = 5 + lane; i < 5 + len; i += 32) cp_async8(tile + line * TW + i, Uin + sBase[line] + sPos[i]);
+    for (int line = threadIdx.x; line < nlines; line += blockDim.x)
+      for (int h = 0; h < 10; ++h) stage(line, h < 5 ? h : len + h);
+  } else {  // threads across lines (consecutive x)
+    for (int line = threadIdx.x; line < nlines; line += blockDim.x)
+      for (int i = 0; i < W; ++i) stage(line, i);
+  }
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+
+  // ---- one line per thread
+  const int line = threadIdx.x;
+  if (line < nlines) {
+    double* row = tile + line * TW;
+    const double* cp = f.thomas + (long long)len * 2 * f.Lmax;
+    const double* im = cp + f.Lmax;
+    if (!F32) {
+      // FP64: the system as written, alpha f^_{i-1} + f^_i + alpha f^_{i+1} = rhs_i; the forward
+      // sweep parks d_i in slot i (position i - 5, no longer read), back substitution overwrites
+      const double al = f.alpha;
+      double win[11];
+#pragma unroll
+      for (int m = 0; m < 11; ++m) win[m] = row[m];
+      const double hm1 = row[4], hpl = row[len + 5];
+      double dprev = 0.0;
+      #pragma unroll 4
+      for (int i = 0; i < len; ++i) {
+        double rhs = f.h[0] * win[5];
+#pragma unroll
+        for (int m = 1; m <= 5; ++m) rhs = fma(f.h[m], win[5 + m] + win[5 - m], rhs);
+        if (i == 0) rhs -= al * hm1;
+        if (i == len - 1) rhs -= al * hpl;
+        const double dcur = (i == 0 ? rhs : rhs - al * dprev) * __ldg(im + i);
+        row[i] = dcur;
+        dprev = dcur;
+#pragma unroll
+        for (int m = 0; m < 10; ++m) win[m] = win[m + 1];
+        if (i + 11 < W) win[10] = row[i + 11];
+      }
+      double xnext = dprev;
+      #pragma unroll 4
+      for (int i = len - 2; i >= 0; --i) {
+        const double x = row[i] - __ldg(cp + i) * xnext;
+        row[i] = x;
+        xnext = x;
+      }
+    } else {
+      // FP32 form: solve for the increment d = f^ - f.  Its right side is
+      // (a_1/2 - alpha) D_1 + sum_{n>=2} (a_n/2) D_n with D_n = f_{i+n} + f_{i-n} - 2 f_i (exact
+      // algebra, using sum a_n = 1 + 2 alpha), the Dirichlet closure becomes d = 0 at the first
+      // halo point, and the values enter as FP32 offsets from an FP64 reference of the line, so
+      // FP32 rounding never acts on the full magnitude of the state.  Conversions run on the
+      // integer pipe; the result U + d (FP64) replaces the value in slot i + 5.
+      float* frow = fd + line * (f.Lmax + 1);
+      const double ref = row[5];
+      const float rh = d2f_fast(ref), rl = dev_fast(ref, rh, 0.f);
+      float win[11];
+#pragma unroll
+      for (int m = 0; m < 11; ++m) win[m] = dev_fast(row[m], rh, rl);
+      const float b1 = (float)f.b1, al32 = (float)f.alpha;
+      float hm[6];
+#pragma unroll
+      for (int m = 2; m <= 5; ++m) hm[m] = (float)f.h[m];
+      float dprev = 0.f;
+      #pragma unroll 4
+      for (int i = 0; i < len; ++i) {
+        const float c2 = 2.f * win[5];
+        float rhs = b1 * (win[6] + win[4] - c2);
+#pragma unroll
+        for (int m = 2; m <= 5; ++m) rhs = fmaf(hm[m], win[5 + m] + win[5 - m] - c2, rhs);
+        const float dcur = (i == 0 ? rhs : rhs - al32 * dprev) * d2f_fast(__ldg(im + i));
+        frow[i] = dcur;
+        dprev = dcur;
+#pragma unroll
+        for (int m = 0; m < 10; ++m) win[m] = win[m + 1];
+        if (i + 11 < W) win[10] = dev_fast(row[i + 11], rh, rl);
+      }
+      float xnext = dprev;
+      row[len + 4] += f2d_fast(xnext);
+      #pragma unroll 4
+      for (int i = len - 2; i >= 0; --i) {
+        const float x = frow[i] - d2f_fast(__ldg(cp + i)) * xnext;
+        row[i + 5] += f2d_fast(x);
+        xnext = x;
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- store the own points
+  const int slot0 = F32 ? 5 : 0;
+  if (axis == 0) {
+    for (int ln = warp; ln < nlines; ln += nwarp)
+      for (int i = lane; i < len; i += 32) Uout[sBase[ln] + sPos[i + 5]] = tile[ln * TW + slot0 + i];
+  } else {
+    for (int ln = threadIdx.x; ln < nlines; ln += blockDim.x)
+      for (int i = 0; i < len; ++i) Uout[sBase[ln] + sPos[i + 5]] = tile[ln * TW + slot0 + i];
+  }
+}
+
+int filter_prepare(int Lmax, int precision) {
+  const size_t sm = filter_smem_bytes(Lmax, precision);
+  if (sm > 227 * 1024) return (int)cudaErrorInvalidValue;
+  const int b = (int)sm;
+  cudaError_t e = cudaSuccess;
+  if (precision == 1) {
+    e = cudaFuncSetAttribute(k_filter<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_filter<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_filter<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  } else {
+    e = cudaFuncSetAttribute(k_filter<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_filter<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_filter<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  }
+  return (int)e;
 }
 
 int launch_filter(const Geometry& g, const StepSched& sc, const FilterLaunch& f, int axis, int precision,
@@ -420,10 +625,22 @@ int launch_filter(const Geometry& g, const StepSched& sc, const FilterLaunch& f,
   const int n[3] = {f.nx, f.ny, f.nz};
   const int f1 = (axis == 0) ? 1 : 0;
   const int f2 = (axis == 2) ? 1 : 2;
-  const long long total = 5LL * f.P[axis] * n[f1] * n[f2];
+  const FilterTile tl = filter_tile(f.Lmax);
+  const long long nl = (long long)n[f1] * n[f2];
+  const unsigned nb = (unsigned)(5LL * f.P[axis] * ((nl + tl.LN - 1) / tl.LN));
+  const size_t sm = filter_smem_bytes(f.Lmax, precision);
   cudaStream_t st = (cudaStream_t)stream;
-  if (precision == 1) TIMED(tm, 3, (k_filter<float><<<nblk(total, 128), 128, 0, st>>>(g, sc, f, axis)));
-  else TIMED(tm, 3, (k_filter<double><<<nblk(total, 128), 128, 0, st>>>(g, sc, f, axis)));
+  if (tm) tm->rec(tm->self, 3, 1);
+  if (precision == 1) {
+    if (axis == 0) k_filter<float, 0><<<nb, 128, sm, st>>>(g, sc, f);
+    else if (axis == 1) k_filter<float, 1><<<nb, 128, sm, st>>>(g, sc, f);
+    else k_filter<float, 2><<<nb, 128, sm, st>>>(g, sc, f);
+  } else {
+    if (axis == 0) k_filter<double, 0><<<nb, 128, sm, st>>>(g, sc, f);
+    else if (axis == 1) k_filter<double, 1><<<nb, 128, sm, st>>>(g, sc, f);
+    else k_filter<double, 2><<<nb, 128, sm, st>>>(g, sc, f);
+  }
+  if (tm) tm->rec(tm->self, 3, 0);
   if (launches) *launches += 1;
   return (int)cudaGetLastError();
 }
@@ -441,15 +658,16 @@ __global__ void __launch_bounds__(256) k_diag(DiagBlock b, const double* __restr
   const int ndim = b.nz > 1 ? 3 : 2;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < b.bN; i += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(i % b.nx), y = (int)((i / b.nx) % b.ny), z = (int)(i / ((long long)b.nx * b.ny));
+    const double dV = b.M ? b.M[5 * b.bN + i] : b.dV;  // cell volume (J^-1 on a curvilinear grid)
     double u[5];
     for (int v = 0; v < 5; ++v) {
       u[v] = U[b.bbase + v * b.bN + i];
       if (!isfinite(u[v])) acc[7] = 1.0;
-      acc[2 + v] += u[v] * b.dV;
+      acc[2 + v] += u[v] * dV;
     }
     const double rho = u[0];
     const double vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
-    acc[0] += 0.5 * rho * (vx * vx + vy * vy + vz * vz);
+    acc[0] += 0.5 * rho * (vx * vx + vy * vy + vz * vz) * dV;
     // vorticity by the CD scheme
     double dv[3][3];
     for (int c = 0; c < 3; ++c)
@@ -462,8 +680,18 @@ __global__ void __launch_bounds__(256) k_diag(DiagBlock b, const double* __restr
                            vel_at(U, b, x - 2 * ex, y - 2 * ey, z - 2 * ez, c));
         dv[c][a] = dd;
       }
+    if (b.M) {  // index-space derivatives -> physical: d/dx_j = J sum_k (metric row k)_j d/dxi_k
+      const double J = b.M[6 * b.bN + i];
+      const double m[3][3] = {{b.M[i], b.M[b.bN + i], 0.0}, {b.M[2 * b.bN + i], b.M[3 * b.bN + i], 0.0},
+                              {0.0, 0.0, b.M[4 * b.bN + i]}};
+      double dp[3][3];
+      for (int c = 0; c < 3; ++c)
+        for (int j = 0; j < 3; ++j) dp[c][j] = J * (m[0][j] * dv[c][0] + m[1][j] * dv[c][1] + m[2][j] * dv[c][2]);
+      for (int c = 0; c < 3; ++c)
+        for (int j = 0; j < 3; ++j) dv[c][j] = dp[c][j];
+    }
     const double wx = dv[2][1] - dv[1][2], wy = dv[0][2] - dv[2][0], wz = dv[1][0] - dv[0][1];
-    acc[1] += 0.5 * rho * (wx * wx + wy * wy + wz * wz);
+    acc[1] += 0.5 * rho * (wx * wx + wy * wy + wz * wz) * dV;
   }
   // block reduction: warp shuffles, then one warp over the warp sums
   __shared__ double sh[8][8];
@@ -486,12 +714,13 @@ __global__ void __launch_bounds__(256) k_diag(DiagBlock b, const double* __restr
 }
 
 // Deterministic second pass: one thread per quantity sums the block partials in block order.
-__global__ void k_diag_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out, long long N) {
+// K and enstrophy are volume averages (sums of value x cell volume over the total volume).
+__global__ void k_diag_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out, double volume) {
   const int c = threadIdx.x;
   if (c >= 8) return;
   double v = 0.0;
   for (int b = 0; b < nblocks; ++b) v = (c == 7) ? fmax(v, partial[(long long)b * 8 + c]) : v + partial[(long long)b * 8 + c];
-  if (c < 2) v /= (double)N;
+  if (c < 2) v /= volume;
   out[c] = v;
 }
 
@@ -510,8 +739,8 @@ int launch_advance_step(long long* dn, void* stream) {
   return (int)cudaGetLastError();
 }
 
-int launch_diagnostics_final(const double* partial, int nrows, double* out, long long N, void* stream) {
-  k_diag_final<<<1, 32, 0, (cudaStream_t)stream>>>(partial, nrows, out, N);
+int launch_diagnostics_final(const double* partial, int nrows, double* out, double volume, void* stream) {
+  k_diag_final<<<1, 32, 0, (cudaStream_t)stream>>>(partial, nrows, out, volume);
   return (int)cudaGetLastError();
 }
 

@@ -50,6 +50,7 @@ class Case:
     alpha_f: float = 0.499
     dt: float = 1e-3
     seed: int = 2506030
+    curv: float = 0.0          # amplitude of the periodic curvilinear grid (0: uniform Cartesian)
 
     @property
     def dx(self) -> float:
@@ -96,6 +97,34 @@ def grid(case: Case):
     return x, y, z
 
 
+def grid_xy(case: Case):
+    """Point coordinates of the periodic curvilinear grid of amplitude A = case.curv:
+    x = x0 + i dx + A sin(2 pi j / ny), y = y0 + j dy + A sin(2 pi i / nx), z = k dz (a smooth
+    mapping of the index space (xi, eta) = (i, j), extruded in z).  Returns (xy [2][ny][nx],
+    shift[4]) with shift = the (x, y) jump across the periodic wrap in i, then in j; or None
+    for the uniform Cartesian grid."""
+    if not case.curv:
+        return None
+    x, y, _ = grid(case)
+    jj, ii = np.meshgrid(np.arange(case.ny), np.arange(case.nx), indexing="ij")
+    X = x[ii] + case.curv * np.sin(2 * math.pi * jj / case.ny)
+    Y = y[jj] + case.curv * np.sin(2 * math.pi * ii / case.nx)
+    xy = np.ascontiguousarray(np.stack([X, Y]), dtype=np.float64)
+    shift = np.array([case.lx, 0.0, 0.0, case.ly], dtype=np.float64)
+    return xy, shift
+
+
+def point_coords(case: Case):
+    """X, Y, Z of every grid point, each [nz][ny][nx]."""
+    x, y, z = grid(case)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    g = grid_xy(case)
+    if g is not None:
+        X = np.broadcast_to(g[0][0], X.shape).copy()
+        Y = np.broadcast_to(g[0][1], Y.shape).copy()
+    return X, Y, Z
+
+
 def conserved(case: Case, rho, u, v, w, p) -> np.ndarray:
     """Pack primitive fields into U[5][nz][ny][nx] using p = rho T/(gamma M^2) and
     rho E_t = p/(gamma-1) + rho |u|^2 / 2 (App. A)."""
@@ -109,8 +138,7 @@ def conserved(case: Case, rho, u, v, w, p) -> np.ndarray:
 
 
 def tgv_primitives(case: Case):
-    x, y, z = grid(case)
-    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    X, Y, Z = point_coords(case)
     u = np.sin(X) * np.cos(Y) * np.cos(Z)
     v = -np.cos(X) * np.sin(Y) * np.cos(Z)
     w = np.zeros_like(u)
@@ -128,12 +156,12 @@ def tgv_state(case: Case) -> np.ndarray:
 def vortex_primitives(case: Case, eps: float = 5.0, t: float = 0.0):
     """Isentropic vortex of strength eps centred at the origin at t = 0, translated by u_inf t = t
     (periodic wrap) at time t.  Exact for the Euler equations on the infinite plane."""
-    x, y, _ = grid(case)
-    Y, X = np.meshgrid(y, x, indexing="ij")
+    X, Y, _ = point_coords(case)
+    X, Y = X[0], Y[0]
     # position relative to the translated centre, wrapped into the periodic box
     xr = X - t
     xr = (xr + case.lx / 2) % case.lx - case.lx / 2
-    yr = Y
+    yr = (Y + case.ly / 2) % case.ly - case.ly / 2
     r2 = xr * xr + yr * yr
     g = case.gamma
     f = np.exp(0.5 * (1.0 - r2))

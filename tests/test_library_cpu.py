@@ -108,3 +108,23 @@ def test_call_order_and_block_validation(lib):
         assert "dt" in cfs.cfs_last_error(ctx)
     finally:
         cfs.cfs_destroy(ctx)
+
+
+def test_set_block_grid_validation(lib):
+    p = cfs.CfsParams(order=4, viscous=0, gamma=1.4, mach=0.5, re=1.0, pr=1.0, filter=0, alpha_f=0.0)
+    ctx = cfs.cfs_create(p)
+    try:
+        assert cfs.cfs_add_block(ctx, 16, 12, 1, (0.1, 0.1, 1.0)) == 0
+        xy = np.zeros((2, 12, 16))
+        with pytest.raises(cfs.CfsError) as e:
+            cfs.cfs_set_block_grid(ctx, 1, xy, (1.6, 0, 0, 1.2))
+        assert e.value.status == cfs.CFS_EINVAL
+        bad = xy.copy()
+        bad[0, 3, 4] = np.nan
+        with pytest.raises(cfs.CfsError):
+            cfs.cfs_set_block_grid(ctx, 0, bad, (1.6, 0, 0, 1.2))
+        with pytest.raises(cfs.CfsError):
+            cfs.cfs_set_block_grid(ctx, 0, xy, (1.6, np.inf, 0, 1.2))
+        cfs.cfs_set_block_grid(ctx, 0, xy, (1.6, 0, 0, 1.2))
+    finally:
+        cfs.cfs_destroy(ctx)

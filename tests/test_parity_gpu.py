@@ -214,6 +214,39 @@ def test_batched_uneven_blocks_parity():
     s.close()
 
 
+def test_batched_uneven_blocks_fp32_form():
+    """The same three uneven blocks in the FP32-intermediate form: one persistent fused launch per
+    RK stage over the tiles of all blocks, in a CUDA graph; each block stays within the FP32-form
+    error bound of its own oracle run."""
+    base = I.tgv_case(20, 2, "SAA", kmax=2)
+    blocks = [base.replace(nx=20, ny=18, nz=16, px=2, py=2, pz=2),
+              base.replace(nx=26, ny=20, nz=22, px=3, py=2, pz=2, lx=3.0, ly=2.5, lz=2.0),
+              base.replace(nx=16, ny=16, nz=24, px=1, py=1, pz=3, lz=4.0)]
+    dt = min(I.cfl_dt(b, I.tgv_state(b), 0.1) for b in blocks)
+    blocks = [b.replace(dt=dt) for b in blocks]
+    nsteps = 14
+    nsub = sum(b.nsub for b in blocks)
+    d = I.saa_delays(blocks[0].replace(px=nsub, py=1, pz=1), nsteps)
+    import torch
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = cfs.Solver(blocks[0], blocks=blocks, precision=1, graph=True, stream=stream)
+        s.set_schedule(delays=d)
+        for i, b in enumerate(blocks):
+            s.set_state(I.tgv_state(b), block=i)
+        s.step(nsteps)
+        # per step: halo store, 5 fused stages, 3 filter passes per block, step counter
+        assert s.launches() == nsteps * (1 + 5 + 3 * len(blocks) + 1)
+        Ug = [s.get_state(block=i) for i in range(len(blocks))]
+        s.close()
+    sid0 = 0
+    for i, b in enumerate(blocks):
+        Uo = orc.run(b, I.tgv_state(b), nsteps, delays=np.ascontiguousarray(d[:, sid0:sid0 + b.nsub, :]))
+        e = rel_l2(Ug[i], Uo)
+        assert np.all(np.isfinite(Ug[i])) and np.all(e < 1e-6), (i, e)
+        sid0 += b.nsub
+
+
 @pytest.mark.parametrize("precision,learned", [(0, False), (1, False), (0, True)])
 def test_graph_mode_is_bitwise_identical(precision, learned):
     """Replaying one captured step (step counter in device memory) gives exactly the results of
@@ -253,3 +286,50 @@ def test_launch_shapes_do_not_change_results(precision, tiles):
         res.append(s.get_state())
         s.close()
     np.testing.assert_array_equal(res[0], res[1])
+
+
+# ------------------------------------------------------------------ curvilinear blocks (App. A)
+
+@pytest.mark.parametrize("case_name", ["vortex", "tgv_saa"])
+def test_curvilinear_parity(case_name):
+    """Periodic mapped grids (x = x0 + i dx + A sin(2 pi j/ny), y = y0 + j dy + A sin(2 pi i/nx),
+    extruded in z): the GPU path (metric terms from the coordinates, contravariant fluxes, chain-
+    rule viscous terms, J-scaled update, volume-weighted diagnostics) against the oracle."""
+    if case_name == "vortex":
+        c = I.vortex_case(40, 2, curv=0.6)
+        U0 = I.vortex_state(c)
+        nst, d = 60, None
+    else:
+        c = I.tgv_case(26, 2, "SAA", kmax=2, filter=True, curv=0.25)
+        c = c.replace(dt=I.cfl_dt(c, I.tgv_state(c), 0.1))
+        U0 = I.tgv_state(c)
+        nst = 14
+        d = I.saa_delays(c, nst)
+    Ug, dg = gpu_run(c, U0, nst, delays=d)
+    Uo, do = orc.run(c, U0, nst, delays=d, diag=True)
+    check(Ug, Uo)
+    check_diagnostics(dg, do[-1], Uo, c)
+
+
+def test_curvilinear_freestream_on_gpu():
+    """A uniform flow on the deformed grid stays uniform to rounding over many steps."""
+    c = I.tgv_case(24, 2, "SA", filter=True, curv=0.3)
+    U = np.empty((5, c.nz, c.ny, c.nx))
+    p = 1.0 / (c.gamma * c.mach ** 2)
+    U[0] = 1.0
+    U[1], U[2], U[3] = 0.6, -0.3, 0.2
+    U[4] = p / (c.gamma - 1) + 0.5 * (0.36 + 0.09 + 0.04)
+    Ug, _ = gpu_run(c, U, 30)
+    assert np.abs(Ug - U).max() < 1e-12 * np.abs(U).max()
+
+
+def test_curvilinear_fp32_form():
+    """FP32 intermediates on a curvilinear block (multi-kernel stage): error against the oracle
+    within the FP32-form bound."""
+    c = I.tgv_case(26, 2, "CAA", filter=True, curv=0.25)
+    c = c.replace(dt=I.cfl_dt(c, I.tgv_state(c), 0.25))
+    U0 = I.tgv_state(c)
+    Ug, _ = gpu_run(c, U0, 16, precision=1)
+    Uo = orc.run(c, U0, 16)
+    e = rel_l2(Ug, Uo)
+    assert np.all(np.isfinite(Ug)) and np.all(e < 1e-6), e
