@@ -219,7 +219,8 @@ def run_ours(args, rank, world, local_rank):
     U0 = I.tgv_state(case)
     stream = torch.cuda.current_stream()
 
-    solver = cfs.Solver(case, precision=args.precision)
+    tiles = tuple(int(t) for t in args.tiles.split(",")) if args.tiles else None
+    solver = cfs.Solver(case, precision=args.precision, tiles=tiles)
     solver.set_schedule(delays=delays)
     solver.set_state(U0)
     solver.step(W)
@@ -613,6 +614,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-halo form (trains a network)")
     ap.add_argument("--grid", type=int, default=128, help="grid points per axis (profiling runs only)")
     ap.add_argument("--split", type=int, default=4, help="sub-domains per axis (profiling runs only)")
+    ap.add_argument("--tiles", default="", help="fy,zc,threads launch shapes of the main path (profiling runs only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -148,8 +148,8 @@ cfs_status cfs_step(cfs_ctx* ctx, long long nsteps);
 
 /* Launch shapes (before cfs_finalize): tile height fy (4, 8 or 16) and z chunk zc of the fused
  * FP32-intermediate stage kernel (tiles of 32 x fy columns marching zc planes), and the threads per
- * CTA (128, 256, 512) of the other stage kernels.  Results are identical for every choice; the
- * autotuner of the Python package picks the fastest and stores it. */
+ * CTA (128, 256, 512) of the other stage kernels; defaults 16, 32 and 256.  Results are identical
+ * for every choice; the autotuner of the Python package picks the fastest and stores it. */
 cfs_status cfs_set_tiles(cfs_ctx* ctx, int fy, int zc, int threads);
 
 /* CUDA-graph mode (on = 1): cfs_step captures the kernels of one step once -- the step index is

@@ -88,8 +88,8 @@ struct cfs_ctx {
   // fused FP32-intermediate stage (3-D Navier-Stokes, CD4)
   bool fused = false;
   int threads = 256;   // threads per CTA of the FP64 / 3-kernel stage kernels
-  int fused_zc = 16;
-  int fused_fy = 8;
+  int fused_zc = 32;
+  int fused_fy = 16;
   int fused_grid = 0;
   double* d_metric = nullptr;  // metric fields of the curvilinear blocks
   double volume = 0.0;         // total cell volume (diagnostics averages)

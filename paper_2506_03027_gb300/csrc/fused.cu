@@ -143,34 +143,61 @@ __global__ void __launch_bounds__(256) k_halo_prims(Geometry g, Physics ph, Step
 
 template <int FX, int FY>
 struct FusedSmem {
+  static constexpr int NT = FX * FY;
   static constexpr int BX = FX + 2 * HB, BY = FY + 2 * HB, NB = BX * BY;  // box: tile + halo of 4
   static constexpr int WX = FX + 4, WY = FY + 4, NW = WX * WY;            // window: tile + strips of 2
-  static constexpr int STG = 2 * 5 * NB;                                  // staging, 5 x 8 bytes per box point
-  static constexpr int R4 = 5 * 4 * NB;   // u, v, w, T of planes G-2..G+2
-  static constexpr int R3 = 3 * 3 * NW;   // rho, p', et' of planes G..G+2 on the window
-  static constexpr int FXS = 5 * FY * (FX + 4);  // Phi_x of tile + x strips
-  static constexpr int FYS = 5 * (FY + 4) * FX;  // Phi_y of tile + y strips
-  static constexpr size_t bytes = sizeof(float) * (STG + R4 + R3 + FXS + FYS);
+  static constexpr int STG = 2 * 5 * NB;      // staging, 5 x 8 bytes per box point
+  static constexpr int R4 = 4 * 5 * NB;       // float4 (u, v, w, T) of planes G-2..G+2 on the box
+  static constexpr int R3 = 4 * 3 * NW;       // float4 (rho, p', et', -) of planes G..G+2 on the window
+  static constexpr int FX4 = 4 * FY * (FX + 4), FX1 = FY * (FX + 4);  // Phi_x (components 0-3, 4)
+  static constexpr int FY4 = 4 * (FY + 4) * FX, FY1 = (FY + 4) * FX;  // Phi_y
+  static constexpr size_t bytes = sizeof(float) * (STG + R4 + R3 + FX4 + FX1 + FY4 + FY1);
 };
 
-// Where the stage input of a box point comes from: the FP64 state (own points, synchronous halos,
-// and box points no output depends on) or the per-step halo store.  dx, dy, dz: distance outside
-// the sub-domain along each axis.  The sub-domain's view holds faces up to depth HB and edges up
-// to r x r; a narrow ragged tile's box reaches further, and those points feed no output.
-__device__ __forceinline__ bool from_store(int mode, int r, int dx, int dy, int dz) {
+// The view of a sub-domain holds faces up to depth HB and edges up to r x r (corners unused).
+__device__ __forceinline__ bool in_view(int r, int dx, int dy, int dz) {
   const int nout = (dx > 0) + (dy > 0) + (dz > 0);
-  const bool inview = (nout == 1 && dx <= HB && dy <= HB && dz <= HB) || (nout == 2 && dx <= r && dy <= r && dz <= r);
-  return mode != 0 && nout > 0 && inview;
+  return (nout == 1 && dx <= HB && dy <= HB && dz <= HB) || (nout == 2 && dx <= r && dy <= r && dz <= r);
 }
 
-// Per-thread description of the box columns (i, j) it loads on every plane of a work item.
+// Source of a box point on a plane: 0 skip (no output reads it), 1 the FP64 stage input (own
+// points; every point in synchronous mode), 2 the per-step halo store.  dx, dy, dz: distance
+// outside the sub-domain along each axis.
+__device__ __forceinline__ int box_source(int mode, int r, int dx, int dy, int dz) {
+  if (dx == 0 && dy == 0 && dz == 0) return 1;
+  if (!in_view(r, dx, dy, dz)) return 0;
+  return mode == 0 ? 1 : 2;
+}
+
+// Per-thread box columns (i, j) of a work item, loaded on every plane.
 template <int KB>
 struct BoxCols {
   int xy[KB];   // gx + bnx gy of the wrapped in-block position
   int pxy[KB];  // (lx + G) + ex (ly + G) in the padded box
   int dxy[KB];  // dx | dy << 8 (distance outside the sub-domain), -1 for no column
+  int pq[KB];   // box index | window index << 16 (window index 0xffff: outside the window)
 };
 
+__device__ __forceinline__ float2 lo2(const float4& a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 hi2(const float4& a) { return make_float2(a.z, a.w); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+// CD4 first derivative along one axis of (u, v) and (w, T) from the box values at offsets
+// -2, -1, +1, +2: c1 (f+1 - f-1) + c2 (f+2 - f-2), packed FP32 pairs.
+__device__ __forceinline__ void cd4_pair(const float4& m2, const float4& m1, const float4& p1, const float4& p2, float c1,
+                                         float c2, float2& duv, float2& dwT) {
+  duv = __ffma2_rn(bc2(c1), sub2(lo2(p1), lo2(m1)), __fmul2_rn(bc2(c2), sub2(lo2(p2), lo2(m2))));
+  dwT = __ffma2_rn(bc2(c1), sub2(hi2(p1), hi2(m1)), __fmul2_rn(bc2(c2), sub2(hi2(p2), hi2(m2))));
+}
+
+// Fused stage.  Per CTA a tile of FX x FY columns of one sub-domain and a chunk of its z-planes;
+// one thread per tile column.  Per plane L of the march: asynchronous copies of plane L + 1
+// (FP64 state for own points, FP32 halo primitives from the store) run while plane L is
+// converted into the rings and plane G = L - 2 is differentiated; the dt R queue of the column
+// then completes plane G - 2, which takes its FP64 low-storage update.  Box columns are handed out
+// in two lists (inside the sub-domain first, then halo columns) so that a warp takes one source;
+// columns no output reads are not loaded.
 template <int FX, int FY>
 __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fused(Geometry g, Physics ph, StepSched sc,
                                                         const double* __restrict__ Uin0, double* __restrict__ Uout0,
@@ -184,14 +211,19 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
   double* __restrict__ Uout = const_cast<double*>(ring_or(Uout0, out_ring, ring, sc, 1));
   using S = FusedSmem<FX, FY>;
   constexpr int BX = S::BX, NB = S::NB, WX = S::WX, NW = S::NW, NT = FX * FY;
+  constexpr int FXW = FX + 4;
   extern __shared__ __align__(16) float smem[];
   double* sStg = reinterpret_cast<double*>(smem);  // [5][NB] FP64, or FP32 pairs for halo points
   float* sStgF = smem;
-  float* sR4 = smem + S::STG;
-  float* sR3 = sR4 + S::R4;
-  float* sFx = sR3 + S::R3;
-  float* sFy = sFx + S::FXS;
-  const int tid = threadIdx.x, tx = tid % FX, ty = tid / FX;
+  float4* sR4 = reinterpret_cast<float4*>(smem + S::STG);   // [5][NB]
+  float4* sR3 = reinterpret_cast<float4*>(smem + S::STG + S::R4);  // [3][NW]
+  float4* sFx4 = reinterpret_cast<float4*>(smem + S::STG + S::R4 + S::R3);  // [FY][FX + 4]
+  float* sFx1 = smem + S::STG + S::R4 + S::R3 + S::FX4;
+  float4* sFy4 = reinterpret_cast<float4*>(sFx1 + S::FX1);  // [FY + 4][FX]
+  float* sFy1 = sFx1 + S::FX1 + S::FY4;
+  __shared__ unsigned short sList[NB];  // box indices: columns inside the sub-domain, then halo columns
+  __shared__ int sNlist;
+  const int tid = threadIdx.x, tx = tid % FX, ty = tid / FX, lane = tid & 31;
   constexpr int KB = (NB + NT - 1) / NT;
   // constants converted from FP64 once per CTA (physics) and once per work item (dt x CD
   // coefficients) by one thread; the work-item set is double-buffered by parity so that thread
@@ -209,6 +241,7 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
     const SubDev d = subs[wk[0]];
     const int tx0 = wk[1], ty0 = wk[2];
     const int z0 = wk[3] & 0xffff, z1 = wk[3] >> 16;  // output planes [z0, z1) of the sub-domain
+    const int fxa = min(FX, d.sx - tx0), fya = min(FY, d.sy - ty0);  // the tile's own extent
     if (tid == 0) {
       for (int a = 0; a < 3; ++a) {
         sK[par][a] = (float)d.c1[a];
@@ -217,26 +250,64 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
         sK[par][9 + a] = (float)(dt * d.c2[a]);
       }
     }
+    // ---- column lists (warp 0, ordered ballots): a box column is read by some output when it
+    // lies in the tile +- 4 along one axis or in the tile +- 2 along both; outside the sub-domain
+    // in x or y it must also be in the view (faces, r x r edges)
+    __syncthreads();  // the previous item's lists are no longer read
+    if (tid < 32) {
+      int n = 0;
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int p0 = 0; p0 < NB; p0 += 32) {
+          const int p = p0 + lane;
+          bool take = false;
+          if (p < NB) {
+            const int ti = p % BX - HB, tj = p / BX - HB;
+            const bool need = (tj >= 0 && tj < fya && ti >= -HB && ti < fxa + HB) ||
+                              (ti >= 0 && ti < fxa && tj >= -HB && tj < fya + HB) ||
+                              (ti >= -2 && ti < fxa + 2 && tj >= -2 && tj < fya + 2);
+            const int lx = tx0 + ti, ly = ty0 + tj;
+            const int dx = lx < 0 ? -lx : (lx >= d.sx ? lx - d.sx + 1 : 0);
+            const int dy = ly < 0 ? -ly : (ly >= d.sy ? ly - d.sy + 1 : 0);
+            const bool inner = dx == 0 && dy == 0;
+            take = need && (pass == 0 ? inner : (!inner && in_view(g.r, dx, dy, 0)));
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, take);
+          if (take) sList[n + __popc(m & ((1u << lane) - 1u))] = (unsigned short)p;
+          n += __popc(m);
+        }
+      }
+      if (lane == 0) sNlist = n;
+    }
+    __syncthreads();
+    const int nlist = sNlist;
     BoxCols<KB> bc;
 #pragma unroll
     for (int k = 0; k < KB; ++k) {
-      const int p = tid + k * NT;
+      const int i = tid + k * NT;
       bc.dxy[k] = -1;
-      if (p < NB) {
+      if (i < nlist) {
+        const int p = sList[i];
         const int lx = tx0 - HB + p % BX, ly = ty0 - HB + p / BX;
         const int dx = lx < 0 ? -lx : (lx >= d.sx ? lx - d.sx + 1 : 0);
         const int dy = ly < 0 ? -ly : (ly >= d.sy ? ly - d.sy + 1 : 0);
         bc.xy[k] = wrapc(d.ox + lx, d.bnx) + d.bnx * wrapc(d.oy + ly, d.bny);
         bc.pxy[k] = (lx + g.G) + d.ex * (ly + g.G);
         bc.dxy[k] = dx | (dy << 8);
+        const int wi2 = p % BX - (HB - 2), wj2 = p / BX - (HB - 2);
+        const int qw = (wi2 >= 0 && wi2 < WX && wj2 >= 0 && wj2 < S::WY) ? wj2 * WX + wi2 : 0xffff;
+        bc.pq[k] = p | (qw << 16);
       }
     }
-    // dt R of the tile column for planes G-2..G+1 (before the contributions of flux plane G)
-    float acc[4][5];
+    // dt R of the tile column for planes G-2..G+1 (before the contributions of flux plane G),
+    // components (0, 1), (2, 3) as pairs and 4
+    float2 aq[4][2];
+    float aq4[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int c = 0; c < 5; ++c) acc[a][c] = 0.f;
+    for (int a = 0; a < 4; ++a) {
+      aq[a][0] = make_float2(0.f, 0.f);
+      aq[a][1] = make_float2(0.f, 0.f);
+      aq4[a] = 0.f;
+    }
 
     // plane-dependent parts of the source offsets
     auto plane_src = [&](int L, long long& zoff, long long& pz, int& dz) {
@@ -250,16 +321,17 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
       plane_src(L, zoff, pz, dz);
 #pragma unroll
       for (int k = 0; k < KB; ++k) {
-        const int p = tid + k * NT;
         if (bc.dxy[k] < 0) continue;
-        if (!from_store(sc.mode, g.r, bc.dxy[k] & 255, bc.dxy[k] >> 8, dz)) {
-          const double* src = Uin + zoff + bc.xy[k];
+        const int p = bc.pq[k] & 0xffff;
+        const int src = box_source(sc.mode, g.r, bc.dxy[k] & 255, bc.dxy[k] >> 8, dz);
+        if (src == 1) {
+          const double* s0 = Uin + zoff + bc.xy[k];
 #pragma unroll
-          for (int v = 0; v < 5; ++v) cp_async8(sStg + v * NB + p, src + v * d.bN);
-        } else {
-          const float* src = WhS + pz + bc.pxy[k];
+          for (int v = 0; v < 5; ++v) cp_async8(sStg + v * NB + p, s0 + v * d.bN);
+        } else if (src == 2) {
+          const float* s0 = WhS + pz + bc.pxy[k];
 #pragma unroll
-          for (int c = 0; c < 7; ++c) cp_async4(sStgF + 2 * ((c >> 1) * NB + p) + (c & 1), src + (long long)c * P);
+          for (int c = 0; c < 7; ++c) cp_async4(sStgF + 2 * ((c >> 1) * NB + p) + (c & 1), s0 + (long long)c * P);
         }
       }
       cp_async_commit();
@@ -271,34 +343,33 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
       cp_async_wait_all();
       __syncthreads();
       {
-        float* r4 = sR4 + ((L + 15) % 5) * 4 * NB;
-        float* r3 = sR3 + ((L + 15) % 3) * 3 * NW;
+        float4* r4 = sR4 + ((L + 15) % 5) * NB;
+        float4* r3 = sR3 + ((L + 15) % 3) * NW;
         const int dz = L < 0 ? -L : (L >= d.sz ? L - d.sz + 1 : 0);
 #pragma unroll
         for (int k = 0; k < KB; ++k) {
-          const int p = tid + k * NT;
           if (bc.dxy[k] < 0) continue;
+          const int src = box_source(sc.mode, g.r, bc.dxy[k] & 255, bc.dxy[k] >> 8, dz);
+          if (src == 0) continue;
+          const int p = bc.pq[k] & 0xffff, qw = bc.pq[k] >> 16;
           float w[7];
-          if (!from_store(sc.mode, g.r, bc.dxy[k] & 255, bc.dxy[k] >> 8, dz)) {
+          if (src == 1) {
             double u[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v) u[v] = sStg[v * NB + p];
             prims32(u, k32, w);
           } else {
+            const float2* s2 = reinterpret_cast<const float2*>(sStgF);
 #pragma unroll
-            for (int c = 0; c < 7; ++c) w[c] = sStgF[2 * ((c >> 1) * NB + p) + (c & 1)];
+            for (int c = 0; c < 3; ++c) {
+              const float2 t = s2[c * NB + p];
+              w[2 * c] = t.x;
+              w[2 * c + 1] = t.y;
+            }
+            w[6] = sStgF[2 * (3 * NB + p)];
           }
-          r4[p] = w[1];
-          r4[NB + p] = w[2];
-          r4[2 * NB + p] = w[3];
-          r4[3 * NB + p] = w[5];
-          const int wi2 = p % BX - (HB - 2), wj2 = p / BX - (HB - 2);
-          if (wi2 >= 0 && wi2 < WX && wj2 >= 0 && wj2 < S::WY) {
-            const int qw = wj2 * WX + wi2;
-            r3[qw] = w[0];
-            r3[NW + qw] = w[4];
-            r3[2 * NW + qw] = w[6];
-          }
+          r4[p] = make_float4(w[1], w[2], w[3], w[5]);
+          if (qw != 0xffff) r3[qw] = make_float4(w[0], w[4], w[6], 0.f);
         }
       }
       __syncthreads();
@@ -325,33 +396,34 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
         }
       }
       // ---- fluxes of plane G
-      const float* pl[5];
+      const float4* pl[5];
 #pragma unroll
-      for (int o = 0; o < 5; ++o) pl[o] = sR4 + ((G - 2 + o + 15) % 5) * 4 * NB;  // planes G-2..G+2
-      const float* r3c = sR3 + ((G + 15) % 3) * 3 * NW;
+      for (int o = 0; o < 5; ++o) pl[o] = sR4 + ((G - 2 + o + 15) % 5) * NB;  // planes G-2..G+2
+      const float4* r3c = sR3 + ((G + 15) % 3) * NW;
       const bool strips = (G >= z0 && G < z1);
-      float fz[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      float2 fz01 = make_float2(0.f, 0.f), fz23 = make_float2(0.f, 0.f);
+      float fz4 = 0.f;
       // one gradient/flux evaluation at box point (bi, bj) of plane G: kind 0 tile point (Phi_x,
       // Phi_y to shared memory, Phi_z to registers), 1 x-strip (Phi_x), 2 y-strip (Phi_y)
       auto point = [&](int bi, int bj, int kind) {
-        const float* P0 = pl[2];
+        const float4* P0 = pl[2];
         const int q = bj * BX + bi;
         const int qw = (bj - (HB - 2)) * WX + (bi - (HB - 2));
-        float du[3][3], dT[3];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const float* f = P0 + v * NB;
-          const float gx_ = c1x * (f[q + 1] - f[q - 1]) + c2x * (f[q + 2] - f[q - 2]);
-          const float gy_ = c1y * (f[q + BX] - f[q - BX]) + c2y * (f[q + 2 * BX] - f[q - 2 * BX]);
-          const float gz_ = c1z * (pl[3][v * NB + q] - pl[1][v * NB + q]) + c2z * (pl[4][v * NB + q] - pl[0][v * NB + q]);
-          if (v < 3) { du[v][0] = gx_; du[v][1] = gy_; du[v][2] = gz_; }
-          else { dT[0] = gx_; dT[1] = gy_; dT[2] = gz_; }
-        }
-        const float u = P0[q], v = P0[NB + q], w = P0[2 * NB + q], T = P0[3 * NB + q];
-        const float rho = r3c[qw], p = r3c[NW + qw], et = r3c[2 * NW + qw];
+        float2 g0[3], g1[3];  // per axis: (du, dv), (dw, dT)
+        cd4_pair(P0[q - 2], P0[q - 1], P0[q + 1], P0[q + 2], c1x, c2x, g0[0], g1[0]);
+        cd4_pair(P0[q - 2 * BX], P0[q - BX], P0[q + BX], P0[q + 2 * BX], c1y, c2y, g0[1], g1[1]);
+        cd4_pair(pl[0][q], pl[1][q], pl[3][q], pl[4][q], c1z, c2z, g0[2], g1[2]);
+        // du[i][j] = d u_i / d x_j
+        const float du[3][3] = {{g0[0].x, g0[1].x, g0[2].x}, {g0[0].y, g0[1].y, g0[2].y}, {g1[0].x, g1[1].x, g1[2].x}};
+        const float dT[3] = {g1[0].y, g1[1].y, g1[2].y};
+        const float4 c0 = P0[q];
+        const float4 c3 = r3c[qw];
+        const float u = c0.x, v = c0.y, w = c0.z, T = c0.w;
+        const float rho = c3.x, p = c3.y, etH = c3.z + k32.Href;
         float mu = 1.f;
         if (k32.law == 1) mu = powf(T, k32.vexp);
-        const float div = du[0][0] + du[1][1] + du[2][2];
+        const float div = (du[0][0] + du[1][1]) + du[2][2];
+        const float m23 = (-2.f / 3.f) * mu, kmu = k32.kap * mu;
         const float vel[3] = {u, v, w};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -361,23 +433,25 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
           float tau[3];
 #pragma unroll
           for (int i2 = 0; i2 < 3; ++i2) tau[i2] = mu * (du[a][i2] + du[i2][a]);
-          tau[a] -= (2.f / 3.f) * mu * div;
-          const float qa = u * tau[0] + v * tau[1] + w * tau[2] + k32.kap * mu * dT[a];
-          float f[5];
-          f[0] = -mflux;
-          f[1] = -(mflux * u + (a == 0 ? p : 0.f)) + k32.ire * tau[0];
-          f[2] = -(mflux * v + (a == 1 ? p : 0.f)) + k32.ire * tau[1];
-          f[3] = -(mflux * w + (a == 2 ? p : 0.f)) + k32.ire * tau[2];
-          f[4] = -(et * ua + k32.Href * ua) + k32.ire * qa;
+          tau[a] = fmaf(m23, div, tau[a]);
+          const float qa = fmaf(u, tau[0], fmaf(v, tau[1], fmaf(w, tau[2], kmu * dT[a])));
+          const float f0 = -mflux;
+          const float f1 = fmaf(k32.ire, tau[0], -fmaf(mflux, u, a == 0 ? p : 0.f));
+          const float f2 = fmaf(k32.ire, tau[1], -fmaf(mflux, v, a == 1 ? p : 0.f));
+          const float f3 = fmaf(k32.ire, tau[2], -fmaf(mflux, w, a == 2 ? p : 0.f));
+          const float f4 = fmaf(k32.ire, qa, -(etH * ua));
           if (a == 0) {
-#pragma unroll
-            for (int c = 0; c < 5; ++c) sFx[(c * FY + (bj - HB)) * (FX + 4) + (bi - HB + 2)] = f[c];
+            const int o = (bj - HB) * FXW + (bi - HB + 2);
+            sFx4[o] = make_float4(f0, f1, f2, f3);
+            sFx1[o] = f4;
           } else if (a == 1) {
-#pragma unroll
-            for (int c = 0; c < 5; ++c) sFy[(c * (FY + 4) + (bj - HB + 2)) * FX + (bi - HB)] = f[c];
+            const int o = (bj - HB + 2) * FX + (bi - HB);
+            sFy4[o] = make_float4(f0, f1, f2, f3);
+            sFy1[o] = f4;
           } else {
-#pragma unroll
-            for (int c = 0; c < 5; ++c) fz[c] = f[c];
+            fz01 = make_float2(f0, f1);
+            fz23 = make_float2(f2, f3);
+            fz4 = f4;
           }
         }
       };
@@ -396,23 +470,47 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
       __syncthreads();
       // ---- dt R queue: Phi_z(G) enters planes G-2..G+2 with the CD4 weights, the in-plane
       // divergence enters plane G; plane G-2 is then complete
+      float2 r01 = make_float2(0.f, 0.f), r23 = make_float2(0.f, 0.f);
+      float r4s = 0.f;
+      if (strips) {
+        const int ox = ty * FXW + tx + 2, oy = (ty + 2) * FX + tx;
+        const float4 xm2 = sFx4[ox - 2], xm1 = sFx4[ox - 1], xp1 = sFx4[ox + 1], xp2 = sFx4[ox + 2];
+        const float4 ym2 = sFy4[oy - 2 * FX], ym1 = sFy4[oy - FX], yp1 = sFy4[oy + FX], yp2 = sFy4[oy + 2 * FX];
+        r01 = __ffma2_rn(bc2(k1x), sub2(lo2(xp1), lo2(xm1)), __fmul2_rn(bc2(k2x), sub2(lo2(xp2), lo2(xm2))));
+        r01 = __ffma2_rn(bc2(k1y), sub2(lo2(yp1), lo2(ym1)), r01);
+        r01 = __ffma2_rn(bc2(k2y), sub2(lo2(yp2), lo2(ym2)), r01);
+        r23 = __ffma2_rn(bc2(k1x), sub2(hi2(xp1), hi2(xm1)), __fmul2_rn(bc2(k2x), sub2(hi2(xp2), hi2(xm2))));
+        r23 = __ffma2_rn(bc2(k1y), sub2(hi2(yp1), hi2(ym1)), r23);
+        r23 = __ffma2_rn(bc2(k2y), sub2(hi2(yp2), hi2(ym2)), r23);
+        r4s = fmaf(k1x, sFx1[ox + 1] - sFx1[ox - 1], k2x * (sFx1[ox + 2] - sFx1[ox - 2]));
+        r4s = fmaf(k1y, sFy1[oy + FX] - sFy1[oy - FX], r4s);
+        r4s = fmaf(k2y, sFy1[oy + 2 * FX] - sFy1[oy - 2 * FX], r4s);
+      }
+      float out[5];
+      {
+        const float2 o01 = __ffma2_rn(bc2(k2z), fz01, aq[0][0]), o23 = __ffma2_rn(bc2(k2z), fz23, aq[0][1]);
+        aq[0][0] = __ffma2_rn(bc2(k1z), fz01, aq[1][0]);
+        aq[0][1] = __ffma2_rn(bc2(k1z), fz23, aq[1][1]);
+        aq[1][0] = __fadd2_rn(aq[2][0], r01);
+        aq[1][1] = __fadd2_rn(aq[2][1], r23);
+        aq[2][0] = __ffma2_rn(bc2(-k1z), fz01, aq[3][0]);
+        aq[2][1] = __ffma2_rn(bc2(-k1z), fz23, aq[3][1]);
+        aq[3][0] = __fmul2_rn(bc2(-k2z), fz01);
+        aq[3][1] = __fmul2_rn(bc2(-k2z), fz23);
+        out[0] = o01.x;
+        out[1] = o01.y;
+        out[2] = o23.x;
+        out[3] = o23.y;
+        out[4] = fmaf(k2z, fz4, aq4[0]);
+        aq4[0] = fmaf(k1z, fz4, aq4[1]);
+        aq4[1] = aq4[2] + r4s;
+        aq4[2] = fmaf(-k1z, fz4, aq4[3]);
+        aq4[3] = -k2z * fz4;
+      }
+      if (outp) {
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        float r = 0.f;
-        if (strips) {
-          const float* Fx = sFx + (c * FY + ty) * (FX + 4) + tx + 2;
-          const float* Fy = sFy + (c * (FY + 4) + ty + 2) * FX + tx;
-          r = k1x * (Fx[1] - Fx[-1]) + k2x * (Fx[2] - Fx[-2]);
-          r = fmaf(k1y, Fy[FX] - Fy[-FX], r);
-          r = fmaf(k2y, Fy[2 * FX] - Fy[-2 * FX], r);
-        }
-        const float out = fmaf(k2z, fz[c], acc[0][c]);
-        acc[0][c] = fmaf(k1z, fz[c], acc[1][c]);
-        acc[1][c] = acc[2][c] + r;
-        acc[2][c] = fmaf(-k1z, fz[c], acc[3][c]);
-        acc[3][c] = -k2z * fz[c];
-        if (outp) {
-          const double dtR = f2d_fast(out);
+        for (int c = 0; c < 5; ++c) {
+          const double dtR = f2d_fast(out[c]);
           const double qn = first ? dtR : fma(A, qin[c], dtR);
           if (!last) Q[c * d.bN + go] = qn;
           Uout[c * d.bN + go] = fma(B, qn, uin[c]);

@@ -187,6 +187,29 @@ def test_fp32_intermediates_error_is_small(algo):
     assert np.all(e < 1e-6), e
 
 
+def test_fp32_form_subdomain_wider_than_tile():
+    """FP32 form on one 42^3 sub-domain (periodic self-neighbour faces): the fused stage covers it
+    with several tiles in x (32 + 10) and y, so tile boundaries inside the sub-domain take their
+    halo columns from the live stage input; every tile height gives the same bits, within the
+    FP32-form bound of the oracle."""
+    c = small_tgv("SAA", n=42, p=1, kmax=2, cfl=0.1)
+    d = I.saa_delays(c, 10)
+    U0 = I.tgv_state(c)
+    res = []
+    for t in ((4, 8, 256), (8, 16, 256), (16, 32, 256)):
+        s = cfs.Solver(c, precision=1, tiles=t)
+        s.set_schedule(delays=d)
+        s.set_state(U0)
+        s.step(10)
+        res.append(s.get_state())
+        s.close()
+    np.testing.assert_array_equal(res[0], res[1])
+    np.testing.assert_array_equal(res[0], res[2])
+    Uo = orc.run(c, U0, 10, delays=d)
+    e = rel_l2(res[0], Uo)
+    assert np.all(np.isfinite(res[0])) and np.all(e < 1e-6), e
+
+
 def test_batched_uneven_blocks_parity():
     """Three independent periodic blocks of uneven sizes and splits advance together (one launch
     per kernel over the sub-domains of all blocks); each block equals its own oracle run, with the
