@@ -87,6 +87,7 @@ struct cfs_ctx {
 
   // fused FP32-intermediate stage (3-D Navier-Stokes, CD4)
   bool fused = false;
+  int fblock_n = 0;     // FP32 form, asynchronous steps: sub-domain filter for cubic sub-domains of this size
   int threads = 256;   // threads per CTA of the FP64 / 3-kernel stage kernels
   int fused_zc = 32;
   int fused_fy = 16;
@@ -397,6 +398,13 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   }
   g.metric = c->d_metric;
   c->fused = c->p.precision == 1 && c->ndim == 3 && c->p.viscous && c->p.order == 4 && !curv;
+  c->fblock_n = 0;
+  if (c->p.precision == 1 && c->p.filter && c->ndim == 3 && !curv && nsub > 0) {
+    const int n0 = c->subs[0].sx;
+    bool cubic = cfs::filter_block_supported(n0);
+    for (const SubDev& d : c->subs) cubic = cubic && d.sx == n0 && d.sy == n0 && d.sz == n0;
+    if (cubic) c->fblock_n = n0;
+  }
   if (c->fused) {
     // tiles of 32 x fy columns per sub-domain, marching z; one CTA per tile (persistent grid)
     std::vector<int> work;
@@ -610,6 +618,27 @@ cfs_status cfs_set_step(cfs_ctx* c, long long n) {
   return CFS_OK;
 }
 
+// The sub-domain filter of the FP32 form (all three passes): from the last stage's output to
+// level n + 1 (graph mode: the ring slot of the device step counter; the kernel returns on
+// synchronous steps, which the per-pass kernels then filter).
+static int launch_fblock(cfs_ctx* c, const Geometry& g, const StepSched& sc, const double* src, double* dst, bool graph) {
+  cfs::FilterBlockLaunch f{};
+  f.Uin = src;
+  f.Uout = dst;
+  f.ring = c->ring;
+  f.in_ring = 0;
+  f.out_ring = graph ? 1 : 0;
+  f.subs = c->d_subs;
+  f.nsub = (int)c->subs.size();
+  f.thomas = c->d_thomas;
+  f.Lmax = c->Lmax;
+  f.alpha = c->p.alpha_f;
+  for (int m = 0; m < 6; ++m) f.h[m] = c->filt_h[m];
+  f.b1 = c->filt_h[1] - c->p.alpha_f;
+  const cfs::Timer* tm = (c->timing && !graph) ? &c->timer : nullptr;
+  return cfs::launch_filter_block(g, sc, f, c->fblock_n, c->stream, &c->launches, tm);
+}
+
 // Enqueue the kernels of step n on the context's stream.  graph = true: the step index and
 // everything derived from it (mode, delays, ring slots) are read by the kernels from d_n, so the
 // enqueued sequence is the same for every step and can be captured once.
@@ -672,9 +701,18 @@ static cfs_status enqueue_step(cfs_ctx* c, long long n, bool graph) {
       a.max_pad = c->max_pad; a.max_own = c->max_own; a.max_flux = c->max_flux;
       a.halo = c->d_halo; a.nhalo = c->nhalo;
       rc = cfs::launch_stage(g, c->phys, sc, a, c->p.precision, c->stream, &c->launches, tm);
+    } else if (op == c->s && c->fblock_n && !graph && sc.mode != 0) {
+      // asynchronous step, FP32 form: the three passes in one launch, straight into level n + 1
+      rc = launch_fblock(c, g, sc, src, level_ptr(c, n + 1), false);
+      if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
+      break;
     } else {
       rc = 0;
+      // graph mode: the sub-domain filter (returns on synchronous steps) before the per-pass
+      // kernels (which then return on asynchronous steps)
+      if (op == c->s && c->fblock_n && graph) rc = launch_fblock(c, g, sc, src, nullptr, true);
       for (const Block& b : c->blocks) {
+        if (rc != 0) break;
         cfs::FilterLaunch f{};
         f.Uin = src; f.Uout = dst; f.ring = c->ring;
         f.in_ring = in_ring; f.out_ring = out_ring;
@@ -686,6 +724,7 @@ static cfs_status enqueue_step(cfs_ctx* c, long long n, bool graph) {
         f.thomas = c->d_thomas; f.Lmax = c->Lmax; f.alpha = c->p.alpha_f;
         for (int m = 0; m < 6; ++m) f.h[m] = c->filt_h[m];
         f.b1 = c->filt_h[1] - c->p.alpha_f;
+        f.only_sync = graph && c->fblock_n;
         rc = cfs::launch_filter(g, sc, f, op - c->s, c->p.precision, c->stream, &c->launches, tm);
         if (rc != 0) break;
       }

@@ -152,7 +152,27 @@ struct FilterLaunch {
   double alpha;
   double h[6];             // filter right side: a_0, a_1/2, ..., a_5/2
   double b1;               // a_1/2 - alpha: weight of the first second difference (increment form)
+  int only_sync;           // graph mode beside the sub-domain filter: return unless the step is synchronous
 };
+
+// FP32-intermediate filter of asynchronous steps, all three passes per (sub-domain, variable)
+// (filter_block.cu); cubic sub-domains of n points per axis, n in {16, 32}.
+struct FilterBlockLaunch {
+  const double* Uin;
+  double* Uout;
+  const double* ring;
+  int in_ring, out_ring;
+  const SubDev* subs;
+  int nsub;
+  const double* thomas;
+  int Lmax;
+  double alpha;
+  double h[6];
+  double b1;
+};
+bool filter_block_supported(int n);
+int launch_filter_block(const Geometry& g, const StepSched& sc, const FilterBlockLaunch& f, int n, void* stream,
+                        long long* launches, const Timer* tm);
 
 int filter_prepare(int Lmax, int precision);  // shared-memory attribute of the filter kernels; nonzero if too long
 int launch_filter(const Geometry& g, const StepSched& sc, const FilterLaunch& f, int axis, int precision,

@@ -86,19 +86,25 @@ __global__ void __launch_bounds__(256) k_halo_prims(Geometry g, Physics ph, Step
   const Phys32 k32 = phys32(ph);
   const int2 hv = halo[e];
   const int sid = hv.x;
-  const long long t = hv.y;
+  const int t = hv.y;  // index in the sub-domain's padded box (32-bit)
   const SubDev d = subs[sid];
-  const int i = (int)(t % d.ex), j = (int)((t / d.ex) % d.ey), k = (int)(t / ((long long)d.ex * d.ey));
+  const int exy = d.ex * d.ey;
+  const int k = t / exy, r2 = t - k * exy, j = r2 / d.ex, i = r2 - j * d.ex;
   const int ci = i - g.G, cj = j - g.G, ck = k - g.Gz;
   int kd = 0;
   if (ci < 0 || ci >= d.sx) kd = max(kd, face_delay(sc, sid, ci < 0 ? 0 : 1));
   if (cj < 0 || cj >= d.sy) kd = max(kd, face_delay(sc, sid, cj < 0 ? 2 : 3));
   if (ck < 0 || ck >= d.sz) kd = max(kd, face_delay(sc, sid, ck < 0 ? 4 : 5));
-  const int gx = wrapc(d.ox + ci, d.bnx), gy = wrapc(d.oy + cj, d.bny), gz = wrapc(d.oz + ck, d.bnz);
+  // halo points lie within G of the sub-domain: one conditional wrap per axis
+  auto wrap1 = [](int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); };
+  const int gx = wrap1(d.ox + ci, d.bnx), gy = wrap1(d.oy + cj, d.bny), gz = wrap1(d.oz + ck, d.bnz);
   const long long gi = d.bbase + (long long)gx + (long long)d.bnx * ((long long)gy + (long long)d.bny * gz);
   const long long lvN = 5 * g.N, P = g.Ptot, o = d.pbase + t;
+  // ring slot of level n - kd - l: (n mod R) - kd - l, wrapped once (kd + l < R)
+  const int nR = (int)(sc.n % sc.R);
+  auto slot = [&](int l) { const int q = nR - kd - l; return q < 0 ? q + sc.R : q; };
   if (sc.mode == 2) {  // AS: the latest visible level, the same for every stage
-    const double* src = ring + (long long)((sc.n - kd) % sc.R) * lvN;
+    const double* src = ring + (long long)slot(0) * lvN;
     double u[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) u[v] = src[v * d.bN + gi];
@@ -117,7 +123,7 @@ __global__ void __launch_bounds__(256) k_halo_prims(Geometry g, Physics ph, Step
 #pragma unroll
     for (int v = 0; v < 5; ++v) acc[m][v] = learned ? sc.LH[(long long)v * g.Ptot + d.pbase + t] : 0.0;
   for (int l = 0; l < sc.C; ++l) {
-    const double* src = ring + (long long)((sc.n - kd - l) % sc.R) * lvN;
+    const double* src = ring + (long long)slot(l) * lvN;
     double r[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) r[v] = src[v * d.bN + gi];

@@ -420,6 +420,7 @@ __host__ __device__ inline size_t filter_smem_bytes(int Lmax, int precision) {
 template <typename T, int axis>
 __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, FilterLaunch f) {
   sc = resolve(sc);
+  if (f.only_sync && sc.mode != 0) return;
   constexpr bool F32 = std::is_same<T, float>::value;
   const double* __restrict__ Uin = ring_or(f.Uin, f.in_ring, f.ring, sc, 0);
   double* __restrict__ Uout = const_cast<double*>(ring_or(f.Uout, f.out_ring, f.ring, sc, 1));
