@@ -28,7 +28,7 @@ __host__ __device__ constexpr int fb_row(int n) { return n | 1; }
 
 template <int N>
 __host__ __device__ inline size_t fb_smem(void) {
-  return sizeof(float) * ((size_t)fb_row(N) * N * N + 2 * N + 10 * N * N);
+  return sizeof(float) * ((size_t)fb_row(N) * N * N + 2 * N + 10 * (N * N + 1));
 }
 
 template <int N>
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) k_filter_block(Geometry g, Step
   extern __shared__ __align__(16) float fbs[];
   float* blk = fbs;                   // [N][N][RX]: deviations, x fastest
   float* sTh = fbs + (size_t)RXY * N;  // cp[N], im[N]
-  float* sHalo = sTh + 2 * N;          // [10][N * N]: the halo deviations of every line of a pass
+  float* sHalo = sTh + 2 * N;          // [10][N * N + 1]: the halo deviations of every line of a pass
   const int tid = threadIdx.x;
   const long long plane = (long long)d.bnx * d.bny;
   const long long vbase = d.bbase + (long long)var * d.bN;
@@ -80,8 +80,9 @@ __global__ void __launch_bounds__(FB_THREADS, 1) k_filter_block(Geometry g, Step
     const int st[3] = {1, RX, RXY};
     const int sa = st[axis];
     // ---- halo: 5 points beyond each end of every line, from the ring (wrapped in the block);
-    // item e = (h, line) with the line fastest, so that consecutive threads read consecutive
-    // points for the y and z passes; every item's C level loads are independent
+    // items (h, line) ordered so that consecutive threads read consecutive points: h fastest
+    // for the x pass (the 5 points of an end are adjacent in x), the line (x fastest)
+    // otherwise; every item's C level loads are independent
     const int kd[2] = {face_delay(sc, sid, 2 * axis), face_delay(sc, sid, 2 * axis + 1)};
     // per end: ring-level offsets and extrapolation weights c(k + 1) of the C delayed levels
     long long lev[2][CFS_MAX_LEVELS];
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) k_filter_block(Geometry g, Step
     const int nlev = sc.mode == 2 ? 1 : sc.C;
 #pragma unroll 4
     for (int e = tid; e < 10 * N * N; e += FB_THREADS) {
-      const int h = e / (N * N), l = e % (N * N);
+      const int h = axis == 0 ? e % 10 : e / (N * N), l = axis == 0 ? e / 10 : e % (N * N);
       const int t1 = l % N, t2 = l / N;
       const int sd = h < 5 ? 0 : 1;
       int ca = o3[axis] + (h < 5 ? h - 5 : N + h - 5);
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(FB_THREADS, 1) k_filter_block(Geometry g, Step
 #pragma unroll
       for (int lv = 0; lv < CFS_MAX_LEVELS; ++lv)
         if (lv < nlev) v = fma(sd ? wf[1][lv] : wf[0][lv], r[lv], v);
-      sHalo[e] = dev_fast(v, rh, rl);
+      sHalo[h * (N * N + 1) + l] = dev_fast(v, rh, rl);
     }
     __syncthreads();
 #pragma unroll 1
@@ -126,8 +127,8 @@ __global__ void __launch_bounds__(FB_THREADS, 1) k_filter_block(Geometry g, Step
       for (int i = 0; i < N; ++i) w[i + 5] = blk[base + i * sa];
 #pragma unroll
       for (int h = 0; h < 5; ++h) {
-        w[h] = sHalo[h * N * N + l];
-        w[N + 5 + h] = sHalo[(5 + h) * N * N + l];
+        w[h] = sHalo[h * (N * N + 1) + l];
+        w[N + 5 + h] = sHalo[(5 + h) * (N * N + 1) + l];
       }
       // right side sum_n (a_n/2)(f_{i+n} + f_{i-n}) - (alpha f_{i-1} + f_i + alpha f_{i+1}), written
       // as second differences; forward elimination
