@@ -258,9 +258,11 @@ __device__ __forceinline__ void column_point(const SubDev& d, int f, int t1, int
   else c[a] = side == 0 ? j - 1 : sz[a] - j;
 }
 
-// index within a state array: the block's offset plus the wrapped point of the block (variable 0)
+// index within a state array: the block's offset plus the wrapped point of the block (variable 0);
+// column points lie within HDEPTH of the sub-domain, so one conditional wrap per axis suffices
 __device__ __forceinline__ long long global_index(const Geometry& g, const SubDev& d, const int c[3]) {
-  const int gx = wrapc(d.ox + c[0], d.bnx), gy = wrapc(d.oy + c[1], d.bny), gz = wrapc(d.oz + c[2], d.bnz);
+  auto w1 = [](int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); };
+  const int gx = w1(d.ox + c[0], d.bnx), gy = w1(d.oy + c[1], d.bny), gz = w1(d.oz + c[2], d.bnz);
   return d.bbase + (long long)gx + (long long)d.bnx * ((long long)gy + (long long)d.bny * gz);
 }
 
@@ -268,24 +270,28 @@ __device__ __forceinline__ float bf16r(double x) { return __bfloat162float(__flo
 
 // Features of depth j of one column: halo level differences (10 values), own-side change (5
 // values), the 3-level extrapolation of the halo point (5 values, FP64) and optionally the truth.
+// Feature e of the column goes to xrow[e * xs].
 __device__ __forceinline__ void column_depth(const Geometry& g, const StepSched& sc, const double* __restrict__ ring,
                                              const SubDev& d, int f, int t1, int t2, int k, int j, const MlpScales& ms,
-                                             const double* at3w, float* xrow, double* at3, double* truth) {
+                                             const double* at3w, float* xrow, int xs, double* at3, double* truth) {
   const long long lvN = 5 * g.N;
   int c[3];
   column_point(d, f, t1, t2, j, true, c);
   const long long gh = global_index(g, d, c);
   column_point(d, f, t1, t2, j, false, c);
   const long long go = global_index(g, d, c);
-  const double* Lk0 = ring + (long long)((sc.n - k) % sc.R) * lvN;
-  const double* Lk1 = ring + (long long)((sc.n - k - 1) % sc.R) * lvN;
-  const double* Lk2 = ring + (long long)((sc.n - k - 2) % sc.R) * lvN;
-  const double* Ln = ring + (long long)(sc.n % sc.R) * lvN;
+  // ring slots of levels n, n-k, n-k-1, n-k-2 (k + 2 < R)
+  const int nR = (int)(sc.n % sc.R);
+  auto slot = [&](int back) { const int q = nR - back; return q < 0 ? q + sc.R : q; };
+  const double* Lk0 = ring + (long long)slot(k) * lvN;
+  const double* Lk1 = ring + (long long)slot(k + 1) * lvN;
+  const double* Lk2 = ring + (long long)slot(k + 2) * lvN;
+  const double* Ln = ring + (long long)nR * lvN;
   for (int v = 0; v < 5; ++v) {
     const double a = Lk0[v * d.bN + gh], b = Lk1[v * d.bN + gh], cc = Lk2[v * d.bN + gh];
-    xrow[(j - 1) * 5 + v] = bf16r((a - b) * ms.in[v]);
-    xrow[MLP_HDEPTH * 5 + (j - 1) * 5 + v] = bf16r((b - cc) * ms.in[v]);
-    xrow[2 * MLP_HDEPTH * 5 + (j - 1) * 5 + v] = bf16r((Ln[v * d.bN + go] - Lk0[v * d.bN + go]) * ms.own[v]);
+    xrow[((j - 1) * 5 + v) * xs] = bf16r((a - b) * ms.in[v]);
+    xrow[(MLP_HDEPTH * 5 + (j - 1) * 5 + v) * xs] = bf16r((b - cc) * ms.in[v]);
+    xrow[(2 * MLP_HDEPTH * 5 + (j - 1) * 5 + v) * xs] = bf16r((Ln[v * d.bN + go] - Lk0[v * d.bN + go]) * ms.own[v]);
     at3[(j - 1) * 5 + v] = fma(at3w[0], a, fma(at3w[1], b, at3w[2] * cc));
     if (truth) truth[(j - 1) * 5 + v] = Ln[v * d.bN + gh];
   }
@@ -308,41 +314,109 @@ __global__ void k_halo_samples(Geometry g, StepSched sc, const double* __restric
   const SubDev d = subs[sid];
   float xrow[MLP_NIN];
   double at3[MLP_NOUT], truth[MLP_NOUT];
-  for (int j = 1; j <= MLP_HDEPTH; ++j) column_depth(g, sc, ring, d, f, t1, t2, k, j, ms, t3.w[k], xrow, at3, truth);
+  for (int j = 1; j <= MLP_HDEPTH; ++j) column_depth(g, sc, ring, d, f, t1, t2, k, j, ms, t3.w[k], xrow, 1, at3, truth);
   for (int q = 0; q <= MLP_KMAX; ++q) xrow[3 * MLP_HDEPTH * 5 + q] = (q == k) ? 1.f : 0.f;
   for (int e = 0; e < MLP_NIN; ++e) x[i * MLP_NIN + e] = __float2bfloat16_rn(xrow[e]);
   for (int e = 0; e < MLP_NOUT; ++e) target[i * MLP_NOUT + e] = (float)((truth[e] - at3[e]) * ms.out[e % 5]);
 }
 
-// Solver use: each CTA takes S face columns (sub-domain, face, t1, t2), gathers their features at
-// the face's delay, runs the network and writes U^(0) = extrapolation + residual / out scale for
-// the HDEPTH halo points of each column into LH (FP64, padded-box layout).
-__global__ void __launch_bounds__(NT) k_mlp_halo(Geometry g, StepSched sc, const double* __restrict__ ring,
-                                                  const SubDev* __restrict__ subs, const int* __restrict__ cols,
-                                                  long long ncol, const float* __restrict__ params, MlpScales ms,
-                                                  At3Table t3, double* __restrict__ LH) {
+// Solver use: each CTA takes SP face columns (sub-domain, face, t1, t2) at a time, gathers their
+// features at the face's delay (one thread per column depth), runs the network and writes
+// U^(0) = extrapolation + residual / out scale for the HDEPTH halo points of each column into LH
+// (FP64, padded-box layout).  The layers are register-blocked: a thread computes 4 samples x 4
+// outputs from float4 loads of the transposed activations and weights (two shared-memory loads
+// per 16 FMA); every output accumulates its inputs in the same order as the training kernels,
+// so inference gives the same bits.
+namespace {
+
+constexpr int SP = 64;                       // columns per CTA iteration
+constexpr int NOUTP = 20;                    // NOUT, a multiple of 4
+
+struct HaloSmem {
+  __align__(16) float wT1[MLP_NIN][MLP_NH];
+  __align__(16) float b1[MLP_NH];
+  __align__(16) float wT2[MLP_NH][MLP_NH];
+  __align__(16) float b2[MLP_NH];
+  __align__(16) float wT3[MLP_NH][NOUTP];
+  __align__(16) float b3[NOUTP];
+  __align__(16) float xT[MLP_NIN][SP];
+  __align__(16) float h1T[MLP_NH][SP];
+  __align__(16) float h2T[MLP_NH][SP];
+  __align__(16) float yT[NOUTP][SP];
+  double at3[SP][MLP_NOUT];
+};
+
+// out^T[o][s] = act(b[o] + sum_i W[o][i] in[s][i]) with transposed operands wT[i][o], inT[i][s].
+template <int NIN, int NOUT, bool ACT>
+__device__ __forceinline__ void layer_blocked(const float (*wT)[NOUT], const float* b, const float (*inT)[SP],
+                                              float (*outT)[SP]) {
+  constexpr int NOG = NOUT / 4, NSG = SP / 4;
+  for (int t = threadIdx.x; t < NOG * NSG; t += NT) {
+    const int og = t % NOG, sg = t / NOG;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] = b[4 * og + c];
+#pragma unroll 5
+    for (int i = 0; i < NIN; ++i) {
+      const float4 xv = *reinterpret_cast<const float4*>(&inT[i][4 * sg]);
+      const float4 wv = *reinterpret_cast<const float4*>(&wT[i][4 * og]);
+      const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, wc[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(wc[c], xa[a], acc[a][c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) outT[4 * og + c][4 * sg + a] = ACT ? gelu(acc[a][c]) : acc[a][c];
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(NT, 2) k_mlp_halo(Geometry g, StepSched sc, const double* __restrict__ ring,
+                                                     const SubDev* __restrict__ subs, const int* __restrict__ cols,
+                                                     long long ncol, const float* __restrict__ params, MlpScales ms,
+                                                     At3Table t3, double* __restrict__ LH) {
   sc = resolve(sc);
   if (sc.mode != 1) return;  // the network replaces AT halos only
   extern __shared__ __align__(16) unsigned char raw[];
-  Smem& sm = *reinterpret_cast<Smem*>(raw);
-  __shared__ double s_at3[S][MLP_NOUT];
-  for (int p = threadIdx.x; p < MLP_NPARAM; p += NT) sm.w[p] = params[p];
-  for (long long base = (long long)blockIdx.x * S; base < ncol; base += (long long)gridDim.x * S) {
-    const int ns = (int)min((long long)S, ncol - base);
-    // gather: 8 threads per column, thread r handles depth (r % 4) + 1 (features are per depth)
+  HaloSmem& sm = *reinterpret_cast<HaloSmem*>(raw);
+  // weights transposed once per CTA
+  for (int p = threadIdx.x; p < MLP_NH * MLP_NIN; p += NT) sm.wT1[p % MLP_NIN][p / MLP_NIN] = params[MLP_OFF_W1 + p];
+  for (int p = threadIdx.x; p < MLP_NH * MLP_NH; p += NT) sm.wT2[p % MLP_NH][p / MLP_NH] = params[MLP_OFF_W2 + p];
+  for (int p = threadIdx.x; p < MLP_NOUT * MLP_NH; p += NT) sm.wT3[p % MLP_NH][p / MLP_NH] = params[MLP_OFF_W3 + p];
+  for (int p = threadIdx.x; p < MLP_NH; p += NT) {
+    sm.b1[p] = params[MLP_OFF_B1 + p];
+    sm.b2[p] = params[MLP_OFF_B2 + p];
+  }
+  for (int p = threadIdx.x; p < NOUTP; p += NT) sm.b3[p] = params[MLP_OFF_B3 + p];
+  for (long long base = (long long)blockIdx.x * SP; base < ncol; base += (long long)gridDim.x * SP) {
+    const int ns = (int)min((long long)SP, ncol - base);
+    // gather: 4 threads per column, thread r handles depth r + 1 (features are per depth)
     {
-      const int col = threadIdx.x / 8, r = threadIdx.x % 8;
-      if (col < ns && r < MLP_HDEPTH) {
+      const int col = threadIdx.x / MLP_HDEPTH, r = threadIdx.x % MLP_HDEPTH;
+      if (col < ns) {
         const int* cp = cols + 4 * (base + col);
         const int sid = cp[0], f = cp[1], t1 = cp[2], t2 = cp[3];
         const int k = face_delay(sc, sid, f);
-        column_depth(g, sc, ring, subs[sid], f, t1, t2, k, r + 1, ms, t3.w[k], sm.x[col], s_at3[col], nullptr);
+        column_depth(g, sc, ring, subs[sid], f, t1, t2, k, r + 1, ms, t3.w[k], &sm.xT[0][col], SP, sm.at3[col], nullptr);
         if (r == 0)
-          for (int q = 0; q <= MLP_KMAX; ++q) sm.x[col][3 * MLP_HDEPTH * 5 + q] = (q == k) ? 1.f : 0.f;
+          for (int q = 0; q <= MLP_KMAX; ++q) sm.xT[3 * MLP_HDEPTH * 5 + q][col] = (q == k) ? 1.f : 0.f;
+      } else if (col < SP && r == 0) {
+        for (int i = 0; i < MLP_NIN; ++i) sm.xT[i][col] = 0.f;  // idle columns of a partial chunk
       }
     }
     __syncthreads();
-    forward_chunk(sm, ns);
+    layer_blocked<MLP_NIN, MLP_NH, true>(sm.wT1, sm.b1, sm.xT, sm.h1T);
+    __syncthreads();
+    layer_blocked<MLP_NH, MLP_NH, true>(sm.wT2, sm.b2, sm.h1T, sm.h2T);
+    __syncthreads();
+    layer_blocked<MLP_NH, NOUTP, false>(sm.wT3, sm.b3, sm.h2T, sm.yT);
+    __syncthreads();
     for (int e = threadIdx.x; e < ns * MLP_NOUT; e += NT) {
       const int col = e / MLP_NOUT, o = e % MLP_NOUT, j = o / 5 + 1, v = o % 5;
       const int* cp = cols + 4 * (base + col);
@@ -350,7 +424,7 @@ __global__ void __launch_bounds__(NT) k_mlp_halo(Geometry g, StepSched sc, const
       int c[3];
       column_point(d, cp[1], cp[2], cp[3], j, true, c);
       const long long q = (long long)(c[0] + g.G) + (long long)d.ex * ((long long)(c[1] + g.G) + (long long)d.ey * (c[2] + g.Gz));
-      LH[(long long)v * g.Ptot + d.pbase + q] = s_at3[col][o] + (double)sm.y[col][o] / ms.out[v];
+      LH[(long long)v * g.Ptot + d.pbase + q] = sm.at3[col][o] + (double)sm.yT[o][col] / ms.out[v];
     }
     __syncthreads();
   }
@@ -380,14 +454,14 @@ int launch_mlp_halo(const Geometry& g, const StepSched& sc, const double* ring, 
   if (int e = set_attr()) return e;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(HaloSmem));
     if (e != cudaSuccess) return (int)e;
     attr = true;
   }
-  const long long nchunk = (ncol + S - 1) / S;
+  const long long nchunk = (ncol + SP - 1) / SP;
   const unsigned grid = (unsigned)std::min<long long>(nchunk, 152LL * 2);
   if (tm) tm->rec(tm->self, 0, 1);
-  k_mlp_halo<<<grid, NT, sizeof(Smem), (cudaStream_t)stream>>>(g, sc, ring, subs, cols, ncol, params, ms, at3_table(), LH);
+  k_mlp_halo<<<grid, NT, sizeof(HaloSmem), (cudaStream_t)stream>>>(g, sc, ring, subs, cols, ncol, params, ms, at3_table(), LH);
   if (tm) tm->rec(tm->self, 0, 0);
   if (launches) *launches += 1;
   return (int)cudaGetLastError();
