@@ -67,6 +67,23 @@ def measured_peaks():
         return {}
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest value of a per-rank number (a time) over the ranks of the process group; the
+    number itself on a single rank."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput in millions per second: the units all ranks processed over the time
+    of the slowest rank (replicas: every rank advances its own problem of the same size)."""
+    return units_per_rank * world / seconds / 1e6
+
+
 def workload(algo="SAA", grid=128, split=4):
     from paper_2506_03027_gb300 import inputs as I
     c = I.tgv_case(grid, split, algo)
@@ -247,12 +264,9 @@ def run_ours(args, rank, world, local_rank):
     launches = solver.launches()
     ktimes = cfs.cfs_get_timing(solver.ctx)
     cfs.cfs_set_timing(solver.ctx, False)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     n_units = case.npts * case.stages * K * world
-    value = n_units / (ms * 1e-3) / 1e6
+    value = whole_job_rate(case.npts * case.stages * K, world, ms * 1e-3)
 
     # ---------------- end to end through the public API with host buffers
     host = torch.empty((5, case.nz, case.ny, case.nx), dtype=torch.float64, pin_memory=True)
@@ -269,11 +283,8 @@ def run_ours(args, rank, world, local_rank):
         solver.get_state(hnp)          # device -> host copy of the step's result (synchronises)
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([te], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        te = float(t.item())
-    e2e_value = case.npts * case.stages * Ke * world / te / 1e6
+    te = max_over_ranks(te, world)
+    e2e_value = whole_job_rate(case.npts * case.stages * Ke, world, te)
     state_bytes = 5 * case.npts * 8
     U_fp64 = solver.get_state()
     n_done = solver.n
