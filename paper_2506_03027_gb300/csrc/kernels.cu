@@ -62,9 +62,9 @@ __global__ void __launch_bounds__(512) k_view_own(Geometry g, Physics ph, StepSc
   const double* Uin = ring_or(Uin0, in_ring, ring, sc, 0);
   const int sid = blockIdx.y;
   const SubDev d = subs[sid];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)d.sx * d.sy * d.sz) return;
-  const int ci = (int)(t % d.sx), cj = (int)((t / d.sx) % d.sy), ck = (int)(t / ((long long)d.sx * d.sy));
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // own points of a sub-domain: < 2^31
+  if (t >= d.sx * d.sy * d.sz) return;
+  const int sxy = d.sx * d.sy, ck = t / sxy, r2 = t - ck * sxy, cj = r2 / d.sx, ci = r2 - cj * d.sx;
   const long long gi = (long long)(d.ox + ci) + (long long)d.bnx * ((long long)(d.oy + cj) + (long long)d.bny * (d.oz + ck));
   const long long q = (long long)(ci + g.G) + (long long)d.ex * ((long long)(cj + g.G) + (long long)d.ey * (ck + g.Gz));
   double u[5];
@@ -88,12 +88,17 @@ __global__ void __launch_bounds__(512) k_view_halo(Geometry g, Physics ph, StepS
   if (t >= nhalo) return;
   const int2 e = halo[t];
   const int sid = e.x;
-  const long long q = e.y;
+  const int q = e.y;  // index in the sub-domain's padded box (32-bit)
   const SubDev d = subs[sid];
-  const int i = (int)(q % d.ex), j = (int)((q / d.ex) % d.ey), k = (int)(q / ((long long)d.ex * d.ey));
+  const int exy = d.ex * d.ey;
+  const int k = q / exy, r2 = q - k * exy, j = r2 / d.ex, i = r2 - j * d.ex;
   const int ci = i - g.G, cj = j - g.G, ck = k - g.Gz;
-  const int gx = wrapc(d.ox + ci, d.bnx), gy = wrapc(d.oy + cj, d.bny), gz = wrapc(d.oz + ck, d.bnz);
+  // halo points lie within G of the sub-domain: one conditional wrap per axis
+  auto wrap1 = [](int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); };
+  const int gx = wrap1(d.ox + ci, d.bnx), gy = wrap1(d.oy + cj, d.bny), gz = wrap1(d.oz + ck, d.bnz);
   const long long gi = d.bbase + (long long)gx + (long long)d.bnx * ((long long)gy + (long long)d.bny * gz);
+  // ring slot of level n - kd - l: (n mod R) - kd - l, wrapped once (kd + l < R)
+  const int nR = (int)(sc.n % sc.R);
   double u[5];
   if (sc.mode == 0) {
 #pragma unroll
@@ -104,8 +109,9 @@ __global__ void __launch_bounds__(512) k_view_halo(Geometry g, Physics ph, StepS
     if (cj < 0 || cj >= d.sy) kd = max(kd, face_delay(sc, sid, cj < 0 ? 2 : 3));
     if (ck < 0 || ck >= d.sz) kd = max(kd, face_delay(sc, sid, ck < 0 ? 4 : 5));
     const long long lvN = 5 * g.N;
+    auto slot = [&](int l) { const int qq = nR - kd - l; return qq < 0 ? qq + sc.R : qq; };
     if (sc.mode == 2) {
-      const double* src = ring + (long long)((sc.n - kd) % sc.R) * lvN;
+      const double* src = ring + (long long)slot(0) * lvN;
 #pragma unroll
       for (int v = 0; v < 5; ++v) u[v] = src[v * d.bN + gi];
     } else {
@@ -119,7 +125,7 @@ __global__ void __launch_bounds__(512) k_view_halo(Geometry g, Physics ph, StepS
         for (int v = 0; v < 5; ++v) u[v] = sc.LH[(long long)v * g.Ptot + d.pbase + q];
         if (stage > 0)
           for (int l = 0; l < sc.C; ++l) {
-            const double* src = ring + (long long)((sc.n - kd - l) % sc.R) * lvN;
+            const double* src = ring + (long long)slot(l) * lvN;
             const double wl = __ldg(w + l) - __ldg(w0 + l);
 #pragma unroll
             for (int v = 0; v < 5; ++v) u[v] = fma(wl, src[v * d.bN + gi], u[v]);
@@ -128,7 +134,7 @@ __global__ void __launch_bounds__(512) k_view_halo(Geometry g, Physics ph, StepS
 #pragma unroll
         for (int v = 0; v < 5; ++v) u[v] = 0.0;
         for (int l = 0; l < sc.C; ++l) {
-          const double* src = ring + (long long)((sc.n - kd - l) % sc.R) * lvN;
+          const double* src = ring + (long long)slot(l) * lvN;
           const double wl = __ldg(w + l);
 #pragma unroll
           for (int v = 0; v < 5; ++v) u[v] = fma(wl, src[v * d.bN + gi], u[v]);
@@ -229,9 +235,9 @@ __global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubD
   const int r = g.r;
   const int rz = (ND == 3) ? r : 0;
   const int fx = d.sx + 2 * r, fy = d.sy + 2 * r, fz = d.sz + 2 * rz;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)fx * fy * fz) return;
-  const int a0 = (int)(t % fx), b0 = (int)((t / fx) % fy), c0 = (int)(t / ((long long)fx * fy));
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // flux points of a sub-domain: < 2^31
+  if (t >= fx * fy * fz) return;
+  const int fxy = fx * fy, c0 = t / fxy, r2 = t - c0 * fxy, b0 = r2 / fx, a0 = r2 - b0 * fx;
   const int ci = a0 - r, cj = b0 - r, ck = c0 - rz;
   const bool ox = ci < 0 || ci >= d.sx, oy = cj < 0 || cj >= d.sy, oz = ck < 0 || ck >= d.sz;
   const int nout = (int)ox + (int)oy + (int)oz;
@@ -317,9 +323,9 @@ __global__ void __launch_bounds__(512) k_rk(Geometry g, Physics ph, StepSched sc
   double* Uout = const_cast<double*>(ring_or(Uout0, out_ring, ring, sc, 1));
   const int sid = blockIdx.y;
   const SubDev d = subs[sid];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)d.sx * d.sy * d.sz) return;
-  const int ci = (int)(t % d.sx), cj = (int)((t / d.sx) % d.sy), ck = (int)(t / ((long long)d.sx * d.sy));
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // own points of a sub-domain: < 2^31
+  if (t >= d.sx * d.sy * d.sz) return;
+  const int sxy = d.sx * d.sy, ck = t / sxy, r2 = t - ck * sxy, cj = r2 / d.sx, ci = r2 - cj * d.sx;
   const long long sty = d.ex, stz = (long long)d.ex * d.ey;
   const long long q = (long long)(ci + g.G) + sty * (cj + g.G) + stz * (ck + g.Gz);
   const long long gi = d.bbase + (long long)(d.ox + ci) + (long long)d.bnx * ((long long)(d.oy + cj) + (long long)d.bny * (d.oz + ck));
