@@ -266,7 +266,9 @@ __device__ __forceinline__ long long global_index(const Geometry& g, const SubDe
   return d.bbase + (long long)gx + (long long)d.bnx * ((long long)gy + (long long)d.bny * gz);
 }
 
-__device__ __forceinline__ float bf16r(double x) { return __bfloat162float(__float2bfloat16_rn((float)x)); }
+// FP64 -> FP32 -> BF16 (FP32 step on the integer pipe: round to nearest, ties away from zero,
+// which differs from the FP64 pipe's conversion only on exact FP32 ties)
+__device__ __forceinline__ float bf16r(double x) { return __bfloat162float(__float2bfloat16_rn(d2f_fast(x))); }
 
 // Features of depth j of one column: halo level differences (10 values), own-side change (5
 // values), the 3-level extrapolation of the halo point (5 values, FP64) and optionally the truth.
@@ -385,6 +387,10 @@ __global__ void __launch_bounds__(NT, 2) k_mlp_halo(Geometry g, StepSched sc, co
   if (sc.mode != 1) return;  // the network replaces AT halos only
   extern __shared__ __align__(16) unsigned char raw[];
   HaloSmem& sm = *reinterpret_cast<HaloSmem*>(raw);
+  // reciprocal output scales (one division per thread instead of one per output)
+  double inv_out[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) inv_out[v] = 1.0 / ms.out[v];
   // weights transposed once per CTA
   for (int p = threadIdx.x; p < MLP_NH * MLP_NIN; p += NT) sm.wT1[p % MLP_NIN][p / MLP_NIN] = params[MLP_OFF_W1 + p];
   for (int p = threadIdx.x; p < MLP_NH * MLP_NH; p += NT) sm.wT2[p % MLP_NH][p / MLP_NH] = params[MLP_OFF_W2 + p];
@@ -424,7 +430,10 @@ __global__ void __launch_bounds__(NT, 2) k_mlp_halo(Geometry g, StepSched sc, co
       int c[3];
       column_point(d, cp[1], cp[2], cp[3], j, true, c);
       const long long q = (long long)(c[0] + g.G) + (long long)d.ex * ((long long)(c[1] + g.G) + (long long)d.ey * (c[2] + g.Gz));
-      LH[(long long)v * g.Ptot + d.pbase + q] = sm.at3[col][o] + (double)sm.yT[o][col] / ms.out[v];
+      double iv = inv_out[0];
+#pragma unroll
+      for (int vv = 1; vv < 5; ++vv) iv = v == vv ? inv_out[vv] : iv;
+      LH[(long long)v * g.Ptot + d.pbase + q] = fma((double)sm.yT[o][col], iv, sm.at3[col][o]);
     }
     __syncthreads();
   }

@@ -239,6 +239,35 @@ def test_fp32_form_subdomain_filter(n, algo):
     assert np.all(np.isfinite(res[0])) and np.all(e < 1e-6), e
 
 
+@pytest.mark.parametrize("algo", ["SA", "CAA", "SAA"])
+def test_kinetic_energy_history(algo):
+    """The Taylor-Green configuration's three runs (synchronous, CAA with L = 4, SAA with delays
+    0..3): the kinetic energy and enstrophy after every step, and the dissipation rate -dK/dt from
+    them, against the oracle's history."""
+    c = small_tgv(algo, n=32, p=4, kmax=3, cfl=0.1 if algo == "SAA" else 0.25)
+    nst = 30
+    d = I.saa_delays(c, nst) if algo == "SAA" else None
+    U0 = I.tgv_state(c)
+    s = cfs.Solver(c)
+    hist = []
+    try:
+        s.set_schedule(delays=d)
+        s.set_state(U0)
+        for _ in range(nst):
+            s.step(1)
+            hist.append(s.diagnostics(check_finite=False)[:2])
+    finally:
+        s.close()
+    hist = np.array(hist)
+    _, do = orc.run(c, U0, nst, delays=d, diag=True)
+    ref = np.array([r[:2] for r in do])[-nst:]
+    np.testing.assert_allclose(hist, ref, rtol=1e-11, atol=0)
+    eps = -(hist[2:, 0] - hist[:-2, 0]) / (2 * c.dt)
+    eps_ref = -(ref[2:, 0] - ref[:-2, 0]) / (2 * c.dt)
+    assert np.all(eps_ref > 0)  # viscous decay of the kinetic energy
+    assert np.abs(eps - eps_ref).max() <= 1e-5 * np.abs(eps_ref).max()
+
+
 def test_batched_uneven_blocks_parity():
     """Three independent periodic blocks of uneven sizes and splits advance together (one launch
     per kernel over the sub-domains of all blocks); each block equals its own oracle run, with the
