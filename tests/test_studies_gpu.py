@@ -1,0 +1,23 @@
+"""The asynchrony error of CAA-AT (LSERK2-CD2-AT2, Table 1 case 3) on the translating vortex
+grows with the maximum allowable delay L faster than linearly, as the error estimate of the AT
+schemes (a polynomial in the moments of the delay) predicts -- the study behind Fig. 4."""
+import numpy as np
+import pytest
+
+from gpu_util import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+def test_async_error_grows_with_the_delay():
+    ensure_built()
+    from paper_2506_03027_gb300 import studies
+    r = studies.async_error_vs_delay(256, 8, (1, 2, 3, 4, 6), t_end=0.5)
+    E = np.array(r["async_error"])
+    print(r)
+    assert np.all(np.isfinite(E)) and np.all(E > 0)
+    assert np.all(np.diff(E) > 0), E                  # monotone in L
+    assert E[4] / E[2] >= 4.0, E                      # L 3 -> 6: at least quadratic
+    assert E[-1] < 0.1 * r["sa_error"], r             # asynchrony error stays below the scheme's own
+    g, res = studies.cubic_fit(r["L"], E)
+    assert res < 0.1, (g, res)                        # a cubic in L describes it
