@@ -197,10 +197,10 @@ cfs_status cfs_get_timing(cfs_ctx* ctx, double* ms, long long* count);
  *   x[20..39]  (U^{n-k-1} - U^{n-k-2}) * in_scale[v],
  *   x[40..59]  (U^n - U^{n-k}) * own_scale[v] at the 4 own points next to the face,
  *   x[60..64]  one-hot delay k (0..4),
- * each rounded FP64 -> FP32 -> BF16 (round to nearest even), index (depth - 1) * 5 + v.
+ * each rounded FP64 -> FP32 (to nearest) -> BF16 (to nearest even), index (depth - 1) * 5 + v.
  * Output y[(depth - 1) * 5 + v] = (U^n - extrapolation) * out_scale[v].  Parameters are FP32:
  * W1[64][65], b1[64], W2[64][64], b2[64], W3[20][64], b3[20] (CFS_MLP_NPARAM floats).  The paper has
- * no counterpart: this is the learned form of the halo that the plain AT stencil is judged against. */
+ * no counterpart: this is the learned form of the halo, compared against the plain AT stencil. */
 #define CFS_MLP_NIN 65
 #define CFS_MLP_NOUT 20
 #define CFS_MLP_NPARAM 9684
