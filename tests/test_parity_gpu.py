@@ -110,6 +110,28 @@ def test_full_size_tgv_saa_parity():
     check(Ug, Uo)
 
 
+def test_full_size_fp32_form_caa():
+    """The precision configuration at its full size and launch shapes: TGV 256^3, 8x8x8
+    sub-domains of 32^3, CAA L = 4, FP32 intermediates through the fused stage (tiles 32 x 16,
+    z chunks of 32), the per-step AT halo kernel and the sub-domain filter; 7 steps (5 synchronous
+    + 2 asynchronous), whole fields against the FP64 oracle within the FP32-form bound."""
+    c = I.tgv_case(256, 8, "CAA")
+    c = c.replace(dt=I.cfl_dt(c, I.tgv_state(c), 0.25))
+    nsteps = 7
+    U0 = I.tgv_state(c)
+    s = cfs.Solver(c, precision=1, tiles=(16, 32, 256))
+    try:
+        s.set_schedule()
+        s.set_state(U0)
+        s.step(nsteps)
+        Ug = s.get_state()
+    finally:
+        s.close()
+    Uo = orc.run(c, U0, nsteps)
+    e = rel_l2(Ug, Uo)
+    assert np.all(np.isfinite(Ug)) and np.all(e < 1e-6), e
+
+
 def test_checkpoint_resume_is_exact():
     """Ring + step index restore: 7 steps, checkpoint, 5 more in a new context equals 12 steps."""
     c = small_tgv("SAA", n=24, p=2, kmax=3)
