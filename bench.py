@@ -337,6 +337,11 @@ def run_ours(args, rank, world, local_rank):
         forms = forms or {}
         forms["learned_halo"] = learned_form(args)
 
+    # ---------------- the three algorithms and the second-order schemes on the same grid
+    if args.precision == 0 and not args.no_forms and world == 1:
+        forms = forms or {}
+        forms["algorithms"] = algorithms_form(args)
+
     # ---------------- roofline of the dominant kernel
     peaks = measured_peaks()
     clocks = clk.summary()
@@ -499,6 +504,46 @@ def precision_form_256(args):
             "fused_stage_roofline": fused_roofline(case, res[1]["kt"]),
             "workload": "TGV NS 256^3, 8x8x8 sub-domains, CAA L=4 AT4 at CFL 0.25, filter alpha_f 0.499; "
                         "error against the FP64 path from the same initial state"}
+
+
+def algorithms_form(args):
+    """Throughput of the synchronous (SA), communication-avoiding (CAA, L = 4) and
+    synchronization-avoiding (SAA, delays 0..3) runs of the benchmark grid with the fourth-order
+    schemes (Table 1 cases 4 and 6), and of SA / SAA with the second-order ones (cases 1 and 3:
+    LSERK2, CD2, AT2).  On one GPU there is no communication for the asynchrony to avoid; this
+    measures what the AT halo treatment costs against the synchronous halo."""
+    import torch
+    from paper_2506_03027_gb300 import cfs
+    from paper_2506_03027_gb300 import inputs as I
+    K, W = max(3, args.steps // 4), max(args.warmup, 6)
+    out = {"unit": UNIT}
+    for order in (4, 2):
+        for algo in ("SA", "CAA", "SAA"):
+            if order == 2 and algo == "CAA":
+                continue
+            case = workload(algo, 128, 4)
+            if order == 2:
+                case = case.replace(order=2, kmax=min(case.kmax, 3))
+            d = I.saa_delays(case, W + K) if algo == "SAA" else None
+            s = cfs.Solver(case)
+            try:
+                s.set_schedule(delays=d)
+                s.set_state(I.tgv_state(case))
+                s.step(W)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                s.step(K)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / K
+            finally:
+                s.close()
+            out[f"order{order}_{algo}"] = {"value": case.npts * case.stages / (ms * 1e-3) / 1e6, "ms_per_step": ms}
+    out["workload"] = ("TGV NS 128^3, 4x4x4 sub-domains, filter; order 4: LSERK4-CD4-AT4, order 2: LSERK2-CD2-AT2; "
+                       "CAA L=4, SAA delays 0..3; steps after the synchronous warm-up")
+    return out
 
 
 def learned_form(args):
