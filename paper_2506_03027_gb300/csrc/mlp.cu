@@ -272,10 +272,11 @@ __device__ __forceinline__ float bf16r(double x) { return __bfloat162float(__flo
 
 // Features of depth j of one column: halo level differences (10 values), own-side change (5
 // values), the 3-level extrapolation of the halo point (5 values, FP64) and optionally the truth.
-// Feature e of the column goes to xrow[e * xs].
+// put(e, value) receives feature e of the column.
+template <class Put>
 __device__ __forceinline__ void column_depth(const Geometry& g, const StepSched& sc, const double* __restrict__ ring,
                                              const SubDev& d, int f, int t1, int t2, int k, int j, const MlpScales& ms,
-                                             const double* at3w, float* xrow, int xs, double* at3, double* truth) {
+                                             const double* at3w, Put put, double* at3, double* truth) {
   const long long lvN = 5 * g.N;
   int c[3];
   column_point(d, f, t1, t2, j, true, c);
@@ -291,9 +292,9 @@ __device__ __forceinline__ void column_depth(const Geometry& g, const StepSched&
   const double* Ln = ring + (long long)nR * lvN;
   for (int v = 0; v < 5; ++v) {
     const double a = Lk0[v * d.bN + gh], b = Lk1[v * d.bN + gh], cc = Lk2[v * d.bN + gh];
-    xrow[((j - 1) * 5 + v) * xs] = bf16r((a - b) * ms.in[v]);
-    xrow[(MLP_HDEPTH * 5 + (j - 1) * 5 + v) * xs] = bf16r((b - cc) * ms.in[v]);
-    xrow[(2 * MLP_HDEPTH * 5 + (j - 1) * 5 + v) * xs] = bf16r((Ln[v * d.bN + go] - Lk0[v * d.bN + go]) * ms.own[v]);
+    put((j - 1) * 5 + v, bf16r((a - b) * ms.in[v]));
+    put(MLP_HDEPTH * 5 + (j - 1) * 5 + v, bf16r((b - cc) * ms.in[v]));
+    put(2 * MLP_HDEPTH * 5 + (j - 1) * 5 + v, bf16r((Ln[v * d.bN + go] - Lk0[v * d.bN + go]) * ms.own[v]));
     at3[(j - 1) * 5 + v] = fma(at3w[0], a, fma(at3w[1], b, at3w[2] * cc));
     if (truth) truth[(j - 1) * 5 + v] = Ln[v * d.bN + gh];
   }
@@ -316,126 +317,330 @@ __global__ void k_halo_samples(Geometry g, StepSched sc, const double* __restric
   const SubDev d = subs[sid];
   float xrow[MLP_NIN];
   double at3[MLP_NOUT], truth[MLP_NOUT];
-  for (int j = 1; j <= MLP_HDEPTH; ++j) column_depth(g, sc, ring, d, f, t1, t2, k, j, ms, t3.w[k], xrow, 1, at3, truth);
+  auto put = [&](int e, float val) { xrow[e] = val; };
+  for (int j = 1; j <= MLP_HDEPTH; ++j) column_depth(g, sc, ring, d, f, t1, t2, k, j, ms, t3.w[k], put, at3, truth);
   for (int q = 0; q <= MLP_KMAX; ++q) xrow[3 * MLP_HDEPTH * 5 + q] = (q == k) ? 1.f : 0.f;
   for (int e = 0; e < MLP_NIN; ++e) x[i * MLP_NIN + e] = __float2bfloat16_rn(xrow[e]);
   for (int e = 0; e < MLP_NOUT; ++e) target[i * MLP_NOUT + e] = (float)((truth[e] - at3[e]) * ms.out[e % 5]);
 }
 
-// Solver use: each CTA takes SP face columns (sub-domain, face, t1, t2) at a time, gathers their
-// features at the face's delay (one thread per column depth), runs the network and writes
+// Solver use: each CTA takes TM = 128 face columns (sub-domain, face, t1, t2) at a time, gathers
+// their features at the face's delay, runs the network on the tensor cores and writes
 // U^(0) = extrapolation + residual / out scale for the HDEPTH halo points of each column into LH
-// (FP64, padded-box layout).  The layers are register-blocked: a thread computes 4 samples x 4
-// outputs from float4 loads of the transposed activations and weights (two shared-memory loads
-// per 16 FMA); every output accumulates its inputs in the same order as the training kernels,
-// so inference gives the same bits.
+// (FP64, padded-box layout).
+//
+// Every layer is one tcgen05 GEMM of M = 128 columns: D[m][n] = sum_k A[m][k] B[n][k] with A (the
+// activations) and B (the weights) in shared memory, K-major without swizzle (8-row x 16-byte core
+// matrices, K-adjacent cores 128 bytes apart, row groups K/4 x 128 bytes apart), D in tensor
+// memory (FP32).  The operands are FP32 values split into TF32 pairs x = hi + lo (hi rounded to 10
+// mantissa bits, lo = x - hi exactly); each K step issues hi*hi + hi*lo + lo*hi (kind::tf32, FP32
+// accumulation), which keeps the network at FP32 accuracy (the dropped lo*lo and the truncation of
+// lo are below 2^-21 relative).  The features are BF16 values, exact in TF32, so the first layer
+// needs A_hi only.  One thread issues the MMAs and commits them to an mbarrier; all threads wait
+// (bounded), read D with tcgen05.ld, add the bias, apply GELU and write the next layer's operands.
 namespace {
 
-constexpr int SP = 64;                       // columns per CTA iteration
-constexpr int NOUTP = 20;                    // NOUT, a multiple of 4
+constexpr int TM = 128;       // columns per tile (MMA M)
+constexpr int TC_NT = 256;    // threads: 8 warps; warp w reads TMEM lanes 32 (w % 4).. and column half w / 4
+constexpr int K1 = 72;        // NIN = 65 padded to a multiple of 8
+constexpr int N3 = 32;        // NOUT = 20 padded to a multiple of 16
+constexpr int TMEM_COLS = 256;
+constexpr int D1 = 0, D2 = 64, D3 = 128;  // TMEM column of each layer's accumulator
+constexpr unsigned MBAR_SPIN_LIMIT = 1u << 22;
 
-struct HaloSmem {
-  __align__(16) float wT1[MLP_NIN][MLP_NH];
-  __align__(16) float b1[MLP_NH];
-  __align__(16) float wT2[MLP_NH][MLP_NH];
-  __align__(16) float b2[MLP_NH];
-  __align__(16) float wT3[MLP_NH][NOUTP];
-  __align__(16) float b3[NOUTP];
-  __align__(16) float xT[MLP_NIN][SP];
-  __align__(16) float h1T[MLP_NH][SP];
-  __align__(16) float h2T[MLP_NH][SP];
-  __align__(16) float yT[NOUTP][SP];
-  double at3[SP][MLP_NOUT];
+struct TcSmem {
+  __align__(16) float w1h[MLP_NH * K1];
+  __align__(16) float w1l[MLP_NH * K1];
+  __align__(16) float w2h[MLP_NH * MLP_NH];
+  __align__(16) float w2l[MLP_NH * MLP_NH];
+  __align__(16) float w3h[N3 * MLP_NH];
+  __align__(16) float w3l[N3 * MLP_NH];
+  __align__(16) float x[TM * K1];
+  __align__(16) float hh[TM * MLP_NH];
+  __align__(16) float hl[TM * MLP_NH];
+  float b1[MLP_NH], b2[MLP_NH], b3[N3];
+  double at3[TM][MLP_NOUT];
+  unsigned long long mbar;
+  unsigned tmem_base;
+  int fail;
 };
 
-// out^T[o][s] = act(b[o] + sum_i W[o][i] in[s][i]) with transposed operands wT[i][o], inT[i][s].
-template <int NIN, int NOUT, bool ACT>
-__device__ __forceinline__ void layer_blocked(const float (*wT)[NOUT], const float* b, const float (*inT)[SP],
-                                              float (*outT)[SP]) {
-  constexpr int NOG = NOUT / 4, NSG = SP / 4;
-  for (int t = threadIdx.x; t < NOG * NSG; t += NT) {
-    const int og = t % NOG, sg = t / NOG;
-    float acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][c] = b[4 * og + c];
-#pragma unroll 5
-    for (int i = 0; i < NIN; ++i) {
-      const float4 xv = *reinterpret_cast<const float4*>(&inT[i][4 * sg]);
-      const float4 wv = *reinterpret_cast<const float4*>(&wT[i][4 * og]);
-      const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, wc[4] = {wv.x, wv.y, wv.z, wv.w};
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(wc[c], xa[a], acc[a][c]);
+// float index of element (r, k) of an R x K operand in the K-major no-swizzle core layout
+__device__ __forceinline__ int core_off(int r, int k, int K) { return ((r >> 3) * (K >> 2) + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3); }
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// TF32 pair: hi = x rounded to 10 mantissa bits, lo = x - hi (exact)
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+  hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
+  lo = x - hi;
+}
+
+// shared-memory matrix descriptor: start, leading (K-direction core) and stride (row-group)
+// byte offsets, tcgen05 version 1, no swizzle
+__device__ __forceinline__ unsigned long long sdesc(const void* p, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((smem_u32(p) >> 4) & 0x3fffu) | ((unsigned long long)((lbo >> 4) & 0x3fffu) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major, N x M = 128
+__host__ __device__ constexpr unsigned idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(TM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc, int acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the MMAs committed to the barrier (phase parity); bounded.  Returns false (and every
+// thread of the CTA sees the same) when the wait gave up.
+__device__ __forceinline__ bool mma_wait(TcSmem& sm, unsigned parity) {
+  unsigned it = 0;
+  bool ok = true;
+  while (!mbar_try(&sm.mbar, parity))
+    if (++it > MBAR_SPIN_LIMIT) {
+      ok = false;
+      break;
     }
+  if (!ok) sm.fail = 1;
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  return __syncthreads_and(ok) != 0;
+}
+
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float* r) {
+  unsigned u[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
+        "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]), "=r"(u[16]),
+        "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]),
+        "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int a = 0; a < 4; ++a) outT[4 * og + c][4 * sg + a] = ACT ? gelu(acc[a][c]) : acc[a][c];
+  for (int i = 0; i < 32; ++i) r[i] = __uint_as_float(u[i]);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// One layer's MMAs for the tile: K/8 steps of (A_hi B_hi, A_hi B_lo[, A_lo B_hi]).
+__device__ __forceinline__ void layer_mma(unsigned d, const float* ah, const float* al, const float* bh, const float* bl,
+                                          int K, int N) {
+  const unsigned sbo = (unsigned)(K / 4) * 128u, lbo = 128u, id = idesc_tf32(N);
+  for (int ks = 0; ks < K / 8; ++ks) {
+    const int off = ks * 64;  // 2 cores of 32 floats along K per step
+    const unsigned long long a_h = sdesc(ah + off, lbo, sbo), b_h = sdesc(bh + off, lbo, sbo), b_l = sdesc(bl + off, lbo, sbo);
+    mma_tf32(d, a_h, b_h, id, ks > 0);
+    mma_tf32(d, a_h, b_l, id, 1);
+    if (al) mma_tf32(d, sdesc(al + off, lbo, sbo), b_h, id, 1);
   }
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(NT, 2) k_mlp_halo(Geometry g, StepSched sc, const double* __restrict__ ring,
-                                                     const SubDev* __restrict__ subs, const int* __restrict__ cols,
-                                                     long long ncol, const float* __restrict__ params, MlpScales ms,
-                                                     At3Table t3, double* __restrict__ LH) {
+__global__ void __launch_bounds__(TC_NT, 1) k_mlp_halo(Geometry g, StepSched sc, const double* __restrict__ ring,
+                                                        const SubDev* __restrict__ subs, const int* __restrict__ cols,
+                                                        long long ncol, const float* __restrict__ params, MlpScales ms,
+                                                        At3Table t3, double* __restrict__ LH) {
   sc = resolve(sc);
   if (sc.mode != 1) return;  // the network replaces AT halos only
-  extern __shared__ __align__(16) unsigned char raw[];
-  HaloSmem& sm = *reinterpret_cast<HaloSmem*>(raw);
-  // reciprocal output scales (one division per thread instead of one per output)
-  double inv_out[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) inv_out[v] = 1.0 / ms.out[v];
-  // weights transposed once per CTA
-  for (int p = threadIdx.x; p < MLP_NH * MLP_NIN; p += NT) sm.wT1[p % MLP_NIN][p / MLP_NIN] = params[MLP_OFF_W1 + p];
-  for (int p = threadIdx.x; p < MLP_NH * MLP_NH; p += NT) sm.wT2[p % MLP_NH][p / MLP_NH] = params[MLP_OFF_W2 + p];
-  for (int p = threadIdx.x; p < MLP_NOUT * MLP_NH; p += NT) sm.wT3[p % MLP_NH][p / MLP_NH] = params[MLP_OFF_W3 + p];
-  for (int p = threadIdx.x; p < MLP_NH; p += NT) {
+  extern __shared__ __align__(16) unsigned char tc_raw[];
+  TcSmem& sm = *reinterpret_cast<TcSmem*>(tc_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // tensor memory (one warp allocates; the whole CTA frees it at the end) and the barrier
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&sm.tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sm.mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    sm.fail = 0;
+  }
+  // weights as TF32 pairs in the core layout (padding zero), biases
+  for (int p = tid; p < MLP_NH * K1; p += TC_NT) {
+    const int n = p / K1, k = p % K1;
+    float h = 0.f, l = 0.f;
+    if (k < MLP_NIN) tf32_split(params[MLP_OFF_W1 + n * MLP_NIN + k], h, l);
+    sm.w1h[core_off(n, k, K1)] = h;
+    sm.w1l[core_off(n, k, K1)] = l;
+  }
+  for (int p = tid; p < MLP_NH * MLP_NH; p += TC_NT) {
+    const int n = p / MLP_NH, k = p % MLP_NH;
+    float h, l;
+    tf32_split(params[MLP_OFF_W2 + p], h, l);
+    sm.w2h[core_off(n, k, MLP_NH)] = h;
+    sm.w2l[core_off(n, k, MLP_NH)] = l;
+  }
+  for (int p = tid; p < N3 * MLP_NH; p += TC_NT) {
+    const int n = p / MLP_NH, k = p % MLP_NH;
+    float h = 0.f, l = 0.f;
+    if (n < MLP_NOUT) tf32_split(params[MLP_OFF_W3 + p], h, l);
+    sm.w3h[core_off(n, k, MLP_NH)] = h;
+    sm.w3l[core_off(n, k, MLP_NH)] = l;
+  }
+  for (int p = tid; p < MLP_NH; p += TC_NT) {
     sm.b1[p] = params[MLP_OFF_B1 + p];
     sm.b2[p] = params[MLP_OFF_B2 + p];
   }
-  for (int p = threadIdx.x; p < NOUTP; p += NT) sm.b3[p] = params[MLP_OFF_B3 + p];
-  for (long long base = (long long)blockIdx.x * SP; base < ncol; base += (long long)gridDim.x * SP) {
-    const int ns = (int)min((long long)SP, ncol - base);
-    // gather: 4 threads per column, thread r handles depth r + 1 (features are per depth)
+  for (int p = tid; p < N3; p += TC_NT) sm.b3[p] = p < MLP_NOUT ? params[MLP_OFF_B3 + p] : 0.f;
+  double inv_out[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) inv_out[v] = 1.0 / ms.out[v];
+  tc_fence_before();
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const unsigned tmem = sm.tmem_base;
+  // this warp's TMEM lanes (rows 32 q..) and column half
+  const int q = warp & 3, half = warp >> 2, row = 32 * q + lane;
+  const unsigned lane_addr = tmem + ((unsigned)(32 * q) << 16);
+  unsigned parity = 0;
+  bool ok = true;
+
+  for (long long base = (long long)blockIdx.x * TM; ok && base < ncol; base += (long long)gridDim.x * TM) {
+    const int ns = (int)min((long long)TM, ncol - base);
+    // ---- gather: two (column, depth) pairs per thread; the features go to the core layout
     {
-      const int col = threadIdx.x / MLP_HDEPTH, r = threadIdx.x % MLP_HDEPTH;
-      if (col < ns) {
-        const int* cp = cols + 4 * (base + col);
-        const int sid = cp[0], f = cp[1], t1 = cp[2], t2 = cp[3];
-        const int k = face_delay(sc, sid, f);
-        column_depth(g, sc, ring, subs[sid], f, t1, t2, k, r + 1, ms, t3.w[k], &sm.xT[0][col], SP, sm.at3[col], nullptr);
-        if (r == 0)
-          for (int q = 0; q <= MLP_KMAX; ++q) sm.xT[3 * MLP_HDEPTH * 5 + q][col] = (q == k) ? 1.f : 0.f;
-      } else if (col < SP && r == 0) {
-        for (int i = 0; i < MLP_NIN; ++i) sm.xT[i][col] = 0.f;  // idle columns of a partial chunk
+      const int col = tid >> 1;
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const int r = (tid & 1) + 2 * rr;  // depth r + 1
+        if (col < ns) {
+          const int* cp = cols + 4 * (base + col);
+          const int sid = cp[0], f = cp[1], t1 = cp[2], t2 = cp[3];
+          const int k = face_delay(sc, sid, f);
+          auto put = [&](int e, float val) { sm.x[core_off(col, e, K1)] = val; };
+          column_depth(g, sc, ring, subs[sid], f, t1, t2, k, r + 1, ms, t3.w[k], put, sm.at3[col], nullptr);
+          if (r == 0)
+            for (int e = 3 * MLP_HDEPTH * 5; e < K1; ++e)
+              sm.x[core_off(col, e, K1)] = (e - 3 * MLP_HDEPTH * 5 == k) ? 1.f : 0.f;  // one-hot delay, padding
+        } else if (r == 0) {
+          for (int e = 0; e < K1; ++e) sm.x[core_off(col, e, K1)] = 0.f;  // idle rows of a partial tile
+        }
       }
     }
+    async_proxy_fence();
+    tc_fence_before();
     __syncthreads();
-    layer_blocked<MLP_NIN, MLP_NH, true>(sm.wT1, sm.b1, sm.xT, sm.h1T);
-    __syncthreads();
-    layer_blocked<MLP_NH, MLP_NH, true>(sm.wT2, sm.b2, sm.h1T, sm.h2T);
-    __syncthreads();
-    layer_blocked<MLP_NH, NOUTP, false>(sm.wT3, sm.b3, sm.h2T, sm.yT);
-    __syncthreads();
-    for (int e = threadIdx.x; e < ns * MLP_NOUT; e += NT) {
-      const int col = e / MLP_NOUT, o = e % MLP_NOUT, j = o / 5 + 1, v = o % 5;
-      const int* cp = cols + 4 * (base + col);
-      const SubDev d = subs[cp[0]];
-      int c[3];
-      column_point(d, cp[1], cp[2], cp[3], j, true, c);
-      const long long q = (long long)(c[0] + g.G) + (long long)d.ex * ((long long)(c[1] + g.G) + (long long)d.ey * (c[2] + g.Gz));
-      double iv = inv_out[0];
+    // ---- layer 1: z1 = x W1^T (+ b1 below)
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      layer_mma(tmem + D1, sm.x, nullptr, sm.w1h, sm.w1l, K1, MLP_NH);
+      mma_commit(&sm.mbar);
+    }
+    if (!(ok = mma_wait(sm, parity))) break;
+    parity ^= 1;
+    // ---- epilogue: h = GELU(z + b) as TF32 pairs; warp reads 32 of the 64 columns of its rows
+    auto hidden = [&](int dcol, const float* b) {
+      float z[32];
+      tmem_ld32(lane_addr + (unsigned)(dcol + 32 * half), z);
 #pragma unroll
-      for (int vv = 1; vv < 5; ++vv) iv = v == vv ? inv_out[vv] : iv;
-      LH[(long long)v * g.Ptot + d.pbase + q] = fma((double)sm.yT[o][col], iv, sm.at3[col][o]);
+      for (int i = 0; i < 32; ++i) {
+        const int n = 32 * half + i;
+        float h, l;
+        tf32_split(gelu(z[i] + b[n]), h, l);
+        sm.hh[core_off(row, n, MLP_NH)] = h;
+        sm.hl[core_off(row, n, MLP_NH)] = l;
+      }
+      async_proxy_fence();
+      tc_fence_before();
+      __syncthreads();
+    };
+    hidden(D1, sm.b1);
+    // ---- layer 2
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      layer_mma(tmem + D2, sm.hh, sm.hl, sm.w2h, sm.w2l, MLP_NH, MLP_NH);
+      mma_commit(&sm.mbar);
+    }
+    if (!(ok = mma_wait(sm, parity))) break;
+    parity ^= 1;
+    hidden(D2, sm.b2);
+    // ---- layer 3
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      layer_mma(tmem + D3, sm.hh, sm.hl, sm.w3h, sm.w3l, MLP_NH, N3);
+      mma_commit(&sm.mbar);
+    }
+    if (!(ok = mma_wait(sm, parity))) break;
+    parity ^= 1;
+    // ---- outputs: warp half 0 holds outputs 0..15 of its rows, half 1 outputs 16..19
+    {
+      float y[32];
+      unsigned u[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
+            "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+          : "r"(lane_addr + (unsigned)(D3 + 16 * half)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+      for (int i = 0; i < 16; ++i) y[i] = __uint_as_float(u[i]);
+      if (row < ns) {
+        const int* cp = cols + 4 * (base + row);
+        const SubDev d = subs[cp[0]];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int o = 16 * half + i;
+          if (o >= MLP_NOUT) continue;
+          const int j = o / 5 + 1, v = o % 5;
+          int c[3];
+          column_point(d, cp[1], cp[2], cp[3], j, true, c);
+          const long long qq =
+              (long long)(c[0] + g.G) + (long long)d.ex * ((long long)(c[1] + g.G) + (long long)d.ey * (c[2] + g.Gz));
+          double iv = inv_out[0];
+#pragma unroll
+          for (int vv = 1; vv < 5; ++vv) iv = v == vv ? inv_out[vv] : iv;
+          LH[(long long)v * g.Ptot + d.pbase + qq] = fma((double)(y[i] + sm.b3[o]), iv, sm.at3[row][o]);
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  // a wait that gave up: poison this CTA's columns so the run reports a non-finite state
+  if (!ok) {
+    for (long long base = (long long)blockIdx.x * TM; base < ncol; base += (long long)gridDim.x * TM)
+      for (int e = tid; e < TM * MLP_NOUT && base + e / MLP_NOUT < ncol; e += TC_NT) {
+        const int col = e / MLP_NOUT, o = e % MLP_NOUT, j = o / 5 + 1, v = o % 5;
+        const int* cp = cols + 4 * (base + col);
+        const SubDev d = subs[cp[0]];
+        int c[3];
+        column_point(d, cp[1], cp[2], cp[3], j, true, c);
+        const long long qq =
+            (long long)(c[0] + g.G) + (long long)d.ex * ((long long)(c[1] + g.G) + (long long)d.ey * (c[2] + g.Gz));
+        LH[(long long)v * g.Ptot + d.pbase + qq] = __longlong_as_double(0x7ff8000000000000LL);
+      }
+    // give MMAs still in flight a bounded chance to finish before the memory they use is freed
+    for (unsigned it = 0; it < MBAR_SPIN_LIMIT && !mbar_try(&sm.mbar, parity); ++it) {
     }
     __syncthreads();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
 }
 
@@ -460,17 +665,16 @@ int launch_halo_samples(const Geometry& g, const StepSched& sc, const double* ri
 int launch_mlp_halo(const Geometry& g, const StepSched& sc, const double* ring, const SubDev* subs, const int* cols,
                     long long ncol, const float* params, MlpScales ms, double* LH, void* stream, long long* launches,
                     const Timer* tm) {
-  if (int e = set_attr()) return e;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(HaloSmem));
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
     if (e != cudaSuccess) return (int)e;
     attr = true;
   }
-  const long long nchunk = (ncol + SP - 1) / SP;
-  const unsigned grid = (unsigned)std::min<long long>(nchunk, 152LL * 2);
+  const long long ntile = (ncol + TM - 1) / TM;
+  const unsigned grid = (unsigned)std::min<long long>(ntile, 152LL);
   if (tm) tm->rec(tm->self, 0, 1);
-  k_mlp_halo<<<grid, NT, sizeof(HaloSmem), (cudaStream_t)stream>>>(g, sc, ring, subs, cols, ncol, params, ms, at3_table(), LH);
+  k_mlp_halo<<<grid, TC_NT, sizeof(TcSmem), (cudaStream_t)stream>>>(g, sc, ring, subs, cols, ncol, params, ms, at3_table(), LH);
   if (tm) tm->rec(tm->self, 0, 0);
   if (launches) *launches += 1;
   return (int)cudaGetLastError();
