@@ -150,3 +150,32 @@ def halo_errors(params: np.ndarray, X, T) -> dict:
     base = float((T.double() ** 2).mean())
     net = float(((T - y).double() ** 2).mean())
     return {"extrapolation3_mse": base, "learned_mse": net, "ratio": net / base if base > 0 else float("nan")}
+
+
+def solver_run(n: int = 160, p: int = 5, steps: int = 12, seed: int = 1) -> dict:
+    """A Taylor-Green run (n^3, p^3 sub-domains, SAA delays 0..4, CFL 0.05) with a seeded untrained
+    network in the stage-0 face halos; returns the per-kernel-kind times (ms per launch) of the
+    last four steps.  Used to time and profile the network's solver kernel."""
+    import torch
+    from .inputs import cfl_dt, saa_delays, tgv_case, tgv_state
+    c = tgv_case(n, p, "SAA", kmax=4)
+    c = c.replace(dt=cfl_dt(c, tgv_state(c), 0.05))
+    s = cfs.Solver(c, max_delay=4)
+    try:
+        s.set_schedule(delays=saa_delays(c, steps))
+        scales = np.array([3e3, 2e3, 2e3, 2e3, 1e3, 4e2, 3e2, 3e2, 3e2, 2e2, 1e7, 1e6, 1e6, 1e6, 5e5])
+        cfs.cfs_set_halo_model(s.ctx, init_params(seed), scales)
+        s.set_state(tgv_state(c))
+        s.step(steps - 4)
+        torch.cuda.synchronize()
+        cfs.cfs_set_timing(s.ctx, True)
+        s.step(4)
+        torch.cuda.synchronize()
+        return {k: v[0] / max(v[1], 1) for k, v in cfs.cfs_get_timing(s.ctx).items() if v[1]}
+    finally:
+        s.close()
+
+
+if __name__ == "__main__":
+    import sys
+    print(solver_run(int(sys.argv[1]) if len(sys.argv) > 1 else 160, int(sys.argv[2]) if len(sys.argv) > 2 else 5))
