@@ -337,11 +337,13 @@ __global__ void k_halo_samples(Geometry g, StepSched sc, const double* __restric
 // accumulation), which keeps the network at FP32 accuracy (the dropped lo*lo and the truncation of
 // lo are below 2^-21 relative).  The features are BF16 values, exact in TF32, so the first layer
 // needs A_hi only.  One thread issues the MMAs and commits them to an mbarrier; all threads wait
-// (bounded), read D with tcgen05.ld, add the bias, apply GELU and write the next layer's operands.
+// (bounded), read D with tcgen05.ld (warp w: TMEM lanes 32 (w % 4).., a quarter of the columns),
+// add the bias, apply GELU and write the next layer's operands.  512 threads: one (column, depth)
+// pair of the gather each.
 namespace {
 
 constexpr int TM = 128;       // columns per tile (MMA M)
-constexpr int TC_NT = 256;    // threads: 8 warps; warp w reads TMEM lanes 32 (w % 4).. and column half w / 4
+constexpr int TC_NT = 512;    // threads: 16 warps; warp w reads TMEM lanes 32 (w % 4).. and column quarter w / 4
 constexpr int K1 = 72;        // NIN = 65 padded to a multiple of 8
 constexpr int N3 = 32;        // NOUT = 20 padded to a multiple of 16
 constexpr int TMEM_COLS = 256;
@@ -425,19 +427,16 @@ __device__ __forceinline__ bool mma_wait(TcSmem& sm, unsigned parity) {
   return __syncthreads_and(ok) != 0;
 }
 
-__device__ __forceinline__ void tmem_ld32(unsigned taddr, float* r) {
-  unsigned u[32];
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float* r) {
+  unsigned u[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
       : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
-        "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]), "=r"(u[16]),
-        "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]),
-        "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+        "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) r[i] = __uint_as_float(u[i]);
+  for (int i = 0; i < 16; ++i) r[i] = __uint_as_float(u[i]);
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
@@ -513,20 +512,19 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mlp_halo(Geometry g, StepSched sc,
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const unsigned tmem = sm.tmem_base;
-  // this warp's TMEM lanes (rows 32 q..) and column half
-  const int q = warp & 3, half = warp >> 2, row = 32 * q + lane;
+  // this warp's TMEM lanes (rows 32 q..) and column quarter
+  const int q = warp & 3, quarter = warp >> 2, row = 32 * q + lane;
   const unsigned lane_addr = tmem + ((unsigned)(32 * q) << 16);
   unsigned parity = 0;
   bool ok = true;
 
   for (long long base = (long long)blockIdx.x * TM; ok && base < ncol; base += (long long)gridDim.x * TM) {
     const int ns = (int)min((long long)TM, ncol - base);
-    // ---- gather: two (column, depth) pairs per thread; the features go to the core layout
+    // ---- gather: one (column, depth) pair per thread; the features go to the core layout
     {
-      const int col = tid >> 1;
-#pragma unroll
-      for (int rr = 0; rr < 2; ++rr) {
-        const int r = (tid & 1) + 2 * rr;  // depth r + 1
+      const int col = tid >> 2;
+      {
+        const int r = tid & 3;  // depth r + 1
         if (col < ns) {
           const int* cp = cols + 4 * (base + col);
           const int sid = cp[0], f = cp[1], t1 = cp[2], t2 = cp[3];
@@ -552,13 +550,13 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mlp_halo(Geometry g, StepSched sc,
     }
     if (!(ok = mma_wait(sm, parity))) break;
     parity ^= 1;
-    // ---- epilogue: h = GELU(z + b) as TF32 pairs; warp reads 32 of the 64 columns of its rows
+    // ---- epilogue: h = GELU(z + b) as TF32 pairs; warp reads 16 of the 64 columns of its rows
     auto hidden = [&](int dcol, const float* b) {
-      float z[32];
-      tmem_ld32(lane_addr + (unsigned)(dcol + 32 * half), z);
+      float z[16];
+      tmem_ld16(lane_addr + (unsigned)(dcol + 16 * quarter), z);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int n = 32 * half + i;
+      for (int i = 0; i < 16; ++i) {
+        const int n = 16 * quarter + i;
         float h, l;
         tf32_split(gelu(z[i] + b[n]), h, l);
         sm.hh[core_off(row, n, MLP_NH)] = h;
@@ -586,24 +584,22 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mlp_halo(Geometry g, StepSched sc,
     }
     if (!(ok = mma_wait(sm, parity))) break;
     parity ^= 1;
-    // ---- outputs: warp half 0 holds outputs 0..15 of its rows, half 1 outputs 16..19
+    // ---- outputs: warp quarter c holds outputs 8c..8c+7 of its rows (20 of the 32 used)
     {
-      float y[32];
-      unsigned u[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-          : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
-            "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
-          : "r"(lane_addr + (unsigned)(D3 + 16 * half)));
+      float y[8];
+      unsigned u[8];
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                   : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7])
+                   : "r"(lane_addr + (unsigned)(D3 + 8 * quarter)));
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-      for (int i = 0; i < 16; ++i) y[i] = __uint_as_float(u[i]);
-      if (row < ns) {
+      for (int i = 0; i < 8; ++i) y[i] = __uint_as_float(u[i]);
+      if (row < ns && 8 * quarter < MLP_NOUT) {
         const int* cp = cols + 4 * (base + row);
         const SubDev d = subs[cp[0]];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int o = 16 * half + i;
+        for (int i = 0; i < 8; ++i) {
+          const int o = 8 * quarter + i;
           if (o >= MLP_NOUT) continue;
           const int j = o / 5 + 1, v = o % 5;
           int c[3];
