@@ -331,6 +331,8 @@ def run_ours(args, rank, world, local_rank):
         forms = forms or {}
         forms["batched_blocks"] = batched_form(args, 0)
         forms["batched_blocks_fp32_intermediates"] = batched_form(args, 1)
+        forms["batched_blocks_curvilinear"] = batched_form(args, 0, curvilinear=True)
+        forms["batched_blocks_curvilinear_fp32_intermediates"] = batched_form(args, 1, curvilinear=True)
 
     # ---------------- learned halo predictor (trained here on synchronous-run halos)
     if args.precision == 0 and not args.no_forms and not args.no_learned and world == 1:
@@ -409,16 +411,19 @@ def batched_blocks():
     return [b.replace(dt=dt) for b in blocks]
 
 
-def batched_form(args, precision=0):
+def batched_form(args, precision=0, curvilinear=False):
     """All 12 blocks advance together: every kernel launch covers the sub-domains of all blocks
     (work lists over (block, sub-domain, tile)); the FP32-intermediate form runs one persistent
-    fused launch per RK stage.  The step is captured once in a CUDA graph and replayed; launch
-    shapes come from the autotuner."""
+    fused launch per RK stage (Cartesian blocks).  The step is captured once in a CUDA graph and
+    replayed; launch shapes come from the autotuner.  curvilinear: every block on a smoothly
+    deformed periodic grid (metric terms of App. A; amplitude 4% of the block's smaller side)."""
     import torch
     from paper_2506_03027_gb300 import autotune
     from paper_2506_03027_gb300 import cfs
     from paper_2506_03027_gb300 import inputs as I
     blocks = batched_blocks()
+    if curvilinear:
+        blocks = [b.replace(curv=0.04 * min(b.lx, b.ly)) for b in blocks]
     tiles = autotune.tune(blocks[0], precision=precision, blocks=blocks, use_cache=False)
     npts = sum(b.npts for b in blocks)
     nsub = sum(b.nsub for b in blocks)
@@ -445,7 +450,10 @@ def batched_form(args, precision=0):
             "blocks": len(blocks), "subdomains": nsub, "cuda_graph": True, "launches_per_step": launches / K,
             "tiles_autotuned": list(tiles),
             "workload": "12 independent periodic NS blocks with the 12-block airfoil C-grid sizes, SAA 0..2, "
-                        + ("FP64" if precision == 0 else "FP32 intermediates (one fused launch per RK stage)")}
+                        + ("curvilinear (deformed periodic grids), " if curvilinear else "")
+                        + ("FP64" if precision == 0 else
+                           "FP32 intermediates (" + ("multi-kernel stage" if curvilinear else
+                                                     "one fused launch per RK stage") + ")")}
 
 
 def precision_form_256(args):

@@ -23,7 +23,7 @@ def key(case, precision: int, nblocks: int = 1) -> str:
     import torch
     name = torch.cuda.get_device_name()
     return (f"{name}|p{precision}|o{case.order}|v{int(case.viscous)}|f{int(case.filter)}|"
-            f"{case.nx}x{case.ny}x{case.nz}/{case.px}x{case.py}x{case.pz}|b{nblocks}")
+            f"{case.nx}x{case.ny}x{case.nz}/{case.px}x{case.py}x{case.pz}|b{nblocks}|c{int(bool(case.curv))}")
 
 
 def load_cache() -> dict:
@@ -75,7 +75,8 @@ def tune(case, precision: int = 0, blocks=None, use_cache: bool = True):
         hit = load_cache().get(k)
         if hit:
             return tuple(hit["tiles"])
-    fused = precision == 1 and case.nz > 1 and case.viscous and case.order == 4
+    fused = (precision == 1 and case.nz > 1 and case.viscous and case.order == 4
+             and not any(b.curv for b in (blocks or [case])))
     cands = FUSED if fused else PLAIN
     ms = {}
     for t in cands:
