@@ -34,7 +34,18 @@
  *   - Delays: k clamped to n - C + 1 so every referenced level exists; steps n < C are SA.
  *   - CAA delay k(n) = (n - C) mod L for n >= C.
  *
- * Layout: global state U[5][nz][ny][nx] (structure of arrays, FP64), periodic in all directions.
+ *   - Multi-block grids: blocks joined at node-disjoint interfaces (tangential index aligned or
+ *     reversed, spanwise counts equal or different: four-point Lagrange interpolation in z),
+ *     ending at no-slip adiabatic walls (mirrored state, momentum negated; wall points keep zero
+ *     momentum through the stages and the filter), far fields (a given state) or outflows (the
+ *     face values repeated).  Halo values beyond a block face resolve axis by axis, x then y then
+ *     z; metric terms beyond a non-periodic face come from the grid continued across it
+ *     (interfaces) or reflected through the boundary point (physical faces).  A halo source is
+ *     the PE's own value (current) when reached by a wall mirror or an outflow copy within the
+ *     sub-domain; otherwise it is a neighbour's, seen with the face's delay.
+ *
+ * Layout: a state array holds every block's U[5][nz][ny][nx] (structure of arrays, FP64) one
+ * after the other; a single-grid run is one block, periodic in all directions.
  */
 #include <math.h>
 #include <stdint.h>
@@ -45,6 +56,31 @@
 #endif
 
 #define NV 5
+
+/* Face of a block (faces 0..5 = -x, +x, -y, +y, -z, +z).  Types: periodic (the block wraps onto
+ * itself), interface (to face nf of block nb; node-disjoint: the first point beyond the face is
+ * the neighbour's first point inside its face; rev = 1 when the tangential in-plane index runs
+ * the other way on the neighbour; the neighbour's coordinates continue the block's grid after
+ * adding shift, nonzero where the interface closes a periodic direction), no-slip adiabatic wall (the points on the face are wall
+ * points; beyond it the state is mirrored about the face with the momentum negated), far field
+ * (the given conserved state beyond the face) and outflow (the face values repeated beyond it). */
+enum { OR_PERIODIC = 0, OR_INTERFACE = 1, OR_WALL = 2, OR_FARFIELD = 3, OR_OUTFLOW = 4 };
+typedef struct {
+  int type;
+  int nb, nf, rev;
+  double state[5];
+  double shift[2]; /* interface: coordinate jump (x, y) added to the neighbour's points */
+} or_face;
+
+/* One block of a multi-block run: its grid, its split into sub-domains and its six faces
+ * (z faces periodic: blocks are extruded along z). */
+typedef struct {
+  int nx, ny, nz, px, py, pz;
+  double dx, dy, dz;
+  const double* grid_xy;  /* [2][ny][nx] point coordinates, or NULL (uniform Cartesian) */
+  double grid_shift[4];   /* coordinate jumps across periodic wraps in xi (x, y) and eta (x, y) */
+  or_face face[6];
+} or_block;
 
 typedef struct {
   int nx, ny, nz;        /* global grid; nz == 1 means two-dimensional */
@@ -69,6 +105,10 @@ typedef struct {
    * periodic wrap in xi, shift[2..3] = the jump across the wrap in eta */
   const double* grid_xy;
   double grid_shift[4];
+  /* multi-block run: nblocks > 0 blocks replace the single periodic grid above (whose grid,
+   * split and spacing fields are then ignored); states are stored block after block */
+  int nblocks;
+  const or_block* blocks;
 } or_params;
 
 /* ---------------------------------------------------------------- coefficient tables */
@@ -206,6 +246,8 @@ typedef struct {
   int ox, oy, oz, sx, sy, sz;  /* owned box */
   int g, gz;                   /* ghost depth in x/y and in z (0 in 2-D) */
   int ex, ey, ez;              /* extended dims */
+  int b;                       /* block of the sub-domain */
+  int phys[6];                 /* 1: the face lies on a physical boundary of the block */
 } subdom;
 
 static void make_subdom(const or_params* p, int s, int g, subdom* d) {
@@ -219,6 +261,8 @@ static void make_subdom(const or_params* p, int s, int g, subdom* d) {
   d->ex = d->sx + 2 * g;
   d->ey = d->sy + 2 * g;
   d->ez = d->sz + 2 * d->gz;
+  d->b = 0;
+  for (int f = 0; f < 6; ++f) d->phys[f] = 0;
 }
 
 /* Classify extended point (i,j,k): returns number of coordinates outside the owned box and fills
@@ -246,38 +290,355 @@ static int classify(const subdom* d, int i, int j, int k, int dep[3], int face[3
  * space (spacing 1), periodic with the coordinate jump added across the wrap.  With periodic CD
  * operators D_xi D_eta = D_eta D_xi, so sum_a D_a (metric column) = 0 holds discretely and a
  * uniform flow stays uniform (freestream preservation). */
+/* ---------------------------------------------------------------- blocks, faces, halo sources
+ * The run's blocks (a single-grid run is one block with six periodic faces), each block's state
+ * stored after the previous one's ([5][nz][ny][nx] per block), sub-domains numbered block after
+ * block.  Values beyond a block face follow the face's type (see or_face); an interface that
+ * joins blocks of different spanwise counts gives the receiving point the neighbour's values at
+ * the same spanwise position, by four-point Lagrange interpolation between the neighbour's
+ * points (a point that falls on a neighbour point takes it alone). */
+typedef struct {
+  int nb, nsub;
+  or_block* b;    /* the blocks */
+  or_params* pb;  /* per block: a copy of the run's parameters with the block's grid and split */
+  size_t* base;   /* offset of each block's state in a state array (doubles) */
+  size_t* np;     /* points of each block */
+  int* sid0;      /* first sub-domain of each block (nb + 1 entries) */
+  size_t Ntot;    /* points of all blocks */
+  int g;          /* halo depth of the stage (2r viscous, r Euler) */
+  double** M;     /* per block: metric terms on the plane extended by g, or NULL (Cartesian) */
+} topo_t;
+
+static inline size_t at_pt(const topo_t* T, int b, int v, int i, int j, int k) {
+  const or_block* B = &T->b[b];
+  return T->base[b] + (size_t)v * T->np[b] + (size_t)i + (size_t)B->nx * ((size_t)j + (size_t)B->ny * (size_t)k);
+}
+
+static int block_of(const topo_t* T, int s, int* local) {
+  int b = 0;
+  while (b + 1 < T->nb && s >= T->sid0[b + 1]) ++b;
+  *local = s - T->sid0[b];
+  return b;
+}
+
+/* Sub-domain s with its block and the physical boundaries among its faces. */
+static void make_sub(const topo_t* T, int s, int g, subdom* d) {
+  int local;
+  const int b = block_of(T, s, &local);
+  make_subdom(&T->pb[b], local, g, d);
+  d->b = b;
+  const or_block* B = &T->b[b];
+  const int lo[3] = {d->ox, d->oy, d->oz}, hi[3] = {d->ox + d->sx, d->oy + d->sy, d->oz + d->sz};
+  const int n[3] = {B->nx, B->ny, B->nz};
+  for (int a = 0; a < 3; ++a) {
+    d->phys[2 * a] = lo[a] == 0 && B->face[2 * a].type >= OR_WALL;
+    d->phys[2 * a + 1] = hi[a] == n[a] && B->face[2 * a + 1].type >= OR_WALL;
+  }
+}
+
+/* sign of conserved variable v after a wall reflection */
+static inline double refl_sign(int v, int flip) { return (flip && v >= 1 && v <= 3) ? -1.0 : 1.0; }
+
+#define OR_MAXT 4
+typedef struct {
+  int b, i, j, k;
+  int flip;     /* momentum negated (odd number of wall reflections) */
+  int crossed;  /* the path crossed a periodic wrap or a block interface */
+  double w;
+} or_term;
+
+/* Four-point Lagrange weights at fraction th of the way from node 0 to node 1 (nodes -1..2). */
+static void lagrange4(double th, double* l) {
+  l[0] = -th * (th - 1.0) * (th - 2.0) / 6.0;
+  l[1] = (th + 1.0) * (th - 1.0) * (th - 2.0) / 2.0;
+  l[2] = -(th + 1.0) * th * (th - 2.0) / 2.0;
+  l[3] = (th + 1.0) * th * (th - 1.0) / 6.0;
+}
+
+/* Sources of the state at point (i, j, k) of block b's index space (any point within a halo
+ * depth of the block): U_v = sum_t w_t s_v(flip_t) U_v(term t) + cst_v.  The axes are resolved
+ * in the order x, y, z, each in the frame of the block reached so far.  Returns the number of
+ * terms, or -1 when more than OR_MAXT would be needed or the point does not resolve. */
+static int resolve_state(const topo_t* T, int b, int i, int j, int k, or_term* t, double* cst) {
+  int n = 1;
+  t[0].b = b; t[0].i = i; t[0].j = j; t[0].k = k; t[0].flip = 0; t[0].crossed = 0; t[0].w = 1.0;
+  for (int v = 0; v < NV; ++v) cst[v] = 0.0;
+  for (int q = 0; q < n; ++q) {
+    int hop;
+    for (hop = 0; hop < 16; ++hop) {
+      or_term* x = &t[q];
+      const or_block* B = &T->b[x->b];
+      int c[3] = {x->i, x->j, x->k};
+      const int nn[3] = {B->nx, B->ny, B->nz};
+      int a = -1;
+      for (int e = 0; e < 3; ++e)
+        if (c[e] < 0 || c[e] >= nn[e]) { a = e; break; }
+      if (a < 0) break;
+      const int side = c[a] < 0 ? 0 : 1;
+      const or_face* F = &B->face[2 * a + side];
+      if (F->type == OR_PERIODIC) {
+        c[a] = wrapi(c[a], nn[a]);
+        x->crossed = 1;
+      } else if (F->type == OR_WALL) {
+        c[a] = side == 0 ? -c[a] : 2 * (nn[a] - 1) - c[a];
+        x->flip ^= 1;
+      } else if (F->type == OR_OUTFLOW) {
+        c[a] = side == 0 ? 0 : nn[a] - 1;
+      } else if (F->type == OR_FARFIELD) {
+        for (int v = 0; v < NV; ++v) cst[v] += x->w * refl_sign(v, x->flip) * F->state[v];
+        t[q] = t[n - 1];
+        --n;
+        --q;
+        break;
+      } else if (F->type == OR_INTERFACE && a < 2) {
+        const or_block* B2 = &T->b[F->nb];
+        const int m = side == 0 ? -c[a] : c[a] - (nn[a] - 1);  /* depth beyond the face */
+        const int a2 = F->nf / 2, s2 = F->nf % 2, ta = 1 - a, ta2 = 1 - a2;
+        const int n2[3] = {B2->nx, B2->ny, B2->nz};
+        int c2[3];
+        c2[a2] = s2 == 0 ? m - 1 : n2[a2] - m;
+        c2[ta2] = F->rev ? nn[ta] - 1 - c[ta] : c[ta];
+        c2[2] = c[2];
+        x->b = F->nb;
+        x->crossed = 1;
+        if (n2[2] != nn[2]) {
+          /* spanwise position c[2] nz2 / nz on the neighbour */
+          const long num = (long)c[2] * n2[2];
+          long z0 = num / nn[2];
+          if (z0 * nn[2] > num) --z0;
+          const long rem = num - z0 * nn[2];
+          c2[2] = (int)z0;
+          if (rem != 0) {
+            if (n + 3 > OR_MAXT) return -1;
+            double l[4];
+            lagrange4((double)rem / (double)nn[2], l);
+            const or_term base = *x;
+            for (int o = 0; o < 4; ++o) {
+              or_term* y = (o == 0) ? x : &t[n + o - 1];
+              *y = base;
+              y->i = c2[0]; y->j = c2[1]; y->k = (int)z0 + o - 1;
+              y->w = base.w * l[o];
+            }
+            n += 3;
+            continue;
+          }
+        }
+        c[0] = c2[0]; c[1] = c2[1]; c[2] = c2[2];
+      } else {
+        return -1;
+      }
+      x->i = c[0]; x->j = c[1]; x->k = c[2];
+    }
+    if (hop == 16) return -1;
+  }
+  return n;
+}
+
+/* Point coordinates (x, y) at (i, j) of curvilinear block b's plane, for points up to a few halo
+ * depths outside it: a periodic face wraps the index and adds the coordinate jump, an interface
+ * continues into the neighbour (which must be curvilinear too), a physical face reflects the grid
+ * through the boundary point, x(-m) = 2 x(0) - x(m).  Returns nonzero if it does not resolve. */
+static int coord_ext(const topo_t* T, int b, int i, int j, int depth, double* xy) {
+  if (depth > 8) return 1;
+  const or_block* B = &T->b[b];
+  const int nn[2] = {B->nx, B->ny};
+  int wi = 0, wj = 0;
+  for (int hop = 0; hop < 4; ++hop) {
+    int c[2] = {i, j};
+    int a = -1;
+    for (int e = 0; e < 2; ++e)
+      if (c[e] < 0 || c[e] >= nn[e]) { a = e; break; }
+    if (a < 0) break;
+    const int side = c[a] < 0 ? 0 : 1;
+    const or_face* F = &B->face[2 * a + side];
+    double r0[2], r1[2];
+    if (F->type == OR_PERIODIC) {
+      const int w = wrapi(c[a], nn[a]);
+      if (a == 0) wi += (c[a] - w) / nn[a];
+      else wj += (c[a] - w) / nn[a];
+      c[a] = w;
+      i = c[0]; j = c[1];
+      continue;
+    }
+    if (F->type == OR_INTERFACE) {
+      const or_block* B2 = &T->b[F->nb];
+      const int m = side == 0 ? -c[a] : c[a] - (nn[a] - 1);
+      const int a2 = F->nf / 2, s2 = F->nf % 2, ta = 1 - a, ta2 = 1 - a2;
+      const int n2[2] = {B2->nx, B2->ny};
+      int c2[2];
+      c2[a2] = s2 == 0 ? m - 1 : n2[a2] - m;
+      c2[ta2] = F->rev ? nn[ta] - 1 - c[ta] : c[ta];
+      if (coord_ext(T, F->nb, c2[0], c2[1], depth + 1, r0)) return 1;
+      for (int q = 0; q < 2; ++q) xy[q] = r0[q] + F->shift[q] + wi * B->grid_shift[q] + wj * B->grid_shift[2 + q];
+      return 0;
+    }
+    /* physical boundary: reflection through the boundary point */
+    int cb[2] = {c[0], c[1]}, cm[2] = {c[0], c[1]};
+    cb[a] = side == 0 ? 0 : nn[a] - 1;
+    cm[a] = side == 0 ? -c[a] : 2 * (nn[a] - 1) - c[a];
+    if (coord_ext(T, b, cb[0], cb[1], depth + 1, r0) || coord_ext(T, b, cm[0], cm[1], depth + 1, r1)) return 1;
+    for (int q = 0; q < 2; ++q) xy[q] = 2.0 * r0[q] - r1[q] + wi * B->grid_shift[q] + wj * B->grid_shift[2 + q];
+    return 0;
+  }
+  if (i < 0 || i >= nn[0] || j < 0 || j >= nn[1]) return 1;
+  for (int q = 0; q < 2; ++q)
+    xy[q] = B->grid_xy[(size_t)q * nn[0] * nn[1] + (size_t)i + (size_t)nn[0] * j] + wi * B->grid_shift[q] +
+            wj * B->grid_shift[2 + q];
+  return 0;
+}
+
 #define NM 6 /* xi^_x, xi^_y, eta^_x, eta^_y, zeta^_z, J^-1 */
 
-static double coord_at(const or_params* p, int c, int i, int j) {
-  int ii = wrapi(i, p->nx), jj = wrapi(j, p->ny);
-  int wi = (i - ii) / p->nx, wj = (j - jj) / p->ny; /* number of wraps (exact multiples) */
-  return p->grid_xy[(size_t)c * p->nx * p->ny + (size_t)ii + (size_t)p->nx * jj] + wi * p->grid_shift[c] +
-         wj * p->grid_shift[2 + c];
-}
-
-static double cd_coord(const or_params* p, int c, int i, int j, int axis) {
-  double f[5];
-  for (int o = -2; o <= 2; ++o) f[o + 2] = axis == 0 ? coord_at(p, c, i + o, j) : coord_at(p, c, i, j + o);
-  if (p->order == 4) return (-1.0 / 3.0) * (f[4] - f[0]) / 4.0 + (4.0 / 3.0) * (f[3] - f[1]) / 2.0;
-  return (f[3] - f[1]) / 2.0;
-}
-
-/* Metric field [NM][N] of the whole grid (NULL for a Cartesian grid). */
-static double* metric_field(const or_params* p) {
-  if (!p->grid_xy) return NULL;
-  const size_t N = (size_t)p->nx * p->ny * p->nz, n2 = (size_t)p->nx * p->ny;
-  double* M = (double*)malloc(sizeof(double) * NM * N);
+/* Metric terms at point (i, j) of block b's plane (in the block's own index frame); the
+ * coordinate derivatives by the scheme of Eq. 2 in index space.  Nonzero if a coordinate does
+ * not resolve. */
+static int metric_point(const topo_t* T, int b, int i, int j, double* m) {
+  const or_params* p = &T->pb[b];
+  double d[2][2]; /* d[c][axis] = d (x, y)_c / d xi_axis */
+  for (int axis = 0; axis < 2; ++axis) {
+    double f[5][2];
+    for (int o = -2; o <= 2; ++o) {
+      if (p->order != 4 && (o == -2 || o == 2)) { f[o + 2][0] = f[o + 2][1] = 0.0; continue; }
+      if (coord_ext(T, b, axis == 0 ? i + o : i, axis == 0 ? j : j + o, 0, f[o + 2])) return 1;
+    }
+    for (int c = 0; c < 2; ++c) {
+      if (p->order == 4)
+        d[c][axis] = (-1.0 / 3.0) * (f[4][c] - f[0][c]) / 4.0 + (4.0 / 3.0) * (f[3][c] - f[1][c]) / 2.0;
+      else
+        d[c][axis] = (f[3][c] - f[1][c]) / 2.0;
+    }
+  }
+  const double x_xi = d[0][0], x_eta = d[0][1], y_xi = d[1][0], y_eta = d[1][1];
   const double zz = p->nz > 1 ? p->dz : 1.0;
-  for (int j = 0; j < p->ny; ++j)
-    for (int i = 0; i < p->nx; ++i) {
-      double x_xi = cd_coord(p, 0, i, j, 0), x_eta = cd_coord(p, 0, i, j, 1);
-      double y_xi = cd_coord(p, 1, i, j, 0), y_eta = cd_coord(p, 1, i, j, 1);
-      double det = x_xi * y_eta - x_eta * y_xi;
-      double m[NM] = {y_eta * zz, -x_eta * zz, -y_xi * zz, x_xi * zz, det, zz * det};
-      for (int k = 0; k < p->nz; ++k)
-        for (int c = 0; c < NM; ++c) M[(size_t)c * N + (size_t)i + (size_t)p->nx * j + n2 * k] = m[c];
+  const double det = x_xi * y_eta - x_eta * y_xi;
+  m[0] = y_eta * zz; m[1] = -x_eta * zz; m[2] = -y_xi * zz; m[3] = x_xi * zz; m[4] = det; m[5] = zz * det;
+  return 0;
+}
+
+/* Metric terms of curvilinear block b on its plane extended by g points on every side,
+ * [NM][(nx + 2g)(ny + 2g)]: a point beyond a periodic face takes the wrapped point's values;
+ * beyond another face, the values of the grid continued as coord_ext continues it, to the
+ * stencil radius (deeper points, which no flux reads, are NaN). */
+static double* metric_plane(const topo_t* T, int b) {
+  const or_block* B = &T->b[b];
+  if (!B->grid_xy) return NULL;
+  const int g = T->g, r = T->pb[b].order == 4 ? 2 : 1;
+  const int ex = B->nx + 2 * g, ey = B->ny + 2 * g;
+  const size_t pl = (size_t)ex * ey;
+  double* M = (double*)malloc(sizeof(double) * NM * pl);
+  for (int jj = -g; jj < B->ny + g; ++jj)
+    for (int ii = -g; ii < B->nx + g; ++ii) {
+      int i = ii, j = jj;
+      if ((i < 0 && B->face[0].type == OR_PERIODIC) || (i >= B->nx && B->face[1].type == OR_PERIODIC)) i = wrapi(i, B->nx);
+      if ((j < 0 && B->face[2].type == OR_PERIODIC) || (j >= B->ny && B->face[3].type == OR_PERIODIC)) j = wrapi(j, B->ny);
+      const int di = i < 0 ? -i : (i >= B->nx ? i - B->nx + 1 : 0);
+      const int dj = j < 0 ? -j : (j >= B->ny ? j - B->ny + 1 : 0);
+      double m[NM];
+      if (di > r || dj > r || metric_point(T, b, i, j, m))
+        for (int c = 0; c < NM; ++c) m[c] = NAN;
+      const size_t q = (size_t)(ii + g) + (size_t)ex * (jj + g);
+      for (int c = 0; c < NM; ++c) M[c * pl + q] = m[c];
     }
   return M;
+}
+
+static inline double metric_at(const topo_t* T, int b, int c, int i, int j) {
+  const or_block* B = &T->b[b];
+  const int g = T->g, ex = B->nx + 2 * g;
+  const size_t pl = (size_t)ex * (B->ny + 2 * g);
+  return T->M[b][(size_t)c * pl + (size_t)(i + g) + (size_t)ex * (j + g)];
+}
+
+static void topo_free(topo_t* T) {
+  if (T->M)
+    for (int b = 0; b < T->nb; ++b) free(T->M[b]);
+  free(T->M); free(T->b); free(T->pb); free(T->base); free(T->np); free(T->sid0);
+  memset(T, 0, sizeof(*T));
+}
+
+/* The run's blocks: validated faces (z periodic; interfaces paired both ways, in-plane, with
+ * equal tangential counts; curvilinear only to curvilinear; between Cartesian blocks only
+ * opposite faces of one axis with the tangential index unreversed), metric planes, and every
+ * halo point within depth gmax of a block resolvable.  Nonzero on an invalid description. */
+static int topo_build(const or_params* p, int g, int gmax, topo_t* T) {
+  memset(T, 0, sizeof(*T));
+  const int nb = p->nblocks > 0 ? p->nblocks : 1;
+  T->nb = nb;
+  T->g = g;
+  T->b = (or_block*)calloc(nb, sizeof(or_block));
+  T->pb = (or_params*)calloc(nb, sizeof(or_params));
+  T->base = (size_t*)calloc(nb, sizeof(size_t));
+  T->np = (size_t*)calloc(nb, sizeof(size_t));
+  T->sid0 = (int*)calloc(nb + 1, sizeof(int));
+  T->M = (double**)calloc(nb, sizeof(double*));
+  if (p->nblocks > 0) {
+    memcpy(T->b, p->blocks, sizeof(or_block) * nb);
+  } else {
+    or_block* B = &T->b[0];
+    B->nx = p->nx; B->ny = p->ny; B->nz = p->nz; B->px = p->px; B->py = p->py; B->pz = p->pz;
+    B->dx = p->dx; B->dy = p->dy; B->dz = p->dz;
+    B->grid_xy = p->grid_xy;
+    for (int q = 0; q < 4; ++q) B->grid_shift[q] = p->grid_shift[q];
+    for (int f = 0; f < 6; ++f) B->face[f].type = OR_PERIODIC;
+  }
+  size_t off = 0;
+  int s0 = 0;
+  for (int b = 0; b < nb; ++b) {
+    const or_block* B = &T->b[b];
+    if (B->nx < 1 || B->ny < 1 || B->nz < 1 || B->px < 1 || B->py < 1 || B->pz < 1) return 10;
+    or_params* q = &T->pb[b];
+    *q = *p;
+    q->nx = B->nx; q->ny = B->ny; q->nz = B->nz; q->px = B->px; q->py = B->py; q->pz = B->pz;
+    q->dx = B->dx; q->dy = B->dy; q->dz = B->dz;
+    q->grid_xy = B->grid_xy;
+    for (int k = 0; k < 4; ++k) q->grid_shift[k] = B->grid_shift[k];
+    q->nblocks = 0;
+    q->blocks = NULL;
+    T->base[b] = off;
+    T->np[b] = (size_t)B->nx * B->ny * B->nz;
+    off += NV * T->np[b];
+    T->Ntot += T->np[b];
+    T->sid0[b] = s0;
+    s0 += B->px * B->py * B->pz;
+  }
+  T->sid0[nb] = s0;
+  T->nsub = s0;
+  for (int b = 0; b < nb; ++b) {
+    const or_block* B = &T->b[b];
+    const int nn[3] = {B->nx, B->ny, B->nz};
+    for (int f = 0; f < 6; ++f) {
+      const or_face* F = &B->face[f];
+      if (F->type < OR_PERIODIC || F->type > OR_OUTFLOW) return 11;
+      if (f >= 4 && F->type != OR_PERIODIC) return 12;
+      if (F->type != OR_INTERFACE) continue;
+      if (F->nb < 0 || F->nb >= nb || F->nf < 0 || F->nf > 3) return 13;
+      const or_block* B2 = &T->b[F->nb];
+      const or_face* F2 = &B2->face[F->nf];
+      if (F2->type != OR_INTERFACE || F2->nb != b || F2->nf != f || F2->rev != F->rev) return 14;
+      const int n2[3] = {B2->nx, B2->ny, B2->nz};
+      if (nn[1 - f / 2] != n2[1 - F->nf / 2]) return 15;
+      if ((B->grid_xy == NULL) != (B2->grid_xy == NULL)) return 16;
+      if (!B->grid_xy && (F->nf != (f ^ 1) || F->rev)) return 17;
+      if ((nn[2] == 1) != (n2[2] == 1)) return 18;
+    }
+  }
+  const int rr = p->order == 4 ? 2 : 1;
+  for (int b = 0; b < nb; ++b) {
+    const or_block* B = &T->b[b];
+    or_term t[OR_MAXT];
+    double cst[NV];
+    for (int k = 0; k < B->nz; ++k)
+      for (int j = -gmax; j < B->ny + gmax; ++j)
+        for (int i = -gmax; i < B->nx + gmax; ++i) {
+          const int di = i < 0 ? -i : (i >= B->nx ? i - B->nx + 1 : 0);
+          const int dj = j < 0 ? -j : (j >= B->ny ? j - B->ny + 1 : 0);
+          if (!di && !dj) continue;
+          if (di && dj && (di > rr || dj > rr)) continue;  /* corners: viscous edges r x r only */
+          if (resolve_state(T, b, i, j, k, t, cst) < 0) return 19;
+        }
+    T->M[b] = metric_plane(T, b);
+  }
+  return 0;
 }
 
 /* ---------------------------------------------------------------- RHS on an extended array */
@@ -422,10 +783,9 @@ static void rhs_ext(const or_params* p, const subdom* d, work_t* w, double* R) {
  * contravariant velocity U^_a = (metric row a) . u, F^v_a of Eq. A3 = (metric row a) . (Fv_x, Fv_y,
  * Fv_z), and the stresses / heat flux of Eq. A4 from physical gradients
  * d phi / d x_j = J sum_k (metric row k)_j d phi / d xi_k.  Mg: global metric field [NM][N]. */
-static void rhs_ext_curv(const or_params* p, const subdom* d, const double* Mg, work_t* w, double* R) {
+static void rhs_ext_curv(const or_params* p, const topo_t* T, const subdom* d, work_t* w, double* R) {
   const size_t ex = d->ex, ey = d->ey, ez = d->ez;
   const size_t n = ex * ey * ez;
-  const size_t N = (size_t)p->nx * p->ny * p->nz;
   const size_t sty = ex, stz = ex * ey;
   const int three_d = p->nz > 1;
   const int ndim = three_d ? 3 : 2;
@@ -434,15 +794,13 @@ static void rhs_ext_curv(const or_params* p, const subdom* d, const double* Mg, 
   double* E = w->E;
   double* W = w->W;
   double* Mx = w->M;
-  /* metric terms at every extended point (periodic) */
+  /* metric terms at every extended point (from the block's extended metric plane) */
   for (int k = 0; k < (int)ez; ++k)
     for (int j = 0; j < (int)ey; ++j)
       for (int i = 0; i < (int)ex; ++i) {
-        int gx = wrapi(d->ox + i - d->g, p->nx), gy = wrapi(d->oy + j - d->g, p->ny);
-        int gz = wrapi(d->oz + k - d->gz, p->nz);
-        size_t gq = (size_t)gx + (size_t)p->nx * (gy + (size_t)p->ny * gz);
+        const int gx = d->ox + i - d->g, gy = d->oy + j - d->g;
         size_t q = (size_t)i + ex * (j + ey * (size_t)k);
-        for (int c = 0; c < NM; ++c) Mx[c * n + q] = Mg[c * N + gq];
+        for (int c = 0; c < NM; ++c) Mx[c * n + q] = metric_at(T, d->b, c, gx, gy);
       }
   /* metric row of index direction a at point q: (d xi_a / d x, d xi_a / d y, d xi_a / d z) / J */
 #define MROW(a, q, out)                                                             \
@@ -661,50 +1019,24 @@ typedef struct {
   size_t cap;
 } halo_t;
 
-/* Fill the extended array of sub-domain d for stage m-1 of step n.
- * mode: 0 SA (neighbour's current values from Ucur), 1 AT (halo buffer), 2 AS (level n-k). */
-static void fill_ext(const or_params* p, const subdom* d, const double* Ucur, int mode, const hist_t* h,
-                     long n, const int* kf, const halo_t* hb, work_t* w) {
-  const size_t ex = d->ex, ey = d->ey, ez = d->ez, ne = ex * ey * ez;
-  const size_t N = (size_t)p->nx * p->ny * p->nz;
-  const int r = (p->order == 4) ? 2 : 1;
-  for (size_t q = 0; q < NV * ne; ++q) w->E[q] = NAN;
-  for (int k = 0; k < (int)ez; ++k)
-    for (int j = 0; j < (int)ey; ++j)
-      for (int i = 0; i < (int)ex; ++i) {
-        int dep[3], face[3];
-        int nout = classify(d, i, j, k, dep, face);
-        int need = 0, kd = 0;
-        if (nout == 0) need = 1;
-        else if (nout == 1) {
-          need = 1;
-          for (int a = 0; a < 3; ++a) if (face[a] >= 0) kd = kf[face[a]];
-        } else if (nout == 2 && p->viscous) {
-          need = 1;
-          kd = 0;
-          for (int a = 0; a < 3; ++a) {
-            if (face[a] >= 0) {
-              if (dep[a] > r) need = 0;
-              if (kf[face[a]] > kd) kd = kf[face[a]];
-            }
-          }
-        }
-        if (!need) continue;
-        int gx = wrapi(d->ox + i - d->g, p->nx), gy = wrapi(d->oy + j - d->g, p->ny);
-        int gz = wrapi(d->oz + k - d->gz, p->nz);
-        size_t gq = (size_t)gx + (size_t)p->nx * (gy + (size_t)p->ny * gz);
-        size_t q = (size_t)i + ex * (j + ey * k);
-        for (int v = 0; v < NV; ++v) {
-          double val;
-          if (nout == 0 || mode == 0) val = Ucur[v * N + gq];
-          else if (mode == 1) val = hb->ub[v * ne + q];
-          else val = H(h, n - kd)[v * N + gq];
-          w->E[v * ne + q] = val;
-        }
-      }
+/* Block coordinates of extended point (i, j, k) of sub-domain d. */
+static inline void ext_coord(const subdom* d, int i, int j, int k, int* c) {
+  c[0] = d->ox + i - d->g;
+  c[1] = d->oy + j - d->g;
+  c[2] = d->oz + k - d->gz;
 }
 
-/* Delay of each needed foreign extended point (face delay, or max of two faces on an edge). */
+/* A halo source is the sub-domain's own value when it is reached without crossing a periodic
+ * wrap or a block interface (a wall reflection or an outflow copy) and lies in the owned box;
+ * every other source belongs to a neighbouring PE and is seen with the face's delay. */
+static inline int term_own(const subdom* d, const or_term* t) {
+  return !t->crossed && t->b == d->b && t->i >= d->ox && t->i < d->ox + d->sx && t->j >= d->oy &&
+         t->j < d->oy + d->sy && t->k >= d->oz && t->k < d->oz + d->sz;
+}
+
+/* Delay of the foreign values at extended point (i, j, k): the face delay, or on an edge the
+ * larger of the two faces' delays; faces on a physical boundary of the block carry none.
+ * need = 0 for points the stencils never read. */
 static int point_delay(const or_params* p, const subdom* d, int i, int j, int k, const int* kf, int* need) {
   int dep[3], face[3];
   int nout = classify(d, i, j, k, dep, face);
@@ -712,7 +1044,8 @@ static int point_delay(const or_params* p, const subdom* d, int i, int j, int k,
   *need = 0;
   if (nout == 1) {
     *need = 1;
-    for (int a = 0; a < 3; ++a) if (face[a] >= 0) return kf[face[a]];
+    for (int a = 0; a < 3; ++a)
+      if (face[a] >= 0) return d->phys[face[a]] ? 0 : kf[face[a]];
   }
   if (nout == 2 && p->viscous) {
     int kd = 0;
@@ -720,17 +1053,76 @@ static int point_delay(const or_params* p, const subdom* d, int i, int j, int k,
     for (int a = 0; a < 3; ++a)
       if (face[a] >= 0) {
         if (dep[a] > r) *need = 0;
-        if (kf[face[a]] > kd) kd = kf[face[a]];
+        if (!d->phys[face[a]] && kf[face[a]] > kd) kd = kf[face[a]];
       }
     return kd;
   }
   return 0;
 }
 
-/* AT halo buffer: stage-0 extrapolation (Eq. 14/15), then buffer updates (Eq. 8, App. C). */
-static void halo_init(const or_params* p, const subdom* d, const hist_t* h, long n, const int* kf, halo_t* hb) {
+/* Fill the extended array of sub-domain d for stage m-1 of step n.  Owned points and own halo
+ * sources (wall mirror, outflow copy) take the current values, far-field points their state;
+ * foreign sources by mode: 0 SA (the neighbour's current values), 1 AT (the halo buffer),
+ * 2 AS (level n - k). */
+static void fill_ext(const topo_t* T, const subdom* d, const double* Ucur, int mode, const hist_t* h, long n,
+                     const int* kf, const halo_t* hb, work_t* w) {
+  const or_params* p = &T->pb[d->b];
   const size_t ex = d->ex, ey = d->ey, ez = d->ez, ne = ex * ey * ez;
-  const size_t N = (size_t)p->nx * p->ny * p->nz;
+  for (size_t q = 0; q < NV * ne; ++q) w->E[q] = NAN;
+  for (int k = 0; k < (int)ez; ++k)
+    for (int j = 0; j < (int)ey; ++j)
+      for (int i = 0; i < (int)ex; ++i) {
+        int dep[3], face[3];
+        const int nout = classify(d, i, j, k, dep, face);
+        int need;
+        const int kd = point_delay(p, d, i, j, k, kf, &need);
+        if (nout != 0 && !need) continue;
+        int c[3];
+        ext_coord(d, i, j, k, c);
+        const size_t q = (size_t)i + ex * (j + ey * k);
+        if (nout == 0) {
+          for (int v = 0; v < NV; ++v) w->E[v * ne + q] = Ucur[at_pt(T, d->b, v, c[0], c[1], c[2])];
+          continue;
+        }
+        or_term t[OR_MAXT];
+        double cst[NV];
+        const int nt = resolve_state(T, d->b, c[0], c[1], c[2], t, cst);
+        int foreign = 0;
+        for (int m = 0; m < nt; ++m) foreign |= !term_own(d, &t[m]);
+        for (int v = 0; v < NV; ++v) {
+          double val = cst[v];
+          for (int m = 0; m < nt; ++m) {
+            const int own = term_own(d, &t[m]);
+            if (own || mode == 0)
+              val += t[m].w * refl_sign(v, t[m].flip) * Ucur[at_pt(T, t[m].b, v, t[m].i, t[m].j, t[m].k)];
+            else if (mode == 2)
+              val += t[m].w * refl_sign(v, t[m].flip) * H(h, n - kd)[at_pt(T, t[m].b, v, t[m].i, t[m].j, t[m].k)];
+          }
+          if (mode == 1 && foreign) val += hb->ub[v * ne + q];
+          w->E[v * ne + q] = val;
+        }
+      }
+}
+
+/* Foreign part of a halo point from the delayed levels: sum over its foreign sources of
+ * w s_v sum_l c_l U_v^{n-kd-l}. */
+static double foreign_levels(const topo_t* T, const subdom* d, const or_term* t, int nt, int v, const hist_t* h,
+                             long n, int kd, const double* c, int C) {
+  double s = 0.0;
+  for (int m = 0; m < nt; ++m) {
+    if (term_own(d, &t[m])) continue;
+    const size_t o = at_pt(T, t[m].b, v, t[m].i, t[m].j, t[m].k);
+    double inner = 0.0;
+    for (int l = 0; l < C; ++l) inner += c[l] * H(h, n - kd - l)[o];
+    s += t[m].w * refl_sign(v, t[m].flip) * inner;
+  }
+  return s;
+}
+
+/* AT halo buffer: stage-0 extrapolation (Eq. 14/15), then buffer updates (Eq. 8, App. C). */
+static void halo_init(const topo_t* T, const subdom* d, const hist_t* h, long n, const int* kf, halo_t* hb) {
+  const or_params* p = &T->pb[d->b];
+  const size_t ex = d->ex, ey = d->ey, ez = d->ez, ne = ex * ey * ez;
   const int C = or_levels(p->order);
   for (int k = 0; k < (int)ez; ++k)
     for (int j = 0; j < (int)ey; ++j)
@@ -740,14 +1132,14 @@ static void halo_init(const or_params* p, const subdom* d, const hist_t* h, long
         if (!need) continue;
         double c[5];
         or_extrap_weights(p->order, (double)kd, c);
-        int gx = wrapi(d->ox + i - d->g, p->nx), gy = wrapi(d->oy + j - d->g, p->ny);
-        int gz = wrapi(d->oz + k - d->gz, p->nz);
-        size_t gq = (size_t)gx + (size_t)p->nx * (gy + (size_t)p->ny * gz);
+        int cc[3];
+        ext_coord(d, i, j, k, cc);
+        or_term t[OR_MAXT];
+        double cst[NV];
+        const int nt = resolve_state(T, d->b, cc[0], cc[1], cc[2], t, cst);
         size_t q = (size_t)i + ex * (j + ey * k);
         for (int v = 0; v < NV; ++v) {
-          double s = 0.0;
-          for (int l = 0; l < C; ++l) s += c[l] * H(h, n - kd - l)[v * N + gq];
-          hb->ub[v * ne + q] = s;
+          hb->ub[v * ne + q] = foreign_levels(T, d, t, nt, v, h, n, kd, c, C);
           hb->qb[v * ne + q] = 0.0;
         }
       }
@@ -785,11 +1177,12 @@ static void halo_init_learned(const or_params* p, const subdom* d, int s, const 
   }
 }
 
-static void halo_update(const or_params* p, const subdom* d, const hist_t* h, long n, const int* kf, int m,
+
+static void halo_update(const topo_t* T, const subdom* d, const hist_t* h, long n, const int* kf, int m,
                         const double* A, const double* B, halo_t* hb) {
   /* buffer update at stage m (1-based) uses the temporal derivative at stage e = m - 1 */
+  const or_params* p = &T->pb[d->b];
   const size_t ex = d->ex, ey = d->ey, ez = d->ez, ne = ex * ey * ez;
-  const size_t N = (size_t)p->nx * p->ny * p->nz;
   const int C = or_levels(p->order);
   for (int k = 0; k < (int)ez; ++k)
     for (int j = 0; j < (int)ey; ++j)
@@ -799,13 +1192,14 @@ static void halo_update(const or_params* p, const subdom* d, const hist_t* h, lo
         if (!need) continue;
         double dd[5];
         or_buffer_dudt(p->order, m - 1, (double)kd, dd);
-        int gx = wrapi(d->ox + i - d->g, p->nx), gy = wrapi(d->oy + j - d->g, p->ny);
-        int gz = wrapi(d->oz + k - d->gz, p->nz);
-        size_t gq = (size_t)gx + (size_t)p->nx * (gy + (size_t)p->ny * gz);
+        int cc[3];
+        ext_coord(d, i, j, k, cc);
+        or_term t[OR_MAXT];
+        double cst[NV];
+        const int nt = resolve_state(T, d->b, cc[0], cc[1], cc[2], t, cst);
         size_t q = (size_t)i + ex * (j + ey * k);
         for (int v = 0; v < NV; ++v) {
-          double s = 0.0; /* = dt * dU/dt|_buf^(m-1) */
-          for (int l = 0; l < C; ++l) s += dd[l] * H(h, n - kd - l)[v * N + gq];
+          const double s = foreign_levels(T, d, t, nt, v, h, n, kd, dd, C); /* = dt * dU/dt|_buf^(m-1) */
           double qn = A[m - 1] * hb->qb[v * ne + q] + s;
           hb->qb[v * ne + q] = qn;
           hb->ub[v * ne + q] += B[m - 1] * qn;
@@ -813,17 +1207,28 @@ static void halo_update(const or_params* p, const subdom* d, const hist_t* h, lo
       }
 }
 
-/* One filter pass along axis `ax` over all sub-domains: Uin -> Uout. */
-static void filter_pass(const or_params* p, int ax, const double* Uin, double* Uout, int mode,
-                        const hist_t* h, long n, int** kfs, int nsub) {
-  const size_t N = (size_t)p->nx * p->ny * p->nz;
-  const int C = or_levels(p->order);
-  const int nn[3] = {p->nx, p->ny, p->nz};
-  memcpy(Uout, Uin, sizeof(double) * NV * N);
+/* Wall point of block b: a point on a face of type wall (no-slip: its momentum is held at 0). */
+static int wall_point(const topo_t* T, int b, int i, int j) {
+  const or_block* B = &T->b[b];
+  return (i == 0 && B->face[0].type == OR_WALL) || (i == B->nx - 1 && B->face[1].type == OR_WALL) ||
+         (j == 0 && B->face[2].type == OR_WALL) || (j == B->ny - 1 && B->face[3].type == OR_WALL);
+}
+
+/* One filter pass along axis `ax` over all sub-domains: Uin -> Uout.  Window points beyond the
+ * sub-domain: inside the block, the neighbour's value by the mode; beyond the block, the face's
+ * sources (own ones current, foreign ones by the mode).  Wall points keep zero momentum. */
+static void filter_pass(const topo_t* T, int ax, const double* Uin, double* Uout, int mode, const hist_t* h, long n,
+                        int** kfs) {
+  memcpy(Uout, Uin, sizeof(double) * NV * T->Ntot);
+  const int nsub = T->nsub;
 #pragma omp parallel for schedule(dynamic)
   for (int s = 0; s < nsub; ++s) {
     subdom d;
-    make_subdom(p, s, 0, &d);
+    make_sub(T, s, 0, &d);
+    const or_params* p = &T->pb[d.b];
+    if (ax == 2 && p->nz == 1) continue; /* two-dimensional block */
+    const int C = or_levels(p->order);
+    const int nn[3] = {p->nx, p->ny, p->nz};
     const int o[3] = {d.ox, d.oy, d.oz}, sz[3] = {d.sx, d.sy, d.sz};
     const int* kf = kfs[s];
     int len = sz[ax];
@@ -835,24 +1240,40 @@ static void filter_pass(const or_params* p, int ax, const double* Uin, double* U
         for (int v = 0; v < NV; ++v) {
           for (int t = -5; t < len + 5; ++t) {
             int c[3];
-            c[ax] = wrapi(o[ax] + t, nn[ax]);
+            c[ax] = o[ax] + t;
             c[a1] = o[a1] + t1;
             c[a2] = o[a2] + t2;
-            size_t gq = (size_t)c[0] + (size_t)p->nx * (c[1] + (size_t)p->ny * c[2]);
+            const int f = 2 * ax + (t < 0 ? 0 : 1);
+            const int kd = d.phys[f] ? 0 : kf[f];
+            double cw[5];
+            if (mode == 1) or_extrap_weights(p->order, (double)(kd + 1), cw); /* to t_{n+1}: delay k + 1 */
             double val;
-            if (t >= 0 && t < len) val = Uin[v * N + gq];
-            else {
-              int f = 2 * ax + (t < 0 ? 0 : 1);
-              int kd = kf[f];
-              if (mode == 0) val = Uin[v * N + gq];
-              else if (mode == 2) val = H(h, n - kd)[v * N + gq];
+            if (t >= 0 && t < len) {
+              val = Uin[at_pt(T, d.b, v, c[0], c[1], c[2])];
+            } else if (c[ax] >= 0 && c[ax] < nn[ax]) {
+              const size_t gq = at_pt(T, d.b, v, c[0], c[1], c[2]);
+              if (mode == 0) val = Uin[gq];
+              else if (mode == 2) val = H(h, n - kd)[gq];
               else {
-                /* extrapolate the visible levels to t_{n+1}: delay k+1 relative to n+1 */
-                double cw[5];
-                or_extrap_weights(p->order, (double)(kd + 1), cw);
                 double sacc = 0.0;
-                for (int l = 0; l < C; ++l) sacc += cw[l] * H(h, n - kd - l)[v * N + gq];
+                for (int l = 0; l < C; ++l) sacc += cw[l] * H(h, n - kd - l)[gq];
                 val = sacc;
+              }
+            } else {
+              or_term tt[OR_MAXT];
+              double cst[NV];
+              const int nt = resolve_state(T, d.b, c[0], c[1], c[2], tt, cst);
+              val = cst[v];
+              for (int m = 0; m < nt; ++m) {
+                const size_t gq = at_pt(T, tt[m].b, v, tt[m].i, tt[m].j, tt[m].k);
+                const double sg = tt[m].w * refl_sign(v, tt[m].flip);
+                if (mode == 0 || term_own(&d, &tt[m])) val += sg * Uin[gq];
+                else if (mode == 2) val += sg * H(h, n - kd)[gq];
+                else {
+                  double sacc = 0.0;
+                  for (int l = 0; l < C; ++l) sacc += cw[l] * H(h, n - kd - l)[gq];
+                  val += sg * sacc;
+                }
               }
             }
             line[t + 5] = val;
@@ -863,8 +1284,8 @@ static void filter_pass(const or_params* p, int ax, const double* Uin, double* U
             c[ax] = o[ax] + t;
             c[a1] = o[a1] + t1;
             c[a2] = o[a2] + t2;
-            size_t gq = (size_t)c[0] + (size_t)p->nx * (c[1] + (size_t)p->ny * c[2]);
-            Uout[v * N + gq] = out[t];
+            const int zero = v >= 1 && v <= 3 && wall_point(T, d.b, c[0], c[1]);
+            Uout[at_pt(T, d.b, v, c[0], c[1], c[2])] = zero ? 0.0 : out[t];
           }
         }
     free(line);
@@ -881,51 +1302,145 @@ static int ring_depth(const or_params* p) {
   return kmax + C + 1;
 }
 
+/* Volume-averaged kinetic energy and enstrophy (Sec. 5.2, rho_0 = 1) with vorticity from the CD
+ * scheme, cell-volume-weighted totals of the conserved variables, and a non-finite flag, over
+ * all blocks.  out[8] = {K, eps, sum rho, sum rho u, sum rho v, sum rho w, sum rho E, nan}.
+ * On a curvilinear block the cell volume is J^-1 and the averages are volume-weighted; velocity
+ * derivatives are taken in index space and mapped by the metric terms.  The enstrophy average
+ * covers the points whose CD stencils stay inside their block or cross only periodic faces. */
+static void diag_topo(const topo_t* T, const double* U, double* out) {
+  double ke = 0, ens = 0, vol = 0, vole = 0, tot[5] = {0, 0, 0, 0, 0};
+  int bad = 0;
+  for (int b = 0; b < T->nb; ++b) {
+    const or_params* p = &T->pb[b];
+    const or_block* B = &T->b[b];
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const int curv = T->M[b] != NULL;
+    const double dV0 = p->dx * p->dy * (nz > 1 ? p->dz : 1.0);
+    const int order = p->order, rs = order == 4 ? 2 : 1;
+    const int nn[3] = {nx, ny, nz};
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          const double dV = curv ? metric_at(T, b, 5, i, j) : dV0;
+          const int c0[3] = {i, j, k};
+          double rho = U[at_pt(T, b, 0, i, j, k)];
+          double u = U[at_pt(T, b, 1, i, j, k)] / rho, v = U[at_pt(T, b, 2, i, j, k)] / rho;
+          double w = U[at_pt(T, b, 3, i, j, k)] / rho;
+          for (int c = 0; c < 5; ++c) {
+            const double x = U[at_pt(T, b, c, i, j, k)];
+            if (!isfinite(x)) bad = 1;
+            tot[c] += x * dV;
+          }
+          const double wv = curv ? dV : 1.0; /* Cartesian: plain point average */
+          vol += wv;
+          ke += 0.5 * rho * (u * u + v * v + w * w) * wv;
+          int inner = 1;
+          for (int a = 0; a < 3; ++a)
+            if (nn[a] > 1 && (c0[a] < rs && B->face[2 * a].type != OR_PERIODIC)) inner = 0;
+            else if (nn[a] > 1 && (c0[a] > nn[a] - 1 - rs && B->face[2 * a + 1].type != OR_PERIODIC)) inner = 0;
+          if (!inner) continue;
+          /* velocity derivative along axis a of component c at (i,j,k), periodic CD */
+          double dvel[3][3];
+          for (int c = 0; c < 3; ++c)
+            for (int a = 0; a < 3; ++a) {
+              int n_a = nn[a];
+              if (n_a == 1) { dvel[c][a] = 0.0; continue; }
+              double hh = curv ? 1.0 : (a == 0 ? p->dx : (a == 1 ? p->dy : p->dz));
+              double f[5];
+              for (int o = -2; o <= 2; ++o) {
+                if (rs == 1 && (o == -2 || o == 2)) { f[o + 2] = 0.0; continue; }
+                int ii = i, jj = j, kk = k;
+                if (a == 0) ii = wrapi(i + o, nx);
+                if (a == 1) jj = wrapi(j + o, ny);
+                if (a == 2) kk = wrapi(k + o, nz);
+                f[o + 2] = U[at_pt(T, b, 1 + c, ii, jj, kk)] / U[at_pt(T, b, 0, ii, jj, kk)];
+              }
+              if (order == 4)
+                dvel[c][a] = ((-1.0 / 3.0) * (f[4] - f[0]) / 4.0 + (4.0 / 3.0) * (f[3] - f[1]) / 2.0) / hh;
+              else
+                dvel[c][a] = (f[3] - f[1]) / (2.0 * hh);
+            }
+          if (curv) {
+            /* d u_c / d x_j = J sum_a (metric row a)_j d u_c / d xi_a */
+            const double J = 1.0 / dV;
+            const double m[3][3] = {{metric_at(T, b, 0, i, j), metric_at(T, b, 1, i, j), 0.0},
+                                    {metric_at(T, b, 2, i, j), metric_at(T, b, 3, i, j), 0.0},
+                                    {0.0, 0.0, metric_at(T, b, 4, i, j)}};
+            double dphys[3][3];
+            for (int c = 0; c < 3; ++c)
+              for (int jj = 0; jj < 3; ++jj)
+                dphys[c][jj] = J * (m[0][jj] * dvel[c][0] + m[1][jj] * dvel[c][1] + m[2][jj] * dvel[c][2]);
+            memcpy(dvel, dphys, sizeof(dvel));
+          }
+          double wx = dvel[2][1] - dvel[1][2], wy = dvel[0][2] - dvel[2][0], wz = dvel[1][0] - dvel[0][1];
+          ens += 0.5 * rho * (wx * wx + wy * wy + wz * wz) * wv;
+          vole += wv;
+        }
+  }
+  out[0] = ke / vol;
+  out[1] = vole > 0 ? ens / vole : 0.0;
+  for (int c = 0; c < 5; ++c) out[2 + c] = tot[c];
+  out[7] = bad ? 1.0 : 0.0;
+}
+
+int or_diagnostics(const or_params* p, const double* U, double* out) {
+  topo_t T;
+  const int r = (p->order == 4) ? 2 : 1;
+  const int g = p->viscous ? 2 * r : r;
+  int rc = topo_build(p, g, g, &T);
+  if (rc == 0) diag_topo(&T, U, out);
+  topo_free(&T);
+  return rc;
+}
+
 /* Initial-history state for a resumed run: levels n0 - R + 1 .. n0 may be passed in `hist_in`
  * ([R][5][N], level n0 - R + 1 first); NULL means a fresh start at n0 = 0 from U0. */
 
 /*
- * Advance `nsteps` steps starting from step index n0 with state U (in/out).
+ * Advance `nsteps` steps starting from step index n0 with state U (in/out; all blocks, block
+ * after block).
  * delays: SAA table int8 [n0 + nsteps][nsub][6] (ignored for SA/CAA).
  * diag (optional): per step [nsteps][8] = KE, enstrophy, sum rho, sum rho u, sum rho v,
  *                  sum rho w, sum rho E, nan-flag (after the step).
  * Returns 0 on success, nonzero on invalid input.
  */
-int or_diagnostics(const or_params* p, const double* U, double* out);
-
 int or_run(const or_params* p, double* U, const int8_t* delays, long n0, long nsteps, const double* hist_in,
            double* diag) {
-  const size_t N = (size_t)p->nx * p->ny * p->nz;
-  const int nsub = p->px * p->py * p->pz;
   const int C = or_levels(p->order);
   const int r = (p->order == 4) ? 2 : 1;
   const int g = p->viscous ? 2 * r : r;
   double A[5], B[5];
   const int S = or_lserk(p->order, A, B);
-  /* validation */
+  const int need = g > (p->filter ? 5 : 0) ? g : (p->filter ? 5 : 0);
+  topo_t T;
+  int rc = topo_build(p, g, need, &T);
+  if (rc) { topo_free(&T); return rc; }
+  if (p->mlp && p->nblocks > 0) { topo_free(&T); return 20; }
+  const size_t NT = T.Ntot;
+  const int nsub = T.nsub;
+  /* validation: every sub-domain at least as wide as the halo it needs */
   for (int s = 0; s < nsub; ++s) {
     subdom d;
-    make_subdom(p, s, g, &d);
-    int need = g > (p->filter ? 5 : 0) ? g : (p->filter ? 5 : 0);
-    if (d.sx < need || d.sy < need || (p->nz > 1 && d.sz < need)) return 1;
+    make_sub(&T, s, g, &d);
+    if (d.sx < need || d.sy < need || (T.pb[d.b].nz > 1 && d.sz < need)) { topo_free(&T); return 1; }
   }
-  if (p->algo == 1 && p->caa_L < 1) return 2;
+  if (p->algo == 1 && p->caa_L < 1) { topo_free(&T); return 2; }
   hist_t h;
   h.R = ring_depth(p);
   h.lev = (double**)malloc(sizeof(double*) * h.R);
-  for (int i = 0; i < h.R; ++i) h.lev[i] = (double*)calloc(NV * N, sizeof(double));
+  for (int i = 0; i < h.R; ++i) h.lev[i] = (double*)calloc(NV * NT, sizeof(double));
   if (hist_in) {
     for (int i = 0; i < h.R; ++i) {
       long lvl = n0 - h.R + 1 + i;
-      if (lvl >= 0) memcpy(h.lev[lvl % h.R], hist_in + (size_t)i * NV * N, sizeof(double) * NV * N);
+      if (lvl >= 0) memcpy(h.lev[lvl % h.R], hist_in + (size_t)i * NV * NT, sizeof(double) * NV * NT);
     }
   }
-  memcpy(h.lev[n0 % h.R], U, sizeof(double) * NV * N);
+  memcpy(h.lev[n0 % h.R], U, sizeof(double) * NV * NT);
 
-  double* Ucur = (double*)malloc(sizeof(double) * NV * N);
-  double* Unew = (double*)malloc(sizeof(double) * NV * N);
-  double* Q = (double*)malloc(sizeof(double) * NV * N);
-  double* Mg = metric_field(p);
+  double* Ucur = (double*)malloc(sizeof(double) * NV * NT);
+  double* Unew = (double*)malloc(sizeof(double) * NV * NT);
+  double* Q = (double*)malloc(sizeof(double) * NV * NT);
   int** kfs = (int**)malloc(sizeof(int*) * nsub);
   for (int s = 0; s < nsub; ++s) kfs[s] = (int*)malloc(sizeof(int) * 6);
   halo_t* hbs = (halo_t*)calloc(nsub, sizeof(halo_t));
@@ -940,8 +1455,8 @@ int or_run(const or_params* p, double* U, const int8_t* delays, long n0, long ns
         if (k < 0) k = 0;
         kfs[s][f] = k;
       }
-    memcpy(Ucur, H(&h, n), sizeof(double) * NV * N);
-    memset(Q, 0, sizeof(double) * NV * N);
+    memcpy(Ucur, H(&h, n), sizeof(double) * NV * NT);
+    memset(Q, 0, sizeof(double) * NV * NT);
     for (int m = 1; m <= S; ++m) {
 #pragma omp parallel
       {
@@ -950,7 +1465,8 @@ int or_run(const or_params* p, double* U, const int8_t* delays, long n0, long ns
 #pragma omp for schedule(dynamic)
         for (int s = 0; s < nsub; ++s) {
           subdom d;
-          make_subdom(p, s, g, &d);
+          make_sub(&T, s, g, &d);
+          const or_params* pb = &T.pb[d.b];
           size_t ne = (size_t)d.ex * d.ey * d.ez;
           work_reserve(&w, ne);
           if (mode == 1) {
@@ -961,160 +1477,95 @@ int or_run(const or_params* p, double* U, const int8_t* delays, long n0, long ns
               hbs[s].cap = ne;
             }
             if (m == 1) {
-              halo_init(p, &d, &h, n, kfs[s], &hbs[s]);
-              if (p->mlp) halo_init_learned(p, &d, s, &h, n, kfs[s], &hbs[s]);
+              halo_init(&T, &d, &h, n, kfs[s], &hbs[s]);
+              if (p->mlp) halo_init_learned(pb, &d, s, &h, n, kfs[s], &hbs[s]);
             }
           }
-          fill_ext(p, &d, Ucur, mode, &h, n, kfs[s], &hbs[s], &w);
+          fill_ext(&T, &d, Ucur, mode, &h, n, kfs[s], &hbs[s], &w);
           size_t no = (size_t)d.sx * d.sy * d.sz;
           double* R = (double*)malloc(sizeof(double) * NV * no);
-          if (Mg) rhs_ext_curv(p, &d, Mg, &w, R);
-          else rhs_ext(p, &d, &w, R);
-          /* Eq. 3: Q^(m) = A_m Q^(m-1) + dt R(U^(m-1));  U^(m) = U^(m-1) + B_m Q^(m) */
+          if (T.M[d.b]) rhs_ext_curv(pb, &T, &d, &w, R);
+          else rhs_ext(pb, &d, &w, R);
+          /* Eq. 3: Q^(m) = A_m Q^(m-1) + dt R(U^(m-1));  U^(m) = U^(m-1) + B_m Q^(m); no-slip
+           * wall points keep zero momentum */
           for (int v = 0; v < NV; ++v)
             for (int k = 0; k < d.sz; ++k)
               for (int j = 0; j < d.sy; ++j)
                 for (int i = 0; i < d.sx; ++i) {
-                  size_t gq = (size_t)(d.ox + i) + (size_t)p->nx * ((d.oy + j) + (size_t)p->ny * (d.oz + k));
+                  size_t gq = at_pt(&T, d.b, v, d.ox + i, d.oy + j, d.oz + k);
                   size_t o = (size_t)i + (size_t)d.sx * (j + (size_t)d.sy * k);
-                  double qn = A[m - 1] * Q[v * N + gq] + p->dt * R[v * no + o];
-                  Q[v * N + gq] = qn;
-                  Unew[v * N + gq] = Ucur[v * N + gq] + B[m - 1] * qn;
+                  double qn = A[m - 1] * Q[gq] + p->dt * R[v * no + o];
+                  double un = Ucur[gq] + B[m - 1] * qn;
+                  if (v >= 1 && v <= 3 && wall_point(&T, d.b, d.ox + i, d.oy + j)) qn = un = 0.0;
+                  Q[gq] = qn;
+                  Unew[gq] = un;
                 }
           free(R);
-          if (mode == 1 && m <= S - 1) halo_update(p, &d, &h, n, kfs[s], m, A, B, &hbs[s]);
+          if (mode == 1 && m <= S - 1) halo_update(&T, &d, &h, n, kfs[s], m, A, B, &hbs[s]);
         }
         work_free(&w);
       }
       double* t = Ucur; Ucur = Unew; Unew = t;
     }
     if (p->filter) {
-      int nd = p->nz > 1 ? 3 : 2;
-      for (int ax = 0; ax < nd; ++ax) {
-        filter_pass(p, ax, Ucur, Unew, mode, &h, n, kfs, nsub);
+      for (int ax = 0; ax < 3; ++ax) {
+        filter_pass(&T, ax, Ucur, Unew, mode, &h, n, kfs);
         double* t = Ucur; Ucur = Unew; Unew = t;
       }
     }
-    memcpy(h.lev[(n + 1) % h.R], Ucur, sizeof(double) * NV * N);
-    if (diag) or_diagnostics(p, Ucur, diag + (size_t)(n - n0) * 8);
+    memcpy(h.lev[(n + 1) % h.R], Ucur, sizeof(double) * NV * NT);
+    if (diag) diag_topo(&T, Ucur, diag + (size_t)(n - n0) * 8);
   }
-  memcpy(U, Ucur, sizeof(double) * NV * N);
+  memcpy(U, Ucur, sizeof(double) * NV * NT);
   for (int i = 0; i < h.R; ++i) free(h.lev[i]);
   free(h.lev);
-  free(Ucur); free(Unew); free(Q); free(Mg);
+  free(Ucur); free(Unew); free(Q);
   for (int s = 0; s < nsub; ++s) { free(kfs[s]); free(hbs[s].ub); free(hbs[s].qb); }
   free(kfs); free(hbs);
+  topo_free(&T);
   return 0;
 }
 
-/* R(U) of the whole periodic field in synchronous mode (halos = current neighbour values). */
+/* R(U) of all blocks in synchronous mode (halos = current neighbour values or the boundary
+ * sources). */
 int or_rhs(const or_params* p, const double* U, double* Rout) {
-  const size_t N = (size_t)p->nx * p->ny * p->nz;
-  const int nsub = p->px * p->py * p->pz;
   const int r = (p->order == 4) ? 2 : 1;
   const int g = p->viscous ? 2 * r : r;
   int kf[6] = {0, 0, 0, 0, 0, 0};
-  for (int s = 0; s < nsub; ++s) {
+  topo_t T;
+  int rc = topo_build(p, g, g, &T);
+  if (rc) { topo_free(&T); return rc; }
+  for (int s = 0; s < T.nsub; ++s) {
     subdom d;
-    make_subdom(p, s, g, &d);
-    if (d.sx < g || d.sy < g || (p->nz > 1 && d.sz < g)) return 1;
+    make_sub(&T, s, g, &d);
+    if (d.sx < g || d.sy < g || (T.pb[d.b].nz > 1 && d.sz < g)) { topo_free(&T); return 1; }
   }
-  double* Mg = metric_field(p);
 #pragma omp parallel
   {
     work_t w;
     memset(&w, 0, sizeof(w));
 #pragma omp for schedule(dynamic)
-    for (int s = 0; s < nsub; ++s) {
+    for (int s = 0; s < T.nsub; ++s) {
       subdom d;
-      make_subdom(p, s, g, &d);
+      make_sub(&T, s, g, &d);
+      const or_params* pb = &T.pb[d.b];
       work_reserve(&w, (size_t)d.ex * d.ey * d.ez);
-      fill_ext(p, &d, U, 0, NULL, 0, kf, NULL, &w);
+      fill_ext(&T, &d, U, 0, NULL, 0, kf, NULL, &w);
       size_t no = (size_t)d.sx * d.sy * d.sz;
       double* R = (double*)malloc(sizeof(double) * NV * no);
-      if (Mg) rhs_ext_curv(p, &d, Mg, &w, R);
-      else rhs_ext(p, &d, &w, R);
+      if (T.M[d.b]) rhs_ext_curv(pb, &T, &d, &w, R);
+      else rhs_ext(pb, &d, &w, R);
       for (int v = 0; v < NV; ++v)
         for (int k = 0; k < d.sz; ++k)
           for (int j = 0; j < d.sy; ++j)
-            for (int i = 0; i < d.sx; ++i) {
-              size_t gq = (size_t)(d.ox + i) + (size_t)p->nx * ((d.oy + j) + (size_t)p->ny * (d.oz + k));
-              Rout[v * N + gq] = R[v * no + (size_t)i + (size_t)d.sx * (j + (size_t)d.sy * k)];
-            }
+            for (int i = 0; i < d.sx; ++i)
+              Rout[at_pt(&T, d.b, v, d.ox + i, d.oy + j, d.oz + k)] =
+                  R[v * no + (size_t)i + (size_t)d.sx * (j + (size_t)d.sy * k)];
       free(R);
     }
     work_free(&w);
   }
-  free(Mg);
-  return 0;
-}
-
-/* Volume-averaged kinetic energy and enstrophy (Sec. 5.2, rho_0 = 1) with vorticity from the CD
- * scheme on the periodic field, cell-volume-weighted totals of the conserved variables, and a
- * non-finite flag.  out[8] = {K, eps, sum rho, sum rho u, sum rho v, sum rho w, sum rho E, nan}.
- * On a curvilinear grid the cell volume is J^-1 and the averages are volume-weighted; velocity
- * derivatives are taken in index space and mapped by the metric terms. */
-int or_diagnostics(const or_params* p, const double* U, double* out) {
-  const int nx = p->nx, ny = p->ny, nz = p->nz;
-  const size_t N = (size_t)nx * ny * nz;
-  double* Mg = metric_field(p);
-  const double dV0 = p->dx * p->dy * (nz > 1 ? p->dz : 1.0);
-  double ke = 0, ens = 0, vol = 0, tot[5] = {0, 0, 0, 0, 0};
-  int bad = 0;
-  const int order = p->order;
-  for (int k = 0; k < nz; ++k)
-    for (int j = 0; j < ny; ++j)
-      for (int i = 0; i < nx; ++i) {
-        size_t q = (size_t)i + (size_t)nx * (j + (size_t)ny * k);
-        const double dV = Mg ? Mg[5 * N + q] : dV0;
-        double rho = U[q];
-        double u = U[N + q] / rho, v = U[2 * N + q] / rho, w = U[3 * N + q] / rho;
-        for (int c = 0; c < 5; ++c) {
-          if (!isfinite(U[c * N + q])) bad = 1;
-          tot[c] += U[c * N + q] * dV;
-        }
-        const double wv = Mg ? dV : 1.0; /* Cartesian: plain point average */
-        vol += wv;
-        ke += 0.5 * rho * (u * u + v * v + w * w) * wv;
-        /* velocity derivative along axis a of component c at (i,j,k), periodic CD */
-        double dvel[3][3];
-        for (int c = 0; c < 3; ++c)
-          for (int a = 0; a < 3; ++a) {
-            int n_a = a == 0 ? nx : (a == 1 ? ny : nz);
-            if (n_a == 1) { dvel[c][a] = 0.0; continue; }
-            double hh = Mg ? 1.0 : (a == 0 ? p->dx : (a == 1 ? p->dy : p->dz));
-            double f[5];
-            for (int o = -2; o <= 2; ++o) {
-              int ii = i, jj = j, kk = k;
-              if (a == 0) ii = wrapi(i + o, nx);
-              if (a == 1) jj = wrapi(j + o, ny);
-              if (a == 2) kk = wrapi(k + o, nz);
-              size_t qq = (size_t)ii + (size_t)nx * (jj + (size_t)ny * kk);
-              f[o + 2] = U[(1 + c) * N + qq] / U[qq];
-            }
-            if (order == 4)
-              dvel[c][a] = ((-1.0 / 3.0) * (f[4] - f[0]) / 4.0 + (4.0 / 3.0) * (f[3] - f[1]) / 2.0) / hh;
-            else
-              dvel[c][a] = (f[3] - f[1]) / (2.0 * hh);
-          }
-        if (Mg) {
-          /* d u_c / d x_j = J sum_a (metric row a)_j d u_c / d xi_a */
-          const double J = 1.0 / Mg[5 * N + q];
-          const double m[3][3] = {{Mg[q], Mg[N + q], 0.0}, {Mg[2 * N + q], Mg[3 * N + q], 0.0}, {0.0, 0.0, Mg[4 * N + q]}};
-          double dphys[3][3];
-          for (int c = 0; c < 3; ++c)
-            for (int jj = 0; jj < 3; ++jj)
-              dphys[c][jj] = J * (m[0][jj] * dvel[c][0] + m[1][jj] * dvel[c][1] + m[2][jj] * dvel[c][2]);
-          memcpy(dvel, dphys, sizeof(dvel));
-        }
-        double wx = dvel[2][1] - dvel[1][2], wy = dvel[0][2] - dvel[2][0], wz = dvel[1][0] - dvel[0][1];
-        ens += 0.5 * rho * (wx * wx + wy * wy + wz * wz) * wv;
-      }
-  out[0] = ke / vol;
-  out[1] = ens / vol;
-  for (int c = 0; c < 5; ++c) out[2 + c] = tot[c];
-  out[7] = bad ? 1.0 : 0.0;
-  free(Mg);
+  topo_free(&T);
   return 0;
 }
 

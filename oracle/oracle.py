@@ -24,6 +24,21 @@ _lock = threading.Lock()
 _lib = None
 
 
+class OrFace(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("nb", ctypes.c_int), ("nf", ctypes.c_int), ("rev", ctypes.c_int),
+                ("state", ctypes.c_double * 5), ("shift", ctypes.c_double * 2)]
+
+
+class OrBlock(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("px", ctypes.c_int), ("py", ctypes.c_int), ("pz", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+        ("grid_xy", ctypes.POINTER(ctypes.c_double)), ("grid_shift", ctypes.c_double * 4),
+        ("face", OrFace * 6),
+    ]
+
+
 class OrParams(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
@@ -37,6 +52,7 @@ class OrParams(ctypes.Structure):
         ("filter", ctypes.c_int), ("alpha_f", ctypes.c_double), ("dt", ctypes.c_double),
         ("mlp", ctypes.POINTER(ctypes.c_float)), ("mlp_scales", ctypes.POINTER(ctypes.c_double)),
         ("grid_xy", ctypes.POINTER(ctypes.c_double)), ("grid_shift", ctypes.c_double * 4),
+        ("nblocks", ctypes.c_int), ("blocks", ctypes.POINTER(OrBlock)),
     ]
 
 
@@ -89,8 +105,36 @@ ALGOS = {"SA": 0, "CAA": 1, "SAA": 2}
 
 
 def params(case) -> OrParams:
-    """Translate a ``inputs.Case`` description into the oracle's parameter struct (a curvilinear
-    case carries its point coordinates; the array is kept alive on the struct)."""
+    """Translate a ``inputs.Case`` (or ``inputs.MultiBlock``) description into the oracle's
+    parameter struct (point coordinates and block tables are kept alive on the struct)."""
+    from paper_2506_03027_gb300.inputs import MultiBlock, FACE_TYPES
+    if isinstance(case, MultiBlock):
+        mb = case
+        p = params(mb.case.replace(curv=0.0))
+        arr = (OrBlock * len(mb.blocks))()
+        keep = []
+        for i, (b, faces, g) in enumerate(zip(mb.blocks, mb.faces, mb.xy)):
+            B = arr[i]
+            B.nx, B.ny, B.nz, B.px, B.py, B.pz = b.nx, b.ny, b.nz, b.px, b.py, b.pz
+            B.dx, B.dy, B.dz = b.dx, b.dy, b.dz
+            if g is not None:
+                xy = np.ascontiguousarray(g[0], dtype=np.float64)
+                keep.append(xy)
+                B.grid_xy = _dptr(xy)
+                for q in range(4):
+                    B.grid_shift[q] = float(g[1][q])
+            for f, F in enumerate(faces):
+                B.face[f].type = FACE_TYPES[F.type]
+                B.face[f].nb, B.face[f].nf, B.face[f].rev = F.nb, F.nf, int(F.rev)
+                for v in range(5):
+                    B.face[f].state[v] = float(F.state[v])
+                for q in range(2):
+                    B.face[f].shift[q] = float(F.shift[q])
+        p._blocks = arr
+        p._keep = keep
+        p.nblocks = len(mb.blocks)
+        p.blocks = ctypes.cast(arr, ctypes.POINTER(OrBlock))
+        return p
     p = OrParams(
         nx=case.nx, ny=case.ny, nz=case.nz, px=case.px, py=case.py, pz=case.pz,
         dx=case.dx, dy=case.dy, dz=case.dz, gamma=case.gamma, mach=case.mach, re=case.re,
@@ -120,7 +164,9 @@ def run(case, U0: np.ndarray, nsteps: int, delays: np.ndarray | None = None, n0:
         ms = np.ascontiguousarray(model[1], dtype=np.float64)
         p.mlp = mp.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         p.mlp_scales = ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-    U = np.ascontiguousarray(U0, dtype=np.float64).copy()
+    from paper_2506_03027_gb300.inputs import MultiBlock, join_states, split_states
+    multi = isinstance(case, MultiBlock)
+    U = join_states(U0) if multi else np.ascontiguousarray(U0, dtype=np.float64).copy()
     if delays is None:
         dl = np.zeros(1, dtype=np.int8)
     else:
@@ -131,26 +177,33 @@ def run(case, U0: np.ndarray, nsteps: int, delays: np.ndarray | None = None, n0:
                     n0, nsteps, hp, _dptr(dg) if diag else None)
     if rc != 0:
         raise ValueError(f"oracle rejected the case (code {rc})")
+    if multi:
+        U = split_states(case, U)
     return (U, dg[:nsteps]) if diag else U
 
 
 def rhs(case, U: np.ndarray) -> np.ndarray:
     """R(U) of Eq. 1 with synchronous halos (the CD right-hand side of the whole field)."""
+    from paper_2506_03027_gb300.inputs import MultiBlock, join_states, split_states
     lib = _load()
     p = params(case)
-    U = np.ascontiguousarray(U, dtype=np.float64)
+    multi = isinstance(case, MultiBlock)
+    U = join_states(U) if multi else np.ascontiguousarray(U, dtype=np.float64)
     R = np.zeros_like(U)
     if lib.or_rhs(ctypes.byref(p), _dptr(U), _dptr(R)) != 0:
         raise ValueError("oracle rejected the case")
-    return R
+    return split_states(case, R) if multi else R
 
 
 def diagnostics(case, U: np.ndarray) -> np.ndarray:
     """[K, enstrophy, sum rho, sum rho u, sum rho v, sum rho w, sum rho E, nan-flag]."""
+    from paper_2506_03027_gb300.inputs import MultiBlock, join_states
     lib = _load()
     p = params(case)
+    U = join_states(U) if isinstance(case, MultiBlock) else np.ascontiguousarray(U, dtype=np.float64)
     out = np.zeros(8)
-    lib.or_diagnostics(ctypes.byref(p), _dptr(np.ascontiguousarray(U, dtype=np.float64)), _dptr(out))
+    if lib.or_diagnostics(ctypes.byref(p), _dptr(U), _dptr(out)) != 0:
+        raise ValueError("oracle rejected the case")
     return out
 
 

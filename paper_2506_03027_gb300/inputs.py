@@ -233,3 +233,335 @@ def initial_state(case: Case) -> np.ndarray:
     if case.name.startswith("vortex"):
         return vortex_state(case)
     return tgv_state(case)
+
+
+# ------------------------------------------------------------------ connected multi-block grids
+#
+# A multi-block grid: blocks (each a Case giving its size, split and spacing; the first block's
+# Case also gives the physics and the scheme), optional point coordinates per block, and the six
+# faces of every block.  Face types: periodic (the block wraps onto itself), interface (to face
+# nf of block nb; node-disjoint; rev: the tangential in-plane index runs the other way on the
+# neighbour), wall (no-slip adiabatic; the face's points are wall points), farfield (the given
+# conserved state beyond the face) and outflow (the face values repeated beyond it).  Faces
+# 0..5 = -x, +x, -y, +y, -z, +z; z faces are periodic.
+
+FACE_TYPES = {"periodic": 0, "interface": 1, "wall": 2, "farfield": 3, "outflow": 4}
+
+
+@dataclasses.dataclass
+class Face:
+    type: str = "periodic"
+    nb: int = -1
+    nf: int = -1
+    rev: bool = False
+    state: tuple = (0.0, 0.0, 0.0, 0.0, 0.0)
+    shift: tuple = (0.0, 0.0)        # interface: (x, y) jump added to the neighbour's coordinates
+
+
+@dataclasses.dataclass
+class MultiBlock:
+    blocks: list                     # Case per block
+    faces: list                      # per block: six Face
+    xy: list = None                  # per block: None or (xy [2][ny][nx], shift[4])
+    name: str = "multiblock"
+
+    def __post_init__(self):
+        if self.xy is None:
+            self.xy = [grid_xy(b) for b in self.blocks]
+
+    @property
+    def case(self) -> Case:
+        return self.blocks[0]
+
+    @property
+    def npts(self) -> int:
+        return sum(b.npts for b in self.blocks)
+
+    @property
+    def nsub(self) -> int:
+        return sum(b.nsub for b in self.blocks)
+
+    def replace_all(self, **kw) -> "MultiBlock":
+        """The same grid with every block's Case updated (physics, scheme, algorithm, dt)."""
+        return dataclasses.replace(self, blocks=[b.replace(**kw) for b in self.blocks])
+
+
+def periodic_faces() -> list:
+    return [Face() for _ in range(6)]
+
+
+def split_states(mb: MultiBlock, U: np.ndarray) -> list:
+    """A concatenated state (block after block, [5][nz][ny][nx] each) as a list of block states."""
+    out, o = [], 0
+    for b in mb.blocks:
+        n = NV * b.npts
+        out.append(U[o:o + n].reshape(NV, b.nz, b.ny, b.nx))
+        o += n
+    return out
+
+
+def join_states(states) -> np.ndarray:
+    return np.ascontiguousarray(np.concatenate([np.ascontiguousarray(s, dtype=np.float64).ravel() for s in states]))
+
+
+def split_box_x(case: Case, n0: int, p0: int, p1: int) -> MultiBlock:
+    """The periodic box of `case` cut at x index n0 into two blocks joined by two interfaces
+    (y and z stay periodic); block 0 holds x indices [0, n0) split px = p0, block 1 the rest
+    split px = p1."""
+    b0 = case.replace(nx=n0, px=p0, lx=case.dx * n0)
+    b1 = case.replace(nx=case.nx - n0, px=p1, lx=case.dx * (case.nx - n0))
+    f0, f1 = periodic_faces(), periodic_faces()
+    f0[1] = Face("interface", 1, 0)
+    f0[0] = Face("interface", 1, 1)
+    f1[0] = Face("interface", 0, 1)
+    f1[1] = Face("interface", 0, 0)
+    return MultiBlock([b0, b1], [f0, f1], xy=[None, None], name=case.name + "-split")
+
+
+def rotated_pair(case: Case, n0: int, p0: int, p1: int) -> MultiBlock:
+    """The curvilinear periodic grid of `case` (grid_xy) cut at x index n0 into two blocks, the
+    second stored rotated by 180 degrees in the plane: its point (i', j') is the grid's point
+    (nx - 1 - i', ny - 1 - j').  Both x faces of each block are interfaces with the tangential
+    index reversed (-x to -x, +x to +x; the pair of -x faces closes the periodic x direction and
+    carries its coordinate jump); y faces stay periodic (the rotated block's coordinate jump
+    across its y wrap is -Ly)."""
+    xy, shift = grid_xy(case)
+    nx, ny = case.nx, case.ny
+    n1 = nx - n0
+    xy0 = np.ascontiguousarray(xy[:, :, :n0])
+    # rotated block: columns n0..nx-1 reversed in both indices
+    xy1 = np.ascontiguousarray(xy[:, ::-1, :][:, :, ::-1][:, :, :n1])
+    b0 = case.replace(nx=n0, px=p0, lx=case.dx * n0)
+    b1 = case.replace(nx=n1, px=p1, lx=case.dx * n1)
+    f0, f1 = periodic_faces(), periodic_faces()
+    f0[0] = Face("interface", 1, 0, True, shift=(-shift[0], -shift[1]))
+    f0[1] = Face("interface", 1, 1, True)
+    f1[0] = Face("interface", 0, 0, True, shift=(shift[0], shift[1]))
+    f1[1] = Face("interface", 0, 1, True)
+    s0 = np.array([0.0, 0.0, shift[2], shift[3]])
+    s1 = np.array([0.0, 0.0, -shift[2], -shift[3]])
+    return MultiBlock([b0, b1], [f0, f1], xy=[(xy0, s0), (xy1, s1)], name=case.name + "-rotated")
+
+
+def rotate_state_pair(U: np.ndarray, n0: int):
+    """Block states of rotated_pair from a state of the whole grid: block 1 is the columns
+    n0.. of the 180-degree rotation (momentum components unchanged: they are Cartesian)."""
+    nx = U.shape[-1]
+    U0 = np.ascontiguousarray(U[..., :n0])
+    U1 = np.ascontiguousarray(U[:, :, ::-1, ::-1][..., :nx - n0])
+    return U0, U1
+
+
+def span_pair(case: Case, n0: int, nz1: int, p0: int, p1: int) -> MultiBlock:
+    """The periodic box of `case` cut at x index n0 into two blocks of different spanwise
+    counts: block 0 keeps nz, block 1 has nz1 points over the same span."""
+    m = split_box_x(case, n0, p0, p1)
+    m.blocks[1] = m.blocks[1].replace(nz=nz1)
+    m.name = case.name + "-span"
+    return m
+
+
+def wall_channel(case: Case) -> MultiBlock:
+    """The box of `case` with no-slip adiabatic walls on both y faces (points j = 0 and
+    j = ny - 1 are wall points); x and z periodic."""
+    f = periodic_faces()
+    f[2] = Face("wall")
+    f[3] = Face("wall")
+    return MultiBlock([case], [f], xy=[grid_xy(case)], name=case.name + "-channel")
+
+
+def shear_wave_state(case: Case, eps: float) -> np.ndarray:
+    """rho = 1, T = 1, u = eps sin(pi y / H) with y = j dy and H = (ny - 1) dy, v = w = 0."""
+    H = (case.ny - 1) * case.dy
+    y = case.dy * np.arange(case.ny)
+    u = eps * np.sin(math.pi * y / H)
+    shape = (case.nz, case.ny, case.nx)
+    U = np.broadcast_to(u[None, :, None], shape)
+    rho = np.ones(shape)
+    p = np.full(shape, 1.0 / (case.gamma * case.mach ** 2))
+    return conserved(case, rho, U, np.zeros(shape), np.zeros(shape), p)
+
+
+# ------------------------------------------------------------------ NACA0012 C-grid (12 blocks)
+
+def naca0012_half_thickness(x):
+    """Four-digit NACA thickness distribution, t = 0.12, open trailing edge (y_t(1) = 0.00126)."""
+    x = np.asarray(x, dtype=np.float64)
+    return 5 * 0.12 * (0.2969 * np.sqrt(x) - 0.1260 * x - 0.3516 * x ** 2 + 0.2843 * x ** 3 - 0.1015 * x ** 4)
+
+
+def _geometric_ratio(first: float, total: float, n: int) -> float:
+    """Ratio r with first (r^n - 1)/(r - 1) = total (bisection)."""
+    lo, hi = 1.0 + 1e-12, 4.0
+    for _ in range(200):
+        r = 0.5 * (lo + hi)
+        if first * (r ** n - 1) / (r - 1) > total:
+            hi = r
+        else:
+            lo = r
+    return 0.5 * (lo + hi)
+
+
+@dataclasses.dataclass
+class CGridSpec:
+    wake: int = 96           # points per side along the wake cut
+    aft: int = 160           # points per side on the aft part of the airfoil
+    fore: int = 512          # points per side on the fore part
+    nj_in: int = 192         # wall-normal points of the inner layer
+    nj_out: int = 64         # wall-normal points of the outer layer
+    nz_in: int = 64          # spanwise points of the inner layer
+    nz_out: int = 32         # spanwise points of the outer layer
+    sub: tuple = (64, 64, 32)  # target sub-domain size (x, y, z)
+    radius: float = 5.0      # far-field distance (chords)
+    wake_len: float = 4.0    # wake length downstream of the trailing edge (chords)
+    span: float = 0.25       # spanwise period (chords)
+    alpha_deg: float = 2.0   # angle of attack
+    mach: float = 0.3
+    re: float = 5.0e4
+    perturb: float = 1.0e-3  # amplitude of the seeded velocity perturbation (free-stream units)
+    ramp: float = 0.05       # width of the initial wall-distance ramp of the velocity (chords)
+
+
+def cgrid_reduced() -> CGridSpec:
+    """A small C-grid with the same topology (43 k points, 80 sub-domains)."""
+    return CGridSpec(wake=12, aft=20, fore=32, nj_in=24, nj_out=8, nz_in=12, nz_out=6, sub=(8, 12, 6))
+
+
+def cgrid_plane(spec: CGridSpec):
+    """Point coordinates of the whole C-grid plane, X, Y [nj][ni] with ni = 2 (wake + aft + fore)
+    and nj = nj_in + nj_out.  Index i runs along the C from the lower end of the wake cut, under
+    the airfoil to the leading edge, over it and back along the upper side of the cut; j runs
+    outward.  Row j = 0: on the airfoil the surface points x = (1 - s)^2, y = -+ y_t(x) for
+    s = (m + 1/2)/(aft + fore) (no point at the leading or trailing edge: blocks are
+    node-disjoint); along the cut the lines y = -+ y_t(1), so that the cut spacing 2 y_t(1) equals
+    the first wall-normal spacing.  Row nj - 1: the far field, a C of radius `radius` around
+    (1/2, 0) closed by straight lines to the outflow.  Between them straight lines with a
+    geometric wall-normal stretching."""
+    ns = spec.aft + spec.fore
+    nw = spec.wake
+    s = (np.arange(ns) + 0.5) / ns
+    xa = (1.0 - s) ** 2                           # trailing edge -> leading edge
+    ya = naca0012_half_thickness(xa)
+    te = float(naca0012_half_thickness(1.0))
+    # wake: continues the surface spacing at the trailing edge, geometric growth to wake_len
+    h0 = xa[0] - xa[1]
+    q = _geometric_ratio(h0, spec.wake_len, nw)
+    xw = 1.0 + (1.0 - xa[0]) + h0 * (q ** np.arange(nw) - 1.0) / (q - 1.0)  # nearest the trailing edge first
+    # inner row, along i
+    X0 = np.concatenate([xw[::-1], xa, xa[::-1], xw])
+    Y0 = np.concatenate([np.full(nw, -te), -ya, ya[::-1], np.full(nw, te)])
+    # outer row: straight lines y = -+R over the wake, around the airfoil a path from (1, -R)
+    # along y = -R to (1/2, -R), a half circle of radius R around (1/2, 0), back to (1, R)
+    R = spec.radius
+    L1 = 0.5 + 0.5 * math.pi * R                  # one side's path length
+    phi = s * L1
+    def path(ph):
+        if ph <= 0.5:
+            return 1.0 - ph, -R
+        th = (ph - 0.5) / R                       # angle swept from the bottom of the circle
+        return 0.5 - R * math.sin(th), -R * math.cos(th)
+    lower = np.array([path(ph) for ph in phi])
+    X1 = np.concatenate([xw[::-1], lower[:, 0], lower[::-1, 0], xw])
+    Y1 = np.concatenate([np.full(nw, -R), lower[:, 1], -lower[::-1, 1], np.full(nw, R)])
+    nj = spec.nj_in + spec.nj_out
+    r = _geometric_ratio(2 * te / (R - te), 1.0, nj - 1)
+    sj = (r ** np.arange(nj) - 1.0) / (r ** (nj - 1) - 1.0)
+    X = X0[None, :] + sj[:, None] * (X1 - X0)[None, :]
+    Y = Y0[None, :] + sj[:, None] * (Y1 - Y0)[None, :]
+    return X, Y
+
+
+def naca_cgrid(spec: CGridSpec | None = None, algo: str = "SAA", kmax: int = 2) -> MultiBlock:
+    """The 12-block C-grid around a NACA0012 airfoil: six segments along the C (lower wake,
+    lower aft, lower fore, upper fore, upper aft, upper wake) times two layers (inner: nj_in x
+    nz_in, outer: nj_out x nz_out, so the layers meet with different spanwise counts).  Faces:
+    consecutive segments joined, the wake cut joins the two wake segments (tangential index
+    reversed), the inner airfoil segments' j = 0 faces are no-slip adiabatic walls, the outer
+    layer's far side is a far field at the free stream, the ends of the C are outflows; the span
+    is periodic.  Navier-Stokes, Re_c, M, mu = T^0.76, CD4/AT4/LSERK4 with the filter."""
+    spec = spec or CGridSpec()
+    X, Y = cgrid_plane(spec)
+    segs = [spec.wake, spec.aft, spec.fore, spec.fore, spec.aft, spec.wake]
+    i0 = np.concatenate([[0], np.cumsum(segs)])
+    al = math.radians(spec.alpha_deg)
+    gam = 1.4
+    p_inf = 1.0 / (gam * spec.mach ** 2)
+    free = (1.0, math.cos(al), math.sin(al), 0.0, p_inf / (gam - 1.0) + 0.5)
+    base = Case(name="naca0012", nx=8, ny=8, nz=8, mach=spec.mach, re=spec.re, pr=0.72, viscous=True,
+                visc_law=1, visc_exp=0.76, order=4, algo=algo, at=True, caa_L=4, kmax=kmax, filter=True,
+                lx=1.0, ly=1.0, lz=spec.span)
+    blocks, faces, xy = [], [], []
+    for layer in range(2):
+        j0 = 0 if layer == 0 else spec.nj_in
+        nj = spec.nj_in if layer == 0 else spec.nj_out
+        nz = spec.nz_in if layer == 0 else spec.nz_out
+        for sgi, ni in enumerate(segs):
+            b = layer * 6 + sgi
+            blocks.append(base.replace(nx=ni, ny=nj, nz=nz, px=max(1, ni // spec.sub[0]),
+                                       py=max(1, nj // spec.sub[1]), pz=max(1, nz // spec.sub[2]),
+                                       lx=float(ni), ly=float(nj), lz=spec.span))
+            sl = (slice(j0, j0 + nj), slice(i0[sgi], i0[sgi + 1]))
+            xy.append((np.ascontiguousarray(np.stack([X[sl], Y[sl]])), np.zeros(4)))
+            f = periodic_faces()
+            f[0] = Face("outflow") if sgi == 0 else Face("interface", b - 1, 1)
+            f[1] = Face("outflow") if sgi == 5 else Face("interface", b + 1, 0)
+            if layer == 0:
+                if sgi == 0:
+                    f[2] = Face("interface", 5, 2, True)
+                elif sgi == 5:
+                    f[2] = Face("interface", 0, 2, True)
+                else:
+                    f[2] = Face("wall")
+                f[3] = Face("interface", b + 6, 2)
+            else:
+                f[2] = Face("interface", b - 6, 3)
+                f[3] = Face("farfield", state=free)
+            faces.append(f)
+    return MultiBlock(blocks, faces, xy=xy, name="naca0012-cgrid")
+
+
+def cgrid_state(mb: MultiBlock, spec: CGridSpec | None = None, seed: int = 2506030) -> list:
+    """Initial state per block: rho = 1, T = 1, the free-stream velocity times the ramp
+    1 - exp(-(d / ramp)^2) of the distance d to the airfoil (for a point of an airfoil segment the
+    distance to the surface point at the foot of its grid line, for a wake point the distance to
+    the trailing edge (1, 0)), plus seeded uniform perturbations of amplitude perturb times the
+    ramp on all three velocity components (zero on the wall)."""
+    spec = spec or CGridSpec()
+    X, Y = cgrid_plane(spec)
+    segs = [spec.wake, spec.aft, spec.fore, spec.fore, spec.aft, spec.wake]
+    i0 = np.concatenate([[0], np.cumsum(segs)])
+    al = math.radians(spec.alpha_deg)
+    rng = np.random.default_rng(seed)
+    out = []
+    for b, c in enumerate(mb.blocks):
+        layer, sgi = divmod(b, 6)
+        j0 = 0 if layer == 0 else spec.nj_in
+        sl = (slice(j0, j0 + c.ny), slice(i0[sgi], i0[sgi + 1]))
+        x, y = X[sl], Y[sl]
+        if sgi in (0, 5):
+            dist = np.hypot(x - 1.0, y)
+        else:
+            dist = np.hypot(x - X[0, sl[1]][None, :], y - Y[0, sl[1]][None, :])
+        g = 1.0 - np.exp(-(dist / spec.ramp) ** 2)
+        shape = (c.nz, c.ny, c.nx)
+        pert = spec.perturb * (2.0 * rng.random((3,) + shape) - 1.0) * g[None, None]
+        u = math.cos(al) * g[None] + pert[0]
+        v = math.sin(al) * g[None] + pert[1]
+        w = pert[2]
+        rho = np.ones(shape)
+        p = np.full(shape, 1.0 / (c.gamma * c.mach ** 2))
+        U = conserved(c, rho, np.broadcast_to(u, shape), np.broadcast_to(v, shape), w, p)
+        out.append(U)
+    return out
+
+
+def cgrid_dt(mb: MultiBlock, cfl: float = 0.5) -> float:
+    """CFL time step: cfl times the smallest in-plane point spacing (or the spanwise spacing)
+    over the largest free-stream |u| + c = 1 + 1/M."""
+    h = min(b.dz for b in mb.blocks)
+    for (xy, _), b in zip(mb.xy, mb.blocks):
+        X, Y = xy
+        h = min(h, float(np.hypot(np.diff(X, axis=1), np.diff(Y, axis=1)).min()),
+                float(np.hypot(np.diff(X, axis=0), np.diff(Y, axis=0)).min()))
+    c = mb.case
+    return cfl * h / (1.0 + 1.0 / c.mach)
