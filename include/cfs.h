@@ -102,13 +102,41 @@ cfs_status cfs_set_block_grid(cfs_ctx* ctx, int block, const double* xy, const d
  * Euler, r = 2 for CD4 and 1 for CD2; 5 with the filter).  EINVAL otherwise. */
 cfs_status cfs_split_block(cfs_ctx* ctx, int block, int pi, int pj, int pk);
 
-/* Connect face faceA of blockA to faceB of blockB (faces 0..5 = -i,+i,-j,+j,-k,+k).
- * This version supports only the periodic self-connection (blockA == blockB, opposite faces,
- * orientation 0), which is also the default; anything else returns EINVAL. */
+/* Connect face faceA of blockA to faceB of blockB (faces 0..5 = -i,+i,-j,+j,-k,+k) -- the
+ * block interfaces of a multi-block grid such as the paper's airfoil C-grid (Sec. 5.3), whose
+ * topology the paper does not print.  Every face is periodic (self-connected) until connected or
+ * bounded.  The same block and opposite faces with orientation 0 restore the periodic default.
+ * Otherwise both faces must be x or y faces (blocks are extruded and periodic in z); the blocks
+ * are node-disjoint: the first point beyond faceA is blockB's first point inside faceB.
+ * orientation 0: the tangential in-plane index runs the same way on both sides; 1: reversed
+ * (a C-grid's wake cut joins the -j faces of its two wake blocks this way).  The tangential point
+ * counts must match (checked at cfs_finalize); spanwise counts may differ: a point then takes the
+ * neighbour's values at its own spanwise position by four-point Lagrange interpolation.
+ * Curvilinear blocks join only curvilinear blocks; two Cartesian blocks only opposite faces of
+ * one axis, unreversed.  Halo values across an interface are the neighbouring PE's values, seen
+ * with the face's delay (Alg. 2-3).  ESTATE after cfs_finalize, EINVAL on a bad argument. */
 cfs_status cfs_connect(cfs_ctx* ctx, int blockA, int faceA, int blockB, int faceB, int orientation);
 
-/* Physical boundary condition on a face (wall, far field, inflow).  Not supported in this
- * version: every face is periodic.  Returns EINVAL. */
+/* Coordinate jump (x, y) added to the neighbour's point coordinates when the grid of a
+ * curvilinear block is continued across interface `face` (nonzero where an interface closes a
+ * periodic direction).  Call after cfs_connect; EINVAL if the face is not an interface. */
+cfs_status cfs_set_face_shift(cfs_ctx* ctx, int block, int face, const double* shift);
+
+/* Physical boundary condition on x or y face `face` of `block`:
+ *   CFS_BC_WALL      no-slip adiabatic wall: the points on the face are wall points, whose
+ *                    momentum is held at zero; beyond the face the state is mirrored about it
+ *                    with the momentum negated (data unused);
+ *   CFS_BC_FARFIELD  the conserved state data[5] (host, copied) beyond the face;
+ *   CFS_BC_OUTFLOW   the face values repeated beyond it (data unused);
+ *   CFS_BC_PERIODIC  the face and its opposite face periodic again.
+ * These halo closures are readings: the paper does not print its boundary treatment.  Beyond a
+ * physical face the grid of a curvilinear block is reflected through the boundary point.  A halo
+ * source reached by a wall mirror or an outflow copy inside the same sub-domain is the PE's own
+ * current value.  Before cfs_finalize (ESTATE after); EINVAL on a bad argument. */
+#define CFS_BC_PERIODIC 0
+#define CFS_BC_WALL 1
+#define CFS_BC_FARFIELD 2
+#define CFS_BC_OUTFLOW 3
 cfs_status cfs_set_bc(cfs_ctx* ctx, int block, int face, int type, const double* data);
 
 /* Allocate device memory for the state ring, stage buffers and scratch, and build the
@@ -162,7 +190,9 @@ cfs_status cfs_set_graph(cfs_ctx* ctx, int on);
 /* Diagnostics of the current state U^n over all blocks (synchronises): out[8] = {K, enstrophy,
  * sum rho, sum rho u, sum rho v, sum rho w, sum rho E, non-finite flag}, K and enstrophy point averages
  * with rho_0 = 1 (Sec. 5.2), vorticity by the scheme's central difference, sums weighted by the
- * cell volume.  Returns ENAN (and fills out) when the state holds a non-finite value. */
+ * cell volume.  The enstrophy average covers the points whose difference stencils stay inside their
+ * block or cross only periodic faces.  Returns ENAN (and fills out) when the state holds a
+ * non-finite value. */
 cfs_status cfs_diagnostics(cfs_ctx* ctx, double* out);
 
 /* Checkpoint / resume of the ring of delayed levels: R = max_delay + C + 1 full states,

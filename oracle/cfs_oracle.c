@@ -1311,6 +1311,10 @@ static int ring_depth(const or_params* p) {
 static void diag_topo(const topo_t* T, const double* U, double* out) {
   double ke = 0, ens = 0, vol = 0, vole = 0, tot[5] = {0, 0, 0, 0, 0};
   int bad = 0;
+  /* averaging weights: cell volumes in units of the first Cartesian block's cell */
+  double dVref = 1.0;
+  for (int b = T->nb - 1; b >= 0; --b)
+    if (!T->M[b]) dVref = T->pb[b].dx * T->pb[b].dy * (T->pb[b].nz > 1 ? T->pb[b].dz : 1.0);
   for (int b = 0; b < T->nb; ++b) {
     const or_params* p = &T->pb[b];
     const or_block* B = &T->b[b];
@@ -1332,7 +1336,7 @@ static void diag_topo(const topo_t* T, const double* U, double* out) {
             if (!isfinite(x)) bad = 1;
             tot[c] += x * dV;
           }
-          const double wv = curv ? dV : 1.0; /* Cartesian: plain point average */
+          const double wv = dV / dVref; /* volume-weighted averages (a point average on one uniform block) */
           vol += wv;
           ke += 0.5 * rho * (u * u + v * v + w * w) * wv;
           int inner = 1;

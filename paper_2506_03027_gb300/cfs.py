@@ -77,6 +77,7 @@ def load() -> ctypes.CDLL:
             "cfs_set_block_grid": ([vp, ip, dp, dp], ip),
             "cfs_connect": ([vp, ip, ip, ip, ip, ip], ip),
             "cfs_set_bc": ([vp, ip, ip, ip, dp], ip),
+            "cfs_set_face_shift": ([vp, ip, ip, dp], ip),
             "cfs_finalize": ([vp, ip], ip),
             "cfs_set_schedule": ([vp, ip, ip, ip, ll, ctypes.POINTER(ctypes.c_int8)], ip),
             "cfs_set_state": ([vp, ip, vp, ip], ip),
@@ -159,8 +160,24 @@ def cfs_connect(ctx, block_a: int, face_a: int, block_b: int, face_b: int, orien
     _check(ctx, load().cfs_connect(ctx, block_a, face_a, block_b, face_b, orientation))
 
 
+BC_PERIODIC, BC_WALL, BC_FARFIELD, BC_OUTFLOW = 0, 1, 2, 3
+
+
 def cfs_set_bc(ctx, block: int, face: int, bc_type: int, data=None):
-    _check(ctx, load().cfs_set_bc(ctx, block, face, bc_type, None))
+    """Physical boundary on a block face: BC_WALL, BC_FARFIELD (data = 5 conserved values),
+    BC_OUTFLOW, or BC_PERIODIC (back to the periodic default)."""
+    if data is None:
+        _check(ctx, load().cfs_set_bc(ctx, block, face, bc_type, None))
+    else:
+        a = np.ascontiguousarray(data, dtype=np.float64)
+        assert a.size == 5
+        _check(ctx, load().cfs_set_bc(ctx, block, face, bc_type, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+
+def cfs_set_face_shift(ctx, block: int, face: int, shift):
+    a = np.ascontiguousarray(shift, dtype=np.float64)
+    assert a.size == 2
+    _check(ctx, load().cfs_set_face_shift(ctx, block, face, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
 
 
 def cfs_finalize(ctx, max_delay: int):
@@ -363,14 +380,20 @@ class TorchAllocator:
 
 
 class Solver:
-    """A context on the current CUDA device and stream for one periodic block (``case``) or for a
+    """A context on the current CUDA device and stream for one periodic block (``case``), for a
     batch of independent periodic blocks (``blocks``: cases sharing the physics and scheme of the
-    first, each with its own size, spacing and split)."""
+    first, each with its own size, spacing and split), or for a connected multi-block grid
+    (``case`` an ``inputs.MultiBlock``: blocks, their coordinates and their faces)."""
 
     def __init__(self, case, max_delay: int | None = None, precision: int = 0, stream=None,
                  use_torch_allocator: bool = True, blocks=None, tiles=None, graph: bool = False):
         import torch
+        from .inputs import MultiBlock
         self.torch = torch
+        mb = case if isinstance(case, MultiBlock) else None
+        if mb is not None:
+            blocks = mb.blocks
+            case = mb.case
         self.blocks = list(blocks) if blocks is not None else [case]
         case = self.blocks[0]
         self.case = case
@@ -381,12 +404,24 @@ class Solver:
         if use_torch_allocator:
             self.alloc = TorchAllocator(self.device)
             cfs_set_allocator(self.ctx, self.alloc.alloc_cb, self.alloc.free_cb)
-        for b in self.blocks:
+        for i, b in enumerate(self.blocks):
             bid = cfs_add_block(self.ctx, b.nx, b.ny, b.nz, (b.dx, b.dy, b.dz))
             cfs_split_block(self.ctx, bid, b.px, b.py, b.pz)
-            gxy = grid_xy(b)
+            gxy = grid_xy(b) if mb is None else mb.xy[i]
             if gxy is not None:
                 cfs_set_block_grid(self.ctx, bid, gxy[0], gxy[1])
+        if mb is not None:
+            bc = {"wall": BC_WALL, "farfield": BC_FARFIELD, "outflow": BC_OUTFLOW}
+            for i, faces in enumerate(mb.faces):
+                for f, F in enumerate(faces):
+                    if F.type == "interface" and (i, f) < (F.nb, F.nf):
+                        cfs_connect(self.ctx, i, f, F.nb, F.nf, int(F.rev))
+                    elif F.type in bc:
+                        cfs_set_bc(self.ctx, i, f, bc[F.type], F.state if F.type == "farfield" else None)
+            for i, faces in enumerate(mb.faces):
+                for f, F in enumerate(faces):
+                    if F.type == "interface" and any(F.shift):
+                        cfs_set_face_shift(self.ctx, i, f, F.shift)
         if tiles is not None:
             cfs_set_tiles(self.ctx, *tiles)
         if max_delay is None:
@@ -429,6 +464,14 @@ class Solver:
         else:
             cfs_get_state(self.ctx, block, out.data_ptr(), DEVICE)
         return out
+
+    def set_states(self, states):
+        """Every block's state, in block order."""
+        for i, U in enumerate(states):
+            self.set_state(U, block=i)
+
+    def get_states(self) -> list:
+        return [self.get_state(block=i) for i in range(len(self.blocks))]
 
     def step(self, n: int = 1):
         cfs_step(self.ctx, n)

@@ -31,7 +31,9 @@ struct Block {
   // curvilinear grid (cfs_set_block_grid): x, y of every (i, j), and the periodic coordinate jumps
   std::vector<double> xy;
   double shift[4] = {0, 0, 0, 0};
-  long long mbase = -1;   // offset of its metric field in d_metric
+  long long mbase = -1;   // offset of its metric plane in d_metric
+  cfs::FaceSpec face[6];  // periodic unless connected (cfs_connect) or bounded (cfs_set_bc)
+  long long ebase = -1;   // offset of its gather map in d_emap (blocks with a non-periodic face)
 };
 
 struct cfs_ctx {
@@ -92,7 +94,10 @@ struct cfs_ctx {
   int fused_zc = 32;
   int fused_fy = 16;
   int fused_grid = 0;
-  double* d_metric = nullptr;  // metric fields of the curvilinear blocks
+  double* d_metric = nullptr;  // metric planes of the curvilinear blocks
+  int* d_emap = nullptr;       // gather maps of the blocks with non-periodic faces
+  cfs::GatherEntry* d_gent = nullptr;
+  bool all_periodic = true;
   double volume = 0.0;         // total cell volume (diagnostics averages)
   int nwork = 0;
   int* d_work = nullptr;
@@ -279,15 +284,66 @@ cfs_status cfs_split_block(cfs_ctx* c, int block, int pi, int pj, int pk) {
 
 cfs_status cfs_connect(cfs_ctx* c, int blockA, int faceA, int blockB, int faceB, int orientation) {
   if (!c) return CFS_EINVAL;
-  if (blockA == blockB && blockA >= 0 && blockA < (int)c->blocks.size() && orientation == 0 && faceA >= 0 &&
-      faceA < 6 && faceB == (faceA ^ 1))
-    return CFS_OK;  // periodic self-connection: the default
-  return fail(c, CFS_EINVAL, "only periodic self-connections are supported in this version");
+  if (c->finalized) return fail(c, CFS_ESTATE, "connect before cfs_finalize");
+  const int nb = (int)c->blocks.size();
+  if (blockA < 0 || blockA >= nb || blockB < 0 || blockB >= nb) return fail(c, CFS_EINVAL, "unknown block");
+  if (faceA < 0 || faceA > 5 || faceB < 0 || faceB > 5) return fail(c, CFS_EINVAL, "face must be 0..5");
+  if (orientation != 0 && orientation != 1) return fail(c, CFS_EINVAL, "orientation must be 0 or 1");
+  if (blockA == blockB && faceB == (faceA ^ 1) && orientation == 0) {  // periodic self-connection
+    c->blocks[blockA].face[faceA] = cfs::FaceSpec{};
+    c->blocks[blockA].face[faceB] = cfs::FaceSpec{};
+    return CFS_OK;
+  }
+  if (faceA > 3 || faceB > 3) return fail(c, CFS_EINVAL, "interfaces join x or y faces (z is periodic)");
+  if (blockA == blockB && faceA == faceB) return fail(c, CFS_EINVAL, "a face cannot join itself");
+  cfs::FaceSpec fa, fb;
+  fa.type = fb.type = cfs::FACE_INTERFACE;
+  fa.nb = blockB; fa.nf = faceB; fa.rev = orientation;
+  fb.nb = blockA; fb.nf = faceA; fb.rev = orientation;
+  c->blocks[blockA].face[faceA] = fa;
+  c->blocks[blockB].face[faceB] = fb;
+  return CFS_OK;
 }
 
-cfs_status cfs_set_bc(cfs_ctx* c, int, int, int, const double*) {
+cfs_status cfs_set_face_shift(cfs_ctx* c, int block, int face, const double* shift) {
+  if (!c || !shift) return CFS_EINVAL;
+  if (c->finalized) return fail(c, CFS_ESTATE, "face shift before cfs_finalize");
+  if (block < 0 || block >= (int)c->blocks.size() || face < 0 || face > 3) return fail(c, CFS_EINVAL, "unknown block or face");
+  cfs::FaceSpec& f = c->blocks[block].face[face];
+  if (f.type != cfs::FACE_INTERFACE) return fail(c, CFS_EINVAL, "the face is not an interface");
+  if (!std::isfinite(shift[0]) || !std::isfinite(shift[1])) return fail(c, CFS_EINVAL, "non-finite shift");
+  f.shift[0] = shift[0];
+  f.shift[1] = shift[1];
+  return CFS_OK;
+}
+
+cfs_status cfs_set_bc(cfs_ctx* c, int block, int face, int type, const double* data) {
   if (!c) return CFS_EINVAL;
-  return fail(c, CFS_EINVAL, "physical boundary conditions are not supported in this version");
+  if (c->finalized) return fail(c, CFS_ESTATE, "boundary conditions before cfs_finalize");
+  if (block < 0 || block >= (int)c->blocks.size()) return fail(c, CFS_EINVAL, "unknown block");
+  if (face < 0 || face > 3) return fail(c, CFS_EINVAL, "boundaries lie on x or y faces (z is periodic)");
+  cfs::FaceSpec f;
+  switch (type) {
+    case CFS_BC_PERIODIC:
+      c->blocks[block].face[face] = f;
+      c->blocks[block].face[face ^ 1] = f;
+      return CFS_OK;
+    case CFS_BC_WALL: f.type = cfs::FACE_WALL; break;
+    case CFS_BC_OUTFLOW: f.type = cfs::FACE_OUTFLOW; break;
+    case CFS_BC_FARFIELD:
+      if (!data) return fail(c, CFS_EINVAL, "far field needs its conserved state");
+      for (int v = 0; v < 5; ++v) {
+        if (!std::isfinite(data[v])) return fail(c, CFS_EINVAL, "non-finite far-field state");
+        f.state[v] = data[v];
+      }
+      if (!(data[0] > 0.0)) return fail(c, CFS_EINVAL, "far-field density must be positive");
+      f.type = cfs::FACE_FARFIELD;
+      break;
+    default:
+      return fail(c, CFS_EINVAL, "unknown boundary type");
+  }
+  c->blocks[block].face[face] = f;
+  return CFS_OK;
 }
 
 cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
@@ -298,14 +354,32 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   const int need = c->p.filter ? (c->G > 5 ? c->G : 5) : c->G;
   // sub-domain table: blocks in order, x fastest within a block
   int nsub = 0;
-  long long Ntot = 0;
+  long long Ntot = 0, mtot = 0;
   for (Block& b : c->blocks) {
     b.sid0 = nsub;
     b.base = 5 * Ntot;
-    b.mbase = b.xy.empty() ? -1 : (long long)NMETRIC * Ntot;
+    b.mbase = b.xy.empty() ? -1 : mtot;
+    if (!b.xy.empty()) mtot += (long long)NMETRIC * (b.nx + 2 * c->G) * (b.ny + 2 * c->G);
     nsub += b.P[0] * b.P[1] * b.P[2];
     Ntot += b.N;
   }
+  // block topology: faces, gather maps of the blocks with a non-periodic face
+  std::vector<cfs::TopoBlock> topo(c->blocks.size());
+  c->all_periodic = true;
+  for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
+    const Block& b = c->blocks[bi];
+    cfs::TopoBlock& t = topo[bi];
+    t.n[0] = b.nx; t.n[1] = b.ny; t.n[2] = b.nz;
+    for (int a = 0; a < 3; ++a) t.P[a] = b.P[a];
+    t.sid0 = b.sid0;
+    t.base = b.base;
+    t.N = b.N;
+    t.xy = b.xy.empty() ? nullptr : b.xy.data();
+    for (int k = 0; k < 4; ++k) t.shift[k] = b.shift[k];
+    for (int f = 0; f < 6; ++f) t.face[f] = b.face[f];
+    c->all_periodic = c->all_periodic && cfs::topo_periodic(t);
+  }
+  if (const char* why = cfs::topo_check(topo.data(), (int)topo.size())) return fail(c, CFS_EINVAL, why);
   c->subs.resize(nsub);
   long long pbase = 0;
   c->max_pad = c->max_own = c->max_flux = 0;
@@ -330,6 +404,23 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
           d.bN = b.N;
           d.bbase = b.base;
           d.mbase = b.mbase;
+          d.mx = b.nx + 2 * c->G;
+          d.mpl = (long long)(b.nx + 2 * c->G) * (b.ny + 2 * c->G);
+          d.phys = d.wall = 0;
+          {
+            const int lo[3] = {d.ox, d.oy, d.oz}, hi[3] = {d.ox + d.sx, d.oy + d.sy, d.oz + d.sz};
+            const int n3[3] = {b.nx, b.ny, b.nz};
+            for (int a = 0; a < 3; ++a)
+              for (int side = 0; side < 2; ++side) {
+                const int f = 2 * a + side;
+                const bool on = side == 0 ? lo[a] == 0 : hi[a] == n3[a];
+                if (on && b.face[f].type >= cfs::FACE_WALL) d.phys |= 1 << f;
+                if (on && b.face[f].type == cfs::FACE_WALL) d.wall |= 1 << f;
+              }
+          }
+          d.ebase = -1;
+          d.gmx = b.nx + 2 * need;
+          d.gmy = b.ny + 2 * need;
           for (int a = 0; a < 3; ++a) {  // CD coefficients of Eq. 2 (alpha = 0) for the block's spacing
             const double h = b.mbase >= 0 ? 1.0 : b.h[a];  // curvilinear: index space
             d.c1[a] = (a_cd / 2.0) / h;
@@ -381,25 +472,72 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
     if (b.mbase < 0) c->volume += (double)b.N * b.h[0] * b.h[1] * (c->ndim == 3 ? b.h[2] : 1.0);
   }
   if (curv) {
-    c->d_metric = (double*)dev_alloc(c, sizeof(double) * NMETRIC * N);
+    c->d_metric = (double*)dev_alloc(c, sizeof(double) * mtot);
     if (!c->d_metric) return fail(c, CFS_ENOMEM, "device allocation failed");
     std::vector<double> M;
-    for (const Block& b : c->blocks) {
+    for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
+      const Block& b = c->blocks[bi];
       if (b.mbase < 0) continue;
-      M.assign((size_t)NMETRIC * b.N, 0.0);
-      cfs::grid_metrics(b.nx, b.ny, b.nz, b.h[2], c->p.order, b.xy.data(), b.shift, M.data());
-      for (long long q = 0; q < b.N; ++q) {
-        if (!(M[5 * b.N + q] > 0.0)) return fail(c, CFS_EINVAL, "curvilinear grid with a non-positive cell volume");
-        c->volume += M[5 * b.N + q];
-      }
+      const int mx = b.nx + 2 * c->G;
+      const long long pl = (long long)mx * (b.ny + 2 * c->G);
+      M.assign((size_t)NMETRIC * pl, 0.0);
+      if (!cfs::metric_plane(topo.data(), (int)topo.size(), (int)bi, c->G, c->r, c->p.order, b.h[2], c->ndim, M.data()))
+        return fail(c, CFS_EINVAL, "curvilinear grid with a non-positive cell volume, or not continued across a face");
+      double vb = 0.0;
+      for (int j = 0; j < b.ny; ++j)
+        for (int i = 0; i < b.nx; ++i) vb += M[5 * pl + (i + c->G) + (long long)mx * (j + c->G)];
+      c->volume += vb * b.nz;
       CUDA_TRY(c, cudaMemcpy(c->d_metric + b.mbase, M.data(), sizeof(double) * M.size(), cudaMemcpyHostToDevice),
                "upload metrics");
     }
   }
   g.metric = c->d_metric;
-  c->fused = c->p.precision == 1 && c->ndim == 3 && c->p.viscous && c->p.order == 4 && !curv;
+  // gather maps: every point of a non-periodic block's (x, y) range extended by `need` (faces to
+  // that depth, corners to r x r), all z; entries for the points outside the block
+  g.GE = need;
+  g.emap = nullptr;
+  g.gent = nullptr;
+  if (!c->all_periodic) {
+    std::vector<int> emap;
+    std::vector<cfs::GatherEntry> ent;
+    for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
+      Block& b = c->blocks[bi];
+      if (cfs::topo_periodic(topo[bi])) continue;
+      b.ebase = (long long)emap.size();
+      const int gx = b.nx + 2 * need, gy = b.ny + 2 * need;
+      for (int k = 0; k < b.nz; ++k)
+        for (int j = -need; j < b.ny + need; ++j)
+          for (int i = -need; i < b.nx + need; ++i) {
+            const int di = i < 0 ? -i : (i >= b.nx ? i - b.nx + 1 : 0);
+            const int dj = j < 0 ? -j : (j >= b.ny ? j - b.ny + 1 : 0);
+            if ((di == 0 && dj == 0) || (di && dj && (di > c->r || dj > c->r))) {
+              emap.push_back(-1);
+              continue;
+            }
+            cfs::GatherEntry e;
+            if (!cfs::gather_entry(topo.data(), (int)topo.size(), (int)bi, i, j, k, &e))
+              return fail(c, CFS_EINVAL, "a halo point beyond a block face does not resolve (more than 4 sources, "
+                                         "or a face sequence that does not end inside a block)");
+            if (ent.size() >= (size_t)INT32_MAX) return fail(c, CFS_EINVAL, "too many gather entries");
+            emap.push_back((int)ent.size());
+            ent.push_back(e);
+          }
+      (void)gx; (void)gy;
+    }
+    c->d_emap = (int*)dev_alloc(c, sizeof(int) * emap.size());
+    c->d_gent = (cfs::GatherEntry*)dev_alloc(c, sizeof(cfs::GatherEntry) * ent.size());
+    if (!c->d_emap || !c->d_gent) return fail(c, CFS_ENOMEM, "device allocation failed");
+    CUDA_TRY(c, cudaMemcpy(c->d_emap, emap.data(), sizeof(int) * emap.size(), cudaMemcpyHostToDevice), "upload gather map");
+    CUDA_TRY(c, cudaMemcpy(c->d_gent, ent.data(), sizeof(cfs::GatherEntry) * ent.size(), cudaMemcpyHostToDevice),
+             "upload gather entries");
+    g.emap = c->d_emap;
+    g.gent = c->d_gent;
+    for (const Block& b : c->blocks)
+      for (int q = 0; q < b.P[0] * b.P[1] * b.P[2]; ++q) c->subs[b.sid0 + q].ebase = b.ebase;
+  }
+  c->fused = c->p.precision == 1 && c->ndim == 3 && c->p.viscous && c->p.order == 4 && !curv && c->all_periodic;
   c->fblock_n = 0;
-  if (c->p.precision == 1 && c->p.filter && c->ndim == 3 && !curv && nsub > 0) {
+  if (c->p.precision == 1 && c->p.filter && c->ndim == 3 && !curv && c->all_periodic && nsub > 0) {
     const int n0 = c->subs[0].sx;
     bool cubic = cfs::filter_block_supported(n0);
     for (const SubDev& d : c->subs) cubic = cubic && d.sx == n0 && d.sy == n0 && d.sz == n0;
@@ -453,7 +591,7 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
     return fail(c, CFS_EINVAL, "filter: a sub-domain is too long along an axis for the shared-memory line tiles "
                                "(at most about 700 points)");
   c->diag_blocks = 2 * 152;
-  c->d_partial = (double*)dev_alloc(c, sizeof(double) * 8 * c->diag_blocks * c->blocks.size());
+  c->d_partial = (double*)dev_alloc(c, sizeof(double) * DIAG_NQ * c->diag_blocks * c->blocks.size());
   c->d_thomas = (double*)dev_alloc(c, sizeof(double) * (size_t)(c->Lmax + 1) * 2 * c->Lmax);
   for (void* q : c->owned)
     if (!q) return fail(c, CFS_ENOMEM, "device allocation failed");
@@ -717,6 +855,14 @@ static cfs_status enqueue_step(cfs_ctx* c, long long n, bool graph) {
         f.Uin = src; f.Uout = dst; f.ring = c->ring;
         f.in_ring = in_ring; f.out_ring = out_ring;
         f.nx = b.nx; f.ny = b.ny; f.nz = b.nz; f.bN = b.N; f.bbase = b.base; f.sid0 = b.sid0;
+        f.ebase = b.ebase;
+        f.gmx = b.nx + 2 * c->geo.GE;
+        f.gmy = b.ny + 2 * c->geo.GE;
+        f.wall = f.phys = 0;
+        for (int q = 0; q < 6; ++q) {
+          if (b.face[q].type >= cfs::FACE_WALL) f.phys |= 1 << q;
+          if (b.face[q].type == cfs::FACE_WALL) f.wall |= 1 << q;
+        }
         for (int a = 0; a < 3; ++a) {
           f.owner[a] = b.d_owner[a]; f.axis_off[a] = b.d_axis_off[a]; f.axis_len[a] = b.d_axis_len[a];
           f.P[a] = b.P[a];
@@ -859,6 +1005,13 @@ cfs_status cfs_diagnostics(cfs_ctx* c, double* out) {
     }
     db.dV = b.h[0] * b.h[1] * (c->ndim == 3 ? b.h[2] : 1.0);
     db.M = b.mbase >= 0 ? c->d_metric + b.mbase : nullptr;
+    db.mx = b.nx + 2 * c->G;
+    db.G = c->G;
+    db.mpl = (long long)db.mx * (b.ny + 2 * c->G);
+    db.rs = c->r;
+    db.nonper = 0;
+    for (int f = 0; f < 6; ++f)
+      if (b.face[f].type != cfs::FACE_PERIODIC) db.nonper |= 1 << f;
     if (db.M)
       for (int a = 0; a < 3; ++a) {  // index-space coefficients
         db.c1[a] = a_cd / 2.0;
@@ -974,6 +1127,7 @@ cfs_status cfs_set_halo_model(cfs_ctx* c, const float* params, const double* sca
     return CFS_OK;
   }
   if (!params || !scales) return fail(c, CFS_EINVAL, "model parameters and scales required");
+  if (!c->all_periodic) return fail(c, CFS_EINVAL, "the halo model needs blocks periodic on every face");
   if (c->max_delay > MLP_KMAX) return fail(c, CFS_EINVAL, "the halo model covers delays 0..4: max_delay must be <= 4");
   if (c->G < MLP_HDEPTH) return fail(c, CFS_EINVAL, "the halo model needs a face halo of depth 4 (viscous CD4)");
   for (int v = 0; v < 15; ++v)

@@ -37,10 +37,38 @@ struct SubDev {
   long long bN;       // block points
   long long bbase;    // offset of the block's state [5][bnz][bny][bnx] in a state array (doubles)
   double c1[3], c2[3];  // CD coefficients of the block's spacing: c1 = (a/2)/h, c2 = (b/4)/h
-  // curvilinear block: offset of its metric field in Geometry::metric (component stride bN),
-  // -1 for a uniform Cartesian block; c1, c2 are then the index-space coefficients (h = 1)
+  // curvilinear block: offset of its metric plane in Geometry::metric, -1 for a uniform Cartesian
+  // block (c1, c2 are then the index-space coefficients, h = 1).  The plane covers the block's
+  // (x, y) points extended by G on every side, row length mx, component stride mpl; it is the
+  // same for every z (blocks are extruded)
   long long mbase;
+  int mx;
+  long long mpl;
+  // faces of the sub-domain on a physical boundary of the block (bit f, faces -x, +x, -y, +y,
+  // -z, +z) and, among them, the no-slip walls
+  int phys, wall;
+  // block with a non-periodic face: offset of its gather map in Geometry::emap (an entry index,
+  // or -1, for every point of the block's (x, y) range extended by GE, all z: row length gmx,
+  // plane gmx * gmy); -1 for a block periodic on every face
+  long long ebase;
+  int gmx, gmy;
 };
+
+// Sources of the state at a point beyond a non-periodic block face (an interface, a wall mirror,
+// an outflow copy, a far field): U_v = cst_v + sum_t w_t s_v(t) U_v(source t), s_v = -1 for the
+// momentum of a mirrored source.  A source is the receiving sub-domain's own value when it was
+// reached without crossing a periodic wrap or an interface and lies in that sub-domain.
+struct GatherEntry {
+  long long off[4];  // source: state offset of its block plus its point index (component v at + v bN)
+  double w[4];
+  double cst[5];
+  int bN[4];         // source block's points
+  int sid[4];        // sub-domain owning the source
+  int flags[4];      // bit 0: momentum negated; bit 1: crossed a periodic wrap or an interface
+  int nt;
+  int pad;
+};
+#define GATHER_MAXT 4
 
 // Scalars every kernel needs; passed by value.
 struct Geometry {
@@ -52,9 +80,13 @@ struct Geometry {
   int ndim;              // 2 or 3
   int viscous;
   long long Ptot;        // total padded points (scratch length per component)
-  // metric fields of the curvilinear blocks, [NMETRIC][block points] per block (device), or null:
+  // metric planes of the curvilinear blocks, [NMETRIC][mpl] per block (device), or null:
   // xi^_x, xi^_y, eta^_x, eta^_y, zeta^_z (= J^-1 d(xi,eta,zeta)/dx of App. A), J^-1, J
   const double* metric;
+  // gather maps and entries of the blocks with non-periodic faces (device), or null
+  const int* emap;
+  const GatherEntry* gent;
+  int GE;                // depth of the gather maps beyond the block faces
 };
 #define NMETRIC 7
 
@@ -100,7 +132,31 @@ bool buffer_dudt_weights(int order, int e, int k, long double* d);
 int at_weight_table(int order, int kmax, double* W);
 int filter_extrap_table(int order, int kmax, double* Wf);
 bool pade10_coeffs(double alpha, double* a);
-void grid_metrics(int nx, int ny, int nz, double dz, int order, const double* xy, const double* shift, double* M);
+// Block topology (host): faces of the connected multi-block grid.
+enum { FACE_PERIODIC = 0, FACE_INTERFACE = 1, FACE_WALL = 2, FACE_FARFIELD = 3, FACE_OUTFLOW = 4 };
+struct FaceSpec {
+  int type = FACE_PERIODIC;
+  int nb = -1, nf = -1, rev = 0;
+  double state[5] = {0, 0, 0, 0, 0};
+  double shift[2] = {0, 0};
+};
+struct TopoBlock {
+  int n[3];
+  int P[3];
+  int sid0;
+  long long base, N;
+  const double* xy;  // curvilinear: [2][ny][nx], or null
+  double shift[4];
+  FaceSpec face[6];
+};
+// topology.cpp
+const char* topo_check(const TopoBlock* B, int nb);  // null when valid, else the reason
+bool topo_periodic(const TopoBlock& b);
+// Gather entry of point (i, j, k) of block b's index space; false if it does not resolve.
+bool gather_entry(const TopoBlock* B, int nb, int b, int i, int j, int k, GatherEntry* e);
+// Metric plane [NMETRIC][(nx + 2G)(ny + 2G)] of curvilinear block b; false if the grid does not
+// continue far enough across a face, or a cell volume is not positive.
+bool metric_plane(const TopoBlock* B, int nb, int b, int G, int r, int order, double dz, int ndim, double* M);
 
 // kernel launchers (kernels.cu); all return a cudaError_t cast to int
 
@@ -136,6 +192,10 @@ int launch_stage(const Geometry& g, const Physics& ph, const StepSched& sc, cons
                  int precision, void* stream, long long* launches, const Timer* tm);
 
 struct FilterLaunch {
+  long long ebase;         // the block's gather map (SubDev::ebase), or -1
+  int gmx, gmy;
+  int wall;                // bit f: face f of the block is a no-slip wall (momentum held at zero)
+  int phys;                // bit f: face f of the block is a physical boundary
   const double* Uin;
   double* Uout;
   const double* ring;
@@ -230,8 +290,13 @@ struct DiagBlock {
   int nx, ny, nz;
   long long bN, bbase;
   double c1[3], c2[3], dV;
-  const double* M;  // the block's metric field (curvilinear), or null
+  const double* M;  // the block's metric plane (curvilinear), or null
+  int mx, G;        // its row length and extension
+  long long mpl;    // its component stride
+  int nonper;       // bit f: face f is not periodic (no enstrophy within the stencil radius of it)
+  int rs;           // stencil radius
 };
+#define DIAG_NQ 9   // per block row: K, enstrophy, 5 totals, non-finite flag, enstrophy volume
 int launch_diagnostics_block(const Geometry& g, const DiagBlock& b, const double* U, double* partial, int row0,
                              int nblocks, void* stream);
 int launch_diagnostics_final(const double* partial, int nrows, double* out, double volume, void* stream);

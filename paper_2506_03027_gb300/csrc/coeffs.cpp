@@ -156,46 +156,6 @@ bool pade10_coeffs(double alpha, double* a) {
   return true;
 }
 
-// Metric terms of a curvilinear block whose points are x(i, j), y(i, j) (periodic in i and j
-// up to a coordinate jump `shift` = (dx, dy) across the i wrap, then across the j wrap) extruded
-// along z with spacing dz (unit depth in 2-D).  Coordinate derivatives by the block's own CD
-// scheme in index space (Eq. 2, alpha = 0, spacing 1); the metric terms are the cofactors of the
-// Jacobian matrix d(x, y, z)/d(i, j, k):
-//   xi^_x = y_j z_k, xi^_y = -x_j z_k, eta^_x = -y_i z_k, eta^_y = x_i z_k,
-//   zeta^_z = x_i y_j - x_j y_i, J^-1 = z_k (x_i y_j - x_j y_i), J = 1 / J^-1.
-// Output M[NMETRIC][nz][ny][nx].
-void grid_metrics(int nx, int ny, int nz, double dz, int order, const double* xy, const double* shift, double* M) {
-  const double wgt[2] = {order == 4 ? 2.0 / 3.0 : 0.5, order == 4 ? -1.0 / 12.0 : 0.0};  // a/2, b/4
-  const double zk = nz > 1 ? dz : 1.0;
-  const long long n2 = (long long)nx * ny, N = n2 * nz;
-  // coordinate c at (i + di, j + dj) with the periodic continuation
-  auto X = [&](int c, int i, int j) {
-    int wi = 0, wj = 0;
-    while (i < 0) { i += nx; --wi; }
-    while (i >= nx) { i -= nx; ++wi; }
-    while (j < 0) { j += ny; --wj; }
-    while (j >= ny) { j -= ny; ++wj; }
-    return xy[c * n2 + i + (long long)nx * j] + wi * shift[c] + wj * shift[2 + c];
-  };
-  for (int j = 0; j < ny; ++j)
-    for (int i = 0; i < nx; ++i) {
-      double d[2][2];  // d[c][axis]: d x_c / d index_axis
-      for (int c = 0; c < 2; ++c) {
-        d[c][0] = 0.0;
-        d[c][1] = 0.0;
-        for (int o = 1; o <= 2; ++o) {
-          d[c][0] += wgt[o - 1] * (X(c, i + o, j) - X(c, i - o, j));
-          d[c][1] += wgt[o - 1] * (X(c, i, j + o) - X(c, i, j - o));
-        }
-      }
-      const double det = d[0][0] * d[1][1] - d[0][1] * d[1][0];
-      const double m[NMETRIC] = {d[1][1] * zk, -d[0][1] * zk, -d[1][0] * zk, d[0][0] * zk, det, zk * det,
-                                 1.0 / (zk * det)};
-      for (int k = 0; k < nz; ++k)
-        for (int q = 0; q < NMETRIC; ++q) M[q * N + i + (long long)nx * j + n2 * k] = m[q];
-    }
-}
-
 }  // namespace cfs
 
 extern "C" int cfs_at_weights(int order, int kmax, double* W) {

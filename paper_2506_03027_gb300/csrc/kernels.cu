@@ -100,11 +100,58 @@ __global__ void __launch_bounds__(512) k_view_halo(Geometry g, Physics ph, StepS
   // ring slot of level n - kd - l: (n mod R) - kd - l, wrapped once (kd + l < R)
   const int nR = (int)(sc.n % sc.R);
   double u[5];
+  const int ux = d.ox + ci, uy = d.oy + cj;
+  if (d.ebase >= 0 && (ux < 0 || ux >= d.bnx || uy < 0 || uy >= d.bny)) {
+    // beyond a non-periodic block face: own sources (wall mirror, outflow copy) current, a
+    // neighbouring PE's by the mode with the delay of the faces crossed (physical faces carry
+    // none), far-field constants
+    int kd = 0;
+    if (sc.mode != 0) {
+      if ((ci < 0 || ci >= d.sx) && !((d.phys >> (ci < 0 ? 0 : 1)) & 1)) kd = max(kd, face_delay(sc, sid, ci < 0 ? 0 : 1));
+      if ((cj < 0 || cj >= d.sy) && !((d.phys >> (cj < 0 ? 2 : 3)) & 1)) kd = max(kd, face_delay(sc, sid, cj < 0 ? 2 : 3));
+      if ((ck < 0 || ck >= d.sz) && !((d.phys >> (ck < 0 ? 4 : 5)) & 1)) kd = max(kd, face_delay(sc, sid, ck < 0 ? 4 : 5));
+    }
+    auto slot = [&](int l) { const int qq = nR - kd - l; return qq < 0 ? qq + sc.R : qq; };
+    const int ei = g.emap[d.ebase + (ux + g.GE) + (long long)d.gmx * ((uy + g.GE) + (long long)d.gmy * gz)];
+    const GatherEntry& E = g.gent[ei];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = E.cst[v];
+    const long long lvN = 5 * g.N;
+    const double* w = sc.W + (kd * s + stage) * sc.C;
+    for (int t = 0; t < E.nt; ++t) {
+      const bool own = !(E.flags[t] & 2) && E.sid[t] == sid;
+      const double wt = E.w[t], wf = (E.flags[t] & 1) ? -wt : wt;
+      const long long o = E.off[t];
+      const long long bN = E.bN[t];
+      double x[5];
+      if (own || sc.mode == 0) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) x[v] = Uin[o + v * bN];
+      } else if (sc.mode == 2) {
+        const double* src = ring + (long long)slot(0) * lvN;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) x[v] = src[o + v * bN];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) x[v] = 0.0;
+        for (int l = 0; l < sc.C; ++l) {
+          const double* src = ring + (long long)slot(l) * lvN;
+          const double wl = __ldg(w + l);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) x[v] = fma(wl, src[o + v * bN], x[v]);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) u[v] = fma((v >= 1 && v <= 3) ? wf : wt, x[v], u[v]);
+    }
+    store_prims<T>(g, ph, u, d.pbase + q, Wp);
+    return;
+  }
   if (sc.mode == 0) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) u[v] = Uin[v * d.bN + gi];
   } else {
-    int kd = 0;
+    int kd = 0;  // (faces inside the block: none is physical)
     if (ci < 0 || ci >= d.sx) kd = max(kd, face_delay(sc, sid, ci < 0 ? 0 : 1));
     if (cj < 0 || cj >= d.sy) kd = max(kd, face_delay(sc, sid, cj < 0 ? 2 : 3));
     if (ck < 0 || ck >= d.sz) kd = max(kd, face_delay(sc, sid, ck < 0 ? 4 : 5));
@@ -168,11 +215,11 @@ __device__ __forceinline__ void flux_curvilinear(const Geometry& g, const Physic
   const long long P = g.Ptot;
   const int r = g.r;
   const long long sty = d.ex, stz = (long long)d.ex * d.ey;
-  const int gx = wrapc(d.ox + ci, d.bnx), gy = wrapc(d.oy + cj, d.bny), gz = wrapc(d.oz + ck, d.bnz);
-  const long long gp = (long long)gx + (long long)d.bnx * ((long long)gy + (long long)d.bny * gz);
-  const double* M = g.metric + d.mbase + gp;
-  const T m[3][3] = {{(T)M[0], (T)M[d.bN], (T)0}, {(T)M[2 * d.bN], (T)M[3 * d.bN], (T)0}, {(T)0, (T)0, (T)M[4 * d.bN]}};
-  const T J = (T)M[6 * d.bN];
+  // metric plane of the block (extended by G, z-independent): flux points lie within r <= G
+  const double* M = g.metric + d.mbase + (long long)(d.ox + ci + g.G) + (long long)d.mx * (d.oy + cj + g.G);
+  const long long pl = d.mpl;
+  const T m[3][3] = {{(T)M[0], (T)M[pl], (T)0}, {(T)M[2 * pl], (T)M[3 * pl], (T)0}, {(T)0, (T)0, (T)M[4 * pl]}};
+  const T J = (T)M[6 * pl];
   const T rho = W[q], u = W[P + q], v = W[2 * P + q], w = W[3 * P + q], p = W[4 * P + q];
   const T et = W[6 * P + q];
   const T vel[3] = {u, v, w};
@@ -332,6 +379,8 @@ __global__ void __launch_bounds__(512) k_rk(Geometry g, Physics ph, StepSched sc
   const long long P = g.Ptot;
   const T* F = Phi + d.pbase;
   const long long st[3] = {1, sty, stz};
+  const bool wallpt = d.wall && ((((d.wall >> 0) & 1) && ci == 0) || (((d.wall >> 1) & 1) && ci == d.sx - 1) ||
+                                 (((d.wall >> 2) & 1) && cj == 0) || (((d.wall >> 3) & 1) && cj == d.sy - 1));
   // dt R = sum_a (dt c1_a)(Phi_{+1} - Phi_{-1}) + (dt c2_a)(Phi_{+2} - Phi_{-2}) as one FMA chain
   T k1[3], k2[3];
 #pragma unroll
@@ -350,10 +399,14 @@ __global__ void __launch_bounds__(512) k_rk(Geometry g, Physics ph, StepSched sc
       acc = fma(k1[a], Fa[q + st[a]] - Fa[q - st[a]], acc);
       if (g.r == 2) acc = fma(k2[a], Fa[q + 2 * st[a]] - Fa[q - 2 * st[a]], acc);
     }
-    const double dtR = (d.mbase >= 0) ? (double)acc * g.metric[d.mbase + 6 * d.bN + (gi - d.bbase)] : (double)acc;
-    const double qn = first ? dtR : fma(A, Q[c * d.bN + gi], dtR);
+    const double dtR =
+        (d.mbase >= 0) ? (double)acc * g.metric[d.mbase + 6 * d.mpl + (d.ox + ci + g.G) + (long long)d.mx * (d.oy + cj + g.G)]
+                       : (double)acc;
+    double qn = first ? dtR : fma(A, Q[c * d.bN + gi], dtR);
+    double un = fma(B, qn, Uin[c * d.bN + gi]);
+    if (wallpt && c >= 1 && c <= 3) qn = un = 0.0;  // no-slip wall points keep zero momentum
     if (!last) Q[c * d.bN + gi] = qn;
-    Uout[c * d.bN + gi] = fma(B, qn, Uin[c * d.bN + gi]);
+    Uout[c * d.bN + gi] = un;
   }
 }
 
@@ -459,19 +512,29 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
   __shared__ long long sBase[128];
   __shared__ long long sLev[(CFS_MAX_DELAY + 2) * CFS_MAX_LEVELS];
   __shared__ int sKd[2][128];
+  __shared__ int sSid[128], sT1[128], sT2[128];  // blocks with a gather map: the line's sub-domain and position
+  const bool gmap = f.ebase >= 0;
   for (int t = threadIdx.x; t < nlines; t += blockDim.x) {
     const long long t12 = l0 + t;
     const int t1 = (int)(t12 % n[f1]), t2 = (int)(t12 / n[f1]);
     sBase[t] = f.bbase + (long long)var * f.bN + (long long)t1 * strides[f1] + (long long)t2 * strides[f2];
     int kl = 0, kr = 0;
-    if (sc.mode != 0) {
+    if (sc.mode != 0 || gmap) {
       int sidx[3];
       sidx[axis] = seg;
       sidx[f1] = f.owner[f1][t1];
       sidx[f2] = f.owner[f2][t2];
       const int sid = f.sid0 + sidx[0] + f.P[0] * (sidx[1] + f.P[1] * sidx[2]);
-      kl = face_delay(sc, sid, 2 * axis);
-      kr = face_delay(sc, sid, 2 * axis + 1);
+      // a sub-domain face on a physical block boundary has no neighbouring PE and no delay
+      const bool pl = seg == 0 && ((f.phys >> (2 * axis)) & 1);
+      const bool pr = seg == f.P[axis] - 1 && ((f.phys >> (2 * axis + 1)) & 1);
+      if (sc.mode != 0) {
+        kl = pl ? 0 : face_delay(sc, sid, 2 * axis);
+        kr = pr ? 0 : face_delay(sc, sid, 2 * axis + 1);
+      }
+      sSid[t] = sid;
+      sT1[t] = t1;
+      sT2[t] = t2;
     }
     sKd[0][t] = kl;
     sKd[1][t] = kr;
@@ -491,6 +554,36 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
     const int pos = i - 5;
     const long long gi = sBase[line] + sPos[i];
     double* dst = tile + line * TW + i;
+    const int u = off + pos;  // block coordinate along the line
+    if (gmap && axis < 2 && (u < 0 || u >= n[axis])) {
+      // beyond a non-periodic block face: the face's sources -- own ones current, a neighbouring
+      // PE's by the mode, far-field constants
+      int cc[3];
+      cc[axis] = u;
+      cc[f1] = sT1[line];
+      cc[f2] = sT2[line];
+      const int ei = g.emap[f.ebase + (cc[0] + g.GE) + (long long)f.gmx * ((cc[1] + g.GE) + (long long)f.gmy * cc[2])];
+      const GatherEntry& E = g.gent[ei];
+      const int kd = sKd[pos < 0 ? 0 : 1][line];
+      double v = E.cst[var];
+      for (int t = 0; t < E.nt; ++t) {
+        const bool own = !(E.flags[t] & 2) && E.sid[t] == sSid[line];
+        const double sg = ((E.flags[t] & 1) && var >= 1 && var <= 3) ? -E.w[t] : E.w[t];
+        const long long o = E.off[t] + (long long)var * E.bN[t];
+        double x;
+        if (own || sc.mode == 0) {
+          x = Uin[o];
+        } else if (sc.mode == 2) {
+          x = f.ring[sLev[kd * sc.C] + o];
+        } else {
+          x = 0.0;
+          for (int l = 0; l < sc.C; ++l) x = fma(__ldg(sc.Wf + kd * sc.C + l), f.ring[sLev[kd * sc.C + l] + o], x);
+        }
+        v = fma(sg, x, v);
+      }
+      *dst = v;
+      return;
+    }
     if ((pos >= 0 && pos < len) || sc.mode == 0) {
       cp_async8(dst, Uin + gi);
     } else {
@@ -599,14 +692,22 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
   }
   __syncthreads();
 
-  // ---- store the own points
+  // ---- store the own points; no-slip wall points keep zero momentum
   const int slot0 = F32 ? 5 : 0;
+  const bool wz = f.wall && var >= 1 && var <= 3;
+  auto wall_pt = [&](int ln, int i) {
+    const int u = off + i, a1 = sT1[ln], a2 = sT2[ln];
+    return (((f.wall >> (2 * axis)) & 1) && u == 0) || (((f.wall >> (2 * axis + 1)) & 1) && u == n[axis] - 1) ||
+           (((f.wall >> (2 * f1)) & 1) && a1 == 0) || (((f.wall >> (2 * f1 + 1)) & 1) && a1 == n[f1] - 1) ||
+           (((f.wall >> (2 * f2)) & 1) && a2 == 0) || (((f.wall >> (2 * f2 + 1)) & 1) && a2 == n[f2] - 1);
+  };
   if (axis == 0) {
     for (int ln = warp; ln < nlines; ln += nwarp)
-      for (int i = lane; i < len; i += 32) Uout[sBase[ln] + sPos[i + 5]] = tile[ln * TW + slot0 + i];
+      for (int i = lane; i < len; i += 32)
+        Uout[sBase[ln] + sPos[i + 5]] = (wz && wall_pt(ln, i)) ? 0.0 : tile[ln * TW + slot0 + i];
   } else {
     for (int ln = threadIdx.x; ln < nlines; ln += blockDim.x)
-      for (int i = 0; i < len; ++i) Uout[sBase[ln] + sPos[i + 5]] = tile[ln * TW + slot0 + i];
+      for (int i = 0; i < len; ++i) Uout[sBase[ln] + sPos[i + 5]] = (wz && wall_pt(ln, i)) ? 0.0 : tile[ln * TW + slot0 + i];
   }
 }
 
@@ -661,11 +762,12 @@ __device__ __forceinline__ double vel_at(const double* U, const DiagBlock& b, in
 }
 
 __global__ void __launch_bounds__(256) k_diag(DiagBlock b, const double* __restrict__ U, double* __restrict__ partial) {
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double acc[DIAG_NQ] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   const int ndim = b.nz > 1 ? 3 : 2;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < b.bN; i += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(i % b.nx), y = (int)((i / b.nx) % b.ny), z = (int)(i / ((long long)b.nx * b.ny));
-    const double dV = b.M ? b.M[5 * b.bN + i] : b.dV;  // cell volume (J^-1 on a curvilinear grid)
+    const long long mq = (long long)(x + b.G) + (long long)b.mx * (y + b.G);  // metric plane index
+    const double dV = b.M ? b.M[5 * b.mpl + mq] : b.dV;  // cell volume (J^-1 on a curvilinear grid)
     double u[5];
     for (int v = 0; v < 5; ++v) {
       u[v] = U[b.bbase + v * b.bN + i];
@@ -675,6 +777,17 @@ __global__ void __launch_bounds__(256) k_diag(DiagBlock b, const double* __restr
     const double rho = u[0];
     const double vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
     acc[0] += 0.5 * rho * (vx * vx + vy * vy + vz * vz) * dV;
+    // enstrophy only where the CD stencils stay in the block or cross periodic faces
+    if (b.nonper) {
+      const int c3[3] = {x, y, z}, n3[3] = {b.nx, b.ny, b.nz};
+      bool inner = true;
+      for (int a = 0; a < ndim; ++a) {
+        if (((b.nonper >> (2 * a)) & 1) && c3[a] < b.rs) inner = false;
+        if (((b.nonper >> (2 * a + 1)) & 1) && c3[a] > n3[a] - 1 - b.rs) inner = false;
+      }
+      if (!inner) continue;
+    }
+    acc[8] += dV;
     // vorticity by the CD scheme
     double dv[3][3];
     for (int c = 0; c < 3; ++c)
@@ -688,9 +801,9 @@ __global__ void __launch_bounds__(256) k_diag(DiagBlock b, const double* __restr
         dv[c][a] = dd;
       }
     if (b.M) {  // index-space derivatives -> physical: d/dx_j = J sum_k (metric row k)_j d/dxi_k
-      const double J = b.M[6 * b.bN + i];
-      const double m[3][3] = {{b.M[i], b.M[b.bN + i], 0.0}, {b.M[2 * b.bN + i], b.M[3 * b.bN + i], 0.0},
-                              {0.0, 0.0, b.M[4 * b.bN + i]}};
+      const double J = b.M[6 * b.mpl + mq];
+      const double m[3][3] = {{b.M[mq], b.M[b.mpl + mq], 0.0}, {b.M[2 * b.mpl + mq], b.M[3 * b.mpl + mq], 0.0},
+                              {0.0, 0.0, b.M[4 * b.mpl + mq]}};
       double dp[3][3];
       for (int c = 0; c < 3; ++c)
         for (int j = 0; j < 3; ++j) dp[c][j] = J * (m[0][j] * dv[c][0] + m[1][j] * dv[c][1] + m[2][j] * dv[c][2]);
@@ -701,9 +814,9 @@ __global__ void __launch_bounds__(256) k_diag(DiagBlock b, const double* __restr
     acc[1] += 0.5 * rho * (wx * wx + wy * wy + wz * wz) * dV;
   }
   // block reduction: warp shuffles, then one warp over the warp sums
-  __shared__ double sh[8][8];
+  __shared__ double sh[DIAG_NQ][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int c = 0; c < 8; ++c) {
+  for (int c = 0; c < DIAG_NQ; ++c) {
     double v = acc[c];
     for (int o = 16; o > 0; o >>= 1) {
       const double other = __shfl_down_sync(0xffffffffu, v, o);
@@ -712,28 +825,33 @@ __global__ void __launch_bounds__(256) k_diag(DiagBlock b, const double* __restr
     if (lane == 0) sh[c][wid] = v;
   }
   __syncthreads();
-  if (threadIdx.x < 8) {
+  if (threadIdx.x < DIAG_NQ) {
     const int c = threadIdx.x;
     double v = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = (c == 7) ? fmax(v, sh[c][w]) : v + sh[c][w];
-    partial[(long long)blockIdx.x * 8 + c] = v;
+    partial[(long long)blockIdx.x * DIAG_NQ + c] = v;
   }
 }
 
 // Deterministic second pass: one thread per quantity sums the block partials in block order.
-// K and enstrophy are volume averages (sums of value x cell volume over the total volume).
+// K is a volume average (sum of value x cell volume over the total volume), the enstrophy an
+// average over the volume of the points it covers.
 __global__ void k_diag_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out, double volume) {
   const int c = threadIdx.x;
   if (c >= 8) return;
-  double v = 0.0;
-  for (int b = 0; b < nblocks; ++b) v = (c == 7) ? fmax(v, partial[(long long)b * 8 + c]) : v + partial[(long long)b * 8 + c];
-  if (c < 2) v /= volume;
+  double v = 0.0, ve = 0.0;
+  for (int b = 0; b < nblocks; ++b) {
+    v = (c == 7) ? fmax(v, partial[(long long)b * DIAG_NQ + c]) : v + partial[(long long)b * DIAG_NQ + c];
+    ve += partial[(long long)b * DIAG_NQ + 8];
+  }
+  if (c == 0) v /= volume;
+  if (c == 1) v = ve > 0.0 ? v / ve : 0.0;
   out[c] = v;
 }
 
 int launch_diagnostics_block(const Geometry& g, const DiagBlock& b, const double* U, double* partial, int row0,
                              int nblocks, void* stream) {
-  k_diag<<<nblocks, 256, 0, (cudaStream_t)stream>>>(b, U, partial + (long long)row0 * 8);
+  k_diag<<<nblocks, 256, 0, (cudaStream_t)stream>>>(b, U, partial + (long long)row0 * DIAG_NQ);
   return (int)cudaGetLastError();
 }
 

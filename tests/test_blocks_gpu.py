@@ -1,0 +1,158 @@
+"""Parity of the connected multi-block path (interfaces, the wake cut's reversed orientation,
+spanwise interpolation, no-slip walls, far fields, outflows) through the C ABI with the FP64
+oracle: relative L2 per conserved variable at most 1e-12 per block for the FP64 path."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2506_03027_gb300 import cfs
+from paper_2506_03027_gb300 import inputs as I
+
+from gpu_util import PARITY_TOL, ensure_built, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+
+
+def run_mb(mb, U0, nsteps, delays=None, precision=0, graph=False, diag=False):
+    import torch
+    st = torch.cuda.Stream() if graph else None
+    ctx = torch.cuda.stream(st) if graph else torch.cuda.stream(torch.cuda.current_stream())
+    with ctx:
+        s = cfs.Solver(mb, precision=precision, graph=graph, stream=st)
+        try:
+            s.set_schedule(delays=delays)
+            s.set_states(U0)
+            s.step(nsteps)
+            U = s.get_states()
+            d = s.diagnostics(check_finite=False) if diag else None
+        finally:
+            s.close()
+    return (U, d) if diag else U
+
+
+def check_blocks(Ug, Uo, tol=PARITY_TOL):
+    for b, (a, r) in enumerate(zip(Ug, Uo)):
+        e = rel_l2(a, r)
+        assert np.all(np.isfinite(a)) and np.all(e <= tol), (b, e)
+
+
+def cgrid(algo, cfl=0.05):
+    sp = I.cgrid_reduced()
+    mb = I.naca_cgrid(sp, algo=algo)
+    mb = mb.replace_all(dt=I.cgrid_dt(mb, cfl))
+    return mb, I.cgrid_state(mb, sp)
+
+
+def sub_delays(mb, n):
+    return I.saa_delays(mb.case.replace(px=mb.nsub, py=1, pz=1), n)
+
+
+@pytest.mark.parametrize("algo", ["SA", "CAA", "SAA"])
+def test_cgrid_parity(algo):
+    """The reduced 12-block NACA0012 C-grid (walls, wake cut, far field, outflows, inner/outer
+    layers of different spanwise counts), 30 steps; each block against the oracle, and the
+    diagnostics (volume-weighted K, enstrophy away from non-periodic faces, totals)."""
+    mb, U0 = cgrid(algo)
+    if algo == "CAA":
+        mb = mb.replace_all(caa_L=3, kmax=2)
+    n = 30
+    d = sub_delays(mb, n) if algo == "SAA" else None
+    Ug, dg = run_mb(mb, U0, n, delays=d, diag=True)
+    Uo, do = orc.run(mb, U0, n, delays=d, diag=True)
+    check_blocks(Ug, Uo)
+    for b in range(1, 5):  # wall points at rest
+        assert np.all(Ug[b][1:4, :, 0, :] == 0.0)
+    np.testing.assert_allclose(dg[:2], do[-1][:2], rtol=1e-11)
+    np.testing.assert_allclose(dg[2], do[-1][2], rtol=1e-12)
+    np.testing.assert_allclose(dg[6], do[-1][6], rtol=1e-12)
+
+
+def test_cgrid_graph_mode_is_bitwise_identical():
+    mb, U0 = cgrid("SAA")
+    n = 12
+    d = sub_delays(mb, n)
+    Ua = run_mb(mb, U0, n, delays=d)
+    Ub = run_mb(mb, U0, n, delays=d, graph=True)
+    for a, b in zip(Ua, Ub):
+        assert np.array_equal(a, b)
+
+
+def test_cgrid_fp32_form():
+    """FP32 intermediates on the C-grid (multi-kernel stage, gather halos): within the FP32-form
+    error bound of the oracle."""
+    mb, U0 = cgrid("SAA")
+    n = 20
+    d = sub_delays(mb, n)
+    Ug = run_mb(mb, U0, n, delays=d, precision=1)
+    Uo = orc.run(mb, U0, n, delays=d)
+    for b, (a, r) in enumerate(zip(Ug, Uo)):
+        e = rel_l2(a, r)
+        assert np.all(np.isfinite(a)) and np.all(e < 1e-6), (b, e)
+
+
+def test_cgrid_freestream_preserved_on_gpu():
+    mb, _ = cgrid("SAA")
+    free = mb.faces[6][3].state
+    faces = [[dataclasses.replace(f, type="farfield", state=free) if f.type == "wall" else f for f in fs]
+             for fs in mb.faces]
+    mb = dataclasses.replace(mb, faces=faces)
+    U0 = [np.ascontiguousarray(np.broadcast_to(np.asarray(free)[:, None, None, None], (5, b.nz, b.ny, b.nx)))
+          for b in mb.blocks]
+    n = 12
+    Ug = run_mb(mb, U0, n, delays=sub_delays(mb, n))
+    assert max(float(np.abs(a - b).max()) for a, b in zip(Ug, U0)) < 1e-12 * max(free)
+
+
+def test_rotated_block_parity():
+    c = I.tgv_case(24, 2, "SAA", kmax=2, filter=True, curv=0.2)
+    c = c.replace(dt=I.cfl_dt(c, I.tgv_state(c), 0.1), px=3)
+    mb = I.rotated_pair(c, 16, 2, 1)
+    U0 = list(I.rotate_state_pair(I.tgv_state(c), 16))
+    n = 12
+    d = sub_delays(mb, n)
+    check_blocks(run_mb(mb, U0, n, delays=d), orc.run(mb, U0, n, delays=d))
+
+
+def test_split_and_span_pairs_parity():
+    c = I.tgv_case(24, 2, "SAA", kmax=2, filter=True)
+    c = c.replace(dt=I.cfl_dt(c, I.tgv_state(c), 0.1), px=3)
+    U = I.tgv_state(c)
+    n = 10
+    mb = I.split_box_x(c, 16, 2, 1)
+    U0 = [U[..., :16], U[..., 16:]]
+    d = sub_delays(mb, n)
+    check_blocks(run_mb(mb, U0, n, delays=d), orc.run(mb, U0, n, delays=d))
+    mb = I.span_pair(c, 16, 12, 2, 1)
+    U0 = [U[..., :16], np.ascontiguousarray(U[:, ::2, :, 16:])]
+    check_blocks(run_mb(mb, U0, n, delays=d), orc.run(mb, U0, n, delays=d))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_wall_channel_parity(precision):
+    """No-slip walls on both y faces of a Cartesian box, SAA delays on the sub-domain faces inside
+    the block, TGV-like initial field with zero wall momentum."""
+    c = I.tgv_case(20, 2, "SAA", kmax=2, filter=True).replace(ny=21, py=3, ly=2.0)
+    U = I.tgv_state(c)
+    U[1:4, :, 0, :] = 0.0
+    U[1:4, :, -1, :] = 0.0
+    c = c.replace(dt=I.cfl_dt(c, U, 0.1))
+    mb = I.wall_channel(c)
+    n = 16
+    d = I.saa_delays(c, n)
+    Ug = run_mb(mb, [U], n, delays=d, precision=precision)
+    Uo = orc.run(mb, [U], n, delays=d)
+    if precision == 0:
+        check_blocks(Ug, Uo)
+    else:
+        assert np.all(rel_l2(Ug[0], Uo[0]) < 1e-6)
+    assert np.all(Ug[0][1:4, :, 0, :] == 0.0) and np.all(Ug[0][1:4, :, -1, :] == 0.0)

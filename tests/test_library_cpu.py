@@ -95,11 +95,17 @@ def test_call_order_and_block_validation(lib):
             cfs.cfs_split_block(ctx, 2, 1, 1, 1)  # unknown block
         with pytest.raises(cfs.CfsError):
             cfs.cfs_split_block(ctx, 0, 17, 1, 1)
+        for bad in [(0, 6, 1, 0, 0), (0, 0, 1, 1, 2), (0, 4, 1, 0, 0), (0, 1, 0, 1, 0), (0, 0, 3, 1, 0)]:
+            with pytest.raises(cfs.CfsError) as e:
+                cfs.cfs_connect(ctx, *bad)  # bad face, orientation, z face, face to itself, block
+            assert e.value.status == cfs.CFS_EINVAL
+        cfs.cfs_connect(ctx, 0, 0, 0, 1)  # the periodic default
+        for bad in [(0, 0, 7), (0, 4, cfs.BC_WALL), (0, 0, cfs.BC_FARFIELD), (5, 0, cfs.BC_WALL)]:
+            with pytest.raises(cfs.CfsError) as e:
+                cfs.cfs_set_bc(ctx, *bad)  # unknown type, z face, far field without a state, block
+            assert e.value.status == cfs.CFS_EINVAL
         with pytest.raises(cfs.CfsError):
-            cfs.cfs_connect(ctx, 0, 0, 0, 2)
-        cfs.cfs_connect(ctx, 0, 0, 0, 1)
-        with pytest.raises(cfs.CfsError):
-            cfs.cfs_set_bc(ctx, 0, 0, 1)
+            cfs.cfs_set_face_shift(ctx, 0, 0, (1.0, 0.0))  # not an interface
         with pytest.raises(cfs.CfsError) as e:
             cfs.cfs_set_schedule(ctx, 1, 1, 4, None)
         assert e.value.status == cfs.CFS_ESTATE
@@ -128,3 +134,37 @@ def test_set_block_grid_validation(lib):
         cfs.cfs_set_block_grid(ctx, 0, xy, (1.6, 0, 0, 1.2))
     finally:
         cfs.cfs_destroy(ctx)
+
+
+def test_topology_validation_at_finalize(lib):
+    """Face descriptions are checked when the context is finalized, before any device memory is
+    touched: an interface between faces of different tangential point counts, a Cartesian
+    interface joining non-opposite faces, and a curvilinear block joined to a Cartesian one are
+    rejected with EINVAL."""
+    p = cfs.CfsParams(order=4, viscous=0, gamma=1.4, mach=0.5, re=1.0, pr=1.0, filter=0, alpha_f=0.0)
+
+    def attempt(setup):
+        ctx = cfs.cfs_create(p)
+        try:
+            cfs.cfs_add_block(ctx, 16, 16, 1, (0.1, 0.1, 1.0))
+            cfs.cfs_add_block(ctx, 12, 20, 1, (0.1, 0.1, 1.0))
+            cfs.cfs_add_block(ctx, 12, 16, 1, (0.1, 0.1, 1.0))
+            setup(ctx)
+            with pytest.raises(cfs.CfsError) as e:
+                cfs.cfs_finalize(ctx, 0)
+            return e.value.status, cfs.cfs_last_error(ctx)
+        finally:
+            cfs.cfs_destroy(ctx)
+
+    st, msg = attempt(lambda ctx: cfs.cfs_connect(ctx, 0, 1, 1, 0))  # 16 vs 20 points along y
+    assert st == cfs.CFS_EINVAL and "tangential" in msg
+    st, msg = attempt(lambda ctx: cfs.cfs_connect(ctx, 0, 3, 2, 1))  # Cartesian +y to +x
+    assert st == cfs.CFS_EINVAL and "Cartesian" in msg
+
+    def curv_to_cart(ctx):
+        xy = np.stack(np.meshgrid(np.arange(16) * 0.1, np.arange(16) * 0.1)).astype(np.float64)
+        cfs.cfs_set_block_grid(ctx, 0, xy, (1.6, 0.0, 0.0, 1.6))
+        cfs.cfs_connect(ctx, 0, 1, 2, 0)
+    st, msg = attempt(curv_to_cart)
+    assert st == cfs.CFS_EINVAL and "curvilinear" in msg
+
