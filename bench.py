@@ -333,6 +333,8 @@ def run_ours(args, rank, world, local_rank):
         forms["batched_blocks_fp32_intermediates"] = batched_form(args, 1)
         forms["batched_blocks_curvilinear"] = batched_form(args, 0, curvilinear=True)
         forms["batched_blocks_curvilinear_fp32_intermediates"] = batched_form(args, 1, curvilinear=True)
+        forms["cgrid_naca0012"] = cgrid_form(args, 0)
+        forms["cgrid_naca0012_fp32_intermediates"] = cgrid_form(args, 1)
 
     # ---------------- learned halo predictor (trained here on synchronous-run halos)
     if args.precision == 0 and not args.no_forms and not args.no_learned and world == 1:
@@ -454,6 +456,50 @@ def batched_form(args, precision=0, curvilinear=False):
                         + ("FP64" if precision == 0 else
                            "FP32 intermediates (" + ("multi-kernel stage" if curvilinear else
                                                      "one fused launch per RK stage") + ")")}
+
+
+def cgrid_form(args, precision=0):
+    """The 12-block NACA0012 C-grid (22.0 M points: inner layer 192 x 64 spanwise, outer layer
+    64 x 32, segments of 96, 160 and 512 points per side along the C), connected by interfaces
+    (the wake cut reversed, inner/outer layers by spanwise interpolation), no-slip walls on the
+    airfoil, far field and outflows; Re_c 5e4, M 0.3, SAA delays 0..2 at CFL 0.05 of the smallest
+    cell.  All blocks advance in one launch per kernel, the step captured in a CUDA graph, launch
+    shapes from the autotuner."""
+    import torch
+    from paper_2506_03027_gb300 import autotune
+    from paper_2506_03027_gb300 import cfs
+    from paper_2506_03027_gb300 import inputs as I
+    spec = I.CGridSpec()
+    mb = I.naca_cgrid(spec, algo="SAA", kmax=2)
+    mb = mb.replace_all(dt=I.cgrid_dt(mb, 0.05))
+    U0 = I.cgrid_state(mb, spec)
+    tiles = autotune.tune(mb, precision=precision, use_cache=False, states=U0)
+    K, W = max(3, args.steps // 4), args.warmup
+    delays = I.saa_delays(mb.case.replace(px=mb.nsub, py=1, pz=1), W + K)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        s = cfs.Solver(mb, graph=True, stream=st, precision=precision, tiles=tiles)
+        s.set_schedule(delays=delays)
+        s.set_states(U0)
+        s.step(W)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.step(K)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = s.launches()
+        d = s.diagnostics(check_finite=False)
+        walls_at_rest = all(bool(np.all(s.get_state(block=b)[1:4, :, 0, :] == 0.0)) for b in range(1, 5))
+        s.close()
+    return {"value": mb.npts * 5 * K / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms / K, "points": mb.npts,
+            "blocks": len(mb.blocks), "subdomains": mb.nsub, "cuda_graph": True,
+            "launches_per_step": launches / K, "tiles_autotuned": list(tiles),
+            "finite": bool(d[7] == 0.0), "wall_points_at_rest": walls_at_rest, "K_after": float(d[0]),
+            "workload": "NACA0012 12-block C-grid (interfaces, wake cut, walls, far field, outflows), NS Re_c 5e4 "
+                        "M 0.3, SAA 0..2, " + ("FP64" if precision == 0 else "FP32 intermediates (multi-kernel stage)")}
 
 
 def precision_form_256(args):

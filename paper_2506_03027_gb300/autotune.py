@@ -9,7 +9,7 @@ import os
 import numpy as np
 
 from . import cfs
-from .inputs import initial_state, saa_delays
+from .inputs import MultiBlock, initial_state, saa_delays
 
 FUSED = [(fy, zc, 256) for fy in (4, 8, 16) for zc in (8, 16, 32)]
 PLAIN = [(8, 16, t) for t in (128, 256, 512)]
@@ -45,16 +45,19 @@ def store(k: str, tiles, ms: dict) -> None:
     os.replace(tmp, path)
 
 
-def time_candidate(case, tiles, precision: int, blocks=None, steps: int = 4, warmup: int = 6) -> float:
+def time_candidate(case, tiles, precision: int, blocks=None, steps: int = 4, warmup: int = 6, states=None) -> float:
+    """Milliseconds per step of `case` (a Case, or an inputs.MultiBlock with its block `states`)."""
     import torch
-    blocks = blocks or [case]
+    mb = case if isinstance(case, MultiBlock) else None
+    c0 = mb.case if mb is not None else case
+    blocks = mb.blocks if mb is not None else (blocks or [case])
     nsub = sum(b.nsub for b in blocks)
-    s = cfs.Solver(case, precision=precision, blocks=blocks, tiles=tiles)
+    s = cfs.Solver(case, precision=precision, blocks=None if mb is not None else blocks, tiles=tiles)
     try:
-        d = saa_delays(case.replace(px=nsub, py=1, pz=1), warmup + steps) if case.algo == "SAA" else None
+        d = saa_delays(c0.replace(px=nsub, py=1, pz=1), warmup + steps) if c0.algo == "SAA" else None
         s.set_schedule(delays=d)
         for i, b in enumerate(blocks):
-            s.set_state(initial_state(b), block=i)
+            s.set_state(states[i] if states is not None else initial_state(b), block=i)
         s.step(warmup)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -68,19 +71,24 @@ def time_candidate(case, tiles, precision: int, blocks=None, steps: int = 4, war
         s.close()
 
 
-def tune(case, precision: int = 0, blocks=None, use_cache: bool = True):
-    """Fastest launch shapes for the workload (from the cache when present)."""
-    k = key(case, precision, len(blocks or [case]))
+def tune(case, precision: int = 0, blocks=None, use_cache: bool = True, states=None):
+    """Fastest launch shapes for the workload (from the cache when present).  `case` may be an
+    inputs.MultiBlock (connected blocks; `states` its initial block states)."""
+    mb = case if isinstance(case, MultiBlock) else None
+    c0 = mb.case if mb is not None else case
+    k = key(c0, precision, len(mb.blocks) if mb is not None else len(blocks or [case]))
+    if mb is not None:
+        k += f"|{mb.name}|{mb.npts}"
     if use_cache:
         hit = load_cache().get(k)
         if hit:
             return tuple(hit["tiles"])
-    fused = (precision == 1 and case.nz > 1 and case.viscous and case.order == 4
+    fused = (mb is None and precision == 1 and c0.nz > 1 and c0.viscous and c0.order == 4
              and not any(b.curv for b in (blocks or [case])))
     cands = FUSED if fused else PLAIN
     ms = {}
     for t in cands:
-        ms[str(t)] = time_candidate(case, t, precision, blocks)
+        ms[str(t)] = time_candidate(case, t, precision, blocks, states=states)
     best = min(cands, key=lambda t: ms[str(t)])
     store(k, best, ms)
     return best

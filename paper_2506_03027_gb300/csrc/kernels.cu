@@ -194,6 +194,15 @@ __global__ void __launch_bounds__(512) k_view_halo(Geometry g, Physics ph, StepS
 
 // ------------------------------------------------------------------------------- k_flux
 
+// Viscosity law: mu = 1, or the power law mu = T^visc_exp -- in the intermediate precision (the
+// FP32 form evaluates it in FP32: a power in FP64 runs at the FP64 rate)
+template <typename T>
+__device__ __forceinline__ T visc_mu(const Physics& ph, T temp) {
+  if (ph.visc_law != 1) return (T)1;
+  if (std::is_same<T, float>::value) return (T)powf((float)temp, (float)ph.visc_exp);
+  return (T)pow((double)temp, ph.visc_exp);
+}
+
 template <typename T>
 __device__ __forceinline__ T cdiff(const T* __restrict__ f, long long q, long long st, T c1, T c2, int r) {
   T d = c1 * (f[q + st] - f[q - st]);
@@ -241,7 +250,7 @@ __device__ __forceinline__ void flux_curvilinear(const Geometry& g, const Physic
 #pragma unroll
       for (int j = 0; j < 3; ++j) dx[c][j] = J * (m[0][j] * dxi[c][0] + m[1][j] * dxi[c][1] + m[2][j] * dxi[c][2]);
     T mu = (T)1;
-    if (ph.visc_law == 1) mu = (T)pow((double)W[5 * P + q], ph.visc_exp);
+    if (ph.visc_law == 1) mu = visc_mu<T>(ph, W[5 * P + q]);
     const T div = dx[0][0] + dx[1][1] + dx[2][2];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -314,7 +323,7 @@ __global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubD
       du[2][b] = cdiff(W + 3 * P, q, st[b], c1, c2, r);
       dT[b] = cdiff(W + 5 * P, q, st[b], c1, c2, r);
     }
-    if (ph.visc_law == 1) mu = (T)pow((double)W[5 * P + q], ph.visc_exp);
+    if (ph.visc_law == 1) mu = visc_mu<T>(ph, W[5 * P + q]);
   }
   const T div = du[0][0] + du[1][1] + du[2][2];
   const T ire = (T)ph.ire, kap = (T)ph.kappa;

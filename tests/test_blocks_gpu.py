@@ -156,3 +156,18 @@ def test_wall_channel_parity(precision):
     else:
         assert np.all(rel_l2(Ug[0], Uo[0]) < 1e-6)
     assert np.all(Ug[0][1:4, :, 0, :] == 0.0) and np.all(Ug[0][1:4, :, -1, :] == 0.0)
+
+
+def test_cgrid_full_size_parity():
+    """The full 12-block C-grid of the benchmark (22.0 M points, 154 sub-domains, CUDA graph) for 7
+    steps -- five synchronous warm-up steps, then two with SAA delays -- against the oracle over
+    the whole field (the oracle takes about a minute on the host cores)."""
+    spec = I.CGridSpec()
+    mb = I.naca_cgrid(spec, algo="SAA", kmax=2)
+    mb = mb.replace_all(dt=I.cgrid_dt(mb, 0.05))
+    U0 = I.cgrid_state(mb, spec)
+    n = 7
+    d = sub_delays(mb, n)
+    Ug = run_mb(mb, U0, n, delays=d, graph=True)
+    Uo = orc.run(mb, U0, n, delays=d)
+    check_blocks(Ug, Uo)
