@@ -473,7 +473,10 @@ def cgrid_form(args, precision=0):
     mb = I.naca_cgrid(spec, algo="SAA", kmax=2)
     mb = mb.replace_all(dt=I.cgrid_dt(mb, 0.05))
     U0 = I.cgrid_state(mb, spec)
-    tiles = autotune.tune(mb, precision=precision, use_cache=False, states=U0)
+    if args.only_form and args.tiles:
+        tiles = tuple(int(t) for t in args.tiles.split(","))
+    else:
+        tiles = autotune.tune(mb, precision=precision, use_cache=False, states=U0)
     K, W = max(3, args.steps // 4), args.warmup
     delays = I.saa_delays(mb.case.replace(px=mb.nsub, py=1, pz=1), W + K)
     st = torch.cuda.Stream()
@@ -728,9 +731,16 @@ def main():
     ap.add_argument("--grid", type=int, default=128, help="grid points per axis (profiling runs only)")
     ap.add_argument("--split", type=int, default=4, help="sub-domains per axis (profiling runs only)")
     ap.add_argument("--tiles", default="", help="fy,zc,threads launch shapes of the main path (profiling runs only)")
+    ap.add_argument("--only-form", default="", choices=["", "cgrid_naca0012", "cgrid_naca0012_fp32_intermediates"],
+                    help="run one form alone and print its result (profiling runs only; --tiles skips its autotuning)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.only_form:
+        import torch
+        torch.cuda.init()
+        print(json.dumps(cgrid_form(args, 1 if args.only_form.endswith("fp32_intermediates") else 0)), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -78,6 +78,7 @@ def load() -> ctypes.CDLL:
             "cfs_connect": ([vp, ip, ip, ip, ip, ip], ip),
             "cfs_set_bc": ([vp, ip, ip, ip, dp], ip),
             "cfs_set_face_shift": ([vp, ip, ip, dp], ip),
+            "cfs_eval_power": ([vp, ctypes.c_double, vp, ll, vp], ip),
             "cfs_finalize": ([vp, ip], ip),
             "cfs_set_schedule": ([vp, ip, ip, ip, ll, ctypes.POINTER(ctypes.c_int8)], ip),
             "cfs_set_state": ([vp, ip, vp, ip], ip),
@@ -158,6 +159,15 @@ def cfs_set_block_grid(ctx, block: int, xy: np.ndarray, shift):
 
 def cfs_connect(ctx, block_a: int, face_a: int, block_b: int, face_b: int, orientation: int = 0):
     _check(ctx, load().cfs_connect(ctx, block_a, face_a, block_b, face_b, orientation))
+
+
+def cfs_eval_power(x, a: float, y, stream: int | None = None):
+    """y = x^a on device tensors (float64, same size) with the library's FP64 power."""
+    assert x.dtype == y.dtype and x.numel() == y.numel() and x.is_cuda and y.is_cuda
+    st = load().cfs_eval_power(ctypes.c_void_p(x.data_ptr()), float(a), ctypes.c_void_p(y.data_ptr()), x.numel(),
+                               ctypes.c_void_p(stream or 0))
+    if st != CFS_OK:
+        raise CfsError(st, "cfs_eval_power failed")
 
 
 BC_PERIODIC, BC_WALL, BC_FARFIELD, BC_OUTFLOW = 0, 1, 2, 3

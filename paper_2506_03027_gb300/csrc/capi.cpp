@@ -1031,6 +1031,12 @@ cfs_status cfs_diagnostics(cfs_ctx* c, double* out) {
   return CFS_OK;
 }
 
+cfs_status cfs_eval_power(const double* x, double a, double* y, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return CFS_EINVAL;
+  if (n > (1LL << 40)) return CFS_EINVAL;
+  return cfs::launch_eval_power(x, a, y, n, stream) == 0 ? CFS_OK : CFS_ECUDA;
+}
+
 cfs_status cfs_ring_depth(cfs_ctx* c, int* R) {
   if (!c || !R) return CFS_EINVAL;
   if (!c->finalized) return fail(c, CFS_ESTATE, "ring depth after cfs_finalize");

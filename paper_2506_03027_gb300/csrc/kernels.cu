@@ -200,7 +200,7 @@ template <typename T>
 __device__ __forceinline__ T visc_mu(const Physics& ph, T temp) {
   if (ph.visc_law != 1) return (T)1;
   if (std::is_same<T, float>::value) return (T)powf((float)temp, (float)ph.visc_exp);
-  return (T)pow((double)temp, ph.visc_exp);
+  return (T)pow_pos((double)temp, ph.visc_exp);
 }
 
 template <typename T>
@@ -866,6 +866,16 @@ int launch_diagnostics_block(const Geometry& g, const DiagBlock& b, const double
 
 __global__ void k_advance_step(long long* dn) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *dn += 1;
+}
+
+__global__ void k_eval_power(const double* __restrict__ x, double a, double* __restrict__ y, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = pow_pos(x[i], a);
+}
+
+int launch_eval_power(const double* x, double a, double* y, long long n, void* stream) {
+  if (n > 0) k_eval_power<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, a, y, n);
+  return (int)cudaGetLastError();
 }
 
 int launch_advance_step(long long* dn, void* stream) {

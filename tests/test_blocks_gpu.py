@@ -171,3 +171,30 @@ def test_cgrid_full_size_parity():
     Ug = run_mb(mb, U0, n, delays=d, graph=True)
     Uo = orc.run(mb, U0, n, delays=d)
     check_blocks(Ug, Uo)
+
+
+def test_fp64_power_within_a_few_ulp():
+    """The FP64 path's own power (the viscosity law mu = T^0.76 of the C-grid) against numpy's
+    and CUDA's pow: exp(a ln x) carries the rounding of a ln x into the result, so the relative
+    error is bounded by 4.5e-16 (1 + |a ln x|) -- 1e-15 near T = 1 -- over positive normal x;
+    equal special cases."""
+    import torch
+    rng = np.random.default_rng(7)
+    x = np.concatenate([np.exp(rng.uniform(np.log(1e-300), np.log(1e300), 100000)), rng.uniform(0.5, 2.0, 100000),
+                        [1.0, 2.0, 0.5, 2.2250738585072014e-308, 5e-324, 0.0, np.inf]])
+    xt = torch.tensor(x, device="cuda", dtype=torch.float64)
+    for a in (0.76, 0.5, 1.0, -1.3, 0.0):
+        yt = torch.empty_like(xt)
+        cfs.cfs_eval_power(xt, a, yt)
+        torch.cuda.synchronize()
+        y = yt.cpu().numpy()
+        ref = np.power(x, a)
+        cuda_ref = torch.pow(xt, a).cpu().numpy()
+        ok = np.isfinite(ref) & (ref > 0) & (ref < 1e300) & (x > 2.3e-308) & np.isfinite(x)
+        bound = 4.5e-16 * (1.0 + np.abs(a * np.log(x[ok])))
+        assert np.all(np.abs(y[ok] / ref[ok] - 1.0) <= bound), a
+        assert np.all(np.abs(y[ok] / cuda_ref[ok] - 1.0) <= bound + 2.3e-16), a
+        near = ok & (np.abs(x - 1.0) < 0.5)
+        assert np.max(np.abs(y[near] / ref[near] - 1.0)) < 1e-15, a
+        assert np.array_equal(np.isinf(y), np.isinf(ref)) and np.array_equal(y[~ok & np.isfinite(ref)],
+                                                                            cuda_ref[~ok & np.isfinite(ref)])
