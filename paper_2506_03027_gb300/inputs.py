@@ -217,6 +217,35 @@ def vortex_case(n: int = 64, p: int = 2, **kw) -> Case:
     return c
 
 
+def paper_vortex_case(n: int = 60, order: int = 4, algo: str = "SA", at: bool = True, L: int = 8, **kw) -> Case:
+    """The paper's own vortex test (Sec. 5.1): Euler, M = 0.1, periodic [-8, 8]^2 on n x n points,
+    three PEs along x, maximum allowable delay L (CAA: delays (n - C) mod L; SAA: 0..L-1), the
+    time step 2e-3 (SA) or 1e-3 (CAA, SAA) at n = 60, scaled with the grid spacing."""
+    dt = (2e-3 if algo == "SA" else 1e-3) * 60.0 / n
+    c = Case(name="vortex_paper", nx=n, ny=n, nz=1, px=3, py=1, pz=1, lx=16.0, ly=16.0, lz=1.0, mach=0.1,
+             viscous=False, order=order, algo=algo, at=at, caa_L=L, kmax=L - 1, filter=False, dt=dt)
+    return c.replace(**kw)
+
+
+def paper_vortex_state(case: Case, t: float = 0.0, beta: float = 0.02, R: float = 1.0) -> np.ndarray:
+    """The Gaussian vortex of Sec. 5.1 at time t (centre translated by u_inf t = t, periodic):
+    u = 1 - beta (y - y_c)/R^2 exp(-W^2/2), v = beta (x - x_c)/R^2 exp(-W^2/2),
+    p = p_inf - rho beta^2/(2 R^2) exp(-W^2), W^2 = ((x - x_c)^2 + (y - y_c)^2)/R^2, with the strength
+    beta/(u_inf R) = 0.02 of the paper, R = 1 (not printed) and constant density rho = 1 (the
+    pressure of the paper's formula then balances the swirl exactly: a steady vortex carried by
+    the free stream, an exact Euler solution)."""
+    X, Y, _ = point_coords(case)
+    xr = (X - t + case.lx / 2) % case.lx - case.lx / 2
+    yr = (Y + case.ly / 2) % case.ly - case.ly / 2
+    w2 = (xr * xr + yr * yr) / (R * R)
+    g = np.exp(-0.5 * w2)
+    rho = np.ones_like(X)
+    u = 1.0 - beta * yr / (R * R) * g
+    v = beta * xr / (R * R) * g
+    p = 1.0 / (case.gamma * case.mach ** 2) - rho * beta ** 2 / (2 * R * R) * g * g
+    return conserved(case, rho, u, v, np.zeros_like(X), p)
+
+
 def tgv_case(n: int = 128, p: int = 4, algo: str = "SA", **kw) -> Case:
     """3-D Taylor-Green vortex, Navier-Stokes, Re 1600, Mach 0.1, gamma 1.4, Pr 0.71, periodic
     [0, 2 pi]^3, n^3, p^3 sub-domains, LSERK4-CD4-AT4, tenth-order filter alpha_f = 0.499."""

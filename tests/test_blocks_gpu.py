@@ -190,11 +190,12 @@ def test_fp64_power_within_a_few_ulp():
         y = yt.cpu().numpy()
         ref = np.power(x, a)
         cuda_ref = torch.pow(xt, a).cpu().numpy()
-        ok = np.isfinite(ref) & (ref > 0) & (ref < 1e300) & (x > 2.3e-308) & np.isfinite(x)
+        normal = (x >= 2.2250738585072014e-308) & np.isfinite(x)
+        ok = normal & np.isfinite(ref) & (ref > 0) & (ref < 1e300)
         bound = 4.5e-16 * (1.0 + np.abs(a * np.log(x[ok])))
         assert np.all(np.abs(y[ok] / ref[ok] - 1.0) <= bound), a
         assert np.all(np.abs(y[ok] / cuda_ref[ok] - 1.0) <= bound + 2.3e-16), a
         near = ok & (np.abs(x - 1.0) < 0.5)
         assert np.max(np.abs(y[near] / ref[near] - 1.0)) < 1e-15, a
-        assert np.array_equal(np.isinf(y), np.isinf(ref)) and np.array_equal(y[~ok & np.isfinite(ref)],
-                                                                            cuda_ref[~ok & np.isfinite(ref)])
+        # zero, subnormal and infinite x go to CUDA's pow
+        assert np.array_equal(np.isinf(y), np.isinf(ref)) and np.array_equal(y[~normal], cuda_ref[~normal])

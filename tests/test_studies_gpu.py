@@ -21,3 +21,26 @@ def test_async_error_grows_with_the_delay():
     assert E[-1] < 0.1 * r["sa_error"], r             # asynchrony error stays below the scheme's own
     g, res = studies.cubic_fit(r["L"], E)
     assert res < 0.1, (g, res)                        # a cubic in L describes it
+
+
+def test_paper_vortex_orders_of_table1():
+    """The paper's own vortex test (Sec. 5.1): one advection cycle of the Gaussian vortex with
+    three PEs and L = 8 at the paper's time steps.  Between n = 120 and 240 the density error
+    falls at the orders Table 1 states: 2 (SA, AT2) and 4 (SA, AT4) for LSERK2/CD2 and
+    LSERK4/CD4, and about 1 for the standard schemes on delayed data (AS), whose error is the
+    largest of each group."""
+    ensure_built()
+    from paper_2506_03027_gb300 import studies
+    r = studies.paper_vortex_errors(ns=(120, 240), seeds=(1, 2))
+    print(r)
+    by = {(row["case"], row["algorithm"]): row for row in r["rows"]}
+    for (case, algo), row in by.items():
+        p = row["orders"][0]
+        assert np.all(np.isfinite(row["errors"])), row
+        if row["expected_order"] == 1:
+            assert 0.6 <= p <= 1.6, row
+        else:
+            assert p >= row["expected_order"] - 0.4, row
+    for sa, asy in ((1, 2), (4, 5)):
+        for algo in ("CAA-AS", "SAA-AS"):
+            assert by[(asy, algo)]["errors"][-1] > by[(sa, "SA")]["errors"][-1], (asy, algo)
