@@ -207,6 +207,24 @@ def saa_delays(case: Case, nsteps: int, kmax: int | None = None, seed: int | Non
 
 # ---------------------------------------------------------------- the paper-shaped workloads
 
+def saa_delays_arrival(case: Case, nsteps: int, L: int, p_late: float = 0.6, seed: int | None = None) -> np.ndarray:
+    """SAA delays with the time structure of Alg. 3 (int8 [nsteps][nsub][6]): per (sub-domain,
+    face) the newest visible level either stays one more step -- the delay grows by one, with
+    probability p_late -- or a message arrives and the delay drops to 0; a delay that would reach
+    L is reset by the local synchronization Alg. 3 forces.  The visible levels are therefore
+    always consecutive, and the delays follow a geometric law truncated at L - 1 (mean about
+    p_late / (1 - p_late) = 1.5 for p_late = 0.6: smaller delays more likely, a mean between 1 and
+    2 levels, as the measured delay distributions of Sec. 5.3 show)."""
+    rng = np.random.default_rng(case.seed if seed is None else seed)
+    k = np.zeros((case.nsub, 6), dtype=np.int64)
+    out = np.zeros((nsteps, case.nsub, 6), dtype=np.int8)
+    for n in range(nsteps):
+        late = rng.random((case.nsub, 6)) < p_late
+        k = np.where(late & (k + 1 <= L - 1), k + 1, 0)
+        out[n] = k
+    return out
+
+
 def vortex_case(n: int = 64, p: int = 2, **kw) -> Case:
     """2-D isentropic vortex, Euler, gamma 1.4, strength 5, Mach 0.5, periodic [-5,5]^2, n x n,
     p x p sub-domains, synchronous halos, LSERK4-CD4 (Table 1 case 4)."""
