@@ -60,12 +60,12 @@ def sub_delays(mb, n):
 @pytest.mark.parametrize("algo", ["SA", "CAA", "SAA"])
 def test_cgrid_parity(algo):
     """The reduced 12-block NACA0012 C-grid (walls, wake cut, far field, outflows, inner/outer
-    layers of different spanwise counts), 30 steps; each block against the oracle, and the
+    layers of different spanwise counts), 50 steps; each block against the oracle, and the
     diagnostics (volume-weighted K, enstrophy away from non-periodic faces, totals)."""
     mb, U0 = cgrid(algo)
     if algo == "CAA":
         mb = mb.replace_all(caa_L=3, kmax=2)
-    n = 30
+    n = 50
     d = sub_delays(mb, n) if algo == "SAA" else None
     Ug, dg = run_mb(mb, U0, n, delays=d, diag=True)
     Uo, do = orc.run(mb, U0, n, delays=d, diag=True)

@@ -110,6 +110,22 @@ def test_full_size_tgv_saa_parity():
     check(Ug, Uo)
 
 
+@pytest.mark.parametrize("algo,cfl", [("SA", 0.5), ("CAA", 0.25), ("SAA", 0.05)])
+def test_full_size_tgv_200_steps(algo, cfl):
+    """The Taylor-Green configuration's three runs at full size -- TGV 128^3 on 4x4x4 sub-domains,
+    filter on, (a) synchronous, (b) CAA with L = 4, (c) SAA with delays 0..3 -- for 200 steps at
+    the CFL numbers the benchmark runs them, whole fields against the oracle (about a minute of
+    host time each)."""
+    c = I.tgv_case(128, 4, algo)
+    c = c.replace(dt=I.cfl_dt(c, I.tgv_state(c), cfl))
+    nsteps = 200
+    d = I.saa_delays(c, nsteps) if algo == "SAA" else None
+    U0 = I.tgv_state(c)
+    Ug, _ = gpu_run(c, U0, nsteps, delays=d)
+    Uo = orc.run(c, U0, nsteps, delays=d)
+    check(Ug, Uo)
+
+
 def test_full_size_fp32_form_caa():
     """The precision configuration at its full size and launch shapes: TGV 256^3, 8x8x8
     sub-domains of 32^3, CAA L = 4, FP32 intermediates through the fused stage (tiles 32 x 16,
