@@ -868,6 +868,10 @@ static cfs_status enqueue_step(cfs_ctx* c, long long n, bool graph) {
           f.P[a] = b.P[a];
         }
         f.thomas = c->d_thomas; f.Lmax = c->Lmax; f.alpha = c->p.alpha_f;
+        {
+          const int ax = op - c->s, n3[3] = {b.nx, b.ny, b.nz};
+          f.Lt = (n3[ax] + b.P[ax] - 1) / b.P[ax];
+        }
         for (int m = 0; m < 6; ++m) f.h[m] = c->filt_h[m];
         f.b1 = c->filt_h[1] - c->p.alpha_f;
         f.only_sync = graph && c->fblock_n;

@@ -208,6 +208,7 @@ struct FilterLaunch {
   const int* axis_len[3];  // device: ... and its length
   const double* thomas;    // device: [Lmax+1 rows][2][Lmax] Thomas factors per line length
   int Lmax;
+  int Lt;                  // longest sub-domain line of this block along the pass axis (sizes the tiles)
   int P[3];                // sub-domains per axis
   double alpha;
   double h[6];             // filter right side: a_0, a_1/2, ..., a_5/2

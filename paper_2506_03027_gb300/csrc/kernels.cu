@@ -496,12 +496,12 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
   constexpr int f2 = (axis == 2) ? 1 : 2;
   const int n[3] = {f.nx, f.ny, f.nz};
   const long long strides[3] = {1, f.nx, (long long)f.nx * f.ny};
-  const FilterTile tl = filter_tile(f.Lmax);
+  const FilterTile tl = filter_tile(f.Lt);
   const int LN = tl.LN, TW = tl.TW;
   extern __shared__ __align__(16) double fsm[];
   double* tile = fsm;                                              // [LN][TW]: positions -5 .. len+4
   long long* sPos = reinterpret_cast<long long*>(fsm + (size_t)LN * TW);  // [TW]: offsets of the positions
-  float* fd = reinterpret_cast<float*>(fsm + (size_t)(LN + 1) * TW);      // FP32 form: [LN][Lmax+1]
+  float* fd = reinterpret_cast<float*>(fsm + (size_t)(LN + 1) * TW);      // FP32 form: [LN][Lt+1]
 
   const long long nl = (long long)n[f1] * n[f2];
   const int groups = (int)((nl + LN - 1) / LN);
@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
       // halo point, and the values enter as FP32 offsets from an FP64 reference of the line, so
       // FP32 rounding never acts on the full magnitude of the state.  Conversions run on the
       // integer pipe; the result U + d (FP64) replaces the value in slot i + 5.
-      float* frow = fd + line * (f.Lmax + 1);
+      float* frow = fd + line * (f.Lt + 1);
       const double ref = row[5];
       const float rh = d2f_fast(ref), rl = dev_fast(ref, rh, 0.f);
       float win[11];
@@ -742,10 +742,10 @@ int launch_filter(const Geometry& g, const StepSched& sc, const FilterLaunch& f,
   const int n[3] = {f.nx, f.ny, f.nz};
   const int f1 = (axis == 0) ? 1 : 0;
   const int f2 = (axis == 2) ? 1 : 2;
-  const FilterTile tl = filter_tile(f.Lmax);
+  const FilterTile tl = filter_tile(f.Lt);
   const long long nl = (long long)n[f1] * n[f2];
   const unsigned nb = (unsigned)(5LL * f.P[axis] * ((nl + tl.LN - 1) / tl.LN));
-  const size_t sm = filter_smem_bytes(f.Lmax, precision);
+  const size_t sm = filter_smem_bytes(f.Lt, precision);
   cudaStream_t st = (cudaStream_t)stream;
   if (tm) tm->rec(tm->self, 3, 1);
   if (precision == 1) {
