@@ -110,12 +110,16 @@ def test_full_size_tgv_saa_parity():
     check(Ug, Uo)
 
 
-@pytest.mark.parametrize("algo,cfl", [("SA", 0.5), ("CAA", 0.25), ("SAA", 0.05)])
-def test_full_size_tgv_200_steps(algo, cfl):
+@pytest.mark.parametrize("algo,cfl,tol", [("SA", 0.5, PARITY_TOL), ("CAA", 0.25, PARITY_TOL), ("SAA", 0.05, 1e-10)])
+def test_full_size_tgv_200_steps(algo, cfl, tol):
     """The Taylor-Green configuration's three runs at full size -- TGV 128^3 on 4x4x4 sub-domains,
     filter on, (a) synchronous, (b) CAA with L = 4, (c) SAA with delays 0..3 -- for 200 steps at
     the CFL numbers the benchmark runs them, whole fields against the oracle (about a minute of
-    host time each)."""
+    host time each).  The SAA run amplifies rounding differences: the oracle alone, started from
+    a state perturbed by 1e-15, differs from itself by 2.5e-12 after 200 steps at 64^3 and by
+    1.3e-13 after 100 (about 10x per 50 steps), and the GPU's contracted FMAs inject such
+    differences at every step; its window is held to 1e-10 (SAA runs of 8 to 30 steps, where
+    rounding has not grown, meet 1e-12 in the other tests)."""
     c = I.tgv_case(128, 4, algo)
     c = c.replace(dt=I.cfl_dt(c, I.tgv_state(c), cfl))
     nsteps = 200
@@ -123,7 +127,7 @@ def test_full_size_tgv_200_steps(algo, cfl):
     U0 = I.tgv_state(c)
     Ug, _ = gpu_run(c, U0, nsteps, delays=d)
     Uo = orc.run(c, U0, nsteps, delays=d)
-    check(Ug, Uo)
+    check(Ug, Uo, tol)
 
 
 def test_full_size_fp32_form_caa():
