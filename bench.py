@@ -47,16 +47,30 @@ FP64_FLOP_PER_CLK_SM = 4        # 2 FP64 FMA per clock per SM on GB300
 HBM_GBS_FALLBACK = 6800.0
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel kind, with the sha1 of
-# the kernel source they were taken from (null once the kernels change); filled from profiles/.
-TRAFFIC = {"source_sha1": "bc0833240b9555d6c2a5495a52f6caf09805d3e3",
+# the flux kernel's source they were taken from (kernels_sha1; null once it changes); filled
+# from profiles/.
+TRAFFIC = {"source_sha1": "5c111a48ebda02a60022a9a55094e22eca35f1b3",
            # k_flux<double,3>: 93.3 MB read + 78.8 MB written per launch in an ncu capture of the
            # 96^3 case (27 sub-domains of 32^3), x 64/27 for the 64 sub-domains of 128^3
            "bytes_per_launch": {"flux": 407.9e6}}
 
 
-def kernels_sha1() -> str:
-    with open(os.path.join(ROOT, "paper_2506_03027_gb300", "csrc", "kernels.cu"), "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()
+def kernels_sha1(root: str = ROOT) -> str:
+    """sha1 of the source the flux kernel is built from: its section of kernels.cu (from the k_flux
+    banner to the k_rk banner), the device helpers it includes, and the descriptors it reads
+    (Geometry, Physics, SubDev); other kernels' edits leave it unchanged."""
+    csrc = os.path.join(root, "paper_2506_03027_gb300", "csrc")
+    with open(os.path.join(csrc, "kernels.cu")) as f:
+        k = f.read()
+    a = k.index("// " + "-" * 79 + " k_flux")
+    b = k.index("// " + "-" * 79 + " k_rk")
+    with open(os.path.join(csrc, "device_common.cuh")) as f:
+        dc = f.read()
+    with open(os.path.join(csrc, "cfs_internal.h")) as f:
+        h = f.read()
+    structs = "".join(h[h.index("struct " + n + " {"):h.index("};", h.index("struct " + n + " {")) + 2]
+                      for n in ("SubDev", "Geometry", "Physics"))
+    return hashlib.sha1((k[a:b] + dc + structs).encode()).hexdigest()
 
 
 def measured_peaks():
