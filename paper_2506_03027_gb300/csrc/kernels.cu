@@ -480,9 +480,14 @@ __host__ __device__ inline FilterTile filter_tile(int Lmax) {
   return t;
 }
 
+// Shared memory of k_filter: the line tiles ([LN][TW] doubles, or floats in the FP32 form) and the
+// TW position offsets.
+__host__ __device__ inline size_t filter_tile_doubles(const FilterTile& t, int precision) {
+  return precision == 1 ? ((size_t)t.LN * t.TW + 1) / 2 : (size_t)t.LN * t.TW;
+}
 __host__ __device__ inline size_t filter_smem_bytes(int Lmax, int precision) {
   const FilterTile t = filter_tile(Lmax);
-  return (size_t)(t.LN + 1) * t.TW * 8 + (precision == 1 ? (size_t)t.LN * (Lmax + 1) * 4 : 0);
+  return (filter_tile_doubles(t, precision) + t.TW) * 8;
 }
 
 template <typename T, int axis>
@@ -499,9 +504,11 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
   const FilterTile tl = filter_tile(f.Lt);
   const int LN = tl.LN, TW = tl.TW;
   extern __shared__ __align__(16) double fsm[];
-  double* tile = fsm;                                              // [LN][TW]: positions -5 .. len+4
-  long long* sPos = reinterpret_cast<long long*>(fsm + (size_t)LN * TW);  // [TW]: offsets of the positions
-  float* fd = reinterpret_cast<float*>(fsm + (size_t)(LN + 1) * TW);      // FP32 form: [LN][Lt+1]
+  // [LN][TW] window slots (positions -5 .. len+4): FP64 values, or in the FP32 form FP32 offsets
+  // from the line's first own value (staged converted, so a line needs 4 bytes per slot)
+  double* tile = fsm;
+  float* ftile = reinterpret_cast<float*>(fsm);
+  long long* sPos = reinterpret_cast<long long*>(fsm + filter_tile_doubles(tl, F32 ? 1 : 0));  // [TW] offsets
 
   const long long nl = (long long)n[f1] * n[f2];
   const int groups = (int)((nl + LN - 1) / LN);
@@ -522,6 +529,7 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
   __shared__ long long sLev[(CFS_MAX_DELAY + 2) * CFS_MAX_LEVELS];
   __shared__ int sKd[2][128];
   __shared__ int sSid[128], sT1[128], sT2[128];  // blocks with a gather map: the line's sub-domain and position
+  __shared__ double sRef[128];                   // FP32 form: the line's first own value
   const bool gmap = f.ebase >= 0;
   for (int t = threadIdx.x; t < nlines; t += blockDim.x) {
     const long long t12 = l0 + t;
@@ -547,6 +555,7 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
     }
     sKd[0][t] = kl;
     sKd[1][t] = kr;
+    if (F32) sRef[t] = Uin[sBase[t] + (long long)off * st];
   }
   for (int t = threadIdx.x; t < W; t += blockDim.x) sPos[t] = (long long)wrapc(off + t - 5, n[axis]) * st;
   if (sc.mode != 0) {
@@ -559,64 +568,95 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
   __syncthreads();
 
   // ---- stage the windows: value at window slot i (position i - 5) of line `line`
-  auto stage = [&](int line, int i) {
-    const int pos = i - 5;
-    const long long gi = sBase[line] + sPos[i];
-    double* dst = tile + line * TW + i;
-    const int u = off + pos;  // block coordinate along the line
-    if (gmap && axis < 2 && (u < 0 || u >= n[axis])) {
-      // beyond a non-periodic block face: the face's sources -- own ones current, a neighbouring
-      // PE's by the mode, far-field constants
-      int cc[3];
-      cc[axis] = u;
-      cc[f1] = sT1[line];
-      cc[f2] = sT2[line];
-      const int ei = g.emap[f.ebase + (cc[0] + g.GE) + (long long)f.gmx * ((cc[1] + g.GE) + (long long)f.gmy * cc[2])];
-      const GatherEntry& E = g.gent[ei];
-      const int kd = sKd[pos < 0 ? 0 : 1][line];
-      double v = E.cst[var];
-      for (int t = 0; t < E.nt; ++t) {
-        const bool own = !(E.flags[t] & 2) && E.sid[t] == sSid[line];
-        const double sg = ((E.flags[t] & 1) && var >= 1 && var <= 3) ? -E.w[t] : E.w[t];
-        const long long o = E.off[t] + (long long)var * E.bN[t];
-        double x;
-        if (own || sc.mode == 0) {
-          x = Uin[o];
-        } else if (sc.mode == 2) {
-          x = f.ring[sLev[kd * sc.C] + o];
-        } else {
-          x = 0.0;
-          for (int l = 0; l < sc.C; ++l) x = fma(__ldg(sc.Wf + kd * sc.C + l), f.ring[sLev[kd * sc.C + l] + o], x);
-        }
-        v = fma(sg, x, v);
-      }
-      *dst = v;
-      return;
-    }
-    if ((pos >= 0 && pos < len) || sc.mode == 0) {
-      cp_async8(dst, Uin + gi);
-    } else {
-      const int kd = sKd[pos < 0 ? 0 : 1][line];
-      if (sc.mode == 2) {
-        cp_async8(dst, f.ring + sLev[kd * sc.C] + gi);
+  // beyond a non-periodic block face: the face's sources -- own ones current, a neighbouring PE's
+  // by the mode, far-field constants
+  auto gather_value = [&](int line, int pos, int u) -> double {
+    int cc[3];
+    cc[axis] = u;
+    cc[f1] = sT1[line];
+    cc[f2] = sT2[line];
+    const int ei = g.emap[f.ebase + (cc[0] + g.GE) + (long long)f.gmx * ((cc[1] + g.GE) + (long long)f.gmy * cc[2])];
+    const GatherEntry& E = g.gent[ei];
+    const int kd = sKd[pos < 0 ? 0 : 1][line];
+    double v = E.cst[var];
+    for (int t = 0; t < E.nt; ++t) {
+      const bool own = !(E.flags[t] & 2) && E.sid[t] == sSid[line];
+      const double sg = ((E.flags[t] & 1) && var >= 1 && var <= 3) ? -E.w[t] : E.w[t];
+      const long long o = E.off[t] + (long long)var * E.bN[t];
+      double x;
+      if (own || sc.mode == 0) {
+        x = Uin[o];
+      } else if (sc.mode == 2) {
+        x = f.ring[sLev[kd * sc.C] + o];
       } else {
-        double v = 0.0;  // extrapolation to t_{n+1} with weights c(k+1), in FP64
-        for (int l = 0; l < sc.C; ++l) v = fma(__ldg(sc.Wf + kd * sc.C + l), f.ring[sLev[kd * sc.C + l] + gi], v);
-        *dst = v;
+        x = 0.0;
+        for (int l = 0; l < sc.C; ++l) x = fma(__ldg(sc.Wf + kd * sc.C + l), f.ring[sLev[kd * sc.C + l] + o], x);
       }
+      v = fma(sg, x, v);
     }
+    return v;
+  };
+  // halo slot inside the block: SA the neighbour's value, AS the latest visible level, AT the
+  // extrapolation to t_{n+1} with the weights c(k+1), in FP64
+  auto halo_value = [&](int line, int pos, long long gi) -> double {
+    const int kd = sKd[pos < 0 ? 0 : 1][line];
+    if (sc.mode == 2) return f.ring[sLev[kd * sc.C] + gi];
+    double v = 0.0;
+    for (int l = 0; l < sc.C; ++l) v = fma(__ldg(sc.Wf + kd * sc.C + l), f.ring[sLev[kd * sc.C + l] + gi], v);
+    return v;
   };
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  if (axis == 0) {
-    // own points: a warp per line, lanes along it (contiguous in memory); the 10 window points
-    // outside the segment: a thread per line, so that no warp mixes copies with extrapolations
-    for (int line = warp; line < nlines; line += nwarp)
-      for (int i = 5 + lane; i < 5 + len; i += 32) cp_async8(tile + line * TW + i, Uin + sBase[line] + sPos[i]);
-    for (int line = threadIdx.x; line < nlines; line += blockDim.x)
-      for (int h = 0; h < 10; ++h) stage(line, h < 5 ? h : len + h);
-  } else {  // threads across lines (consecutive x)
-    for (int line = threadIdx.x; line < nlines; line += blockDim.x)
-      for (int i = 0; i < W; ++i) stage(line, i);
+  if (!F32) {
+    // FP64 values; plain copies of U or of one ring level through cp.async
+    auto stage = [&](int line, int i) {
+      const int pos = i - 5;
+      const long long gi = sBase[line] + sPos[i];
+      double* dst = tile + line * TW + i;
+      const int u = off + pos;
+      if (gmap && axis < 2 && (u < 0 || u >= n[axis])) *dst = gather_value(line, pos, u);
+      else if ((pos >= 0 && pos < len) || sc.mode == 0) cp_async8(dst, Uin + gi);
+      else if (sc.mode == 2) cp_async8(dst, f.ring + sLev[sKd[pos < 0 ? 0 : 1][line] * sc.C] + gi);
+      else *dst = halo_value(line, pos, gi);
+    };
+    if (axis == 0) {
+      // own points: a warp per line, lanes along it (contiguous in memory); the 10 window points
+      // outside the segment: a thread per line, so that no warp mixes copies with extrapolations
+      for (int line = warp; line < nlines; line += nwarp)
+        for (int i = 5 + lane; i < 5 + len; i += 32) cp_async8(tile + line * TW + i, Uin + sBase[line] + sPos[i]);
+      for (int line = threadIdx.x; line < nlines; line += blockDim.x)
+        for (int h = 0; h < 10; ++h) stage(line, h < 5 ? h : len + h);
+    } else {  // threads across lines (consecutive x)
+      for (int line = threadIdx.x; line < nlines; line += blockDim.x)
+        for (int i = 0; i < W; ++i) stage(line, i);
+    }
+  } else {
+    // FP32 form: every value converted on arrival to its offset from the line's first own value
+    // (dev_fast: the FP64 difference rounded once), so a slot is 4 bytes
+    auto value = [&](int line, int i) -> double {
+      const int pos = i - 5;
+      const long long gi = sBase[line] + sPos[i];
+      const int u = off + pos;
+      if (gmap && axis < 2 && (u < 0 || u >= n[axis])) return gather_value(line, pos, u);
+      if ((pos >= 0 && pos < len) || sc.mode == 0) return Uin[gi];
+      return halo_value(line, pos, gi);
+    };
+    auto put = [&](int line, int i, double v) {
+      const double ref = sRef[line];
+      const float rh = d2f_fast(ref), rl = dev_fast(ref, rh, 0.f);
+      ftile[line * TW + i] = dev_fast(v, rh, rl);
+    };
+    if (axis == 0) {
+      for (int line = warp; line < nlines; line += nwarp)
+        for (int i = 5 + lane; i < 5 + len; i += 32) put(line, i, Uin[sBase[line] + sPos[i]]);
+      for (int line = threadIdx.x; line < nlines; line += blockDim.x)
+        for (int h = 0; h < 10; ++h) {
+          const int i = h < 5 ? h : len + h;
+          put(line, i, value(line, i));
+        }
+    } else {
+      for (int line = threadIdx.x; line < nlines; line += blockDim.x)
+        for (int i = 0; i < W; ++i) put(line, i, value(line, i));
+    }
   }
   cp_async_commit();
   cp_async_wait_all();
@@ -662,15 +702,14 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
       // FP32 form: solve for the increment d = f^ - f.  Its right side is
       // (a_1/2 - alpha) D_1 + sum_{n>=2} (a_n/2) D_n with D_n = f_{i+n} + f_{i-n} - 2 f_i (exact
       // algebra, using sum a_n = 1 + 2 alpha), the Dirichlet closure becomes d = 0 at the first
-      // halo point, and the values enter as FP32 offsets from an FP64 reference of the line, so
-      // FP32 rounding never acts on the full magnitude of the state.  Conversions run on the
-      // integer pipe; the result U + d (FP64) replaces the value in slot i + 5.
-      float* frow = fd + line * (f.Lt + 1);
-      const double ref = row[5];
-      const float rh = d2f_fast(ref), rl = dev_fast(ref, rh, 0.f);
+      // halo point, and the values enter as the FP32 offsets staged from an FP64 reference of the
+      // line, so FP32 rounding never acts on the full magnitude of the state.  The forward sweep
+      // parks its d_i in slot i (no longer read), back substitution leaves the increment of point
+      // i there; the store adds it to the FP64 value.
+      float* frow = ftile + line * TW;
       float win[11];
 #pragma unroll
-      for (int m = 0; m < 11; ++m) win[m] = dev_fast(row[m], rh, rl);
+      for (int m = 0; m < 11; ++m) win[m] = frow[m];
       const float b1 = (float)f.b1, al32 = (float)f.alpha;
       float hm[6];
 #pragma unroll
@@ -687,14 +726,13 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
         dprev = dcur;
 #pragma unroll
         for (int m = 0; m < 10; ++m) win[m] = win[m + 1];
-        if (i + 11 < W) win[10] = dev_fast(row[i + 11], rh, rl);
+        if (i + 11 < W) win[10] = frow[i + 11];
       }
       float xnext = dprev;
-      row[len + 4] += f2d_fast(xnext);
       #pragma unroll 4
       for (int i = len - 2; i >= 0; --i) {
         const float x = frow[i] - d2f_fast(__ldg(cp + i)) * xnext;
-        row[i + 5] += f2d_fast(x);
+        frow[i] = x;
         xnext = x;
       }
     }
@@ -702,7 +740,6 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
   __syncthreads();
 
   // ---- store the own points; no-slip wall points keep zero momentum
-  const int slot0 = F32 ? 5 : 0;
   const bool wz = f.wall && var >= 1 && var <= 3;
   auto wall_pt = [&](int ln, int i) {
     const int u = off + i, a1 = sT1[ln], a2 = sT2[ln];
@@ -710,13 +747,24 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
            (((f.wall >> (2 * f1)) & 1) && a1 == 0) || (((f.wall >> (2 * f1 + 1)) & 1) && a1 == n[f1] - 1) ||
            (((f.wall >> (2 * f2)) & 1) && a2 == 0) || (((f.wall >> (2 * f2 + 1)) & 1) && a2 == n[f2] - 1);
   };
+  // the filtered value of point i: slot i (FP64), or the FP64 value plus the FP32 increment
+  auto result = [&](int ln, int i, long long gi) -> double {
+    if (wz && wall_pt(ln, i)) return 0.0;
+    if (F32) return Uin[gi] + f2d_fast(ftile[ln * TW + i]);
+    return tile[ln * TW + i];
+  };
   if (axis == 0) {
     for (int ln = warp; ln < nlines; ln += nwarp)
-      for (int i = lane; i < len; i += 32)
-        Uout[sBase[ln] + sPos[i + 5]] = (wz && wall_pt(ln, i)) ? 0.0 : tile[ln * TW + slot0 + i];
+      for (int i = lane; i < len; i += 32) {
+        const long long gi = sBase[ln] + sPos[i + 5];
+        Uout[gi] = result(ln, i, gi);
+      }
   } else {
     for (int ln = threadIdx.x; ln < nlines; ln += blockDim.x)
-      for (int i = 0; i < len; ++i) Uout[sBase[ln] + sPos[i + 5]] = (wz && wall_pt(ln, i)) ? 0.0 : tile[ln * TW + slot0 + i];
+      for (int i = 0; i < len; ++i) {
+        const long long gi = sBase[ln] + sPos[i + 5];
+        Uout[gi] = result(ln, i, gi);
+      }
   }
 }
 
