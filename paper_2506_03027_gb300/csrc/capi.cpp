@@ -69,6 +69,7 @@ struct cfs_ctx {
   std::vector<SubDev> subs;
   int max_pad = 0, max_own = 0, max_flux = 0;
   double* d_thomas = nullptr;
+  float* d_thomas32 = nullptr;
   int Lmax = 0;
   double filt_h[6] = {0};
   double* d_partial = nullptr;
@@ -593,10 +594,11 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   c->diag_blocks = 2 * 152;
   c->d_partial = (double*)dev_alloc(c, sizeof(double) * DIAG_NQ * c->diag_blocks * c->blocks.size());
   c->d_thomas = (double*)dev_alloc(c, sizeof(double) * (size_t)(c->Lmax + 1) * 2 * c->Lmax);
+  c->d_thomas32 = (float*)dev_alloc(c, sizeof(float) * (size_t)(c->Lmax + 1) * 2 * c->Lmax);
   for (void* q : c->owned)
     if (!q) return fail(c, CFS_ENOMEM, "device allocation failed");
   if (!c->d_n || !c->ring || !c->buf[0] || !c->buf[1] || !c->Q || (!c->fused && (!c->Wp || !c->Phi)) || !c->d_subs || !c->d_W || !c->d_Wf ||
-      !c->d_partial || !c->d_out || !c->d_thomas)
+      !c->d_partial || !c->d_out || !c->d_thomas || !c->d_thomas32)
     return fail(c, CFS_ENOMEM, "device allocation failed");
   for (const Block& b : c->blocks)
     for (int a = 0; a < 3; ++a)
@@ -656,6 +658,10 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   CUDA_TRY(c, cudaMemcpyAsync(c->d_W, W.data(), sizeof(double) * nW, cudaMemcpyHostToDevice, st), "upload weights");
   CUDA_TRY(c, cudaMemcpyAsync(c->d_Wf, Wf.data(), sizeof(double) * nWf, cudaMemcpyHostToDevice, st), "upload weights");
   CUDA_TRY(c, cudaMemcpyAsync(c->d_thomas, th.data(), sizeof(double) * th.size(), cudaMemcpyHostToDevice, st), "upload filter");
+  {
+    const int rc = cfs::launch_round_table(c->d_thomas, c->d_thomas32, (long long)th.size(), st);
+    if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "filter table");
+  }
   std::vector<std::vector<int>> keep;  // host tables stay alive until the stream is synchronised below
   for (Block& b : c->blocks) {
     const int n3[3] = {b.nx, b.ny, b.nz};
@@ -867,7 +873,7 @@ static cfs_status enqueue_step(cfs_ctx* c, long long n, bool graph) {
           f.owner[a] = b.d_owner[a]; f.axis_off[a] = b.d_axis_off[a]; f.axis_len[a] = b.d_axis_len[a];
           f.P[a] = b.P[a];
         }
-        f.thomas = c->d_thomas; f.Lmax = c->Lmax; f.alpha = c->p.alpha_f;
+        f.thomas = c->d_thomas; f.thomas32 = c->d_thomas32; f.Lmax = c->Lmax; f.alpha = c->p.alpha_f;
         {
           const int ax = op - c->s, n3[3] = {b.nx, b.ny, b.nz};
           f.Lt = (n3[ax] + b.P[ax] - 1) / b.P[ax];

@@ -207,6 +207,7 @@ struct FilterLaunch {
   const int* axis_off[3];  // device: per sub-domain index along the axis, its origin
   const int* axis_len[3];  // device: ... and its length
   const double* thomas;    // device: [Lmax+1 rows][2][Lmax] Thomas factors per line length
+  const float* thomas32;   // device: the same table rounded to FP32 (d2f_fast), for the FP32 form
   int Lmax;
   int Lt;                  // longest sub-domain line of this block along the pass axis (sizes the tiles)
   int P[3];                // sub-domains per axis
@@ -235,7 +236,8 @@ bool filter_block_supported(int n);
 int launch_filter_block(const Geometry& g, const StepSched& sc, const FilterBlockLaunch& f, int n, void* stream,
                         long long* launches, const Timer* tm);
 
-int filter_prepare(int Lmax, int precision);  // shared-memory attribute of the filter kernels; nonzero if too long
+int filter_prepare(int Lmax, int precision);
+int launch_round_table(const double* x, float* y, long long n, void* stream);  // y = d2f_fast(x)  // shared-memory attribute of the filter kernels; nonzero if too long
 int launch_filter(const Geometry& g, const StepSched& sc, const FilterLaunch& f, int axis, int precision,
                   void* stream, long long* launches, const Timer* tm);
 

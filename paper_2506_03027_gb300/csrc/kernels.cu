@@ -707,6 +707,8 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
       // parks its d_i in slot i (no longer read), back substitution leaves the increment of point
       // i there; the store adds it to the FP64 value.
       float* frow = ftile + line * TW;
+      const float* cp32 = f.thomas32 + (long long)len * 2 * f.Lmax;  // the factors in FP32
+      const float* im32 = cp32 + f.Lmax;
       float win[11];
 #pragma unroll
       for (int m = 0; m < 11; ++m) win[m] = frow[m];
@@ -721,7 +723,7 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
         float rhs = b1 * (win[6] + win[4] - c2);
 #pragma unroll
         for (int m = 2; m <= 5; ++m) rhs = fmaf(hm[m], win[5 + m] + win[5 - m] - c2, rhs);
-        const float dcur = (i == 0 ? rhs : rhs - al32 * dprev) * d2f_fast(__ldg(im + i));
+        const float dcur = (i == 0 ? rhs : rhs - al32 * dprev) * __ldg(im32 + i);
         frow[i] = dcur;
         dprev = dcur;
 #pragma unroll
@@ -731,7 +733,7 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
       float xnext = dprev;
       #pragma unroll 4
       for (int i = len - 2; i >= 0; --i) {
-        const float x = frow[i] - d2f_fast(__ldg(cp + i)) * xnext;
+        const float x = frow[i] - __ldg(cp32 + i) * xnext;
         frow[i] = x;
         xnext = x;
       }
@@ -766,6 +768,16 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
         Uout[gi] = result(ln, i, gi);
       }
   }
+}
+
+__global__ void k_round_table(const double* __restrict__ x, float* __restrict__ y, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = d2f_fast(x[i]);
+}
+
+int launch_round_table(const double* x, float* y, long long n, void* stream) {
+  if (n > 0) k_round_table<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, y, n);
+  return (int)cudaGetLastError();
 }
 
 int filter_prepare(int Lmax, int precision) {
