@@ -18,6 +18,17 @@ Metric: point-RK-stage updates per second (Mpoint-stage/s) = 128^3 x 5 x steps /
             event-timed launch duration) against the GB300 FP64 peak.
   cpu_baseline  the FP64 CPU oracle on the host cores on a bounded sample of the workload.
 
+forms (same metric, one GPU; each a dict in the JSON line):
+  fp32_intermediates, fp32_intermediates_256   the precision form (FP32 derivative / flux / filter
+            intermediates, FP64 state and AT application) at 128^3 and at 256^3 with CAA L = 4,
+            with its error against the FP64 path;
+  batched_blocks[_curvilinear][_fp32_intermediates]   12 independent periodic blocks of the
+            airfoil grid's uneven sizes (20.8 M points) in one context, CUDA graph, autotuned;
+  cgrid_naca0012[_fp32_intermediates]   the connected 12-block NACA0012 C-grid (22.0 M points:
+            wake cut, walls, far field, outflows, spanwise interpolation), SAA 0..2, CUDA graph;
+  learned_halo   the learned stage-0 halo against the plain AT extrapolation;
+  algorithms     SA, CAA and SAA with the fourth- and second-order schemes on the 128^3 grid.
+
 --impl reference times the oracle itself (the CPU program the GPU path is checked against) on
 the same configuration and metric; under torchrun only rank 0 runs it.
 """
