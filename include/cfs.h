@@ -122,6 +122,16 @@ cfs_status cfs_connect(cfs_ctx* ctx, int blockA, int faceA, int blockB, int face
  * periodic direction).  Call after cfs_connect; EINVAL if the face is not an interface. */
 cfs_status cfs_set_face_shift(cfs_ctx* ctx, int block, int face, const double* shift);
 
+/* The sources of the state the kernels take at point (i, j, k) of `block`'s index space (a point
+ * up to the halo depth beyond its faces), for inspecting a multi-block description: the faces are
+ * validated as at cfs_finalize (which need not have been called).  out[34] (host): out[0] the
+ * number of sources (up to 4), out[1..5] the far-field constant added to the conserved values,
+ * then per source 7 values: block, i, j, k, weight, mirrored (momentum negated), crossed (reached
+ * through a periodic wrap or an interface: a neighbouring PE's value).  Value v of the point =
+ * out[1 + v] + sum over sources of weight * (mirrored and 1 <= v <= 3 ? -1 : 1) * U_v(source).
+ * EINVAL for a bad block, a point beyond the halo depth or an invalid face description. */
+cfs_status cfs_halo_sources(cfs_ctx* ctx, int block, int i, int j, int k, double* out);
+
 /* Physical boundary condition on x or y face `face` of `block`:
  *   CFS_BC_WALL      no-slip adiabatic wall: the points on the face are wall points, whose
  *                    momentum is held at zero; beyond the face the state is mirrored about it

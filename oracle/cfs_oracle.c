@@ -1573,6 +1573,38 @@ int or_rhs(const or_params* p, const double* U, double* Rout) {
   return 0;
 }
 
+/* Sources of the points ijk[npts][3] of block b (beyond its faces) as the oracle resolves them,
+ * for cross-checking another implementation: per point 34 values -- count, far-field constant
+ * [5], then per source block, i, j, k, weight, mirrored, crossed (7 values, up to OR_MAXT
+ * sources).  Returns nonzero for an invalid description or a point that does not resolve. */
+int or_halo_sources(const or_params* p, int b, long npts, const int* ijk, double* outs) {
+  const int r = (p->order == 4) ? 2 : 1;
+  const int g = p->viscous ? 2 * r : r;
+  topo_t T;
+  int rc = topo_build(p, g, g, &T);
+  if (rc == 0 && (b < 0 || b >= T.nb)) rc = 21;
+  for (long q = 0; rc == 0 && q < npts; ++q) {
+    const int i = ijk[3 * q], j = ijk[3 * q + 1], k = ijk[3 * q + 2];
+    double* out = outs + 34 * q;
+    or_term t[OR_MAXT];
+    double cst[NV];
+    const int n = resolve_state(&T, b, i, j, k, t, cst);
+    if (n < 0) rc = 22;
+    else {
+      out[0] = n;
+      for (int v = 0; v < NV; ++v) out[1 + v] = cst[v];
+      for (int m = 0; m < OR_MAXT; ++m) {
+        double* o = out + 6 + 7 * m;
+        if (m >= n) { for (int q = 0; q < 7; ++q) o[q] = 0.0; continue; }
+        o[0] = t[m].b; o[1] = t[m].i; o[2] = t[m].j; o[3] = t[m].k;
+        o[4] = t[m].w; o[5] = t[m].flip; o[6] = t[m].crossed;
+      }
+    }
+  }
+  topo_free(&T);
+  return rc;
+}
+
 int or_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -92,6 +92,8 @@ def _load():
             lib.or_bf16.restype = ctypes.c_double
             lib.or_mlp_forward.argtypes = [ctypes.POINTER(ctypes.c_float), d, d]
             lib.or_set_num_threads.argtypes = [ctypes.c_int]
+            lib.or_halo_sources.argtypes = [P(OrParams), ctypes.c_int, ctypes.c_long, P(ctypes.c_int), d]
+            lib.or_halo_sources.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -269,3 +271,20 @@ def mlp_forward_c(params: np.ndarray, x: np.ndarray) -> np.ndarray:
     y = np.zeros(20)
     _load().or_mlp_forward(p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _dptr(xx), _dptr(y))
     return y
+
+
+def halo_sources(case, block: int, points):
+    """Per point (i, j, k) of ``points`` beyond a block face: (constant[5], [(block, i, j, k, weight,
+    mirrored, crossed), ...]) as the oracle resolves it."""
+    p = params(case)
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.int32).reshape(-1, 3))
+    out = np.zeros((len(pts), 34))
+    if _load().or_halo_sources(ctypes.byref(p), block, len(pts), pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                               _dptr(out)) != 0:
+        raise ValueError("oracle rejected a point or the description")
+    res = []
+    for row in out:
+        n = int(row[0])
+        terms = [tuple(row[6 + 7 * t: 13 + 7 * t]) for t in range(n)]
+        res.append((row[1:6].copy(), [(int(a), int(b), int(c), int(d), w, int(f), int(x)) for a, b, c, d, w, f, x in terms]))
+    return res

@@ -79,6 +79,7 @@ def load() -> ctypes.CDLL:
             "cfs_set_bc": ([vp, ip, ip, ip, dp], ip),
             "cfs_set_face_shift": ([vp, ip, ip, dp], ip),
             "cfs_eval_power": ([vp, ctypes.c_double, vp, ll, vp], ip),
+            "cfs_halo_sources": ([vp, ip, ip, ip, ip, dp], ip),
             "cfs_finalize": ([vp, ip], ip),
             "cfs_set_schedule": ([vp, ip, ip, ip, ll, ctypes.POINTER(ctypes.c_int8)], ip),
             "cfs_set_state": ([vp, ip, vp, ip], ip),
@@ -168,6 +169,16 @@ def cfs_eval_power(x, a: float, y, stream: int | None = None):
                                ctypes.c_void_p(stream or 0))
     if st != CFS_OK:
         raise CfsError(st, "cfs_eval_power failed")
+
+
+def cfs_halo_sources(ctx, block: int, i: int, j: int, k: int):
+    """(constant[5], [(block, i, j, k, weight, mirrored, crossed), ...]) of a point beyond a block
+    face, as the kernels gather it."""
+    out = np.zeros(34)
+    _check(ctx, load().cfs_halo_sources(ctx, block, i, j, k, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    n = int(out[0])
+    terms = [tuple(out[6 + 7 * t: 13 + 7 * t]) for t in range(n)]
+    return out[1:6].copy(), [(int(a), int(b), int(c), int(d), w, int(f), int(x)) for a, b, c, d, w, f, x in terms]
 
 
 BC_PERIODIC, BC_WALL, BC_FARFIELD, BC_OUTFLOW = 0, 1, 2, 3
@@ -389,6 +400,30 @@ class TorchAllocator:
         self.live.pop(ptr, None)
 
 
+def describe_blocks(ctx, blocks, mb=None):
+    """Add the blocks (sizes, splits, curvilinear grids) to a context and, for an
+    ``inputs.MultiBlock``, their interfaces and boundary conditions (cfs_connect, cfs_set_bc,
+    cfs_set_face_shift)."""
+    for i, b in enumerate(blocks):
+        bid = cfs_add_block(ctx, b.nx, b.ny, b.nz, (b.dx, b.dy, b.dz))
+        cfs_split_block(ctx, bid, b.px, b.py, b.pz)
+        gxy = grid_xy(b) if mb is None else mb.xy[i]
+        if gxy is not None:
+            cfs_set_block_grid(ctx, bid, gxy[0], gxy[1])
+    if mb is not None:
+        bc = {"wall": BC_WALL, "farfield": BC_FARFIELD, "outflow": BC_OUTFLOW}
+        for i, faces in enumerate(mb.faces):
+            for f, F in enumerate(faces):
+                if F.type == "interface" and (i, f) < (F.nb, F.nf):
+                    cfs_connect(ctx, i, f, F.nb, F.nf, int(F.rev))
+                elif F.type in bc:
+                    cfs_set_bc(ctx, i, f, bc[F.type], F.state if F.type == "farfield" else None)
+        for i, faces in enumerate(mb.faces):
+            for f, F in enumerate(faces):
+                if F.type == "interface" and any(F.shift):
+                    cfs_set_face_shift(ctx, i, f, F.shift)
+
+
 class Solver:
     """A context on the current CUDA device and stream for one periodic block (``case``), for a
     batch of independent periodic blocks (``blocks``: cases sharing the physics and scheme of the
@@ -414,24 +449,7 @@ class Solver:
         if use_torch_allocator:
             self.alloc = TorchAllocator(self.device)
             cfs_set_allocator(self.ctx, self.alloc.alloc_cb, self.alloc.free_cb)
-        for i, b in enumerate(self.blocks):
-            bid = cfs_add_block(self.ctx, b.nx, b.ny, b.nz, (b.dx, b.dy, b.dz))
-            cfs_split_block(self.ctx, bid, b.px, b.py, b.pz)
-            gxy = grid_xy(b) if mb is None else mb.xy[i]
-            if gxy is not None:
-                cfs_set_block_grid(self.ctx, bid, gxy[0], gxy[1])
-        if mb is not None:
-            bc = {"wall": BC_WALL, "farfield": BC_FARFIELD, "outflow": BC_OUTFLOW}
-            for i, faces in enumerate(mb.faces):
-                for f, F in enumerate(faces):
-                    if F.type == "interface" and (i, f) < (F.nb, F.nf):
-                        cfs_connect(self.ctx, i, f, F.nb, F.nf, int(F.rev))
-                    elif F.type in bc:
-                        cfs_set_bc(self.ctx, i, f, bc[F.type], F.state if F.type == "farfield" else None)
-            for i, faces in enumerate(mb.faces):
-                for f, F in enumerate(faces):
-                    if F.type == "interface" and any(F.shift):
-                        cfs_set_face_shift(self.ctx, i, f, F.shift)
+        describe_blocks(self.ctx, self.blocks, mb)
         if tiles is not None:
             cfs_set_tiles(self.ctx, *tiles)
         if max_delay is None:

@@ -318,6 +318,36 @@ cfs_status cfs_set_face_shift(cfs_ctx* c, int block, int face, const double* shi
   return CFS_OK;
 }
 
+cfs_status cfs_halo_sources(cfs_ctx* c, int block, int i, int j, int k, double* out) {
+  if (!c || !out) return CFS_EINVAL;
+  if (block < 0 || block >= (int)c->blocks.size()) return fail(c, CFS_EINVAL, "unknown block");
+  std::vector<cfs::TopoBlock> topo(c->blocks.size());
+  int sid0 = 0;
+  long long base = 0;
+  for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
+    const Block& b = c->blocks[bi];
+    cfs::TopoBlock& t = topo[bi];
+    t.n[0] = b.nx; t.n[1] = b.ny; t.n[2] = b.nz;
+    for (int a = 0; a < 3; ++a) t.P[a] = b.P[a];
+    t.sid0 = sid0;
+    t.base = base;
+    t.N = b.N;
+    t.xy = b.xy.empty() ? nullptr : b.xy.data();
+    for (int q = 0; q < 4; ++q) t.shift[q] = b.shift[q];
+    for (int f = 0; f < 6; ++f) t.face[f] = b.face[f];
+    sid0 += b.P[0] * b.P[1] * b.P[2];
+    base += 5 * b.N;
+  }
+  if (const char* why = cfs::topo_check(topo.data(), (int)topo.size())) return fail(c, CFS_EINVAL, why);
+  const Block& b = c->blocks[block];
+  const int G = c->p.filter ? std::max(c->G, 5) : c->G;
+  if (i < -G || i >= b.nx + G || j < -G || j >= b.ny + G || k < -G || k >= b.nz + G)
+    return fail(c, CFS_EINVAL, "point farther than the halo depth from the block");
+  if (cfs::halo_sources(topo.data(), (int)topo.size(), block, i, j, k, out) < 0)
+    return fail(c, CFS_EINVAL, "the point does not resolve");
+  return CFS_OK;
+}
+
 cfs_status cfs_set_bc(cfs_ctx* c, int block, int face, int type, const double* data) {
   if (!c) return CFS_EINVAL;
   if (c->finalized) return fail(c, CFS_ESTATE, "boundary conditions before cfs_finalize");

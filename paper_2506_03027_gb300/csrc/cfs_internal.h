@@ -152,6 +152,9 @@ struct TopoBlock {
 // topology.cpp
 const char* topo_check(const TopoBlock* B, int nb);  // null when valid, else the reason
 bool topo_periodic(const TopoBlock& b);
+// Sources of point (i, j, k) of block b's index space, for inspection: out[0] = count, out[1..5]
+// the far-field constant, then per source (up to 4) block, i, j, k, weight, mirrored, crossed.
+int halo_sources(const TopoBlock* B, int nb, int b, int i, int j, int k, double* out);
 // Gather entry of point (i, j, k) of block b's index space; false if it does not resolve.
 bool gather_entry(const TopoBlock* B, int nb, int b, int i, int j, int k, GatherEntry* e);
 // Metric plane [NMETRIC][(nx + 2G)(ny + 2G)] of curvilinear block b; false if the grid does not

@@ -212,6 +212,29 @@ const char* topo_check(const TopoBlock* B, int nb) {
   return nullptr;
 }
 
+int halo_sources(const TopoBlock* B, int nb, int b, int i, int j, int k, double* out) {
+  (void)nb;
+  Src s[GATHER_MAXT];
+  s[0].b = b;
+  s[0].c[0] = i; s[0].c[1] = j; s[0].c[2] = k;
+  s[0].flip = 0; s[0].crossed = 0; s[0].w = 1.0;
+  double cst[5] = {0, 0, 0, 0, 0};
+  const int n = resolve(B, s, 1, cst);
+  if (n < 0) return -1;
+  out[0] = n;
+  for (int v = 0; v < 5; ++v) out[1 + v] = cst[v];
+  for (int t = 0; t < GATHER_MAXT; ++t) {
+    double* o = out + 6 + 7 * t;
+    if (t >= n) {
+      for (int q = 0; q < 7; ++q) o[q] = 0.0;
+      continue;
+    }
+    o[0] = s[t].b; o[1] = s[t].c[0]; o[2] = s[t].c[1]; o[3] = s[t].c[2];
+    o[4] = s[t].w; o[5] = s[t].flip; o[6] = s[t].crossed;
+  }
+  return n;
+}
+
 bool gather_entry(const TopoBlock* B, int nb, int b, int i, int j, int k, GatherEntry* e) {
   (void)nb;
   Src s[GATHER_MAXT];

@@ -168,3 +168,61 @@ def test_topology_validation_at_finalize(lib):
     st, msg = attempt(curv_to_cart)
     assert st == cfs.CFS_EINVAL and "curvilinear" in msg
 
+
+
+def _ctx_for(mb):
+    c = mb.case
+    p = cfs.CfsParams(order=c.order, viscous=int(c.viscous), visc_law=c.visc_law, visc_exp=c.visc_exp,
+                      gamma=c.gamma, mach=c.mach, re=c.re, pr=c.pr, filter=int(c.filter), alpha_f=c.alpha_f)
+    ctx = cfs.cfs_create(p)
+    cfs.describe_blocks(ctx, mb.blocks, mb)
+    return ctx
+
+
+@pytest.mark.parametrize("topology", ["cgrid", "rotated", "span", "channel"])
+def test_halo_sources_match_the_oracle(lib, topology):
+    """The library's host resolution of the points beyond non-periodic block faces (the gather
+    entries its kernels read: sources, weights, mirror and crossing flags, far-field constants)
+    agrees, point by point, with the oracle's independent resolution -- on the reduced C-grid
+    (wake cut, walls, far field, outflows, spanwise interpolation), a 180-degree rotated block, a
+    spanwise-interpolated pair and a wall channel; faces to the filter's depth 5, corners to r x r.
+    No device is touched: the faces are validated and resolved on the host."""
+    from paper_2506_03027_gb300 import inputs as I
+    if topology == "cgrid":
+        mb = I.naca_cgrid(I.cgrid_reduced())
+    elif topology == "rotated":
+        c = I.tgv_case(24, 2, "CAA", filter=True, curv=0.2).replace(px=3)
+        mb = I.rotated_pair(c, 16, 2, 1)
+    elif topology == "span":
+        mb = I.span_pair(I.tgv_case(24, 2, "SAA", kmax=2, filter=True).replace(px=3), 16, 12, 2, 1)
+    else:
+        mb = I.wall_channel(I.tgv_case(20, 2, "SAA", kmax=2, filter=True).replace(ny=21, py=3, ly=2.0))
+    ctx = _ctx_for(mb)
+    try:
+        n = 0
+        for bi, b in enumerate(mb.blocks):
+            nonper = [F.type != "periodic" for F in mb.faces[bi]]
+            pts = []
+            for k in range(b.nz):
+                for j in range(-5, b.ny + 5):
+                    for i in range(-5, b.nx + 5):
+                        di = -i if i < 0 else (i - b.nx + 1 if i >= b.nx else 0)
+                        dj = -j if j < 0 else (j - b.ny + 1 if j >= b.ny else 0)
+                        if (di == 0 and dj == 0) or (di and dj and (di > 2 or dj > 2)):
+                            continue
+                        if (di and nonper[0 if i < 0 else 1]) or (dj and nonper[2 if j < 0 else 3]):
+                            pts.append((i, j, k))
+            if not pts:
+                continue
+            ref = orc.halo_sources(mb, bi, pts)
+            for (i, j, k), (co, to) in zip(pts, ref):
+                cl, tl = cfs.cfs_halo_sources(ctx, bi, i, j, k)
+                assert np.array_equal(cl, co), (bi, i, j, k, cl, co)
+                key = lambda t: t[:4] + t[5:]
+                tl, to = sorted(tl, key=key), sorted(to, key=key)
+                assert [key(t) for t in tl] == [key(t) for t in to], (bi, i, j, k, tl, to)
+                assert np.allclose([t[4] for t in tl], [t[4] for t in to], rtol=0, atol=1e-15), (tl, to)
+                n += 1
+        assert n > 0
+    finally:
+        cfs.cfs_destroy(ctx)
