@@ -1,10 +1,11 @@
 /*
  * cfs.h -- C ABI of the GB300 asynchronous compressible flow solver library (libcfs.so).
  *
- * The library advances the compressible Navier-Stokes (or Euler) equations on a periodic uniform
- * Cartesian block split into sub-domains ("processing elements" of arXiv 2506.03027, Sec. 3),
- * with the asynchrony-tolerant (AT) halo treatment of Sec. 3.1-3.2 under the SA, CAA and SAA
- * algorithms of Alg. 1-3.  Every step of the hot path runs in the library's CUDA kernels for
+ * The library advances the compressible Navier-Stokes (or Euler) equations on blocks -- uniform
+ * Cartesian or curvilinear (App. A), periodic or joined by interfaces and bounded by walls, far
+ * fields and outflows (a multi-block grid such as the airfoil C-grid of Sec. 5.3) -- split into
+ * sub-domains ("processing elements" of arXiv 2506.03027, Sec. 3), with the asynchrony-tolerant
+ * (AT) halo treatment of Sec. 3.1-3.2 under the SA, CAA and SAA algorithms of Alg. 1-3.  Every step of the hot path runs in the library's CUDA kernels for
  * sm_103a; there is no CPU fallback: a call that needs the GPU fails with CFS_ECUDA when the
  * device or the kernels are unavailable.
  *
@@ -70,10 +71,10 @@ cfs_status cfs_create(const cfs_params* p, void* cuda_stream, cfs_ctx** out);
 cfs_status cfs_set_allocator(cfs_ctx* ctx, cfs_alloc_fn alloc, cfs_free_fn free_fn, void* user);
 
 /* Add a uniform Cartesian block of ni x nj x nk points with spacing {dx, dy, dz} (host array of
- * 3 doubles), periodic in every direction (each face connected to the opposite face of the same
- * block).  nk = 1 makes the run two-dimensional.  *block_id receives the index (0, 1, ... in the
- * order of the calls).  Several blocks of uneven sizes form a batch of independent problems that
- * advance together: every stage launch covers the sub-domains of all blocks, whose states are
+ * 3 doubles), periodic in every direction until connected (cfs_connect) or bounded (cfs_set_bc).
+ * nk = 1 makes the run two-dimensional.  *block_id receives the index (0, 1, ... in the order of
+ * the calls).  Several blocks of uneven sizes advance together -- independent problems, or one
+ * connected grid: every stage launch covers the sub-domains of all blocks, whose states are
  * stored one after another (block b at offset 5 x the points of blocks 0..b-1 in a state array).
  * All blocks share the physics, scheme, dt and schedule algorithm; they must all be 2-D or all
  * 3-D.  EINVAL for non-positive sizes or mixed dimensionality. */
@@ -83,10 +84,10 @@ cfs_status cfs_add_block(cfs_ctx* ctx, int ni, int nj, int nk, const double* spa
  * coordinates, fluxes of Eq. A2 with contravariant velocities, viscous terms of Eq. A3-A4 with
  * the chain rule through the metric terms).  The grid is a smooth mapping of the index plane
  * (i, j) extruded along z: xy is a HOST array [2][nj][ni] with x(i, j) then y(i, j); z = k dz
- * with dz the block's third spacing (unit depth in 2-D).  The block stays periodic in every
- * index direction: shift[0..1] is the (x, y) jump of the coordinates across the wrap in i,
- * shift[2..3] the jump across the wrap in j (for example (Lx, 0, 0, Ly) for a deformed
- * rectangle).  At cfs_finalize the library computes the metric terms xi^_x = J^-1 dxi/dx ...
+ * with dz the block's third spacing (unit depth in 2-D).  Across a periodic face shift[0..1] is
+ * the (x, y) jump of the coordinates across the wrap in i, shift[2..3] the jump across the wrap
+ * in j (for example (Lx, 0, 0, Ly) for a deformed rectangle); across an interface the grid
+ * continues into the neighbour, across a physical boundary it is reflected (cfs_set_bc).  At cfs_finalize the library computes the metric terms xi^_x = J^-1 dxi/dx ...
  * and J from the coordinates with the block's own CD scheme in index space (their cofactor
  * form keeps a uniform flow uniform to rounding); derivatives of the solution are then taken
  * in index space.  The data are copied.  Call after cfs_add_block, before cfs_finalize
