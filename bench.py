@@ -495,6 +495,8 @@ def cgrid_form(args, precision=0):
     from paper_2506_03027_gb300 import cfs
     from paper_2506_03027_gb300 import inputs as I
     spec = I.CGridSpec()
+    if getattr(args, "cgrid_half", False):
+        spec = I.CGridSpec(wake=48, aft=80, fore=256, nj_in=96, nj_out=32, nz_in=32, nz_out=16)
     mb = I.naca_cgrid(spec, algo="SAA", kmax=2)
     mb = mb.replace_all(dt=I.cgrid_dt(mb, 0.05))
     U0 = I.cgrid_state(mb, spec)
@@ -758,6 +760,8 @@ def main():
     ap.add_argument("--tiles", default="", help="fy,zc,threads launch shapes of the main path (profiling runs only)")
     ap.add_argument("--only-form", default="", choices=["", "cgrid_naca0012", "cgrid_naca0012_fp32_intermediates"],
                     help="run one form alone and print its result (profiling runs only; --tiles skips its autotuning)")
+    ap.add_argument("--cgrid-half", action="store_true",
+                    help="with --only-form: the C-grid at half the points per direction (profiling runs only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
