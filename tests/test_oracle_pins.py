@@ -390,3 +390,33 @@ def test_async_error_order_viscous_3d():
         e.append(max(math.sqrt(np.mean((runs[0][v] - runs[1][v]) ** 2)) for v in range(5)))
     rate = math.log2(e[0] / e[1])
     assert rate > 3.5, (e, rate)
+
+
+def test_paper_vortex_is_an_exact_solution():
+    """The paper's own vortex (Sec. 5.1; constant density, the printed pressure deficit) is an
+    exact Euler solution carried by the free stream: the SA scheme (CD4 / LSERK4) converges to it
+    at fourth order in the u-velocity.  With the pressure deficit's sign flipped the swirl is not
+    balanced: the error falls at less than second order and stays several times larger (the
+    check has teeth)."""
+    import math
+    from paper_2506_03027_gb300 import inputs as I
+
+    def err(n, flip=False):
+        c = I.paper_vortex_case(n, order=4, algo="SA").replace(px=1, py=1)
+        dt = 0.5 * (16.0 / n) / (1 + 1 / c.mach)
+        ns = int(math.ceil(1.0 / dt))
+        c = c.replace(dt=1.0 / ns)
+        U0 = I.paper_vortex_state(c)
+        ex = I.paper_vortex_state(c, t=1.0)
+        if flip:  # p = p_inf + (deficit) instead of p_inf - (deficit): rho E changes by 2 x deficit / (gamma - 1)
+            p_def = (1.0 / (c.gamma * c.mach ** 2)) - (U0[4] - 0.5 * (U0[1] ** 2 + U0[2] ** 2) / U0[0]) * (c.gamma - 1)
+            U0 = U0.copy()
+            U0[4] += 2 * p_def / (c.gamma - 1)
+        U = orc.run(c, U0, ns)
+        return float(np.sqrt(np.mean((U[1] / U[0] - ex[1] / ex[0]) ** 2)))
+
+    e = [err(n) for n in (24, 48, 96)]
+    orders = [math.log(e[i] / e[i + 1], 2) for i in range(2)]
+    assert orders[-1] > 3.6, (e, orders)
+    f = [err(n, flip=True) for n in (48, 96)]
+    assert math.log(f[0] / f[1], 2) < 2.0 and f[1] > 5 * e[-1], (f, e)
