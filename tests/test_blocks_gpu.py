@@ -199,3 +199,22 @@ def test_fp64_power_within_a_few_ulp():
         assert np.max(np.abs(y[near] / ref[near] - 1.0)) < 1e-15, a
         # zero, subnormal and infinite x go to CUDA's pow
         assert np.array_equal(np.isinf(y), np.isinf(ref)) and np.array_equal(y[~normal], cuda_ref[~normal])
+
+
+def test_connected_grid_rejects_the_learned_halo():
+    """The learned halo model is built on periodic face columns: a context with non-periodic
+    block faces refuses it (EINVAL) and keeps running the plain AT halo."""
+    mb, U0 = cgrid("SAA")
+    s = cfs.Solver(mb)
+    try:
+        params = np.zeros(9684, dtype=np.float32)
+        scales = np.ones(15)
+        with pytest.raises(cfs.CfsError) as e:
+            cfs.cfs_set_halo_model(s.ctx, params, scales, True)
+        assert e.value.status == cfs.CFS_EINVAL and "periodic" in cfs.cfs_last_error(s.ctx)
+        s.set_schedule(delays=sub_delays(mb, 6))
+        s.set_states(U0)
+        s.step(6)
+        assert all(np.all(np.isfinite(u)) for u in s.get_states())
+    finally:
+        s.close()
