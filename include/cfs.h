@@ -133,6 +133,15 @@ cfs_status cfs_set_face_shift(cfs_ctx* ctx, int block, int face, const double* s
  * EINVAL for a bad block, a point beyond the halo depth or an invalid face description. */
 cfs_status cfs_halo_sources(cfs_ctx* ctx, int block, int i, int j, int k, double* out);
 
+/* The metric terms the kernels use at point (i, j) of curvilinear `block`'s plane (up to the halo
+ * depth beyond its faces; blocks are extruded, so every z has the same): out[7] (host) =
+ * {xi^_x, xi^_y, eta^_x, eta^_y, zeta^_z, J^-1, J} of App. A, from the grid continued across the
+ * faces (NaN beyond a non-periodic face deeper than the stencil radius, where no flux is
+ * evaluated).  For inspecting a grid before cfs_finalize; EINVAL for a Cartesian or unknown
+ * block, a point beyond the halo depth, an invalid face description or a grid with a
+ * non-positive cell volume. */
+cfs_status cfs_metric_terms(cfs_ctx* ctx, int block, int i, int j, double* out);
+
 /* Physical boundary condition on x or y face `face` of `block`:
  *   CFS_BC_WALL      no-slip adiabatic wall: the points on the face are wall points, whose
  *                    momentum is held at zero; beyond the face the state is mirrored about it

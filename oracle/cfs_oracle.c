@@ -1605,6 +1605,21 @@ int or_halo_sources(const or_params* p, int b, long npts, const int* ijk, double
   return rc;
 }
 
+/* Metric terms {xi^_x, xi^_y, eta^_x, eta^_y, zeta^_z, J^-1} at the points ij[npts][2] of curvilinear
+ * block b's extended plane, as the oracle computes them (for cross-checking another
+ * implementation); out[npts][6].  Returns nonzero for an invalid description or a Cartesian block. */
+int or_metric_terms(const or_params* p, int b, long npts, const int* ij, double* out) {
+  const int r = (p->order == 4) ? 2 : 1;
+  const int g = p->viscous ? 2 * r : r;
+  topo_t T;
+  int rc = topo_build(p, g, g, &T);
+  if (rc == 0 && (b < 0 || b >= T.nb || !T.M[b])) rc = 23;
+  for (long q = 0; rc == 0 && q < npts; ++q)
+    for (int c = 0; c < NM; ++c) out[NM * q + c] = metric_at(&T, b, c, ij[2 * q], ij[2 * q + 1]);
+  topo_free(&T);
+  return rc;
+}
+
 int or_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

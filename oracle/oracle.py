@@ -94,6 +94,8 @@ def _load():
             lib.or_set_num_threads.argtypes = [ctypes.c_int]
             lib.or_halo_sources.argtypes = [P(OrParams), ctypes.c_int, ctypes.c_long, P(ctypes.c_int), d]
             lib.or_halo_sources.restype = ctypes.c_int
+            lib.or_metric_terms.argtypes = [P(OrParams), ctypes.c_int, ctypes.c_long, P(ctypes.c_int), d]
+            lib.or_metric_terms.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -288,3 +290,16 @@ def halo_sources(case, block: int, points):
         terms = [tuple(row[6 + 7 * t: 13 + 7 * t]) for t in range(n)]
         res.append((row[1:6].copy(), [(int(a), int(b), int(c), int(d), w, int(f), int(x)) for a, b, c, d, w, f, x in terms]))
     return res
+
+
+def metric_terms(case, block: int, points) -> np.ndarray:
+    """[npts][6] metric terms (xi^_x, xi^_y, eta^_x, eta^_y, zeta^_z, J^-1) at (i, j) points of a
+    curvilinear block's extended plane, as the oracle computes them."""
+    p = params(case)
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.int32).reshape(-1, 2))
+    out = np.zeros((len(pts), 6))
+    if _load().or_metric_terms(ctypes.byref(p), block, len(pts), pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                               _dptr(out)) != 0:
+        raise ValueError("oracle rejected the block or the description")
+    return out
+

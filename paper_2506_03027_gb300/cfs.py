@@ -80,6 +80,7 @@ def load() -> ctypes.CDLL:
             "cfs_set_face_shift": ([vp, ip, ip, dp], ip),
             "cfs_eval_power": ([vp, ctypes.c_double, vp, ll, vp], ip),
             "cfs_halo_sources": ([vp, ip, ip, ip, ip, dp], ip),
+            "cfs_metric_terms": ([vp, ip, ip, ip, dp], ip),
             "cfs_finalize": ([vp, ip], ip),
             "cfs_set_schedule": ([vp, ip, ip, ip, ll, ctypes.POINTER(ctypes.c_int8)], ip),
             "cfs_set_state": ([vp, ip, vp, ip], ip),
@@ -179,6 +180,13 @@ def cfs_halo_sources(ctx, block: int, i: int, j: int, k: int):
     n = int(out[0])
     terms = [tuple(out[6 + 7 * t: 13 + 7 * t]) for t in range(n)]
     return out[1:6].copy(), [(int(a), int(b), int(c), int(d), w, int(f), int(x)) for a, b, c, d, w, f, x in terms]
+
+
+def cfs_metric_terms(ctx, block: int, i: int, j: int) -> np.ndarray:
+    """xi^_x, xi^_y, eta^_x, eta^_y, zeta^_z, J^-1, J at (i, j) of a curvilinear block's plane."""
+    out = np.zeros(7)
+    _check(ctx, load().cfs_metric_terms(ctx, block, i, j, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
 
 
 BC_PERIODIC, BC_WALL, BC_FARFIELD, BC_OUTFLOW = 0, 1, 2, 3

@@ -318,6 +318,47 @@ cfs_status cfs_set_face_shift(cfs_ctx* c, int block, int face, const double* shi
   return CFS_OK;
 }
 
+// The blocks' faces and grids as the host topology code sees them (validated); sid0 and base as
+// cfs_finalize assigns them.
+static const char* host_topology(cfs_ctx* c, std::vector<cfs::TopoBlock>& topo) {
+  topo.assign(c->blocks.size(), cfs::TopoBlock{});
+  int sid0 = 0;
+  long long base = 0;
+  for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
+    const Block& b = c->blocks[bi];
+    cfs::TopoBlock& t = topo[bi];
+    t.n[0] = b.nx; t.n[1] = b.ny; t.n[2] = b.nz;
+    for (int a = 0; a < 3; ++a) t.P[a] = b.P[a];
+    t.sid0 = sid0;
+    t.base = base;
+    t.N = b.N;
+    t.xy = b.xy.empty() ? nullptr : b.xy.data();
+    for (int q = 0; q < 4; ++q) t.shift[q] = b.shift[q];
+    for (int f = 0; f < 6; ++f) t.face[f] = b.face[f];
+    sid0 += b.P[0] * b.P[1] * b.P[2];
+    base += 5 * b.N;
+  }
+  return cfs::topo_check(topo.data(), (int)topo.size());
+}
+
+cfs_status cfs_metric_terms(cfs_ctx* c, int block, int i, int j, double* out) {
+  if (!c || !out) return CFS_EINVAL;
+  if (block < 0 || block >= (int)c->blocks.size()) return fail(c, CFS_EINVAL, "unknown block");
+  const Block& b = c->blocks[block];
+  if (b.xy.empty()) return fail(c, CFS_EINVAL, "the block is Cartesian");
+  if (i < -c->G || i >= b.nx + c->G || j < -c->G || j >= b.ny + c->G)
+    return fail(c, CFS_EINVAL, "point farther than the halo depth from the block");
+  std::vector<cfs::TopoBlock> topo;
+  if (const char* why = host_topology(c, topo)) return fail(c, CFS_EINVAL, why);
+  const int mx = b.nx + 2 * c->G, my = b.ny + 2 * c->G;
+  std::vector<double> M((size_t)NMETRIC * mx * my);
+  if (!cfs::metric_plane(topo.data(), (int)topo.size(), block, c->G, c->r, c->p.order, b.h[2], b.nz > 1 ? 3 : 2, M.data()))
+    return fail(c, CFS_EINVAL, "curvilinear grid with a non-positive cell volume, or not continued across a face");
+  const size_t pl = (size_t)mx * my, at = (size_t)(i + c->G) + (size_t)mx * (j + c->G);
+  for (int q = 0; q < NMETRIC; ++q) out[q] = M[q * pl + at];
+  return CFS_OK;
+}
+
 cfs_status cfs_halo_sources(cfs_ctx* c, int block, int i, int j, int k, double* out) {
   if (!c || !out) return CFS_EINVAL;
   if (block < 0 || block >= (int)c->blocks.size()) return fail(c, CFS_EINVAL, "unknown block");

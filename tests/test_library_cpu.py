@@ -226,3 +226,32 @@ def test_halo_sources_match_the_oracle(lib, topology):
         assert n > 0
     finally:
         cfs.cfs_destroy(ctx)
+
+
+@pytest.mark.parametrize("topology", ["cgrid", "rotated"])
+def test_metric_terms_match_the_oracle(lib, topology):
+    """The library's metric terms (App. A) of curvilinear blocks, continued across interfaces, the
+    wake cut and physical faces, agree with the oracle's own computation at every point of the
+    block planes and their halos to the stencil radius (1e-12 relative to the largest term of
+    each kind; beyond it both give NaN).  No device is touched."""
+    from paper_2506_03027_gb300 import inputs as I
+    if topology == "cgrid":
+        mb = I.naca_cgrid(I.cgrid_reduced())
+    else:
+        c = I.tgv_case(24, 2, "CAA", filter=True, curv=0.2).replace(px=3)
+        mb = I.rotated_pair(c, 16, 2, 1)
+    ctx = _ctx_for(mb)
+    try:
+        G = 4
+        for bi, b in enumerate(mb.blocks):
+            pts = [(i, j) for j in range(-G, b.ny + G) for i in range(-G, b.nx + G)]
+            ref = orc.metric_terms(mb, bi, pts)
+            got = np.array([cfs.cfs_metric_terms(ctx, bi, i, j)[:6] for i, j in pts])
+            fin = np.isfinite(ref)
+            assert np.array_equal(fin, np.isfinite(got)), bi
+            scale = np.nanmax(np.abs(ref), axis=0)
+            err = np.where(fin, np.abs(got - ref), 0.0) / scale
+            assert err.max() < 1e-12, (bi, err.max(axis=0))
+            assert fin[:, 5].sum() > b.nx * b.ny  # the halo carries finite terms too
+    finally:
+        cfs.cfs_destroy(ctx)
