@@ -531,6 +531,11 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
     ph.c1[a] = (a_cd / 2.0) / b0.h[a];
     ph.c2[a] = (b_cd / 4.0) / b0.h[a];
   }
+  // tables of the FP64 power (power-law viscosity)
+  if (c->p.viscous && c->p.visc_law == 1) {
+    const int rc = cfs::pow_tables_init();
+    if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "power tables");
+  }
   // device memory
   c->ring = (double*)dev_alloc(c, sizeof(double) * 5 * N * c->R);
   c->buf[0] = (double*)dev_alloc(c, sizeof(double) * 5 * N);

@@ -308,5 +308,6 @@ int launch_diagnostics_block(const Geometry& g, const DiagBlock& b, const double
 int launch_diagnostics_final(const double* partial, int nrows, double* out, double volume, void* stream);
 int launch_advance_step(long long* dn, void* stream);
 int launch_eval_power(const double* x, double a, double* y, long long n, void* stream);
+int pow_tables_init();  // tables of the FP64 power, once per process; nonzero on a CUDA error
 
 }  // namespace cfs

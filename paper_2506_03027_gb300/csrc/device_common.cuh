@@ -25,66 +25,6 @@ __device__ __forceinline__ double recip(double x) {
 }
 __device__ __forceinline__ float recip(float x) { return 1.0f / x; }
 
-// x^a = exp(a ln x) in FP64 for positive normal x (the viscosity law mu = T^a), with about 40
-// FP64 operations.  ln x: reduction x = m 2^e with m in [1/sqrt(2), sqrt(2)) read off the bit
-// fields, ln m = 2 atanh(s) with s = (m - 1)/(m + 1), |s| <= 0.1716, by the series
-// sum s^(2j+1)/(2j+1) to s^23.  exp y: reduction y = k ln 2 + r, |r| <= ln(2)/2, with ln 2 split
-// into a head of 32 significant bits and the tail (Cody and Waite's reduction: k ln2_head is
-// exact), the Taylor series of exp r to r^14/14!, and 2^k added to the exponent field.  The split
-// constants: the head is the double nearest ln 2 with its low 21 mantissa bits cleared, the tail
-// ln 2 - head rounded (from a 60-digit ln 2).  Relative error below 4.5e-16 (1 + |a ln x|): the
-// rounding of a ln x passes into the result.  Any other x (zero, subnormal, negative, infinite,
-// NaN), or |a ln x| >= 700, goes to the library's pow.
-__device__ __forceinline__ double pow_pos(double x, double a) {
-  if (!(x >= 2.2250738585072014e-308) || !(x <= 1.7976931348623157e308)) return pow(x, a);
-  const int hi = __double2hiint(x);
-  int e = ((hi >> 20) & 0x7ff) - 1023;
-  double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, __double2loint(x));  // [1, 2)
-  if (m > 1.4142135623730951) {
-    m *= 0.5;
-    e += 1;
-  }
-  const double s = (m - 1.0) * recip(m + 1.0);
-  const double s2 = s * s;
-  double p = 1.0 / 23.0;
-  p = fma(p, s2, 1.0 / 21.0);
-  p = fma(p, s2, 1.0 / 19.0);
-  p = fma(p, s2, 1.0 / 17.0);
-  p = fma(p, s2, 1.0 / 15.0);
-  p = fma(p, s2, 1.0 / 13.0);
-  p = fma(p, s2, 1.0 / 11.0);
-  p = fma(p, s2, 1.0 / 9.0);
-  p = fma(p, s2, 1.0 / 7.0);
-  p = fma(p, s2, 1.0 / 5.0);
-  p = fma(p, s2, 1.0 / 3.0);
-  const double lnm = 2.0 * s * fma(p, s2, 1.0);
-  const double LN2_HEAD = 0.6931471803691238, LN2_TAIL = 1.9082149292705877e-10;
-  const double ed = (double)e;
-  // a ln x = a (e ln2_head + (e ln2_tail + ln m)); e ln2_head is exact (32 + 11 bits)
-  const double y = a * fma(ed, LN2_HEAD, fma(ed, LN2_TAIL, lnm));
-  if (!(fabs(y) < 700.0)) return pow(x, a);  // 2^k must stay in the normal range
-  // k = nearest integer of y / ln 2
-  const double kd = rint(y * 1.4426950408889634);
-  double r = fma(-kd, LN2_HEAD, y);
-  r = fma(-kd, LN2_TAIL, r);
-  double q = 1.0 / 87178291200.0;  // 1/14!
-  q = fma(q, r, 1.0 / 6227020800.0);
-  q = fma(q, r, 1.0 / 479001600.0);
-  q = fma(q, r, 1.0 / 39916800.0);
-  q = fma(q, r, 1.0 / 3628800.0);
-  q = fma(q, r, 1.0 / 362880.0);
-  q = fma(q, r, 1.0 / 40320.0);
-  q = fma(q, r, 1.0 / 5040.0);
-  q = fma(q, r, 1.0 / 720.0);
-  q = fma(q, r, 1.0 / 120.0);
-  q = fma(q, r, 1.0 / 24.0);
-  q = fma(q, r, 1.0 / 6.0);
-  q = fma(q, r, 0.5);
-  q = fma(q, r, 1.0);
-  q = fma(q, r, 1.0);
-  const int k = (int)kd;
-  return __hiloint2double(__double2hiint(q) + (k << 20), __double2loint(q));
-}
 
 // ---- FP64 <-> FP32 conversions on the integer pipe
 // On this GPU conversions between FP64 and FP32 issue on the FP64 pipe, which runs at 1/64 of the

@@ -19,6 +19,8 @@
 // boxes of all sub-domains.
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <mutex>
 #include <type_traits>
 
 #include "cfs_internal.h"
@@ -194,13 +196,58 @@ __global__ void __launch_bounds__(512) k_view_halo(Geometry g, Physics ph, StepS
 
 // ------------------------------------------------------------------------------- k_flux
 
+// x^a = exp(a ln x) in FP64 for positive normal x (the viscosity law mu = T^a), table-driven
+// after Tang (ACM TOMS 1989, 1990), about 20 FP64 operations.  ln x: x = m 2^e with m in [1, 2)
+// from the bit fields; the top six mantissa bits pick c_j = 1 + (j + 1/2)/64, u = m / c_j - 1
+// (|u| <= 1/129) from a table of 1/c_j, ln m = ln c_j + log1p(u) with the series of log1p to u^7.
+// exp y: y = (64 k' + j') ln2/64 + r with |r| <= ln2/128 (ln 2 / 64 split into a 32-bit head and
+// its tail: k ln2_head is exact), exp r by its Taylor series to r^5/5!, times the tabulated
+// 2^(j'/64), and 2^k' added to the exponent field.  Tables: 1/c_j rounded from the exact
+// quotient, ln c_j and 2^(j/64) rounded from long-double log1p and exp2 (cfs_pow_tables_init).
+// Relative error below 4.5e-16 (1 + |a ln x|).  Any other x, or |a ln x| >= 700, goes to the
+// library's pow.
+__device__ double g_pow_tab[3 * 64];  // 1/c_j, ln c_j, 2^(j/64)
+
+__device__ __forceinline__ double pow_tab(double x, double a) {
+  if (!(x >= 2.2250738585072014e-308) || !(x <= 1.7976931348623157e308)) return pow(x, a);
+  const int hi = __double2hiint(x);
+  const int e = ((hi >> 20) & 0x7ff) - 1023;
+  const int j = (hi >> 14) & 63;
+  const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, __double2loint(x));  // [1, 2)
+  const double u = fma(m, __ldg(g_pow_tab + j), -1.0);
+  double p = 1.0 / 7.0;
+  p = fma(p, u, -1.0 / 6.0);
+  p = fma(p, u, 1.0 / 5.0);
+  p = fma(p, u, -1.0 / 4.0);
+  p = fma(p, u, 1.0 / 3.0);
+  p = fma(p, u, -0.5);
+  p = fma(p, u, 1.0);
+  const double l1p = p * u;
+  const double LN2_HEAD = 0.6931471803691238, LN2_TAIL = 1.9082149292705877e-10;
+  const double ed = (double)e;
+  const double y = a * fma(ed, LN2_HEAD, fma(ed, LN2_TAIL, __ldg(g_pow_tab + 64 + j) + l1p));
+  if (!(fabs(y) < 700.0)) return pow(x, a);
+  const double kd = rint(y * (64.0 / 0.6931471805599453));
+  double r = fma(-kd, LN2_HEAD / 64.0, y);
+  r = fma(-kd, LN2_TAIL / 64.0, r);
+  double q = 1.0 / 120.0;
+  q = fma(q, r, 1.0 / 24.0);
+  q = fma(q, r, 1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  q = fma(q, r, 1.0);
+  q = fma(q, r, 1.0);
+  const int k = (int)kd;
+  q *= __ldg(g_pow_tab + 128 + (k & 63));
+  return __hiloint2double(__double2hiint(q) + ((k >> 6) << 20), __double2loint(q));
+}
+
 // Viscosity law: mu = 1, or the power law mu = T^visc_exp -- in the intermediate precision (the
 // FP32 form evaluates it in FP32: a power in FP64 runs at the FP64 rate)
 template <typename T>
 __device__ __forceinline__ T visc_mu(const Physics& ph, T temp) {
   if (ph.visc_law != 1) return (T)1;
   if (std::is_same<T, float>::value) return (T)powf((float)temp, (float)ph.visc_exp);
-  return (T)pow_pos((double)temp, ph.visc_exp);
+  return (T)pow_tab((double)temp, ph.visc_exp);
 }
 
 template <typename T>
@@ -930,10 +977,27 @@ __global__ void k_advance_step(long long* dn) {
 
 __global__ void k_eval_power(const double* __restrict__ x, double a, double* __restrict__ y, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = pow_pos(x[i], a);
+  if (i < n) y[i] = pow_tab(x[i], a);
+}
+
+// The tables of pow_tab, once per process (the device's copy of a __device__ array).
+int pow_tables_init() {
+  static std::once_flag once;
+  static int rc = -1;
+  std::call_once(once, [] {
+    double t[3 * 64];
+    for (int j = 0; j < 64; ++j) {
+      t[j] = 128.0 / (129.0 + 2.0 * j);  // 1/c_j, c_j = (129 + 2j)/128
+      t[64 + j] = (double)log1pl((long double)(2 * j + 1) / 128.0L);
+      t[128 + j] = (double)exp2l((long double)j / 64.0L);
+    }
+    rc = (int)cudaMemcpyToSymbol(g_pow_tab, t, sizeof(t));
+  });
+  return rc;
 }
 
 int launch_eval_power(const double* x, double a, double* y, long long n, void* stream) {
+  if (int rc = pow_tables_init()) return rc;
   if (n > 0) k_eval_power<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, a, y, n);
   return (int)cudaGetLastError();
 }
