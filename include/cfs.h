@@ -218,7 +218,7 @@ cfs_status cfs_diagnostics(cfs_ctx* ctx, double* out);
 /* The library's FP64 power y[i] = x[i]^a for n device values, asynchronously on `stream` (the
  * power-law viscosity mu = T^a of App. A's constitutive law, as the FP64 path evaluates it: a
  * table-driven logarithm and exponential of about 20 FP64 operations; for positive normal x its
- * relative error is below 4.5e-16 (1 + |a ln x|), 1e-15 for x near 1).  For checking that power against
+ * relative error is below 6e-16 (1 + |a ln x|), 1.2e-15 for x near 1).  For checking that power against
  * a reference; EINVAL for a negative n or null buffers, ECUDA if the launch fails. */
 cfs_status cfs_eval_power(const double* x, double a, double* y, long long n, void* stream);
 

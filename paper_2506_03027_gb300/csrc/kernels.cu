@@ -203,8 +203,8 @@ __global__ void __launch_bounds__(512) k_view_halo(Geometry g, Physics ph, StepS
 // exp y: y = (64 k' + j') ln2/64 + r with |r| <= ln2/128 (ln 2 / 64 split into a 32-bit head and
 // its tail: k ln2_head is exact), exp r by its Taylor series to r^5/5!, times the tabulated
 // 2^(j'/64), and 2^k' added to the exponent field.  Tables: 1/c_j rounded from the exact
-// quotient, ln c_j and 2^(j/64) rounded from long-double log1p and exp2 (cfs_pow_tables_init).
-// Relative error below 4.5e-16 (1 + |a ln x|).  Any other x, or |a ln x| >= 700, goes to the
+// quotient, ln c_j and 2^(j/64) rounded from long-double log1p and exp2 (pow_tables_init).
+// Relative error below 6e-16 (1 + |a ln x|).  Any other x, or |a ln x| >= 700, goes to the
 // library's pow.
 __device__ double g_pow_tab[3 * 64];  // 1/c_j, ln c_j, 2^(j/64)
 
@@ -225,7 +225,8 @@ __device__ __forceinline__ double pow_tab(double x, double a) {
   const double l1p = p * u;
   const double LN2_HEAD = 0.6931471803691238, LN2_TAIL = 1.9082149292705877e-10;
   const double ed = (double)e;
-  const double y = a * fma(ed, LN2_HEAD, fma(ed, LN2_TAIL, __ldg(g_pow_tab + 64 + j) + l1p));
+  // (e ln2_head + ln c_j) is exact where it cancels (x just below 1: Sterbenz), then the tails
+  const double y = a * (fma(ed, LN2_HEAD, __ldg(g_pow_tab + 64 + j)) + fma(ed, LN2_TAIL, l1p));
   if (!(fabs(y) < 700.0)) return pow(x, a);
   const double kd = rint(y * (64.0 / 0.6931471805599453));
   double r = fma(-kd, LN2_HEAD / 64.0, y);

@@ -176,7 +176,7 @@ def test_cgrid_full_size_parity():
 def test_fp64_power_within_a_few_ulp():
     """The FP64 path's own power (the viscosity law mu = T^0.76 of the C-grid) against numpy's
     and CUDA's pow: exp(a ln x) carries the rounding of a ln x into the result, so the relative
-    error is bounded by 4.5e-16 (1 + |a ln x|) -- 1e-15 near T = 1 -- over positive normal x;
+    error is bounded by 6e-16 (1 + |a ln x|) -- 1.2e-15 near T = 1 -- over positive normal x;
     equal special cases."""
     import torch
     rng = np.random.default_rng(7)
@@ -192,11 +192,11 @@ def test_fp64_power_within_a_few_ulp():
         cuda_ref = torch.pow(xt, a).cpu().numpy()
         normal = (x >= 2.2250738585072014e-308) & np.isfinite(x)
         ok = normal & np.isfinite(ref) & (ref >= 2.3e-308) & (ref < 1e300)  # normal results
-        bound = 4.5e-16 * (1.0 + np.abs(a * np.log(x[ok])))
+        bound = 6e-16 * (1.0 + np.abs(a * np.log(x[ok])))
         assert np.all(np.abs(y[ok] / ref[ok] - 1.0) <= bound), a
         assert np.all(np.abs(y[ok] / cuda_ref[ok] - 1.0) <= bound + 2.3e-16), a
         near = ok & (np.abs(x - 1.0) < 0.5)
-        assert np.max(np.abs(y[near] / ref[near] - 1.0)) < 1e-15, a
+        assert np.max(np.abs(y[near] / ref[near] - 1.0)) < 1.2e-15, a
         # zero, subnormal and infinite x go to CUDA's pow
         assert np.array_equal(np.isinf(y), np.isinf(ref)) and np.array_equal(y[~normal], cuda_ref[~normal])
 
