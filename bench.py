@@ -60,10 +60,10 @@ HBM_GBS_FALLBACK = 6800.0
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel kind, with the sha1 of
 # the flux kernel's source they were taken from (kernels_sha1; null once it changes); filled
 # from profiles/.
-TRAFFIC = {"source_sha1": "5c111a48ebda02a60022a9a55094e22eca35f1b3",
-           # k_flux<double,3>: 93.3 MB read + 78.8 MB written per launch in an ncu capture of the
+TRAFFIC = {"source_sha1": "fd2d86cea02a0be1b631fb40bba5b45d6402a26a",
+           # k_flux<double,3>: 93.3 MB read + 78.6 MB written per launch in an ncu capture of the
            # 96^3 case (27 sub-domains of 32^3), x 64/27 for the 64 sub-domains of 128^3
-           "bytes_per_launch": {"flux": 407.9e6}}
+           "bytes_per_launch": {"flux": 407.4e6}}
 
 
 def kernels_sha1(root: str = ROOT) -> str:
