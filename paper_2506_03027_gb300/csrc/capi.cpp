@@ -362,24 +362,8 @@ cfs_status cfs_metric_terms(cfs_ctx* c, int block, int i, int j, double* out) {
 cfs_status cfs_halo_sources(cfs_ctx* c, int block, int i, int j, int k, double* out) {
   if (!c || !out) return CFS_EINVAL;
   if (block < 0 || block >= (int)c->blocks.size()) return fail(c, CFS_EINVAL, "unknown block");
-  std::vector<cfs::TopoBlock> topo(c->blocks.size());
-  int sid0 = 0;
-  long long base = 0;
-  for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
-    const Block& b = c->blocks[bi];
-    cfs::TopoBlock& t = topo[bi];
-    t.n[0] = b.nx; t.n[1] = b.ny; t.n[2] = b.nz;
-    for (int a = 0; a < 3; ++a) t.P[a] = b.P[a];
-    t.sid0 = sid0;
-    t.base = base;
-    t.N = b.N;
-    t.xy = b.xy.empty() ? nullptr : b.xy.data();
-    for (int q = 0; q < 4; ++q) t.shift[q] = b.shift[q];
-    for (int f = 0; f < 6; ++f) t.face[f] = b.face[f];
-    sid0 += b.P[0] * b.P[1] * b.P[2];
-    base += 5 * b.N;
-  }
-  if (const char* why = cfs::topo_check(topo.data(), (int)topo.size())) return fail(c, CFS_EINVAL, why);
+  std::vector<cfs::TopoBlock> topo;
+  if (const char* why = host_topology(c, topo)) return fail(c, CFS_EINVAL, why);
   const Block& b = c->blocks[block];
   const int G = c->p.filter ? std::max(c->G, 5) : c->G;
   if (i < -G || i >= b.nx + G || j < -G || j >= b.ny + G || k < -G || k >= b.nz + G)
@@ -436,22 +420,10 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
     Ntot += b.N;
   }
   // block topology: faces, gather maps of the blocks with a non-periodic face
-  std::vector<cfs::TopoBlock> topo(c->blocks.size());
+  std::vector<cfs::TopoBlock> topo;
+  if (const char* why = host_topology(c, topo)) return fail(c, CFS_EINVAL, why);
   c->all_periodic = true;
-  for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
-    const Block& b = c->blocks[bi];
-    cfs::TopoBlock& t = topo[bi];
-    t.n[0] = b.nx; t.n[1] = b.ny; t.n[2] = b.nz;
-    for (int a = 0; a < 3; ++a) t.P[a] = b.P[a];
-    t.sid0 = b.sid0;
-    t.base = b.base;
-    t.N = b.N;
-    t.xy = b.xy.empty() ? nullptr : b.xy.data();
-    for (int k = 0; k < 4; ++k) t.shift[k] = b.shift[k];
-    for (int f = 0; f < 6; ++f) t.face[f] = b.face[f];
-    c->all_periodic = c->all_periodic && cfs::topo_periodic(t);
-  }
-  if (const char* why = cfs::topo_check(topo.data(), (int)topo.size())) return fail(c, CFS_EINVAL, why);
+  for (const cfs::TopoBlock& t : topo) c->all_periodic = c->all_periodic && cfs::topo_periodic(t);
   c->subs.resize(nsub);
   long long pbase = 0;
   c->max_pad = c->max_own = c->max_flux = 0;
