@@ -207,3 +207,37 @@ def test_conservation_across_reversed_interfaces():
     Ub, db = orc.run(bad, U0, 20, diag=True)
     drift = abs(db[-1][6] - d0[6]) / scale[4]
     assert not np.isfinite(drift) or drift > 1e-9, drift
+
+
+def test_cgrid_geometry_recipe():
+    """The C-grid of config 3 as its recipe states it: airfoil rows on the NACA0012 surface
+    (y = -+ y_t(x), no point at either edge), wake rows on y = -+ y_t(1) so that the cut spacing
+    2 y_t(1) equals the first wall-normal spacing, the far field a C of radius 5 chords around
+    (1/2, 0) closed by straight lines, the wake reaching 4
+    chords downstream, the two sides of the cut mirror images, and the block sizes of the
+    configuration (96 x 64 x 32 up to 512 x 192 x 64, 22.0 M points)."""
+    for sp in (I.CGridSpec(), I.cgrid_reduced()):
+        X, Y = I.cgrid_plane(sp)
+        nw, ns = sp.wake, sp.aft + sp.fore
+        te = float(I.naca0012_half_thickness(1.0))
+        assert abs(te - 0.00126) < 1e-6
+        air = slice(nw, nw + 2 * ns)
+        xa, ya = X[0, air], Y[0, air]
+        assert np.all((xa > 0) & (xa < 1))
+        assert np.allclose(np.abs(ya), I.naca0012_half_thickness(xa), rtol=0, atol=1e-15)
+        assert np.all(Y[0, :nw] == -te) and np.all(Y[0, -nw:] == te)
+        # first wall-normal spacing in the wake equals the cut spacing 2 y_t(1)
+        assert abs((Y[0, 0] - Y[1, 0]) - 2 * te) < 1e-9
+        xf, yf = X[-1], Y[-1]  # far field: |y| = 5 downstream of x = 1/2, a half circle ahead of it
+        assert np.allclose(np.abs(yf[xf >= 0.5]), 5.0, atol=1e-9)
+        assert np.allclose(np.hypot(xf[xf < 0.5] - 0.5, yf[xf < 0.5]), 5.0, atol=1e-9)
+        # the wake ends one geometric growth step short of x = 1 + 4 chords
+        assert 3.0 < X[0, 0] < 5.0 and X[0, -1] == X[0, 0]
+        h = np.diff(X[0, nw - 1::-1])  # wake spacings from the trailing edge downstream
+        assert np.all(h > 0) and np.allclose(h[1:] / h[:-1], h[1] / h[0], rtol=1e-9)
+        # the cut's two sides are mirror images
+        assert np.allclose(X[:, :nw], X[:, ::-1][:, :nw], atol=1e-12)
+        assert np.allclose(Y[:, :nw], -Y[:, ::-1][:, :nw], atol=1e-12)
+    mb = I.naca_cgrid()
+    sizes = sorted((b.nx * b.ny * b.nz, (b.nx, b.ny, b.nz)) for b in mb.blocks)
+    assert sizes[0][1] == (96, 64, 32) and sizes[-1][1] == (512, 192, 64) and mb.npts == 22020096
