@@ -91,6 +91,9 @@ def _load():
             lib.or_bf16.argtypes = [ctypes.c_double]
             lib.or_bf16.restype = ctypes.c_double
             lib.or_mlp_forward.argtypes = [ctypes.POINTER(ctypes.c_float), d, d]
+            lib.or_column_features.argtypes = [P(OrParams), P(d), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_int, d, d]
+            lib.or_column_features.restype = None
             lib.or_set_num_threads.argtypes = [ctypes.c_int]
             lib.or_halo_sources.argtypes = [P(OrParams), ctypes.c_int, ctypes.c_long, P(ctypes.c_int), d]
             lib.or_halo_sources.restype = ctypes.c_int
@@ -273,6 +276,21 @@ def mlp_forward_c(params: np.ndarray, x: np.ndarray) -> np.ndarray:
     y = np.zeros(20)
     _load().or_mlp_forward(p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _dptr(xx), _dptr(y))
     return y
+
+
+def column_features(case, levels, scales, sub: int, face: int, t1: int, t2: int, k: int):
+    """The learned halo's input features of one face column and its 3-level extrapolation, as the
+    oracle builds them: levels = (U^n, U^{n-k}, U^{n-k-1}, U^{n-k-2}) full states, scales[15] =
+    (in_scale[5], own_scale[5], out_scale[5]).  Returns (x[65], at3[20])."""
+    p = params(case)
+    sc = np.ascontiguousarray(scales, dtype=np.float64)
+    p.mlp_scales = _dptr(sc)
+    lv = [np.ascontiguousarray(L, dtype=np.float64) for L in levels]
+    ptrs = (ctypes.POINTER(ctypes.c_double) * 4)(*[_dptr(L) for L in lv])
+    x = np.zeros(65)
+    at3 = np.zeros(20)
+    _load().or_column_features(ctypes.byref(p), ptrs, sub, face, t1, t2, k, _dptr(x), _dptr(at3))
+    return x, at3
 
 
 def halo_sources(case, block: int, points):
