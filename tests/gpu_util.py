@@ -27,15 +27,36 @@ def gpu_run(case, U0, nsteps, delays=None, precision=0, max_delay=None):
 
 
 def rel_l2(a, ref):
-    """Relative L2 error per conserved variable.  The three momentum components are measured
-    against the norm of the momentum vector field: a component that is small (rho w of the TGV at
-    early times, zero in 2-D) carries the rounding error of the whole momentum balance (pressure
-    gradients of p ~ 1/(gamma M^2) with O(1) variations), which a per-component norm would
-    magnify."""
+    """The parity metric that gates the tests: relative L2 error of rho and rho E each against its
+    own norm, of rho u, rho v, rho w against the norm of the momentum vector field (a variable whose
+    reference norm is ~0 has no relative error and is measured against that scale too).  The
+    rounding of a momentum component comes from the whole momentum balance (the pressure gradient
+    of p ~ 1/(gamma M^2) and the convective terms): the oracle alone, started from a state changed
+    by one ulp, moves rho w of the Taylor-Green vortex -- zero at t = 0, 0.3 to 0.6 % of the
+    momentum norm after 24 steps -- by 7e-12 (SA) to 1e-10 (SAA) of its own norm while every
+    momentum component moves by 4e-14 to 3e-13 of the momentum norm
+    (test_momentum_component_rounding_floor), so two correct FP64 evaluation orders cannot agree
+    to 1e-12 of rho w's own norm."""
     mom = np.sqrt(sum(np.linalg.norm(ref[v]) ** 2 for v in (1, 2, 3)))
     out = []
     for v in range(5):
         den = mom if v in (1, 2, 3) else np.linalg.norm(ref[v])
+        if den <= 1e-14 * max(mom, 1e-300):
+            den = mom
+        num = np.linalg.norm(a[v] - ref[v])
+        out.append(num / den if den > 0 else num)
+    return np.array(out)
+
+
+def rel_l2_per_component(a, ref):
+    """Relative L2 error of every conserved variable against its own norm (reported beside the
+    gate; a variable whose reference norm is ~0 against the momentum vector's norm)."""
+    mom = np.sqrt(sum(np.linalg.norm(ref[v]) ** 2 for v in (1, 2, 3)))
+    out = []
+    for v in range(5):
+        den = np.linalg.norm(ref[v])
+        if den <= 1e-14 * max(mom, 1e-300):
+            den = mom
         num = np.linalg.norm(a[v] - ref[v])
         out.append(num / den if den > 0 else num)
     return np.array(out)

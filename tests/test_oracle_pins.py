@@ -420,3 +420,30 @@ def test_paper_vortex_is_an_exact_solution():
     assert orders[-1] > 3.6, (e, orders)
     f = [err(n, flip=True) for n in (48, 96)]
     assert math.log(f[0] / f[1], 2) < 2.0 and f[1] > 5 * e[-1], (f, e)
+
+
+# ------------------------------------------------------------------ rounding floor of the parity metric
+
+@pytest.mark.parametrize("algo,cfl,kmax", [("SA", 0.25, 0), ("SAA", 0.1, 3)])
+def test_momentum_component_rounding_floor(algo, cfl, kmax):
+    """Why the parity metric measures the momentum components against the momentum vector's norm:
+    the oracle alone, started from the Taylor-Green state changed by one ulp at every value, ends
+    24 steps later (ragged 34^3 grid, 4^3 sub-domains) with rho w -- zero at t = 0 -- moved by more
+    than 1e-12 of its own norm, while every momentum component moved by far less than 1e-12 of
+    the momentum vector's norm.  Two correct FP64 evaluation orders of the same method therefore
+    cannot agree on rho w to 1e-12 of its own norm, and do agree to 1e-12 on the vector scale."""
+    c = I.tgv_case(34, 4, algo)
+    c = c.replace(dt=I.cfl_dt(c, I.tgv_state(c), cfl), kmax=kmax)
+    n = 24
+    d = I.saa_delays(c, n) if algo == "SAA" else None
+    U0 = I.tgv_state(c)
+    rng = np.random.default_rng(0)
+    U0p = U0 * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=U0.shape))
+    a = orc.run(c, U0, n, delays=d)
+    b = orc.run(c, U0p, n, delays=d)
+    mom = math.sqrt(sum(np.linalg.norm(a[v]) ** 2 for v in (1, 2, 3)))
+    own_w = np.linalg.norm(b[3] - a[3]) / np.linalg.norm(a[3])
+    vec = [np.linalg.norm(b[v] - a[v]) / mom for v in (1, 2, 3)]
+    assert np.linalg.norm(a[3]) < 1e-2 * mom          # rho w is small at early times
+    assert own_w > 1e-12, own_w                       # below the method's own rounding floor
+    assert max(vec) < 1e-12, vec

@@ -8,7 +8,7 @@ from oracle import oracle as orc
 from paper_2506_03027_gb300 import cfs
 from paper_2506_03027_gb300 import inputs as I
 
-from gpu_util import PARITY_TOL, check_diagnostics, ensure_built, gpu_run, rel_l2
+from gpu_util import PARITY_TOL, check_diagnostics, ensure_built, gpu_run, rel_l2, rel_l2_per_component
 
 pytestmark = pytest.mark.gpu
 
@@ -30,7 +30,7 @@ def small_tgv(algo, n=34, p=4, cfl=0.25, **kw):
 def check(U, ref, tol=PARITY_TOL):
     e = rel_l2(U, ref)
     assert np.all(np.isfinite(U))
-    assert np.all(e <= tol), e
+    assert np.all(e <= tol), (e, rel_l2_per_component(U, ref))
     return e
 
 
