@@ -177,6 +177,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def rel_l2(a, ref):
+    """Relative L2 difference per conserved variable: rho and rho E against their own norms, the
+    momentum components against the norm of the momentum vector field."""
+    mom = math.sqrt(sum(float(np.linalg.norm(ref[v])) ** 2 for v in (1, 2, 3)))
+    return [float(np.linalg.norm(a[v] - ref[v])) / (mom if v in (1, 2, 3) else float(np.linalg.norm(ref[v])))
+            for v in range(5)]
+
+
+def rel_l2_own(a, ref):
+    """The same with every variable against its own norm."""
+    return [float(np.linalg.norm(a[v] - ref[v]) / np.linalg.norm(ref[v])) for v in range(5)]
+
+
 def face_points(case, depth):
     """Points of the face strips (depth `depth`) of all sub-domains along each axis."""
     from paper_2506_03027_gb300 import inputs as I  # noqa: F401
@@ -244,6 +257,32 @@ def fused_roofline(case, ktimes):
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
 
 
+def fp64_peak(local_rank: int = 0):
+    """The FP64 pipe rate of this GPU, measured: the library's probe kernel (8 independent DFMA
+    chains per thread, 8 CTAs of 256 threads per SM) timed with CUDA events, median of 5 launches
+    after a warm-up launch.  Returns TFLOP/s (FMA = 2 flops) and the clock samples taken meanwhile."""
+    import torch
+    from paper_2506_03027_gb300 import cfs
+    blocks, iters = SM_COUNT * 8, 4096
+    sink = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    cfs.cfs_fp64_probe(sink, blocks, iters, st.cuda_stream)
+    ts = []
+    with ClockSampler(local_rank) as clk:
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            cfs.cfs_fp64_probe(sink, blocks, iters, st.cuda_stream)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    fmas = blocks * 256 * iters * 8
+    return {"tflops": 2 * fmas / (ms * 1e-3) / 1e12, "ms": ms, "fmas": fmas,
+            "sm_mhz": clk.summary().get("sm_mhz")}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2506_03027_gb300 import build as B
@@ -259,20 +298,22 @@ def run_ours(args, rank, world, local_rank):
     case = workload(args.schedule, args.grid, args.split)
     case = case.replace(seed=case.seed + rank)
     K, W = args.steps, args.warmup
-    total = W + 2 * K + 8
+    total = W + 3 * K + 8  # warm-up, timed steps, the per-kernel timing pass, end-to-end steps
     delays = I.saa_delays(case, total)
     U0 = I.tgv_state(case)
     stream = torch.cuda.current_stream()
 
     tiles = tuple(int(t) for t in args.tiles.split(",")) if args.tiles else None
-    solver = cfs.Solver(case, precision=args.precision, tiles=tiles)
+    # the step is captured once in a CUDA graph and replayed (the step index lives on the device)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    solver = cfs.Solver(case, precision=args.precision, tiles=tiles, stream=stream, graph=True)
     solver.set_schedule(delays=delays)
     solver.set_state(U0)
     solver.step(W)
     torch.cuda.synchronize()
 
-    # ---------------- device-resident timed region
-    cfs.cfs_set_timing(solver.ctx, True)
+    # ---------------- device-resident timed region (graph replays, no per-kernel events)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     if world > 1:
@@ -287,11 +328,17 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
     launches = solver.launches()
-    ktimes = cfs.cfs_get_timing(solver.ctx)
-    cfs.cfs_set_timing(solver.ctx, False)
     ms = max_over_ranks(ms, world)
     n_units = case.npts * case.stages * K * world
     value = whole_job_rate(case.npts * case.stages * K, world, ms * 1e-3)
+
+    # ---------------- per-kernel times: a separate pass of K steps with CUDA events around every
+    # launch on the solver's stream (this bypasses the graph; not part of the timed value)
+    cfs.cfs_set_timing(solver.ctx, True)
+    solver.step(K)
+    ktimes = cfs.cfs_get_timing(solver.ctx)
+    cfs.cfs_set_timing(solver.ctx, False)
+    torch.cuda.synchronize()
 
     # ---------------- end to end through the public API with host buffers
     host = torch.empty((5, case.nz, case.ny, case.nx), dtype=torch.float64, pin_memory=True)
@@ -314,6 +361,8 @@ def run_ours(args, rank, world, local_rank):
     U_fp64 = solver.get_state()
     n_done = solver.n
     solver.close()
+    torch.cuda.set_stream(torch.cuda.default_stream())
+    stream = torch.cuda.current_stream()
 
     # ---------------- precision form (FP32 intermediates), same steps, error vs the FP64 path
     forms = None
@@ -338,12 +387,12 @@ def run_ours(args, rank, world, local_rank):
         s32.step(n_done - s32.n)
         U32 = s32.get_state()
         s32.close()
-        mom = math.sqrt(sum(float(np.linalg.norm(U_fp64[v])) ** 2 for v in (1, 2, 3)))
-        err = [float(np.linalg.norm(U32[v] - U_fp64[v]) / (mom if v in (1, 2, 3) else np.linalg.norm(U_fp64[v])))
-               for v in range(5)]
+        err = rel_l2(U32, U_fp64)
+        err_own = rel_l2_own(U32, U_fp64)
         forms = {"fp32_intermediates": {"value": n_units / (ms32 * 1e-3) / 1e6, "unit": UNIT,
                                         "speedup_vs_fp64": ms / ms32,
-                                        "rel_l2_vs_fp64_path": err, "after_steps": n_done,
+                                        "rel_l2_vs_fp64_path": err, "rel_l2_own_norm_vs_fp64_path": err_own,
+                                        "after_steps": n_done,
                                         "tiles_autotuned": list(tiles32),
                                         "per_kernel_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in kt32.items() if v[1]},
                                         "fused_stage_roofline": fused_roofline(case, kt32)}}
@@ -381,13 +430,14 @@ def run_ours(args, rank, world, local_rank):
     flops = algorithmic_flops(case, dom)
     achieved_tf = flops / (dom_ms / dom_n * 1e-3) / 1e12
     if args.precision == 0:
-        peak_tf = SM_COUNT * FP64_FLOP_PER_CLK_SM * sm_max * 1e6 / 1e12
+        probe = fp64_peak(local_rank)
+        peak_tf = probe["tflops"]
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved_tf / peak_tf, "kernel": dom,
-                "peak_source": f"FP64 pipe: {SM_COUNT} SMs x {FP64_FLOP_PER_CLK_SM} flop/clk x {sm_max:.0f} MHz"}
-    else:
-        roof = {"bound": "alu", "achieved": achieved_tf, "peak": None, "unit": "TFLOP/s", "frac": None,
-                "kernel": dom}
+                "peak_source": "measured FP64 pipe rate (cfs_fp64_probe: dependent-free DFMA chains, median of 5, "
+                               "on this GPU in this run)",
+                "fp64_probe": probe,
+                "nominal_peak": SM_COUNT * FP64_FLOP_PER_CLK_SM * sm_max * 1e6 / 1e12}
     tr = TRAFFIC["bytes_per_launch"].get(dom) if TRAFFIC["source_sha1"] == kernels_sha1() else None
     roof["traffic"] = tr
     roof["per_kernel_ms"] = {k: round(v[0] / max(v[1], 1), 4) for k, v in kinds.items()}
@@ -410,6 +460,8 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes},
         "gpu_launches": launches,
+        "launches_per_step": launches / K,
+        "cuda_graph": True,
         "clocks": clocks,
     }
     if forms:
@@ -573,15 +625,14 @@ def precision_form_256(args):
         res[prec] = {"ms": ms, "U": s.get_state(), "K": np.array(ke), "kt": kt}
         s.close()
     U64, U32 = res[0]["U"], res[1]["U"]
-    mom = math.sqrt(sum(float(np.linalg.norm(U64[v])) ** 2 for v in (1, 2, 3)))
-    err = [float(np.linalg.norm(U32[v] - U64[v]) / (mom if v in (1, 2, 3) else np.linalg.norm(U64[v])))
-           for v in range(5)]
+    err = rel_l2(U32, U64)
+    err_own = rel_l2_own(U32, U64)
     eps64 = -(res[0]["K"][2:] - res[0]["K"][:-2]) / (2 * case.dt)
     eps32 = -(res[1]["K"][2:] - res[1]["K"][:-2]) / (2 * case.dt)
     return {"value": case.npts * 5 / (res[1]["ms"] * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": res[1]["ms"],
             "fp64_path": {"value": case.npts * 5 / (res[0]["ms"] * 1e-3) / 1e6, "ms_per_step": res[0]["ms"]},
             "speedup_vs_fp64": res[0]["ms"] / res[1]["ms"],
-            "rel_l2_vs_fp64_path": err, "after_steps": nst,
+            "rel_l2_vs_fp64_path": err, "rel_l2_own_norm_vs_fp64_path": err_own, "after_steps": nst,
             "dissipation_rate_rel_err": float(np.abs(eps32 - eps64).max() / np.abs(eps64).max()),
             "tiles_autotuned": list(tiles[1]),
             "per_kernel_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in res[1]["kt"].items() if v[1]},
@@ -713,14 +764,43 @@ def oracle_sample(case, nsteps):
     return time.perf_counter() - t0
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(case):
+    """The oracle on the host cores: one asynchronous step of the full workload with OpenMP over
+    the sub-domains on every core, and one on a single thread."""
     from oracle import oracle as orc
     orc.build()
     steps = 1
+    cores = orc.num_threads()
     dt = oracle_sample(case, steps)
-    return {"value": case.npts * case.stages * steps / dt / 1e6, "unit": UNIT, "cores": orc.num_threads(),
-            "kind": "oracle",
-            "sample": f"{steps} asynchronous step(s) of the full 128^3 workload (SAA-AT, filter), {dt:.1f} s"}
+    orc.set_num_threads(1)
+    try:
+        dt1 = oracle_sample(case, steps)
+    finally:
+        orc.set_num_threads(cores)
+    return {"value": case.npts * case.stages * steps / dt / 1e6, "unit": UNIT, "cores": cores,
+            "kind": "oracle", "cpu_model": cpu_model(),
+            "single_thread": {"value": case.npts * case.stages * steps / dt1 / 1e6, "cores": 1, "seconds": dt1},
+            "sample": f"{steps} asynchronous step(s) of the full 128^3 workload (SAA-AT, filter): {dt:.1f} s on "
+                      f"{cores} threads, {dt1:.1f} s on one"}
 
 
 def run_reference(args):

@@ -37,7 +37,8 @@ typedef enum {
   CFS_ECUDA = 3,    /* CUDA runtime error (sticky) */
   CFS_ESTATE = 4,   /* call out of order (e.g. cfs_step before cfs_finalize) */
   CFS_ENAN = 5,     /* non-finite value found in the state */
-  CFS_ETIMEOUT = 6  /* a bounded device wait gave up */
+  CFS_ETIMEOUT = 6, /* a bounded device wait gave up */
+  CFS_EXCHANGE = 7  /* the exchange callback of a partitioned context reported a failure */
 } cfs_status;
 
 typedef struct cfs_ctx cfs_ctx;
@@ -214,6 +215,9 @@ cfs_status cfs_set_graph(cfs_ctx* ctx, int on);
  * block or cross only periodic faces.  Returns ENAN (and fills out) when the state holds a
  * non-finite value. */
 cfs_status cfs_diagnostics(cfs_ctx* ctx, double* out);
+/* (On a partitioned context the diagnostics cover the points of the sub-domains computed here:
+ * K, the totals and the non-finite flag combine over the processes by sums and a max; the
+ * enstrophy is the average over this process's points.) */
 
 /* The library's FP64 power y[i] = x[i]^a for n device values, asynchronously on `stream` (the
  * power-law viscosity mu = T^a of App. A's constitutive law, as the FP64 path evaluates it: a
@@ -221,6 +225,14 @@ cfs_status cfs_diagnostics(cfs_ctx* ctx, double* out);
  * relative error is below 6e-16 (1 + |a ln x|), 1.2e-15 for x near 1).  For checking that power against
  * a reference; EINVAL for a negative n or null buffers, ECUDA if the launch fails. */
 cfs_status cfs_eval_power(const double* x, double a, double* y, long long n, void* stream);
+
+/* Measurement aid (no counterpart in the paper): the FP64 pipe rate that the FP64 path's roofline
+ * divides by.  Launches `blocks` CTAs of 256 threads, each thread running 8 independent FP64 FMA
+ * chains of `iters` steps, and writes one value per thread to sink (device, blocks x 256 doubles,
+ * caller-owned), asynchronously on `stream`.  FMAs executed = blocks x 256 x iters x 8 (2 flops
+ * each); the caller times the launch.  EINVAL for a null sink, blocks outside 1..2^20 or
+ * iters < 1; ECUDA if the launch fails. */
+cfs_status cfs_fp64_probe(double* sink, int blocks, int iters, void* stream);
 
 /* Checkpoint / resume of the ring of delayed levels: R = max_delay + C + 1 full states,
  * slot i holds level n - R + 1 + i (host or device buffer of R * 5 * npoints doubles). */
@@ -233,6 +245,50 @@ cfs_status cfs_set_ring(cfs_ctx* ctx, const double* buf, int where);
  * extrapolation; m >= 1: after the buffer updates of Eq. 8 at stages 1..m), k = 0..kmax.
  * Returns the number of doubles written (kmax+1)*s*C, or -1 on bad arguments. */
 int cfs_at_weights(int order, int kmax, double* W);
+
+/* ------------------------------------------------------------------ partitioned contexts
+ * The paper's PEs (Sec. 3) spread over processes (one GPU each): every process creates a context
+ * for the whole grid, with the same blocks, splits, physics and schedule, and computes a
+ * contiguous range of sub-domains.  The only data that travel are the boundary strips of the
+ * new solution that neighbouring PEs read (Alg. 1-3: the send of U^{n+1} at the end of every step
+ * into the neighbours' delayed levels, and under SA -- also the synchronous warm-up steps of CAA
+ * and SAA -- the strips of every stage's and filter pass's input).  A process keeps state arrays
+ * of the whole grid; points of other processes' sub-domains hold the strips it received (the
+ * rest of them is never read and keeps whatever cfs_set_state or cfs_set_ring wrote).  The
+ * delays stay those of the schedule, so a partitioned run gives bit for bit the results of one
+ * context computing every sub-domain. */
+
+/* Compute sub-domains [starts[rank], starts[rank + 1]) of the nranks ranges in starts[nranks + 1]
+ * (host, copied; starts[0] = 0, non-decreasing, starts[nranks] = the number of sub-domains, checked
+ * at cfs_finalize).  Before cfs_finalize (ESTATE after).  nranks = 1 restores the single-process
+ * context.  At cfs_finalize EINVAL unless every block is periodic on every face, the precision is
+ * FP64 (0); the learned halo and CUDA-graph mode are refused on a partitioned context. */
+cfs_status cfs_set_partition(cfs_ctx* ctx, int nranks, const int* starts, int rank);
+
+/* Transport of a partitioned context, called by cfs_step at every exchange point with:
+ * send (device) -- the packed strips for every peer, peer q's send_counts[q] doubles starting at
+ * the sum of send_counts[0..q-1]; recv (device) -- room for what every peer sends here, laid out
+ * the same way with recv_counts; nranks; and the context's stream.  The packing is enqueued on
+ * that stream: the callback orders its reads after it (cudaStreamSynchronize, or transfers
+ * enqueued on the stream such as NCCL send/recv), and before returning has the received values in
+ * recv, or enqueued on the stream ahead of anything enqueued later.  Counts to and from the own
+ * rank are 0.  Layout of a peer's part: 5 doubles (rho, rho u, rho v, rho w, rho E) per point, points
+ * in the order of cfs_exchange_plan.  Return 0 on success; anything else makes cfs_step fail with
+ * CFS_EXCHANGE. */
+typedef int (*cfs_exchange_fn)(void* user, int nranks, const double* send, const long long* send_counts, double* recv,
+                               const long long* recv_counts, void* stream);
+cfs_status cfs_set_exchange(cfs_ctx* ctx, cfs_exchange_fn fn, void* user);
+
+/* The exchange plan of a partitioned context (host; cfs_finalize need not have been called):
+ * which = 0 the points this rank sends to `peer` -- its own points that peer's sub-domains read
+ * (faces to the halo depth, 5 with the filter, viscous edges to r x r) --, which = 1 those it
+ * receives from peer.  *count receives the number of points; offsets (host, may be NULL) receives
+ * their state offsets (block base + point index; variable v at + v x the block's points), sorted.
+ * Rank p's send list to q equals rank q's receive list from p.  ESTATE without a partition. */
+cfs_status cfs_exchange_plan(cfs_ctx* ctx, int peer, int which, long long* offsets, long long* count);
+
+/* Exchange callbacks made by the last cfs_step call. */
+cfs_status cfs_exchange_count(cfs_ctx* ctx, long long* n);
 
 /* Counters of the last cfs_step call: number of kernel launches issued. */
 cfs_status cfs_launch_count(cfs_ctx* ctx, long long* launches);
@@ -284,8 +340,13 @@ cfs_status cfs_mlp_adamw(float* params, const float* grad, float* m, float* v, i
  * current halo values): spec (device int32 [n][5]) = (sub-domain, face 0..5, t1, t2, delay k) with
  * t1, t2 the owned coordinates along the axes (a+1)%3 and (a+2)%3 of the face's axis a; scales
  * (host, 15 doubles: in_scale[5], own_scale[5], out_scale[5]); writes x (device BF16 [n][65]) and
- * target (device FP32 [n][20]).  Needs n >= 6 and a ring that holds levels n-6..n. */
-cfs_status cfs_halo_samples(cfs_ctx* ctx, const int* spec, long long n, const double* scales, uint16_t* x, float* target);
+ * target (device FP32 [n][20]).  Needs n >= 6 and a ring that holds levels n-6..n.  at4 (device FP32
+ * [n][20], or NULL): the residual of the AT4 stage-0 halo value of Eq. 15 -- the five-level
+ * extrapolation with c(k) from levels n-k .. n-k-4 -- over the true value, times out_scale, the
+ * same units as target: the error of the method the network replaces (needs the fourth-order
+ * scheme, max_delay >= 4 and n >= 8). */
+cfs_status cfs_halo_samples(cfs_ctx* ctx, const int* spec, long long n, const double* scales, uint16_t* x, float* target,
+                            float* at4);
 
 /* Use (enable = 1) or stop using (0) the network for the stage-0 face halos of AT steps: each step,
  * every face column's U_buf^(0) = extrapolation + y / out_scale; later stages add the AT buffer-update
@@ -306,7 +367,9 @@ cfs_status cfs_set_halo_model(cfs_ctx* ctx, const float* params, const double* s
  *     CFS_DIAG_STATIC_MAX_POINTS points; larger grids are rejected with CFS_EINVAL and a message.
  *   - No cudaMalloc, cudaFree or other allocating call is made.
  *   - The first call on each device (with that device current) looks up the array's device
- *     address; make that first call before any stream capture.
+ *     address and keeps it for the life of the process; make that first call before any stream
+ *     capture.  The kept address is not valid across a reset of the device (cudaDeviceReset):
+ *     do not call this entry point in a process after resetting the device it runs on.
  *   - All calls share the array; each call overwrites the partial sums it reads, so nothing has
  *     to be cleared, but calls whose GPU work overlaps (other streams, other host threads) race.
  *   - err (may be NULL) receives a message of at most err_len bytes on failure.

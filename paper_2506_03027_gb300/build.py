@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libcfs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "fused.cu", "filter_block.cu", "mlp.cu", "capi.cpp", "coeffs.cpp", "topology.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "fused.cu", "filter_block.cu", "mlp.cu", "capi.cpp", "coeffs.cpp", "topology.cpp", "partition.cpp", "noalloc.cu"]
 # fused.cu is instantiated for several tile shapes; without automatic FMA contraction (explicit
 # fma() calls are kept) every instantiation rounds identically, so results do not depend on the
 # launch shape the autotuner picks

@@ -22,8 +22,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libcfs.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "cfs.h")
 
-STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENAN", 6: "ETIMEOUT"}
-CFS_OK, CFS_EINVAL, CFS_ENOMEM, CFS_ECUDA, CFS_ESTATE, CFS_ENAN, CFS_ETIMEOUT = range(7)
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ENAN", 6: "ETIMEOUT", 7: "EXCHANGE"}
+CFS_OK, CFS_EINVAL, CFS_ENOMEM, CFS_ECUDA, CFS_ESTATE, CFS_ENAN, CFS_ETIMEOUT, CFS_EXCHANGE = range(8)
 ALGO = {"SA": 0, "CAA": 1, "SAA": 2}
 HOST, DEVICE = 0, 1
 
@@ -44,6 +44,10 @@ class CfsParams(ctypes.Structure):
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+# exchange transport of a partitioned context: (user, nranks, send, send_counts, recv, recv_counts, stream)
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                               ctypes.POINTER(ctypes.c_longlong), ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
+                               ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 _lib = None
@@ -79,6 +83,7 @@ def load() -> ctypes.CDLL:
             "cfs_set_bc": ([vp, ip, ip, ip, dp], ip),
             "cfs_set_face_shift": ([vp, ip, ip, dp], ip),
             "cfs_eval_power": ([vp, ctypes.c_double, vp, ll, vp], ip),
+            "cfs_fp64_probe": ([vp, ip, ip, vp], ip),
             "cfs_halo_sources": ([vp, ip, ip, ip, ip, dp], ip),
             "cfs_metric_terms": ([vp, ip, ip, ip, dp], ip),
             "cfs_finalize": ([vp, ip], ip),
@@ -95,6 +100,10 @@ def load() -> ctypes.CDLL:
             "cfs_set_ring": ([vp, vp, ip], ip),
             "cfs_at_weights": ([ip, ip, dp], ip),
             "cfs_launch_count": ([vp, ctypes.POINTER(ll)], ip),
+            "cfs_set_partition": ([vp, ip, ctypes.POINTER(ip), ip], ip),
+            "cfs_set_exchange": ([vp, EXCHANGE_FN, vp], ip),
+            "cfs_exchange_plan": ([vp, ip, ip, ctypes.POINTER(ll), ctypes.POINTER(ll)], ip),
+            "cfs_exchange_count": ([vp, ctypes.POINTER(ll)], ip),
             "cfs_set_timing": ([vp, ip], ip),
             "cfs_set_graph": ([vp, ip], ip),
             "cfs_set_tiles": ([vp, ip, ip, ip], ip),
@@ -104,7 +113,7 @@ def load() -> ctypes.CDLL:
             "cfs_mlp_grad": ([vp, vp, vp, ll, vp, vp, vp, vp], ip),
             "cfs_mlp_adamw": ([vp, vp, vp, vp, ip, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                ctypes.c_float, vp], ip),
-            "cfs_halo_samples": ([vp, vp, ll, dp, vp, vp], ip),
+            "cfs_halo_samples": ([vp, vp, ll, dp, vp, vp, vp], ip),
             "cfs_set_halo_model": ([vp, vp, dp, ip], ip),
             "cfs_diagnostics_static": ([vp, ip, ip, ip, dp, ip, vp, vp, ctypes.c_char_p, ctypes.c_size_t], ip),
             "cfs_last_error": ([vp], ctypes.c_char_p),
@@ -170,6 +179,55 @@ def cfs_eval_power(x, a: float, y, stream: int | None = None):
                                ctypes.c_void_p(stream or 0))
     if st != CFS_OK:
         raise CfsError(st, "cfs_eval_power failed")
+
+
+def cfs_fp64_probe(sink, blocks: int, iters: int, stream: int | None = None):
+    """Launch the FP64 pipe probe (blocks x 256 threads x iters x 8 FMAs) into a float64 device
+    tensor of blocks x 256 elements."""
+    assert sink.dtype.is_floating_point and sink.is_cuda and sink.numel() >= blocks * 256
+    st = load().cfs_fp64_probe(ctypes.c_void_p(sink.data_ptr()), blocks, iters, ctypes.c_void_p(stream or 0))
+    if st != CFS_OK:
+        raise CfsError(st, "cfs_fp64_probe failed")
+
+
+def cfs_set_partition(ctx, nranks: int, starts, rank: int):
+    """Compute sub-domains [starts[rank], starts[rank + 1]) of a grid split over nranks processes."""
+    st = (ctypes.c_int * (nranks + 1))(*[int(x) for x in starts])
+    _check(ctx, load().cfs_set_partition(ctx, nranks, st, rank))
+
+
+def cfs_set_exchange(ctx, fn):
+    """Install a transport: fn(nranks, send_ptr, send_counts, recv_ptr, recv_counts, stream_ptr) -> None
+    (counts in doubles per peer, device pointers as ints); an exception makes cfs_step fail with
+    EXCHANGE.  Returns the ctypes callback, which the caller keeps alive."""
+    def tramp(user, nranks, send, scnt, recv, rcnt, stream):
+        try:
+            fn(nranks, send or 0, [scnt[q] for q in range(nranks)], recv or 0, [rcnt[q] for q in range(nranks)],
+               stream or 0)
+            return 0
+        except Exception:  # noqa: BLE001 -- reported to the library as a failed exchange
+            import traceback
+            traceback.print_exc()
+            return 1
+    cb = EXCHANGE_FN(tramp)
+    _check(ctx, load().cfs_set_exchange(ctx, cb, None))
+    return cb
+
+
+def cfs_exchange_plan(ctx, peer: int, which: int) -> np.ndarray:
+    """State offsets of the points this rank sends to (which = 0) or receives from (1) `peer`."""
+    n = ctypes.c_longlong()
+    _check(ctx, load().cfs_exchange_plan(ctx, peer, which, None, ctypes.byref(n)))
+    out = np.zeros(max(n.value, 1), dtype=np.int64)
+    _check(ctx, load().cfs_exchange_plan(ctx, peer, which, out.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                         ctypes.byref(n)))
+    return out[: n.value]
+
+
+def cfs_exchange_count(ctx) -> int:
+    n = ctypes.c_longlong()
+    _check(ctx, load().cfs_exchange_count(ctx, ctypes.byref(n)))
+    return n.value
 
 
 def cfs_halo_sources(ctx, block: int, i: int, j: int, k: int):
@@ -351,10 +409,12 @@ def cfs_mlp_adamw(params_ptr, grad_ptr, m_ptr, v_ptr, step, lr, beta1=0.9, beta2
         raise CfsError(st, "cfs_mlp_adamw failed")
 
 
-def cfs_halo_samples(ctx, spec_ptr: int, n: int, scales: np.ndarray, x_ptr: int, t_ptr: int):
+def cfs_halo_samples(ctx, spec_ptr: int, n: int, scales: np.ndarray, x_ptr: int, t_ptr: int, at4_ptr: int = 0):
+    """Training samples (features, residual targets) at the context's current step; at4_ptr (a device
+    FP32 [n][20] buffer, or 0) also receives the AT4 stage-0 residuals (Eq. 15) in target units."""
     sc = np.ascontiguousarray(scales, dtype=np.float64)
     _check(ctx, load().cfs_halo_samples(ctx, ctypes.c_void_p(spec_ptr), n, sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                        ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr)))
+                                        ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr), ctypes.c_void_p(at4_ptr or 0)))
 
 
 def cfs_set_halo_model(ctx, params: np.ndarray | None, scales: np.ndarray | None, enable: bool = True):
@@ -439,7 +499,8 @@ class Solver:
     (``case`` an ``inputs.MultiBlock``: blocks, their coordinates and their faces)."""
 
     def __init__(self, case, max_delay: int | None = None, precision: int = 0, stream=None,
-                 use_torch_allocator: bool = True, blocks=None, tiles=None, graph: bool = False):
+                 use_torch_allocator: bool = True, blocks=None, tiles=None, graph: bool = False,
+                 partition=None, exchange=None):
         import torch
         from .inputs import MultiBlock
         self.torch = torch
@@ -458,6 +519,12 @@ class Solver:
             self.alloc = TorchAllocator(self.device)
             cfs_set_allocator(self.ctx, self.alloc.alloc_cb, self.alloc.free_cb)
         describe_blocks(self.ctx, self.blocks, mb)
+        self._xcb = None
+        if partition is not None:
+            # (nranks, starts, rank): this process computes sub-domains starts[rank] .. starts[rank+1]-1
+            cfs_set_partition(self.ctx, partition[0], partition[1], partition[2])
+            if exchange is not None:
+                self._xcb = cfs_set_exchange(self.ctx, exchange)
         if tiles is not None:
             cfs_set_tiles(self.ctx, *tiles)
         if max_delay is None:

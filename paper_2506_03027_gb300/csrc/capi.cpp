@@ -118,6 +118,23 @@ struct cfs_ctx {
   cudaGraphExec_t gexec = nullptr;
   long long graph_launches = 0;  // kernel launches captured in one step
 
+  // partitioned context (cfs_set_partition): this process computes sub-domains
+  // [part_starts[part_rank], part_starts[part_rank + 1]); boundary strips travel through the
+  // exchange callback
+  int part_n = 1, part_rank = 0;
+  std::vector<int> part_starts;
+  cfs_exchange_fn xfn = nullptr;
+  void* xuser = nullptr;
+  std::vector<long long> x_send_cnt, x_recv_cnt;  // per peer, in doubles (5 x points)
+  long long x_nsend = 0, x_nrecv = 0;             // points
+  long long* d_x_send = nullptr;
+  long long* d_x_recv = nullptr;
+  int* d_x_send_n = nullptr;
+  int* d_x_recv_n = nullptr;
+  double* d_x_sbuf = nullptr;
+  double* d_x_rbuf = nullptr;
+  long long exchanges = 0;                        // callbacks made by the last cfs_step
+
   // per-kernel event timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -463,6 +480,7 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
               }
           }
           d.ebase = -1;
+          d.own = 1;
           d.gmx = b.nx + 2 * need;
           d.gmy = b.ny + 2 * need;
           for (int a = 0; a < 3; ++a) {  // CD coefficients of Eq. 2 (alpha = 0) for the block's spacing
@@ -480,6 +498,21 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
           c->max_flux = (int)std::max<long long>(c->max_flux, nfl);
           c->subs[b.sid0 + ix + b.P[0] * (iy + b.P[1] * iz)] = d;
         }
+  // partitioned context: validate, mark the sub-domains another process computes
+  const bool parted = c->part_n > 1;
+  cfs::StripPlan plan;
+  if (parted) {
+    if (c->p.precision != 0 || c->learned) return fail(c, CFS_EINVAL, "a partitioned context runs the FP64 path only");
+    if (!c->all_periodic) return fail(c, CFS_EINVAL, "a partitioned context needs blocks periodic on every face");
+    if ((int)c->part_starts.size() != c->part_n + 1 || c->part_starts[c->part_n] != nsub)
+      return fail(c, CFS_EINVAL, "the partition does not cover the sub-domains");
+    for (int sid = 0; sid < nsub; ++sid)
+      c->subs[sid].own = (sid >= c->part_starts[c->part_rank] && sid < c->part_starts[c->part_rank + 1]) ? 1 : 0;
+    const int depth = need, depth_z = c->ndim == 3 ? need : 0;
+    if (const char* why = cfs::strip_plan(topo.data(), (int)topo.size(), nsub, c->part_starts.data(), c->part_n,
+                                          c->part_rank, depth, depth_z, c->r, c->p.viscous != 0, c->ndim, &plan))
+      return fail(c, CFS_EINVAL, why);
+  }
   c->max_delay = max_delay;
   c->R = max_delay + c->C + 1;
   const long long N = Ntot;
@@ -657,6 +690,7 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
     std::vector<int> hl;
     for (int sid = 0; sid < nsub; ++sid) {
       const SubDev& d = c->subs[sid];
+      if (!d.own) continue;  // computed by another process
       for (int k = 0; k < d.ez; ++k)
         for (int j = 0; j < d.ey; ++j)
           for (int i = 0; i < d.ex; ++i) {
@@ -676,6 +710,34 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
       c->d_halo = (int*)dev_alloc(c, sizeof(int) * hl.size());
       if (!c->d_halo) return fail(c, CFS_ENOMEM, "device allocation failed");
       CUDA_TRY(c, cudaMemcpy(c->d_halo, hl.data(), sizeof(int) * hl.size(), cudaMemcpyHostToDevice), "upload halo list");
+    }
+  }
+  // exchange plan of a partitioned context: state offsets and block sizes of the strips sent to /
+  // received from every peer, and the packed buffers (5 values per point)
+  if (parted) {
+    c->x_nsend = (long long)plan.send.size();
+    c->x_nrecv = (long long)plan.recv.size();
+    c->x_send_cnt.assign(c->part_n, 0);
+    c->x_recv_cnt.assign(c->part_n, 0);
+    for (int q = 0; q < c->part_n; ++q) {
+      c->x_send_cnt[q] = 5 * (plan.send_off[q + 1] - plan.send_off[q]);
+      c->x_recv_cnt[q] = 5 * (plan.recv_off[q + 1] - plan.recv_off[q]);
+    }
+    c->d_x_send = (long long*)dev_alloc(c, sizeof(long long) * (c->x_nsend + 1));
+    c->d_x_recv = (long long*)dev_alloc(c, sizeof(long long) * (c->x_nrecv + 1));
+    c->d_x_send_n = (int*)dev_alloc(c, sizeof(int) * (c->x_nsend + 1));
+    c->d_x_recv_n = (int*)dev_alloc(c, sizeof(int) * (c->x_nrecv + 1));
+    c->d_x_sbuf = (double*)dev_alloc(c, sizeof(double) * 5 * (c->x_nsend + 1));
+    c->d_x_rbuf = (double*)dev_alloc(c, sizeof(double) * 5 * (c->x_nrecv + 1));
+    if (!c->d_x_send || !c->d_x_recv || !c->d_x_send_n || !c->d_x_recv_n || !c->d_x_sbuf || !c->d_x_rbuf)
+      return fail(c, CFS_ENOMEM, "device allocation failed");
+    if (c->x_nsend) {
+      CUDA_TRY(c, cudaMemcpy(c->d_x_send, plan.send.data(), sizeof(long long) * c->x_nsend, cudaMemcpyHostToDevice), "upload plan");
+      CUDA_TRY(c, cudaMemcpy(c->d_x_send_n, plan.send_bN.data(), sizeof(int) * c->x_nsend, cudaMemcpyHostToDevice), "upload plan");
+    }
+    if (c->x_nrecv) {
+      CUDA_TRY(c, cudaMemcpy(c->d_x_recv, plan.recv.data(), sizeof(long long) * c->x_nrecv, cudaMemcpyHostToDevice), "upload plan");
+      CUDA_TRY(c, cudaMemcpy(c->d_x_recv_n, plan.recv_bN.data(), sizeof(int) * c->x_nrecv, cudaMemcpyHostToDevice), "upload plan");
     }
   }
   // host tables
@@ -831,6 +893,24 @@ static int launch_fblock(cfs_ctx* c, const Geometry& g, const StepSched& sc, con
   return cfs::launch_filter_block(g, sc, f, c->fblock_n, c->stream, &c->launches, tm);
 }
 
+// Exchange of the boundary strips of state array U with the other processes of a partitioned
+// context: pack the points the peers read from U, hand both buffers to the caller's transport,
+// unpack what arrived into U (the neighbouring PEs' messages of Alg. 1-3).
+static cfs_status exchange_strips(cfs_ctx* c, double* U) {
+  if (c->part_n <= 1) return CFS_OK;
+  if (!c->xfn) return fail(c, CFS_ESTATE, "a partitioned context needs an exchange callback (cfs_set_exchange)");
+  int rc = cfs::launch_strip_pack(U, c->d_x_send, c->d_x_send_n, c->x_nsend, c->d_x_sbuf, c->stream);
+  if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "strip pack");
+  const int xr = c->xfn(c->xuser, c->part_n, c->d_x_sbuf, c->x_send_cnt.data(), c->d_x_rbuf, c->x_recv_cnt.data(),
+                        (void*)c->stream);
+  if (xr != 0) return fail(c, CFS_EXCHANGE, "the exchange callback reported a failure");
+  rc = cfs::launch_strip_unpack(U, c->d_x_recv, c->d_x_recv_n, c->x_nrecv, c->d_x_rbuf, c->stream);
+  if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "strip unpack");
+  c->launches += 2;
+  c->exchanges += 1;
+  return CFS_OK;
+}
+
 // Enqueue the kernels of step n on the context's stream.  graph = true: the step index and
 // everything derived from it (mode, delays, ring slots) are read by the kernels from d_n, so the
 // enqueued sequence is the same for every step and can be captured once.
@@ -875,6 +955,12 @@ static cfs_status enqueue_step(cfs_ctx* c, long long n, bool graph) {
     double* dst = last_op ? (graph ? nullptr : level_ptr(c, n + 1)) : c->buf[pp];
     const int in_ring = graph && op == 0, out_ring = graph && last_op;
     int rc;
+    // partitioned context, synchronous step: the neighbours' strips of this stage's (or filter
+    // pass's) input -- the previous operation's output -- before it is read (Alg. 1)
+    if (c->part_n > 1 && sc.mode == 0 && op > 0) {
+      const cfs_status xs = exchange_strips(c, const_cast<double*>(src));
+      if (xs != CFS_OK) return xs;
+    }
     if (op < c->s && c->fused) {
       cfs::FusedLaunch a{};
       a.Uin = src; a.Uout = dst; a.Q = c->Q; a.subs = c->d_subs; a.work = c->d_work; a.nwork = c->nwork;
@@ -929,6 +1015,7 @@ static cfs_status enqueue_step(cfs_ctx* c, long long n, bool graph) {
         for (int m = 0; m < 6; ++m) f.h[m] = c->filt_h[m];
         f.b1 = c->filt_h[1] - c->p.alpha_f;
         f.only_sync = graph && c->fblock_n;
+        f.subs = c->part_n > 1 ? c->d_subs : nullptr;
         rc = cfs::launch_filter(g, sc, f, op - c->s, c->p.precision, c->stream, &c->launches, tm);
         if (rc != 0) break;
       }
@@ -942,6 +1029,9 @@ static cfs_status enqueue_step(cfs_ctx* c, long long n, bool graph) {
     if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
     c->launches += 1;
   }
+  // partitioned context: publish the boundary strips of U^{n+1} into the neighbours' level n + 1
+  // (the send of Alg. 1-3; delayed levels are then read from the ring as on one process)
+  if (c->part_n > 1) return exchange_strips(c, level_ptr(c, n + 1));
   return CFS_OK;
 }
 
@@ -975,6 +1065,7 @@ cfs_status cfs_step(cfs_ctx* c, long long nsteps) {
   if (c->sticky) return CFS_ECUDA;
   if (nsteps < 0) return fail(c, CFS_EINVAL, "negative step count");
   c->launches = 0;
+  c->exchanges = 0;
   if (c->algo == 2) {  // asynchronous SAA steps need their rows of the delay table
     const long long last = c->n + nsteps - 1;
     if (nsteps > 0 && last >= c->C && last >= c->sched_steps) {
@@ -1022,6 +1113,7 @@ cfs_status cfs_set_tiles(cfs_ctx* c, int fy, int zc, int threads) {
 cfs_status cfs_set_graph(cfs_ctx* c, int on) {
   if (!c) return CFS_EINVAL;
   if (on && c->stream == nullptr) return fail(c, CFS_EINVAL, "graph mode needs a created (non-default) stream");
+  if (on && c->part_n > 1) return fail(c, CFS_EINVAL, "a partitioned context steps without a graph (host exchanges)");
   c->graph_on = on != 0;
   c->graph_dirty = true;
   return CFS_OK;
@@ -1075,6 +1167,14 @@ cfs_status cfs_diagnostics(cfs_ctx* c, double* out) {
         db.c1[a] = a_cd / 2.0;
         db.c2[a] = b_cd / 4.0;
       }
+    if (c->part_n > 1) {  // only the points of the sub-domains computed here
+      db.subs = c->d_subs;
+      for (int a = 0; a < 3; ++a) {
+        db.owner[a] = b.d_owner[a];
+        db.P[a] = b.P[a];
+      }
+      db.sid0 = b.sid0;
+    }
     int rc = cfs::launch_diagnostics_block(c->geo, db, U, c->d_partial, row, c->diag_blocks, c->stream);
     if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "diagnostics launch");
     row += c->diag_blocks;
@@ -1093,6 +1193,11 @@ cfs_status cfs_eval_power(const double* x, double a, double* y, long long n, voi
   if (n < 0 || (n > 0 && (!x || !y))) return CFS_EINVAL;
   if (n > (1LL << 40)) return CFS_EINVAL;
   return cfs::launch_eval_power(x, a, y, n, stream) == 0 ? CFS_OK : CFS_ECUDA;
+}
+
+cfs_status cfs_fp64_probe(double* sink, int blocks, int iters, void* stream) {
+  if (!sink || blocks < 1 || blocks > (1 << 20) || iters < 1) return CFS_EINVAL;
+  return cfs::launch_fp64_probe(sink, blocks, iters, stream) == 0 ? CFS_OK : CFS_ECUDA;
 }
 
 cfs_status cfs_ring_depth(cfs_ctx* c, int* R) {
@@ -1167,17 +1272,22 @@ static cfs::MlpScales scales_from(const double* sc) {
   return m;
 }
 
-cfs_status cfs_halo_samples(cfs_ctx* c, const int* spec, long long n, const double* scales, uint16_t* x, float* target) {
+cfs_status cfs_halo_samples(cfs_ctx* c, const int* spec, long long n, const double* scales, uint16_t* x, float* target,
+                            float* at4) {
   if (!c || !spec || !scales || !x || !target || n < 0) return CFS_EINVAL;
   if (!c->finalized) return fail(c, CFS_ESTATE, "samples after cfs_finalize");
   if (c->sticky) return CFS_ECUDA;
   if (c->n < MLP_KMAX + 2 || c->R < MLP_KMAX + 3)
     return fail(c, CFS_ESTATE, "samples need levels n-k-2 for k up to 4 in the ring (n >= 6, max_delay >= 2)");
+  if (at4 && (c->p.order != 4 || c->n < MLP_KMAX + c->C - 1 || c->R < MLP_KMAX + c->C || c->max_delay < MLP_KMAX))
+    return fail(c, CFS_ESTATE, "AT4 residuals need the fourth-order scheme, max_delay >= 4 and levels n-8..n (n >= 8)");
   StepSched sc{};
   sc.n = c->n;
   sc.R = c->R;
   sc.C = c->C;
-  const int rc = cfs::launch_halo_samples(c->geo, sc, c->ring, c->d_subs, spec, n, scales_from(scales), x, target, c->stream);
+  sc.W = c->d_W;
+  const int rc = cfs::launch_halo_samples(c->geo, sc, c->ring, c->d_subs, spec, n, scales_from(scales), x, target, at4,
+                                          c->s, c->stream);
   if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "samples launch");
   return CFS_OK;
 }
@@ -1191,6 +1301,7 @@ cfs_status cfs_set_halo_model(cfs_ctx* c, const float* params, const double* sca
     return CFS_OK;
   }
   if (!params || !scales) return fail(c, CFS_EINVAL, "model parameters and scales required");
+  if (c->part_n > 1) return fail(c, CFS_EINVAL, "a partitioned context runs the plain AT halos");
   if (!c->all_periodic) return fail(c, CFS_EINVAL, "the halo model needs blocks periodic on every face");
   if (c->max_delay > MLP_KMAX) return fail(c, CFS_EINVAL, "the halo model covers delays 0..4: max_delay must be <= 4");
   if (c->G < MLP_HDEPTH) return fail(c, CFS_EINVAL, "the halo model needs a face halo of depth 4 (viscous CD4)");
@@ -1223,6 +1334,57 @@ cfs_status cfs_set_halo_model(cfs_ctx* c, const float* params, const double* sca
   c->mlp_scales = scales_from(scales);
   c->learned = true;
   c->graph_dirty = true;
+  return CFS_OK;
+}
+
+cfs_status cfs_set_partition(cfs_ctx* c, int nranks, const int* starts, int rank) {
+  if (!c) return CFS_EINVAL;
+  if (c->finalized) return fail(c, CFS_ESTATE, "partition before cfs_finalize");
+  if (nranks < 1 || rank < 0 || rank >= nranks || !starts) return fail(c, CFS_EINVAL, "bad partition");
+  if (starts[0] != 0) return fail(c, CFS_EINVAL, "the partition starts at sub-domain 0");
+  for (int q = 0; q < nranks; ++q)
+    if (starts[q + 1] < starts[q]) return fail(c, CFS_EINVAL, "partition boundaries must not decrease");
+  if (nranks > 1 && c->graph_on) return fail(c, CFS_EINVAL, "a partitioned context steps without a graph");
+  c->part_n = nranks;
+  c->part_rank = rank;
+  c->part_starts.assign(starts, starts + nranks + 1);
+  return CFS_OK;
+}
+
+cfs_status cfs_set_exchange(cfs_ctx* c, cfs_exchange_fn fn, void* user) {
+  if (!c) return CFS_EINVAL;
+  c->xfn = fn;
+  c->xuser = user;
+  return CFS_OK;
+}
+
+cfs_status cfs_exchange_plan(cfs_ctx* c, int peer, int which, long long* offsets, long long* count) {
+  if (!c || !count || (which != 0 && which != 1)) return CFS_EINVAL;
+  if (c->part_n <= 1) return fail(c, CFS_ESTATE, "no partition set");
+  if (peer < 0 || peer >= c->part_n) return fail(c, CFS_EINVAL, "peer out of range");
+  std::vector<cfs::TopoBlock> topo;
+  if (const char* why = host_topology(c, topo)) return fail(c, CFS_EINVAL, why);
+  int nsub = 0;
+  for (const Block& b : c->blocks) nsub += b.P[0] * b.P[1] * b.P[2];
+  if ((int)c->part_starts.size() != c->part_n + 1 || c->part_starts[c->part_n] != nsub)
+    return fail(c, CFS_EINVAL, "the partition does not cover the sub-domains");
+  const int need = c->p.filter ? (c->G > 5 ? c->G : 5) : c->G;
+  cfs::StripPlan plan;
+  if (const char* why = cfs::strip_plan(topo.data(), (int)topo.size(), nsub, c->part_starts.data(), c->part_n,
+                                        c->part_rank, need, c->ndim == 3 ? need : 0, c->r, c->p.viscous != 0, c->ndim,
+                                        &plan))
+    return fail(c, CFS_EINVAL, why);
+  const std::vector<long long>& off = which == 0 ? plan.send_off : plan.recv_off;
+  const std::vector<long long>& lst = which == 0 ? plan.send : plan.recv;
+  *count = off[peer + 1] - off[peer];
+  if (offsets)
+    for (long long i = 0; i < *count; ++i) offsets[i] = lst[off[peer] + i];
+  return CFS_OK;
+}
+
+cfs_status cfs_exchange_count(cfs_ctx* c, long long* n) {
+  if (!c || !n) return CFS_EINVAL;
+  *n = c->exchanges;
   return CFS_OK;
 }
 

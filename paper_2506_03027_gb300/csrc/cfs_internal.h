@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #define CFS_MAX_DELAY 15   // largest supported delay k (ring depth <= 15 + 5 + 1)
 #define CFS_MAX_LEVELS 5   // C: delayed levels of AT4
@@ -52,6 +53,10 @@ struct SubDev {
   // plane gmx * gmy); -1 for a block periodic on every face
   long long ebase;
   int gmx, gmy;
+  // 1: this context computes the sub-domain; 0: another process owns it (a partitioned context,
+  // cfs_set_partition): its points are neither updated nor read here except through the strips
+  // the exchange delivers
+  int own;
 };
 
 // Sources of the state at a point beyond a non-periodic block face (an interface, a wall mirror,
@@ -218,6 +223,8 @@ struct FilterLaunch {
   double h[6];             // filter right side: a_0, a_1/2, ..., a_5/2
   double b1;               // a_1/2 - alpha: weight of the first second difference (increment form)
   int only_sync;           // graph mode beside the sub-domain filter: return unless the step is synchronous
+  const SubDev* subs;      // partitioned context: the sub-domain table (lines of foreign sub-domains are
+                           // skipped); null when every sub-domain is computed here
 };
 
 // FP32-intermediate filter of asynchronous steps, all three passes per (sub-domain, variable)
@@ -283,8 +290,9 @@ struct MlpScales {
 };
 // Samples for training: spec[i] = (sub-domain, face, t1, t2, k); features from levels n-k..n-k-2 of
 // the ring (halo) and n, n-k (own), target = (U^n - 3-level extrapolation) * out scale.
+// at4 (or null): the residual of the AT4 stage-0 value (5 levels, weights sc.W of s stages) likewise.
 int launch_halo_samples(const Geometry& g, const StepSched& sc, const double* ring, const SubDev* subs, const int* spec,
-                        long long n, MlpScales sc_, void* x_bf16, float* target, void* stream);
+                        long long n, MlpScales sc_, void* x_bf16, float* target, float* at4, int s, void* stream);
 // Solver: stage-0 halo values of every face column from the network (AT mode), into LH[5][Ptot].
 int launch_mlp_halo(const Geometry& g, const StepSched& sc, const double* ring, const SubDev* subs, const int* cols,
                     long long ncol, const float* params, MlpScales sc_, double* LH, void* stream, long long* launches,
@@ -301,6 +309,12 @@ struct DiagBlock {
   long long mpl;    // its component stride
   int nonper;       // bit f: face f is not periodic (no enstrophy within the stencil radius of it)
   int rs;           // stencil radius
+  // partitioned context: only the points of sub-domains computed here count (owner[a][coordinate]
+  // = sub-domain index along axis a, P the split, sid0 the block's first sub-domain); subs null
+  // when every sub-domain is computed here
+  const SubDev* subs;
+  const int* owner[3];
+  int P[3], sid0;
 };
 #define DIAG_NQ 9   // per block row: K, enstrophy, 5 totals, non-finite flag, enstrophy volume
 int launch_diagnostics_block(const Geometry& g, const DiagBlock& b, const double* U, double* partial, int row0,
@@ -308,6 +322,24 @@ int launch_diagnostics_block(const Geometry& g, const DiagBlock& b, const double
 int launch_diagnostics_final(const double* partial, int nrows, double* out, double volume, void* stream);
 int launch_advance_step(long long* dn, void* stream);
 int launch_eval_power(const double* x, double a, double* y, long long n, void* stream);
-int pow_tables_init();  // tables of the FP64 power, once per process; nonzero on a CUDA error
+int launch_fp64_probe(double* sink, int blocks, int iters, void* stream);
+// Strip exchange of a partitioned context: buf[5 i + v] = U[off[i] + v bN[i]] (pack) and the
+// reverse (unpack) for the n entries of a plan.
+int launch_strip_pack(const double* U, const long long* off, const int* bN, long long n, double* buf, void* stream);
+int launch_strip_unpack(double* U, const long long* off, const int* bN, long long n, const double* buf, void* stream);
+
+// Exchange plan of a partitioned context (partition.cpp): for this rank and every peer q, the state
+// offsets (block base + point index; component v at + v x the block's points) of the points it
+// sends to q -- its own points that q's sub-domains read -- and of those it receives from q,
+// both sorted, so that rank p's send list to q is rank q's receive list from p.  The read set of
+// a sub-domain: faces to depth `depth` (x, y; z to depth_z), viscous edges to r x r.
+struct StripPlan {
+  std::vector<long long> send_off, recv_off;  // [nranks + 1] prefix offsets into the lists (points)
+  std::vector<long long> send, recv;          // state offsets
+  std::vector<int> send_bN, recv_bN;          // points of the entry's block
+};
+const char* strip_plan(const TopoBlock* B, int nb, int nsub, const int* starts, int nranks, int rank, int depth,
+                       int depth_z, int r, bool viscous, int ndim, StripPlan* out);
+int pow_tables_init();  // tables of the FP64 power on the current device, once per device; nonzero on a CUDA error
 
 }  // namespace cfs

@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(512) k_view_own(Geometry g, Physics ph, StepSc
   const double* Uin = ring_or(Uin0, in_ring, ring, sc, 0);
   const int sid = blockIdx.y;
   const SubDev d = subs[sid];
+  if (!d.own) return;  // another process's sub-domain
   const int t = blockIdx.x * blockDim.x + threadIdx.x;  // own points of a sub-domain: < 2^31
   if (t >= d.sx * d.sy * d.sz) return;
   const int sxy = d.sx * d.sy, ck = t / sxy, r2 = t - ck * sxy, cj = r2 / d.sx, ci = r2 - cj * d.sx;
@@ -336,6 +337,7 @@ __global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubD
                                               const T* __restrict__ Wp, T* __restrict__ Phi) {
   const int sid = blockIdx.y;
   const SubDev d = subs[sid];
+  if (!d.own) return;  // another process's sub-domain
   const int r = g.r;
   const int rz = (ND == 3) ? r : 0;
   const int fx = d.sx + 2 * r, fy = d.sy + 2 * r, fz = d.sz + 2 * rz;
@@ -427,6 +429,7 @@ __global__ void __launch_bounds__(512) k_rk(Geometry g, Physics ph, StepSched sc
   double* Uout = const_cast<double*>(ring_or(Uout0, out_ring, ring, sc, 1));
   const int sid = blockIdx.y;
   const SubDev d = subs[sid];
+  if (!d.own) return;  // another process's sub-domain
   const int t = blockIdx.x * blockDim.x + threadIdx.x;  // own points of a sub-domain: < 2^31
   if (t >= d.sx * d.sy * d.sz) return;
   const int sxy = d.sx * d.sy, ck = t / sxy, r2 = t - ck * sxy, cj = r2 / d.sx, ci = r2 - cj * d.sx;
@@ -578,11 +581,20 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
   __shared__ int sKd[2][128];
   __shared__ int sSid[128], sT1[128], sT2[128];  // blocks with a gather map: the line's sub-domain and position
   __shared__ double sRef[128];                   // FP32 form: the line's first own value
+  __shared__ unsigned char sOk[128];             // the line belongs to a sub-domain computed here
   const bool gmap = f.ebase >= 0;
   for (int t = threadIdx.x; t < nlines; t += blockDim.x) {
     const long long t12 = l0 + t;
     const int t1 = (int)(t12 % n[f1]), t2 = (int)(t12 / n[f1]);
     sBase[t] = f.bbase + (long long)var * f.bN + (long long)t1 * strides[f1] + (long long)t2 * strides[f2];
+    sOk[t] = 1;
+    if (f.subs) {  // partitioned context: skip the lines of another process's sub-domains
+      int sidx[3];
+      sidx[axis] = seg;
+      sidx[f1] = f.owner[f1][t1];
+      sidx[f2] = f.owner[f2][t2];
+      sOk[t] = (unsigned char)f.subs[f.sid0 + sidx[0] + f.P[0] * (sidx[1] + f.P[1] * sidx[2])].own;
+    }
     int kl = 0, kr = 0;
     if (sc.mode != 0 || gmap) {
       int sidx[3];
@@ -603,7 +615,7 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
     }
     sKd[0][t] = kl;
     sKd[1][t] = kr;
-    if (F32) sRef[t] = Uin[sBase[t] + (long long)off * st];
+    if (F32 && sOk[t]) sRef[t] = Uin[sBase[t] + (long long)off * st];
   }
   for (int t = threadIdx.x; t < W; t += blockDim.x) sPos[t] = (long long)wrapc(off + t - 5, n[axis]) * st;
   if (sc.mode != 0) {
@@ -670,12 +682,15 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
       // own points: a warp per line, lanes along it (contiguous in memory); the 10 window points
       // outside the segment: a thread per line, so that no warp mixes copies with extrapolations
       for (int line = warp; line < nlines; line += nwarp)
-        for (int i = 5 + lane; i < 5 + len; i += 32) cp_async8(tile + line * TW + i, Uin + sBase[line] + sPos[i]);
+        if (sOk[line])
+          for (int i = 5 + lane; i < 5 + len; i += 32) cp_async8(tile + line * TW + i, Uin + sBase[line] + sPos[i]);
       for (int line = threadIdx.x; line < nlines; line += blockDim.x)
-        for (int h = 0; h < 10; ++h) stage(line, h < 5 ? h : len + h);
+        if (sOk[line])
+          for (int h = 0; h < 10; ++h) stage(line, h < 5 ? h : len + h);
     } else {  // threads across lines (consecutive x)
       for (int line = threadIdx.x; line < nlines; line += blockDim.x)
-        for (int i = 0; i < W; ++i) stage(line, i);
+        if (sOk[line])
+          for (int i = 0; i < W; ++i) stage(line, i);
     }
   } else {
     // FP32 form: every value converted on arrival to its offset from the line's first own value
@@ -695,15 +710,18 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
     };
     if (axis == 0) {
       for (int line = warp; line < nlines; line += nwarp)
-        for (int i = 5 + lane; i < 5 + len; i += 32) put(line, i, Uin[sBase[line] + sPos[i]]);
+        if (sOk[line])
+          for (int i = 5 + lane; i < 5 + len; i += 32) put(line, i, Uin[sBase[line] + sPos[i]]);
       for (int line = threadIdx.x; line < nlines; line += blockDim.x)
-        for (int h = 0; h < 10; ++h) {
-          const int i = h < 5 ? h : len + h;
-          put(line, i, value(line, i));
-        }
+        if (sOk[line])
+          for (int h = 0; h < 10; ++h) {
+            const int i = h < 5 ? h : len + h;
+            put(line, i, value(line, i));
+          }
     } else {
       for (int line = threadIdx.x; line < nlines; line += blockDim.x)
-        for (int i = 0; i < W; ++i) put(line, i, value(line, i));
+        if (sOk[line])
+          for (int i = 0; i < W; ++i) put(line, i, value(line, i));
     }
   }
   cp_async_commit();
@@ -712,7 +730,7 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
 
   // ---- one line per thread
   const int line = threadIdx.x;
-  if (line < nlines) {
+  if (line < nlines && sOk[line]) {
     double* row = tile + line * TW;
     const double* cp = f.thomas + (long long)len * 2 * f.Lmax;
     const double* im = cp + f.Lmax;
@@ -805,16 +823,18 @@ __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, Filter
   };
   if (axis == 0) {
     for (int ln = warp; ln < nlines; ln += nwarp)
-      for (int i = lane; i < len; i += 32) {
-        const long long gi = sBase[ln] + sPos[i + 5];
-        Uout[gi] = result(ln, i, gi);
-      }
+      if (sOk[ln])
+        for (int i = lane; i < len; i += 32) {
+          const long long gi = sBase[ln] + sPos[i + 5];
+          Uout[gi] = result(ln, i, gi);
+        }
   } else {
     for (int ln = threadIdx.x; ln < nlines; ln += blockDim.x)
-      for (int i = 0; i < len; ++i) {
-        const long long gi = sBase[ln] + sPos[i + 5];
-        Uout[gi] = result(ln, i, gi);
-      }
+      if (sOk[ln])
+        for (int i = 0; i < len; ++i) {
+          const long long gi = sBase[ln] + sPos[i + 5];
+          Uout[gi] = result(ln, i, gi);
+        }
   }
 }
 
@@ -883,6 +903,7 @@ __global__ void __launch_bounds__(256) k_diag(DiagBlock b, const double* __restr
   const int ndim = b.nz > 1 ? 3 : 2;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < b.bN; i += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(i % b.nx), y = (int)((i / b.nx) % b.ny), z = (int)(i / ((long long)b.nx * b.ny));
+    if (b.subs && !b.subs[b.sid0 + b.owner[0][x] + b.P[0] * (b.owner[1][y] + b.P[1] * b.owner[2][z])].own) continue;
     const long long mq = (long long)(x + b.G) + (long long)b.mx * (y + b.G);  // metric plane index
     const double dV = b.M ? b.M[5 * b.mpl + mq] : b.dV;  // cell volume (J^-1 on a curvilinear grid)
     double u[5];
@@ -981,25 +1002,88 @@ __global__ void k_eval_power(const double* __restrict__ x, double a, double* __r
   if (i < n) y[i] = pow_tab(x[i], a);
 }
 
-// The tables of pow_tab, once per process (the device's copy of a __device__ array).
+// The tables of pow_tab in the current device's copy of the __device__ array, once per device
+// (each device that runs the power holds its own copy).  A failed upload is not remembered: the
+// next call on that device tries again.
 int pow_tables_init() {
-  static std::once_flag once;
-  static int rc = -1;
-  std::call_once(once, [] {
-    double t[3 * 64];
-    for (int j = 0; j < 64; ++j) {
-      t[j] = 128.0 / (129.0 + 2.0 * j);  // 1/c_j, c_j = (129 + 2j)/128
-      t[64 + j] = (double)log1pl((long double)(2 * j + 1) / 128.0L);
-      t[128 + j] = (double)exp2l((long double)j / 64.0L);
-    }
-    rc = (int)cudaMemcpyToSymbol(g_pow_tab, t, sizeof(t));
-  });
-  return rc;
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static bool done[kMaxDev] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  if (dev < 0 || dev >= kMaxDev) return (int)cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return 0;
+  double t[3 * 64];
+  for (int j = 0; j < 64; ++j) {
+    t[j] = 128.0 / (129.0 + 2.0 * j);  // 1/c_j, c_j = (129 + 2j)/128
+    t[64 + j] = (double)log1pl((long double)(2 * j + 1) / 128.0L);
+    t[128 + j] = (double)exp2l((long double)j / 64.0L);
+  }
+  e = cudaMemcpyToSymbol(g_pow_tab, t, sizeof(t));
+  if (e != cudaSuccess) return (int)e;
+  done[dev] = true;
+  return 0;
 }
 
 int launch_eval_power(const double* x, double a, double* y, long long n, void* stream) {
   if (int rc = pow_tables_init()) return rc;
   if (n > 0) k_eval_power<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, a, y, n);
+  return (int)cudaGetLastError();
+}
+
+// FP64 pipe probe: every thread runs 8 independent DFMA chains of `iters` steps (x <- x a + b,
+// with a = 1 - 2^-40 and b chosen so the values stay bounded) and writes one sum, so the pipe
+// has independent work and nothing is folded away.  DFMAs executed = blocks x threads x iters x 8.
+__global__ void __launch_bounds__(256) k_fp64_probe(double* __restrict__ sink, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x[c] = 1.0 + (threadIdx.x + c) * 1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) t += x[c];
+  sink[(long long)blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
+int launch_fp64_probe(double* sink, int blocks, int iters, void* stream) {
+  k_fp64_probe<<<blocks, 256, 0, (cudaStream_t)stream>>>(sink, iters, 1.0 - 0x1p-40, 0x1p-41);
+  return (int)cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------- strip exchange
+
+// Boundary strips of a partitioned context: one thread per (entry, variable), entries of a plan
+// in order, 5 values per entry (the layout sent to a peer).
+__global__ void k_strip_pack(const double* __restrict__ U, const long long* __restrict__ off, const int* __restrict__ bN,
+                             long long n, double* __restrict__ buf) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 5 * n) return;
+  const long long i = t / 5;
+  const int v = (int)(t - 5 * i);
+  buf[t] = U[off[i] + (long long)v * bN[i]];
+}
+
+__global__ void k_strip_unpack(double* __restrict__ U, const long long* __restrict__ off, const int* __restrict__ bN,
+                               long long n, const double* __restrict__ buf) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 5 * n) return;
+  const long long i = t / 5;
+  const int v = (int)(t - 5 * i);
+  U[off[i] + (long long)v * bN[i]] = buf[t];
+}
+
+int launch_strip_pack(const double* U, const long long* off, const int* bN, long long n, double* buf, void* stream) {
+  if (n > 0) k_strip_pack<<<(unsigned)((5 * n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(U, off, bN, n, buf);
+  return (int)cudaGetLastError();
+}
+
+int launch_strip_unpack(double* U, const long long* off, const int* bN, long long n, const double* buf, void* stream) {
+  if (n > 0) k_strip_unpack<<<(unsigned)((5 * n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(U, off, bN, n, buf);
   return (int)cudaGetLastError();
 }
 

@@ -307,9 +307,12 @@ struct At3Table {
 }  // namespace
 
 // One thread per training sample spec (sub-domain, face, t1, t2, k).
+// at4 (may be null): the residual of the AT4 stage-0 value of Eq. 15 -- the extrapolation from the
+// five levels n-k .. n-k-4 with the weights W^(0)(k) = c(k) of the context's table sc.W -- in the
+// same units, for comparing the network with the method it would replace.
 __global__ void k_halo_samples(Geometry g, StepSched sc, const double* __restrict__ ring, const SubDev* __restrict__ subs,
                                const int* __restrict__ spec, long long n, MlpScales ms, At3Table t3,
-                               __nv_bfloat16* __restrict__ x, float* __restrict__ target) {
+                               __nv_bfloat16* __restrict__ x, float* __restrict__ target, float* __restrict__ at4, int s) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int* sp = spec + 5 * i;
@@ -322,6 +325,24 @@ __global__ void k_halo_samples(Geometry g, StepSched sc, const double* __restric
   for (int q = 0; q <= MLP_KMAX; ++q) xrow[3 * MLP_HDEPTH * 5 + q] = (q == k) ? 1.f : 0.f;
   for (int e = 0; e < MLP_NIN; ++e) x[i * MLP_NIN + e] = __float2bfloat16_rn(xrow[e]);
   for (int e = 0; e < MLP_NOUT; ++e) target[i * MLP_NOUT + e] = (float)((truth[e] - at3[e]) * ms.out[e % 5]);
+  if (at4) {
+    const long long lvN = 5 * g.N;
+    const int nR = (int)(sc.n % sc.R);
+    const double* w = sc.W + (long long)k * s * sc.C;  // stage 0: c(k)
+    for (int j = 1; j <= MLP_HDEPTH; ++j) {
+      int c[3];
+      column_point(d, f, t1, t2, j, true, c);
+      const long long gh = global_index(g, d, c);
+      for (int v = 0; v < 5; ++v) {
+        double e = 0.0;
+        for (int l = 0; l < sc.C; ++l) {
+          const int q = nR - k - l;
+          e = fma(w[l], ring[(long long)(q < 0 ? q + sc.R : q) * lvN + v * d.bN + gh], e);
+        }
+        at4[i * MLP_NOUT + (j - 1) * 5 + v] = (float)((truth[(j - 1) * 5 + v] - e) * ms.out[v]);
+      }
+    }
+  }
 }
 
 // Solver use: each CTA takes TM = 128 face columns (sub-domain, face, t1, t2) at a time, gathers
@@ -651,10 +672,10 @@ static At3Table at3_table() {
 }
 
 int launch_halo_samples(const Geometry& g, const StepSched& sc, const double* ring, const SubDev* subs, const int* spec,
-                        long long n, MlpScales ms, void* x_bf16, float* target, void* stream) {
+                        long long n, MlpScales ms, void* x_bf16, float* target, float* at4, int s, void* stream) {
   if (n <= 0) return 0;
   k_halo_samples<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
-      g, sc, ring, subs, spec, n, ms, at3_table(), (__nv_bfloat16*)x_bf16, target);
+      g, sc, ring, subs, spec, n, ms, at3_table(), (__nv_bfloat16*)x_bf16, target, at4, s);
   return (int)cudaGetLastError();
 }
 

@@ -89,15 +89,19 @@ __global__ void __launch_bounds__(kThreads) k_diag_blocks(Grid g, const double* 
   }
 }
 
-// Fixed-order second pass: thread c sums quantity c over the blocks, in block order.
-__global__ void k_diag_blocks_final(const double* __restrict__ partials, long long nblocks, long long N,
-                                    double* __restrict__ out) {
-  const int c = threadIdx.x;
-  if (c >= 8) return;
+// Fixed-order second pass, one warp per quantity (8 warps): lane l sums the partials of blocks
+// l, l + 32, l + 64, ... in block order, then the 32 lane sums combine in a fixed shuffle tree.
+// The order depends only on the number of blocks, so the result is deterministic.
+__global__ void __launch_bounds__(256) k_diag_blocks_final(const double* __restrict__ partials, long long nblocks,
+                                                           long long N, double* __restrict__ out) {
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double v = 0.0;
-  for (long long b = 0; b < nblocks; ++b) v = (c == 7) ? fmax(v, partials[b * 8 + c]) : v + partials[b * 8 + c];
-  if (c < 2) v /= (double)N;
-  out[c] = v;
+  for (long long b = lane; b < nblocks; b += 32) v = (c == 7) ? fmax(v, partials[b * 8 + c]) : v + partials[b * 8 + c];
+  for (int o = 16; o > 0; o >>= 1) {
+    const double other = __shfl_down_sync(0xffffffffu, v, o);
+    v = (c == 7) ? fmax(v, other) : v + other;
+  }
+  if (lane == 0) out[c] = (c < 2) ? v / (double)N : v;
 }
 
 void put(char* err, size_t len, const char* msg) {
@@ -164,7 +168,7 @@ extern "C" cfs_status cfs_diagnostics_static(const double* U, int nx, int ny, in
   const long long nblocks = (N + kThreads - 1) / kThreads;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   k_diag_blocks<<<(unsigned)nblocks, kThreads, 0, st>>>(g, U, partials);
-  k_diag_blocks_final<<<1, 32, 0, st>>>(partials, nblocks, N, out);
+  k_diag_blocks_final<<<1, 256, 0, st>>>(partials, nblocks, N, out);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     put(err, err_len, cudaGetErrorString(e));

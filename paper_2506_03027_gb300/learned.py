@@ -45,28 +45,37 @@ def sample_specs(case: Case, n: int, rng: np.random.Generator) -> np.ndarray:
     return np.stack([sid, face, t1, t2, k], axis=1).astype(np.int32)
 
 
-def generate(case: Case, first_step: int, last_step: int, per_step: int, seed: int, scales: np.ndarray):
-    """Run the case synchronously and draw `per_step` samples at every step in [first_step,
-    last_step).  Returns device tensors (x BF16 bit patterns as int16 [n][65], target FP32 [n][20])."""
+def generate(case: Case, first_step: int, last_step: int, per_step: int, seed: int, scales: np.ndarray,
+             start=None, with_at4: bool = False):
+    """Run the case synchronously (from `start`, default its initial state) and draw `per_step`
+    samples at every step in [first_step, last_step).  Returns device tensors (x BF16 bit patterns
+    as int16 [n][65], target FP32 [n][20]) and, with with_at4, the AT4 stage-0 residuals of Eq. 15
+    in target units (FP32 [n][20]) as a third."""
     import torch
-    assert first_step >= KMAX + 2
+    assert first_step >= KMAX + (5 if with_at4 else 2)
     rng = np.random.default_rng(seed)
     sa = case.replace(algo="SA")
     s = cfs.Solver(sa, max_delay=KMAX)
     s.set_schedule()
-    s.set_state(initial_state(sa))
+    s.set_state(initial_state(sa) if start is None else start)
     s.step(first_step)
-    xs, ts = [], []
+    xs, ts, a4 = [], [], []
     for _ in range(first_step, last_step):
         spec = torch.from_numpy(sample_specs(sa, per_step, rng)).cuda()
         x = torch.empty((per_step, NIN), dtype=torch.int16, device="cuda")
         t = torch.empty((per_step, NOUT), dtype=torch.float32, device="cuda")
-        cfs.cfs_halo_samples(s.ctx, spec.data_ptr(), per_step, scales, x.data_ptr(), t.data_ptr())
+        a = torch.empty((per_step, NOUT), dtype=torch.float32, device="cuda") if with_at4 else None
+        cfs.cfs_halo_samples(s.ctx, spec.data_ptr(), per_step, scales, x.data_ptr(), t.data_ptr(),
+                             a.data_ptr() if with_at4 else 0)
         xs.append(x)
         ts.append(t)
+        if with_at4:
+            a4.append(a)
         s.step(1)
     torch.cuda.synchronize()
     s.close()
+    if with_at4:
+        return torch.cat(xs), torch.cat(ts), torch.cat(a4)
     return torch.cat(xs), torch.cat(ts)
 
 
@@ -77,10 +86,11 @@ def bf16_to_float(x):
         ((x.to(torch.int32) & 0xFFFF) << 16).view(torch.float32)
 
 
-def fit_scales(case: Case, seed: int = 1, first_step: int = 6, nsteps: int = 6, per_step: int = 20000) -> np.ndarray:
+def fit_scales(case: Case, seed: int = 1, first_step: int = 6, nsteps: int = 6, per_step: int = 20000,
+               start=None) -> np.ndarray:
     """Per-variable scales from unscaled samples: 1 / RMS of each feature group and of the target."""
     unit = np.ones(15)
-    X, T = generate(case, first_step, first_step + nsteps, per_step, seed, unit)
+    X, T = generate(case, first_step, first_step + nsteps, per_step, seed, unit, start=start)
     Xf = bf16_to_float(X).double().cpu().numpy()
     Tf = T.double().cpu().numpy()
     sc = np.ones(15)
@@ -143,13 +153,76 @@ def predict(params: np.ndarray, X):
     return y
 
 
-def halo_errors(params: np.ndarray, X, T) -> dict:
+def halo_errors(params: np.ndarray, X, T, A4=None) -> dict:
     """Mean squared error of the current-level halo values, in target units, of the three-level
-    extrapolation alone (target itself) and with the network's residual added."""
+    extrapolation alone (target itself), with the network's residual added, and (A4 given) of the
+    AT4 stage-0 value of Eq. 15 that the network replaces in the solver."""
     y = predict(params, X)
     base = float((T.double() ** 2).mean())
     net = float(((T - y).double() ** 2).mean())
-    return {"extrapolation3_mse": base, "learned_mse": net, "ratio": net / base if base > 0 else float("nan")}
+    out = {"extrapolation3_mse": base, "learned_mse": net, "ratio": net / base if base > 0 else float("nan")}
+    if A4 is not None:
+        at4 = float((A4.double() ** 2).mean())
+        out["at4_mse"] = at4
+        out["learned_over_at4"] = net / at4 if at4 > 0 else float("nan")
+    return out
+
+
+def developed_state(case: Case, t_end: float, cfl: float = 0.5):
+    """The synchronous run of the case's initial field to time t_end at CFL `cfl` (no delays):
+    a flow with the smaller scales of later times, from which the comparisons start."""
+    from .inputs import cfl_dt
+    U0 = initial_state(case)
+    dt = cfl_dt(case, U0, cfl)
+    n = int(math.ceil(t_end / dt))
+    c = case.replace(algo="SA", dt=t_end / n)
+    s = cfs.Solver(c)
+    try:
+        s.set_schedule()
+        s.set_state(U0)
+        s.step(n)
+        return s.get_state(), n
+    finally:
+        s.close()
+
+
+def solver_comparison(case: Case, start, params, scales, nsteps: int, seed: int = None) -> dict:
+    """SA, plain AT and the network's stage-0 halos on the same SAA schedule (delays 0..4), all from
+    `start`, for nsteps steps: each asynchronous run's relative L2 difference from the synchronous
+    run per conserved variable (rho, rho E against their own norms, momentum against the momentum
+    vector's) and the ms per step of each."""
+    import torch
+    from .inputs import saa_delays
+    saa = case.replace(algo="SAA", kmax=KMAX)
+    d = saa_delays(saa, nsteps, seed=seed)
+    res = {}
+    for name in ("SA", "AT", "learned"):
+        cc = case.replace(algo="SA") if name == "SA" else saa
+        s = cfs.Solver(cc, max_delay=KMAX)
+        try:
+            s.set_schedule(delays=d if name != "SA" else None)
+            if name == "learned":
+                cfs.cfs_set_halo_model(s.ctx, params, scales)
+            s.set_state(start)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.step(nsteps)
+            e1.record()
+            torch.cuda.synchronize()
+            res[name] = (s.get_state(), e0.elapsed_time(e1) / nsteps)
+        finally:
+            s.close()
+    ref = res["SA"][0]
+    mom = math.sqrt(sum(float(np.linalg.norm(ref[v])) ** 2 for v in (1, 2, 3)))
+
+    def err(U):
+        return [float(np.linalg.norm(U[v] - ref[v]) / (mom if v in (1, 2, 3) else np.linalg.norm(ref[v])))
+                for v in range(5)]
+    return {"rel_l2_vs_sa": {"AT": err(res["AT"][0]), "learned": err(res["learned"][0])},
+            "ms_per_step": {k: v[1] for k, v in res.items()}, "steps": nsteps, "dt": case.dt,
+            "finite": {k: bool(np.all(np.isfinite(v[0]))) for k, v in res.items()}}
 
 
 def solver_run(n: int = 160, p: int = 5, steps: int = 12, seed: int = 1) -> dict:

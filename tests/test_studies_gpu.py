@@ -43,3 +43,50 @@ def test_paper_vortex_orders_of_table1():
             assert row["orders"][0] >= row["expected_order"] - 0.4, row
     for algo in ("CAA", "SAA"):
         assert by[(2, f"{algo}-AS")]["errors"][-1] > 3.0 * by[(3, f"{algo}-AT")]["errors"][-1], algo
+
+
+# ------------------------------------------------------------------ parity at the study configurations
+
+def _check(Ug, Uo):
+    from gpu_util import PARITY_TOL, rel_l2, rel_l2_per_component
+    e = rel_l2(Ug, Uo)
+    assert np.all(np.isfinite(Ug))
+    assert np.all(e <= PARITY_TOL), (e, rel_l2_per_component(Ug, Uo))
+
+
+@pytest.mark.parametrize("L", [4, 8])
+def test_study_vortex_caa_parity(L):
+    """The configuration of the delay study (Sec. 5.1, Fig. 4) against the oracle, whole fields:
+    the translating vortex with LSERK2-CD2-AT2 (Table 1 case 3) under CAA-AT with maximum
+    allowable delay L, 64^2 on 4 x 4 sub-domains of 16^2, CFL 0.2, 60 steps (the first 3
+    synchronous)."""
+    ensure_built()
+    from gpu_util import gpu_run
+    from oracle import oracle as orc
+    from paper_2506_03027_gb300 import inputs as I
+    base = I.vortex_case(64, 4, order=2)
+    c = base.replace(dt=I.cfl_dt(base, I.vortex_state(base), 0.2), algo="CAA", at=True, caa_L=L, kmax=L - 1)
+    U0 = I.vortex_state(c)
+    Ug, _ = gpu_run(c, U0, 60)
+    Uo = orc.run(c, U0, 60)
+    _check(Ug, Uo)
+
+
+@pytest.mark.parametrize("order,algo,at,L", [(2, "SAA", True, 8), (2, "CAA", False, 8), (4, "SAA", True, 4),
+                                             (4, "CAA", True, 8), (2, "SAA", False, 8)])
+def test_paper_vortex_parity(order, algo, at, L):
+    """The paper's own vortex test (Sec. 5.1) against the oracle, whole fields: the Gaussian
+    vortex on [-8, 8]^2, 60^2 points on the three PEs of the paper, its time steps, Table 1 cases
+    2, 3 and 6 under CAA with L = 8 and SAA with delays from the arrival model of Alg. 3
+    (consecutive visible levels, reset at L); 60 steps."""
+    ensure_built()
+    from gpu_util import gpu_run
+    from oracle import oracle as orc
+    from paper_2506_03027_gb300 import inputs as I
+    c = I.paper_vortex_case(60, order=order, algo=algo, at=at, L=L)
+    nsteps = 60
+    d = I.saa_delays_arrival(c, nsteps, L, seed=1) if algo == "SAA" else None
+    U0 = I.paper_vortex_state(c)
+    Ug, _ = gpu_run(c, U0, nsteps, delays=d, max_delay=L - 1)
+    Uo = orc.run(c, U0, nsteps, delays=d)
+    _check(Ug, Uo)

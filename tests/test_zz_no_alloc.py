@@ -73,3 +73,44 @@ def test_static_diagnostics_reject_oversized_grid(torch):
         cfs.cfs_diagnostics_static(U.data_ptr(), 512, 256, 256, (1.0, 1.0, 1.0), 4, out.data_ptr())
     assert e.value.status == cfs.CFS_EINVAL
     assert "exceed" in str(e.value)
+
+
+def test_static_diagnostics_flag_a_non_finite_state(torch):
+    """A state with one NaN entry (made on the host): out[7] = 1 -- the asynchronous call returns
+    no CFS_ENAN, callers read the flag -- while the totals of the other variables stay those of
+    the finite state."""
+    c = I.vortex_case(32, 2)
+    U = I.vortex_state(c)
+    Ud = torch.from_numpy(U).cuda()
+    clean = static_diag(torch, c, Ud)
+    assert clean[7] == 0.0
+    Ubad = U.copy()
+    Ubad[4, 0, 5, 7] = np.nan
+    got = static_diag(torch, c, torch.from_numpy(Ubad).cuda())
+    assert got[7] == 1.0
+    np.testing.assert_array_equal(got[2:6], clean[2:6])   # rho, rho u, rho v, rho w untouched
+    assert np.isnan(got[6])                                # the total of rho E carries the NaN
+
+
+@pytest.mark.parametrize("case", ["order", "spacing", "null_U", "null_out", "null_spacing"])
+def test_static_diagnostics_reject_bad_arguments(torch, case):
+    """Invalid arguments are rejected on the host with CFS_EINVAL before any launch."""
+    U = torch.zeros((5, 1, 4, 4), dtype=torch.float64, device="cuda")
+    out = torch.zeros(8, dtype=torch.float64, device="cuda")
+    up, op, sp, order = U.data_ptr(), out.data_ptr(), (1.0, 1.0, 1.0), 4
+    if case == "order":
+        order = 3
+    elif case == "spacing":
+        sp = (1.0, 0.0, 1.0)
+    elif case == "null_U":
+        up = 0
+    elif case == "null_out":
+        op = 0
+    if case == "null_spacing":
+        st = cfs.load().cfs_diagnostics_static(cfs.ctypes.c_void_p(up), 4, 4, 1, None, order,
+                                               cfs.ctypes.c_void_p(op), None, None, 0)
+        assert st == cfs.CFS_EINVAL
+        return
+    with pytest.raises(cfs.CfsError) as e:
+        cfs.cfs_diagnostics_static(up, 4, 4, 1, sp, order, op)
+    assert e.value.status == cfs.CFS_EINVAL
