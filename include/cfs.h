@@ -178,7 +178,8 @@ cfs_status cfs_set_schedule(cfs_ctx* ctx, int algo, int at, int L, long long nst
 /* Copy the state of block `block` ([5][nz][ny][nx] of that block) in (set) or out (get).
  * where: 0 = host pointer, 1 = device pointer.  set_state defines the state at the current step index (0 after cfs_finalize; see
  * cfs_set_step) and is the start of a fresh history unless the ring is restored as well.
- * get_state synchronises the stream. */
+ * get_state synchronises the stream; it returns ETIMEOUT (with the state copied) when a bounded
+ * device wait gave up since the last report (cfs_wait_check). */
 cfs_status cfs_set_state(cfs_ctx* ctx, int block, const double* U, int where);
 cfs_status cfs_get_state(cfs_ctx* ctx, int block, double* U, int where);
 
@@ -208,12 +209,22 @@ cfs_status cfs_set_tiles(cfs_ctx* ctx, int fy, int zc, int threads);
  * Per-kernel timing (cfs_set_timing) bypasses the graph. */
 cfs_status cfs_set_graph(cfs_ctx* ctx, int on);
 
+/* Self-test of the bounded device waits (no counterpart in the paper: a check of the library's
+ * failure reporting).  The tensor-core kernels wait on mbarriers with a poll limit; a wait that gives
+ * up sets a status word of the context (and poisons that kernel's outputs with NaN), which the next
+ * synchronising call that returns data -- cfs_get_state, cfs_diagnostics -- reports once as
+ * CFS_ETIMEOUT, after which the context stays usable.  This call launches, on the context's stream,
+ * one CTA that waits on an mbarrier nothing arrives at, gives up after `limit` polls and sets the
+ * word.  ESTATE before cfs_finalize. */
+cfs_status cfs_wait_check(cfs_ctx* ctx, unsigned limit);
+
 /* Diagnostics of the current state U^n over all blocks (synchronises): out[8] = {K, enstrophy,
  * sum rho, sum rho u, sum rho v, sum rho w, sum rho E, non-finite flag}, K and enstrophy point averages
  * with rho_0 = 1 (Sec. 5.2), vorticity by the scheme's central difference, sums weighted by the
  * cell volume.  The enstrophy average covers the points whose difference stencils stay inside their
  * block or cross only periodic faces.  Returns ENAN (and fills out) when the state holds a
- * non-finite value. */
+ * non-finite value, ETIMEOUT (and fills out) when a bounded device wait gave up since the last
+ * report (cfs_wait_check). */
 cfs_status cfs_diagnostics(cfs_ctx* ctx, double* out);
 /* (On a partitioned context the diagnostics cover the points of the sub-domains computed here:
  * K, the totals and the non-finite flag combine over the processes by sums and a max; the

@@ -13,7 +13,9 @@
  *     point coordinates: strong conservation form Eq. A1 with the metric terms xi^_x = J^-1
  *     dxi/dx (cofactors of the coordinate derivatives, by the same CD scheme in index space) and
  *     the contravariant velocities of Eq. A2.
- *   - Eq. 2 / App. B: explicit central differences CD2 (a=1,b=0) and CD4 (a=4/3,b=-1/3).
+ *   - Eq. 2 / App. B: explicit central differences CD2 (a=1,b=0) and CD4 (a=4/3,b=-1/3); the
+ *     sixth-order compact scheme (alpha=1/3, a=14/9, b=1/9) for the Euler fluxes, per sub-domain
+ *     line with an explicit sixth-order closure at the first halo point (a reading).
  *   - Eq. 3 / Table 4: 2N-storage low-storage RK (LSERK2, LSERK4).
  *   - Sec. 3.1, Eq. 14-15: stage-0 buffer extrapolation from delayed levels (printed polynomials).
  *   - Eq. 8 + App. C (Table 5): AT buffer updates at intermediate stages with the printed
@@ -109,6 +111,10 @@ typedef struct {
    * split and spacing fields are then ignored); states are stored block after block */
   int nblocks;
   const or_block* blocks;
+  /* 1: the flux divergence by the sixth-order compact scheme of Eq. 2 (alpha = 1/3) with an
+   * explicit sixth-order closure at the first halo point of every sub-domain line (Euler,
+   * single periodic Cartesian grid, LSERK4 / AT4 in time: order = 4); halo depth 4 */
+  int compact;
 } or_params;
 
 /* ---------------------------------------------------------------- coefficient tables */
@@ -240,6 +246,44 @@ static void split_axis(int n, int p, int idx, int* off, int* len) {
 static inline int wrapi(int i, int n) {
   int r = i % n;
   return r < 0 ? r + n : r;
+}
+
+/* Halo depth of the sub-domains: 2r for the viscous CD operator, r for the Euler one, 4 for the
+ * compact scheme (its sixth-order closure at the first halo point reads three points beyond). */
+static int halo_g(const or_params* p) {
+  const int r = (p->order == 4) ? 2 : 1;
+  if (p->compact) return 4;
+  return p->viscous ? 2 * r : r;
+}
+
+/* Sixth-order compact first derivative (Eq. 2 with alpha = 1/3, a = 14/9, b = 1/9) on one
+ * sub-domain line of n points spaced h, from f[0 .. n+7] (point i at f[i + 4]: four halo values on
+ * each side).  The tridiagonal system for the n owned derivatives is closed by the explicit
+ * sixth-order central difference (45, -9, 1)/60h at the first halo point on each side (the paper
+ * prints no closure for its compact schemes at PE boundaries; halo values are the AT ones on
+ * asynchronous steps).  Solved by the Thomas algorithm.  d[0 .. n-1] receives the derivatives. */
+void or_compact_line(int n, double h, const double* f, double* d) {
+  if (n < 1) return;
+  const double al = 1.0 / 3.0, a = 14.0 / 9.0, b = 1.0 / 9.0;
+  const double* F = f + 4;
+  const double dl = (45.0 * (F[0] - F[-2]) - 9.0 * (F[1] - F[-3]) + (F[2] - F[-4])) / (60.0 * h);
+  const double dr = (45.0 * (F[n + 1] - F[n - 1]) - 9.0 * (F[n + 2] - F[n - 2]) + (F[n + 3] - F[n - 3])) / (60.0 * h);
+  double* cp = (double*)malloc(sizeof(double) * (size_t)n);
+  double* rh = (double*)malloc(sizeof(double) * (size_t)n);
+  for (int i = 0; i < n; ++i) rh[i] = a * (F[i + 1] - F[i - 1]) / (2.0 * h) + b * (F[i + 2] - F[i - 2]) / (4.0 * h);
+  rh[0] -= al * dl;
+  rh[n - 1] -= al * dr;
+  /* forward elimination (unit diagonal, off-diagonals alpha), then back substitution */
+  cp[0] = al;
+  for (int i = 1; i < n; ++i) {
+    const double m = 1.0 - al * cp[i - 1];
+    cp[i] = al / m;
+    rh[i] = (rh[i] - al * rh[i - 1]) / m;
+  }
+  d[n - 1] = rh[n - 1];
+  for (int i = n - 2; i >= 0; --i) d[i] = rh[i] - cp[i] * d[i + 1];
+  free(cp);
+  free(rh);
 }
 
 typedef struct {
@@ -753,6 +797,39 @@ static void rhs_ext(const or_params* p, const subdom* d, work_t* w, double* R) {
                         kap * mu * G[(size_t)(9 + a) * n + q];
       }
     }
+  }
+  if (p->compact) {
+    /* Euler with the compact scheme of Eq. 2 (alpha = 1/3): R = -sum_a D_a F_a, D_a one
+     * tridiagonal solve per owned line along a (or_compact_line), axes in the order x, y, z */
+    const int sz3[3] = {d->sx, d->sy, d->sz};
+    const int gz3[3] = {d->g, d->g, d->gz};
+    const size_t no = (size_t)d->sx * d->sy * d->sz;
+    for (size_t q = 0; q < NV * no; ++q) R[q] = 0.0;
+    for (int a = 0; a < ndim; ++a) {
+      const int na = sz3[a], a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+      double* fb = (double*)malloc(sizeof(double) * (size_t)(na + 8));
+      double* db = (double*)malloc(sizeof(double) * (size_t)na);
+      for (int t2 = 0; t2 < sz3[a2]; ++t2)
+        for (int t1 = 0; t1 < sz3[a1]; ++t1)
+          for (int vv = 0; vv < NV; ++vv) {
+            const double* F = w->F + (size_t)a * NV * n + (size_t)vv * n;
+            int c[3];
+            c[a1] = t1;
+            c[a2] = t2;
+            for (int i = -4; i < na + 4; ++i) {
+              c[a] = i;
+              fb[i + 4] = F[(size_t)(c[0] + gz3[0]) + sty * (size_t)(c[1] + gz3[1]) + stz * (size_t)(c[2] + gz3[2])];
+            }
+            or_compact_line(na, h[a], fb, db);
+            for (int i = 0; i < na; ++i) {
+              c[a] = i;
+              R[vv * no + (size_t)c[0] + (size_t)d->sx * ((size_t)c[1] + (size_t)d->sy * c[2])] -= db[i];
+            }
+          }
+      free(fb);
+      free(db);
+    }
+    return;
   }
   /* Eq. 1 on a uniform Cartesian grid: R = -sum_a D_a F_a + (1/Re) sum_a D_a Fv_a */
   const double ire = 1.0 / p->re;
@@ -1390,8 +1467,7 @@ static void diag_topo(const topo_t* T, const double* U, double* out) {
 
 int or_diagnostics(const or_params* p, const double* U, double* out) {
   topo_t T;
-  const int r = (p->order == 4) ? 2 : 1;
-  const int g = p->viscous ? 2 * r : r;
+  const int g = halo_g(p);
   int rc = topo_build(p, g, g, &T);
   if (rc == 0) diag_topo(&T, U, out);
   topo_free(&T);
@@ -1412,8 +1488,7 @@ int or_diagnostics(const or_params* p, const double* U, double* out) {
 int or_run(const or_params* p, double* U, const int8_t* delays, long n0, long nsteps, const double* hist_in,
            double* diag) {
   const int C = or_levels(p->order);
-  const int r = (p->order == 4) ? 2 : 1;
-  const int g = p->viscous ? 2 * r : r;
+  const int g = halo_g(p);
   double A[5], B[5];
   const int S = or_lserk(p->order, A, B);
   const int need = g > (p->filter ? 5 : 0) ? g : (p->filter ? 5 : 0);
@@ -1421,6 +1496,7 @@ int or_run(const or_params* p, double* U, const int8_t* delays, long n0, long ns
   int rc = topo_build(p, g, need, &T);
   if (rc) { topo_free(&T); return rc; }
   if (p->mlp && p->nblocks > 0) { topo_free(&T); return 20; }
+  if (p->compact && (p->viscous || p->order != 4 || p->nblocks > 0 || p->grid_xy || p->mlp)) { topo_free(&T); return 24; }
   const size_t NT = T.Ntot;
   const int nsub = T.nsub;
   /* validation: every sub-domain at least as wide as the halo it needs */
@@ -1533,8 +1609,8 @@ int or_run(const or_params* p, double* U, const int8_t* delays, long n0, long ns
 /* R(U) of all blocks in synchronous mode (halos = current neighbour values or the boundary
  * sources). */
 int or_rhs(const or_params* p, const double* U, double* Rout) {
-  const int r = (p->order == 4) ? 2 : 1;
-  const int g = p->viscous ? 2 * r : r;
+  const int g = halo_g(p);
+  if (p->compact && (p->viscous || p->order != 4 || p->nblocks > 0 || p->grid_xy)) return 24;
   int kf[6] = {0, 0, 0, 0, 0, 0};
   topo_t T;
   int rc = topo_build(p, g, g, &T);
@@ -1578,8 +1654,7 @@ int or_rhs(const or_params* p, const double* U, double* Rout) {
  * [5], then per source block, i, j, k, weight, mirrored, crossed (7 values, up to OR_MAXT
  * sources).  Returns nonzero for an invalid description or a point that does not resolve. */
 int or_halo_sources(const or_params* p, int b, long npts, const int* ijk, double* outs) {
-  const int r = (p->order == 4) ? 2 : 1;
-  const int g = p->viscous ? 2 * r : r;
+  const int g = halo_g(p);
   topo_t T;
   int rc = topo_build(p, g, g, &T);
   if (rc == 0 && (b < 0 || b >= T.nb)) rc = 21;
@@ -1609,8 +1684,7 @@ int or_halo_sources(const or_params* p, int b, long npts, const int* ijk, double
  * block b's extended plane, as the oracle computes them (for cross-checking another
  * implementation); out[npts][6].  Returns nonzero for an invalid description or a Cartesian block. */
 int or_metric_terms(const or_params* p, int b, long npts, const int* ij, double* out) {
-  const int r = (p->order == 4) ? 2 : 1;
-  const int g = p->viscous ? 2 * r : r;
+  const int g = halo_g(p);
   topo_t T;
   int rc = topo_build(p, g, g, &T);
   if (rc == 0 && (b < 0 || b >= T.nb || !T.M[b])) rc = 23;

@@ -53,6 +53,7 @@ class OrParams(ctypes.Structure):
         ("mlp", ctypes.POINTER(ctypes.c_float)), ("mlp_scales", ctypes.POINTER(ctypes.c_double)),
         ("grid_xy", ctypes.POINTER(ctypes.c_double)), ("grid_shift", ctypes.c_double * 4),
         ("nblocks", ctypes.c_int), ("blocks", ctypes.POINTER(OrBlock)),
+        ("compact", ctypes.c_int),
     ]
 
 
@@ -87,6 +88,8 @@ def _load():
             lib.or_lserk.restype = ctypes.c_int
             lib.or_filter_coeffs.argtypes = [ctypes.c_double, d]
             lib.or_filter_line.argtypes = [ctypes.c_int, ctypes.c_double, d, d]
+            lib.or_compact_line.argtypes = [ctypes.c_int, ctypes.c_double, d, d]
+            lib.or_compact_line.restype = None
             lib.or_num_threads.restype = ctypes.c_int
             lib.or_bf16.argtypes = [ctypes.c_double]
             lib.or_bf16.restype = ctypes.c_double
@@ -148,7 +151,7 @@ def params(case) -> OrParams:
         pr=case.pr, viscous=int(case.viscous), visc_law=int(case.visc_law),
         visc_exp=case.visc_exp, order=case.order, algo=ALGOS[case.algo], at=int(case.at),
         caa_L=case.caa_L, kmax=case.kmax, filter=int(case.filter), alpha_f=case.alpha_f,
-        dt=case.dt)
+        dt=case.dt, compact=int(getattr(case, "compact", 0)))
     from paper_2506_03027_gb300.inputs import grid_xy
     g = grid_xy(case)
     if g is not None:
@@ -253,6 +256,16 @@ def filter_line(alpha: float, f: np.ndarray) -> np.ndarray:
     n = f.size - 10
     out = np.zeros(n)
     _load().or_filter_line(n, alpha, _dptr(f), _dptr(out))
+    return out
+
+
+def compact_line(h: float, f: np.ndarray) -> np.ndarray:
+    """Sixth-order compact derivative (Eq. 2, alpha = 1/3) of one line: f holds n values plus 4
+    halo values on each side; returns the n derivatives."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    n = f.size - 8
+    out = np.zeros(n)
+    _load().or_compact_line(n, float(h), _dptr(f), _dptr(out))
     return out
 
 

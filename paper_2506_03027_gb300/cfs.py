@@ -84,6 +84,7 @@ def load() -> ctypes.CDLL:
             "cfs_set_face_shift": ([vp, ip, ip, dp], ip),
             "cfs_eval_power": ([vp, ctypes.c_double, vp, ll, vp], ip),
             "cfs_fp64_probe": ([vp, ip, ip, vp], ip),
+            "cfs_wait_check": ([vp, ctypes.c_uint], ip),
             "cfs_halo_sources": ([vp, ip, ip, ip, ip, dp], ip),
             "cfs_metric_terms": ([vp, ip, ip, ip, dp], ip),
             "cfs_finalize": ([vp, ip], ip),
@@ -228,6 +229,12 @@ def cfs_exchange_count(ctx) -> int:
     n = ctypes.c_longlong()
     _check(ctx, load().cfs_exchange_count(ctx, ctypes.byref(n)))
     return n.value
+
+
+def cfs_wait_check(ctx, limit: int):
+    """Launch the bounded-wait self-test on the context's stream (the next cfs_get_state or
+    cfs_diagnostics then reports ETIMEOUT once)."""
+    _check(ctx, load().cfs_wait_check(ctx, limit))
 
 
 def cfs_halo_sources(ctx, block: int, i: int, j: int, k: int):

@@ -135,6 +135,9 @@ struct cfs_ctx {
   double* d_x_rbuf = nullptr;
   long long exchanges = 0;                        // callbacks made by the last cfs_step
 
+  // device status word: bit 0 set by a bounded device wait that gave up
+  int* d_status = nullptr;
+
   // per-kernel event timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -659,6 +662,7 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   c->d_Wf = (double*)dev_alloc(c, sizeof(double) * nWf);
   c->d_out = (double*)dev_alloc(c, sizeof(double) * 8);
   c->d_n = (long long*)dev_alloc(c, sizeof(long long));
+  c->d_status = (int*)dev_alloc(c, sizeof(int));
   c->Lmax = 0;
   for (Block& b : c->blocks) {
     const int n3[3] = {b.nx, b.ny, b.nz};
@@ -678,7 +682,7 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   c->d_thomas32 = (float*)dev_alloc(c, sizeof(float) * (size_t)(c->Lmax + 1) * 2 * c->Lmax);
   for (void* q : c->owned)
     if (!q) return fail(c, CFS_ENOMEM, "device allocation failed");
-  if (!c->d_n || !c->ring || !c->buf[0] || !c->buf[1] || !c->Q || (!c->fused && (!c->Wp || !c->Phi)) || !c->d_subs || !c->d_W || !c->d_Wf ||
+  if (!c->d_n || !c->d_status || !c->ring || !c->buf[0] || !c->buf[1] || !c->Q || (!c->fused && (!c->Wp || !c->Phi)) || !c->d_subs || !c->d_W || !c->d_Wf ||
       !c->d_partial || !c->d_out || !c->d_thomas || !c->d_thomas32)
     return fail(c, CFS_ENOMEM, "device allocation failed");
   for (const Block& b : c->blocks)
@@ -789,6 +793,7 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
     }
   }
   CUDA_TRY(c, cudaMemsetAsync(c->ring, 0, sizeof(double) * 5 * N * c->R, st), "clear ring");
+  CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), st), "clear status");
   // the host vectors above are pageable: make sure the copies have consumed them
   CUDA_TRY(c, cudaStreamSynchronize(st), "finalize");
   c->finalized = true;
@@ -838,6 +843,26 @@ cfs_status cfs_set_state(cfs_ctx* c, int block, const double* U, int where) {
   return CFS_OK;
 }
 
+// The device status word after the stream's work so far (synchronises): a bounded device wait that
+// gave up is reported once as CFS_ETIMEOUT and the word is cleared, so the context stays usable.
+static cfs_status device_status(cfs_ctx* c) {
+  int st = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream), "status");
+  if (st == 0) return CFS_OK;
+  CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "status");
+  return fail(c, CFS_ETIMEOUT, "a bounded device wait gave up (its outputs were set to NaN)");
+}
+
+cfs_status cfs_wait_check(cfs_ctx* c, unsigned limit) {
+  if (!c) return CFS_EINVAL;
+  if (!c->finalized) return fail(c, CFS_ESTATE, "wait check after cfs_finalize");
+  if (c->sticky) return CFS_ECUDA;
+  const int rc = cfs::launch_wait_check(c->d_status, limit, c->stream);
+  if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "wait check launch");
+  return CFS_OK;
+}
+
 cfs_status cfs_get_state(cfs_ctx* c, int block, double* U, int where) {
   if (!c) return CFS_EINVAL;
   if (!c->finalized) return fail(c, CFS_ESTATE, "get_state after cfs_finalize");
@@ -847,7 +872,7 @@ cfs_status cfs_get_state(cfs_ctx* c, int block, double* U, int where) {
   const size_t bytes = sizeof(double) * 5 * b.N;
   CUDA_TRY(c, cudaMemcpyAsync(U, level_ptr(c, c->n) + b.base, bytes, where ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream), "get_state");
   CUDA_TRY(c, cudaStreamSynchronize(c->stream), "get_state");
-  return CFS_OK;
+  return device_status(c);
 }
 
 cfs_status cfs_set_dt(cfs_ctx* c, double dt) {
@@ -928,6 +953,7 @@ static cfs_status enqueue_step(cfs_ctx* c, long long n, bool graph) {
   sc.W = c->d_W;
   sc.Wf = c->d_Wf;
   sc.LH = nullptr;
+  sc.status = c->d_status;
   sc.table = nullptr;
   sc.at = c->at;
   sc.nsub = (int)c->subs.size();
@@ -1185,6 +1211,10 @@ cfs_status cfs_diagnostics(cfs_ctx* c, double* out) {
   }
   CUDA_TRY(c, cudaMemcpyAsync(out, c->d_out, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream), "diagnostics");
   CUDA_TRY(c, cudaStreamSynchronize(c->stream), "diagnostics");
+  {
+    const cfs_status ds = device_status(c);
+    if (ds != CFS_OK) return ds;
+  }
   if (out[7] != 0.0) return fail(c, CFS_ENAN, "non-finite value in the state");
   return CFS_OK;
 }

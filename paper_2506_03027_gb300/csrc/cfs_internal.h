@@ -128,6 +128,7 @@ struct StepSched {
   int nsub;
   const int8_t* table_base;
   long long Ntot;        // points of a state array (ring level stride / 5)
+  int* status;           // device: bit 0 set by a bounded wait that gave up (read as CFS_ETIMEOUT), or null
 };
 
 // coefficient generation (coeffs.cpp)
@@ -323,6 +324,9 @@ int launch_diagnostics_final(const double* partial, int nrows, double* out, doub
 int launch_advance_step(long long* dn, void* stream);
 int launch_eval_power(const double* x, double a, double* y, long long n, void* stream);
 int launch_fp64_probe(double* sink, int blocks, int iters, void* stream);
+// Self-test of the bounded device waits: one CTA waits on an mbarrier that nothing arrives at, gives
+// up after `limit` polls and sets bit 0 of *status.
+int launch_wait_check(int* status, unsigned limit, void* stream);
 // Strip exchange of a partitioned context: buf[5 i + v] = U[off[i] + v bN[i]] (pack) and the
 // reverse (unpack) for the n entries of a plan.
 int launch_strip_pack(const double* U, const long long* off, const int* bN, long long n, double* buf, void* stream);

@@ -92,6 +92,26 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// One poll of an mbarrier phase (try_wait: may suspend the thread for a short time); true when the
+// phase with the given parity has completed.
+__device__ __forceinline__ bool mbar_poll(const unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"((unsigned)__cvta_generic_to_shared(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for an mbarrier phase: at most limit + 1 polls; false when it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(const unsigned long long* bar, unsigned parity, unsigned limit) {
+  for (unsigned it = 0;; ++it) {
+    if (mbar_poll(bar, parity)) return true;
+    if (it >= limit) return false;
+  }
+}
+
 // Delay of face f (0..5) of sub-domain sid at this step, clamped so every level exists.
 __device__ __forceinline__ int face_delay(const StepSched& sc, int sid, int f) {
   int k = 0;

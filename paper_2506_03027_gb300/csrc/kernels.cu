@@ -332,6 +332,55 @@ __device__ __forceinline__ void flux_curvilinear(const Geometry& g, const Physic
   }
 }
 
+// Flux points of a sub-domain, in warp-uniform groups: first the owned points (x fastest), then
+// the strips of 2r points beyond each face where only the flux along that axis is needed (x
+// strips: the 2r columns fastest, then y and z; y strips: x fastest; z strips: x fastest).  A warp
+// of strip points evaluates one flux direction and only the gradients it needs.
+template <int ND>
+__device__ __forceinline__ bool flux_point(const SubDev& d, int r, int t, int& ci, int& cj, int& ck, int& kind) {
+  const int sxy = d.sx * d.sy, nown = sxy * d.sz;
+  if (t < nown) {
+    ck = t / sxy;
+    const int r2 = t - ck * sxy;
+    cj = r2 / d.sx;
+    ci = r2 - cj * d.sx;
+    kind = 0;
+    return true;
+  }
+  t -= nown;
+  const int w = 2 * r;
+  const int nx = w * d.sy * d.sz;
+  if (t < nx) {  // x strips
+    const int s = t % w, rest = t / w;
+    cj = rest % d.sy;
+    ck = rest / d.sy;
+    ci = s < r ? s - r : d.sx + s - r;
+    kind = 1;
+    return true;
+  }
+  t -= nx;
+  const int ny = w * d.sx * d.sz;
+  if (t < ny) {  // y strips
+    ci = t % d.sx;
+    const int rest = t / d.sx, s = rest % w;
+    ck = rest / w;
+    cj = s < r ? s - r : d.sy + s - r;
+    kind = 2;
+    return true;
+  }
+  t -= ny;
+  if (ND == 3 && t < w * sxy) {  // z strips
+    ci = t % d.sx;
+    const int rest = t / d.sx;
+    cj = rest % d.sy;
+    const int s = rest / d.sy;
+    ck = s < r ? s - r : d.sz + s - r;
+    kind = 3;
+    return true;
+  }
+  return false;
+}
+
 template <typename T, int ND>
 __global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubDev* __restrict__ subs,
                                               const T* __restrict__ Wp, T* __restrict__ Phi) {
@@ -339,15 +388,11 @@ __global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubD
   const SubDev d = subs[sid];
   if (!d.own) return;  // another process's sub-domain
   const int r = g.r;
-  const int rz = (ND == 3) ? r : 0;
-  const int fx = d.sx + 2 * r, fy = d.sy + 2 * r, fz = d.sz + 2 * rz;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;  // flux points of a sub-domain: < 2^31
-  if (t >= fx * fy * fz) return;
-  const int fxy = fx * fy, c0 = t / fxy, r2 = t - c0 * fxy, b0 = r2 / fx, a0 = r2 - b0 * fx;
-  const int ci = a0 - r, cj = b0 - r, ck = c0 - rz;
-  const bool ox = ci < 0 || ci >= d.sx, oy = cj < 0 || cj >= d.sy, oz = ck < 0 || ck >= d.sz;
-  const int nout = (int)ox + (int)oy + (int)oz;
-  if (nout >= 2) return;
+  int ci, cj, ck, kind;
+  if (!flux_point<ND>(d, r, t, ci, cj, ck, kind)) return;
+  const bool ox = kind == 1, oy = kind == 2, oz = kind == 3;
+  const int nout = kind > 0 ? 1 : 0;
   const long long sty = d.ex, stz = (long long)d.ex * d.ey;
   const long long q = (long long)(ci + g.G) + sty * (cj + g.G) + stz * (ck + g.Gz);
   const long long P = g.Ptot;
@@ -359,19 +404,22 @@ __global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubD
   const T rho = W[q], u = W[P + q], v = W[2 * P + q], w = W[3 * P + q], p = W[4 * P + q];
   const T et = W[6 * P + q];
   const T vel[3] = {u, v, w};
-  // gradients du[i][j] = d u_i / d x_j, dT[j]
+  // gradients du[i][j] = d u_i / d x_j, dT[j].  A strip point beyond the faces of axis a needs the
+  // flux along a only: du[a][*], du[*][a], du[b][b] (the divergence) and dT[a].
   T du[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   T dT[3] = {0, 0, 0};
   T mu = (T)1;
+  const int as = kind - 1;  // strip axis (-1: owned point)
   if (g.viscous) {
     const long long st[3] = {1, sty, stz};
 #pragma unroll
     for (int b = 0; b < ND; ++b) {
       const T c1 = (T)d.c1[b], c2 = (T)d.c2[b];
-      du[0][b] = cdiff(W + P, q, st[b], c1, c2, r);
-      du[1][b] = cdiff(W + 2 * P, q, st[b], c1, c2, r);
-      du[2][b] = cdiff(W + 3 * P, q, st[b], c1, c2, r);
-      dT[b] = cdiff(W + 5 * P, q, st[b], c1, c2, r);
+      const bool all = as < 0 || as == b;
+      if (all || as == 0 || b == 0) du[0][b] = cdiff(W + P, q, st[b], c1, c2, r);
+      if (all || as == 1 || b == 1) du[1][b] = cdiff(W + 2 * P, q, st[b], c1, c2, r);
+      if (all || as == 2 || b == 2) du[2][b] = cdiff(W + 3 * P, q, st[b], c1, c2, r);
+      if (all) dT[b] = cdiff(W + 5 * P, q, st[b], c1, c2, r);
     }
     if (ph.visc_law == 1) mu = visc_mu<T>(ph, W[5 * P + q]);
   }
@@ -1048,6 +1096,25 @@ __global__ void __launch_bounds__(256) k_fp64_probe(double* __restrict__ sink, i
 #pragma unroll
   for (int c = 0; c < 8; ++c) t += x[c];
   sink[(long long)blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
+// Self-test of the bounded waits the tensor-core kernels use: an mbarrier expecting one arrival
+// that never comes; every thread polls it at most limit + 1 times, gives up, and thread 0 records
+// the give-up in the status word the host reads (CFS_ETIMEOUT).  Nothing is left in flight.
+__global__ void k_wait_check(int* status, unsigned limit) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"((unsigned)__cvta_generic_to_shared(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0u, limit);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(status, 1);
+}
+
+int launch_wait_check(int* status, unsigned limit, void* stream) {
+  k_wait_check<<<1, 128, 0, (cudaStream_t)stream>>>(status, limit);
+  return (int)cudaGetLastError();
 }
 
 int launch_fp64_probe(double* sink, int blocks, int iters, void* stream) {

@@ -637,8 +637,10 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mlp_halo(Geometry g, StepSched sc,
     tc_fence_before();
     __syncthreads();
   }
-  // a wait that gave up: poison this CTA's columns so the run reports a non-finite state
+  // a wait that gave up: record it in the status word (the host reports CFS_ETIMEOUT) and poison
+  // this CTA's columns so the state shows it too
   if (!ok) {
+    if (tid == 0 && sc.status) atomicOr(sc.status, 1);
     for (long long base = (long long)blockIdx.x * TM; base < ncol; base += (long long)gridDim.x * TM)
       for (int e = tid; e < TM * MLP_NOUT && base + e / MLP_NOUT < ncol; e += TC_NT) {
         const int col = e / MLP_NOUT, o = e % MLP_NOUT, j = o / 5 + 1, v = o % 5;

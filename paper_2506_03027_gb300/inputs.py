@@ -51,6 +51,7 @@ class Case:
     dt: float = 1e-3
     seed: int = 2506030
     curv: float = 0.0          # amplitude of the periodic curvilinear grid (0: uniform Cartesian)
+    compact: int = 0           # 1: sixth-order compact derivatives (Eq. 2, alpha = 1/3) for the Euler fluxes
 
     @property
     def dx(self) -> float:

@@ -187,22 +187,26 @@ def developed_state(case: Case, t_end: float, cfl: float = 0.5):
 
 
 def solver_comparison(case: Case, start, params, scales, nsteps: int, seed: int = None) -> dict:
-    """SA, plain AT and the network's stage-0 halos on the same SAA schedule (delays 0..4), all from
-    `start`, for nsteps steps: each asynchronous run's relative L2 difference from the synchronous
-    run per conserved variable (rho, rho E against their own norms, momentum against the momentum
-    vector's) and the ms per step of each."""
+    """SA, plain AT, the 3-level extrapolation of Eq. 14 alone in the stage-0 face halos (the
+    network's base: a network whose parameters are all zero) and the trained network, on the same
+    SAA schedule (delays 0..4), all from `start`, for nsteps steps: each asynchronous run's
+    relative L2 difference from the synchronous run per conserved variable (rho, rho E against
+    their own norms, momentum against the momentum vector's), whether it stayed finite, and the ms
+    per step of each."""
     import torch
     from .inputs import saa_delays
     saa = case.replace(algo="SAA", kmax=KMAX)
     d = saa_delays(saa, nsteps, seed=seed)
     res = {}
-    for name in ("SA", "AT", "learned"):
+    for name in ("SA", "AT", "extrap3", "learned"):
         cc = case.replace(algo="SA") if name == "SA" else saa
         s = cfs.Solver(cc, max_delay=KMAX)
         try:
             s.set_schedule(delays=d if name != "SA" else None)
             if name == "learned":
                 cfs.cfs_set_halo_model(s.ctx, params, scales)
+            elif name == "extrap3":
+                cfs.cfs_set_halo_model(s.ctx, np.zeros(NPARAM, dtype=np.float32), scales)
             s.set_state(start)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -220,7 +224,7 @@ def solver_comparison(case: Case, start, params, scales, nsteps: int, seed: int 
     def err(U):
         return [float(np.linalg.norm(U[v] - ref[v]) / (mom if v in (1, 2, 3) else np.linalg.norm(ref[v])))
                 for v in range(5)]
-    return {"rel_l2_vs_sa": {"AT": err(res["AT"][0]), "learned": err(res["learned"][0])},
+    return {"rel_l2_vs_sa": {k: err(res[k][0]) for k in ("AT", "extrap3", "learned")},
             "ms_per_step": {k: v[1] for k, v in res.items()}, "steps": nsteps, "dt": case.dt,
             "finite": {k: bool(np.all(np.isfinite(v[0]))) for k, v in res.items()}}
 

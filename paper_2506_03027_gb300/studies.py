@@ -9,7 +9,8 @@ synchronous run's error against the exact translated vortex is returned beside i
 
 paper_vortex_errors: the paper's own vortex setup (Sec. 5.1, Table 1, Fig. 2(a)) -- convergence
 of the density error over one advection cycle for the six scheme cases, on the GPU.
-Command line: python -m paper_2506_03027_gb300.studies paper-vortex [n ...]
+stability_sweep: the first non-finite step of the Taylor-Green configuration per schedule and CFL.
+Command line: python -m paper_2506_03027_gb300.studies paper-vortex [n ...] | stability [n p nsteps]
 """
 from __future__ import annotations
 
@@ -119,6 +120,36 @@ def paper_vortex_errors(ns=(60, 120, 240), runs=PAPER_VORTEX_RUNS, seeds=(1, 2, 
     return {"n": list(ns), "t_end": t_end, "p_late": p_late, "rows": rows}
 
 
+def stability_sweep(n: int = 128, p: int = 4, algos=("SAA", "CAA", "SA"), cfls=(0.5, 0.25, 0.1, 0.05),
+                    nsteps: int = 600, every: int = 25, kmax: int = 3) -> list:
+    """Asynchronous stability of the Taylor-Green configuration (Navier-Stokes, filter, n^3 on p^3
+    sub-domains, FP64): per schedule (SA, CAA with L = 4, SAA with delays 0..kmax) and CFL number,
+    the first multiple of `every` steps at which the state holds a non-finite value (None when it
+    stays finite for nsteps steps) and the kinetic energy at the last finite check."""
+    rows = []
+    for algo in algos:
+        for cfl in cfls:
+            c = I.tgv_case(n, p, algo, kmax=kmax)
+            c = c.replace(dt=I.cfl_dt(c, I.tgv_state(c), cfl))
+            d = I.saa_delays(c, nsteps) if algo == "SAA" else None
+            s = cfs.Solver(c)
+            first, k_last = None, None
+            try:
+                s.set_schedule(delays=d)
+                s.set_state(I.tgv_state(c))
+                for done in range(every, nsteps + 1, every):
+                    s.step(every)
+                    dg = s.diagnostics(check_finite=False)
+                    if dg[7] != 0.0:
+                        first = done
+                        break
+                    k_last = float(dg[0])
+            finally:
+                s.close()
+            rows.append({"algo": algo, "cfl": cfl, "dt": c.dt, "first_nonfinite_by_step": first, "K_last": k_last})
+    return rows
+
+
 def _main(argv):
     import json
     if argv and argv[0] == "paper-vortex":
@@ -129,8 +160,15 @@ def _main(argv):
         for r in out["rows"]:
             print(f"{r['case']:4d}  {r['algorithm']:10s} {r['L']:2d} {r['expected_order']:5d}     "
                   + "  ".join(f"{e:.3e}" for e in r["errors"]) + "   " + "  ".join(f"{o:.2f}" for o in r["orders"]))
+    elif argv and argv[0] == "stability":
+        n = int(argv[1]) if len(argv) > 1 else 128
+        p = int(argv[2]) if len(argv) > 2 else 4
+        nsteps = int(argv[3]) if len(argv) > 3 else 600
+        for r in stability_sweep(n, p, nsteps=nsteps):
+            print(f"{r['algo']} cfl={r['cfl']} dt={r['dt']:.3e} first_nonfinite_by_step={r['first_nonfinite_by_step']} "
+                  f"K_last={r['K_last']}")
     else:
-        print("usage: python -m paper_2506_03027_gb300.studies paper-vortex [n ...]")
+        print("usage: python -m paper_2506_03027_gb300.studies paper-vortex [n ...] | stability [n p nsteps]")
 
 
 if __name__ == "__main__":
