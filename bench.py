@@ -421,6 +421,7 @@ def run_ours(args, rank, world, local_rank):
     if args.precision == 0 and not args.no_forms and world == 1:
         forms = forms or {}
         forms["algorithms"] = algorithms_form(args)
+        forms["compact_euler"] = compact_form(args)
 
     # ---------------- roofline of the dominant kernel
     peaks = measured_peaks()
@@ -440,6 +441,11 @@ def run_ours(args, rank, world, local_rank):
                                "on this GPU in this run)",
                 "fp64_probe": probe,
                 "nominal_peak": SM_COUNT * FP64_FLOP_PER_CLK_SM * sm_max * 1e6 / 1e12}
+    else:
+        # the FP32-intermediate form's dominant kernel: the fused stage against HBM
+        roof = fused_roofline(case, ktimes) or {"bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s",
+                                                "frac": None}
+        roof["kernel"] = dom
     tr = TRAFFIC["bytes_per_launch"].get(dom) if TRAFFIC["source_sha1"] == kernels_sha1() else None
     roof["traffic"] = tr
     roof["per_kernel_ms"] = {k: round(v[0] / max(v[1], 1), 4) for k, v in kinds.items()}
@@ -719,6 +725,49 @@ def learned_form(args):
                         "momentum components against the momentum vector norm"}
 
 
+def compact_form(args):
+    """The sixth-order compact scheme (Eq. 2, alpha = 1/3) against CD4 on the Euler Taylor-Green
+    field: 128^3 on 4^3 sub-domains of 32^3, CAA-AT (L = 4) at CFL 0.25, filter on, CUDA graph;
+    ms per step of both and the per-kernel times of the compact path (a separate timing pass)."""
+    import torch
+    from paper_2506_03027_gb300 import cfs
+    from paper_2506_03027_gb300 import inputs as I
+    K, W = max(3, args.steps // 4), max(args.warmup, 6)
+    out = {"unit": UNIT}
+    for name, cp in (("cd4", 0), ("compact6", 1)):
+        case = I.tgv_case(128, 4, "CAA", viscous=False, compact=cp)
+        case = case.replace(dt=I.cfl_dt(case, I.tgv_state(case), 0.25))
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            s = cfs.Solver(case, graph=True, stream=st)
+            try:
+                s.set_schedule()
+                s.set_state(I.tgv_state(case))
+                s.step(W)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                s.step(K)
+                e1.record(st)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / K
+                cfs.cfs_set_timing(s.ctx, True)
+                s.step(2)
+                kt = cfs.cfs_get_timing(s.ctx)
+                cfs.cfs_set_timing(s.ctx, False)
+                fin = bool(np.all(np.isfinite(s.get_state())))
+            finally:
+                s.close()
+        out[name] = {"value": case.npts * case.stages / (ms * 1e-3) / 1e6, "ms_per_step": ms, "finite": fin,
+                     "per_kernel_ms_per_step": {k: round(v[0] / 2, 4) for k, v in kt.items() if v[1]}}
+    out["compact_over_cd4_time"] = out["compact6"]["ms_per_step"] / out["cd4"]["ms_per_step"]
+    out["workload"] = ("Euler TGV 128^3, 4^3 sub-domains of 32^3, CAA-AT L=4 at CFL 0.25, filter; sixth-order compact "
+                       "(Eq. 2, alpha 1/3, halo depth 4) against CD4; per-kernel: stage_update = compact line solves + "
+                       "update")
+    return out
+
+
 def oracle_sample(case, nsteps):
     """Time `nsteps` asynchronous oracle steps of the workload (starting after the warm-up with a
     history of copies of the initial state: the cost does not depend on the values)."""
@@ -809,7 +858,7 @@ def main():
     ap.add_argument("--split", type=int, default=4, help="sub-domains per axis (profiling runs only)")
     ap.add_argument("--tiles", default="", help="fy,zc,threads launch shapes of the main path (profiling runs only)")
     ap.add_argument("--only-form", default="", choices=["", "cgrid_naca0012", "cgrid_naca0012_fp32_intermediates",
-                                                        "learned_halo"],
+                                                        "learned_halo", "compact_euler"],
                     help="run one form alone and print its result (profiling runs only; --tiles skips its autotuning)")
     ap.add_argument("--cgrid-half", action="store_true",
                     help="with --only-form: the C-grid at half the points per direction (profiling runs only)")
@@ -823,6 +872,9 @@ def main():
         B.build()
         if args.only_form == "learned_halo":
             print(json.dumps(learned_form(args)), flush=True)
+            return
+        if args.only_form == "compact_euler":
+            print(json.dumps(compact_form(args)), flush=True)
             return
         print(json.dumps(cgrid_form(args, 1 if args.only_form.endswith("fp32_intermediates") else 0)), flush=True)
         return

@@ -56,6 +56,11 @@ typedef struct {
   double alpha_f;
   int precision;     /* 0: FP64 throughout; 1: FP32 derivative/flux/filter intermediates with
                         FP64 state, RK accumulation and AT coefficient application */
+  int compact;       /* 1: the flux divergence by the sixth-order compact scheme of Eq. 2 (alpha =
+                        1/3, a = 14/9, b = 1/9), one tridiagonal solve per sub-domain line, closed by
+                        the explicit sixth-order central difference at the first halo point (halo
+                        depth 4); Euler (viscous = 0) with order 4 (LSERK4, AT4) on Cartesian
+                        blocks periodic on every face, FP64 (precision 0) only; 0: explicit CD */
 } cfs_params;
 
 /* Device allocator used by cfs_finalize and cfs_set_schedule.  alloc returns a device pointer

@@ -39,7 +39,7 @@ class CfsParams(ctypes.Structure):
         ("order", ctypes.c_int), ("viscous", ctypes.c_int), ("visc_law", ctypes.c_int),
         ("visc_exp", ctypes.c_double), ("gamma", ctypes.c_double), ("mach", ctypes.c_double),
         ("re", ctypes.c_double), ("pr", ctypes.c_double), ("filter", ctypes.c_int),
-        ("alpha_f", ctypes.c_double), ("precision", ctypes.c_int),
+        ("alpha_f", ctypes.c_double), ("precision", ctypes.c_int), ("compact", ctypes.c_int),
     ]
 
 
@@ -448,7 +448,8 @@ def cfs_destroy(ctx):
 def params_from_case(case, precision: int = 0) -> CfsParams:
     return CfsParams(order=case.order, viscous=int(case.viscous), visc_law=int(case.visc_law),
                      visc_exp=case.visc_exp, gamma=case.gamma, mach=case.mach, re=case.re, pr=case.pr,
-                     filter=int(case.filter), alpha_f=case.alpha_f, precision=precision)
+                     filter=int(case.filter), alpha_f=case.alpha_f, precision=precision,
+                     compact=int(getattr(case, "compact", 0)))
 
 
 class TorchAllocator:

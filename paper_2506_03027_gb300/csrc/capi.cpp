@@ -138,6 +138,10 @@ struct cfs_ctx {
   // device status word: bit 0 set by a bounded device wait that gave up
   int* d_status = nullptr;
 
+  // compact scheme: the flux divergence [5][N] and the Thomas factors of its line systems
+  double* Rbuf = nullptr;
+  double* d_cthomas = nullptr;
+
   // per-kernel event timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -233,6 +237,7 @@ cfs_status cfs_create(const cfs_params* p, void* cuda_stream, cfs_ctx** out) {
   if (p->precision != 0 && p->precision != 1) return CFS_EINVAL;
   if (p->filter && !(std::fabs(p->alpha_f) < 0.5)) return CFS_EINVAL;
   if (!(p->gamma > 1.0) || !(p->mach > 0.0) || (p->viscous && (!(p->re > 0.0) || !(p->pr > 0.0)))) return CFS_EINVAL;
+  if (p->compact != 0 && (p->compact != 1 || p->viscous || p->order != 4 || p->precision != 0)) return CFS_EINVAL;
   cfs_ctx* c = new cfs_ctx();
   c->p = *p;
   c->stream = (cudaStream_t)cuda_stream;
@@ -241,7 +246,7 @@ cfs_status cfs_create(const cfs_params* p, void* cuda_stream, cfs_ctx** out) {
   c->s = cfs::lserk_coeffs(p->order, c->A, c->B);
   c->C = p->order == 4 ? 5 : 3;
   c->r = p->order == 4 ? 2 : 1;
-  c->G = p->viscous ? 2 * c->r : c->r;
+  c->G = p->compact ? 4 : (p->viscous ? 2 * c->r : c->r);
   *out = c;
   return CFS_OK;
 }
@@ -447,7 +452,8 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   c->subs.resize(nsub);
   long long pbase = 0;
   c->max_pad = c->max_own = c->max_flux = 0;
-  const int rz = c->ndim == 3 ? c->r : 0;
+  const int fs = c->p.compact ? 4 : c->r;  // flux strips beyond each face
+  const int rz = c->ndim == 3 ? fs : 0;
   const double a_cd = c->p.order == 4 ? 4.0 / 3.0 : 1.0, b_cd = c->p.order == 4 ? -1.0 / 3.0 : 0.0;
   for (const Block& b : c->blocks)
     for (int iz = 0; iz < b.P[2]; ++iz)
@@ -494,7 +500,7 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
           const long long npad = (long long)d.ex * d.ey * d.ez;
           pbase += npad;
           const long long nown = (long long)d.sx * d.sy * d.sz;
-          const long long nfl = (long long)(d.sx + 2 * c->r) * (d.sy + 2 * c->r) * (d.sz + 2 * rz);
+          const long long nfl = (long long)(d.sx + 2 * fs) * (d.sy + 2 * fs) * (d.sz + 2 * rz);
           if (npad > (1LL << 30)) return fail(c, CFS_EINVAL, "sub-domain too large");
           c->max_pad = (int)std::max<long long>(c->max_pad, npad);
           c->max_own = (int)std::max<long long>(c->max_own, nown);
@@ -525,6 +531,7 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   Geometry& g = c->geo;
   g.nx = b0.nx; g.ny = b0.ny; g.nz = b0.nz; g.N = N; g.nsub = nsub;
   g.G = c->G; g.Gz = c->Gz; g.r = c->r; g.ndim = c->ndim; g.viscous = c->p.viscous; g.Ptot = pbase;
+  g.fs = fs;
   Physics& ph = c->phys;
   ph.gamma = c->p.gamma; ph.gm1 = c->p.gamma - 1.0; ph.gM2 = c->p.gamma * c->p.mach * c->p.mach;
   ph.ire = c->p.viscous ? 1.0 / c->p.re : 0.0;
@@ -672,6 +679,31 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
       b.d_axis_len[a] = (int*)dev_alloc(c, sizeof(int) * b.P[a]);
       c->Lmax = std::max(c->Lmax, (n3[a] + b.P[a] - 1) / b.P[a]);
     }
+  }
+  if (c->p.compact) {
+    for (const Block& b : c->blocks)
+      if (b.mbase >= 0) return fail(c, CFS_EINVAL, "the compact scheme runs on Cartesian blocks");
+    if (!c->all_periodic) return fail(c, CFS_EINVAL, "the compact scheme needs blocks periodic on every face");
+    if (c->Lmax > CFS_MAX_LINE) return fail(c, CFS_EINVAL, "the compact scheme's sub-domain lines are limited to 128 points");
+    c->Rbuf = (double*)dev_alloc(c, sizeof(double) * 5 * (size_t)N);
+    c->d_cthomas = (double*)dev_alloc(c, sizeof(double) * (size_t)(c->Lmax + 1) * 2 * c->Lmax);
+    if (!c->Rbuf || !c->d_cthomas) return fail(c, CFS_ENOMEM, "device allocation failed");
+    // Thomas factors of the compact system (unit diagonal, off-diagonals 1/3) per line length
+    std::vector<double> ct((size_t)(c->Lmax + 1) * 2 * c->Lmax, 0.0);
+    const double al = 1.0 / 3.0;
+    for (int len = 1; len <= c->Lmax; ++len) {
+      double* cp = ct.data() + (size_t)len * 2 * c->Lmax;
+      double* im = cp + c->Lmax;
+      double m = 1.0;
+      cp[0] = al;
+      im[0] = 1.0;
+      for (int i = 1; i < len; ++i) {
+        m = 1.0 - al * cp[i - 1];
+        cp[i] = al / m;
+        im[i] = 1.0 / m;
+      }
+    }
+    CUDA_TRY(c, cudaMemcpy(c->d_cthomas, ct.data(), sizeof(double) * ct.size(), cudaMemcpyHostToDevice), "upload compact factors");
   }
   if (c->p.filter && cfs::filter_prepare(c->Lmax, c->p.precision) != 0)
     return fail(c, CFS_EINVAL, "filter: a sub-domain is too long along an axis for the shared-memory line tiles "
@@ -1004,6 +1036,7 @@ static cfs_status enqueue_step(cfs_ctx* c, long long n, bool graph) {
       a.threads = c->threads;
       a.max_pad = c->max_pad; a.max_own = c->max_own; a.max_flux = c->max_flux;
       a.halo = c->d_halo; a.nhalo = c->nhalo;
+      a.compact = c->p.compact; a.R = c->Rbuf; a.cthomas = c->d_cthomas; a.Lmax = c->Lmax;
       rc = cfs::launch_stage(g, c->phys, sc, a, c->p.precision, c->stream, &c->launches, tm);
     } else if (op == c->s && c->fblock_n && !graph && sc.mode != 0) {
       // asynchronous step, FP32 form: the three passes in one launch, straight into level n + 1

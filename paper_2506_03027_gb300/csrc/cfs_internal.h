@@ -9,6 +9,7 @@
 #define CFS_MAX_DELAY 15   // largest supported delay k (ring depth <= 15 + 5 + 1)
 #define CFS_MAX_LEVELS 5   // C: delayed levels of AT4
 #define CFS_MAX_STAGES 5   // s: stages of LSERK4
+#define CFS_MAX_LINE 128   // longest sub-domain line of the compact scheme
 
 // learned halo predictor: one face column of HDEPTH halo points, 5 variables
 #define MLP_HDEPTH 4
@@ -92,6 +93,7 @@ struct Geometry {
   const int* emap;
   const GatherEntry* gent;
   int GE;                // depth of the gather maps beyond the block faces
+  int fs;                // depth of the flux strips beyond each face: r, or 4 for the compact scheme
 };
 #define NMETRIC 7
 
@@ -188,6 +190,13 @@ struct StageLaunch {
   long long nhalo;
   int max_own;          // largest owned box (points)
   int max_flux;         // largest flux region box (points)
+  // compact scheme (Eq. 2, alpha = 1/3): the flux divergence by line solves into R ([5][N], FP64),
+  // then the stage update from R; cthomas = [Lmax + 1 rows][2][Lmax] Thomas factors per line
+  // length (forward factor c'_i, reciprocal pivot 1 / m_i)
+  int compact;
+  double* R;
+  const double* cthomas;
+  int Lmax;
 };
 
 // Optional per-kernel event timing: when non-null, the launchers call rec(kind, begin) around

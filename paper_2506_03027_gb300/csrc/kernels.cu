@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubD
   const int r = g.r;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;  // flux points of a sub-domain: < 2^31
   int ci, cj, ck, kind;
-  if (!flux_point<ND>(d, r, t, ci, cj, ck, kind)) return;
+  if (!flux_point<ND>(d, g.fs, t, ci, cj, ck, kind)) return;
   const bool ox = kind == 1, oy = kind == 2, oz = kind == 3;
   const int nout = kind > 0 ? 1 : 0;
   const long long sty = d.ex, stz = (long long)d.ex * d.ey;
@@ -518,6 +518,96 @@ __global__ void __launch_bounds__(512) k_rk(Geometry g, Physics ph, StepSched sc
   }
 }
 
+// ------------------------------------------------------------------------------- compact scheme
+
+// Sixth-order compact derivative (Eq. 2 with alpha = 1/3, a = 14/9, b = 1/9) of the combined
+// fluxes Phi_axis along every owned line of a sub-domain, one thread per (line, component): the
+// right side from the owned values and 2 halo values beyond each face, the closure values at the
+// first halo point on each side by the explicit sixth-order central difference (45, -9, 1)/60h
+// (which reads 4 halo values), then the tridiagonal solve (unit diagonal, off-diagonals alpha)
+// with precomputed Thomas factors.  R = D_x Phi_x (axis 0), R += D_a Phi_a (axes 1, 2), FP64.
+template <typename T, int axis>
+__global__ void __launch_bounds__(128) k_compact_div(Geometry g, const SubDev* __restrict__ subs,
+                                                     const T* __restrict__ Phi, double* __restrict__ R,
+                                                     const double* __restrict__ cth, int Lmax) {
+  const int sid = blockIdx.y;
+  const SubDev d = subs[sid];
+  if (!d.own) return;
+  const int sz3[3] = {d.sx, d.sy, d.sz};
+  constexpr int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
+  const int nl = sz3[a1] * sz3[a2];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 5 * nl) return;
+  const int comp = t / nl, line = t - comp * nl;
+  const int t1 = line % sz3[a1], t2 = line / sz3[a1];
+  const int n = sz3[axis];
+  const long long stp[3] = {1, d.ex, (long long)d.ex * d.ey};
+  const long long st = stp[axis];
+  int c0[3];
+  c0[axis] = 0;
+  c0[a1] = t1;
+  c0[a2] = t2;
+  const long long q0 = d.pbase + (long long)(c0[0] + g.G) + stp[1] * (c0[1] + g.G) + stp[2] * (c0[2] + g.Gz);
+  const T* F = Phi + (long long)(axis * 5 + comp) * g.Ptot + q0;  // F[i * st]: point i of the line
+  // own-point offsets in the state arrays (R)
+  const long long r0 = d.bbase + (long long)comp * d.bN + (long long)(d.ox + c0[0]) +
+                       (long long)d.bnx * ((long long)(d.oy + c0[1]) + (long long)d.bny * (d.oz + c0[2]));
+  const long long gst[3] = {1, d.bnx, (long long)d.bnx * d.bny};
+  const long long rs = gst[axis];
+  const double h = 1.0 / (2.0 * d.c1[axis] * 3.0 / 4.0);  // c1 = (4/3 / 2) / h for the block's CD4 coefficients
+  const double al = 1.0 / 3.0, ca = (14.0 / 9.0) / (2.0 * h), cb = (1.0 / 9.0) / (4.0 * h);
+  auto f = [&](int i) { return (double)F[(long long)i * st]; };
+  const double dl = (45.0 * (f(0) - f(-2)) - 9.0 * (f(1) - f(-3)) + (f(2) - f(-4))) / (60.0 * h);
+  const double dr = (45.0 * (f(n + 1) - f(n - 1)) - 9.0 * (f(n + 2) - f(n - 2)) + (f(n + 3) - f(n - 3))) / (60.0 * h);
+  const double* cp = cth + (long long)n * 2 * Lmax;
+  const double* im = cp + Lmax;
+  // forward sweep: the eliminated right sides go to a per-thread array (local memory)
+  double w[CFS_MAX_LINE];
+  double prev = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double rhs = ca * (f(i + 1) - f(i - 1)) + cb * (f(i + 2) - f(i - 2));
+    if (i == 0) rhs -= al * dl;
+    if (i == n - 1) rhs -= al * dr;
+    prev = (i == 0 ? rhs : rhs - al * prev) * __ldg(im + i);
+    w[i] = prev;
+  }
+  // Phi_a = -F_a (k_flux stores the negated inviscid flux), so R = -sum_a D_a F_a = sum_a D_a Phi_a
+  double x = prev;
+  double* Rl = R + r0;
+  if (axis == 0) Rl[(long long)(n - 1) * rs] = x;
+  else Rl[(long long)(n - 1) * rs] += x;
+  for (int i = n - 2; i >= 0; --i) {
+    x = w[i] - __ldg(cp + i) * x;
+    if (axis == 0) Rl[(long long)i * rs] = x;
+    else Rl[(long long)i * rs] += x;
+  }
+}
+
+// Stage update from R: Q = A Q + dt R, U^(m) = U^(m-1) + B Q (Eq. 3, FP64).
+__global__ void __launch_bounds__(512) k_rk_from_R(StepSched sc, const SubDev* __restrict__ subs,
+                                                   const double* __restrict__ R, const double* __restrict__ Uin0,
+                                                   double* __restrict__ Uout0, const double* __restrict__ ring,
+                                                   int in_ring, int out_ring, double* __restrict__ Q, double A, double B,
+                                                   double dt, int first, int last) {
+  sc = resolve(sc);
+  const double* Uin = ring_or(Uin0, in_ring, ring, sc, 0);
+  double* Uout = const_cast<double*>(ring_or(Uout0, out_ring, ring, sc, 1));
+  const int sid = blockIdx.y;
+  const SubDev d = subs[sid];
+  if (!d.own) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.sx * d.sy * d.sz) return;
+  const int sxy = d.sx * d.sy, ck = t / sxy, r2 = t - ck * sxy, cj = r2 / d.sx, ci = r2 - cj * d.sx;
+  const long long gi = d.bbase + (long long)(d.ox + ci) + (long long)d.bnx * ((long long)(d.oy + cj) + (long long)d.bny * (d.oz + ck));
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    const double dtR = dt * R[c * d.bN + gi];
+    const double qn = first ? dtR : fma(A, Q[c * d.bN + gi], dtR);
+    if (!last) Q[c * d.bN + gi] = qn;
+    Uout[c * d.bN + gi] = fma(B, qn, Uin[c * d.bN + gi]);
+  }
+}
+
 static inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
 #define TIMED(tm, kind, launch)              \
@@ -536,6 +626,25 @@ static int stage_impl(const Geometry& g, const Physics& ph, const StepSched& sc,
   if (a.nhalo > 0)
     TIMED(tm, 0, (k_view_halo<T><<<nblk(a.nhalo, B), B, 0, st>>>(g, ph, sc, a.Uin, a.ring, a.in_ring, a.subs,
                                                                  (const int2*)a.halo, a.nhalo, (T*)a.Wp, a.stage, a.s)));
+  if (a.compact) {
+    // compact scheme: fluxes, then one line-solve launch per axis into R, then the update
+    const long long nl = 5LL * a.Lmax * a.Lmax;
+    const dim3 gl(nblk(nl, 128), g.nsub);
+    if (g.ndim == 3) {
+      TIMED(tm, 1, (k_flux<T, 3><<<gf, B, 0, st>>>(g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
+      TIMED(tm, 2, (k_compact_div<T, 0><<<gl, 128, 0, st>>>(g, a.subs, (const T*)a.Phi, a.R, a.cthomas, a.Lmax)));
+      TIMED(tm, 2, (k_compact_div<T, 1><<<gl, 128, 0, st>>>(g, a.subs, (const T*)a.Phi, a.R, a.cthomas, a.Lmax)));
+      TIMED(tm, 2, (k_compact_div<T, 2><<<gl, 128, 0, st>>>(g, a.subs, (const T*)a.Phi, a.R, a.cthomas, a.Lmax)));
+    } else {
+      TIMED(tm, 1, (k_flux<T, 2><<<gf, B, 0, st>>>(g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
+      TIMED(tm, 2, (k_compact_div<T, 0><<<gl, 128, 0, st>>>(g, a.subs, (const T*)a.Phi, a.R, a.cthomas, a.Lmax)));
+      TIMED(tm, 2, (k_compact_div<T, 1><<<gl, 128, 0, st>>>(g, a.subs, (const T*)a.Phi, a.R, a.cthomas, a.Lmax)));
+    }
+    TIMED(tm, 2, (k_rk_from_R<<<gr, B, 0, st>>>(sc, a.subs, a.R, a.Uin, a.Uout, a.ring, a.in_ring, a.out_ring, a.Q, a.A,
+                                                a.B, a.dt, a.first, a.last)));
+    if (launches) *launches += (a.nhalo > 0 ? 2 : 1) + 1 + g.ndim + 1;
+    return (int)cudaGetLastError();
+  }
   if (g.ndim == 3) {
     TIMED(tm, 1, (k_flux<T, 3><<<gf, B, 0, st>>>(g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
     TIMED(tm, 2, (k_rk<T, 3><<<gr, B, 0, st>>>(g, ph, sc, a.subs, (const T*)a.Phi, a.Uin, a.Uout, a.ring, a.in_ring,

@@ -255,3 +255,17 @@ def test_metric_terms_match_the_oracle(lib, topology):
             assert fin[:, 5].sum() > b.nx * b.ny  # the halo carries finite terms too
     finally:
         cfs.cfs_destroy(ctx)
+
+
+def test_compact_scheme_accepted_only_where_built(lib):
+    """The compact scheme (cfs_params.compact = 1) is accepted for the Euler equations with the
+    fourth-order time / AT schemes in FP64, and rejected with EINVAL otherwise."""
+    from paper_2506_03027_gb300 import inputs as I
+    ok = I.tgv_case(16, 2, "SA", viscous=False, filter=False, compact=1)
+    ctx = cfs.cfs_create(cfs.params_from_case(ok), None)
+    cfs.cfs_destroy(ctx)
+    for bad in (ok.replace(viscous=True), ok.replace(order=2)):
+        with pytest.raises(cfs.CfsError):
+            cfs.cfs_create(cfs.params_from_case(bad), None)
+    with pytest.raises(cfs.CfsError):
+        cfs.cfs_create(cfs.params_from_case(ok, precision=1), None)
