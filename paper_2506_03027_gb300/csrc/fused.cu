@@ -30,6 +30,25 @@ namespace cfs {
 namespace {
 
 constexpr int HB = 4;  // halo of the box: 2r for the viscous CD4 operator
+constexpr unsigned STG_WAIT_LIMIT = 1u << 20;  // polls of the staging mbarrier before giving up
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Every thread of the CTA arrives on the staging barrier once per plane, announcing the bytes of
+// the bulk copy it is about to issue (0: none).
+__device__ __forceinline__ void stg_arrive(unsigned long long* bar, unsigned tx) {
+  if (tx) asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(tx) : "memory");
+  else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// One row of FP64 values global -> shared by the bulk-copy engine, completing on the barrier
+// (both addresses 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void stg_bulk(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
 
 // FP32 copies of the physical constants, converted once per thread.
 struct Phys32 {
@@ -236,8 +255,15 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
   // can run ahead of the others by one item
   __shared__ Phys32 sPh;
   __shared__ float sK[2][12];
-  if (tid == 0) sPh = phys32(ph);
+  // staging barrier: NT arrivals per phase plus the bytes of the plane's bulk row copies
+  __shared__ __align__(8) unsigned long long sBar;
+  if (tid == 0) {
+    sPh = phys32(ph);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(&sBar)), "r"(NT) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
   __syncthreads();
+  unsigned stg_phase = 0;  // parity of the staging barrier's next phase
   const Phys32 k32 = sPh;
   const long long P = g.Ptot;
   const float* __restrict__ WhS = Wh + (long long)((sc.mode == 2) ? 0 : stage) * 7 * P;
@@ -321,15 +347,37 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
       zoff = d.bbase + (long long)d.bnx * d.bny * wrapc(d.oz + L, d.bnz);
       pz = d.pbase + (long long)d.ex * d.ey * (L + g.Gz);
     };
+    // On asynchronous steps the FP64 values come only from the sub-domain's own points: the rows
+    // of the box inside the sub-domain, x in [lx0, lx1), y in [ly0, ly1), are contiguous in the
+    // state and go as bulk row copies (when 16-byte aligned) instead of per-value copies.
+    const int lx0 = max(tx0 - HB, 0), lx1 = min(tx0 + fxa + HB, d.sx);
+    const int ly0 = max(ty0 - HB, 0), ly1 = min(ty0 + fya + HB, d.sy);
+    const bool bulk = sc.mode != 0 && ((d.ox + lx0) & 1) == 0 && ((lx1 - lx0) & 1) == 0 && (d.bnx & 1) == 0 &&
+                      (d.bbase & 1) == 0 && (d.bN & 1) == 0 && (g.N & 1) == 0;
     auto issue = [&](int L) {
       long long zoff, pz;
       int dz;
       plane_src(L, zoff, pz, dz);
+      unsigned txb = 0;
+      const double* bsrc = nullptr;
+      double* bdst = nullptr;
+      if (bulk && dz == 0 && tid < 5 * S::BY) {
+        const int v = tid / S::BY, j = tid - v * S::BY, ly = ty0 - HB + j;
+        if (ly >= ly0 && ly < ly1) {
+          bsrc = Uin + zoff + (long long)v * d.bN + (long long)d.bnx * (d.oy + ly) + (d.ox + lx0);
+          bdst = sStg + v * NB + j * BX + (lx0 - (tx0 - HB));
+          txb = (unsigned)(lx1 - lx0) * 8u;
+        }
+      }
+      if (txb) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // after the generic reads of the buffer
+      stg_arrive(&sBar, txb);
+      if (txb) stg_bulk(bdst, bsrc, txb, &sBar);
 #pragma unroll
       for (int k = 0; k < KB; ++k) {
         if (bc.dxy[k] < 0) continue;
         const int p = bc.pq[k] & 0xffff;
         const int src = box_source(sc.mode, g.r, bc.dxy[k] & 255, bc.dxy[k] >> 8, dz);
+        if (src == 1 && bulk) continue;  // in a bulk row
         if (src == 1) {
           const double* s0 = Uin + zoff + bc.xy[k];
 #pragma unroll
@@ -345,9 +393,16 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
 
     issue(z0 - HB);
     for (int L = z0 - HB; L < z1 + HB; ++L) {
-      // ---- staged plane L -> primitives in the rings
+      // ---- staged plane L -> primitives in the rings (bounded wait on the bulk rows: a wait that
+      // gives up records it in the status word and ends the CTA after its copies have landed)
       cp_async_wait_all();
-      __syncthreads();
+      const bool stg_ok = mbar_wait_bounded(&sBar, stg_phase, STG_WAIT_LIMIT);
+      stg_phase ^= 1u;
+      if (__syncthreads_or(!stg_ok)) {
+        if (tid == 0 && sc.status) atomicOr(sc.status, 1);
+        mbar_wait_bounded(&sBar, stg_phase ^ 1u, STG_WAIT_LIMIT);
+        return;
+      }
       {
         float4* r4 = sR4 + ((L + 15) % 5) * NB;
         float4* r3 = sR3 + ((L + 15) % 3) * NW;
