@@ -539,8 +539,7 @@ def batched_form(args, precision=0, curvilinear=False):
             "workload": "12 independent periodic NS blocks with the 12-block airfoil C-grid sizes, SAA 0..2, "
                         + ("curvilinear (deformed periodic grids), " if curvilinear else "")
                         + ("FP64" if precision == 0 else
-                           "FP32 intermediates (" + ("multi-kernel stage" if curvilinear else
-                                                     "one fused launch per RK stage") + ")")}
+                           "FP32 intermediates (one fused launch per RK stage)")}
 
 
 def cgrid_form(args, precision=0):

@@ -99,7 +99,8 @@ cfs_status cfs_add_block(cfs_ctx* ctx, int ni, int nj, int nk, const double* spa
  * in index space.  The data are copied.  Call after cfs_add_block, before cfs_finalize
  * (ESTATE otherwise); EINVAL for an unknown block, null pointers or non-finite values, and at
  * cfs_finalize for a grid with a non-positive cell volume.  The FP32-intermediate precision runs
- * curvilinear blocks through the multi-kernel stage (the fused stage is Cartesian only). */
+ * curvilinear blocks periodic on every face through the fused stage (one launch per RK stage);
+ * connected blocks take the multi-kernel stage. */
 cfs_status cfs_set_block_grid(cfs_ctx* ctx, int block, const double* xy, const double* shift);
 
 /* Decompose a block into pi x pj x pk sub-domains (the paper's PEs, Sec. 3); sub-domains are

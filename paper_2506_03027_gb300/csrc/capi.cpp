@@ -95,6 +95,7 @@ struct cfs_ctx {
   int fused_zc = 32;
   int fused_fy = 16;
   int fused_grid = 0;
+  bool fused_curv = false;  // the fused stage runs curvilinear blocks (metric window in shared memory)
   double* d_metric = nullptr;  // metric planes of the curvilinear blocks
   int* d_emap = nullptr;       // gather maps of the blocks with non-periodic faces
   cfs::GatherEntry* d_gent = nullptr;
@@ -627,7 +628,8 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
     for (const Block& b : c->blocks)
       for (int q = 0; q < b.P[0] * b.P[1] * b.P[2]; ++q) c->subs[b.sid0 + q].ebase = b.ebase;
   }
-  c->fused = c->p.precision == 1 && c->ndim == 3 && c->p.viscous && c->p.order == 4 && !curv && c->all_periodic;
+  c->fused = c->p.precision == 1 && c->ndim == 3 && c->p.viscous && c->p.order == 4 && c->all_periodic;
+  c->fused_curv = curv;
   c->fblock_n = 0;
   if (c->p.precision == 1 && c->p.filter && c->ndim == 3 && !curv && c->all_periodic && nsub > 0) {
     const int n0 = c->subs[0].sx;
@@ -656,7 +658,7 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = 0;
-    if (cfs::fused_blocks_per_sm(c->fused_fy, &per_sm) != 0 || per_sm < 1)
+    if (cfs::fused_blocks_per_sm(c->fused_fy, curv ? 1 : 0, &per_sm) != 0 || per_sm < 1)
       return fail(c, CFS_ECUDA, "fused stage kernel does not fit on this device");
     c->fused_grid = std::max(1, std::min(c->nwork, per_sm * std::max(1, sms)));
   } else {
@@ -1025,6 +1027,7 @@ static cfs_status enqueue_step(cfs_ctx* c, long long n, bool graph) {
       a.grid = c->fused_grid; a.fy = c->fused_fy; a.Wh = c->Wh; a.stage = op;
       a.A = c->A[op]; a.B = c->B[op]; a.dt = c->dt; a.first = op == 0; a.last = op == c->s - 1;
       a.ring = c->ring; a.in_ring = in_ring; a.out_ring = out_ring;
+      a.curv = c->fused_curv ? 1 : 0;
       rc = cfs::launch_stage_fused(g, c->phys, sc, a, c->stream, &c->launches, tm);
     } else if (op < c->s) {
       cfs::StageLaunch a{};

@@ -277,9 +277,10 @@ struct FusedLaunch {
   int first, last;
   const double* ring;
   int in_ring, out_ring;
+  int curv;             // 1: the context has curvilinear blocks (metric window in shared memory)
 };
-int fused_smem_bytes(int fy);
-int fused_blocks_per_sm(int fy, int* blocks);  // sets the shared-memory attribute, then asks the occupancy API
+int fused_smem_bytes(int fy, int curv);
+int fused_blocks_per_sm(int fy, int curv, int* blocks);  // sets the shared-memory attribute, then asks the occupancy API
 int launch_halo_prims(const Geometry& g, const Physics& ph, const StepSched& sc, const double* ring, const SubDev* subs,
                       const int* halo, long long nhalo, float* Wh, int s, void* stream, long long* launches,
                       const Timer* tm);

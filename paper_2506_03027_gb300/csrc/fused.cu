@@ -177,6 +177,10 @@ struct FusedSmem {
   static constexpr int FX4 = 4 * FY * (FX + 4), FX1 = FY * (FX + 4);  // Phi_x (components 0-3, 4)
   static constexpr int FY4 = 4 * (FY + 4) * FX, FY1 = (FY + 4) * FX;  // Phi_y
   static constexpr size_t bytes = sizeof(float) * (STG + R4 + R3 + FX4 + FX1 + FY4 + FY1);
+  // curvilinear blocks (App. A): the window's metric terms xi^_x, xi^_y, eta^_x, eta^_y, zeta^_z
+  // and J in FP32 (z-independent, loaded once per work item), after the arrays above
+  static constexpr int MET = 6 * NW;
+  static constexpr size_t bytes_curv = bytes + sizeof(float) * MET;
 };
 
 // The view of a sub-domain holds faces up to depth HB and edges up to r x r (corners unused).
@@ -246,6 +250,7 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
   float* sFx1 = smem + S::STG + S::R4 + S::R3 + S::FX4;
   float4* sFy4 = reinterpret_cast<float4*>(sFx1 + S::FX1);  // [FY + 4][FX]
   float* sFy1 = sFx1 + S::FX1 + S::FY4;
+  float* sMet = sFy1 + S::FY1;  // [6][NW], curvilinear blocks only
   __shared__ unsigned short sList[NB];  // box indices: columns inside the sub-domain, then halo columns
   __shared__ int sNlist;
   const int tid = threadIdx.x, tx = tid % FX, ty = tid / FX, lane = tid & 31;
@@ -285,7 +290,25 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
     // ---- column lists (warp 0, ordered ballots): a box column is read by some output when it
     // lies in the tile +- 4 along one axis or in the tile +- 2 along both; outside the sub-domain
     // in x or y it must also be in the view (faces, r x r edges)
-    __syncthreads();  // the previous item's lists are no longer read
+    __syncthreads();  // the previous item's lists (and metric window) are no longer read
+    // curvilinear block: the metric terms of the window (tile + strips of 2), z-independent, and
+    // J of this thread's own column in FP64 for the update
+    const bool curv = d.mbase >= 0;
+    double Jown = 1.0;
+    if (curv) {
+      for (int e = tid; e < NW; e += NT) {
+        const int gxw = d.ox + tx0 - 2 + e % WX, gyw = d.oy + ty0 - 2 + e / WX;
+        // window points of a partial tile can lie beyond the plane (extended by G): no output
+        // reads their fluxes, give them zeros
+        const bool in = gxw >= -g.G && gxw < d.bnx + g.G && gyw >= -g.G && gyw < d.bny + g.G;
+        const double* M = g.metric + d.mbase + (long long)(gxw + g.G) + (long long)d.mx * (gyw + g.G);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) sMet[k * NW + e] = in ? (float)M[(long long)k * d.mpl] : 0.f;
+        sMet[5 * NW + e] = in ? (float)M[6 * d.mpl] : 0.f;
+      }
+      const int lxo = min(tx0 + tx, d.sx - 1), lyo = min(ty0 + ty, d.sy - 1);
+      Jown = g.metric[d.mbase + 6 * d.mpl + (long long)(d.ox + lxo + g.G) + (long long)d.mx * (d.oy + lyo + g.G)];
+    }
     if (tid < 32) {
       int n = 0;
       for (int pass = 0; pass < 2; ++pass) {
@@ -466,6 +489,67 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
       float fz4 = 0.f;
       // one gradient/flux evaluation at box point (bi, bj) of plane G: kind 0 tile point (Phi_x,
       // Phi_y to shared memory, Phi_z to registers), 1 x-strip (Phi_x), 2 y-strip (Phi_y)
+      // Curvilinear flux point (App. A, Eq. A1-A4): the index-space gradients g0, g1 are mapped to
+      // physical ones through the metric terms, d/dx_j = J sum_k (metric row k)_j d/dxi_k, and the
+      // combined flux along index direction a uses the metric row m_a = (d xi_a / dx) / J:
+      //   Phi_a = -[rho U, rho u U + m_a,x p, rho v U + m_a,y p, rho w U + m_a,z p, (rho E + p) U]
+      //           + (1/Re) [0, m_a . tau_1, m_a . tau_2, m_a . tau_3, m_a . b],  U = m_a . u.
+      // Rows: xi = (m0, m1, 0), eta = (m2, m3, 0), zeta = (0, 0, m4).
+      auto curvilinear_point = [&](const float* mw, int nw, const float2* g0, const float2* g1, float4 c0, float4 c3,
+                                   const Phys32& k, int kind, int bi, int bj) {
+        const float m0 = mw[0], m1 = mw[nw], m2 = mw[2 * nw], m3 = mw[3 * nw], m4 = mw[4 * nw], J = mw[5 * nw];
+        // physical gradients of (u, v) and (w, T) along x, y, z
+        const float2 ax0 = __fmul2_rn(bc2(J), __ffma2_rn(bc2(m0), g0[0], __fmul2_rn(bc2(m2), g0[1])));
+        const float2 ay0 = __fmul2_rn(bc2(J), __ffma2_rn(bc2(m1), g0[0], __fmul2_rn(bc2(m3), g0[1])));
+        const float2 az0 = __fmul2_rn(bc2(J * m4), g0[2]);
+        const float2 ax1 = __fmul2_rn(bc2(J), __ffma2_rn(bc2(m0), g1[0], __fmul2_rn(bc2(m2), g1[1])));
+        const float2 ay1 = __fmul2_rn(bc2(J), __ffma2_rn(bc2(m1), g1[0], __fmul2_rn(bc2(m3), g1[1])));
+        const float2 az1 = __fmul2_rn(bc2(J * m4), g1[2]);
+        const float du[3][3] = {{ax0.x, ay0.x, az0.x}, {ax0.y, ay0.y, az0.y}, {ax1.x, ay1.x, az1.x}};
+        const float dT[3] = {ax1.y, ay1.y, az1.y};
+        const float u = c0.x, v = c0.y, w = c0.z, T = c0.w;
+        const float rho = c3.x, p = c3.y, etH = c3.z + k.Href;
+        float mu = 1.f;
+        if (k.law == 1) mu = powf(T, k.vexp);
+        const float div = (du[0][0] + du[1][1]) + du[2][2];
+        const float vel[3] = {u, v, w};
+        float tau[3][3], bq[3];
+#pragma unroll
+        for (int i2 = 0; i2 < 3; ++i2)
+#pragma unroll
+          for (int j2 = 0; j2 < 3; ++j2)
+            tau[i2][j2] = fmaf(i2 == j2 ? (-2.f / 3.f) * mu : 0.f, div, mu * (du[i2][j2] + du[j2][i2]));
+#pragma unroll
+        for (int i2 = 0; i2 < 3; ++i2) bq[i2] = fmaf(u, tau[i2][0], fmaf(v, tau[i2][1], fmaf(w, tau[i2][2], k.kap * mu * dT[i2])));
+        const float mr[3][3] = {{m0, m1, 0.f}, {m2, m3, 0.f}, {0.f, 0.f, m4}};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (kind == 1 && a != 0) continue;
+          if (kind == 2 && a != 1) continue;
+          const float Uc = fmaf(mr[a][0], u, fmaf(mr[a][1], v, mr[a][2] * w)), mflux = rho * Uc;
+          float f[5];
+          f[0] = -mflux;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float vis = fmaf(mr[a][0], tau[0][c], fmaf(mr[a][1], tau[1][c], mr[a][2] * tau[2][c]));
+            f[1 + c] = fmaf(k.ire, vis, -fmaf(mflux, vel[c], mr[a][c] * p));
+          }
+          f[4] = fmaf(k.ire, fmaf(mr[a][0], bq[0], fmaf(mr[a][1], bq[1], mr[a][2] * bq[2])), -(etH * Uc));
+          if (a == 0) {
+            const int o = (bj - HB) * FXW + (bi - HB + 2);
+            sFx4[o] = make_float4(f[0], f[1], f[2], f[3]);
+            sFx1[o] = f[4];
+          } else if (a == 1) {
+            const int o = (bj - HB + 2) * FX + (bi - HB);
+            sFy4[o] = make_float4(f[0], f[1], f[2], f[3]);
+            sFy1[o] = f[4];
+          } else {
+            fz01 = make_float2(f[0], f[1]);
+            fz23 = make_float2(f[2], f[3]);
+            fz4 = f[4];
+          }
+        }
+      };
       auto point = [&](int bi, int bj, int kind) {
         const float4* P0 = pl[2];
         const int q = bj * BX + bi;
@@ -474,6 +558,10 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
         cd4_pair(P0[q - 2], P0[q - 1], P0[q + 1], P0[q + 2], c1x, c2x, g0[0], g1[0]);
         cd4_pair(P0[q - 2 * BX], P0[q - BX], P0[q + BX], P0[q + 2 * BX], c1y, c2y, g0[1], g1[1]);
         cd4_pair(pl[0][q], pl[1][q], pl[3][q], pl[4][q], c1z, c2z, g0[2], g1[2]);
+        if (curv) {
+          curvilinear_point(sMet + qw, NW, g0, g1, P0[q], r3c[qw], k32, kind, bi, bj);
+          return;
+        }
         // du[i][j] = d u_i / d x_j
         const float du[3][3] = {{g0[0].x, g0[1].x, g0[2].x}, {g0[0].y, g0[1].y, g0[2].y}, {g1[0].x, g1[1].x, g1[2].x}};
         const float dT[3] = {g1[0].y, g1[1].y, g1[2].y};
@@ -571,7 +659,7 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
       if (outp) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
-          const double dtR = f2d_fast(out[c]);
+          const double dtR = curv ? f2d_fast(out[c]) * Jown : f2d_fast(out[c]);  // index-space divergence x J
           const double qn = first ? dtR : fma(A, qin[c], dtR);
           if (!last) Q[c * d.bN + go] = qn;
           Uout[c * d.bN + go] = fma(B, qn, uin[c]);
@@ -583,10 +671,10 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
 
 // ------------------------------------------------------------------------------- launchers
 
-int fused_smem_bytes(int fy) {
-  if (fy == 4) return (int)FusedSmem<32, 4>::bytes;
-  if (fy == 16) return (int)FusedSmem<32, 16>::bytes;
-  return (int)FusedSmem<32, 8>::bytes;
+int fused_smem_bytes(int fy, int curv) {
+  if (fy == 4) return (int)(curv ? FusedSmem<32, 4>::bytes_curv : FusedSmem<32, 4>::bytes);
+  if (fy == 16) return (int)(curv ? FusedSmem<32, 16>::bytes_curv : FusedSmem<32, 16>::bytes);
+  return (int)(curv ? FusedSmem<32, 8>::bytes_curv : FusedSmem<32, 8>::bytes);
 }
 
 int launch_halo_prims(const Geometry& g, const Physics& ph, const StepSched& sc, const double* ring, const SubDev* subs,
@@ -604,11 +692,12 @@ int launch_halo_prims(const Geometry& g, const Physics& ph, const StepSched& sc,
 }
 
 template <int FX, int FY>
-static int fused_prepare(int* blocks_per_sm) {
-  const size_t sm = FusedSmem<FX, FY>::bytes;
-  static bool attr_set = false;  // per process: the attribute is a property of the kernel
+static int fused_prepare(int* blocks_per_sm, int curv) {
+  const size_t sm = curv ? FusedSmem<FX, FY>::bytes_curv : FusedSmem<FX, FY>::bytes;
+  static bool attr_set = false;  // per process: the attribute (the largest size) is a property of the kernel
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_stage_fused<FX, FY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_stage_fused<FX, FY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)FusedSmem<FX, FY>::bytes_curv);
     if (e != cudaSuccess) return (int)e;
     attr_set = true;
   }
@@ -619,17 +708,17 @@ static int fused_prepare(int* blocks_per_sm) {
   return 0;
 }
 
-int fused_blocks_per_sm(int fy, int* blocks) {
-  if (fy == 4) return fused_prepare<32, 4>(blocks);
-  if (fy == 16) return fused_prepare<32, 16>(blocks);
-  return fused_prepare<32, 8>(blocks);
+int fused_blocks_per_sm(int fy, int curv, int* blocks) {
+  if (fy == 4) return fused_prepare<32, 4>(blocks, curv);
+  if (fy == 16) return fused_prepare<32, 16>(blocks, curv);
+  return fused_prepare<32, 8>(blocks, curv);
 }
 
 template <int FX, int FY>
 static int fused_impl(const Geometry& g, const Physics& ph, const StepSched& sc, const FusedLaunch& a, cudaStream_t st) {
-  const int rc = fused_prepare<FX, FY>(nullptr);
+  const int rc = fused_prepare<FX, FY>(nullptr, a.curv);
   if (rc) return rc;
-  k_stage_fused<FX, FY><<<a.grid, FX * FY, FusedSmem<FX, FY>::bytes, st>>>(
+  k_stage_fused<FX, FY><<<a.grid, FX * FY, a.curv ? FusedSmem<FX, FY>::bytes_curv : FusedSmem<FX, FY>::bytes, st>>>(
       g, ph, sc, a.Uin, a.Uout, a.ring, a.in_ring, a.out_ring, a.Q, a.subs, a.work, a.nwork, a.Wh, a.stage, a.A, a.B,
       a.dt, a.first, a.last);
   return (int)cudaGetLastError();

@@ -477,8 +477,9 @@ def test_curvilinear_freestream_on_gpu():
 
 
 def test_curvilinear_fp32_form():
-    """FP32 intermediates on a curvilinear block (multi-kernel stage): error against the oracle
-    within the FP32-form bound."""
+    """FP32 intermediates on a curvilinear block (the fused stage: metric window in shared memory,
+    index-space divergence times J in the FP64 update; sub-domains of 13 points, narrower than a
+    tile): error against the oracle within the FP32-form bound."""
     c = I.tgv_case(26, 2, "CAA", filter=True, curv=0.25)
     c = c.replace(dt=I.cfl_dt(c, I.tgv_state(c), 0.25))
     U0 = I.tgv_state(c)
@@ -486,3 +487,55 @@ def test_curvilinear_fp32_form():
     Uo = orc.run(c, U0, 16)
     e = rel_l2(Ug, Uo)
     assert np.all(np.isfinite(Ug)) and np.all(e < 1e-6), e
+
+
+@pytest.mark.parametrize("tiles", [(4, 8, 256), (16, 32, 256)])
+def test_curvilinear_fused_launch_shapes_identical(tiles):
+    """The fused stage on a deformed grid gives the same bits for every tile shape (no FMA
+    contraction in fused.cu, every product written out)."""
+    c = I.tgv_case(34, 2, "SAA", kmax=2, filter=True, curv=0.3)
+    c = c.replace(dt=I.cfl_dt(c, I.tgv_state(c), 0.05))
+    d = I.saa_delays(c, 9)
+    res = []
+    for t in ((8, 16, 256), tiles):
+        s = cfs.Solver(c, precision=1, tiles=t)
+        s.set_schedule(delays=d)
+        s.set_state(I.tgv_state(c))
+        s.step(9)
+        res.append(s.get_state())
+        s.close()
+    np.testing.assert_array_equal(res[0], res[1])
+
+
+def test_batched_curvilinear_blocks_fp32_form():
+    """Uneven curvilinear and Cartesian blocks in one context, FP32 intermediates: one fused
+    launch per stage covers all of them (CUDA graph); each block within the FP32-form bound of its
+    own oracle run under the SAA delays of its sub-domains."""
+    import torch
+    base = I.tgv_case(20, 2, "SAA", kmax=2, filter=True)
+    blocks = [base.replace(nx=40, ny=36, nz=32, px=2, py=2, pz=2, curv=0.3),
+              base.replace(nx=32, ny=32, nz=32, px=1, py=1, pz=2, lz=4.0),
+              base.replace(nx=48, ny=32, nz=16, px=3, py=2, pz=1, lx=3.0, ly=2.5, lz=2.0, curv=0.05)]
+    dt = min(I.cfl_dt(b, I.tgv_state(b), 0.1) for b in blocks)
+    blocks = [b.replace(dt=dt) for b in blocks]
+    nsteps = 10
+    nsub = sum(b.nsub for b in blocks)
+    d = I.saa_delays(blocks[0].replace(px=nsub, py=1, pz=1), nsteps)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = cfs.Solver(blocks[0], blocks=blocks, graph=True, stream=stream, precision=1)
+        s.set_schedule(delays=d)
+        for i, b in enumerate(blocks):
+            s.set_state(I.tgv_state(b), block=i)
+        s.step(nsteps)
+        launches = s.launches()
+        Ug = [s.get_state(block=i) for i in range(len(blocks))]
+        s.close()
+    sid0 = 0
+    for i, b in enumerate(blocks):
+        Uo = orc.run(b, I.tgv_state(b), nsteps, delays=np.ascontiguousarray(d[:, sid0:sid0 + b.nsub, :]))
+        e = rel_l2(Ug[i], Uo)
+        assert np.all(np.isfinite(Ug[i])) and np.all(e < 1e-6), (i, e)
+        sid0 += b.nsub
+    # one halo-primitive launch and 5 fused stages per step, the filter passes, the step counter
+    assert launches / nsteps < 20, launches / nsteps
