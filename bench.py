@@ -422,6 +422,7 @@ def run_ours(args, rank, world, local_rank):
         forms = forms or {}
         forms["algorithms"] = algorithms_form(args)
         forms["compact_euler"] = compact_form(args)
+        forms["static_diagnostics"] = static_diagnostics_form()
 
     # ---------------- roofline of the dominant kernel
     peaks = measured_peaks()
@@ -588,7 +589,7 @@ def cgrid_form(args, precision=0):
             "launches_per_step": launches / K, "tiles_autotuned": list(tiles),
             "finite": bool(d[7] == 0.0), "wall_points_at_rest": walls_at_rest, "K_after": float(d[0]),
             "workload": "NACA0012 12-block C-grid (interfaces, wake cut, walls, far field, outflows), NS Re_c 5e4 "
-                        "M 0.3, SAA 0..2, " + ("FP64" if precision == 0 else "FP32 intermediates (multi-kernel stage)")}
+                        "M 0.3, SAA 0..2, " + ("FP64" if precision == 0 else "FP32 intermediates (one fused launch per RK stage)")}
 
 
 def precision_form_256(args):
@@ -765,6 +766,31 @@ def compact_form(args):
                        "(Eq. 2, alpha 1/3, halo depth 4) against CD4; per-kernel: stage_update = compact line solves + "
                        "update")
     return out
+
+
+def static_diagnostics_form():
+    """Latency of the allocation-free diagnostics (cfs_diagnostics_static) at its size limit: a
+    256^3 TGV state (16.8 M points, the 4 MiB scratch full), CUDA events around each call, median
+    of 10 after 2 warm-up calls, beside cfs_diagnostics of a context on the same state."""
+    import torch
+    from paper_2506_03027_gb300 import cfs
+    from paper_2506_03027_gb300 import inputs as I
+    c = I.tgv_case(256, 8, "SA")
+    U = torch.from_numpy(I.tgv_state(c)).cuda()
+    out = torch.empty(8, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    ts = []
+    for it in range(12):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        cfs.cfs_diagnostics_static(U.data_ptr(), c.nx, c.ny, c.nz, (c.dx, c.dy, c.dz), 4, out.data_ptr(), st.cuda_stream)
+        e1.record(st)
+        torch.cuda.synchronize()
+        if it >= 2:
+            ts.append(e0.elapsed_time(e1))
+    return {"ms_median": statistics.median(ts), "ms_min": min(ts), "points": c.npts,
+            "workload": "TGV 256^3 state (the size limit), order 4; CUDA events around each call"}
 
 
 def oracle_sample(case, nsteps):

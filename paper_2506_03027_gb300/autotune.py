@@ -83,8 +83,9 @@ def tune(case, precision: int = 0, blocks=None, use_cache: bool = True, states=N
         hit = load_cache().get(k)
         if hit:
             return tuple(hit["tiles"])
-    fused = (mb is None and precision == 1 and c0.nz > 1 and c0.viscous and c0.order == 4
-             and not any(b.curv for b in (blocks or [case])))
+    # the fused FP32 stage: 3-D Navier-Stokes CD4 blocks, Cartesian or curvilinear, periodic or
+    # connected
+    fused = precision == 1 and c0.nz > 1 and c0.viscous and c0.order == 4
     cands = FUSED if fused else PLAIN
     ms = {}
     for t in cands:

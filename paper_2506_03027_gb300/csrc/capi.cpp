@@ -590,6 +590,7 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   g.GE = need;
   g.emap = nullptr;
   g.gent = nullptr;
+  bool simple_own = true;  // every entry with a source reached without crossing is one unit copy of it
   if (!c->all_periodic) {
     std::vector<int> emap;
     std::vector<cfs::GatherEntry> ent;
@@ -614,6 +615,11 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
             if (ent.size() >= (size_t)INT32_MAX) return fail(c, CFS_EINVAL, "too many gather entries");
             emap.push_back((int)ent.size());
             ent.push_back(e);
+            bool uncrossed = false;
+            for (int q = 0; q < e.nt; ++q) uncrossed = uncrossed || !(e.flags[q] & 2);
+            if (uncrossed && !(e.nt == 1 && e.w[0] == 1.0 && e.cst[0] == 0.0 && e.cst[1] == 0.0 && e.cst[2] == 0.0 &&
+                               e.cst[3] == 0.0 && e.cst[4] == 0.0))
+              simple_own = false;
           }
       (void)gx; (void)gy;
     }
@@ -628,7 +634,9 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
     for (const Block& b : c->blocks)
       for (int q = 0; q < b.P[0] * b.P[1] * b.P[2]; ++q) c->subs[b.sid0 + q].ebase = b.ebase;
   }
-  c->fused = c->p.precision == 1 && c->ndim == 3 && c->p.viscous && c->p.order == 4 && c->all_periodic;
+  // the fused FP32 stage: 3-D Navier-Stokes CD4; on connected grids its halo gather takes wall
+  // mirrors / outflow copies as one unit copy of an own point of the same plane
+  c->fused = c->p.precision == 1 && c->ndim == 3 && c->p.viscous && c->p.order == 4 && simple_own;
   c->fused_curv = curv;
   c->fblock_n = 0;
   if (c->p.precision == 1 && c->p.filter && c->ndim == 3 && !curv && c->all_periodic && nsub > 0) {

@@ -110,18 +110,59 @@ __global__ void __launch_bounds__(256) k_halo_prims(Geometry g, Physics ph, Step
   const int exy = d.ex * d.ey;
   const int k = t / exy, r2 = t - k * exy, j = r2 / d.ex, i = r2 - j * d.ex;
   const int ci = i - g.G, cj = j - g.G, ck = k - g.Gz;
-  int kd = 0;
-  if (ci < 0 || ci >= d.sx) kd = max(kd, face_delay(sc, sid, ci < 0 ? 0 : 1));
-  if (cj < 0 || cj >= d.sy) kd = max(kd, face_delay(sc, sid, cj < 0 ? 2 : 3));
-  if (ck < 0 || ck >= d.sz) kd = max(kd, face_delay(sc, sid, ck < 0 ? 4 : 5));
   // halo points lie within G of the sub-domain: one conditional wrap per axis
   auto wrap1 = [](int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); };
   const int gx = wrap1(d.ox + ci, d.bnx), gy = wrap1(d.oy + cj, d.bny), gz = wrap1(d.oz + ck, d.bnz);
   const long long gi = d.bbase + (long long)gx + (long long)d.bnx * ((long long)gy + (long long)d.bny * gz);
   const long long lvN = 5 * g.N, P = g.Ptot, o = d.pbase + t;
+  const int ux = d.ox + ci, uy = d.oy + cj;
+  const bool gather = d.ebase >= 0 && (ux < 0 || ux >= d.bnx || uy < 0 || uy >= d.bny);
+  // delay of the faces the point lies beyond (faces on a physical boundary of the block: none)
+  int kd = 0;
+  if ((ci < 0 || ci >= d.sx) && !(gather && ((d.phys >> (ci < 0 ? 0 : 1)) & 1))) kd = max(kd, face_delay(sc, sid, ci < 0 ? 0 : 1));
+  if ((cj < 0 || cj >= d.sy) && !(gather && ((d.phys >> (cj < 0 ? 2 : 3)) & 1))) kd = max(kd, face_delay(sc, sid, cj < 0 ? 2 : 3));
+  if (ck < 0 || ck >= d.sz) kd = max(kd, face_delay(sc, sid, ck < 0 ? 4 : 5));
   // ring slot of level n - kd - l: (n mod R) - kd - l, wrapped once (kd + l < R)
   const int nR = (int)(sc.n % sc.R);
   auto slot = [&](int l) { const int q = nR - kd - l; return q < 0 ? q + sc.R : q; };
+  if (gather) {
+    // beyond a non-periodic block face (a connected grid): the gather entry's sources.  Entries
+    // whose sources are the sub-domain's own points (wall mirrors, outflow copies) take the
+    // current stage values inside the fused stage; the others -- neighbouring PEs' values seen
+    // with the delay of the faces crossed, and far-field constants -- are prepared here per stage
+    // as for any other halo point.
+    const GatherEntry& E = g.gent[g.emap[d.ebase + (ux + g.GE) + (long long)d.gmx * ((uy + g.GE) + (long long)d.gmy * gz)]];
+    if (E.nt == 1 && !(E.flags[0] & 2) && E.sid[0] == sid) return;
+    double acc[S][5];
+#pragma unroll
+    for (int m = 0; m < S; ++m)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) acc[m][v] = E.cst[v];
+    for (int q = 0; q < E.nt; ++q) {
+      const double wt = E.w[q], wf = (E.flags[q] & 1) ? -wt : wt;
+      const long long so = E.off[q], sbN = E.bN[q];
+      for (int l = 0; l < (sc.mode == 2 ? 1 : sc.C); ++l) {
+        const double* src = ring + (long long)slot(l) * lvN;
+        double r[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) r[v] = src[so + v * sbN];
+#pragma unroll
+        for (int m = 0; m < S; ++m) {
+          const double wl = sc.mode == 2 ? 1.0 : __ldg(sc.W + (kd * S + m) * sc.C + l);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) acc[m][v] = fma(((v >= 1 && v <= 3) ? wf : wt) * wl, r[v], acc[m][v]);
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < (sc.mode == 2 ? 1 : S); ++m) {
+      float w[7];
+      prims32(acc[m], k32, w);
+#pragma unroll
+      for (int c = 0; c < 7; ++c) Wh[(long long)(m * 7 + c) * P + o] = w[c];
+    }
+    return;
+  }
   if (sc.mode == 2) {  // AS: the latest visible level, the same for every stage
     const double* src = ring + (long long)slot(0) * lvN;
     double u[5];
@@ -205,6 +246,12 @@ struct BoxCols {
   int pxy[KB];  // (lx + G) + ex (ly + G) in the padded box
   int dxy[KB];  // dx | dy << 8 (distance outside the sub-domain), -1 for no column
   int pq[KB];   // box index | window index << 16 (window index 0xffff: outside the window)
+  // beyond a non-periodic block face (connected grids): 0 not such a column; 1 | src << 2 |
+  // mirror << 18 a wall mirror / outflow copy of the sub-domain's own point at box index src on
+  // the planes inside the sub-domain (current stage value, momentum negated when mirrored; on
+  // planes beyond it in z the source is the z-neighbour's, as for 2); 2 a neighbouring PE's or
+  // far-field value (the halo store on asynchronous steps, an inline gather on synchronous ones)
+  int gm[KB];
 };
 
 __device__ __forceinline__ float2 lo2(const float4& a) { return make_float2(a.x, a.y); }
@@ -351,6 +398,19 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
         const int wi2 = p % BX - (HB - 2), wj2 = p / BX - (HB - 2);
         const int qw = (wi2 >= 0 && wi2 < WX && wj2 >= 0 && wj2 < S::WY) ? wj2 * WX + wi2 : 0xffff;
         bc.pq[k] = p | (qw << 16);
+        bc.gm[k] = 0;
+        const int ux = d.ox + lx, uy = d.oy + ly;
+        if (d.ebase >= 0 && (ux < 0 || ux >= d.bnx || uy < 0 || uy >= d.bny)) {
+          // the gather entry of this column (extruded blocks: its kind does not depend on z)
+          const GatherEntry& E = g.gent[g.emap[d.ebase + (ux + g.GE) + (long long)d.gmx * ((uy + g.GE) + (long long)d.gmy * d.oz)]];
+          bc.gm[k] = 2;
+          if (E.nt == 1 && !(E.flags[0] & 2) && E.sid[0] == wk[0]) {
+            const long long gi = E.off[0] - d.bbase;
+            const int sxg = (int)(gi % d.bnx), syg = (int)((gi / d.bnx) % d.bny);
+            const int bi = sxg - d.ox - (tx0 - HB), bj = syg - d.oy - (ty0 - HB);
+            if (bi >= 0 && bi < BX && bj >= 0 && bj < S::BY) bc.gm[k] = 1 | ((bj * BX + bi) << 2) | ((E.flags[0] & 1) << 18);
+          }
+        }
       }
     }
     // dt R of the tile column for planes G-2..G+1 (before the contributions of flux plane G),
@@ -401,6 +461,10 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
         const int p = bc.pq[k] & 0xffff;
         const int src = box_source(sc.mode, g.r, bc.dxy[k] & 255, bc.dxy[k] >> 8, dz);
         if (src == 1 && bulk) continue;  // in a bulk row
+        // a wall mirror's source is the own point of the same plane only inside the sub-domain in z;
+        // beyond it in z the source belongs to the neighbouring PE in z (foreign)
+        const int gmk = ((bc.gm[k] & 3) == 1 && dz > 0) ? 2 : bc.gm[k];
+        if ((gmk & 3) == 1 || (gmk == 2 && sc.mode == 0)) continue;  // taken at conversion
         if (src == 1) {
           const double* s0 = Uin + zoff + bc.xy[k];
 #pragma unroll
@@ -437,7 +501,32 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
           if (src == 0) continue;
           const int p = bc.pq[k] & 0xffff, qw = bc.pq[k] >> 16;
           float w[7];
-          if (src == 1) {
+          const int gmk = ((bc.gm[k] & 3) == 1 && dz > 0) ? 2 : bc.gm[k];  // (as in the staging)
+          if ((gmk & 3) == 1) {
+            // wall mirror / outflow copy: the own source point staged in this plane
+            const int ps = (gmk >> 2) & 0xffff;
+            const double sg = (gmk >> 18) & 1 ? -1.0 : 1.0;
+            double u[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) u[v] = (v >= 1 && v <= 3) ? sg * sStg[v * NB + ps] : sStg[v * NB + ps];
+            prims32(u, k32, w);
+          } else if (gmk == 2 && sc.mode == 0) {
+            // synchronous step beyond an interface / far field: the entry's sources from the live
+            // stage input, weighted (spanwise interpolation), plus the far-field constant
+            const int lxc = tx0 - HB + p % BX, lyc = ty0 - HB + p / BX;
+            const int gzc = wrapc(d.oz + L, d.bnz);
+            const GatherEntry& E =
+                g.gent[g.emap[d.ebase + (d.ox + lxc + g.GE) + (long long)d.gmx * ((d.oy + lyc + g.GE) + (long long)d.gmy * gzc)]];
+            double u[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) u[v] = E.cst[v];
+            for (int q = 0; q < E.nt; ++q) {
+              const double wt = E.w[q], wf = (E.flags[q] & 1) ? -wt : wt;
+#pragma unroll
+              for (int v = 0; v < 5; ++v) u[v] = fma((v >= 1 && v <= 3) ? wf : wt, Uin[E.off[q] + (long long)v * E.bN[q]], u[v]);
+            }
+            prims32(u, k32, w);
+          } else if (src == 1) {
             double u[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v) u[v] = sStg[v * NB + p];
@@ -657,12 +746,17 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
         aq4[3] = -k2z * fz4;
       }
       if (outp) {
+        // no-slip wall points keep zero momentum (connected grids)
+        const bool wallpt = d.wall && ((((d.wall >> 0) & 1) && lx == 0) || (((d.wall >> 1) & 1) && lx == d.sx - 1) ||
+                                       (((d.wall >> 2) & 1) && ly == 0) || (((d.wall >> 3) & 1) && ly == d.sy - 1));
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
           const double dtR = curv ? f2d_fast(out[c]) * Jown : f2d_fast(out[c]);  // index-space divergence x J
-          const double qn = first ? dtR : fma(A, qin[c], dtR);
+          double qn = first ? dtR : fma(A, qin[c], dtR);
+          double un = fma(B, qn, uin[c]);
+          if (wallpt && c >= 1 && c <= 3) qn = un = 0.0;
           if (!last) Q[c * d.bN + go] = qn;
-          Uout[c * d.bN + go] = fma(B, qn, uin[c]);
+          Uout[c * d.bN + go] = un;
         }
       }
     }

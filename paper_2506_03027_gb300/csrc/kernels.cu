@@ -22,11 +22,38 @@
 #include <cmath>
 #include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "cfs_internal.h"
 #include "device_common.cuh"
 
 namespace cfs {
+
+// Programmatic dependent launch: the kernels of the FP64 stage sequence (view, flux, stage update,
+// filter passes, step counter) are launched with programmatic stream serialization, so the next
+// kernel's CTAs are scheduled while this one drains.  Every such kernel first lets its successor
+// launch, then waits for its predecessor to complete (and its memory to be visible) before it
+// reads anything the predecessor wrote; launched without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+static inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // ------------------------------------------------------------------------------- k_view
 
@@ -55,17 +82,13 @@ __device__ __forceinline__ void store_prims(const Geometry& g, const Physics& ph
   Wp[6 * P + o] = rE + p;  // rho E + p (energy flux factor; minus H_ref in the FP32 form)
 }
 
-// k_view, owned points: the stage input of the sub-domain's own points as primitives.
+// k_view, owned points: the stage input of the sub-domain's own points as primitives (thread t
+// of sub-domain sid).
 template <typename T>
-__global__ void __launch_bounds__(512) k_view_own(Geometry g, Physics ph, StepSched sc, const double* __restrict__ Uin0,
-                                                  const double* __restrict__ ring, int in_ring,
-                                                  const SubDev* __restrict__ subs, T* __restrict__ Wp) {
-  sc = resolve(sc);
-  const double* Uin = ring_or(Uin0, in_ring, ring, sc, 0);
-  const int sid = blockIdx.y;
+__device__ __forceinline__ void view_own(const Geometry& g, const Physics& ph, const double* __restrict__ Uin,
+                                         const SubDev* __restrict__ subs, T* __restrict__ Wp, int sid, int t) {
   const SubDev d = subs[sid];
   if (!d.own) return;  // another process's sub-domain
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // own points of a sub-domain: < 2^31
   if (t >= d.sx * d.sy * d.sz) return;
   const int sxy = d.sx * d.sy, ck = t / sxy, r2 = t - ck * sxy, cj = r2 / d.sx, ci = r2 - cj * d.sx;
   const long long gi = (long long)(d.ox + ci) + (long long)d.bnx * ((long long)(d.oy + cj) + (long long)d.bny * (d.oz + ck));
@@ -81,13 +104,10 @@ __global__ void __launch_bounds__(512) k_view_own(Geometry g, Physics ph, StepSc
 // that no warp mixes owned points with the AT weighting.  SA: the neighbour's live value; AT:
 // sum_l W^(m)_l(k) U^{n-k-l} in FP64 (Eq. 14-15, buffer updates of Eq. 8 collapsed); AS: U^{n-k}.
 template <typename T>
-__global__ void __launch_bounds__(512) k_view_halo(Geometry g, Physics ph, StepSched sc, const double* __restrict__ Uin0,
-                                                   const double* __restrict__ ring, int in_ring,
-                                                   const SubDev* __restrict__ subs, const int2* __restrict__ halo,
-                                                   long long nhalo, T* __restrict__ Wp, int stage, int s) {
-  sc = resolve(sc);
-  const double* Uin = ring_or(Uin0, in_ring, ring, sc, 0);
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void view_halo(const Geometry& g, const Physics& ph, const StepSched& sc,
+                                          const double* __restrict__ Uin, const double* __restrict__ ring,
+                                          const SubDev* __restrict__ subs, const int2* __restrict__ halo, long long nhalo,
+                                          T* __restrict__ Wp, int stage, int s, long long t) {
   if (t >= nhalo) return;
   const int2 e = halo[t];
   const int sid = e.x;
@@ -193,6 +213,25 @@ __global__ void __launch_bounds__(512) k_view_halo(Geometry g, Physics ph, StepS
     }
   }
   store_prims<T>(g, ph, u, d.pbase + q, Wp);
+}
+
+// The stage input as primitives, own points and halo points in one launch: the first own_blocks x
+// nsub CTAs take the owned points (own_blocks CTAs per sub-domain), the rest the halo list.
+template <typename T>
+__global__ void __launch_bounds__(512) k_view(Geometry g, Physics ph, StepSched sc, const double* __restrict__ Uin0,
+                                              const double* __restrict__ ring, int in_ring, const SubDev* __restrict__ subs,
+                                              const int2* __restrict__ halo, long long nhalo, T* __restrict__ Wp,
+                                              int stage, int s, int own_blocks) {
+  pdl_enter();
+  sc = resolve(sc);
+  const double* Uin = ring_or(Uin0, in_ring, ring, sc, 0);
+  const long long b = blockIdx.x, nown = (long long)own_blocks * g.nsub;
+  if (b < nown) {
+    const int sid = (int)(b / own_blocks);
+    view_own<T>(g, ph, Uin, subs, Wp, sid, (int)(b - (long long)sid * own_blocks) * blockDim.x + threadIdx.x);
+  } else {
+    view_halo<T>(g, ph, sc, Uin, ring, subs, halo, nhalo, Wp, stage, s, (b - nown) * blockDim.x + threadIdx.x);
+  }
 }
 
 // ------------------------------------------------------------------------------- k_flux
@@ -384,6 +423,7 @@ __device__ __forceinline__ bool flux_point(const SubDev& d, int r, int t, int& c
 template <typename T, int ND>
 __global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubDev* __restrict__ subs,
                                               const T* __restrict__ Wp, T* __restrict__ Phi) {
+  pdl_enter();
   const int sid = blockIdx.y;
   const SubDev d = subs[sid];
   if (!d.own) return;  // another process's sub-domain
@@ -472,6 +512,7 @@ __global__ void __launch_bounds__(512) k_rk(Geometry g, Physics ph, StepSched sc
                                             double* __restrict__ Uout0, const double* __restrict__ ring, int in_ring,
                                             int out_ring, double* __restrict__ Q, double A, double B, double dt,
                                             int first, int last) {
+  pdl_enter();
   sc = resolve(sc);
   const double* Uin = ring_or(Uin0, in_ring, ring, sc, 0);
   double* Uout = const_cast<double*>(ring_or(Uout0, out_ring, ring, sc, 1));
@@ -622,10 +663,12 @@ static int stage_impl(const Geometry& g, const Physics& ph, const StepSched& sc,
                       cudaStream_t st, long long* launches, const Timer* tm) {
   const int B = (a.threads == 128 || a.threads == 512) ? a.threads : 256;
   dim3 gf(nblk(a.max_flux, B), g.nsub), gr(nblk(a.max_own, B), g.nsub);
-  TIMED(tm, 0, (k_view_own<T><<<gr, B, 0, st>>>(g, ph, sc, a.Uin, a.ring, a.in_ring, a.subs, (T*)a.Wp)));
-  if (a.nhalo > 0)
-    TIMED(tm, 0, (k_view_halo<T><<<nblk(a.nhalo, B), B, 0, st>>>(g, ph, sc, a.Uin, a.ring, a.in_ring, a.subs,
-                                                                 (const int2*)a.halo, a.nhalo, (T*)a.Wp, a.stage, a.s)));
+  {
+    const unsigned own_blocks = nblk(a.max_own, B);
+    const unsigned nb = own_blocks * (unsigned)g.nsub + nblk(a.nhalo, B);
+    TIMED(tm, 0, (launch_pdl(k_view<T>, dim3(nb), dim3(B), 0, st, g, ph, sc, a.Uin, a.ring, a.in_ring, a.subs,
+                             (const int2*)a.halo, a.nhalo, (T*)a.Wp, a.stage, a.s, (int)own_blocks)));
+  }
   if (a.compact) {
     // compact scheme: fluxes, then one line-solve launch per axis into R, then the update
     const long long nl = 5LL * a.Lmax * a.Lmax;
@@ -642,19 +685,19 @@ static int stage_impl(const Geometry& g, const Physics& ph, const StepSched& sc,
     }
     TIMED(tm, 2, (k_rk_from_R<<<gr, B, 0, st>>>(sc, a.subs, a.R, a.Uin, a.Uout, a.ring, a.in_ring, a.out_ring, a.Q, a.A,
                                                 a.B, a.dt, a.first, a.last)));
-    if (launches) *launches += (a.nhalo > 0 ? 2 : 1) + 1 + g.ndim + 1;
+    if (launches) *launches += 1 + 1 + g.ndim + 1;
     return (int)cudaGetLastError();
   }
   if (g.ndim == 3) {
-    TIMED(tm, 1, (k_flux<T, 3><<<gf, B, 0, st>>>(g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
-    TIMED(tm, 2, (k_rk<T, 3><<<gr, B, 0, st>>>(g, ph, sc, a.subs, (const T*)a.Phi, a.Uin, a.Uout, a.ring, a.in_ring,
-                                               a.out_ring, a.Q, a.A, a.B, a.dt, a.first, a.last)));
+    TIMED(tm, 1, (launch_pdl(k_flux<T, 3>, gf, dim3(B), 0, st, g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
+    TIMED(tm, 2, (launch_pdl(k_rk<T, 3>, gr, dim3(B), 0, st, g, ph, sc, a.subs, (const T*)a.Phi, a.Uin, a.Uout, a.ring,
+                             a.in_ring, a.out_ring, a.Q, a.A, a.B, a.dt, a.first, a.last)));
   } else {
-    TIMED(tm, 1, (k_flux<T, 2><<<gf, B, 0, st>>>(g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
-    TIMED(tm, 2, (k_rk<T, 2><<<gr, B, 0, st>>>(g, ph, sc, a.subs, (const T*)a.Phi, a.Uin, a.Uout, a.ring, a.in_ring,
-                                               a.out_ring, a.Q, a.A, a.B, a.dt, a.first, a.last)));
+    TIMED(tm, 1, (launch_pdl(k_flux<T, 2>, gf, dim3(B), 0, st, g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
+    TIMED(tm, 2, (launch_pdl(k_rk<T, 2>, gr, dim3(B), 0, st, g, ph, sc, a.subs, (const T*)a.Phi, a.Uin, a.Uout, a.ring,
+                             a.in_ring, a.out_ring, a.Q, a.A, a.B, a.dt, a.first, a.last)));
   }
-  if (launches) *launches += a.nhalo > 0 ? 4 : 3;
+  if (launches) *launches += 3;
   return (int)cudaGetLastError();
 }
 
@@ -700,6 +743,7 @@ __host__ __device__ inline size_t filter_smem_bytes(int Lmax, int precision) {
 
 template <typename T, int axis>
 __global__ void __launch_bounds__(128) k_filter(Geometry g, StepSched sc, FilterLaunch f) {
+  pdl_enter();
   sc = resolve(sc);
   if (f.only_sync && sc.mode != 0) return;
   constexpr bool F32 = std::is_same<T, float>::value;
@@ -1038,9 +1082,9 @@ int launch_filter(const Geometry& g, const StepSched& sc, const FilterLaunch& f,
     else if (axis == 1) k_filter<float, 1><<<nb, 128, sm, st>>>(g, sc, f);
     else k_filter<float, 2><<<nb, 128, sm, st>>>(g, sc, f);
   } else {
-    if (axis == 0) k_filter<double, 0><<<nb, 128, sm, st>>>(g, sc, f);
-    else if (axis == 1) k_filter<double, 1><<<nb, 128, sm, st>>>(g, sc, f);
-    else k_filter<double, 2><<<nb, 128, sm, st>>>(g, sc, f);
+    if (axis == 0) launch_pdl(k_filter<double, 0>, dim3(nb), dim3(128), sm, st, g, sc, f);
+    else if (axis == 1) launch_pdl(k_filter<double, 1>, dim3(nb), dim3(128), sm, st, g, sc, f);
+    else launch_pdl(k_filter<double, 2>, dim3(nb), dim3(128), sm, st, g, sc, f);
   }
   if (tm) tm->rec(tm->self, 3, 0);
   if (launches) *launches += 1;
@@ -1151,6 +1195,7 @@ int launch_diagnostics_block(const Geometry& g, const DiagBlock& b, const double
 }
 
 __global__ void k_advance_step(long long* dn) {
+  pdl_enter();
   if (threadIdx.x == 0 && blockIdx.x == 0) *dn += 1;
 }
 
@@ -1264,7 +1309,7 @@ int launch_strip_unpack(double* U, const long long* off, const int* bN, long lon
 }
 
 int launch_advance_step(long long* dn, void* stream) {
-  k_advance_step<<<1, 32, 0, (cudaStream_t)stream>>>(dn);
+  launch_pdl(k_advance_step, dim3(1), dim3(32), 0, (cudaStream_t)stream, dn);
   return (int)cudaGetLastError();
 }
 

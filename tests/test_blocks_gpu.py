@@ -87,17 +87,46 @@ def test_cgrid_graph_mode_is_bitwise_identical():
         assert np.array_equal(a, b)
 
 
-def test_cgrid_fp32_form():
-    """FP32 intermediates on the C-grid (multi-kernel stage, gather halos): within the FP32-form
-    error bound of the oracle."""
-    mb, U0 = cgrid("SAA")
+@pytest.mark.parametrize("algo", ["SA", "CAA", "SAA"])
+def test_cgrid_fp32_form(algo):
+    """FP32 intermediates on the C-grid through the fused stage (one launch per RK stage): halo
+    points beyond interfaces and far fields from the per-step halo store (AT/AS steps) or an inline
+    gather of the live values (synchronous steps), wall mirrors and outflow copies from the own
+    points of the same plane, wall points' momentum held at zero; within the FP32-form error bound
+    of the oracle, walls at rest."""
+    mb, U0 = cgrid(algo)
+    if algo == "CAA":
+        mb = mb.replace_all(caa_L=3, kmax=2)
     n = 20
-    d = sub_delays(mb, n)
+    d = sub_delays(mb, n) if algo == "SAA" else None
     Ug = run_mb(mb, U0, n, delays=d, precision=1)
     Uo = orc.run(mb, U0, n, delays=d)
     for b, (a, r) in enumerate(zip(Ug, Uo)):
         e = rel_l2(a, r)
         assert np.all(np.isfinite(a)) and np.all(e < 1e-6), (b, e)
+    for b in range(1, 5):  # the airfoil blocks' wall rows
+        assert np.all(Ug[b][1:4, :, 0, :] == 0.0)
+
+
+def test_cgrid_fp32_fused_graph_and_tiles_identical():
+    """The C-grid's fused FP32 stage gives the same bits step by step, as CUDA-graph replays and
+    for another tile shape."""
+    import torch
+    mb, U0 = cgrid("SAA")
+    n = 9
+    d = sub_delays(mb, n)
+    Ua = run_mb(mb, U0, n, delays=d, precision=1)
+    Ub = run_mb(mb, U0, n, delays=d, precision=1, graph=True)
+    s = cfs.Solver(mb, precision=1, tiles=(4, 8, 256))
+    try:
+        s.set_schedule(delays=d)
+        s.set_states(U0)
+        s.step(n)
+        Uc = s.get_states()
+    finally:
+        s.close()
+    for a, b, c in zip(Ua, Ub, Uc):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
 
 
 def test_cgrid_freestream_preserved_on_gpu():

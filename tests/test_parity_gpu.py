@@ -211,7 +211,7 @@ def test_launch_count():
     s.set_schedule()
     s.set_state(I.tgv_state(c))
     s.step(3)
-    assert s.launches() == 3 * (5 * 4 + 3)  # per step: 5 stages x 4 kernels (view own/halo, flux, rk) + 3 filter passes
+    assert s.launches() == 3 * (5 * 3 + 3)  # per step: 5 stages x 3 kernels (view, flux, rk) + 3 filter passes
     s.close()
 
 
