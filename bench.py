@@ -60,10 +60,10 @@ HBM_GBS_FALLBACK = 6800.0
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel kind, with the sha1 of
 # the flux kernel's source they were taken from (kernels_sha1; null once it changes); filled
 # from profiles/.
-TRAFFIC = {"source_sha1": "184971aca5f84c6d0a544168dc2fdc1cca98847e",
-           # k_flux<double,3>: 92.5 MB read + 81.3 MB written per launch in an ncu capture of the
+TRAFFIC = {"source_sha1": "b28dc3501138b4889ce49f889d2dba9ffc46cffc",
+           # k_flux<double,3>: 92.7 MB read + 82.0 MB written per launch in an ncu capture of the
            # 96^3 case (27 sub-domains of 32^3), x 64/27 for the 64 sub-domains of 128^3
-           "bytes_per_launch": {"flux": 411.9e6}}
+           "bytes_per_launch": {"flux": 414.1e6}}
 
 
 def kernels_sha1(root: str = ROOT) -> str:
@@ -883,7 +883,8 @@ def main():
     ap.add_argument("--split", type=int, default=4, help="sub-domains per axis (profiling runs only)")
     ap.add_argument("--tiles", default="", help="fy,zc,threads launch shapes of the main path (profiling runs only)")
     ap.add_argument("--only-form", default="", choices=["", "cgrid_naca0012", "cgrid_naca0012_fp32_intermediates",
-                                                        "learned_halo", "compact_euler"],
+                                                        "learned_halo", "compact_euler", "batched_blocks_curvilinear",
+                                                        "static_diagnostics"],
                     help="run one form alone and print its result (profiling runs only; --tiles skips its autotuning)")
     ap.add_argument("--cgrid-half", action="store_true",
                     help="with --only-form: the C-grid at half the points per direction (profiling runs only)")
@@ -900,6 +901,12 @@ def main():
             return
         if args.only_form == "compact_euler":
             print(json.dumps(compact_form(args)), flush=True)
+            return
+        if args.only_form == "batched_blocks_curvilinear":
+            print(json.dumps(batched_form(args, 0, curvilinear=True)), flush=True)
+            return
+        if args.only_form == "static_diagnostics":
+            print(json.dumps(static_diagnostics_form()), flush=True)
             return
         print(json.dumps(cgrid_form(args, 1 if args.only_form.endswith("fp32_intermediates") else 0)), flush=True)
         return

@@ -278,8 +278,10 @@ int cfs_at_weights(int order, int kmax, double* W);
 /* Compute sub-domains [starts[rank], starts[rank + 1]) of the nranks ranges in starts[nranks + 1]
  * (host, copied; starts[0] = 0, non-decreasing, starts[nranks] = the number of sub-domains, checked
  * at cfs_finalize).  Before cfs_finalize (ESTATE after).  nranks = 1 restores the single-process
- * context.  At cfs_finalize EINVAL unless every block is periodic on every face, the precision is
- * FP64 (0); the learned halo and CUDA-graph mode are refused on a partitioned context. */
+ * context.  Periodic blocks and connected grids (interfaces, walls, far fields, outflows: the
+ * sources of the points beyond their faces travel like any other halo point).  At cfs_finalize
+ * EINVAL unless the precision is FP64 (0); the learned halo and CUDA-graph mode are refused on a
+ * partitioned context. */
 cfs_status cfs_set_partition(cfs_ctx* ctx, int nranks, const int* starts, int rank);
 
 /* Transport of a partitioned context, called by cfs_step at every exchange point with:

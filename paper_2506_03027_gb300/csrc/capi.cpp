@@ -513,7 +513,6 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   cfs::StripPlan plan;
   if (parted) {
     if (c->p.precision != 0 || c->learned) return fail(c, CFS_EINVAL, "a partitioned context runs the FP64 path only");
-    if (!c->all_periodic) return fail(c, CFS_EINVAL, "a partitioned context needs blocks periodic on every face");
     if ((int)c->part_starts.size() != c->part_n + 1 || c->part_starts[c->part_n] != nsub)
       return fail(c, CFS_EINVAL, "the partition does not cover the sub-domains");
     for (int sid = 0; sid < nsub; ++sid)
@@ -538,6 +537,8 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   ph.ire = c->p.viscous ? 1.0 / c->p.re : 0.0;
   ph.kappa = c->p.viscous ? 1.0 / ((c->p.gamma - 1.0) * c->p.pr * c->p.mach * c->p.mach) : 0.0;
   ph.visc_law = c->p.visc_law; ph.visc_exp = c->p.visc_exp;
+  ph.kgM2 = ph.kappa * ph.gM2;
+  ph.ivT = (c->p.viscous && c->p.visc_law == 1) ? ph.ire * std::pow(ph.kappa, -c->p.visc_exp) : ph.ire;
   ph.p_ref = 1.0 / ph.gM2;
   ph.E_ref = ph.p_ref / ph.gm1;
   ph.H_ref = ph.E_ref + ph.p_ref;

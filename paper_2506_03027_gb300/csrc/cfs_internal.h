@@ -101,6 +101,10 @@ struct Physics {
   double gamma, gm1, gM2;  // gamma, gamma - 1, gamma M^2
   double ire;              // 1 / Re
   double kappa;            // 1 / ((gamma - 1) Pr M^2)
+  // the primitives' temperature slot holds kappa T (the heat flux is then its plain gradient):
+  // kgM2 = kappa gamma M^2; ivT = 1/Re, times kappa^-a for the power law (its mu = T^a is taken as
+  // (kappa T)^a kappa^-a)
+  double kgM2, ivT;
   int visc_law;
   double visc_exp;
   double c1[3], c2[3];     // CD coefficients per axis: c1 = (a/2)/h, c2 = (b/4)/h

@@ -71,7 +71,8 @@ __device__ __forceinline__ void store_prims(const Geometry& g, const Physics& ph
   const T ke = (T)0.5 * ((T)u[1] * uu + (T)u[2] * vv + (T)u[3] * ww);
   const T rE = f32 ? (T)(u[4] - ph.E_ref) : (T)u[4];
   const T p = (T)ph.gm1 * (rE - ke);
-  const T temp = f32 ? ((T)ph.gM2 * p + (T)1) * ir : (T)ph.gM2 * p * ir;
+  // kappa T (the heat flux kappa mu dT/dx is then mu times its gradient)
+  const T temp = f32 ? fma((T)ph.kgM2, p, (T)ph.kappa) * ir : (T)ph.kgM2 * p * ir;
   const long long P = g.Ptot;
   Wp[o] = rho;
   Wp[P + o] = uu;
@@ -283,7 +284,8 @@ __device__ __forceinline__ double pow_tab(double x, double a) {
 }
 
 // Viscosity law: mu = 1, or the power law mu = T^visc_exp -- in the intermediate precision (the
-// FP32 form evaluates it in FP32: a power in FP64 runs at the FP64 rate)
+// FP32 form evaluates it in FP32: a power in FP64 runs at the FP64 rate).  The flux kernels pass
+// kappa T and take the factor kappa^-a with 1/Re (Physics::ivT).
 template <typename T>
 __device__ __forceinline__ T visc_mu(const Physics& ph, T temp) {
   if (ph.visc_law != 1) return (T)1;
@@ -298,13 +300,25 @@ __device__ __forceinline__ T cdiff(const T* __restrict__ f, long long q, long lo
   return d;
 }
 
+// The same difference without its factor: CD4 (f_{+2} - f_{-2}) - 8 (f_{+1} - f_{-1}) (times c2
+// gives cdiff), CD2 f_{+1} - f_{-1} (times c1)
+template <typename T>
+__device__ __forceinline__ T cdiff_iso(const T* __restrict__ f, long long q, long long st, int r) {
+  const T d1 = f[q + st] - f[q - st];
+  return r == 2 ? fma((T)-8, d1, f[q + 2 * st] - f[q - 2 * st]) : d1;
+}
+
 // Curvilinear flux point (App. A, Eq. A1-A4 with a time-invariant grid): gradients in index
-// space (c1, c2 of the block are the index-space coefficients), mapped to physical gradients by
-// d phi / d x_j = J sum_k (metric row k)_j d phi / d xi_k; combined fluxes along each index
-// direction a with the metric row m_a = (d xi_a / dx, d xi_a / dy, d xi_a / dz) / J:
+// space, mapped to physical gradients by d phi / d x_j = J sum_k (metric row k)_j d phi / d xi_k;
+// combined fluxes along each index direction a with the metric row
+// m_a = (d xi_a / dx, d xi_a / dy, d xi_a / dz) / J:
 //   Phi_a = -[rho U^, rho u U^ + m_x p, rho v U^ + m_y p, rho w U^ + m_z p, (rho E + p) U^]
 //           + (1/Re) [0, m . tau_1, m . tau_2, m . tau_3, m . b],   U^ = m . u.
-// The grid is extruded in z: rows xi = (m0, m1, 0), eta = (m2, m3, 0), zeta = (0, 0, m4).
+// The grid is extruded in z: rows xi = (a00, a01, 0), eta = (a10, a11, 0), zeta = (0, 0, a22), so
+// the products with the zero entries are left out.  The index spacing is 1 on every axis, so the
+// differences are taken without their factor gs (as cdiff_iso); the viscous flux is linear in the
+// gradients, so gs, J and mu multiply it once, in iv.  A strip point evaluates the flux along its
+// axis only, with the temperature gradients that flux needs.
 template <typename T, int ND>
 __device__ __forceinline__ void flux_curvilinear(const Geometry& g, const Physics& ph, const SubDev& d,
                                                  const T* __restrict__ W, T* __restrict__ out, long long q, int ci,
@@ -315,56 +329,79 @@ __device__ __forceinline__ void flux_curvilinear(const Geometry& g, const Physic
   // metric plane of the block (extended by G, z-independent): flux points lie within r <= G
   const double* M = g.metric + d.mbase + (long long)(d.ox + ci + g.G) + (long long)d.mx * (d.oy + cj + g.G);
   const long long pl = d.mpl;
-  const T m[3][3] = {{(T)M[0], (T)M[pl], (T)0}, {(T)M[2 * pl], (T)M[3 * pl], (T)0}, {(T)0, (T)0, (T)M[4 * pl]}};
-  const T J = (T)M[6 * pl];
+  const T a00 = (T)M[0], a01 = (T)M[pl], a10 = (T)M[2 * pl], a11 = (T)M[3 * pl], a22 = (T)M[4 * pl];
   const T rho = W[q], u = W[P + q], v = W[2 * P + q], w = W[3 * P + q], p = W[4 * P + q];
   const T et = W[6 * P + q];
-  const T vel[3] = {u, v, w};
-  T tau[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-  T bq[3] = {0, 0, 0};
+  // tau / (gs J mu) and b / (gs J mu) (b_i = u_j tau_ij + kappa mu dT/dx_i)
+  T t00 = 0, t11 = 0, t22 = 0, t01 = 0, t02 = 0, t12 = 0, b0 = 0, b1 = 0, b2 = 0;
+  T iv = (T)ph.ivT;
   if (g.viscous) {
     const long long st[3] = {1, sty, stz};
-    T dxi[4][3];  // d (u, v, w, T) / d xi_k
+    const bool needTxy = nout == 0 || !oz, needTz = nout == 0 || oz;
+    T dxi[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // d (u, v, w, T) / d xi_k / gs
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const T c1 = (T)d.c1[k], c2 = (T)d.c2[k];
+    for (int k = 0; k < ND; ++k) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
-        dxi[c][k] = (k < ND) ? cdiff(W + (c == 3 ? 5 : 1 + c) * P, q, st[k], c1, c2, r) : (T)0;
+      for (int c = 0; c < 3; ++c) dxi[c][k] = cdiff_iso(W + (1 + c) * P, q, st[k], r);
+      if (k < 2 ? needTxy : needTz) dxi[3][k] = cdiff_iso(W + 5 * P, q, st[k], r);
     }
-    T dx[4][3];  // physical gradients
+    T G[4][3];  // physical gradients / (gs J)
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) dx[c][j] = J * (m[0][j] * dxi[c][0] + m[1][j] * dxi[c][1] + m[2][j] * dxi[c][2]);
-    T mu = (T)1;
-    if (ph.visc_law == 1) mu = visc_mu<T>(ph, W[5 * P + q]);
-    const T div = dx[0][0] + dx[1][1] + dx[2][2];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) tau[i][j] = mu * (dx[i][j] + dx[j][i]) - (i == j ? (T)(2.0 / 3.0) * mu * div : (T)0);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) bq[i] = u * tau[i][0] + v * tau[i][1] + w * tau[i][2] + (T)ph.kappa * mu * dx[3][i];
+    for (int c = 0; c < 4; ++c) {
+      G[c][0] = fma(a10, dxi[c][1], a00 * dxi[c][0]);
+      G[c][1] = fma(a11, dxi[c][1], a01 * dxi[c][0]);
+      G[c][2] = ND == 3 ? a22 * dxi[c][2] : (T)0;
+    }
+    const T d23 = (T)(-2.0 / 3.0) * (G[0][0] + G[1][1] + G[2][2]);
+    t00 = fma((T)2, G[0][0], d23);
+    t11 = fma((T)2, G[1][1], d23);
+    t22 = fma((T)2, G[2][2], d23);
+    t01 = G[0][1] + G[1][0];
+    t02 = G[0][2] + G[2][0];
+    t12 = G[1][2] + G[2][1];
+    // the temperature slot holds kappa T: G[3] is the heat-flux gradient
+    b0 = fma(u, t00, fma(v, t01, fma(w, t02, G[3][0])));
+    b1 = fma(u, t01, fma(v, t11, fma(w, t12, G[3][1])));
+    b2 = fma(u, t02, fma(v, t12, fma(w, t22, G[3][2])));
+    iv *= (T)(r == 2 ? d.c2[0] : d.c1[0]) * (T)M[6 * pl];
+    if (ph.visc_law == 1) iv *= visc_mu<T>(ph, W[5 * P + q]);
   }
-  const T ire = (T)ph.ire;
 #pragma unroll
   for (int a = 0; a < ND; ++a) {
     if (nout == 1) {
       if ((a == 0 && !ox) || (a == 1 && !oy) || (a == 2 && !oz)) continue;
     }
-    const T Uc = m[a][0] * vel[0] + m[a][1] * vel[1] + m[a][2] * vel[2];
-    const T mflux = rho * Uc;
     T f[5];
-    f[0] = -mflux;
-    f[1] = -(mflux * u + m[a][0] * p);
-    f[2] = -(mflux * v + m[a][1] * p);
-    f[3] = -(mflux * w + m[a][2] * p);
-    f[4] = std::is_same<T, float>::value ? -(et * Uc + (T)ph.H_ref * Uc) : -(et * Uc);
-    if (g.viscous) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) f[1 + c] += ire * (m[a][0] * tau[0][c] + m[a][1] * tau[1][c] + m[a][2] * tau[2][c]);
-      f[4] += ire * (m[a][0] * bq[0] + m[a][1] * bq[1] + m[a][2] * bq[2]);
+    if (a < 2) {
+      const T m0 = a == 0 ? a00 : a10, m1 = a == 0 ? a01 : a11;
+      const T Uc = fma(m1, v, m0 * u);
+      const T nm = -rho * Uc;
+      f[0] = nm;
+      f[1] = fma(nm, u, -(m0 * p));
+      f[2] = fma(nm, v, -(m1 * p));
+      f[3] = nm * w;
+      f[4] = std::is_same<T, float>::value ? -(et * Uc + (T)ph.H_ref * Uc) : -et * Uc;
+      if (g.viscous) {
+        f[1] = fma(iv, fma(m1, t01, m0 * t00), f[1]);
+        f[2] = fma(iv, fma(m1, t11, m0 * t01), f[2]);
+        f[3] = fma(iv, fma(m1, t12, m0 * t02), f[3]);
+        f[4] = fma(iv, fma(m1, b1, m0 * b0), f[4]);
+      }
+    } else {
+      const T Uc = a22 * w;
+      const T nm = -rho * Uc;
+      f[0] = nm;
+      f[1] = nm * u;
+      f[2] = nm * v;
+      f[3] = fma(nm, w, -(a22 * p));
+      f[4] = std::is_same<T, float>::value ? -(et * Uc + (T)ph.H_ref * Uc) : -et * Uc;
+      if (g.viscous) {
+        const T iz = iv * a22;
+        f[1] = fma(iz, t02, f[1]);
+        f[2] = fma(iz, t12, f[2]);
+        f[3] = fma(iz, t22, f[3]);
+        f[4] = fma(iz, b2, f[4]);
+      }
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) out[(long long)(a * 5 + c) * P + q] = f[c];
@@ -420,9 +457,11 @@ __device__ __forceinline__ bool flux_point(const SubDev& d, int r, int t, int& c
   return false;
 }
 
-template <typename T, int ND>
+// CURV: the context has curvilinear blocks (their flux points take flux_curvilinear), so the
+// Cartesian instantiation keeps a register allocation of its own.
+template <typename T, int ND, bool CURV>
 __global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubDev* __restrict__ subs,
-                                              const T* __restrict__ Wp, T* __restrict__ Phi) {
+                                                            const T* __restrict__ Wp, T* __restrict__ Phi) {
   pdl_enter();
   const int sid = blockIdx.y;
   const SubDev d = subs[sid];
@@ -437,7 +476,7 @@ __global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubD
   const long long q = (long long)(ci + g.G) + sty * (cj + g.G) + stz * (ck + g.Gz);
   const long long P = g.Ptot;
   const T* W = Wp + d.pbase;
-  if (d.mbase >= 0) {
+  if (CURV && d.mbase >= 0) {
     flux_curvilinear<T, ND>(g, ph, d, W, Phi + d.pbase, q, ci, cj, ck, ox, oy, oz, nout);
     return;
   }
@@ -445,59 +484,101 @@ __global__ void __launch_bounds__(512) k_flux(Geometry g, Physics ph, const SubD
   const T et = W[6 * P + q];
   const T vel[3] = {u, v, w};
   // gradients du[i][j] = d u_i / d x_j, dT[j].  A strip point beyond the faces of axis a needs the
-  // flux along a only: du[a][*], du[*][a], du[b][b] (the divergence) and dT[a].
+  // flux along a only: du[a][*], du[*][a], du[b][b] (the divergence) and dT[a].  With the same
+  // spacing on every axis they are taken in units of the common factor gs (CD4: a = 4/3, b = -1/3
+  // make c1 = -8 c2, so d = c2 ((f_{+2} - f_{-2}) - 8 (f_{+1} - f_{-1})); CD2: d = c1 (f_{+1} -
+  // f_{-1})): the viscous flux is linear in them, so gs joins 1/Re (and mu) in one factor.
   T du[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   T dT[3] = {0, 0, 0};
-  T mu = (T)1;
+  T iv = (T)ph.ivT;  // the factor of the viscous terms: 1/Re x gs x mu
   const int as = kind - 1;  // strip axis (-1: owned point)
   if (g.viscous) {
     const long long st[3] = {1, sty, stz};
+    // (compared as bit patterns: an FP64 compare would occupy the FP64 pipe)
+    bool iso = true;
 #pragma unroll
-    for (int b = 0; b < ND; ++b) {
-      const T c1 = (T)d.c1[b], c2 = (T)d.c2[b];
-      const bool all = as < 0 || as == b;
-      if (all || as == 0 || b == 0) du[0][b] = cdiff(W + P, q, st[b], c1, c2, r);
-      if (all || as == 1 || b == 1) du[1][b] = cdiff(W + 2 * P, q, st[b], c1, c2, r);
-      if (all || as == 2 || b == 2) du[2][b] = cdiff(W + 3 * P, q, st[b], c1, c2, r);
-      if (all) dT[b] = cdiff(W + 5 * P, q, st[b], c1, c2, r);
+    for (int b = 1; b < ND; ++b)
+      iso = iso && __double_as_longlong(d.c1[b]) == __double_as_longlong(d.c1[0]) &&
+            __double_as_longlong(d.c2[b]) == __double_as_longlong(d.c2[0]);
+    if (iso) {
+#pragma unroll
+      for (int b = 0; b < ND; ++b) {
+        const bool all = as < 0 || as == b;
+        if (all || as == 0 || b == 0) du[0][b] = cdiff_iso(W + P, q, st[b], r);
+        if (all || as == 1 || b == 1) du[1][b] = cdiff_iso(W + 2 * P, q, st[b], r);
+        if (all || as == 2 || b == 2) du[2][b] = cdiff_iso(W + 3 * P, q, st[b], r);
+        if (all) dT[b] = cdiff_iso(W + 5 * P, q, st[b], r);
+      }
+      iv *= (T)(r == 2 ? d.c2[0] : d.c1[0]);
+    } else {
+#pragma unroll
+      for (int b = 0; b < ND; ++b) {
+        const T c1 = (T)d.c1[b], c2 = (T)d.c2[b];
+        const bool all = as < 0 || as == b;
+        if (all || as == 0 || b == 0) du[0][b] = cdiff(W + P, q, st[b], c1, c2, r);
+        if (all || as == 1 || b == 1) du[1][b] = cdiff(W + 2 * P, q, st[b], c1, c2, r);
+        if (all || as == 2 || b == 2) du[2][b] = cdiff(W + 3 * P, q, st[b], c1, c2, r);
+        if (all) dT[b] = cdiff(W + 5 * P, q, st[b], c1, c2, r);
+      }
     }
-    if (ph.visc_law == 1) mu = visc_mu<T>(ph, W[5 * P + q]);
+    if (ph.visc_law == 1) iv *= visc_mu<T>(ph, W[5 * P + q]);
   }
-  const T div = du[0][0] + du[1][1] + du[2][2];
-  const T ire = (T)ph.ire, kap = (T)ph.kappa;
+  // tau_ai = mu (du_a/dx_i + du_i/dx_a - 2/3 div delta_ai), q_a = u_i tau_ai + kappa mu dT/dx_a:
+  // mu is in iv; the symmetric sums are shared by the axes
+  const T d23 = (T)(-2.0 / 3.0) * (du[0][0] + du[1][1] + du[2][2]);
+  const T s01 = du[0][1] + du[1][0], s02 = du[0][2] + du[2][0], s12 = du[1][2] + du[2][1];
   T* out = Phi + d.pbase;
+  constexpr bool F32 = std::is_same<T, float>::value;
+  if (nout == 0) {
+    // owned point, every axis: the momentum flux -rho u_a u_c - p delta_ac + tau_ac / Re is
+    // symmetric in (a, c), so its six distinct entries are formed once
+    const T n0 = -rho * u, n1 = -rho * v, n2 = -rho * w;  // -rho u_a
+    T m00 = fma(n0, u, -p), m11 = fma(n1, v, -p), m22 = fma(n2, w, -p);
+    T m01 = n0 * v, m02 = n0 * w, m12 = n1 * w;
+    T e0 = F32 ? -(et * u + (T)ph.H_ref * u) : -et * u;
+    T e1 = F32 ? -(et * v + (T)ph.H_ref * v) : -et * v;
+    T e2 = F32 ? -(et * w + (T)ph.H_ref * w) : -et * w;
+    if (g.viscous) {
+      const T t00 = fma((T)2, du[0][0], d23), t11 = fma((T)2, du[1][1], d23), t22 = fma((T)2, du[2][2], d23);
+      m00 = fma(iv, t00, m00);
+      m11 = fma(iv, t11, m11);
+      m22 = fma(iv, t22, m22);
+      m01 = fma(iv, s01, m01);
+      m02 = fma(iv, s02, m02);
+      m12 = fma(iv, s12, m12);
+      e0 = fma(iv, fma(u, t00, fma(v, s01, fma(w, s02, dT[0]))), e0);
+      e1 = fma(iv, fma(u, s01, fma(v, t11, fma(w, s12, dT[1]))), e1);
+      e2 = fma(iv, fma(u, s02, fma(v, s12, fma(w, t22, dT[2]))), e2);
+    }
+    const T f[3][5] = {{n0, m00, m01, m02, e0}, {n1, m01, m11, m12, e1}, {n2, m02, m12, m22, e2}};
+#pragma unroll
+    for (int a = 0; a < ND; ++a)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) out[(long long)(a * 5 + c) * P + q] = f[a][c];
+    return;
+  }
+  // strip point: the flux along its axis only
 #pragma unroll
   for (int a = 0; a < ND; ++a) {
-    if (nout == 1) {
-      if ((a == 0 && !ox) || (a == 1 && !oy) || (a == 2 && !oz)) continue;
-    }
+    if ((a == 0 && !ox) || (a == 1 && !oy) || (a == 2 && !oz)) continue;
     const T ua = vel[a];
-    const T mflux = rho * ua;
+    const T nm = -rho * ua;  // -rho u_a
     T f[5];
-    f[0] = -mflux;
-    f[1] = -(mflux * u + (a == 0 ? p : (T)0));
-    f[2] = -(mflux * v + (a == 1 ? p : (T)0));
-    f[3] = -(mflux * w + (a == 2 ? p : (T)0));
-    f[4] = std::is_same<T, float>::value ? -(et * ua + (T)ph.H_ref * ua) : -(et * ua);
+    f[0] = nm;
+    f[1] = a == 0 ? fma(nm, u, -p) : nm * u;
+    f[2] = a == 1 ? fma(nm, v, -p) : nm * v;
+    f[3] = a == 2 ? fma(nm, w, -p) : nm * w;
+    f[4] = F32 ? -(et * ua + (T)ph.H_ref * ua) : -et * ua;
     if (g.viscous) {
-      // tau_ai = mu (du_a/dx_i + du_i/dx_a) - 2/3 mu div delta_ai,  q_a = u_i tau_ai + kappa mu dT/dx_a
       T tau[3];
-      T qa;
-      if (ph.visc_law == 0) {  // mu = 1: the products with mu are exact and skipped
-#pragma unroll
-        for (int i2 = 0; i2 < 3; ++i2) tau[i2] = du[a][i2] + du[i2][a];
-        tau[a] = fma((T)(-2.0 / 3.0), div, tau[a]);
-        qa = fma(u, tau[0], fma(v, tau[1], fma(w, tau[2], kap * dT[a])));
-      } else {
-#pragma unroll
-        for (int i2 = 0; i2 < 3; ++i2) tau[i2] = mu * (du[a][i2] + du[i2][a]);
-        tau[a] -= (T)(2.0 / 3.0) * mu * div;
-        qa = u * tau[0] + v * tau[1] + w * tau[2] + kap * mu * dT[a];
-      }
-      f[1] = fma(ire, tau[0], f[1]);
-      f[2] = fma(ire, tau[1], f[2]);
-      f[3] = fma(ire, tau[2], f[3]);
-      f[4] = fma(ire, qa, f[4]);
+      tau[0] = a == 0 ? fma((T)2, du[0][0], d23) : (a == 1 ? s01 : s02);
+      tau[1] = a == 1 ? fma((T)2, du[1][1], d23) : (a == 0 ? s01 : s12);
+      tau[2] = a == 2 ? fma((T)2, du[2][2], d23) : (a == 0 ? s02 : s12);
+      const T qa = fma(u, tau[0], fma(v, tau[1], fma(w, tau[2], dT[a])));
+      f[1] = fma(iv, tau[0], f[1]);
+      f[2] = fma(iv, tau[1], f[2]);
+      f[3] = fma(iv, tau[2], f[3]);
+      f[4] = fma(iv, qa, f[4]);
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) out[(long long)(a * 5 + c) * P + q] = f[c];
@@ -530,13 +611,18 @@ __global__ void __launch_bounds__(512) k_rk(Geometry g, Physics ph, StepSched sc
   const long long st[3] = {1, sty, stz};
   const bool wallpt = d.wall && ((((d.wall >> 0) & 1) && ci == 0) || (((d.wall >> 1) & 1) && ci == d.sx - 1) ||
                                  (((d.wall >> 2) & 1) && cj == 0) || (((d.wall >> 3) & 1) && cj == d.sy - 1));
-  // dt R = sum_a (dt c1_a)(Phi_{+1} - Phi_{-1}) + (dt c2_a)(Phi_{+2} - Phi_{-2}) as one FMA chain
+  // R = sum_a c1_a (Phi_{+1} - Phi_{-1}) + c2_a (Phi_{+2} - Phi_{-2}) as one FMA chain, times dt
+  // (and J on a curvilinear block) once, for all five components before the first store (the
+  // output may be a ring level the compiler cannot tell apart from Phi, so loads after a store
+  // would wait for it)
   T k1[3], k2[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    k1[a] = (T)(dt * d.c1[a]);
-    k2[a] = (T)(dt * d.c2[a]);
+    k1[a] = (T)d.c1[a];
+    k2[a] = (T)d.c2[a];
   }
+  const double sdt = (d.mbase >= 0) ? dt * g.metric[d.mbase + 6 * d.mpl + (d.ox + ci + g.G) + (long long)d.mx * (d.oy + cj + g.G)] : dt;
+  double dtR[5], qv[5], uv[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
     const T* Fx = F + (long long)c * P;
@@ -548,11 +634,17 @@ __global__ void __launch_bounds__(512) k_rk(Geometry g, Physics ph, StepSched sc
       acc = fma(k1[a], Fa[q + st[a]] - Fa[q - st[a]], acc);
       if (g.r == 2) acc = fma(k2[a], Fa[q + 2 * st[a]] - Fa[q - 2 * st[a]], acc);
     }
-    const double dtR =
-        (d.mbase >= 0) ? (double)acc * g.metric[d.mbase + 6 * d.mpl + (d.ox + ci + g.G) + (long long)d.mx * (d.oy + cj + g.G)]
-                       : (double)acc;
-    double qn = first ? dtR : fma(A, Q[c * d.bN + gi], dtR);
-    double un = fma(B, qn, Uin[c * d.bN + gi]);
+    dtR[c] = (double)acc * sdt;
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    qv[c] = first ? 0.0 : Q[c * d.bN + gi];
+    uv[c] = Uin[c * d.bN + gi];
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    double qn = first ? dtR[c] : fma(A, qv[c], dtR[c]);
+    double un = fma(B, qn, uv[c]);
     if (wallpt && c >= 1 && c <= 3) qn = un = 0.0;  // no-slip wall points keep zero momentum
     if (!last) Q[c * d.bN + gi] = qn;
     Uout[c * d.bN + gi] = un;
@@ -674,12 +766,12 @@ static int stage_impl(const Geometry& g, const Physics& ph, const StepSched& sc,
     const long long nl = 5LL * a.Lmax * a.Lmax;
     const dim3 gl(nblk(nl, 128), g.nsub);
     if (g.ndim == 3) {
-      TIMED(tm, 1, (k_flux<T, 3><<<gf, B, 0, st>>>(g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
+      TIMED(tm, 1, ((g.metric ? k_flux<T, 3, true> : k_flux<T, 3, false>)<<<gf, B, 0, st>>>(g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
       TIMED(tm, 2, (k_compact_div<T, 0><<<gl, 128, 0, st>>>(g, a.subs, (const T*)a.Phi, a.R, a.cthomas, a.Lmax)));
       TIMED(tm, 2, (k_compact_div<T, 1><<<gl, 128, 0, st>>>(g, a.subs, (const T*)a.Phi, a.R, a.cthomas, a.Lmax)));
       TIMED(tm, 2, (k_compact_div<T, 2><<<gl, 128, 0, st>>>(g, a.subs, (const T*)a.Phi, a.R, a.cthomas, a.Lmax)));
     } else {
-      TIMED(tm, 1, (k_flux<T, 2><<<gf, B, 0, st>>>(g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
+      TIMED(tm, 1, ((g.metric ? k_flux<T, 2, true> : k_flux<T, 2, false>)<<<gf, B, 0, st>>>(g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
       TIMED(tm, 2, (k_compact_div<T, 0><<<gl, 128, 0, st>>>(g, a.subs, (const T*)a.Phi, a.R, a.cthomas, a.Lmax)));
       TIMED(tm, 2, (k_compact_div<T, 1><<<gl, 128, 0, st>>>(g, a.subs, (const T*)a.Phi, a.R, a.cthomas, a.Lmax)));
     }
@@ -689,11 +781,11 @@ static int stage_impl(const Geometry& g, const Physics& ph, const StepSched& sc,
     return (int)cudaGetLastError();
   }
   if (g.ndim == 3) {
-    TIMED(tm, 1, (launch_pdl(k_flux<T, 3>, gf, dim3(B), 0, st, g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
+    TIMED(tm, 1, (launch_pdl(g.metric ? k_flux<T, 3, true> : k_flux<T, 3, false>, gf, dim3(B), 0, st, g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
     TIMED(tm, 2, (launch_pdl(k_rk<T, 3>, gr, dim3(B), 0, st, g, ph, sc, a.subs, (const T*)a.Phi, a.Uin, a.Uout, a.ring,
                              a.in_ring, a.out_ring, a.Q, a.A, a.B, a.dt, a.first, a.last)));
   } else {
-    TIMED(tm, 1, (launch_pdl(k_flux<T, 2>, gf, dim3(B), 0, st, g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
+    TIMED(tm, 1, (launch_pdl(g.metric ? k_flux<T, 2, true> : k_flux<T, 2, false>, gf, dim3(B), 0, st, g, ph, a.subs, (const T*)a.Wp, (T*)a.Phi)));
     TIMED(tm, 2, (launch_pdl(k_rk<T, 2>, gr, dim3(B), 0, st, g, ph, sc, a.subs, (const T*)a.Phi, a.Uin, a.Uout, a.ring,
                              a.in_ring, a.out_ring, a.Q, a.A, a.B, a.dt, a.first, a.last)));
   }

@@ -12,6 +12,7 @@
 #include <mutex>
 
 #include "cfs.h"
+#include "device_common.cuh"
 
 namespace {
 
@@ -37,9 +38,14 @@ __device__ __forceinline__ int wrap(int i, int n) {
   return r < 0 ? r + n : r;
 }
 
-__device__ __forceinline__ double vel(const double* U, const Grid& g, int x, int y, int z, int c) {
+// Two velocity components (c0, c1) of the point (x, y, z), periodic wrap: one reciprocal of the
+// density (Newton-refined) per stencil point instead of a division per component.
+__device__ __forceinline__ void vel2(const double* U, const Grid& g, int x, int y, int z, int c0, int c1, double* a,
+                                     double* b) {
   const long long i = (long long)wrap(x, g.nx) + (long long)g.nx * ((long long)wrap(y, g.ny) + (long long)g.ny * wrap(z, g.nz));
-  return U[(1 + c) * g.N + i] / U[i];
+  const double ir = cfs::recip(U[i]);
+  *a = U[(1 + c0) * g.N + i] * ir;
+  *b = U[(1 + c1) * g.N + i] * ir;
 }
 
 // One point per thread; block b writes its 8 partial sums to partials[8 b .. 8 b + 7].
@@ -55,18 +61,28 @@ __global__ void __launch_bounds__(kThreads) k_diag_blocks(Grid g, const double* 
       if (!isfinite(u[v])) acc[7] = 1.0;
       acc[2 + v] = u[v] * g.dV;
     }
-    const double rho = u[0], vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
+    const double rho = u[0], ir = cfs::recip(rho), vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
     acc[0] = 0.5 * rho * (vx * vx + vy * vy + vz * vz);
-    double dv[3][3];
-    for (int c = 0; c < 3; ++c)
-      for (int a = 0; a < 3; ++a) {
-        if (a >= g.ndim) { dv[c][a] = 0.0; continue; }
-        const int ex = a == 0, ey = a == 1, ez = a == 2;
-        double d = g.c1[a] * (vel(U, g, x + ex, y + ey, z + ez, c) - vel(U, g, x - ex, y - ey, z - ez, c));
-        if (g.r == 2)
-          d += g.c2[a] * (vel(U, g, x + 2 * ex, y + 2 * ey, z + 2 * ez, c) - vel(U, g, x - 2 * ex, y - 2 * ey, z - 2 * ez, c));
-        dv[c][a] = d;
+    // the vorticity needs d v_c / d x_a for c != a only: along axis a, the two other components
+    double dv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= g.ndim) break;
+      const int c0 = a == 0 ? 1 : 0, c1 = a == 2 ? 1 : 2;
+      const int ex = a == 0, ey = a == 1, ez = a == 2;
+      double p0, p1, m0, m1;
+      vel2(U, g, x + ex, y + ey, z + ez, c0, c1, &p0, &p1);
+      vel2(U, g, x - ex, y - ey, z - ez, c0, c1, &m0, &m1);
+      double d0 = g.c1[a] * (p0 - m0), d1 = g.c1[a] * (p1 - m1);
+      if (g.r == 2) {
+        vel2(U, g, x + 2 * ex, y + 2 * ey, z + 2 * ez, c0, c1, &p0, &p1);
+        vel2(U, g, x - 2 * ex, y - 2 * ey, z - 2 * ez, c0, c1, &m0, &m1);
+        d0 += g.c2[a] * (p0 - m0);
+        d1 += g.c2[a] * (p1 - m1);
       }
+      dv[c0][a] = d0;
+      dv[c1][a] = d1;
+    }
     const double wx = dv[2][1] - dv[1][2], wy = dv[0][2] - dv[2][0], wz = dv[1][0] - dv[0][1];
     acc[1] = 0.5 * rho * (wx * wx + wy * wy + wz * wz);
   }

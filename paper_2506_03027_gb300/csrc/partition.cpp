@@ -6,9 +6,12 @@
 // range of sub-domains and keeps state arrays of the whole grid; the points of other processes'
 // sub-domains that its own sub-domains read -- the halo of the difference stencils (faces to the
 // halo depth, viscous edges to r x r) and of the filter lines (faces to depth 5) -- arrive through
-// the exchange, everything else of a foreign sub-domain is never read.  Both sides derive the
-// lists from the same decomposition in the same order, so a list can be sent as a plain array of
-// values with no indices.
+// the exchange, everything else of a foreign sub-domain is never read.  On a connected grid a
+// point beyond a non-periodic block face is read through its gather entry (an interface
+// neighbour's points, interpolated spanwise; the mirror point of a wall; the face point of an
+// outflow), so the sources of those entries join the lists.  Both sides derive the lists from the
+// same decomposition in the same order, so a list can be sent as a plain array of values with no
+// indices.
 #include <algorithm>
 #include <vector>
 
@@ -58,7 +61,7 @@ const char* strip_plan(const TopoBlock* B, int nb, int nsub, const int* starts, 
   std::vector<std::vector<int>> send_n(nranks), recv_n(nranks);
   for (int b = 0; b < nb; ++b) {
     const TopoBlock& T = B[b];
-    if (!topo_periodic(T)) return "a partitioned context needs blocks periodic on every face";
+    const bool per = topo_periodic(T);
     const int n3[3] = {T.n[0], T.n[1], T.n[2]};
     for (int iz = 0; iz < T.P[2]; ++iz)
       for (int iy = 0; iy < T.P[1]; ++iy)
@@ -84,22 +87,37 @@ const char* strip_plan(const TopoBlock* B, int nb, int nsub, const int* starts, 
                 }
                 if (nout == 0 || nout == 3) continue;
                 if (nout == 2 && (!viscous || far)) continue;
+                auto add = [&](long long off, int bN, int q) {
+                  if (q == p) return;
+                  if (p == rank) {
+                    recv[q].push_back(off);
+                    recv_n[q].push_back(bN);
+                  } else if (q == rank) {
+                    send[p].push_back(off);
+                    send_n[p].push_back(bN);
+                  }
+                };
+                bool beyond = false;  // beyond a non-periodic face of the block
+                for (int a = 0; a < 3; ++a) {
+                  const int x = o[a] + c[a];
+                  if ((x < 0 && T.face[2 * a].type != FACE_PERIODIC) || (x >= n3[a] && T.face[2 * a + 1].type != FACE_PERIODIC))
+                    beyond = true;
+                }
+                if (!per && beyond) {
+                  GatherEntry e;
+                  if (!gather_entry(B, nb, b, o[0] + c[0], o[1] + c[1], o[2] + c[2], &e))
+                    return "a point beyond a block face does not resolve";
+                  for (int t = 0; t < e.nt; ++t) add(e.off[t], e.bN[t], rank_of[e.sid[t]]);
+                  continue;
+                }
                 int gc[3], oc[3];
                 for (int a = 0; a < 3; ++a) {
                   gc[a] = wrap(o[a] + c[a], n3[a]);
                   oc[a] = owner[(size_t)b * 3 + a][gc[a]];
                 }
                 const int src = T.sid0 + oc[0] + T.P[0] * (oc[1] + T.P[1] * oc[2]);
-                const int q = rank_of[src];
-                if (q == p) continue;
                 const long long off = T.base + (long long)gc[0] + (long long)n3[0] * ((long long)gc[1] + (long long)n3[1] * gc[2]);
-                if (p == rank) {
-                  recv[q].push_back(off);
-                  recv_n[q].push_back((int)T.N);
-                } else if (q == rank) {
-                  send[p].push_back(off);
-                  send_n[p].push_back((int)T.N);
-                }
+                add(off, (int)T.N, rank_of[src]);
               }
         }
   }

@@ -110,6 +110,91 @@ def test_plan_matches_brute_force_read_sets(name, nranks):
     assert any(len(plans[0, q, 1]) for q in range(1, nranks))
 
 
+def cgrid_read_sets(mb, ctx):
+    """Read sets of every sub-domain of a connected grid, in sub-domain order: as read_set, with
+    every point beyond a non-periodic block face replaced by the sources of its gather entry
+    (cfs_halo_sources: interface neighbours, wall mirror points, outflow face points; a far field
+    has none) -- as state offsets (5 x the points of the blocks before, plus the point index)."""
+    c0 = mb.case
+    r = 2 if c0.order == 4 else 1
+    G = 2 * r if c0.viscous else r
+    D = max(G, 5) if c0.filter else G
+    base = 5 * np.concatenate([[0], np.cumsum([b.nx * b.ny * b.nz for b in mb.blocks])])
+    sets = []
+    for bi, b in enumerate(mb.blocks):
+        n = (b.nx, b.ny, b.nz)
+        per = [(mb.faces[bi][2 * a].type == "periodic", mb.faces[bi][2 * a + 1].type == "periodic") for a in range(3)]
+        dep = (D, D, D if b.nz > 1 else 0)
+        for iz in range(b.pz):
+            for iy in range(b.py):
+                for ix in range(b.px):
+                    o, s = zip(split(b.nx, b.px, ix), split(b.ny, b.py, iy), split(b.nz, b.pz, iz))
+                    out = set()
+                    for k in range(-dep[2], s[2] + dep[2]):
+                        for j in range(-dep[1], s[1] + dep[1]):
+                            for i in range(-dep[0], s[0] + dep[0]):
+                                c = (i, j, k)
+                                d = [(-c[a] if c[a] < 0 else (c[a] - s[a] + 1 if c[a] >= s[a] else 0)) for a in range(3)]
+                                nout = sum(x > 0 for x in d)
+                                if nout == 0 or nout == 3:
+                                    continue
+                                if nout == 2 and not (c0.viscous and max(d) <= r):
+                                    continue
+                                g = [o[a] + c[a] for a in range(3)]
+                                if any((g[a] < 0 and not per[a][0]) or (g[a] >= n[a] and not per[a][1]) for a in range(3)):
+                                    for sb, si, sj, sk, _, _, _ in cfs.cfs_halo_sources(ctx, bi, *g)[1]:
+                                        B2 = mb.blocks[sb]
+                                        out.add(int(base[sb]) + si + B2.nx * (sj + B2.ny * sk))
+                                else:
+                                    g = [g[a] % n[a] for a in range(3)]
+                                    out.add(int(base[bi]) + g[0] + n[0] * (g[1] + n[1] * g[2]))
+                    sets.append(out)
+    return sets
+
+
+@pytest.mark.parametrize("nranks", [2, 3])
+def test_plan_on_a_connected_grid(nranks):
+    """The 12-block C-grid (reduced size: interfaces with reversed and non-matching spanwise
+    neighbours, walls, far field, outflows): the plan equals the brute-force read sets with the
+    gather sources of the points beyond the block faces, and both sides of a pair agree."""
+    mb = I.naca_cgrid(I.cgrid_reduced())
+    nsub = sum(b.px * b.py * b.pz for b in mb.blocks)
+    starts = [round(q * nsub / nranks) for q in range(nranks + 1)]
+    # sub-domain of every state offset of variable 0 (a block's points follow its 5 x points base)
+    own = np.full(5 * sum(b.nx * b.ny * b.nz for b in mb.blocks), -1, dtype=np.int64)
+    base, sid0 = 0, 0
+    for b in mb.blocks:
+        npb = b.nx * b.ny * b.nz
+        own[base:base + npb] = owner_of(b) + sid0
+        base += 5 * npb
+        sid0 += b.px * b.py * b.pz
+    rank_of = np.searchsorted(np.array(starts[1:]), np.arange(nsub), side="right")
+    plans = {}
+    reads = None
+    for p in range(nranks):
+        ctx = cfs.cfs_create(cfs.params_from_case(mb.case), None)
+        try:
+            cfs.describe_blocks(ctx, mb.blocks, mb)
+            cfs.cfs_set_partition(ctx, nranks, starts, p)
+            if reads is None:
+                reads = cgrid_read_sets(mb, ctx)
+            for q in range(nranks):
+                plans[p, q, 0] = cfs.cfs_exchange_plan(ctx, q, 0)
+                plans[p, q, 1] = cfs.cfs_exchange_plan(ctx, q, 1)
+        finally:
+            cfs.cfs_destroy(ctx)
+    assert len(reads) == nsub
+    crossing = 0
+    for p in range(nranks):
+        mine = set().union(*[reads[s] for s in range(nsub) if rank_of[s] == p])
+        for q in range(nranks):
+            expect = sorted(x for x in mine if rank_of[own[x]] == q) if q != p else []
+            assert list(plans[p, q, 1]) == expect, (p, q)
+            np.testing.assert_array_equal(plans[p, q, 0], plans[q, p, 1])
+            crossing += len(expect)
+    assert crossing > 0
+
+
 def test_plan_rejects_bad_partitions():
     case = CASES["ns_filter_3d"]
     ctx = cfs.cfs_create(cfs.params_from_case(case), None)

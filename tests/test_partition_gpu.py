@@ -27,6 +27,32 @@ class _DevArray:
                                          "version": 2}
 
 
+def _transport(rank, dist, torch):
+    """The exchange callback: device -> host -> gloo send/recv with every peer -> host -> device."""
+
+    def transport(nranks, send, scnt, recv, rcnt, stream):
+        torch.cuda.synchronize()                   # the packed strips are ready
+        soff = np.concatenate([[0], np.cumsum(scnt)])
+        roff = np.concatenate([[0], np.cumsum(rcnt)])
+        sdev = torch.as_tensor(_DevArray(send, max(soff[-1], 1)), device="cuda")
+        rdev = torch.as_tensor(_DevArray(recv, max(roff[-1], 1)), device="cuda")
+        for q in range(nranks):
+            if q == rank:
+                continue
+            sb = sdev[soff[q]:soff[q + 1]].cpu()
+            rb = torch.empty(int(rcnt[q]), dtype=torch.float64)
+            if rank < q:
+                dist.send(sb, q)
+                dist.recv(rb, q)
+            else:
+                dist.recv(rb, q)
+                dist.send(sb, q)
+            rdev[roff[q]:roff[q + 1]].copy_(rb)   # on the context's stream, before the unpack
+        torch.cuda.synchronize()
+
+    return transport
+
+
 def _case(name):
     from paper_2506_03027_gb300 import inputs as I
     algo, kmax, cfl = {"SA": ("SA", 0, 0.25), "CAA": ("CAA", 0, 0.25), "SAA": ("SAA", 3, 0.1)}[name]
@@ -53,25 +79,7 @@ def _rank(rank, world, port, name, starts, nsteps, out):
         d = I.saa_delays(case, nsteps) if case.algo == "SAA" else None
         U0 = I.tgv_state(case)
 
-        def transport(nranks, send, scnt, recv, rcnt, stream):
-            torch.cuda.synchronize()                   # the packed strips are ready
-            soff = np.concatenate([[0], np.cumsum(scnt)])
-            roff = np.concatenate([[0], np.cumsum(rcnt)])
-            sdev = torch.as_tensor(_DevArray(send, max(soff[-1], 1)), device="cuda")
-            rdev = torch.as_tensor(_DevArray(recv, max(roff[-1], 1)), device="cuda")
-            for q in range(nranks):
-                if q == rank:
-                    continue
-                sb = sdev[soff[q]:soff[q + 1]].cpu()
-                rb = torch.empty(int(rcnt[q]), dtype=torch.float64)
-                if rank < q:
-                    dist.send(sb, q)
-                    dist.recv(rb, q)
-                else:
-                    dist.recv(rb, q)
-                    dist.send(sb, q)
-                rdev[roff[q]:roff[q + 1]].copy_(rb)   # on the context's stream, before the unpack
-            torch.cuda.synchronize()
+        transport = _transport(rank, dist, torch)
 
         part = cfs.Solver(case, partition=(world, starts, rank), exchange=transport)
         part.set_schedule(delays=d)
@@ -145,3 +153,98 @@ def test_two_processes_match_one_context_bit_for_bit(name, starts):
     scale = np.abs(df[2:7]).max()
     np.testing.assert_allclose(dp0[2:7] + dp1[2:7], df[2:7], rtol=1e-12, atol=1e-12 * scale)  # totals
     assert dp0[7] == dp1[7] == df[7] == 0.0
+
+
+def _rank_cgrid(rank, world, port, algo, starts, nsteps, out):
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import torch
+    import torch.distributed as dist
+    from paper_2506_03027_gb300 import build as B
+    from paper_2506_03027_gb300 import cfs
+    from paper_2506_03027_gb300 import inputs as I
+    B.build()
+    torch.cuda.set_device(0)
+    import datetime
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=180))
+    try:
+        sp = I.cgrid_reduced()
+        mb = I.naca_cgrid(sp, algo=algo, kmax=2)
+        mb = mb.replace_all(dt=I.cgrid_dt(mb, 0.2))
+        d = I.saa_delays(mb.case.replace(px=mb.nsub, py=1, pz=1), nsteps) if algo == "SAA" else None
+        U0 = I.cgrid_state(mb, sp)
+        part = cfs.Solver(mb, partition=(world, starts, rank), exchange=_transport(rank, dist, torch))
+        part.set_schedule(delays=d)
+        part.set_states(U0)
+        part.step(nsteps)
+        Up = part.get_states()
+        xc = cfs.cfs_exchange_count(part.ctx)
+        part.close()
+        full = cfs.Solver(mb)
+        full.set_schedule(delays=d)
+        full.set_states(U0)
+        full.step(nsteps)
+        Uf = full.get_states()
+        full.close()
+        same, ndiff, npts, sid0 = True, 0, 0, 0
+        for b, up, uf in zip(mb.blocks, Up, Uf):
+            mask = np.zeros((b.nz, b.ny, b.nx), dtype=bool)
+            for sid in range(sid0, sid0 + b.px * b.py * b.pz):
+                if not starts[rank] <= sid < starts[rank + 1]:
+                    continue
+                loc = sid - sid0
+                ix, iy, iz = loc % b.px, (loc // b.px) % b.py, loc // (b.px * b.py)
+                sl = []
+                for n, p, i in ((b.nz, b.pz, iz), (b.ny, b.py, iy), (b.nx, b.px, ix)):
+                    q, rem = divmod(n, p)
+                    o = i * q + min(i, rem)
+                    sl.append(slice(o, o + q + (1 if i < rem else 0)))
+                mask[tuple(sl)] = True
+            sid0 += b.px * b.py * b.pz
+            same = same and bool(np.array_equal(up[:, mask], uf[:, mask]))
+            ndiff += int(np.count_nonzero(up[:, mask] != uf[:, mask]))
+            npts += int(mask.sum())
+        out[rank] = (same, ndiff, npts, xc, bool(all(np.isfinite(u).all() for u in Uf)))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("algo,cut", [("SA", 0.5), ("SAA", 0.3)])
+def test_connected_grid_two_processes_match_one_context(algo, cut):
+    """The 12-block NACA0012 C-grid (reduced size) split between two processes -- interfaces, the
+    wake cut, walls and the spanwise interpolation between the layers all crossing the split --
+    gives every point bit for bit as one context."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_03027_gb300 import build as B
+    from paper_2506_03027_gb300 import inputs as I
+    B.build()
+    nsub = I.naca_cgrid(I.cgrid_reduced()).nsub
+    starts = [0, int(round(cut * nsub)), nsub]
+    import torch.multiprocessing as mp
+    world, nsteps = 2, 10                              # 5 synchronous warm-up steps, then the schedule
+    mctx = mp.get_context("spawn")
+    with mctx.Manager() as mgr:
+        out = mgr.dict()
+        port = _free_port()
+        procs = [mctx.Process(target=_rank_cgrid, args=(r, world, port, algo, starts, nsteps, out)) for r in range(world)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=600)
+        for p in procs:
+            if p.is_alive():
+                p.terminate()
+                p.join(timeout=30)
+        assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+        res = dict(out)
+    mb = I.naca_cgrid(I.cgrid_reduced())
+    assert res[0][2] + res[1][2] == sum(b.nx * b.ny * b.nz for b in mb.blocks)
+    for r in range(world):
+        same, ndiff, _, xc, finite = res[r]
+        assert finite
+        assert same, (r, ndiff)
+        assert xc > 0
