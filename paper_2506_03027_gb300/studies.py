@@ -9,8 +9,11 @@ synchronous run's error against the exact translated vortex is returned beside i
 
 paper_vortex_errors: the paper's own vortex setup (Sec. 5.1, Table 1, Fig. 2(a)) -- convergence
 of the density error over one advection cycle for the six scheme cases, on the GPU.
+paper_delay_study: the study of Fig. 4 at the paper's size -- the asynchrony error of CAA-AT
+(case 3) on the paper's vortex on 2048^2 points against L at P = 1024 PEs and against P at L = 4.
 stability_sweep: the first non-finite step of the Taylor-Green configuration per schedule and CFL.
-Command line: python -m paper_2506_03027_gb300.studies paper-vortex [n ...] | stability [n p nsteps]
+Command line: python -m paper_2506_03027_gb300.studies paper-vortex [n ...] | stability [n p nsteps] |
+delay-study [paper|c1 n t_end cfl]
 """
 from __future__ import annotations
 
@@ -120,6 +123,92 @@ def paper_vortex_errors(ns=(60, 120, 240), runs=PAPER_VORTEX_RUNS, seeds=(1, 2, 
     return {"n": list(ns), "t_end": t_end, "p_late": p_late, "rows": rows}
 
 
+def cubic_fit_full(L, E):
+    """Least-squares fit E ~ g0 + g1 L + g2 L^2 + g3 L^3 (a constant for the error the AT buffer
+    updates add even at zero delay); returns (g0 .. g3) and the relative RMS residual."""
+    L = np.asarray(L, dtype=np.float64)
+    E = np.asarray(E, dtype=np.float64)
+    A = np.stack([np.ones_like(L), L, L ** 2, L ** 3], axis=1)
+    g, *_ = np.linalg.lstsq(A, E, rcond=None)
+    return g, float(np.sqrt(np.mean((A @ g - E) ** 2)) / np.sqrt(np.mean(E ** 2)))
+
+
+def paper_delay_study(n: int = 2048, Ls=(1, 2, 3, 4, 5, 6, 7, 8), Ps=(16, 64, 256, 1024, 4096), P_fixed: int = 1024,
+                      L_fixed: int = 4, t_end: float = 4.0, cfl: float = 0.1, vortex: str = "paper") -> dict:
+    """Fig. 4 of the paper: the u-velocity error the asynchrony adds under CAA-AT with the
+    second-order schemes (LSERK2, CD2, AT2: Table 1 case 3) on an advected vortex with a
+    two-dimensional decomposition into P = p x p PEs, after t_end -- (a) against the maximum
+    allowable delay L at P = P_fixed, (b) against P at L = L_fixed.  vortex "paper": the Gaussian
+    vortex of Sec. 5.1 (beta 0.02, M 0.1, periodic [-8, 8]^2); "c1": the isentropic vortex of
+    strength 5 at M 0.5 on [-5, 5]^2.  The added error of a run is the RMS difference of its
+    u-velocity from the synchronous run (one run: SA with P sub-domains equals the single-domain
+    run to rounding for every P); the synchronous run's error against the exact solution is
+    returned beside it.  The time step is that of CFL `cfl` (the paper's own steps, CFL about 0.04,
+    would take 136 k steps per run at 2048^2); a run that goes non-finite reports NaN and stays
+    out of the fits; CUDA-graph mode."""
+    import torch
+    paper = vortex == "paper"
+    state = I.paper_vortex_state if paper else I.vortex_state
+
+    def case(P, algo, L):
+        p = int(round(math.sqrt(P)))
+        assert p * p == P, P
+        if paper:
+            c = I.paper_vortex_case(n, order=2, algo=algo, at=True, L=L).replace(px=p, py=p)
+        else:
+            c = I.vortex_case(n, p, order=2, algo=algo, at=True, caa_L=L, kmax=max(0, L - 1))
+        dt = I.cfl_dt(c, state(c), cfl)
+        nsteps = int(math.ceil(t_end / dt))
+        return c.replace(dt=t_end / nsteps), nsteps
+
+    def run(c, nsteps):
+        U0 = state(c)
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            s = cfs.Solver(c, max_delay=0 if c.algo == "SA" else c.caa_L - 1, graph=True, stream=st)
+            try:
+                s.set_schedule()
+                s.set_state(U0)
+                s.step(nsteps)
+                return s.get_state()
+            finally:
+                s.close()
+
+    c_sa, nsteps = case(P_fixed, "SA", 8)
+    Usa = run(c_sa, nsteps)
+    exact = state(c_sa, t=t_end)
+    out = {"vortex": vortex, "n": n, "t_end": t_end, "steps": nsteps, "dt": c_sa.dt, "cfl": cfl,
+           "sa_error": float(math.sqrt(np.mean((_u(Usa) - _u(exact)) ** 2))),
+           "P_fixed": P_fixed, "L": [], "error_vs_L": [], "L_fixed": L_fixed, "P": [], "error_vs_P": []}
+
+    def added(P, L):
+        c, ns = case(P, "CAA", L)
+        assert ns == nsteps
+        U = run(c, ns)
+        return float(math.sqrt(np.mean((_u(U) - _u(Usa)) ** 2)))
+
+    for L in Ls:
+        out["L"].append(int(L))
+        out["error_vs_L"].append(added(P_fixed, int(L)))
+    for P in Ps:
+        out["P"].append(int(P))
+        out["error_vs_P"].append(out["error_vs_L"][out["L"].index(L_fixed)] if P == P_fixed and L_fixed in out["L"]
+                                 else added(int(P), L_fixed))
+    okL = [i for i, e in enumerate(out["error_vs_L"]) if math.isfinite(e)]
+    g, res = cubic_fit_full([out["L"][i] for i in okL], [out["error_vs_L"][i] for i in okL])
+    out["cubic_fit_L"] = {"g0_g1_g2_g3": [float(v) for v in g], "relative_rms_residual": res,
+                          "points": len(okL)}
+    okP = [i for i, e in enumerate(out["error_vs_P"]) if math.isfinite(e)]
+    Pv = np.array([out["P"][i] for i in okP], dtype=np.float64)
+    Ev = np.array([out["error_vs_P"][i] for i in okP])
+    A = np.stack([Pv, np.ones_like(Pv)], axis=1)
+    ab, *_ = np.linalg.lstsq(A, Ev, rcond=None)
+    out["linear_fit_P"] = {"slope": float(ab[0]), "intercept": float(ab[1]),
+                           "relative_rms_residual": float(np.sqrt(np.mean((A @ ab - Ev) ** 2)) / np.sqrt(np.mean(Ev ** 2)))}
+    out["loglog_slope_P"] = float(np.polyfit(np.log(Pv), np.log(Ev), 1)[0])
+    return out
+
+
 def stability_sweep(n: int = 128, p: int = 4, algos=("SAA", "CAA", "SA"), cfls=(0.5, 0.25, 0.1, 0.05),
                     nsteps: int = 600, every: int = 25, kmax: int = 3) -> list:
     """Asynchronous stability of the Taylor-Green configuration (Navier-Stokes, filter, n^3 on p^3
@@ -167,8 +256,30 @@ def _main(argv):
         for r in stability_sweep(n, p, nsteps=nsteps):
             print(f"{r['algo']} cfl={r['cfl']} dt={r['dt']:.3e} first_nonfinite_by_step={r['first_nonfinite_by_step']} "
                   f"K_last={r['K_last']}")
+    elif argv and argv[0] == "delay-study":
+        vortex = argv[1] if len(argv) > 1 else "paper"
+        n = int(argv[2]) if len(argv) > 2 else 2048
+        t_end = float(argv[3]) if len(argv) > 3 else 4.0
+        cfl = float(argv[4]) if len(argv) > 4 else 0.1
+        out = paper_delay_study(n, t_end=t_end, cfl=cfl, vortex=vortex)
+        print(json.dumps(out))
+        print(f"{vortex} vortex, n = {n}, t = {t_end}, {out['steps']} steps of dt = {out['dt']:.3e} (CFL {cfl}); "
+              f"SA error against the exact solution {out['sa_error']:.3e}")
+        print(f"(a) P = {out['P_fixed']}:  L  added error")
+        for L, e in zip(out["L"], out["error_vs_L"]):
+            print(f"    {L:2d}  {e:.4e}")
+        cf = out["cubic_fit_L"]
+        print(f"    cubic fit g0 + g1 L + g2 L^2 + g3 L^3 over {cf['points']} finite points: g = "
+              + ", ".join(f"{v:.3e}" for v in cf["g0_g1_g2_g3"]) + f"; relative residual {cf['relative_rms_residual']:.3f}")
+        print(f"(b) L = {out['L_fixed']}:  P  added error")
+        for P, e in zip(out["P"], out["error_vs_P"]):
+            print(f"    {P:5d}  {e:.4e}")
+        lf = out["linear_fit_P"]
+        print(f"    linear fit a P + b: a = {lf['slope']:.4e}, b = {lf['intercept']:.4e}, relative residual "
+              f"{lf['relative_rms_residual']:.3f}; log-log slope {out['loglog_slope_P']:.3f}")
     else:
-        print("usage: python -m paper_2506_03027_gb300.studies paper-vortex [n ...] | stability [n p nsteps]")
+        print("usage: python -m paper_2506_03027_gb300.studies paper-vortex [n ...] | stability [n p nsteps] | "
+              "delay-study [paper|c1 n t_end cfl]")
 
 
 if __name__ == "__main__":

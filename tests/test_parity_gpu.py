@@ -229,6 +229,45 @@ def test_fp32_intermediates_error_is_small(algo):
     assert np.all(e < 1e-6), e
 
 
+@pytest.mark.parametrize("kind", ["ns_cd2", "ns_cd2_power_law", "euler_cd4"])
+def test_fp32_form_multikernel_stage(kind):
+    """FP32 intermediates on the multi-kernel stage (k_view, k_flux, k_rk; the fused stage takes
+    3-D Navier-Stokes with CD4 only): second-order Navier-Stokes with mu = 1 and with the power law
+    mu = T^0.76 (both read kappa T from the primitives' temperature slot), and CD4 Euler."""
+    if kind == "ns_cd2":
+        c = small_tgv("CAA", order=2)
+    elif kind == "ns_cd2_power_law":
+        c = small_tgv("CAA", order=2, visc_law=1, visc_exp=0.76)
+    else:
+        c = small_tgv("CAA", viscous=False)
+    U0 = I.tgv_state(c)
+    Ug, _ = gpu_run(c, U0, 16, precision=1)
+    Uo = orc.run(c, U0, 16)
+    e = rel_l2(Ug, Uo)
+    print(f"FP32-intermediate form, {kind}, 16 steps: relative L2 per variable {e}")
+    assert np.all(np.isfinite(Ug)) and np.all(e < 1e-6), e
+
+
+@pytest.mark.parametrize("curv", [0.0, 0.2])
+@pytest.mark.parametrize("visc_law", [0, 1])
+def test_non_isothermal_power_law_parity(visc_law, curv):
+    """The heat flux and the power-law viscosity on the GPU: the TGV velocity with a temperature
+    that varies along all three axes (kappa dT/dx and mu = T^0.76 act from the first step), SAA
+    delays, ragged sub-domains, Cartesian and curvilinear grids; whole fields against the oracle."""
+    c = I.tgv_case(26, 3, "SAA", kmax=2, visc_law=visc_law, visc_exp=0.76, re=200.0, curv=curv)
+    X, Y, Z = I.point_coords(c)
+    u = np.sin(X) * np.cos(Y) * np.cos(Z)
+    v = -np.cos(X) * np.sin(Y) * np.cos(Z)
+    p = 1.0 / (c.gamma * c.mach ** 2) + (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0) / 16.0
+    T = 1.0 + 0.1 * np.sin(X) * np.cos(2 * Y) * np.sin(Z + 0.3)
+    U0 = I.conserved(c, c.gamma * c.mach ** 2 * p / T, u, v, np.zeros_like(u), p)
+    c = c.replace(dt=I.cfl_dt(c, U0, 0.25))
+    d = I.saa_delays(c, 10)
+    Ug, _ = gpu_run(c, U0, 10, delays=d)
+    Uo = orc.run(c, U0, 10, delays=d)
+    check(Ug, Uo)
+
+
 def test_fp32_form_subdomain_wider_than_tile():
     """FP32 form on one 42^3 sub-domain (periodic self-neighbour faces): the fused stage covers it
     with several tiles in x (32 + 10) and y, so tile boundaries inside the sub-domain take their

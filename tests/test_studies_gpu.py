@@ -45,6 +45,19 @@ def test_paper_vortex_orders_of_table1():
         assert by[(2, f"{algo}-AS")]["errors"][-1] > 3.0 * by[(3, f"{algo}-AT")]["errors"][-1], algo
 
 
+def test_async_error_grows_with_the_number_of_pes():
+    """The paper's vortex under CAA-AT (case 3) split into P = p x p PEs: the added error grows with
+    P at fixed L and with L at fixed P (Fig. 4 (b) and (a), at a small size)."""
+    ensure_built()
+    from paper_2506_03027_gb300 import studies
+    r = studies.paper_delay_study(n=256, Ls=(2, 4), Ps=(4, 16, 64), P_fixed=16, L_fixed=4, t_end=0.5)
+    print(r)
+    EL, EP = np.array(r["error_vs_L"]), np.array(r["error_vs_P"])
+    assert np.all(np.isfinite(EL)) and np.all(EL > 0) and np.all(np.isfinite(EP)) and np.all(EP > 0)
+    assert np.all(np.diff(EL) > 0), EL
+    assert np.all(np.diff(EP) > 0), EP
+
+
 # ------------------------------------------------------------------ parity at the study configurations
 
 def _check(Ug, Uo):
