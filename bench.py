@@ -13,7 +13,8 @@ Metric: point-RK-stage updates per second (Mpoint-stage/s) = 128^3 x 5 x steps /
             synchronize on both sides, max over ranks); the working set (~1.8 GB) is larger
             than the 129 MB L2.
   e2e       the same metric through the public API with host buffers: per step the state is
-            copied in from pinned host memory, stepped, and copied back out.
+            copied in from pinned host memory, stepped, and copied back out; host_link gives the
+            measured bandwidth of those copies and the floor they put under an e2e step.
   roofline  the dominant kernel's achieved FP64 rate (algorithmic flops per launch / average
             event-timed launch duration) against the GB300 FP64 peak.
   cpu_baseline  the FP64 CPU oracle on the host cores on a bounded sample of the workload.
@@ -82,6 +83,30 @@ def kernels_sha1(root: str = ROOT) -> str:
     structs = "".join(h[h.index("struct " + n + " {"):h.index("};", h.index("struct " + n + " {")) + 2]
                       for n in ("SubDev", "Geometry", "Physics"))
     return hashlib.sha1((k[a:b] + dc + structs).encode()).hexdigest()
+
+
+def host_link(host, nbytes: int) -> dict:
+    """Bandwidth of the host link for the e2e copies: the pinned state buffer to a device buffer
+    and back (copy engine, CUDA events, median of 5 after 2 warm-ups), and the floor they put
+    under an e2e step (one copy each way per step)."""
+    import torch
+    dev = torch.empty_like(host, device="cuda")
+    st = torch.cuda.current_stream()
+    out = {}
+    for name, dst, src in (("h2d", dev, host), ("d2h", host, dev)):
+        ts = []
+        for rep in range(7):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            dst.copy_(src, non_blocking=True)
+            e1.record(st)
+            e1.synchronize()
+            if rep >= 2:
+                ts.append(e0.elapsed_time(e1))
+        out[name + "_gbs"] = nbytes / (sorted(ts)[len(ts) // 2] * 1e-3) / 1e9
+    out["copy_floor_ms_per_step"] = (nbytes / out["h2d_gbs"] + nbytes / out["d2h_gbs"]) / 1e6
+    del dev
+    return out
 
 
 def measured_peaks():
@@ -360,6 +385,7 @@ def run_ours(args, rank, world, local_rank):
     te = max_over_ranks(te, world)
     e2e_value = whole_job_rate(case.npts * case.stages * Ke, world, te)
     state_bytes = 5 * case.npts * 8
+    link = host_link(host, state_bytes)
     U_fp64 = solver.get_state()
     n_done = solver.n
     solver.close()
@@ -467,7 +493,7 @@ def run_ours(args, rank, world, local_rank):
         "hbm_frac_algorithmic": hbm_frac,
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
-                "d2h_bytes_per_step": state_bytes},
+                "d2h_bytes_per_step": state_bytes, "ms_per_step": te * 1e3 / Ke, "host_link": link},
         "gpu_launches": launches,
         "launches_per_step": launches / K,
         "cuda_graph": True,

@@ -688,17 +688,20 @@ __global__ void __launch_bounds__(128) k_compact_div(Geometry g, const SubDev* _
   const long long gst[3] = {1, d.bnx, (long long)d.bnx * d.bny};
   const long long rs = gst[axis];
   const double h = 1.0 / (2.0 * d.c1[axis] * 3.0 / 4.0);  // c1 = (4/3 / 2) / h for the block's CD4 coefficients
-  const double al = 1.0 / 3.0, ca = (14.0 / 9.0) / (2.0 * h), cb = (1.0 / 9.0) / (4.0 * h);
+  // the system is linear in its right side, so it is solved in units of cb = b / (4h): the right
+  // side becomes (f_{i+2} - f_{i-2}) + 28 (f_{i+1} - f_{i-1}) (a / (2h) = 28 cb), the closures
+  // (...) / (60 h) = 0.6 cb (...), and cb multiplies the solution once per point
+  const double al = 1.0 / 3.0, cb = (1.0 / 9.0) / (4.0 * h);
   auto f = [&](int i) { return (double)F[(long long)i * st]; };
-  const double dl = (45.0 * (f(0) - f(-2)) - 9.0 * (f(1) - f(-3)) + (f(2) - f(-4))) / (60.0 * h);
-  const double dr = (45.0 * (f(n + 1) - f(n - 1)) - 9.0 * (f(n + 2) - f(n - 2)) + (f(n + 3) - f(n - 3))) / (60.0 * h);
+  const double dl = 0.6 * (45.0 * (f(0) - f(-2)) - 9.0 * (f(1) - f(-3)) + (f(2) - f(-4)));
+  const double dr = 0.6 * (45.0 * (f(n + 1) - f(n - 1)) - 9.0 * (f(n + 2) - f(n - 2)) + (f(n + 3) - f(n - 3)));
   const double* cp = cth + (long long)n * 2 * Lmax;
   const double* im = cp + Lmax;
   // forward sweep: the eliminated right sides go to a per-thread array (local memory)
   double w[CFS_MAX_LINE];
   double prev = 0.0;
   for (int i = 0; i < n; ++i) {
-    double rhs = ca * (f(i + 1) - f(i - 1)) + cb * (f(i + 2) - f(i - 2));
+    double rhs = fma(28.0, f(i + 1) - f(i - 1), f(i + 2) - f(i - 2));
     if (i == 0) rhs -= al * dl;
     if (i == n - 1) rhs -= al * dr;
     prev = (i == 0 ? rhs : rhs - al * prev) * __ldg(im + i);
@@ -707,12 +710,12 @@ __global__ void __launch_bounds__(128) k_compact_div(Geometry g, const SubDev* _
   // Phi_a = -F_a (k_flux stores the negated inviscid flux), so R = -sum_a D_a F_a = sum_a D_a Phi_a
   double x = prev;
   double* Rl = R + r0;
-  if (axis == 0) Rl[(long long)(n - 1) * rs] = x;
-  else Rl[(long long)(n - 1) * rs] += x;
+  if (axis == 0) Rl[(long long)(n - 1) * rs] = cb * x;
+  else Rl[(long long)(n - 1) * rs] = fma(cb, x, Rl[(long long)(n - 1) * rs]);
   for (int i = n - 2; i >= 0; --i) {
     x = w[i] - __ldg(cp + i) * x;
-    if (axis == 0) Rl[(long long)i * rs] = x;
-    else Rl[(long long)i * rs] += x;
+    if (axis == 0) Rl[(long long)i * rs] = cb * x;
+    else Rl[(long long)i * rs] = fma(cb, x, Rl[(long long)i * rs]);
   }
 }
 
