@@ -84,6 +84,8 @@ struct cfs_ctx {
   bool learned = false;
   float* d_mlp = nullptr;
   double* LH = nullptr;
+  float* d_mlpx = nullptr;   // the network's feature tiles: [ceil(ncol / MLP_TILE)][MLP_TILE x MLP_K1] FP32
+  double* d_mlpa = nullptr;  // their 3-level extrapolations: [ceil(ncol / MLP_TILE)][MLP_TILE x MLP_NOUT] FP64
   int* d_cols = nullptr;
   long long ncol = 0;
   cfs::MlpScales mlp_scales{};
@@ -1009,7 +1011,7 @@ static cfs_status enqueue_step(cfs_ctx* c, long long n, bool graph) {
   int pp = 0;
   if (c->learned && (graph || sc.mode == 1)) {
     // stage-0 face halos from the network, once per step (the later stages add AT increments)
-    const int rc = cfs::launch_mlp_halo(g, sc, c->ring, c->d_subs, c->d_cols, c->ncol, c->d_mlp, c->mlp_scales, c->LH,
+    const int rc = cfs::launch_mlp_halo(g, sc, c->ring, c->d_subs, c->d_cols, c->ncol, c->d_mlp, c->mlp_scales, c->d_mlpx, c->d_mlpa, c->LH,
                                         c->stream, &c->launches, tm);
     if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
     sc.LH = c->LH;
@@ -1400,7 +1402,10 @@ cfs_status cfs_set_halo_model(cfs_ctx* c, const float* params, const double* sca
     c->d_cols = (int*)dev_alloc(c, sizeof(int) * cols.size());
     c->d_mlp = (float*)dev_alloc(c, sizeof(float) * MLP_NPARAM);
     c->LH = (double*)dev_alloc(c, sizeof(double) * 5 * (size_t)c->geo.Ptot);
-    if (!c->d_cols || !c->d_mlp || !c->LH) return fail(c, CFS_ENOMEM, "device allocation failed");
+    const size_t ntile = (size_t)((c->ncol + MLP_TILE - 1) / MLP_TILE);
+    c->d_mlpx = (float*)dev_alloc(c, sizeof(float) * ntile * MLP_TILE * MLP_K1);
+    c->d_mlpa = (double*)dev_alloc(c, sizeof(double) * ntile * MLP_TILE * MLP_NOUT);
+    if (!c->d_cols || !c->d_mlp || !c->LH || !c->d_mlpx || !c->d_mlpa) return fail(c, CFS_ENOMEM, "device allocation failed");
     CUDA_TRY(c, cudaMemcpyAsync(c->d_cols, cols.data(), sizeof(int) * cols.size(), cudaMemcpyHostToDevice, c->stream), "upload columns");
     CUDA_TRY(c, cudaStreamSynchronize(c->stream), "upload columns");
   }

@@ -17,6 +17,9 @@
 #define MLP_NIN (3 * MLP_HDEPTH * 5 + MLP_KMAX + 1)  // 65
 #define MLP_NH 64
 #define MLP_NOUT (MLP_HDEPTH * 5)                    // 20
+// the solver's feature tiles: 128 face columns x 72 inputs (65 padded to a multiple of 8), FP32
+#define MLP_TILE 128
+#define MLP_K1 72
 #define MLP_OFF_W1 0
 #define MLP_OFF_B1 (MLP_OFF_W1 + MLP_NH * MLP_NIN)
 #define MLP_OFF_W2 (MLP_OFF_B1 + MLP_NH)
@@ -310,7 +313,7 @@ int launch_halo_samples(const Geometry& g, const StepSched& sc, const double* ri
                         long long n, MlpScales sc_, void* x_bf16, float* target, float* at4, int s, void* stream);
 // Solver: stage-0 halo values of every face column from the network (AT mode), into LH[5][Ptot].
 int launch_mlp_halo(const Geometry& g, const StepSched& sc, const double* ring, const SubDev* subs, const int* cols,
-                    long long ncol, const float* params, MlpScales sc_, double* LH, void* stream, long long* launches,
+                    long long ncol, const float* params, MlpScales sc_, float* X, double* A3, double* LH, void* stream, long long* launches,
                     const Timer* tm);
 
 // Diagnostics over all blocks: per block (size, state offset, CD coefficients, cell volume) the

@@ -9,6 +9,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include <algorithm>
 
 #include "cfs_internal.h"
@@ -345,10 +347,15 @@ __global__ void k_halo_samples(Geometry g, StepSched sc, const double* __restric
   }
 }
 
-// Solver use: each CTA takes TM = 128 face columns (sub-domain, face, t1, t2) at a time, gathers
-// their features at the face's delay, runs the network on the tensor cores and writes
-// U^(0) = extrapolation + residual / out scale for the HDEPTH halo points of each column into LH
-// (FP64, padded-box layout).
+// Solver use, two launches per asynchronous step.  k_mlp_features: one thread per (face column,
+// depth) pair gathers that depth's features at the face's delay (FP64 differences and scaling,
+// BF16 rounding) into the column's row of its 128-column tile -- FP32 values in the tensor cores'
+// operand layout, so a tile is one contiguous block -- and writes the 3-level extrapolation of the
+// halo point to LH (FP64, padded-box layout).  k_mlp_halo: each CTA takes tiles of TM = 128
+// columns, fetches a tile's features with one bulk copy (the next tile's copy is issued as soon
+// as the first layer has consumed the current one, so it overlaps the rest of the network), runs
+// the network on the tensor cores and adds residual / out scale to LH for the HDEPTH halo points
+// of each column.
 //
 // Every layer is one tcgen05 GEMM of M = 128 columns: D[m][n] = sum_k A[m][k] B[n][k] with A (the
 // activations) and B (the weights) in shared memory, K-major without swizzle (8-row x 16-byte core
@@ -359,13 +366,15 @@ __global__ void k_halo_samples(Geometry g, StepSched sc, const double* __restric
 // lo are below 2^-21 relative).  The features are BF16 values, exact in TF32, so the first layer
 // needs A_hi only.  One thread issues the MMAs and commits them to an mbarrier; all threads wait
 // (bounded), read D with tcgen05.ld (warp w: TMEM lanes 32 (w % 4).., a quarter of the columns),
-// add the bias, apply GELU and write the next layer's operands.  512 threads: one (column, depth)
-// pair of the gather each.
+// add the bias, apply GELU and write the next layer's operands.
 namespace {
 
-constexpr int TM = 128;       // columns per tile (MMA M)
+constexpr int TM = MLP_TILE;  // columns per tile (MMA M)
 constexpr int TC_NT = 512;    // threads: 16 warps; warp w reads TMEM lanes 32 (w % 4).. and column quarter w / 4
-constexpr int K1 = 72;        // NIN = 65 padded to a multiple of 8
+constexpr int K1 = MLP_K1;    // NIN = 65 padded to a multiple of 8
+constexpr unsigned XT_BYTES = TM * K1 * 4;          // one feature tile
+constexpr unsigned AT_BYTES = TM * MLP_NOUT * 8;     // one tile's extrapolations
+constexpr unsigned FEAT_SMEM = XT_BYTES + AT_BYTES;   // k_mlp_features: one tile of each
 constexpr int N3 = 32;        // NOUT = 20 padded to a multiple of 16
 constexpr int TMEM_COLS = 256;
 constexpr int D1 = 0, D2 = 64, D3 = 128;  // TMEM column of each layer's accumulator
@@ -382,8 +391,10 @@ struct TcSmem {
   __align__(16) float hh[TM * MLP_NH];
   __align__(16) float hl[TM * MLP_NH];
   float b1[MLP_NH], b2[MLP_NH], b3[N3];
-  double at3[TM][MLP_NOUT];
+  __align__(16) double at3[TM][MLP_NOUT];  // the tile's 3-level extrapolations
   unsigned long long mbar;
+  unsigned long long xbar;  // the bulk copy of a feature tile
+  unsigned long long abar;  // the bulk copy of a tile's extrapolations
   unsigned tmem_base;
   int fail;
 };
@@ -448,6 +459,30 @@ __device__ __forceinline__ bool mma_wait(TcSmem& sm, unsigned parity) {
   return __syncthreads_and(ok) != 0;
 }
 
+// Bounded wait for phase `parity` of a tile-copy barrier; every thread of the CTA sees the same
+// result.
+__device__ __forceinline__ bool tile_wait(TcSmem& sm, unsigned long long* bar, unsigned parity) {
+  unsigned it = 0;
+  bool ok = true;
+  while (!mbar_try(bar, parity))
+    if (++it > MBAR_SPIN_LIMIT) {
+      ok = false;
+      break;
+    }
+  if (!ok) sm.fail = 1;
+  return __syncthreads_and(ok) != 0;
+}
+
+// `bytes` global -> shared by the bulk-copy engine, completing on `bar` (one thread; both
+// addresses 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void tile_fetch(unsigned long long* bar, void* dst, const void* src, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(unsigned taddr, float* r) {
   unsigned u[16];
   asm volatile(
@@ -478,10 +513,52 @@ __device__ __forceinline__ void layer_mma(unsigned d, const float* ah, const flo
 
 }  // namespace
 
-__global__ void __launch_bounds__(TC_NT, 1) k_mlp_halo(Geometry g, StepSched sc, const double* __restrict__ ring,
-                                                        const SubDev* __restrict__ subs, const int* __restrict__ cols,
-                                                        long long ncol, const float* __restrict__ params, MlpScales ms,
-                                                        At3Table t3, double* __restrict__ LH) {
+// One CTA per tile of TM face columns, one thread per (column, depth): that depth's features
+// into the column's row of the tile and the 3-level extrapolation of its halo point, both
+// assembled in shared memory (features in the operand layout of the first layer, the depth-1
+// thread adding the one-hot delay and the padding; the idle rows of the last tile zero) and
+// stored with 16-byte writes: X [tile][TM x K1] FP32, A3 [tile][TM][MLP_NOUT] FP64.
+__global__ void __launch_bounds__(TM * MLP_HDEPTH) k_mlp_features(Geometry g, StepSched sc, const double* __restrict__ ring,
+                                                                 const SubDev* __restrict__ subs,
+                                                                 const int* __restrict__ cols, long long ncol,
+                                                                 MlpScales ms, At3Table t3, float* __restrict__ X,
+                                                                 double* __restrict__ A3) {
+  sc = resolve(sc);
+  if (sc.mode != 1) return;  // the network replaces AT halos only
+  extern __shared__ __align__(16) unsigned char feat_raw[];
+  float* sx = reinterpret_cast<float*>(feat_raw);                         // [TM * K1]
+  double* sa = reinterpret_cast<double*>(feat_raw + sizeof(float) * TM * K1);  // [TM * MLP_NOUT]
+  const long long tile = blockIdx.x;
+  const int tid = threadIdx.x, row = tid >> 2, r = tid & 3;  // depth r + 1
+  const long long col = tile * TM + row;
+  if (col < ncol) {
+    const int* cp = cols + 4 * col;
+    const int sid = cp[0], f = cp[1], t1 = cp[2], t2 = cp[3];
+    const int k = face_delay(sc, sid, f);
+    const SubDev d = subs[sid];
+    auto put = [&](int q, float val) { sx[core_off(row, q, K1)] = val; };
+    column_depth(g, sc, ring, d, f, t1, t2, k, r + 1, ms, t3.w[k], put, sa + row * MLP_NOUT, nullptr);
+    if (r == 0)
+      for (int q = 3 * MLP_HDEPTH * 5; q < K1; ++q) put(q, (q - 3 * MLP_HDEPTH * 5 == k) ? 1.f : 0.f);  // one-hot, padding
+  } else {
+    for (int q = r; q < K1; q += 4) sx[core_off(row, q, K1)] = 0.f;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sa[row * MLP_NOUT + 5 * r + v] = 0.0;
+  }
+  __syncthreads();
+  float4* gx = reinterpret_cast<float4*>(X + tile * (TM * K1));
+  const float4* s4 = reinterpret_cast<const float4*>(sx);
+  for (int i = tid; i < TM * K1 / 4; i += TM * MLP_HDEPTH) gx[i] = s4[i];
+  double2* ga = reinterpret_cast<double2*>(A3 + tile * (TM * MLP_NOUT));
+  const double2* s2 = reinterpret_cast<const double2*>(sa);
+  for (int i = tid; i < TM * MLP_NOUT / 2; i += TM * MLP_HDEPTH) ga[i] = s2[i];
+}
+
+__global__ void __launch_bounds__(TC_NT, 1) k_mlp_halo(Geometry g, StepSched sc, const SubDev* __restrict__ subs,
+                                                        const int* __restrict__ cols, long long ncol,
+                                                        const float* __restrict__ params, MlpScales ms,
+                                                        const float* __restrict__ X, const double* __restrict__ A3,
+                                                        double* __restrict__ LH) {
   sc = resolve(sc);
   if (sc.mode != 1) return;  // the network replaces AT halos only
   extern __shared__ __align__(16) unsigned char tc_raw[];
@@ -496,6 +573,8 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mlp_halo(Geometry g, StepSched sc,
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sm.mbar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sm.xbar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sm.abar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     sm.fail = 0;
   }
@@ -536,33 +615,20 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mlp_halo(Geometry g, StepSched sc,
   // this warp's TMEM lanes (rows 32 q..) and column quarter
   const int q = warp & 3, quarter = warp >> 2, row = 32 * q + lane;
   const unsigned lane_addr = tmem + ((unsigned)(32 * q) << 16);
-  unsigned parity = 0;
+  unsigned parity = 0, xparity = 0, aparity = 0;
   bool ok = true;
+  // the first tile's features and extrapolations (the barriers were initialised before the
+  // block-wide barrier above)
+  if (tid == 0 && (long long)blockIdx.x * TM < ncol) {
+    tile_fetch(&sm.xbar, sm.x, X + (long long)blockIdx.x * (TM * K1), XT_BYTES);
+    tile_fetch(&sm.abar, sm.at3, A3 + (long long)blockIdx.x * (TM * MLP_NOUT), AT_BYTES);
+  }
 
   for (long long base = (long long)blockIdx.x * TM; ok && base < ncol; base += (long long)gridDim.x * TM) {
     const int ns = (int)min((long long)TM, ncol - base);
-    // ---- gather: one (column, depth) pair per thread; the features go to the core layout
-    {
-      const int col = tid >> 2;
-      {
-        const int r = tid & 3;  // depth r + 1
-        if (col < ns) {
-          const int* cp = cols + 4 * (base + col);
-          const int sid = cp[0], f = cp[1], t1 = cp[2], t2 = cp[3];
-          const int k = face_delay(sc, sid, f);
-          auto put = [&](int e, float val) { sm.x[core_off(col, e, K1)] = val; };
-          column_depth(g, sc, ring, subs[sid], f, t1, t2, k, r + 1, ms, t3.w[k], put, sm.at3[col], nullptr);
-          if (r == 0)
-            for (int e = 3 * MLP_HDEPTH * 5; e < K1; ++e)
-              sm.x[core_off(col, e, K1)] = (e - 3 * MLP_HDEPTH * 5 == k) ? 1.f : 0.f;  // one-hot delay, padding
-        } else if (r == 0) {
-          for (int e = 0; e < K1; ++e) sm.x[core_off(col, e, K1)] = 0.f;  // idle rows of a partial tile
-        }
-      }
-    }
-    async_proxy_fence();
-    tc_fence_before();
-    __syncthreads();
+    const long long tile = base / TM, ntile_next = tile + gridDim.x;
+    if (!(ok = tile_wait(sm, &sm.xbar, xparity))) break;
+    xparity ^= 1;
     // ---- layer 1: z1 = x W1^T (+ b1 below)
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -571,6 +637,8 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mlp_halo(Geometry g, StepSched sc,
     }
     if (!(ok = mma_wait(sm, parity))) break;
     parity ^= 1;
+    // the first layer has read this tile's features: fetch the next tile's during the rest
+    if (tid == 0 && ntile_next * TM < ncol) tile_fetch(&sm.xbar, sm.x, X + ntile_next * (TM * K1), XT_BYTES);
     // ---- epilogue: h = GELU(z + b) as TF32 pairs; warp reads 16 of the 64 columns of its rows
     auto hidden = [&](int dcol, const float* b) {
       float z[16];
@@ -606,6 +674,8 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mlp_halo(Geometry g, StepSched sc,
     if (!(ok = mma_wait(sm, parity))) break;
     parity ^= 1;
     // ---- outputs: warp quarter c holds outputs 8c..8c+7 of its rows (20 of the 32 used)
+    if (!(ok = tile_wait(sm, &sm.abar, aparity))) break;
+    aparity ^= 1;
     {
       float y[8];
       unsigned u[8];
@@ -636,6 +706,12 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mlp_halo(Geometry g, StepSched sc,
     }
     tc_fence_before();
     __syncthreads();
+    // this tile's extrapolations are read (generic loads, ordered before the async-proxy copy
+    // that overwrites them by the barrier and the proxy fence): fetch the next tile's
+    if (tid == 0 && ntile_next * TM < ncol) {
+      async_proxy_fence();
+      tile_fetch(&sm.abar, sm.at3, A3 + ntile_next * (TM * MLP_NOUT), AT_BYTES);
+    }
   }
   // a wait that gave up: record it in the status word (the host reports CFS_ETIMEOUT) and poison
   // this CTA's columns so the state shows it too
@@ -652,8 +728,13 @@ __global__ void __launch_bounds__(TC_NT, 1) k_mlp_halo(Geometry g, StepSched sc,
             (long long)(c[0] + g.G) + (long long)d.ex * ((long long)(c[1] + g.G) + (long long)d.ey * (c[2] + g.Gz));
         LH[(long long)v * g.Ptot + d.pbase + qq] = __longlong_as_double(0x7ff8000000000000LL);
       }
-    // give MMAs still in flight a bounded chance to finish before the memory they use is freed
+    // give MMAs and a feature copy still in flight a bounded chance to finish before the memory
+    // they use is freed
     for (unsigned it = 0; it < MBAR_SPIN_LIMIT && !mbar_try(&sm.mbar, parity); ++it) {
+    }
+    for (unsigned it = 0; it < MBAR_SPIN_LIMIT && !mbar_try(&sm.xbar, xparity); ++it) {
+    }
+    for (unsigned it = 0; it < MBAR_SPIN_LIMIT && !mbar_try(&sm.abar, aparity); ++it) {
     }
     __syncthreads();
   }
@@ -682,20 +763,33 @@ int launch_halo_samples(const Geometry& g, const StepSched& sc, const double* ri
 }
 
 int launch_mlp_halo(const Geometry& g, const StepSched& sc, const double* ring, const SubDev* subs, const int* cols,
-                    long long ncol, const float* params, MlpScales ms, double* LH, void* stream, long long* launches,
-                    const Timer* tm) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
-    if (e != cudaSuccess) return (int)e;
-    attr = true;
+                    long long ncol, const float* params, MlpScales ms, float* X, double* A3, double* LH,
+                    void* stream, long long* launches, const Timer* tm) {
+  // the shared-memory opt-in is a per-device attribute: set once on every device that launches
+  static std::mutex mu;
+  static bool attr[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!attr[dev]) {
+      e = cudaFuncSetAttribute(k_mlp_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mlp_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FEAT_SMEM);
+      if (e != cudaSuccess) return (int)e;
+      attr[dev] = true;
+    }
   }
   const long long ntile = (ncol + TM - 1) / TM;
   const unsigned grid = (unsigned)std::min<long long>(ntile, 152LL);
+  const cudaStream_t st = (cudaStream_t)stream;
   if (tm) tm->rec(tm->self, 0, 1);
-  k_mlp_halo<<<grid, TC_NT, sizeof(TcSmem), (cudaStream_t)stream>>>(g, sc, ring, subs, cols, ncol, params, ms, at3_table(), LH);
+  k_mlp_features<<<(unsigned)ntile, TM * MLP_HDEPTH, FEAT_SMEM, st>>>(g, sc, ring, subs, cols, ncol, ms, at3_table(), X, A3);
+  k_mlp_halo<<<grid, TC_NT, sizeof(TcSmem), st>>>(g, sc, subs, cols, ncol, params, ms, X, A3, LH);
   if (tm) tm->rec(tm->self, 0, 0);
-  if (launches) *launches += 1;
+  if (launches) *launches += 2;
   return (int)cudaGetLastError();
 }
 
