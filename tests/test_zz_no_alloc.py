@@ -1,5 +1,6 @@
 """The allocation-free diagnostics entry point (cfs_diagnostics_static), for callers that cannot
-allocate device memory, checked through the C ABI against cfs_diagnostics on the same states.
+allocate device memory, checked through the C ABI against cfs_diagnostics on the same states and
+against the oracle's diagnostics.
 
 Collected last on purpose: it runs after every other test, and also passes alone in a fresh
 process."""
@@ -64,6 +65,22 @@ def test_static_diagnostics_match_context_diagnostics_twice(torch):
     # be affected by the second call
     again = static_diag(torch, c3, U3)
     np.testing.assert_allclose(again[:7], ref3[:7], rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("order", [4, 2])
+def test_static_diagnostics_match_the_oracle(torch, order):
+    """Against the FP64 oracle's diagnostics (the definition of the quantities) on states that no
+    solver produced: the Taylor-Green field on a ragged grid and a seeded perturbation of it, with
+    the CD4 and the CD2 vorticity."""
+    from oracle import oracle as orc
+    rng = np.random.default_rng(7 + order)
+    c = I.tgv_case(30, 3, "SA", order=order).replace(ny=28, nz=26)
+    U = I.tgv_state(c)
+    for X in (U, U * (1.0 + 1e-3 * rng.standard_normal(U.shape))):
+        got = static_diag(torch, c, torch.from_numpy(np.ascontiguousarray(X)).cuda())
+        ref = orc.diagnostics(c, X)
+        np.testing.assert_allclose(got[:7], ref[:7], rtol=1e-12, atol=1e-13 * np.abs(ref[:7]).max())
+        assert got[7] == ref[7] == 0.0
 
 
 def test_static_diagnostics_reject_oversized_grid(torch):
