@@ -195,6 +195,36 @@ def test_plan_on_a_connected_grid(nranks):
     assert crossing > 0
 
 
+def test_plan_with_a_process_that_computes_nothing():
+    """starts = [0, 5, 5, 12]: the middle process owns no sub-domain, so it reads nothing and
+    nobody reads from it; the two others exchange as in a two-process split."""
+    case = CASES["ns_filter_3d"]
+    starts = [0, 5, 5, 12]
+    plans = {}
+    for p in range(3):
+        ctx = context(case, starts, p)
+        try:
+            for q in range(3):
+                plans[p, q, 0] = cfs.cfs_exchange_plan(ctx, q, 0)
+                plans[p, q, 1] = cfs.cfs_exchange_plan(ctx, q, 1)
+        finally:
+            cfs.cfs_destroy(ctx)
+    for q in range(3):
+        assert len(plans[1, q, 0]) == 0 and len(plans[1, q, 1]) == 0
+        assert len(plans[q, 1, 0]) == 0 and len(plans[q, 1, 1]) == 0
+    two = {}
+    for p, r in ((0, 0), (2, 1)):
+        ctx = context(case, [0, 5, 12], r)
+        try:
+            two[p] = (cfs.cfs_exchange_plan(ctx, 1 - r, 0), cfs.cfs_exchange_plan(ctx, 1 - r, 1))
+        finally:
+            cfs.cfs_destroy(ctx)
+    np.testing.assert_array_equal(plans[0, 2, 0], two[0][0])
+    np.testing.assert_array_equal(plans[0, 2, 1], two[0][1])
+    np.testing.assert_array_equal(plans[2, 0, 0], two[2][0])
+    assert len(plans[0, 2, 1]) > 0
+
+
 def test_plan_rejects_bad_partitions():
     case = CASES["ns_filter_3d"]
     ctx = cfs.cfs_create(cfs.params_from_case(case), None)

@@ -211,7 +211,7 @@ def _rank_cgrid(rank, world, port, algo, starts, nsteps, out):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("algo,cut", [("SA", 0.5), ("SAA", 0.3)])
+@pytest.mark.parametrize("algo,cut", [("SA", 0.5), ("CAA", 0.6), ("SAA", 0.3)])
 def test_connected_grid_two_processes_match_one_context(algo, cut):
     """The 12-block NACA0012 C-grid (reduced size) split between two processes -- interfaces, the
     wake cut, walls and the spanwise interpolation between the layers all crossing the split --
