@@ -215,6 +215,65 @@ def cfs_set_exchange(ctx, fn):
     return cb
 
 
+class DeviceDoubles:
+    """A device buffer of the library seen by torch (CUDA array interface, no copy)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f8", "data": (int(ptr), False),
+                                         "version": 2}
+
+
+def torch_exchange(group=None):
+    """A transport for a partitioned context (Solver(..., exchange=...)) over torch.distributed
+    point-to-point messages; the ranks of the partition are the ranks of `group`.  With the NCCL
+    backend the packed device buffers are sent and received as they are (a batch of isend / irecv
+    per exchange); with another backend (gloo) every peer's part is staged through host memory and
+    the pairs exchange in rank order (the lower rank sends first), so blocking sends cannot
+    deadlock.  The context's stream is synchronised before the messages (the pack kernel has
+    written the send buffer) and the device after them (the unpack kernel reads the receive
+    buffer).  The NCCL branch needs one GPU per process and is not exercised by the tests, which
+    run on one GPU."""
+    import torch
+    import torch.distributed as dist
+    rank = dist.get_rank(group)
+    nccl = dist.get_backend(group) == "nccl"
+
+    def transport(nranks, send, scnt, recv, rcnt, stream):
+        torch.cuda.synchronize()
+        soff = np.concatenate([[0], np.cumsum(scnt)]).astype(np.int64)
+        roff = np.concatenate([[0], np.cumsum(rcnt)]).astype(np.int64)
+        sdev = torch.as_tensor(DeviceDoubles(send, max(int(soff[-1]), 1)), device="cuda")
+        rdev = torch.as_tensor(DeviceDoubles(recv, max(int(roff[-1]), 1)), device="cuda")
+        if nccl:
+            ops = []
+            for q in range(nranks):
+                if q == rank:
+                    continue
+                if scnt[q]:
+                    ops.append(dist.P2POp(dist.isend, sdev[soff[q]:soff[q + 1]], q, group))
+                if rcnt[q]:
+                    ops.append(dist.P2POp(dist.irecv, rdev[roff[q]:roff[q + 1]], q, group))
+            if ops:
+                for w in dist.batch_isend_irecv(ops):
+                    w.wait()
+        else:
+            for q in range(nranks):
+                if q == rank:
+                    continue
+                sb = sdev[soff[q]:soff[q + 1]].cpu()
+                rb = torch.empty(int(rcnt[q]), dtype=torch.float64)
+                if rank < q:
+                    dist.send(sb, q, group)
+                    dist.recv(rb, q, group)
+                else:
+                    dist.recv(rb, q, group)
+                    dist.send(sb, q, group)
+                rdev[roff[q]:roff[q + 1]].copy_(rb)
+        torch.cuda.synchronize()
+
+    return transport
+
+
 def cfs_exchange_plan(ctx, peer: int, which: int) -> np.ndarray:
     """State offsets of the points this rank sends to (which = 0) or receives from (1) `peer`."""
     n = ctypes.c_longlong()

@@ -1,7 +1,7 @@
 """A grid split over two processes (the paper's PEs spread over processes, Sec. 3, Alg. 1-3), both on
 the one GPU, exchanging boundary strips through the library's exchange callback over a gloo
-process group (device -> host -> gloo -> host -> device).  No kernel waits on another process: every
-exchange happens on the host between launches.  Every point each process computes must equal, bit
+process group (cfs.torch_exchange: device -> host -> gloo -> host -> device).  No kernel waits on
+another process: every exchange happens on the host between launches.  Every point each process computes must equal, bit
 for bit, the run of one context computing every sub-domain; the diagnostics of the two processes
 must add up to the whole grid's."""
 import os
@@ -17,40 +17,6 @@ def _free_port() -> int:
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         return s.getsockname()[1]
-
-
-class _DevArray:
-    """A device buffer of the library seen by torch (CUDA array interface, no copy)."""
-
-    def __init__(self, ptr, n):
-        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f8", "data": (int(ptr), False),
-                                         "version": 2}
-
-
-def _transport(rank, dist, torch):
-    """The exchange callback: device -> host -> gloo send/recv with every peer -> host -> device."""
-
-    def transport(nranks, send, scnt, recv, rcnt, stream):
-        torch.cuda.synchronize()                   # the packed strips are ready
-        soff = np.concatenate([[0], np.cumsum(scnt)])
-        roff = np.concatenate([[0], np.cumsum(rcnt)])
-        sdev = torch.as_tensor(_DevArray(send, max(soff[-1], 1)), device="cuda")
-        rdev = torch.as_tensor(_DevArray(recv, max(roff[-1], 1)), device="cuda")
-        for q in range(nranks):
-            if q == rank:
-                continue
-            sb = sdev[soff[q]:soff[q + 1]].cpu()
-            rb = torch.empty(int(rcnt[q]), dtype=torch.float64)
-            if rank < q:
-                dist.send(sb, q)
-                dist.recv(rb, q)
-            else:
-                dist.recv(rb, q)
-                dist.send(sb, q)
-            rdev[roff[q]:roff[q + 1]].copy_(rb)   # on the context's stream, before the unpack
-        torch.cuda.synchronize()
-
-    return transport
 
 
 def _case(name):
@@ -78,10 +44,7 @@ def _rank(rank, world, port, name, starts, nsteps, out):
         case = _case(name)
         d = I.saa_delays(case, nsteps) if case.algo == "SAA" else None
         U0 = I.tgv_state(case)
-
-        transport = _transport(rank, dist, torch)
-
-        part = cfs.Solver(case, partition=(world, starts, rank), exchange=transport)
+        part = cfs.Solver(case, partition=(world, starts, rank), exchange=cfs.torch_exchange())
         part.set_schedule(delays=d)
         part.set_state(U0)
         part.step(nsteps)
@@ -175,7 +138,7 @@ def _rank_cgrid(rank, world, port, algo, starts, nsteps, out):
         mb = mb.replace_all(dt=I.cgrid_dt(mb, 0.2))
         d = I.saa_delays(mb.case.replace(px=mb.nsub, py=1, pz=1), nsteps) if algo == "SAA" else None
         U0 = I.cgrid_state(mb, sp)
-        part = cfs.Solver(mb, partition=(world, starts, rank), exchange=_transport(rank, dist, torch))
+        part = cfs.Solver(mb, partition=(world, starts, rank), exchange=cfs.torch_exchange())
         part.set_schedule(delays=d)
         part.set_states(U0)
         part.step(nsteps)
