@@ -910,7 +910,7 @@ def main():
     ap.add_argument("--tiles", default="", help="fy,zc,threads launch shapes of the main path (profiling runs only)")
     ap.add_argument("--only-form", default="", choices=["", "cgrid_naca0012", "cgrid_naca0012_fp32_intermediates",
                                                         "learned_halo", "compact_euler", "batched_blocks_curvilinear",
-                                                        "static_diagnostics"],
+                                                        "static_diagnostics", "fp32_intermediates_256"],
                     help="run one form alone and print its result (profiling runs only; --tiles skips its autotuning)")
     ap.add_argument("--cgrid-half", action="store_true",
                     help="with --only-form: the C-grid at half the points per direction (profiling runs only)")
@@ -933,6 +933,9 @@ def main():
             return
         if args.only_form == "static_diagnostics":
             print(json.dumps(static_diagnostics_form()), flush=True)
+            return
+        if args.only_form == "fp32_intermediates_256":
+            print(json.dumps(precision_form_256(args)), flush=True)
             return
         print(json.dumps(cgrid_form(args, 1 if args.only_form.endswith("fp32_intermediates") else 0)), flush=True)
         return

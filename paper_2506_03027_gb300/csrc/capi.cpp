@@ -93,6 +93,7 @@ struct cfs_ctx {
   // fused FP32-intermediate stage (3-D Navier-Stokes, CD4)
   bool fused = false;
   int fblock_n = 0;     // FP32 form, asynchronous steps: sub-domain filter for cubic sub-domains of this size
+  float* d_fbhalo = nullptr;  // its halos: [nsub * 5][3][10][fblock_n^2] FP32 deviations
   int threads = 256;   // threads per CTA of the FP64 / 3-kernel stage kernels
   int fused_zc = 32;
   int fused_fy = 16;
@@ -646,7 +647,11 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
     const int n0 = c->subs[0].sx;
     bool cubic = cfs::filter_block_supported(n0);
     for (const SubDev& d : c->subs) cubic = cubic && d.sx == n0 && d.sy == n0 && d.sz == n0;
-    if (cubic) c->fblock_n = n0;
+    if (cubic) {
+      c->fblock_n = n0;
+      c->d_fbhalo = (float*)dev_alloc(c, sizeof(float) * (size_t)nsub * 15 * 10 * n0 * n0);
+      if (!c->d_fbhalo) return fail(c, CFS_ENOMEM, "device allocation failed");
+    }
   }
   if (c->fused) {
     // tiles of 32 x fy columns per sub-domain, marching z; one CTA per tile (persistent grid)
@@ -959,6 +964,7 @@ static int launch_fblock(cfs_ctx* c, const Geometry& g, const StepSched& sc, con
   f.alpha = c->p.alpha_f;
   for (int m = 0; m < 6; ++m) f.h[m] = c->filt_h[m];
   f.b1 = c->filt_h[1] - c->p.alpha_f;
+  f.halo = c->d_fbhalo;
   const cfs::Timer* tm = (c->timing && !graph) ? &c->timer : nullptr;
   return cfs::launch_filter_block(g, sc, f, c->fblock_n, c->stream, &c->launches, tm);
 }

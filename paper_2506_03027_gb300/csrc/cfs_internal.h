@@ -258,6 +258,9 @@ struct FilterBlockLaunch {
   double alpha;
   double h[6];
   double b1;
+  // the passes' halos as FP32 deviations from the (sub-domain, variable) reference value,
+  // [nsub * 5][3 axes][10][N * N], written by k_filter_block_halo
+  float* halo;
 };
 bool filter_block_supported(int n);
 int launch_filter_block(const Geometry& g, const StepSched& sc, const FilterBlockLaunch& f, int n, void* stream,

@@ -12,8 +12,13 @@
 // the first halo point), adds the increments in FP32 between passes, and writes
 // U + (w_final - w_initial) in FP64 once.  The state is read and written once per step instead of
 // once per pass.  Synchronous steps keep the per-pass kernels (their halo is the neighbours'
-// previous pass).
+// previous pass).  The halo values -- 10 per line and pass, each a C-level FP64 sum over the
+// ring -- come from k_filter_block_halo, which runs just before with one thread per value (many
+// warps per SM hide the ring reads that a 512-thread, 176-KB CTA cannot) and stores them as FP32
+// deviations for coalesced loads.
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include "cfs_internal.h"
 #include "device_common.cuh"
@@ -29,6 +34,56 @@ __host__ __device__ constexpr int fb_row(int n) { return n | 1; }
 template <int N>
 __host__ __device__ inline size_t fb_smem(void) {
   return sizeof(float) * ((size_t)fb_row(N) * N * N + 2 * N + 10 * (N * N + 1));
+}
+
+// The halos of one (sub-domain, variable, pass): 5 points beyond each end of every line, from the
+// ring (wrapped in the block): AT the extrapolation to t_{n+1} with the weights c(k+1) of the C
+// delayed levels in FP64, AS the latest visible level; stored as FP32 deviations from the
+// sub-domain's reference value (its first own value of the filter input), [10][N * N] per pass.
+// Items are ordered so that consecutive threads read consecutive points: h fastest for the x pass
+// (the 5 points of an end are adjacent in x), the line (x fastest) otherwise.
+template <int N>
+__global__ void __launch_bounds__(256) k_filter_block_halo(Geometry g, StepSched sc, FilterBlockLaunch f) {
+  sc = resolve(sc);
+  if (sc.mode == 0) return;  // synchronous step: the per-pass kernels filter it
+  const double* __restrict__ Uin = ring_or(f.Uin, f.in_ring, f.ring, sc, 0);
+  constexpr int CH = (10 * N * N + 255) / 256;  // blocks per (sub-domain, variable, axis)
+  const int b = blockIdx.x / CH;                // (sub-domain, variable, axis)
+  const int sid = b / 15, var = (b / 3) % 5, axis = b % 3;
+  const SubDev d = f.subs[sid];
+  const long long plane = (long long)d.bnx * d.bny;
+  const long long vbase = d.bbase + (long long)var * d.bN;
+  const long long lvN = 5 * g.N;
+  const long long own0 = (long long)d.ox + (long long)d.bnx * d.oy + plane * d.oz;
+  const double ref = Uin[vbase + own0];
+  const float rh = d2f_fast(ref), rl = dev_fast(ref, rh, 0.f);
+  const int f1 = axis == 0 ? 1 : 0, f2 = axis == 2 ? 1 : 2;
+  const int bn3[3] = {d.bnx, d.bny, d.bnz};
+  const int o3[3] = {d.ox, d.oy, d.oz};
+  const int kd[2] = {face_delay(sc, sid, 2 * axis), face_delay(sc, sid, 2 * axis + 1)};
+  const int nlev = sc.mode == 2 ? 1 : sc.C;
+  float* __restrict__ out = f.halo + (long long)b * 10 * N * N;
+  const int e = (blockIdx.x % CH) * blockDim.x + threadIdx.x;
+  if (e >= 10 * N * N) return;
+  const int h = axis == 0 ? e % 10 : e / (N * N), l = axis == 0 ? e / 10 : e % (N * N);
+  const int t1 = l % N, t2 = l / N;
+  const int sd = h < 5 ? 0 : 1;
+  int ca = o3[axis] + (h < 5 ? h - 5 : N + h - 5);
+  ca = ca < 0 ? ca + bn3[axis] : (ca >= bn3[axis] ? ca - bn3[axis] : ca);
+  int c3[3];
+  c3[f1] = o3[f1] + t1;
+  c3[f2] = o3[f2] + t2;
+  c3[axis] = ca;
+  const long long gi = vbase + c3[0] + (long long)d.bnx * c3[1] + plane * c3[2];
+  double r[CFS_MAX_LEVELS];
+#pragma unroll
+  for (int lv = 0; lv < CFS_MAX_LEVELS; ++lv)
+    r[lv] = lv < nlev ? f.ring[(long long)((sc.n - kd[sd] - lv) % sc.R) * lvN + gi] : 0.0;
+  double v = 0.0;
+#pragma unroll
+  for (int lv = 0; lv < CFS_MAX_LEVELS; ++lv)
+    if (lv < nlev) v = fma(sc.mode == 2 ? 1.0 : __ldg(sc.Wf + kd[sd] * sc.C + lv), r[lv], v);
+  out[h * (N * N) + l] = dev_fast(v, rh, rl);
 }
 
 template <int N>
@@ -49,7 +104,6 @@ __global__ void __launch_bounds__(FB_THREADS, 1) k_filter_block(Geometry g, Step
   const long long vbase = d.bbase + (long long)var * d.bN;
   const double* __restrict__ U = Uin + vbase;
   double* __restrict__ Uo = Uout + vbase;
-  const long long lvN = 5 * g.N;
   const long long own0 = (long long)d.ox + (long long)d.bnx * d.oy + plane * d.oz;
   const double ref = U[own0];
   const float rh = d2f_fast(ref), rl = dev_fast(ref, rh, 0.f);
@@ -72,50 +126,17 @@ __global__ void __launch_bounds__(FB_THREADS, 1) k_filter_block(Geometry g, Step
   for (int m = 2; m <= 5; ++m) hm[m] = (float)f.h[m];
   const float* cpf = sTh;
   const float* imf = sTh + N;
-  const int bn3[3] = {d.bnx, d.bny, d.bnz};
-  const int o3[3] = {d.ox, d.oy, d.oz};
 #pragma unroll
   for (int axis = 0; axis < 3; ++axis) {
     const int f1 = axis == 0 ? 1 : 0, f2 = axis == 2 ? 1 : 2;
     const int st[3] = {1, RX, RXY};
     const int sa = st[axis];
-    // ---- halo: 5 points beyond each end of every line, from the ring (wrapped in the block);
-    // items (h, line) ordered so that consecutive threads read consecutive points: h fastest
-    // for the x pass (the 5 points of an end are adjacent in x), the line (x fastest)
-    // otherwise; every item's C level loads are independent
-    const int kd[2] = {face_delay(sc, sid, 2 * axis), face_delay(sc, sid, 2 * axis + 1)};
-    // per end: ring-level offsets and extrapolation weights c(k + 1) of the C delayed levels
-    long long lev[2][CFS_MAX_LEVELS];
-    double wf[2][CFS_MAX_LEVELS];
-#pragma unroll
-    for (int sd = 0; sd < 2; ++sd)
-#pragma unroll
-      for (int lv = 0; lv < CFS_MAX_LEVELS; ++lv) {
-        const bool on = sc.mode == 2 ? lv == 0 : lv < sc.C;
-        lev[sd][lv] = on ? (long long)((sc.n - kd[sd] - lv) % sc.R) * lvN : 0;
-        wf[sd][lv] = sc.mode == 2 ? (lv == 0 ? 1.0 : 0.0) : (on ? __ldg(sc.Wf + kd[sd] * sc.C + lv) : 0.0);
-      }
-    const int nlev = sc.mode == 2 ? 1 : sc.C;
+    // ---- halo: the pass's 10 x N^2 values from k_filter_block_halo (coalesced)
+    const float* __restrict__ hsrc = f.halo + ((long long)blockIdx.x * 3 + axis) * 10 * N * N;
 #pragma unroll 4
     for (int e = tid; e < 10 * N * N; e += FB_THREADS) {
-      const int h = axis == 0 ? e % 10 : e / (N * N), l = axis == 0 ? e / 10 : e % (N * N);
-      const int t1 = l % N, t2 = l / N;
-      const int sd = h < 5 ? 0 : 1;
-      int ca = o3[axis] + (h < 5 ? h - 5 : N + h - 5);
-      ca = ca < 0 ? ca + bn3[axis] : (ca >= bn3[axis] ? ca - bn3[axis] : ca);
-      int c3[3];
-      c3[f1] = o3[f1] + t1;
-      c3[f2] = o3[f2] + t2;
-      c3[axis] = ca;
-      const long long gi = vbase + c3[0] + (long long)d.bnx * c3[1] + plane * c3[2];
-      double r[CFS_MAX_LEVELS];
-#pragma unroll
-      for (int lv = 0; lv < CFS_MAX_LEVELS; ++lv) r[lv] = lv < nlev ? f.ring[(sd ? lev[1][lv] : lev[0][lv]) + gi] : 0.0;
-      double v = 0.0;
-#pragma unroll
-      for (int lv = 0; lv < CFS_MAX_LEVELS; ++lv)
-        if (lv < nlev) v = fma(sd ? wf[1][lv] : wf[0][lv], r[lv], v);
-      sHalo[h * (N * N + 1) + l] = dev_fast(v, rh, rl);
+      const int h = e / (N * N), l = e % (N * N);
+      sHalo[h * (N * N + 1) + l] = __ldg(hsrc + e);
     }
     __syncthreads();
 #pragma unroll 1
@@ -166,12 +187,19 @@ __global__ void __launch_bounds__(FB_THREADS, 1) k_filter_block(Geometry g, Step
   }
 }
 
+// The shared-memory opt-in is a per-device attribute: set once on every device that launches.
 template <int N>
 int fb_prepare() {
-  static bool done = false;
-  if (done) return 0;
-  const cudaError_t e = cudaFuncSetAttribute(k_filter_block<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem<N>());
-  if (e == cudaSuccess) done = true;
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return 0;
+  e = cudaFuncSetAttribute(k_filter_block<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_smem<N>());
+  if (e == cudaSuccess) done[dev] = true;
   return (int)e;
 }
 
@@ -186,10 +214,15 @@ int launch_filter_block(const Geometry& g, const StepSched& sc, const FilterBloc
   if (rc) return rc;
   if (tm) tm->rec(tm->self, 3, 1);
   const unsigned nb = (unsigned)(5 * f.nsub);
-  if (n == 32) k_filter_block<32><<<nb, FB_THREADS, fb_smem<32>(), st>>>(g, sc, f);
-  else k_filter_block<16><<<nb, FB_THREADS, fb_smem<16>(), st>>>(g, sc, f);
+  if (n == 32) {
+    k_filter_block_halo<32><<<(unsigned)(15 * f.nsub * ((10 * 32 * 32 + 255) / 256)), 256, 0, st>>>(g, sc, f);
+    k_filter_block<32><<<nb, FB_THREADS, fb_smem<32>(), st>>>(g, sc, f);
+  } else {
+    k_filter_block_halo<16><<<(unsigned)(15 * f.nsub * ((10 * 16 * 16 + 255) / 256)), 256, 0, st>>>(g, sc, f);
+    k_filter_block<16><<<nb, FB_THREADS, fb_smem<16>(), st>>>(g, sc, f);
+  }
   if (tm) tm->rec(tm->self, 3, 0);
-  if (launches) *launches += 1;
+  if (launches) *launches += 2;
   return (int)cudaGetLastError();
 }
 

@@ -22,6 +22,8 @@
 // and the buffer updates of Eq. 8 / Table 5) and stores the FP32 primitives per stage.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "cfs_internal.h"
 #include "device_common.cuh"
 
@@ -132,7 +134,9 @@ __global__ void __launch_bounds__(256) k_halo_prims(Geometry g, Physics ph, Step
     // with the delay of the faces crossed, and far-field constants -- are prepared here per stage
     // as for any other halo point.
     const GatherEntry& E = g.gent[g.emap[d.ebase + (ux + g.GE) + (long long)d.gmx * ((uy + g.GE) + (long long)d.gmy * gz)]];
-    if (E.nt == 1 && !(E.flags[0] & 2) && E.sid[0] == sid) return;
+    // (own sources beyond the sub-domain in z are reached across the periodic wrap: foreign,
+    // prepared here like any other; the fused stage reads them from this store)
+    if (E.nt == 1 && !(E.flags[0] & 2) && E.sid[0] == sid && ck >= 0 && ck < d.sz) return;
     double acc[S][5];
 #pragma unroll
     for (int m = 0; m < S; ++m)
@@ -788,12 +792,21 @@ int launch_halo_prims(const Geometry& g, const Physics& ph, const StepSched& sc,
 template <int FX, int FY>
 static int fused_prepare(int* blocks_per_sm, int curv) {
   const size_t sm = curv ? FusedSmem<FX, FY>::bytes_curv : FusedSmem<FX, FY>::bytes;
-  static bool attr_set = false;  // per process: the attribute (the largest size) is a property of the kernel
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_stage_fused<FX, FY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)FusedSmem<FX, FY>::bytes_curv);
-    if (e != cudaSuccess) return (int)e;
-    attr_set = true;
+  // the shared-memory opt-in (the largest size) is a per-device attribute of the kernel
+  static std::mutex mu;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!attr_set[dev]) {
+      e = cudaFuncSetAttribute(k_stage_fused<FX, FY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)FusedSmem<FX, FY>::bytes_curv);
+      if (e != cudaSuccess) return (int)e;
+      attr_set[dev] = true;
+    }
   }
   if (blocks_per_sm) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_stage_fused<FX, FY>, FX * FY, sm);

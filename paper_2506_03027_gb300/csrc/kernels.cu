@@ -136,6 +136,7 @@ __device__ __forceinline__ void view_halo(const Geometry& g, const Physics& ph, 
       if ((ck < 0 || ck >= d.sz) && !((d.phys >> (ck < 0 ? 4 : 5)) & 1)) kd = max(kd, face_delay(sc, sid, ck < 0 ? 4 : 5));
     }
     auto slot = [&](int l) { const int qq = nR - kd - l; return qq < 0 ? qq + sc.R : qq; };
+    const bool zin = ck >= 0 && ck < d.sz;
     const int ei = g.emap[d.ebase + (ux + g.GE) + (long long)d.gmx * ((uy + g.GE) + (long long)d.gmy * gz)];
     const GatherEntry& E = g.gent[ei];
 #pragma unroll
@@ -143,7 +144,11 @@ __device__ __forceinline__ void view_halo(const Geometry& g, const Physics& ph, 
     const long long lvN = 5 * g.N;
     const double* w = sc.W + (kd * s + stage) * sc.C;
     for (int t = 0; t < E.nt; ++t) {
-      const bool own = !(E.flags[t] & 2) && E.sid[t] == sid;
+      // an own source (wall mirror, outflow copy of this sub-domain's point) is current only for
+      // points inside the sub-domain in z: the map is indexed at the wrapped z, so beyond a z
+      // face the source is reached across the periodic wrap -- a neighbouring PE's in z (with a
+      // single sub-domain along z, the sub-domain's own PE across that face), seen with delay
+      const bool own = zin && !(E.flags[t] & 2) && E.sid[t] == sid;
       const double wt = E.w[t], wf = (E.flags[t] & 1) ? -wt : wt;
       const long long o = E.off[t];
       const long long bN = E.bN[t];

@@ -206,14 +206,21 @@ long long mlp_workspace_floats(long long nsamp) {
   return nchunk * MLP_NPARAM + nchunk;
 }
 
-static bool g_attr = false;
-
+// The shared-memory opt-in of the training kernels is a per-device attribute: set once on every
+// device that launches them.
 static int set_attr() {
-  if (g_attr) return 0;
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return 0;
+  e = cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_mlp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-  if (e == cudaSuccess) g_attr = true;
+  if (e == cudaSuccess) done[dev] = true;
   return (int)e;
 }
 
