@@ -1149,11 +1149,22 @@ int launch_round_table(const double* x, float* y, long long n, void* stream) {
   return (int)cudaGetLastError();
 }
 
+// The shared-memory opt-in of the line-filter kernels is a per-device attribute shared by every
+// context of the process: it only ever rises (to the largest size a context on the device has
+// needed), so a context with shorter lines cannot lower it under another one still stepping.
 int filter_prepare(int Lmax, int precision) {
   const size_t sm = filter_smem_bytes(Lmax, precision);
   if (sm > 227 * 1024) return (int)cudaErrorInvalidValue;
+  static std::mutex mu;
+  static int set_to[64][2] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  int& cur = set_to[dev][precision == 1 ? 1 : 0];
+  if ((int)sm <= cur) return 0;
   const int b = (int)sm;
-  cudaError_t e = cudaSuccess;
   if (precision == 1) {
     e = cudaFuncSetAttribute(k_filter<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_filter<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
@@ -1163,6 +1174,7 @@ int filter_prepare(int Lmax, int precision) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_filter<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_filter<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   }
+  if (e == cudaSuccess) cur = b;
   return (int)e;
 }
 

@@ -99,3 +99,45 @@ def test_no_read_of_unwritten_device_memory(torch, monkeypatch, name):
     for a, b in zip(res[0], res[255]):
         assert np.all(np.isfinite(b))
         np.testing.assert_array_equal(a, b)
+
+
+def test_contexts_alive_together_give_their_own_bits(torch):
+    """Three contexts of different kinds -- the FP64 TGV path, the FP32 fused stage with the
+    sub-domain filter, the FP32 C-grid -- created together and stepped alternately, each on its own
+    stream, give the bits each gives alone (no state shared between contexts)."""
+    cases = [dict(case=lambda: _tgv(34, 4, "SAA")),
+             dict(case=lambda: _tgv(32, 2, "CAA"), precision=1),
+             dict(mb=lambda: _cgrid("SAA"), precision=1)]
+    nst = 8
+    alone = [_run(torch, nst=nst, **kw) for kw in cases]
+    solvers, streams = [], []
+    try:
+        for kw in cases:
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                if "mb" in kw:
+                    m = kw["mb"]()
+                    s = cfs.Solver(m, precision=kw.get("precision", 0), stream=st)
+                    s.set_schedule(delays=I.saa_delays(m.case.replace(px=m.nsub, py=1, pz=1), nst))
+                    s.set_states(I.cgrid_state(m, I.cgrid_reduced()))
+                else:
+                    c = kw["case"]()
+                    s = cfs.Solver(c, precision=kw.get("precision", 0), stream=st)
+                    s.set_schedule(delays=I.saa_delays(c, nst) if c.algo == "SAA" else None)
+                    s.set_state(I.tgv_state(c))
+            solvers.append(s)
+            streams.append(st)
+        for _ in range(nst):
+            for s, st in zip(solvers, streams):
+                with torch.cuda.stream(st):
+                    s.step(1)
+        together = []
+        for s, st, kw in zip(solvers, streams, cases):
+            with torch.cuda.stream(st):
+                together.append(s.get_states() if "mb" in kw else [s.get_state()])
+    finally:
+        for s in solvers:
+            s.close()
+    for a_list, b_list in zip(alone, together):
+        for a, b in zip(a_list, b_list):
+            np.testing.assert_array_equal(a, b)
