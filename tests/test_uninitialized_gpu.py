@@ -141,3 +141,30 @@ def test_contexts_alive_together_give_their_own_bits(torch):
     for a_list, b_list in zip(alone, together):
         for a, b in zip(a_list, b_list):
             np.testing.assert_array_equal(a, b)
+
+
+def test_repeated_contexts_leave_no_device_memory(torch):
+    """Contexts created, stepped as CUDA graphs and destroyed over and over return their memory:
+    PyTorch's count of allocated bytes comes back to its start, and the device's free memory stays
+    level after the first round (graph executables, events, tables)."""
+    c = _tgv(32, 2, "CAA")
+    U0 = I.tgv_state(c)
+    torch.cuda.synchronize()
+    base_alloc = torch.cuda.memory_allocated()
+    free = []
+    for it in range(12):
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            s = cfs.Solver(c, precision=it % 2, graph=True, stream=st)
+            try:
+                s.set_schedule()
+                s.set_state(U0)
+                s.step(3)
+                s.diagnostics()
+            finally:
+                s.close()
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() == base_alloc
+        torch.cuda.empty_cache()  # the caching allocator keeps freed blocks per stream
+        free.append(torch.cuda.mem_get_info()[0])
+    assert max(free[2:]) - min(free[2:]) < (64 << 20), [f - free[2] for f in free]
