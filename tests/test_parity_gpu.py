@@ -176,6 +176,60 @@ def test_checkpoint_resume_is_exact():
     np.testing.assert_array_equal(U, U12)
 
 
+@pytest.mark.parametrize("kind", ["fp32_fused_graph", "cgrid_fp64_saa", "cgrid_fp32_caa"])
+def test_checkpoint_resume_other_paths(kind):
+    """Ring + step index restore on the FP32 form (fused stage, sub-domain filter, CUDA graph) and on
+    the connected C-grid (every block's levels in one ring), FP64 and FP32: 7 steps, checkpoint,
+    5 more in a new context equal 12 steps in one, bit for bit."""
+    import torch
+    from test_blocks_gpu import cgrid, sub_delays
+    if kind == "fp32_fused_graph":
+        case, mb, precision, graph = small_tgv("CAA", n=32, p=2), None, 1, True
+        d = None
+        U0 = [I.tgv_state(case)]
+    else:
+        mb, U0 = cgrid("SAA" if kind.endswith("saa") else "CAA")
+        if kind.endswith("caa"):
+            mb = mb.replace_all(caa_L=3, kmax=2)
+        case, precision, graph = mb.case, 1 if "fp32" in kind else 0, False
+        d = sub_delays(mb, 12) if kind.endswith("saa") else None
+
+    def solver():
+        st = torch.cuda.Stream()
+        return cfs.Solver(mb if mb is not None else case, precision=precision, graph=graph, stream=st), st
+
+    def states(s):
+        return s.get_states() if mb is not None else [s.get_state()]
+
+    s, st = solver()
+    with torch.cuda.stream(st):
+        s.set_schedule(delays=d)
+        s.set_states(U0) if mb is not None else s.set_state(U0[0])
+        s.step(12)
+        U12 = states(s)
+    s.close()
+    s, st = solver()
+    with torch.cuda.stream(st):
+        s.set_schedule(delays=d)
+        s.set_states(U0) if mb is not None else s.set_state(U0[0])
+        s.step(7)
+        R = cfs.cfs_ring_depth(s.ctx)
+        ntot = sum(b.nx * b.ny * b.nz for b in (mb.blocks if mb is not None else [case]))
+        ring = np.empty(R * 5 * ntot)
+        cfs.cfs_get_ring(s.ctx, ring.ctypes.data, cfs.HOST)
+    s.close()
+    s2, st2 = solver()
+    with torch.cuda.stream(st2):
+        s2.set_schedule(delays=d)
+        cfs.cfs_set_step(s2.ctx, 7)
+        cfs.cfs_set_ring(s2.ctx, ring.ctypes.data, cfs.HOST)
+        s2.step(5)
+        U = states(s2)
+    s2.close()
+    for a, b in zip(U, U12):
+        np.testing.assert_array_equal(a, b)
+
+
 def test_nonfinite_state_is_reported():
     """A NaN planted in the host copy of the state makes the diagnostics return ENAN."""
     c = small_tgv("SA", n=16, p=2, filter=False)
