@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
         const float u = c0.x, v = c0.y, w = c0.z, T = c0.w;
         const float rho = c3.x, p = c3.y, etH = c3.z + k.Href;
         float mu = 1.f;
-        if (k.law == 1) mu = powf(T, k.vexp);
+        if (k.law == 1) mu = __powf(T, k.vexp);  // the hardware log2 / exp2 pair: a few ulp, FP32-form accuracy
         const float div = (du[0][0] + du[1][1]) + du[2][2];
         const float vel[3] = {u, v, w};
         float tau[3][3], bq[3];
@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(FX* FY, (FX * FY >= 512) ? 1 : 2) k_stage_fuse
         const float u = c0.x, v = c0.y, w = c0.z, T = c0.w;
         const float rho = c3.x, p = c3.y, etH = c3.z + k32.Href;
         float mu = 1.f;
-        if (k32.law == 1) mu = powf(T, k32.vexp);
+        if (k32.law == 1) mu = __powf(T, k32.vexp);
         const float div = (du[0][0] + du[1][1]) + du[2][2];
         const float m23 = (-2.f / 3.f) * mu, kmu = k32.kap * mu;
         const float vel[3] = {u, v, w};

@@ -289,12 +289,13 @@ __device__ __forceinline__ double pow_tab(double x, double a) {
 }
 
 // Viscosity law: mu = 1, or the power law mu = T^visc_exp -- in the intermediate precision (the
-// FP32 form evaluates it in FP32: a power in FP64 runs at the FP64 rate).  The flux kernels pass
+// FP32 form evaluates it in FP32 with the hardware log2 / exp2 pair, a few ulp: a power in FP64
+// runs at the FP64 rate).  The flux kernels pass
 // kappa T and take the factor kappa^-a with 1/Re (Physics::ivT).
 template <typename T>
 __device__ __forceinline__ T visc_mu(const Physics& ph, T temp) {
   if (ph.visc_law != 1) return (T)1;
-  if (std::is_same<T, float>::value) return (T)powf((float)temp, (float)ph.visc_exp);
+  if (std::is_same<T, float>::value) return (T)__powf((float)temp, (float)ph.visc_exp);
   return (T)pow_tab((double)temp, ph.visc_exp);
 }
 
