@@ -210,19 +210,41 @@ def test_wall_channel_parity(precision):
     assert np.all(Ug[0][1:4, :, 0, :] == 0.0) and np.all(Ug[0][1:4, :, -1, :] == 0.0)
 
 
+_FULL = {}
+
+
+def _full_cgrid():
+    """The full C-grid, its initial state, delays and the oracle's 7 steps (computed once)."""
+    if not _FULL:
+        spec = I.CGridSpec()
+        mb = I.naca_cgrid(spec, algo="SAA", kmax=2)
+        mb = mb.replace_all(dt=I.cgrid_dt(mb, 0.05))
+        U0 = I.cgrid_state(mb, spec)
+        n = 7
+        d = sub_delays(mb, n)
+        _FULL.update(mb=mb, U0=U0, n=n, d=d, Uo=orc.run(mb, U0, n, delays=d))
+    return _FULL
+
+
 def test_cgrid_full_size_parity():
     """The full 12-block C-grid of the benchmark (22.0 M points, 154 sub-domains, CUDA graph) for 7
     steps -- five synchronous warm-up steps, then two with SAA delays -- against the oracle over
     the whole field (the oracle takes about a minute on the host cores)."""
-    spec = I.CGridSpec()
-    mb = I.naca_cgrid(spec, algo="SAA", kmax=2)
-    mb = mb.replace_all(dt=I.cgrid_dt(mb, 0.05))
-    U0 = I.cgrid_state(mb, spec)
-    n = 7
-    d = sub_delays(mb, n)
-    Ug = run_mb(mb, U0, n, delays=d, graph=True)
-    Uo = orc.run(mb, U0, n, delays=d)
-    check_blocks(Ug, Uo)
+    f = _full_cgrid()
+    Ug = run_mb(f["mb"], f["U0"], f["n"], delays=f["d"], graph=True)
+    check_blocks(Ug, f["Uo"])
+
+
+def test_cgrid_full_size_fp32_form():
+    """The same run through the FP32 form as the benchmark times it (one fused launch per RK stage,
+    CUDA graph): every block within the FP32-form bound of the oracle, the wall points at rest."""
+    f = _full_cgrid()
+    Ug = run_mb(f["mb"], f["U0"], f["n"], delays=f["d"], precision=1, graph=True)
+    for b, (a, r) in enumerate(zip(Ug, f["Uo"])):
+        e = rel_l2(a, r)
+        assert np.all(np.isfinite(a)) and np.all(e < 1e-6), (b, e)
+    for b in range(1, 5):  # the airfoil blocks' wall rows
+        assert np.all(Ug[b][1:4, :, 0, :] == 0.0)
 
 
 def test_fp64_power_within_a_few_ulp():
