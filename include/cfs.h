@@ -99,8 +99,8 @@ cfs_status cfs_add_block(cfs_ctx* ctx, int ni, int nj, int nk, const double* spa
  * in index space.  The data are copied.  Call after cfs_add_block, before cfs_finalize
  * (ESTATE otherwise); EINVAL for an unknown block, null pointers or non-finite values, and at
  * cfs_finalize for a grid with a non-positive cell volume.  The FP32-intermediate precision runs
- * curvilinear blocks periodic on every face through the fused stage (one launch per RK stage);
- * connected blocks take the multi-kernel stage. */
+ * 3-D Navier-Stokes CD4 on curvilinear blocks -- periodic or connected (interfaces, walls, far
+ * fields, outflows) -- through the fused stage (one launch per RK stage). */
 cfs_status cfs_set_block_grid(cfs_ctx* ctx, int block, const double* xy, const double* shift);
 
 /* Decompose a block into pi x pj x pk sub-domains (the paper's PEs, Sec. 3); sub-domains are
@@ -159,7 +159,9 @@ cfs_status cfs_metric_terms(cfs_ctx* ctx, int block, int i, int j, double* out);
  * These halo closures are readings: the paper does not print its boundary treatment.  Beyond a
  * physical face the grid of a curvilinear block is reflected through the boundary point.  A halo
  * source reached by a wall mirror or an outflow copy inside the same sub-domain is the PE's own
- * current value.  Before cfs_finalize (ESTATE after); EINVAL on a bad argument. */
+ * current value for points inside the sub-domain along z; beyond a z face such a source is
+ * reached across the periodic wrap (or lies in the z-neighbour) and is seen with that face's
+ * delay.  Before cfs_finalize (ESTATE after); EINVAL on a bad argument. */
 #define CFS_BC_PERIODIC 0
 #define CFS_BC_WALL 1
 #define CFS_BC_FARFIELD 2
