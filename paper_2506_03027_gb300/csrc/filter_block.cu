@@ -75,10 +75,15 @@ __global__ void __launch_bounds__(256) k_filter_block_halo(Geometry g, StepSched
   c3[f2] = o3[f2] + t2;
   c3[axis] = ca;
   const long long gi = vbase + c3[0] + (long long)d.bnx * c3[1] + plane * c3[2];
+  // ring slot of level n - k - l: (n mod R) - k - l, wrapped once (k + l < R)
+  const int nR = (int)(sc.n % sc.R);
   double r[CFS_MAX_LEVELS];
 #pragma unroll
-  for (int lv = 0; lv < CFS_MAX_LEVELS; ++lv)
-    r[lv] = lv < nlev ? f.ring[(long long)((sc.n - kd[sd] - lv) % sc.R) * lvN + gi] : 0.0;
+  for (int lv = 0; lv < CFS_MAX_LEVELS; ++lv) {
+    int q = nR - kd[sd] - lv;
+    q = q < 0 ? q + sc.R : q;
+    r[lv] = lv < nlev ? f.ring[(long long)q * lvN + gi] : 0.0;
+  }
   double v = 0.0;
 #pragma unroll
   for (int lv = 0; lv < CFS_MAX_LEVELS; ++lv)
