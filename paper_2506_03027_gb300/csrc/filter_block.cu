@@ -47,8 +47,7 @@ __global__ void __launch_bounds__(256) k_filter_block_halo(Geometry g, StepSched
   sc = resolve(sc);
   if (sc.mode == 0) return;  // synchronous step: the per-pass kernels filter it
   const double* __restrict__ Uin = ring_or(f.Uin, f.in_ring, f.ring, sc, 0);
-  constexpr int CH = (10 * N * N + 255) / 256;  // blocks per (sub-domain, variable, axis)
-  const int b = blockIdx.x / CH;                // (sub-domain, variable, axis)
+  const int b = blockIdx.x;  // (sub-domain, variable, axis); the CTA loops over its 10 N^2 values
   const int sid = b / 15, var = (b / 3) % 5, axis = b % 3;
   const SubDev d = f.subs[sid];
   const long long plane = (long long)d.bnx * d.bny;
@@ -57,38 +56,47 @@ __global__ void __launch_bounds__(256) k_filter_block_halo(Geometry g, StepSched
   const long long own0 = (long long)d.ox + (long long)d.bnx * d.oy + plane * d.oz;
   const double ref = Uin[vbase + own0];
   const float rh = d2f_fast(ref), rl = dev_fast(ref, rh, 0.f);
-  const int f1 = axis == 0 ? 1 : 0, f2 = axis == 2 ? 1 : 2;
-  const int bn3[3] = {d.bnx, d.bny, d.bnz};
-  const int o3[3] = {d.ox, d.oy, d.oz};
-  const int kd[2] = {face_delay(sc, sid, 2 * axis), face_delay(sc, sid, 2 * axis + 1)};
+  // strides along the pass axis and the two line axes (x fastest), the wrap length along the axis
+  const long long sA = axis == 0 ? 1 : (axis == 1 ? (long long)d.bnx : plane);
+  const long long s1 = axis == 0 ? (long long)d.bnx : 1, s2 = axis == 2 ? (long long)d.bnx : plane;
+  const int nA = axis == 0 ? d.bnx : (axis == 1 ? d.bny : d.bnz);
+  const int oA = axis == 0 ? d.ox : (axis == 1 ? d.oy : d.oz);
+  const long long base12 = vbase + own0 - (long long)oA * sA;  // origin of the lines, axis coordinate 0
   const int nlev = sc.mode == 2 ? 1 : sc.C;
-  float* __restrict__ out = f.halo + (long long)b * 10 * N * N;
-  const int e = (blockIdx.x % CH) * blockDim.x + threadIdx.x;
-  if (e >= 10 * N * N) return;
-  const int h = axis == 0 ? e % 10 : e / (N * N), l = axis == 0 ? e / 10 : e % (N * N);
-  const int t1 = l % N, t2 = l / N;
-  const int sd = h < 5 ? 0 : 1;
-  int ca = o3[axis] + (h < 5 ? h - 5 : N + h - 5);
-  ca = ca < 0 ? ca + bn3[axis] : (ca >= bn3[axis] ? ca - bn3[axis] : ca);
-  int c3[3];
-  c3[f1] = o3[f1] + t1;
-  c3[f2] = o3[f2] + t2;
-  c3[axis] = ca;
-  const long long gi = vbase + c3[0] + (long long)d.bnx * c3[1] + plane * c3[2];
-  // ring slot of level n - k - l: (n mod R) - k - l, wrapped once (k + l < R)
+  // per end of the lines: ring-level offsets of the C delayed levels (slot (n mod R) - k - l,
+  // wrapped once) and their weights c(k + 1)
+  long long lev[2][CFS_MAX_LEVELS];
+  double wf[2][CFS_MAX_LEVELS];
   const int nR = (int)(sc.n % sc.R);
-  double r[CFS_MAX_LEVELS];
 #pragma unroll
-  for (int lv = 0; lv < CFS_MAX_LEVELS; ++lv) {
-    int q = nR - kd[sd] - lv;
-    q = q < 0 ? q + sc.R : q;
-    r[lv] = lv < nlev ? f.ring[(long long)q * lvN + gi] : 0.0;
+  for (int sd = 0; sd < 2; ++sd) {
+    const int kd = face_delay(sc, sid, 2 * axis + sd);
+#pragma unroll
+    for (int lv = 0; lv < CFS_MAX_LEVELS; ++lv) {
+      int q = nR - kd - lv;
+      q = q < 0 ? q + sc.R : q;
+      lev[sd][lv] = lv < nlev ? (long long)q * lvN : 0;
+      wf[sd][lv] = sc.mode == 2 ? 1.0 : (lv < nlev ? __ldg(sc.Wf + kd * sc.C + lv) : 0.0);
+    }
   }
-  double v = 0.0;
+  float* __restrict__ out = f.halo + (long long)b * 10 * N * N;
+#pragma unroll 4
+  for (int e = threadIdx.x; e < 10 * N * N; e += blockDim.x) {
+    const int h = axis == 0 ? e % 10 : e / (N * N), l = axis == 0 ? e / 10 : e % (N * N);
+    const int t1 = l % N, t2 = l / N;
+    const int sd = h < 5 ? 0 : 1;
+    int ca = oA + (h < 5 ? h - 5 : N + h - 5);
+    ca = ca < 0 ? ca + nA : (ca >= nA ? ca - nA : ca);
+    const long long gi = base12 + t1 * s1 + t2 * s2 + ca * sA;
+    double r[CFS_MAX_LEVELS];
 #pragma unroll
-  for (int lv = 0; lv < CFS_MAX_LEVELS; ++lv)
-    if (lv < nlev) v = fma(sc.mode == 2 ? 1.0 : __ldg(sc.Wf + kd[sd] * sc.C + lv), r[lv], v);
-  out[h * (N * N) + l] = dev_fast(v, rh, rl);
+    for (int lv = 0; lv < CFS_MAX_LEVELS; ++lv) r[lv] = lv < nlev ? f.ring[(sd ? lev[1][lv] : lev[0][lv]) + gi] : 0.0;
+    double v = 0.0;
+#pragma unroll
+    for (int lv = 0; lv < CFS_MAX_LEVELS; ++lv)
+      if (lv < nlev) v = fma(sd ? wf[1][lv] : wf[0][lv], r[lv], v);
+    out[h * (N * N) + l] = dev_fast(v, rh, rl);
+  }
 }
 
 template <int N>
@@ -220,10 +228,10 @@ int launch_filter_block(const Geometry& g, const StepSched& sc, const FilterBloc
   if (tm) tm->rec(tm->self, 3, 1);
   const unsigned nb = (unsigned)(5 * f.nsub);
   if (n == 32) {
-    k_filter_block_halo<32><<<(unsigned)(15 * f.nsub * ((10 * 32 * 32 + 255) / 256)), 256, 0, st>>>(g, sc, f);
+    k_filter_block_halo<32><<<(unsigned)(15 * f.nsub), 256, 0, st>>>(g, sc, f);
     k_filter_block<32><<<nb, FB_THREADS, fb_smem<32>(), st>>>(g, sc, f);
   } else {
-    k_filter_block_halo<16><<<(unsigned)(15 * f.nsub * ((10 * 16 * 16 + 255) / 256)), 256, 0, st>>>(g, sc, f);
+    k_filter_block_halo<16><<<(unsigned)(15 * f.nsub), 256, 0, st>>>(g, sc, f);
     k_filter_block<16><<<nb, FB_THREADS, fb_smem<16>(), st>>>(g, sc, f);
   }
   if (tm) tm->rec(tm->self, 3, 0);
