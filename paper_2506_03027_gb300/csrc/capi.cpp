@@ -65,6 +65,8 @@ struct cfs_ctx {
   void* Phi = nullptr;
   double* d_W = nullptr;
   double* d_Wf = nullptr;
+  float* d_W32 = nullptr;   // pairs of W for level-difference sums, then pairs of W - W^(0)
+  float* d_W32d = nullptr;
   SubDev* d_subs = nullptr;
   std::vector<SubDev> subs;
   int max_pad = 0, max_own = 0, max_flux = 0;
@@ -685,6 +687,8 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   const int nW = (max_delay + 1) * c->s * c->C, nWf = (max_delay + 1) * c->C;
   c->d_W = (double*)dev_alloc(c, sizeof(double) * nW);
   c->d_Wf = (double*)dev_alloc(c, sizeof(double) * nWf);
+  c->d_W32 = (float*)dev_alloc(c, sizeof(float) * 4 * nW);
+  c->d_W32d = c->d_W32 ? c->d_W32 + 2 * (size_t)nW : nullptr;
   c->d_out = (double*)dev_alloc(c, sizeof(double) * 8);
   c->d_n = (long long*)dev_alloc(c, sizeof(long long));
   c->d_status = (int*)dev_alloc(c, sizeof(int));
@@ -732,7 +736,7 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   c->d_thomas32 = (float*)dev_alloc(c, sizeof(float) * (size_t)(c->Lmax + 1) * 2 * c->Lmax);
   for (void* q : c->owned)
     if (!q) return fail(c, CFS_ENOMEM, "device allocation failed");
-  if (!c->d_n || !c->d_status || !c->ring || !c->buf[0] || !c->buf[1] || !c->Q || (!c->fused && (!c->Wp || !c->Phi)) || !c->d_subs || !c->d_W || !c->d_Wf ||
+  if (!c->d_n || !c->d_status || !c->ring || !c->buf[0] || !c->buf[1] || !c->Q || (!c->fused && (!c->Wp || !c->Phi)) || !c->d_subs || !c->d_W || !c->d_Wf || !c->d_W32 ||
       !c->d_partial || !c->d_out || !c->d_thomas || !c->d_thomas32)
     return fail(c, CFS_ENOMEM, "device allocation failed");
   for (const Block& b : c->blocks)
@@ -799,6 +803,27 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   if (cfs::at_weight_table(c->p.order, max_delay, W.data()) != nW ||
       cfs::filter_extrap_table(c->p.order, max_delay, Wf.data()) != nWf)
     return fail(c, CFS_EINVAL, "coefficient generation failed");
+  // the AT weights for sums over the differences of the delayed levels from the newest one, as
+  // pairs of floats (hi, lo = the rest of the FP64 value): per delay and stage S - 1 (S = sum_l W_l,
+  // summed in a fixed order) and W_1 .. W_{C-1}; then the same for W^(m) - W^(0)
+  std::vector<float> W32(4 * (size_t)nW);
+  auto pair = [&](size_t i, double x) {
+    W32[2 * i] = (float)x;
+    W32[2 * i + 1] = (float)(x - (double)W32[2 * i]);
+  };
+  for (int tab = 0; tab < 2; ++tab)
+    for (int km = 0; km < nW / c->C; ++km) {
+      const double* w = W.data() + (size_t)km * c->C;
+      const double* w0 = W.data() + (size_t)(km - km % c->s) * c->C;  // stage 0 of the same delay
+      double x[CFS_MAX_LEVELS], sum = 0.0;
+      for (int l = 0; l < c->C; ++l) {
+        x[l] = tab ? w[l] - w0[l] : w[l];
+        sum += x[l];
+      }
+      const size_t base = (size_t)tab * nW + (size_t)km * c->C;
+      pair(base, tab ? sum : sum - 1.0);
+      for (int l = 1; l < c->C; ++l) pair(base + l, x[l]);
+    }
   double filt[6] = {1, 0, 0, 0, 0, 0};
   if (c->p.filter && !cfs::pade10_coeffs(c->p.alpha_f, filt)) return fail(c, CFS_EINVAL, "filter coefficients failed");
   c->filt_h[0] = filt[0];
@@ -821,6 +846,7 @@ cfs_status cfs_finalize(cfs_ctx* c, int max_delay) {
   CUDA_TRY(c, cudaMemcpyAsync(c->d_subs, c->subs.data(), sizeof(SubDev) * nsub, cudaMemcpyHostToDevice, st), "upload sub-domains");
   CUDA_TRY(c, cudaMemcpyAsync(c->d_W, W.data(), sizeof(double) * nW, cudaMemcpyHostToDevice, st), "upload weights");
   CUDA_TRY(c, cudaMemcpyAsync(c->d_Wf, Wf.data(), sizeof(double) * nWf, cudaMemcpyHostToDevice, st), "upload weights");
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_W32, W32.data(), sizeof(float) * W32.size(), cudaMemcpyHostToDevice, st), "upload weights");
   CUDA_TRY(c, cudaMemcpyAsync(c->d_thomas, th.data(), sizeof(double) * th.size(), cudaMemcpyHostToDevice, st), "upload filter");
   {
     const int rc = cfs::launch_round_table(c->d_thomas, c->d_thomas32, (long long)th.size(), st);
@@ -1002,6 +1028,8 @@ static cfs_status enqueue_step(cfs_ctx* c, long long n, bool graph) {
   sc.cap = n - c->C + 1;
   sc.mode = (c->algo == 0 || n < c->C) ? 0 : (c->at ? 1 : 2);
   sc.W = c->d_W;
+  sc.W32 = c->d_W32;
+  sc.W32d = c->d_W32d;
   sc.Wf = c->d_Wf;
   sc.LH = nullptr;
   sc.status = c->d_status;

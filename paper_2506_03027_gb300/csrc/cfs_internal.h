@@ -128,6 +128,9 @@ struct StepSched {
   long long cap;         // clamp: k <= n - C + 1
   const int8_t* table;   // SAA delays of this step [nsub][6] (device), or null
   const double* W;       // device: AT halo weights [(k * s + m) * C + l]
+  const float* W32;      // device: the same table for sums over level differences as pairs of floats
+                         // (hi, lo) per entry: entry l = 0 holds sum_l W - 1, entries l >= 1 W_l
+  const float* W32d;     // device: as W32 for the differences W^(m) - W^(0) (learned face halos)
   const double* LH;      // device: learned stage-0 face-halo values [5][Ptot], or null (plain AT)
   const double* Wf;      // device: filter-halo extrapolation weights c(k+1) [k * C + l]
   // CUDA-graph mode: the step index lives in device memory (dn); kernels derive n, mode, cap and

@@ -57,26 +57,33 @@ __device__ __forceinline__ double f2d_fast(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
-// x - ref in FP32 with the accuracy of the FP64 difference rounded once more: x = h + e with h
-// the FP32 truncation of x (exact) and e the remaining 29 mantissa bits scaled by 2^(E-1075);
-// ref = rh + rl given as two floats.  (h - rh) is exact when x and ref are within a factor of two
-// (Sterbenz), so the deviation keeps full FP32 precision however small it is relative to x.
-__device__ __forceinline__ float dev_fast(double x, float rh, float rl) {
+// x = h + r with h the FP32 truncation of x (exact) and r the remaining 29 mantissa bits scaled by
+// 2^(E-1075), rounded once to FP32.  The range rules of d2f_fast hold for h; r is zero when
+// 2^(E-1052) is not a normal float.
+__device__ __forceinline__ void split_fast(double x, float& h, float& r) {
   const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
   const unsigned ahi = hi & 0x7fffffffu, e = ahi >> 20;
   unsigned t = (__funnelshift_l(lo, hi, 3) & 0x7fffffffu) ^ 0x40000000u;
   t = (ahi < 0x38100000u) ? 0u : t;
   t = (ahi >= 0x47f00000u) ? 0x7fc00000u : t;
-  const float h = __uint_as_float(t | (hi & 0x80000000u));
-  // remainder m 2^(E-1075), m = lo & (2^29 - 1), in FP32 arithmetic only: its top 23 and bottom 6
-  // bits become exact floats by writing them as the mantissa under a power of two 2^k and
-  // subtracting 2^k; the sum of the two rounds once.  Zero when 2^(E-1052) is not a normal float.
+  h = __uint_as_float(t | (hi & 0x80000000u));
+  // m 2^(E-1075), m = lo & (2^29 - 1), in FP32 arithmetic only: its top 23 and bottom 6 bits become
+  // exact floats by writing them as the mantissa under a power of two 2^k and subtracting 2^k;
+  // the sum of the two rounds once.
   const unsigned m = lo & 0x1fffffffu;
   const unsigned eb1 = (e - 919u) << 23, eb2 = (e - 925u) << 23;  // 2^(E-1046), 2^(E-1052)
-  float r = (__uint_as_float(eb1 | (m >> 6)) - __uint_as_float(eb1)) +
+  float q = (__uint_as_float(eb1 | (m >> 6)) - __uint_as_float(eb1)) +
             (__uint_as_float(eb2 | (m & 63u)) - __uint_as_float(eb2));
-  r = (e >= 926u) ? r : 0.f;
-  r = (hi & 0x80000000u) ? -r : r;
+  q = (e >= 926u) ? q : 0.f;
+  r = (hi & 0x80000000u) ? -q : q;
+}
+
+// x - ref in FP32 with the accuracy of the FP64 difference rounded once more, ref = rh + rl given
+// as two floats: (h - rh) is exact when x and ref are within a factor of two (Sterbenz), so the
+// deviation keeps full FP32 precision however small it is relative to x.
+__device__ __forceinline__ float dev_fast(double x, float rh, float rl) {
+  float h, r;
+  split_fast(x, h, r);
   return (h - rh) + (r - rl);
 }
 

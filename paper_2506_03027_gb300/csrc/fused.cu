@@ -18,8 +18,10 @@
 //   plane z = G - 2      complete: FP64 low-storage update Q = A Q + dt R, U^(m) = U^(m-1) + B Q.
 // Conversions between FP64 and FP32 use the integer-pipe routines of device_common.cuh.
 // k_halo_prims runs once per asynchronous step: for every halo point a sub-domain reads from a
-// neighbour it applies the AT weights of all s stages to the C delayed levels in FP64 (Eq. 14-15
-// and the buffer updates of Eq. 8 / Table 5) and stores the FP32 primitives per stage.
+// neighbour it applies the AT weights of all s stages to the C delayed levels (Eq. 14-15 and the
+// buffer updates of Eq. 8 / Table 5) -- FP32 sums over the levels' differences from the newest
+// level, in FP64 for the gather entries of connected grids -- and stores the FP32 primitives per
+// stage.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -72,16 +74,14 @@ __device__ __forceinline__ Phys32 phys32(const Physics& ph) {
   return q;
 }
 
-// FP32 primitives (rho, u, v, w, p - p_ref, T, rho E + p - H_ref) from an FP64 conserved state
-// (App. A; p and rho E carried as deviations from the reference state p_ref = 1/(gamma M^2),
-// E_ref = p_ref/(gamma-1), so that FP32 rounding acts on O(1) deviations).
-__device__ __forceinline__ void prims32(const double* u, const Phys32& k, float* w) {
-  const float rho = d2f_fast(u[0]);
+// FP32 primitives (rho, u, v, w, p - p_ref, T, rho E + p - H_ref) from the FP32 conserved values
+// rho, rho u, rho v, rho w and the deviation rho E - E_ref (App. A; p and rho E carried as
+// deviations from the reference state p_ref = 1/(gamma M^2), E_ref = p_ref/(gamma-1), so that FP32
+// rounding acts on O(1) deviations).
+__device__ __forceinline__ void prims32f(float rho, float mx, float my, float mz, float rE, const Phys32& k, float* w) {
   const float ir = __fdividef(1.0f, rho);
-  const float mx = d2f_fast(u[1]), my = d2f_fast(u[2]), mz = d2f_fast(u[3]);
   const float uu = mx * ir, vv = my * ir, ww = mz * ir;
   const float ke = 0.5f * (mx * uu + my * vv + mz * ww);
-  const float rE = dev_fast(u[4], k.Eh, k.El);
   const float p = k.gm1 * (rE - ke);
   w[0] = rho;
   w[1] = uu;
@@ -90,6 +90,11 @@ __device__ __forceinline__ void prims32(const double* u, const Phys32& k, float*
   w[4] = p;
   w[5] = (k.gM2 * p + 1.0f) * ir;  // T
   w[6] = rE + p;                   // rho E + p - H_ref
+}
+
+// The same from an FP64 conserved state.
+__device__ __forceinline__ void prims32(const double* u, const Phys32& k, float* w) {
+  prims32f(d2f_fast(u[0]), d2f_fast(u[1]), d2f_fast(u[2]), d2f_fast(u[3]), dev_fast(u[4], k.Eh, k.El), k, w);
 }
 
 }  // namespace
@@ -178,34 +183,94 @@ __global__ void __launch_bounds__(256) k_halo_prims(Geometry g, Physics ph, Step
     for (int c = 0; c < 7; ++c) Wh[(long long)c * P + o] = w[c];
     return;
   }
-  // AT: U_buf^(m) = sum_l W^(m)_l(k) U^{n-k-l} for every stage m, accumulated in FP64; with the
-  // learned halo, face points start from the network's stage-0 value and add (W^(m) - W^(0)) R
+  // AT: U_buf^(m) = sum_l W^(m)_l(k) U^{n-k-l} for every stage m, written as
+  // S_m U_0 + sum_{l>=1} W^(m)_l (U_l - U_0) with U_l = U^{n-k-l} and S_m = sum_l W^(m)_l, which is 1
+  // up to the rounding of the table (the stage-0 extrapolation weights reproduce constants, the
+  // derivative weights the later stages add sum to zero), and evaluated without FP64 arithmetic:
+  // - each difference U_l - U_0 as an exact pair of floats: U_l = h + r (split_fast: h its FP32
+  //   truncation), U_0 = h0 + l0, (h - h0) exact when the levels are within a factor of two;
+  // - the weights as pairs of floats (table W32: S_m - 1, then W^(m)_1 .. W^(m)_{C-1});
+  // - products of the high parts split exactly with an FMA and summed with TwoSum: the weights
+  //   of large delays alternate in sign (sum |W| about 1,400 at k = 4 against 1 for the result),
+  //   so plain FP32 sums would lose that factor; compensated, the sum has the accuracy of the
+  //   FP64 one before its final rounding to the FP32 primitives.
+  // With the learned halo, face points start from the network's stage-0 value and add the same
+  // sums with W^(m) - W^(0) (table W32d).
   const bool learned = sc.LH && ((int)(ci < 0 || ci >= d.sx) + (int)(cj < 0 || cj >= d.sy) + (int)(ck < 0 || ck >= d.sz) == 1);
-  double acc[S][5];
+  const int C = sc.C;
+  double r[CFS_MAX_LEVELS][5];
 #pragma unroll
-  for (int m = 0; m < S; ++m)
+  for (int l = 0; l < CFS_MAX_LEVELS; ++l)
+    if (l < C) {
+      const double* src = ring + (long long)slot(l) * lvN;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) acc[m][v] = learned ? sc.LH[(long long)v * g.Ptot + d.pbase + t] : 0.0;
-  for (int l = 0; l < sc.C; ++l) {
-    const double* src = ring + (long long)slot(l) * lvN;
-    double r[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) r[v] = src[v * d.bN + gi];
-    const double w0 = learned ? __ldg(sc.W + (kd * S) * sc.C + l) : 0.0;
-#pragma unroll
-    for (int m = 0; m < S; ++m) {
-      if (learned && m == 0) continue;
-      const double wl = __ldg(sc.W + (kd * S + m) * sc.C + l) - w0;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) acc[m][v] = fma(wl, r[v], acc[m][v]);
+      for (int v = 0; v < 5; ++v) r[l][v] = src[v * d.bN + gi];
     }
+  float h0[5], l0[5], ah[CFS_MAX_LEVELS][5], al[CFS_MAX_LEVELS][5];  // U_l - U_0 = ah[l] + al[l]
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    h0[v] = d2f_fast(r[0][v]);
+    l0[v] = dev_fast(r[0][v], h0[v], 0.f);
   }
 #pragma unroll
-  for (int m = 0; m < S; ++m) {
-    float w[7];
-    prims32(acc[m], k32, w);
+  for (int l = 1; l < CFS_MAX_LEVELS; ++l)
+    if (l < C)
 #pragma unroll
-    for (int c = 0; c < 7; ++c) Wh[(long long)(m * 7 + c) * P + o] = w[c];
+      for (int v = 0; v < 5; ++v) {
+        float h, q;
+        split_fast(r[l][v], h, q);
+        ah[l][v] = __fsub_rn(h, h0[v]);
+        al[l][v] = __fsub_rn(q, l0[v]);
+      }
+  // the value the sums are added to: U_0, or the network's stage-0 value (rho, momenta as pairs
+  // of floats, rho E as its deviation from E_ref)
+  float bh[4], bl[4], be;
+  if (learned) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const double x = sc.LH[(long long)v * g.Ptot + d.pbase + t];
+      bh[v] = d2f_fast(x);
+      bl[v] = dev_fast(x, bh[v], 0.f);
+    }
+    be = dev_fast(sc.LH[4LL * g.Ptot + d.pbase + t], k32.Eh, k32.El);
+  } else {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      bh[v] = h0[v];
+      bl[v] = l0[v];
+    }
+    be = dev_fast(r[0][4], k32.Eh, k32.El);
+  }
+  const float2* __restrict__ wt = (const float2*)(learned ? sc.W32d : sc.W32) + (long long)kd * S * C;
+#pragma unroll
+  for (int m = 0; m < S; ++m) {
+    float2 c[CFS_MAX_LEVELS];
+#pragma unroll
+    for (int l = 0; l < CFS_MAX_LEVELS; ++l) c[l] = l < C ? __ldg(wt + m * C + l) : make_float2(0.f, 0.f);
+    float dl[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      float sh = 0.f, st = __fmul_rn(c[0].x, h0[v]);  // running sum and its error terms
+#pragma unroll
+      for (int l = 1; l < CFS_MAX_LEVELS; ++l)
+        if (l < C) {
+          const float p = __fmul_rn(c[l].x, ah[l][v]);
+          const float pe = __fmaf_rn(c[l].x, ah[l][v], -p);  // exact: p + pe = c.x * ah
+          const float s2 = __fadd_rn(sh, p);                  // TwoSum(sh, p)
+          const float bv = __fsub_rn(s2, sh);
+          const float se = __fadd_rn(__fsub_rn(sh, __fsub_rn(s2, bv)), __fsub_rn(p, bv));
+          sh = s2;
+          st = __fadd_rn(st, __fadd_rn(se, pe));
+          st = __fmaf_rn(c[l].x, al[l][v], st);
+          st = __fmaf_rn(c[l].y, ah[l][v], st);
+        }
+      dl[v] = (learned && m == 0) ? 0.f : __fadd_rn(sh, st);
+    }
+    float w[7];
+    prims32f(bh[0] + (bl[0] + dl[0]), bh[1] + (bl[1] + dl[1]), bh[2] + (bl[2] + dl[2]), bh[3] + (bl[3] + dl[3]),
+             be + dl[4], k32, w);
+#pragma unroll
+    for (int c7 = 0; c7 < 7; ++c7) Wh[(long long)(m * 7 + c7) * P + o] = w[c7];
   }
 }
 
