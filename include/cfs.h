@@ -55,7 +55,9 @@ typedef struct {
   int filter;        /* 1: tenth-order Pade filter (coefficient alpha_f) once per step */
   double alpha_f;
   int precision;     /* 0: FP64 throughout; 1: FP32 derivative/flux/filter intermediates with
-                        FP64 state, RK accumulation and AT coefficient application */
+                        FP64 state and RK accumulation; the AT halo values are summed to FP64
+                        accuracy (compensated FP32 sums over the delayed levels' differences,
+                        FP64 sums for the filter halos) before their rounding to FP32 */
   int compact;       /* 1: the flux divergence by the sixth-order compact scheme of Eq. 2 (alpha =
                         1/3, a = 14/9, b = 1/9), one tridiagonal solve per sub-domain line, closed by
                         the explicit sixth-order central difference at the first halo point (halo
