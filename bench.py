@@ -61,10 +61,10 @@ HBM_GBS_FALLBACK = 6800.0
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each kernel kind, with the sha1 of
 # the flux kernel's source they were taken from (kernels_sha1; null once it changes); filled
 # from profiles/.
-TRAFFIC = {"source_sha1": "b28dc3501138b4889ce49f889d2dba9ffc46cffc",
-           # k_flux<double,3>: 92.7 MB read + 82.0 MB written per launch in an ncu capture of the
+TRAFFIC = {"source_sha1": "c488e6aad06093ada1bf5e2b117f15b1ca3752b9",
+           # k_flux<double,3>: 92.56 MB read + 81.52 MB written per launch in an ncu capture of the
            # 96^3 case (27 sub-domains of 32^3), x 64/27 for the 64 sub-domains of 128^3
-           "bytes_per_launch": {"flux": 414.1e6}}
+           "bytes_per_launch": {"flux": 412.6e6}}
 
 
 def kernels_sha1(root: str = ROOT) -> str:
