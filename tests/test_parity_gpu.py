@@ -288,8 +288,8 @@ def test_fp32_form_largest_delays():
     levels from the newest one.  The weights of large delays alternate in sign (sum |W| about
     1,400 at k = 4 against 25 at k = 0), so a plain FP32 sum would lose that factor; with the
     largest delays of the tables (SAA 0..4) the form stays within its bound of the oracle.  (At CFL
-    0.25 on this grid, SAA with delays of 3 and 4 amplifies per-step rounding about 3x every 4
-    steps whatever the precision -- the FP64 path reaches 2e-11 of the oracle after 24 steps -- so
+    0.25 on this grid, SAA with delays of 3 and 4 amplifies per-step rounding 2-6x every 4 steps
+    whatever the precision -- the FP64 path reaches 2e-11 of the oracle after 24 steps -- so
     the run is taken at the CFL of the other SAA parity tests.)"""
     c = small_tgv("SAA", kmax=4, cfl=0.05)
     d = I.saa_delays(c, 24)
